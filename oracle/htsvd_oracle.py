@@ -1,0 +1,548 @@
+"""FP64 CPU oracle for the Haar-tSVD denoising core (Kong, Zhang & Yang, arXiv 2508.10307).
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import or execute this
+module; only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg use it. It shares no code with the CUDA path.
+
+Every function restates a step of the paper in plain numpy, float64 unless the
+quantity is an exact integer, without blocking or fusion beyond what the
+definition states:
+
+* grouping by green-channel-prior block matching       -- Sec. III-A, Eq. (GCP distance)
+* global t-SVD bases from all reference patches        -- Sec. III-B.1, Eqs. (BCR nonlocal SVD), Alg. 1 Step 2(1)
+* t-product via mode-3 FFT                               -- Sec. II-C, Def. T-product, Eqs. (FFT product, FFT third mode)
+* Haar matrix                                            -- Sec. II-D, Eqs. (H_2), (H_2N)
+* forward transform, hard threshold, inverse           -- Sec. III-B.2, Eqs. (forward transform), (hard thresholding), (backward transform)
+* aggregation                                            -- Sec. II-B, Eq. (aggregation); Alg. 1 Step 3
+* circulant eigen-analysis and sigma adjustment         -- Sec. III-D, Eqs. (other eigenvalue), (adjust noise level)
+* eigenvalue noise-level estimate (patch-covariance rule, used in place of the paper's CNN)
+
+Readings where the paper is silent or ambiguous (each is listed in the design doc):
+  R1 distance = exact integer SSD on the chosen plane; the "avg" branch uses the
+     R+G+B sum plane (SSD = 9x the SSD of the average, same order).
+  R2 the GCP test is evaluated on the reference patch with raw L2 norms, in
+     float64 as (gamma*gamma)*|G|^2 >= |R|^2 and likewise for B.
+  R3 reference grid per axis = {0, s, 2s, ...} U {n - ps}.
+  R4 window = W x W candidate top-left positions, start clamped so the window
+     lies inside the image; all positions if fewer than W exist.
+  R5 slot 0 is the reference; slots 1..K-1 are the K-1 smallest (SSD, y*W+x)
+     keys among the other candidates (ties -> lowest linear index).
+  R6 global bases: per Fourier slice f, U_f = eigenvectors of sum_r P_f P_f^H,
+     V_f = eigenvectors of sum_r P_f^H P_f (uncentred, reference patches),
+     eigenvalues descending, each eigenvector's largest-modulus entry made real
+     positive (ties within 1e-6 relative -> lowest index); slice C-f := conj(slice f).
+  R7 coefficients along the group mode are H_K applied to each K-fibre
+     (U_Haar = H_K^T); the inverse is H_K^T.
+  R8 tau = tau_mult * sigma; tau_mult <= 0 means sqrt(2 ln(C K ps^2)); the
+     threshold applies to every coefficient and |S| == tau is kept.
+  R9 aggregation weights: 1 per group (uniform), or 1/max(1, #kept) (sparsity),
+     or caller-given per-group weights.
+  R10 noise estimate: covariance of reference patches, ascending eigenvalues,
+     r* = max{r : mean(l_1..r) <= 1.02 median(l_1..r)}, sigma = sqrt(mean(l_1..r*)).
+  R11 adaptive adjustment: groups of every 8th reference per axis; rank
+     a = 1 + #{f : lambda_f < lambda_{K/2}}; majority of a <= gamma_rank divides
+     sigma by beta.
+  R12 float inputs: matching, bases and sigma use q = clip(rint(x)); the
+     transforms use x.
+
+Parity pins for every function are in tests/test_oracle_pins.py.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from numpy.lib.stride_tricks import sliding_window_view
+
+
+# --------------------------------------------------------------------------- params
+
+@dataclass
+class Params:
+    ps: int = 8
+    stride: int = 3
+    window: int = 18
+    K: int = 32
+    tau_mult: float = 0.0          # <= 0 -> sqrt(2 ln(C K ps^2))   (Sec. IV-A)
+    match_mode: str = "auto"       # auto | gcp | full | gray
+    gcp_gamma: float = 1.2         # Sec. III-A
+    agg_mode: str = "uniform"      # uniform | sparsity
+    adapt: bool = False            # Sec. III-D adjustment
+    beta: float = 1.2
+    rank_gamma: int = 0            # 0 -> round(13 K / 32)
+
+    @staticmethod
+    def of(d: dict | "Params" | None) -> "Params":
+        if d is None:
+            return Params()
+        if isinstance(d, Params):
+            return d
+        return Params(**d)
+
+
+def tau_multiplier(p: Params, C: int) -> float:
+    """Universal threshold multiplier sqrt(2 log(c K ps^2)) (Sec. IV-A), natural log."""
+    if p.tau_mult > 0:
+        return float(p.tau_mult)
+    return math.sqrt(2.0 * math.log(C * p.K * p.ps * p.ps))
+
+
+def rank_gamma(p: Params) -> int:
+    return p.rank_gamma if p.rank_gamma > 0 else (13 * p.K + 16) // 32
+
+
+# --------------------------------------------------------------------------- Haar
+
+def haar_matrix(K: int) -> np.ndarray:
+    """H_K built recursively from H_2 (Sec. II-D):
+    H_2N = 1/sqrt(2) [ H_N kron [1, 1] ; I_N kron [1, -1] ]."""
+    if K < 2 or K & (K - 1):
+        raise ValueError("K must be a power of two >= 2")
+    H = np.array([[1.0, 1.0], [1.0, -1.0]]) / math.sqrt(2.0)
+    n = 2
+    while n < K:
+        top = np.kron(H, np.array([[1.0, 1.0]]))
+        bot = np.kron(np.eye(n), np.array([[1.0, -1.0]]))
+        H = np.vstack([top, bot]) / math.sqrt(2.0)
+        n *= 2
+    return H
+
+
+# --------------------------------------------------------------------------- geometry
+
+def reference_positions(n: int, ps: int, stride: int) -> np.ndarray:
+    """Reading R3: {0, s, 2s, ...} U {n - ps} along one axis."""
+    last = n - ps
+    pos = list(range(0, last + 1, stride))
+    if pos[-1] != last:
+        pos.append(last)
+    return np.array(pos, dtype=np.int64)
+
+
+def window_range(r: int, n: int, ps: int, W: int) -> tuple[int, int]:
+    """Reading R4: (start, count) of candidate top-left positions along one axis."""
+    npos = n - ps + 1
+    if npos <= W:
+        return 0, npos
+    start = min(max(r - (W - 1) // 2, 0), npos - W)
+    return start, W
+
+
+# --------------------------------------------------------------------------- grouping (Sec. III-A)
+
+def match_planes(img: np.ndarray):
+    """Integer planes the distance of Eq. (GCP distance) is taken on.
+    Returns (green_or_gray, rgb_sum); rgb_sum is None for one channel."""
+    x = img.astype(np.int64)
+    if x.shape[2] == 1:
+        return x[:, :, 0], None
+    return x[:, :, 1], x[:, :, 0] + x[:, :, 1] + x[:, :, 2]
+
+
+def gcp_uses_green(img: np.ndarray, ry: int, rx: int, ps: int, gamma: float) -> bool:
+    """Eq. (GCP distance) condition on the reference patch:
+    ||P^G|| >= max(||P^R||/gamma, ||P^B||/gamma), evaluated as (gamma*gamma)*|G|^2 >= |R|^2, |B|^2."""
+    p = img[ry:ry + ps, rx:rx + ps, :].astype(np.int64)
+    r2, g2, b2 = (int((p[:, :, c] ** 2).sum()) for c in range(3))
+    g = float(gamma) * float(gamma)
+    return (g * float(g2) >= float(r2)) and (g * float(g2) >= float(b2))
+
+
+def _match_plane_ssd(planes, ry, rxs, y0, ny, x0s, nx, ps):
+    """SSD of the reference patches at (ry, rxs[n]) against every candidate of their windows:
+    (n, ny, nx) int64, summed over the given integer planes."""
+    ssd = np.zeros((len(rxs), ny, nx), dtype=np.int64)
+    cols = x0s[:, None] + np.arange(nx)[None, :]                       # (n, nx)
+    for pl in planes:
+        views = sliding_window_view(pl, (ps, ps))                       # [y, x, i, j]
+        cand = views[y0:y0 + ny][:, cols]                               # (ny, n, nx, i, j)
+        ref = views[ry, rxs]                                            # (n, i, j)
+        d = cand - ref[None, :, None]
+        ssd += np.einsum("ynxij,ynxij->nyx", d, d)
+    return ssd
+
+
+def _match_row(img: np.ndarray, ry: int, rxs: np.ndarray, p: Params):
+    """Grouping for the references (ry, rxs[n]) of one reference row (Alg. 1 Step 1)."""
+    H, Wd, C = img.shape
+    ps, K = p.ps, p.K
+    y0, ny = window_range(ry, H, ps, p.window)
+    xw = [window_range(int(rx), Wd, ps, p.window) for rx in rxs]
+    x0s = np.array([a for a, _ in xw], dtype=np.int64)
+    nx = xw[0][1]
+    if ny * nx < K:
+        raise ValueError("search window holds fewer than K candidates")
+    mode = p.match_mode
+    if mode == "auto":
+        mode = "gray" if C == 1 else "gcp"
+    x = img.astype(np.int64)
+    n = len(rxs)
+    if mode == "full":
+        ssd = _match_plane_ssd([x[:, :, c] for c in range(C)], ry, rxs, y0, ny, x0s, nx, ps)
+        green = np.zeros(n, dtype=bool)
+    elif C == 1 or mode == "gray":
+        ssd = _match_plane_ssd([x[:, :, 0] if C == 1 else x[:, :, 1]], ry, rxs, y0, ny, x0s, nx, ps)
+        green = np.ones(n, dtype=bool)
+    else:
+        green = np.array([gcp_uses_green(img, ry, int(rx), ps, p.gcp_gamma) for rx in rxs])
+        g, s = match_planes(img)
+        ssd = np.where(green[:, None, None],
+                       _match_plane_ssd([g], ry, rxs, y0, ny, x0s, nx, ps),
+                       _match_plane_ssd([s], ry, rxs, y0, ny, x0s, nx, ps))
+    lin = ((y0 + np.arange(ny))[None, :, None] * Wd + (x0s[:, None, None] + np.arange(nx)[None, None, :]))
+    lin = np.broadcast_to(lin, ssd.shape).reshape(n, -1)
+    ssd = ssd.reshape(n, -1)
+    ref_lin = ry * Wd + rxs
+    idx = np.empty((n, K), dtype=np.int64)
+    dist = np.empty((n, K), dtype=np.int64)
+    for r in range(n):
+        keep = lin[r] != ref_lin[r]
+        cl, cs = lin[r][keep], ssd[r][keep]
+        order = np.lexsort((cl, cs))[:K - 1]                 # ascending SSD, ties -> lowest index
+        idx[r, 0], dist[r, 0] = ref_lin[r], 0
+        idx[r, 1:], dist[r, 1:] = cl[order], cs[order]
+    return idx, dist, green
+
+
+def block_match_one(img: np.ndarray, ry: int, rx: int, p: Params):
+    """Group of one reference patch: its own position in slot 0, then the K-1 nearest other
+    candidates of its search window by (SSD, linear index).  Returns (linear indices[K], ssd[K], uses_green)."""
+    idx, dist, green = _match_row(img, int(ry), np.array([rx], dtype=np.int64), p)
+    return idx[0], dist[0], bool(green[0])
+
+
+def block_match(img: np.ndarray, p: Params):
+    """Alg. 1 Step 1 for every reference patch, row-major over the reference grid.
+    Returns idx (N_ref, K) int64 linear indices y*W+x and the per-reference green flags."""
+    H, Wd, _ = img.shape
+    ys = reference_positions(H, p.ps, p.stride)
+    xs = reference_positions(Wd, p.ps, p.stride)
+    rows = [_match_row(img, int(ry), xs, p) for ry in ys]
+    return np.concatenate([r[0] for r in rows]), np.concatenate([r[2] for r in rows])
+
+
+def gather_groups(x: np.ndarray, idx: np.ndarray, ps: int) -> np.ndarray:
+    """Stack the K patches named by each row of idx: (n, K, ps, ps, C) float64."""
+    H, Wd, C = x.shape
+    views = sliding_window_view(x.astype(np.float64), (ps, ps), axis=(0, 1))  # [y, x, C, i, j]
+    g = views[idx // Wd, idx % Wd]                                              # [n, K, C, i, j]
+    return np.ascontiguousarray(np.moveaxis(g, 2, -1))
+
+
+def reference_patches(x: np.ndarray, p: Params) -> np.ndarray:
+    """All reference patches (N_ref, ps, ps, C) in reference-grid order."""
+    H, Wd, C = x.shape
+    ys = reference_positions(H, p.ps, p.stride)
+    xs = reference_positions(Wd, p.ps, p.stride)
+    lin = (ys[:, None] * Wd + xs[None, :]).ravel()
+    return gather_groups(x, lin[:, None], p.ps)[:, 0]
+
+
+# --------------------------------------------------------------------------- t-product algebra (Sec. II-C)
+
+def bcirc(A: np.ndarray) -> np.ndarray:
+    """Block circulant matrix of the frontal slices A[:, :, k] (Sec. II-C)."""
+    n1, n2, n3 = A.shape
+    B = np.zeros((n1 * n3, n2 * n3), dtype=A.dtype)
+    for i in range(n3):
+        for j in range(n3):
+            B[i * n1:(i + 1) * n1, j * n2:(j + 1) * n2] = A[:, :, (i - j) % n3]
+    return B
+
+
+def t_transpose(A: np.ndarray) -> np.ndarray:
+    """Tensor transpose: each frontal slice transposed, slices 2..n3 in reverse order,
+    so that bcirc(A^T) = bcirc(A)^T."""
+    n3 = A.shape[2]
+    return np.stack([A[:, :, (-k) % n3].T for k in range(n3)], axis=2)
+
+
+def t_product_bcirc(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Definition T-product: bcirc(C) = bcirc(A) bcirc(B); C is read off the first block column."""
+    n1, _, n3 = A.shape
+    n2 = B.shape[1]
+    first_col = bcirc(A) @ np.concatenate([B[:, :, k] for k in range(n3)], axis=0)
+    return np.stack([first_col[k * n1:(k + 1) * n1] for k in range(n3)], axis=2).reshape(n1, n2, n3)
+
+
+def t_product_fft(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """T-product computed slice-wise after an FFT along mode 3 (Eqs. FFT product, FFT third mode)."""
+    AF = np.fft.fft(A, axis=2)
+    BF = np.fft.fft(B, axis=2)
+    CF = np.einsum("abk,bck->ack", AF, BF)
+    return np.fft.ifft(CF, axis=2).real
+
+
+# --------------------------------------------------------------------------- global bases (Sec. III-B.1)
+
+def canonical_eigvecs(A: np.ndarray):
+    """Eigenpairs of a Hermitian matrix, eigenvalues descending, each eigenvector scaled by a
+    unit phase so its largest-modulus entry (lowest index within 1e-6 relative) is real positive."""
+    w, Q = np.linalg.eigh(A)
+    w, Q = w[::-1].copy(), Q[:, ::-1].copy()
+    for c in range(Q.shape[1]):
+        mod = np.abs(Q[:, c])
+        a = int(np.nonzero(mod >= mod.max() * (1.0 - 1e-6))[0][0])
+        Q[:, c] *= np.conj(Q[a, c]) / abs(Q[a, c])
+    return w, Q
+
+
+def global_basis(ref_patches: np.ndarray):
+    """Global projections U, V of Eq. (BCR nonlocal SVD simplified), read as the 2-D SVD of the
+    reference patches per Fourier slice (reading R6).  Returns complex (C, ps, ps) arrays
+    U_F, V_F of the Fourier slices, plus the eigenvalues."""
+    C = ref_patches.shape[-1]
+    PF = np.fft.fft(ref_patches.astype(np.float64), axis=-1)      # (N, ps, ps, C)
+    ps = ref_patches.shape[1]
+    U = np.zeros((C, ps, ps), dtype=np.complex128)
+    V = np.zeros((C, ps, ps), dtype=np.complex128)
+    lu = np.zeros((C, ps))
+    lv = np.zeros((C, ps))
+    for f in range(C // 2 + 1):
+        X = PF[..., f]                                  # (N, a, b)
+        Xr = X.transpose(1, 0, 2).reshape(ps, -1)       # rows a against (n, b)
+        Xc = X.transpose(2, 0, 1).reshape(ps, -1)       # columns b against (n, a)
+        A = Xr @ Xr.conj().T                            # sum_r P_f P_f^H   (rows)
+        B = Xc.conj() @ Xc.T                            # sum_r P_f^H P_f   (columns)
+        lu[f], U[f] = canonical_eigvecs(A)
+        lv[f], V[f] = canonical_eigvecs(B)
+    for f in range(C // 2 + 1, C):
+        U[f], V[f] = U[C - f].conj(), V[C - f].conj()
+        lu[f], lv[f] = lu[C - f], lv[C - f]
+    return U, V, lu, lv
+
+
+def basis_gap(lam: np.ndarray) -> float:
+    """Smallest relative gap between consecutive eigenvalues (degeneracy check of reading R6)."""
+    top = max(abs(lam.max()), 1e-300)
+    return float(np.min(np.abs(np.diff(np.sort(lam)))) / top) if lam.size > 1 else 1.0
+
+
+# --------------------------------------------------------------------------- group transform (Sec. III-B.2)
+
+def patch_forward(G: np.ndarray, U: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """U^T * P * V for every patch P = G[..., k, :, :, :] (t-products in the Fourier domain):
+    S_f = U_f^H P_f V_f, then the inverse FFT along the channel mode."""
+    GF = np.fft.fft(G, axis=-1)
+    SF = np.empty_like(GF)
+    for f in range(GF.shape[-1]):
+        Y = np.tensordot(GF[..., f], U[f].conj(), axes=([-2], [0]))     # (..., b, i) = (U_f^H P_f)^T
+        SF[..., f] = np.tensordot(Y, V[f], axes=([-2], [0]))            # (U_f^H P_f) V_f
+    return np.fft.ifft(SF, axis=-1).real
+
+
+def patch_inverse(S: np.ndarray, U: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """U * S * V^T per patch: P_f = U_f S_f V_f^H."""
+    SF = np.fft.fft(S, axis=-1)
+    GF = np.empty_like(SF)
+    for f in range(SF.shape[-1]):
+        Y = np.tensordot(SF[..., f], U[f].T, axes=([-2], [0]))          # (..., j, a) = (U_f S_f)^T
+        GF[..., f] = np.tensordot(Y, V[f].conj().T, axes=([-2], [0]))   # (U_f S_f) V_f^H
+    return np.fft.ifft(GF, axis=-1).real
+
+
+def forward_transform(G: np.ndarray, U, V, H: np.ndarray) -> np.ndarray:
+    """Eq. (forward transform): S = U^T * G * V x_4 U_Haar^T, with coefficient m = sum_k H[m,k] (.)_k.
+    G has shape (..., K, ps, ps, C)."""
+    T = patch_forward(G, U, V)
+    return np.moveaxis(np.tensordot(H, T, axes=([1], [-4])), 0, -4)     # sum_k H[m, k] T_k
+
+
+def inverse_transform(S: np.ndarray, U, V, H: np.ndarray) -> np.ndarray:
+    """Eq. (backward transform) read as the exact inverse (reading R7): x_4 H_K^T then U * . * V^T."""
+    T = np.moveaxis(np.tensordot(H.T, S, axes=([1], [-4])), 0, -4)   # sum_m H[m, k] S_m
+    return patch_inverse(T, U, V)
+
+
+def hard_threshold_mask(S: np.ndarray, tau: float) -> np.ndarray:
+    """Eq. (hard thresholding): keep |S| >= tau."""
+    return np.abs(S) >= tau
+
+
+# --------------------------------------------------------------------------- aggregation (Eq. aggregation)
+
+def aggregate(shape, idx: np.ndarray, Ghat: np.ndarray, w: np.ndarray, ps: int):
+    """Weighted write-back of every estimated patch: num[p] += w_g Ghat, den[p] += w_g."""
+    H, Wd, C = shape
+    yy, xx = idx // Wd, idx % Wd                                        # (n, K)
+    ii, jj = np.mgrid[0:ps, 0:ps]
+    pix = ((yy[:, :, None, None] + ii) * Wd + (xx[:, :, None, None] + jj)).ravel()
+    wk = np.broadcast_to(w[:, None, None, None], (w.size, idx.shape[1], ps, ps)).ravel()
+    num = np.stack([np.bincount(pix, weights=(Ghat[..., c] * w[:, None, None, None]).ravel(),
+                                minlength=H * Wd) for c in range(C)], axis=-1).reshape(H, Wd, C)
+    den = np.bincount(pix, weights=wk, minlength=H * Wd).reshape(H, Wd)
+    return num, den
+
+
+# --------------------------------------------------------------------------- full denoiser (Alg. 1)
+
+@dataclass
+class Result:
+    out: np.ndarray
+    idx: np.ndarray
+    tau: float
+    U: np.ndarray
+    V: np.ndarray
+    weights: np.ndarray
+    masks: np.ndarray | None = None       # (n, K, ps, ps, C) bool
+    coeffs: np.ndarray | None = None      # |S| values, for guard-band accounting
+    den: np.ndarray | None = None
+    extra: dict = field(default_factory=dict)
+
+
+def _as_quantised(x: np.ndarray) -> np.ndarray:
+    if x.dtype == np.uint8:
+        return x
+    return np.clip(np.rint(x.astype(np.float64)), 0, 255).astype(np.uint8)
+
+
+def denoise(x: np.ndarray, sigma: float, params=None, *, idx=None, weights=None,
+            keep_masks=False, keep_coeffs=False, chunk=2048) -> Result:
+    """Alg. 1: grouping, global bases, forward transform, hard threshold, inverse, aggregation.
+
+    x: (H, W, C) uint8 or float image on the [0, 255] scale.  For float input the matching and the
+    bases use the quantised image (reading R12) and the transforms use x itself."""
+    p = Params.of(params)
+    if x.ndim == 2:
+        x = x[:, :, None]
+    H, Wd, C = x.shape
+    q = _as_quantised(x)
+    if idx is None:
+        idx, _ = block_match(q, p)
+    U, V, _, _ = global_basis(reference_patches(q, p))
+    Hk = haar_matrix(p.K)
+    tau = tau_multiplier(p, C) * float(sigma)
+    xf = x.astype(np.float64)
+    n = idx.shape[0]
+    w = np.ones(n) if weights is None else np.asarray(weights, dtype=np.float64)
+    num = np.zeros((H, Wd, C))
+    den = np.zeros((H, Wd))
+    masks = np.zeros((n, p.K, p.ps, p.ps, C), dtype=bool) if keep_masks else None
+    coeffs = np.zeros((n, p.K, p.ps, p.ps, C)) if keep_coeffs else None
+    w_out = w.copy()
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        G = gather_groups(xf, idx[a:b], p.ps)
+        S = forward_transform(G, U, V, Hk)
+        m = hard_threshold_mask(S, tau)
+        if weights is None and p.agg_mode == "sparsity":
+            w_out[a:b] = 1.0 / np.maximum(1, m.reshape(b - a, -1).sum(axis=1))
+        Ghat = inverse_transform(S * m, U, V, Hk)
+        nu, de = aggregate((H, Wd, C), idx[a:b], Ghat, w_out[a:b], p.ps)
+        num += nu
+        den += de
+        if keep_masks:
+            masks[a:b] = m
+        if keep_coeffs:
+            coeffs[a:b] = np.abs(S)
+    out = num / den[:, :, None]
+    return Result(out=out, idx=idx, tau=tau, U=U, V=V, weights=w_out, masks=masks,
+                  coeffs=coeffs, den=den)
+
+
+# --------------------------------------------------------------------------- frozen-mask linear map and its adjoint
+
+def denoise_fixed(x: np.ndarray, idx: np.ndarray, masks: np.ndarray, U, V, w: np.ndarray, ps: int):
+    """The denoiser with grouping, bases and masks held fixed: out = N(x) / D,
+    N(x) = sum_g w_g Scatter_g T^-1 (M_g . T Gather_g x), D = sum_g w_g Scatter_g 1.  Linear in x."""
+    if x.ndim == 2:
+        x = x[:, :, None]
+    H, Wd, C = x.shape
+    K = idx.shape[1]
+    Hk = haar_matrix(K)
+    G = gather_groups(x.astype(np.float64), idx, ps)
+    Ghat = inverse_transform(forward_transform(G, U, V, Hk) * masks, U, V, Hk)
+    num, den = aggregate((H, Wd, C), idx, Ghat, w, ps)
+    return num / den[:, :, None], den
+
+
+def denoise_fixed_vjp(x: np.ndarray, gout: np.ndarray, idx: np.ndarray, masks: np.ndarray, U, V,
+                      w: np.ndarray, ps: int):
+    """Adjoint of denoise_fixed at x for cotangent gout.
+    d/dx  = sum_g w_g Gather_g^T T^T (M_g . T Gather_g (gout / D))
+    d/dw_g = sum over g's patches of (gout/D)[q] * (Ghat_g[q] - out[q])."""
+    if x.ndim == 2:
+        x = x[:, :, None]
+    if gout.ndim == 2:
+        gout = gout[:, :, None]
+    H, Wd, C = x.shape
+    K = idx.shape[1]
+    Hk = haar_matrix(K)
+    out, den = denoise_fixed(x, idx, masks, U, V, w, ps)
+    r = gout.astype(np.float64) / den[:, :, None]
+    Gr = gather_groups(r, idx, ps)
+    back = inverse_transform(forward_transform(Gr, U, V, Hk) * masks, U, V, Hk)
+    gx, _ = aggregate((H, Wd, C), idx, back, w, ps)
+    Gx = gather_groups(x.astype(np.float64), idx, ps)
+    Ghat = inverse_transform(forward_transform(Gx, U, V, Hk) * masks, U, V, Hk)
+    Gout = gather_groups(out, idx, ps)
+    gw = ((Ghat - Gout) * Gr).reshape(idx.shape[0], -1).sum(axis=1)
+    return gx, gw
+
+
+# --------------------------------------------------------------------------- noise level (Sec. III-D + reading R10/R11)
+
+def patch_covariance(q: np.ndarray, p: Params) -> np.ndarray:
+    P = reference_patches(q, p).reshape(-1, p.ps * p.ps * q.shape[2])
+    mu = P.mean(axis=0)
+    return P.T @ P / P.shape[0] - np.outer(mu, mu)
+
+
+def sigma_from_eigenvalues(lam: np.ndarray) -> float:
+    """Reading R10: the largest leading run of ascending eigenvalues whose mean stays within 2% of
+    its median is taken as the noise subspace; sigma = sqrt(mean of that run)."""
+    lam = np.sort(lam)
+    rstar = 1
+    for r in range(1, lam.size + 1):
+        if lam[:r].mean() <= 1.02 * np.median(lam[:r]):
+            rstar = r
+    return float(math.sqrt(max(lam[:rstar].mean(), 0.0)))
+
+
+def circulant_eigenvalues(G: np.ndarray) -> np.ndarray:
+    """Eigenvalues of circ(G) circ(G)^T in closed form: lambda_f = || sum_m p_m exp(-2 pi i f m / K) ||^2
+    (Sec. III-B.2; lambda_0 = ||sum p||^2 is Eq. (first eigen), lambda_{K/2} is Eq. (other eigenvalue))."""
+    K = G.shape[0]
+    P = G.reshape(K, -1).astype(np.float64)
+    F = np.fft.fft(P, axis=0)
+    return (np.abs(F) ** 2).sum(axis=1)
+
+
+def rank_position(G: np.ndarray) -> int:
+    """a = rank of lambda_hat = lambda_{K/2} among the K eigenvalues in ascending order (Sec. III-D)."""
+    lam = circulant_eigenvalues(G)
+    K = G.shape[0]
+    return 1 + int(np.sum(lam < lam[K // 2]))
+
+
+def estimate_sigma(x: np.ndarray, params=None, return_details=False):
+    """Noise level from the patch covariance (reading R10), optionally adjusted by the
+    eigen-rank vote of Eq. (adjust noise level) over sampled groups (reading R11)."""
+    p = Params.of(params)
+    if x.ndim == 2:
+        x = x[:, :, None]
+    q = _as_quantised(x)
+    lam = np.linalg.eigvalsh(patch_covariance(q, p))
+    sigma = sigma_from_eigenvalues(lam)
+    det = {"lam": lam, "sigma_est": sigma}
+    if p.adapt:
+        H, Wd, C = q.shape
+        ys = reference_positions(H, p.ps, p.stride)[::8]
+        xs = reference_positions(Wd, p.ps, p.stride)[::8]
+        gam = rank_gamma(p)
+        low = high = 0
+        ranks = []
+        for ry in ys:
+            for rx in xs:
+                idx1, _, _ = block_match_one(q, int(ry), int(rx), p)
+                a = rank_position(gather_groups(q, idx1[None], p.ps)[0])
+                ranks.append(a)
+                if a <= gam:
+                    low += 1
+                else:
+                    high += 1
+        if low > high:
+            sigma = sigma / p.beta
+        det.update(ranks=np.array(ranks), low=low, high=high)
+    return (sigma, det) if return_details else sigma

@@ -1,0 +1,401 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: a worked example,
+a closed form, a definition written out another way, brute force on a tiny input,
+or an invariant that a dropped term, wrong sign, wrong index or transposed operand breaks.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import htsvd_oracle as O
+from paper_2508_10307_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Haar (Sec. II-D)
+
+def test_haar_worked_example_h4():
+    rows = [l for l in open(os.path.join(GOLDEN, "haar4.txt")) if not l.startswith("#")]
+    x = np.array(rows[0].split(), dtype=float)
+    y = np.array(rows[1].split(), dtype=float)
+    np.testing.assert_allclose(O.haar_matrix(4) @ x, y, rtol=0, atol=1e-15)
+
+
+def test_haar_h2_matches_equation():
+    np.testing.assert_allclose(O.haar_matrix(2), np.array([[1, 1], [1, -1]]) / math.sqrt(2), atol=0)
+
+
+@pytest.mark.parametrize("K", [2, 4, 8, 16, 32, 64])
+def test_haar_orthonormal_and_first_row(K):
+    H = O.haar_matrix(K)
+    np.testing.assert_allclose(H @ H.T, np.eye(K), atol=1e-14)
+    # Eq. (first eigen) / Sec. III-B.2: u_max = 1/sqrt(K) (1,...,1) is the first Haar row.
+    np.testing.assert_allclose(H[0], np.full(K, 1 / math.sqrt(K)), atol=1e-15)
+    # rows K/2..K-1 are the pairwise differences of Eq. (H_2N)
+    for m in range(K // 2):
+        e = np.zeros(K)
+        e[2 * m], e[2 * m + 1] = 1 / math.sqrt(2), -1 / math.sqrt(2)
+        np.testing.assert_allclose(H[K // 2 + m], e, atol=1e-15)
+
+
+def test_haar_rejects_non_power_of_two():
+    with pytest.raises(ValueError):
+        O.haar_matrix(12)
+
+
+# ---------------------------------------------------------------- t-product (Sec. II-C)
+
+@pytest.mark.parametrize("n3", [1, 3, 4])
+def test_t_product_fft_equals_bcirc_definition(n3):
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((5, 4, n3))
+    B = rng.standard_normal((4, 6, n3))
+    np.testing.assert_allclose(O.t_product_fft(A, B), O.t_product_bcirc(A, B), atol=1e-12)
+    # bcirc(A*B) = bcirc(A) bcirc(B)
+    np.testing.assert_allclose(O.bcirc(O.t_product_bcirc(A, B)), O.bcirc(A) @ O.bcirc(B), atol=1e-12)
+
+
+def test_t_transpose_is_bcirc_transpose():
+    A = np.random.default_rng(1).standard_normal((3, 5, 3))
+    np.testing.assert_allclose(O.bcirc(O.t_transpose(A)), O.bcirc(A).T, atol=0)
+
+
+def _rgb_patches(seed=3, n=400, ps=4):
+    clean = synth.clean_image(40, 40, 3, seed)
+    noisy = synth.add_gaussian(clean, 20.0, seed)
+    p = O.Params(ps=ps, stride=2, window=7, K=8)
+    return noisy, p, O.reference_patches(noisy, p)
+
+
+def test_basis_is_real_orthogonal_tensor():
+    _, _, P = _rgb_patches()
+    U, V, lu, lv = O.global_basis(P)
+    for F in (U, V):
+        T = np.fft.ifft(F, axis=0)                      # slices -> real tensor, mode 3 last
+        assert np.abs(T.imag).max() < 1e-13
+        Tr = np.moveaxis(T.real, 0, -1)                 # (ps, ps, C)
+        # U^T * U = identity tensor (Sec. II-C orthogonality), checked through bcirc
+        UtU = O.t_product_bcirc(O.t_transpose(Tr), Tr)
+        I = np.zeros_like(UtU)
+        I[:, :, 0] = np.eye(Tr.shape[0])
+        np.testing.assert_allclose(UtU, I, atol=1e-12)
+    assert np.all(np.diff(lu[0]) <= 0) and np.all(np.diff(lv[1]) <= 0)
+
+
+def test_basis_diagonalises_slice_second_moments():
+    _, _, P = _rgb_patches()
+    U, V, lu, lv = O.global_basis(P)
+    PF = np.fft.fft(P, axis=-1)
+    for f in range(3):
+        A = sum(X @ X.conj().T for X in PF[..., f])      # plain sum over patches
+        B = sum(X.conj().T @ X for X in PF[..., f])
+        np.testing.assert_allclose(U[f].conj().T @ A @ U[f], np.diag(lu[f]), atol=1e-7 * lu[f][0])
+        np.testing.assert_allclose(V[f].conj().T @ B @ V[f], np.diag(lv[f]), atol=1e-7 * lv[f][0])
+        # canonical phase: largest-modulus entry real and positive
+        for Q in (U[f], V[f]):
+            for c in range(Q.shape[1]):
+                a = int(np.argmax(np.abs(Q[:, c])))
+                assert abs(Q[a, c].imag) < 1e-12 and Q[a, c].real > 0
+
+
+def test_gray_basis_is_plain_eigenvectors_of_row_and_column_scatter():
+    clean = synth.clean_image(48, 48, 1, 5)
+    noisy = synth.add_gaussian(clean, 15.0, 5)
+    p = O.Params(ps=8, stride=3, window=9, K=8)
+    P = O.reference_patches(noisy, p)[..., 0]
+    U, V, _, _ = O.global_basis(P[..., None])
+    Arow = np.zeros((8, 8))
+    Bcol = np.zeros((8, 8))
+    for X in P:                                          # textbook 2-D SVD scatter matrices
+        Arow += X @ X.T
+        Bcol += X.T @ X
+    for F, S in ((U[0], Arow), (V[0], Bcol)):
+        w, Q = np.linalg.eigh(S)
+        Q = Q[:, ::-1]
+        np.testing.assert_allclose(np.abs(np.sum(Q * F.real, axis=0)), 1.0, atol=1e-10)
+
+
+def test_patch_projection_equals_t_products_by_definition():
+    noisy, p, P = _rgb_patches()
+    U, V, _, _ = O.global_basis(P)
+    Ur = np.moveaxis(np.fft.ifft(U, axis=0).real, 0, -1)
+    Vr = np.moveaxis(np.fft.ifft(V, axis=0).real, 0, -1)
+    X = P[17]
+    S_def = O.t_product_bcirc(O.t_product_bcirc(O.t_transpose(Ur), X), Vr)   # U^T * P * V
+    np.testing.assert_allclose(O.patch_forward(X, U, V), S_def, atol=1e-10)
+    back = O.t_product_bcirc(O.t_product_bcirc(Ur, S_def), O.t_transpose(Vr))  # U * S * V^T
+    np.testing.assert_allclose(back, X, atol=1e-10)
+    np.testing.assert_allclose(O.patch_inverse(S_def, U, V), X, atol=1e-10)
+
+
+def test_group_transform_is_orthogonal_and_uses_haar_along_group_mode():
+    noisy, p, P = _rgb_patches()
+    U, V, _, _ = O.global_basis(P)
+    H = O.haar_matrix(8)
+    G = P[:8]
+    S = O.forward_transform(G, U, V, H)
+    np.testing.assert_allclose(np.linalg.norm(S), np.linalg.norm(G), rtol=1e-13)
+    np.testing.assert_allclose(O.inverse_transform(S, U, V, H), G, atol=1e-10)
+    T = O.patch_forward(G, U, V)
+    # coefficient row 0 is the scaled group sum (first principal direction, Eq. first eigen)
+    np.testing.assert_allclose(S[0], T.sum(axis=0) / math.sqrt(8), atol=1e-10)
+    # last row is the difference of the last pair (Eq. H_2N)
+    np.testing.assert_allclose(S[7], (T[6] - T[7]) / math.sqrt(2), atol=1e-10)
+
+
+# ---------------------------------------------------------------- grouping (Sec. III-A)
+
+def _brute_force_match(img, ry, rx, p):
+    """Pure-Python brute force: every candidate, Python integers, full sort on (ssd, index)."""
+    H, W, C = img.shape
+    ps = p.ps
+    npy, npx = H - ps + 1, W - ps + 1
+    def win(r, npos):
+        if npos <= p.window:
+            return range(npos)
+        s = min(max(r - (p.window - 1) // 2, 0), npos - p.window)
+        return range(s, s + p.window)
+    im = img.astype(int).tolist()
+    if C == 1:
+        plane = [[px[0] for px in row] for row in im]
+    else:
+        r2 = g2 = b2 = 0
+        for i in range(ps):
+            for j in range(ps):
+                r, g, b = im[ry + i][rx + j]
+                r2 += r * r; g2 += g * g; b2 += b * b
+        gg = p.gcp_gamma * p.gcp_gamma
+        green = gg * g2 >= r2 and gg * g2 >= b2
+        plane = [[px[1] if green else px[0] + px[1] + px[2] for px in row] for row in im]
+    keys = []
+    for y in win(ry, npy):
+        for x in win(rx, npx):
+            if (y, x) == (ry, rx):
+                continue
+            d = 0
+            for i in range(ps):
+                for j in range(ps):
+                    t = plane[ry + i][rx + j] - plane[y + i][x + j]
+                    d += t * t
+            keys.append((d, y * W + x))
+    keys.sort()
+    return [ry * W + rx] + [k[1] for k in keys[:p.K - 1]]
+
+
+@pytest.mark.parametrize("C,shape,window,K,stride", [
+    (1, (17, 19), 5, 8, 3), (3, (16, 21), 7, 8, 2), (3, (13, 13), 31, 16, 3), (1, (12, 30), 6, 4, 4)])
+def test_block_matching_equals_brute_force(C, shape, window, K, stride):
+    rng = np.random.default_rng(11)
+    img = rng.integers(0, 256, size=shape + (C,), dtype=np.uint8)
+    p = O.Params(ps=4, stride=stride, window=window, K=K)
+    idx, _ = O.block_match(img, p)
+    ys = O.reference_positions(shape[0], 4, stride)
+    xs = O.reference_positions(shape[1], 4, stride)
+    n = 0
+    for ry in ys:
+        for rx in xs:
+            assert list(idx[n]) == _brute_force_match(img, int(ry), int(rx), p)
+            n += 1
+
+
+def test_block_matching_ties_break_by_lowest_index():
+    tile = np.random.default_rng(2).integers(0, 256, size=(4, 4), dtype=np.uint8)
+    img = np.tile(tile, (5, 5))[:, :, None]             # many exact duplicates -> SSD ties at 0
+    p = O.Params(ps=4, stride=4, window=9, K=8)
+    idx, _ = O.block_match(img, p)
+    for row in idx:
+        W = img.shape[1]
+        assert row[0] == idx[list(idx[:, 0]).index(row[0]), 0]
+        zeros = [v for v in row[1:]]
+        assert zeros == sorted(zeros)                   # all SSD = 0 -> ascending linear index
+    # the same through brute force
+    assert list(idx[7]) == _brute_force_match(img, int(idx[7, 0] // 20), int(idx[7, 0] % 20), p)
+
+
+def test_gcp_rule_switches_plane():
+    p = np.zeros((4, 4, 3), dtype=np.uint8)
+    p[:, :, 0], p[:, :, 1], p[:, :, 2] = 100, 90, 50      # 1.44*90^2 = 11664 >= 10000 -> green
+    assert O.gcp_uses_green(p, 0, 0, 4, 1.2)
+    p[:, :, 1] = 80                                       # 1.44*80^2 = 9216 < 10000 -> average
+    assert not O.gcp_uses_green(p, 0, 0, 4, 1.2)
+    p[:, :, 1] = 84                                       # 1.44*7056 = 10160.6 >= 10000 but B large
+    p[:, :, 2] = 101
+    assert not O.gcp_uses_green(p, 0, 0, 4, 1.2)
+
+
+def test_reference_grid_and_window():
+    assert len(O.reference_positions(128, 8, 3)) == 41
+    assert len(O.reference_positions(512, 8, 2)) == 253
+    assert len(O.reference_positions(2160, 8, 3)) == 719
+    assert len(O.reference_positions(3840, 8, 3)) == 1279
+    assert list(O.reference_positions(20, 8, 5)) == [0, 5, 10, 12]
+    assert O.window_range(0, 100, 8, 31) == (0, 31)
+    assert O.window_range(50, 100, 8, 31) == (35, 31)
+    assert O.window_range(92, 100, 8, 31) == (62, 31)
+    assert O.window_range(3, 20, 8, 31) == (0, 13)
+
+
+# ---------------------------------------------------------------- whole filter (Alg. 1)
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_zero_threshold_is_identity(C):
+    clean = synth.clean_image(24, 26, C, 9)
+    noisy = synth.add_gaussian(clean, 20.0, 9)
+    r = O.denoise(noisy, 0.0, dict(ps=8, stride=3, window=9, K=8))
+    np.testing.assert_allclose(r.out, noisy.astype(float), atol=1e-10)
+
+
+def test_infinite_threshold_gives_zero():
+    noisy = synth.add_gaussian(synth.clean_image(24, 24, 3, 9), 20.0, 9)
+    r = O.denoise(noisy, 1e30, dict(ps=8, stride=3, window=9, K=8))
+    assert np.abs(r.out).max() == 0.0
+
+
+def test_constant_image_is_fixed_point():
+    img = np.full((24, 24, 3), 77, dtype=np.uint8)
+    r = O.denoise(img, 25.0, dict(ps=8, stride=3, window=9, K=8))
+    np.testing.assert_allclose(r.out, 77.0, atol=1e-9)
+
+
+def test_aggregation_denominator_counts_covering_patches():
+    noisy = synth.add_gaussian(synth.clean_image(20, 22, 1, 4), 20.0, 4)
+    p = O.Params(ps=4, stride=3, window=7, K=4)
+    idx, _ = O.block_match(noisy, p)
+    count = np.zeros((20, 22))
+    for row in idx:
+        for v in row:
+            y, x = divmod(int(v), 22)
+            count[y:y + 4, x:x + 4] += 1
+    G = O.gather_groups(noisy.astype(float), idx, 4)
+    _, den = O.aggregate(noisy.shape, idx, G, np.ones(len(idx)), 4)
+    np.testing.assert_array_equal(den, count)
+    assert den.min() >= 1
+
+
+def test_denoiser_improves_psnr_on_gray_workload():
+    clean, noisy, sigma, prm = synth.workload_gray128()
+    r = O.denoise(noisy, sigma, prm)
+    assert synth.psnr(r.out, clean) > synth.psnr(noisy, clean) + 6.0
+
+
+def test_default_threshold_multiplier():
+    assert abs(O.tau_multiplier(O.Params(ps=8, K=32), 3) - 4.176896) < 1e-6
+    assert abs(O.tau_multiplier(O.Params(ps=8, K=16, tau_mult=2.7), 1) - 2.7) == 0
+
+
+def test_sparsity_weights():
+    noisy = synth.add_gaussian(synth.clean_image(24, 24, 1, 4), 20.0, 4)
+    r = O.denoise(noisy, 20.0, dict(ps=8, stride=3, window=9, K=8, agg_mode="sparsity"), keep_masks=True)
+    kept = r.masks.reshape(len(r.idx), -1).sum(axis=1)
+    np.testing.assert_allclose(r.weights, 1.0 / np.maximum(1, kept))
+
+
+# ---------------------------------------------------------------- circulant eigen-analysis (Sec. III-B.2, III-D)
+
+def _circ(G):
+    K = G.shape[0]
+    p = G.reshape(K, -1)
+    return np.vstack([np.concatenate([p[(i - j) % K] for j in range(K)]) for i in range(K)])
+
+
+def test_circulant_eigenvalues_closed_form():
+    rng = np.random.default_rng(4)
+    G = rng.integers(0, 256, size=(8, 3, 3, 2)).astype(float)
+    C = _circ(G)
+    dense = np.sort(np.linalg.eigvalsh(C @ C.T))
+    lam = O.circulant_eigenvalues(G)
+    np.testing.assert_allclose(np.sort(lam), dense, rtol=1e-10)
+    p = G.reshape(8, -1)
+    np.testing.assert_allclose(lam[0], np.sum(p.sum(axis=0) ** 2))                            # Eq. (first eigen)
+    np.testing.assert_allclose(lam[4], np.sum((((-1.0) ** np.arange(8))[:, None] * p).sum(0) ** 2))  # Eq. (other eigenvalue)
+    assert lam[0] == lam.max()                          # non-negative data: lambda_max = ||sum p||^2
+
+
+def test_rank_position_extremes():
+    base = np.random.default_rng(5).integers(0, 256, size=(4, 4, 1)).astype(float)
+    smooth = np.stack([base + 0.01 * k for k in range(8)])         # nearly identical patches
+    assert O.rank_position(smooth) <= 4
+    alt = np.stack([base if k % 2 == 0 else 255 - base for k in range(8)])
+    # alternating patches: only lambda_0 and lambda_{K/2} are non-zero and lambda_0 = ||sum p||^2 is the
+    # larger for non-negative data, so lambda_hat is the second largest (rank K-1), cf. Fig. (change lambda)
+    assert O.rank_position(alt) == 7
+
+
+# ---------------------------------------------------------------- noise level estimate
+
+@pytest.mark.parametrize("sigma", [5.0, 10.0, 25.0])
+def test_sigma_estimate_recovers_pure_noise(sigma):
+    rng = np.random.default_rng(int(sigma))
+    img = np.clip(np.rint(128 + sigma * rng.standard_normal((256, 256, 1))), 0, 255).astype(np.uint8)
+    s = O.estimate_sigma(img, dict(ps=8, stride=2))
+    assert abs(s - math.sqrt(sigma ** 2 + 1 / 12)) / sigma < 0.02
+
+
+def test_sigma_estimate_rgb_pure_noise():
+    rng = np.random.default_rng(8)
+    img = np.clip(np.rint(128 + 10 * rng.standard_normal((256, 256, 3))), 0, 255).astype(np.uint8)
+    s = O.estimate_sigma(img, dict(ps=8, stride=2))
+    assert abs(s - 10.0) / 10.0 < 0.02
+
+
+def test_sigma_rule_on_constructed_spectrum():
+    lam = np.concatenate([np.full(50, 4.0), np.linspace(30, 900, 14)])
+    assert abs(O.sigma_from_eigenvalues(lam) - 2.0) < 1e-12
+
+
+def test_adaptive_vote_direction():
+    clean = synth.clean_image(96, 96, 3, 21)
+    noisy = synth.add_gaussian(clean, 40.0, 21)
+    s0, d = O.estimate_sigma(noisy, dict(ps=8, stride=3, window=15, K=32, adapt=True), return_details=True)
+    assert d["low"] + d["high"] == len(d["ranks"]) > 0
+    if d["low"] > d["high"]:
+        assert abs(s0 - d["sigma_est"] / 1.2) < 1e-12
+    else:
+        assert s0 == d["sigma_est"]
+
+
+# ---------------------------------------------------------------- frozen-mask map and its adjoint
+
+def _frozen_problem(C=1, seed=6):
+    clean = synth.clean_image(16, 18, C, seed)
+    x = synth.add_gaussian_float(clean, 20.0, seed).astype(np.float64)
+    p = O.Params(ps=4, stride=2, window=7, K=4)
+    r = O.denoise(x, 20.0, p, keep_masks=True)
+    w = np.random.default_rng(seed).uniform(0.5, 1.5, size=len(r.idx))
+    return x, r, w, p
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_frozen_map_is_linear_and_adjoint_dot_product(C):
+    x, r, w, p = _frozen_problem(C)
+    rng = np.random.default_rng(1)
+    v, u = rng.standard_normal(x.shape), rng.standard_normal(x.shape)
+    f = lambda z: O.denoise_fixed(z, r.idx, r.masks, r.U, r.V, w, p.ps)[0]
+    np.testing.assert_allclose(f(2 * v + x), 2 * f(v) + f(x), atol=1e-9)
+    gx, _ = O.denoise_fixed_vjp(x, u, r.idx, r.masks, r.U, r.V, w, p.ps)
+    assert abs(np.sum(f(v) * u) - np.sum(v * O.denoise_fixed_vjp(v, u, r.idx, r.masks, r.U, r.V, w, p.ps)[0])) < 1e-8
+    assert abs(np.sum(f(v) * u) - np.sum(v * gx)) < 1e-8
+
+
+def test_frozen_map_gradients_match_central_differences():
+    x, r, w, p = _frozen_problem(3)
+    u = np.random.default_rng(2).standard_normal(x.shape)
+    L = lambda z, ww: float(np.sum(O.denoise_fixed(z, r.idx, r.masks, r.U, r.V, ww, p.ps)[0] * u))
+    gx, gw = O.denoise_fixed_vjp(x, u, r.idx, r.masks, r.U, r.V, w, p.ps)
+    h = 1e-3
+    rng = np.random.default_rng(3)
+    for _ in range(6):
+        pos = tuple(int(rng.integers(0, s)) for s in x.shape)
+        e = np.zeros_like(x)
+        e[pos] = h
+        fd = (L(x + e, w) - L(x - e, w)) / (2 * h)
+        assert abs(fd - gx[pos]) < 1e-7 * max(1, abs(fd))
+    for g in rng.integers(0, len(w), size=6):
+        e = np.zeros_like(w)
+        e[g] = h
+        fd = (L(x, w + e) - L(x, w - e)) / (2 * h)
+        assert abs(fd - gw[g]) < 1e-6 * max(1, abs(fd))
