@@ -1,0 +1,157 @@
+/*
+ * htsvd.h — C ABI of the GB300 Haar-tSVD denoising core.
+ *
+ * Method: Kong, Zhang & Yang, "Efficient Image Denoising Using Global and Local
+ * Circulant Representation" (arXiv 2508.10307), Algorithm 1 (Haar-tSVD) and the
+ * eigenvalue analysis of Sec. III-D.
+ *
+ * Conventions shared by every entry point
+ *  - Images are contiguous row-major H x W x C (HWC), C in {1, 3}, on the
+ *    [0, 255] scale. Pointers named d_* are DEVICE pointers owned by the caller;
+ *    pointers named h_* or documented as host are HOST pointers.
+ *  - Patches are ps x ps with ps = 8 (the paper's value, Sec. IV-A; other sizes
+ *    return HTSVD_ERR_UNSUPPORTED). K is a power of two in [2, 32].
+ *  - Reference patches sit on the grid {0, s, 2s, ...} U {n - ps} of each axis,
+ *    row-major; group g belongs to the g-th reference of that order.
+ *  - Match indices are int32 linear top-left positions y * W + x, K per group;
+ *    slot 0 is the reference itself, slots 1..K-1 the K-1 nearest other
+ *    candidates of its search window by (SSD, linear index) ascending.
+ *  - Calls are asynchronous on `stream` except where a host result is
+ *    returned (documented per call). The library owns a workspace cached per
+ *    (device, stream); it grows with cudaMalloc on first use at a size and is
+ *    never touched by two calls on the same stream at once.
+ *  - No exceptions cross this ABI; every call returns an htsvd_status.
+ */
+#ifndef HTSVD_H
+#define HTSVD_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum htsvd_status {
+    HTSVD_OK = 0,
+    HTSVD_ERR_INVALID_ARG = 1,   /* bad size, pointer or parameter */
+    HTSVD_ERR_UNSUPPORTED = 2,   /* valid for the method, not built here (ps != 8, K > 32, window > 64) */
+    HTSVD_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    HTSVD_ERR_OOM = 4,           /* workspace allocation failed */
+    HTSVD_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (persistent batch) */
+} htsvd_status;
+
+typedef enum htsvd_match_mode {
+    HTSVD_MATCH_AUTO = 0,   /* C=1: the gray plane; C=3: green-channel prior (GCP) */
+    HTSVD_MATCH_GCP = 1,    /* Sec. III-A, Eq. (GCP distance): G plane if ||G|| >= max(||R||,||B||)/gamma on the
+                               reference patch, else the R+G+B plane (same order as the channel average) */
+    HTSVD_MATCH_FULL = 2,   /* SSD summed over all channels */
+    HTSVD_MATCH_GREEN = 3,  /* always the G plane (C=3) */
+} htsvd_match_mode;
+
+typedef enum htsvd_agg_mode {
+    HTSVD_AGG_UNIFORM = 0,  /* every group weighs 1: the plain average of Alg. 1 Step 3 */
+    HTSVD_AGG_SPARSITY = 1, /* w_g = 1 / max(1, number of kept coefficients of g), Eq. (aggregation) weights */
+} htsvd_agg_mode;
+
+/* Parameters. A zero-filled struct means the paper's defaults (Sec. IV-A):
+ * ps 8, K 32, window 18, stride 3, tau = sigma * sqrt(2 ln(C K ps^2)), gamma 1.2,
+ * beta 1.2, rank gamma 13 (scaled by K/32). */
+typedef struct htsvd_params {
+    int32_t ps;            /* patch size; 0 -> 8 */
+    int32_t stride;        /* reference grid step; 0 -> 3 */
+    int32_t window;        /* search window W (candidate top-left positions per axis); 0 -> 18, at most 64 */
+    int32_t K;             /* patches per group; 0 -> 32 */
+    double  tau_mult;      /* tau = tau_mult * sigma; <= 0 -> sqrt(2 ln(C K ps^2)) (Sec. IV-A) */
+    int32_t match_mode;    /* htsvd_match_mode */
+    double  gcp_gamma;     /* <= 0 -> 1.2 (Sec. III-A) */
+    int32_t agg_mode;      /* htsvd_agg_mode */
+    int32_t adapt;         /* sigma estimation: apply the eigen-rank vote of Eq. (adjust noise level) */
+    double  beta;          /* <= 0 -> 1.2 (Sec. III-D) */
+    int32_t rank_gamma;    /* <= 0 -> round(13 K / 32) (Sec. III-D) */
+    int32_t tile;          /* reference tile edge for the filter (0 -> automatic) */
+    int64_t max_wait_cycles; /* persistent batch: clock64 budget of a queue wait; 0 -> 2^34 */
+    /* Optional outputs (may be NULL). */
+    double*   h_sigma_out;   /* HOST: the sigma actually used (estimated when sigma < 0) */
+    uint32_t* d_mask_out;    /* DEVICE: threshold masks, per group ceil(K*ps*ps*C/32) words, bit index
+                                ((m*ps + i)*ps + j)*C + c for Haar row m, pixel (i, j), channel c */
+    float*    d_weights_out; /* DEVICE: per-group aggregation weights actually used */
+    double*   d_basis_out;   /* DEVICE: 2*C*ps*ps complex values (re, im): U_F slices then V_F slices,
+                                each slice row-major [a][i] (column i = i-th eigenvector) */
+} htsvd_params;
+
+/* One image of a batch. */
+typedef struct htsvd_image {
+    const uint8_t* d_in;   /* H x W x C uint8 */
+    int32_t H, W, C;
+    double sigma;          /* noise level; must be >= 0 in a batch */
+    float* d_out;          /* H x W x C float32 */
+} htsvd_image;
+
+/* Alg. 1 (Haar-tSVD) on a uint8 image.
+ * sigma >= 0: the given noise level; sigma < 0: estimated on the device with the
+ * eigenvalue rule of htsvd_estimate_sigma (one host synchronisation, overlapped with
+ * block matching).
+ * d_out: H*W*C float32, the aggregated estimate, unclipped.
+ * d_idx_out: optional N_groups*K int32 match indices (see conventions).
+ * Errors: INVALID_ARG if H or W < ps, C not 1 or 3, K not a power of two, stride < 1,
+ * window < 1, or the search window holds fewer than K positions. */
+htsvd_status htsvd_denoise(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, double sigma,
+                           const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t stream);
+
+/* Alg. 1 on a float32 image x (H x W x C on the [0, 255] scale). Grouping, the global
+ * bases and an estimated sigma use q = clip(rint(x), 0, 255); the transforms use x.
+ * d_w: optional per-group aggregation weights (N_groups floats); NULL uses p->agg_mode.
+ * Other arguments as htsvd_denoise. */
+htsvd_status htsvd_denoise_f32(const float* d_x, int32_t H, int32_t W, int32_t C, double sigma,
+                               const htsvd_params* p, const float* d_w, float* d_out, int32_t* d_idx_out,
+                               cudaStream_t stream);
+
+/* Noise level from the eigenvalues of the covariance of the reference patches:
+ * ascending eigenvalues l_1..l_d, r* = max{r : mean(l_1..r) <= 1.02 median(l_1..r)},
+ * sigma = sqrt(mean(l_1..r*)). With p->adapt the eigen-rank vote of Sec. III-D,
+ * Eq. (adjust noise level), over groups of every 8th reference per axis divides it by beta.
+ * h_sigma: HOST output. Synchronises `stream`. */
+htsvd_status htsvd_estimate_sigma(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C,
+                                  const htsvd_params* p, double* h_sigma, cudaStream_t stream);
+
+/* Alg. 1 on n uint8 images of any sizes with per-image sigma (>= 0), as one
+ * persistent launch per phase over a work queue. The launch sequence contains no host
+ * synchronisation. Optional outputs of p are ignored. */
+htsvd_status htsvd_denoise_batch(const htsvd_image* h_imgs, int32_t n, const htsvd_params* p,
+                                 cudaStream_t stream);
+
+/* Vector-Jacobian product of htsvd_denoise_f32 at x with the grouping (d_idx), the
+ * global bases, tau and the threshold masks held fixed (masks are recomputed at x).
+ * d_w: per-group weights used by the forward (NULL = all ones); d_out: the forward's
+ * output at x; d_grad_out: cotangent of the output (H*W*C).
+ * d_grad_x: H*W*C float32 output; d_grad_w: optional N_groups float32 output.
+ * sigma must be >= 0 (pass the sigma the forward used). */
+htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C, double sigma,
+                               const htsvd_params* p, const int32_t* d_idx, const float* d_w,
+                               const float* d_out, const float* d_grad_out, float* d_grad_x,
+                               float* d_grad_w, cudaStream_t stream);
+
+/* Number of groups (reference patches) of an H x W image, or -1 on bad arguments. */
+int64_t htsvd_num_groups(int32_t H, int32_t W, const htsvd_params* p);
+
+/* Static description of a status code. */
+const char* htsvd_status_string(htsvd_status s);
+
+/* Benchmark instrumentation (not needed for correct use). While enabled, every kernel
+ * launch of the library is bracketed by CUDA events on its stream.
+ * htsvd_profile_collect waits for the recorded events and writes, for up to max_kernels
+ * kernel names, the name (NUL-terminated, name_len bytes per entry, HOST), the number of
+ * launches and their total device time in ms (HOST arrays); it then clears the record and
+ * returns the number of entries written, or -1 if an event could not be read. */
+htsvd_status htsvd_profile_enable(int32_t enable);
+int32_t htsvd_profile_collect(int32_t max_kernels, char* names, int32_t name_len, int64_t* launches,
+                              double* total_ms);
+
+/* Releases the workspaces of the calling thread's current device. */
+htsvd_status htsvd_release_workspace(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HTSVD_H */

@@ -386,7 +386,8 @@ class Result:
     V: np.ndarray
     weights: np.ndarray
     masks: np.ndarray | None = None       # (n, K, ps, ps, C) bool
-    coeffs: np.ndarray | None = None      # |S| values, for guard-band accounting
+    coeffs: np.ndarray | None = None      # |S| values
+    ambiguous: np.ndarray | None = None   # (group, flat coefficient index) with | |S| - tau | <= 1e-9 max(tau, 1)
     den: np.ndarray | None = None
     extra: dict = field(default_factory=dict)
 
@@ -398,7 +399,7 @@ def _as_quantised(x: np.ndarray) -> np.ndarray:
 
 
 def denoise(x: np.ndarray, sigma: float, params=None, *, idx=None, weights=None,
-            keep_masks=False, keep_coeffs=False, chunk=2048) -> Result:
+            keep_masks=False, keep_coeffs=False, chunk=2048, tau=None) -> Result:
     """Alg. 1: grouping, global bases, forward transform, hard threshold, inverse, aggregation.
 
     x: (H, W, C) uint8 or float image on the [0, 255] scale.  For float input the matching and the
@@ -412,7 +413,8 @@ def denoise(x: np.ndarray, sigma: float, params=None, *, idx=None, weights=None,
         idx, _ = block_match(q, p)
     U, V, _, _ = global_basis(reference_patches(q, p))
     Hk = haar_matrix(p.K)
-    tau = tau_multiplier(p, C) * float(sigma)
+    if tau is None:
+        tau = tau_multiplier(p, C) * float(sigma)
     xf = x.astype(np.float64)
     n = idx.shape[0]
     w = np.ones(n) if weights is None else np.asarray(weights, dtype=np.float64)
@@ -421,11 +423,14 @@ def denoise(x: np.ndarray, sigma: float, params=None, *, idx=None, weights=None,
     masks = np.zeros((n, p.K, p.ps, p.ps, C), dtype=bool) if keep_masks else None
     coeffs = np.zeros((n, p.K, p.ps, p.ps, C)) if keep_coeffs else None
     w_out = w.copy()
+    amb = []
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
         G = gather_groups(xf, idx[a:b], p.ps)
         S = forward_transform(G, U, V, Hk)
         m = hard_threshold_mask(S, tau)
+        near = np.nonzero(np.abs(np.abs(S.reshape(b - a, -1)) - tau) <= 1e-9 * max(tau, 1.0))
+        amb.extend(zip((near[0] + a).tolist(), near[1].tolist()))
         if weights is None and p.agg_mode == "sparsity":
             w_out[a:b] = 1.0 / np.maximum(1, m.reshape(b - a, -1).sum(axis=1))
         Ghat = inverse_transform(S * m, U, V, Hk)
@@ -438,7 +443,7 @@ def denoise(x: np.ndarray, sigma: float, params=None, *, idx=None, weights=None,
             coeffs[a:b] = np.abs(S)
     out = num / den[:, :, None]
     return Result(out=out, idx=idx, tau=tau, U=U, V=V, weights=w_out, masks=masks,
-                  coeffs=coeffs, den=den)
+                  coeffs=coeffs, den=den, ambiguous=np.array(amb, dtype=np.int64).reshape(-1, 2))
 
 
 # --------------------------------------------------------------------------- frozen-mask linear map and its adjoint

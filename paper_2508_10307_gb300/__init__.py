@@ -1,0 +1,241 @@
+"""GB300 Haar-tSVD denoising core (Kong, Zhang & Yang, arXiv 2508.10307).
+
+Thin PyTorch-facing binding over the C ABI of libhtsvd.so (include/htsvd.h): it only
+moves tensors' device pointers and the current CUDA stream across the boundary. Every
+step of the method runs in the library's CUDA kernels; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, fields
+
+from . import _lib
+
+__all__ = ["HtsvdParams", "denoise", "denoise_f32", "estimate_sigma", "denoise_batch", "denoise_vjp",
+           "num_groups", "HtsvdFn", "load_library"]
+
+_MATCH = {"auto": 0, "gcp": 1, "full": 2, "green": 3}
+_AGG = {"uniform": 0, "sparsity": 1}
+
+
+@dataclass
+class HtsvdParams:
+    """Method parameters (Sec. IV-A defaults: ps 8, K 32, window 18; tau = sigma sqrt(2 ln(C K ps^2)))."""
+    ps: int = 8
+    stride: int = 3
+    window: int = 18
+    K: int = 32
+    tau_mult: float = 0.0
+    match_mode: str = "auto"
+    gcp_gamma: float = 1.2
+    agg_mode: str = "uniform"
+    adapt: bool = False
+    beta: float = 1.2
+    rank_gamma: int = 0
+    tile: int = 0
+
+    @staticmethod
+    def of(p) -> "HtsvdParams":
+        if p is None:
+            return HtsvdParams()
+        if isinstance(p, HtsvdParams):
+            return p
+        names = {f.name for f in fields(HtsvdParams)}
+        return HtsvdParams(**{k: v for k, v in dict(p).items() if k in names})
+
+    def c(self) -> _lib.CParams:
+        cp = _lib.CParams()
+        cp.ps, cp.stride, cp.window, cp.K = self.ps, self.stride, self.window, self.K
+        cp.tau_mult = float(self.tau_mult)
+        cp.match_mode = _MATCH[self.match_mode]
+        cp.gcp_gamma = float(self.gcp_gamma)
+        cp.agg_mode = _AGG[self.agg_mode]
+        cp.adapt = int(bool(self.adapt))
+        cp.beta = float(self.beta)
+        cp.rank_gamma = int(self.rank_gamma)
+        cp.tile = int(self.tile)
+        return cp
+
+
+def load_library():
+    return _lib.load()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _hwc(x):
+    if x.dim() == 2:
+        x = x.unsqueeze(-1)
+    if x.dim() != 3 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor of shape (H, W) or (H, W, C)")
+    return x
+
+
+def num_groups(H: int, W: int, params=None) -> int:
+    lib = _lib.load()
+    cp = HtsvdParams.of(params).c()
+    return int(lib.htsvd_num_groups(H, W, ctypes.byref(cp)))
+
+
+def _outputs(x, p, params, want_idx, want_masks, want_weights, want_basis):
+    torch = _torch()
+    H, W, C = x.shape
+    n = num_groups(H, W, p)
+    out = torch.empty((H, W, C), dtype=torch.float32, device=x.device)
+    info = {}
+    idx = torch.empty((n, p.K), dtype=torch.int32, device=x.device) if want_idx else None
+    if want_masks:
+        info["masks"] = torch.empty((n, (p.K * 64 * C + 31) // 32), dtype=torch.int32, device=x.device)
+        params.d_mask_out = info["masks"].data_ptr()
+    if want_weights:
+        info["weights"] = torch.empty(n, dtype=torch.float32, device=x.device)
+        params.d_weights_out = info["weights"].data_ptr()
+    if want_basis:
+        info["basis"] = torch.empty((2, C, 8, 8, 2), dtype=torch.float64, device=x.device)
+        params.d_basis_out = info["basis"].data_ptr()
+    return out, idx, info
+
+
+def denoise(noisy, sigma=None, params=None, *, return_info=False, masks=False, weights=False, basis=False,
+            stream=None):
+    """Alg. 1 on a uint8 (H, W[, C]) CUDA tensor. sigma=None estimates it on the device.
+    Returns the float32 (H, W, C) estimate, or (estimate, info) with return_info."""
+    lib = _lib.load()
+    x = _hwc(noisy)
+    if x.dtype != _torch().uint8:
+        raise TypeError("denoise expects uint8; use denoise_f32 for float images")
+    p = HtsvdParams.of(params)
+    cp = p.c()
+    sig_out = ctypes.c_double(-1.0)
+    cp.h_sigma_out = ctypes.pointer(sig_out)
+    out, idx, info = _outputs(x, p, cp, return_info, masks, weights, basis)
+    H, W, C = x.shape
+    st = lib.htsvd_denoise(_ptr(x), H, W, C, -1.0 if sigma is None else float(sigma), ctypes.byref(cp),
+                           _ptr(out), _ptr(idx), _stream_ptr(stream))
+    _lib.check(st, "htsvd_denoise")
+    if return_info:
+        info.update(idx=idx, sigma=sig_out.value)
+        return out, info
+    return out
+
+
+def denoise_f32(x, sigma=None, params=None, *, w=None, return_info=False, masks=False, weights=False,
+                basis=False, stream=None):
+    """Alg. 1 on a float32 image; grouping and bases use the rounded image, the filter uses x."""
+    lib = _lib.load()
+    x = _hwc(x)
+    torch = _torch()
+    if x.dtype != torch.float32:
+        raise TypeError("denoise_f32 expects float32")
+    p = HtsvdParams.of(params)
+    cp = p.c()
+    sig_out = ctypes.c_double(-1.0)
+    cp.h_sigma_out = ctypes.pointer(sig_out)
+    out, idx, info = _outputs(x, p, cp, True, masks, weights, basis)
+    H, W, C = x.shape
+    wt = None if w is None else w.contiguous().float()
+    st = lib.htsvd_denoise_f32(_ptr(x), H, W, C, -1.0 if sigma is None else float(sigma), ctypes.byref(cp),
+                               _ptr(wt), _ptr(out), _ptr(idx), _stream_ptr(stream))
+    _lib.check(st, "htsvd_denoise_f32")
+    if return_info:
+        info.update(idx=idx, sigma=sig_out.value)
+        return out, info
+    return out
+
+
+def estimate_sigma(noisy, params=None, stream=None) -> float:
+    """Noise level from the covariance eigenvalues of the reference patches (optionally adjusted by
+    the eigen-rank vote of Sec. III-D). Synchronises the stream."""
+    lib = _lib.load()
+    x = _hwc(noisy)
+    p = HtsvdParams.of(params)
+    cp = p.c()
+    s = ctypes.c_double(0.0)
+    H, W, C = x.shape
+    _lib.check(lib.htsvd_estimate_sigma(_ptr(x), H, W, C, ctypes.byref(cp), ctypes.byref(s), _stream_ptr(stream)),
+               "htsvd_estimate_sigma")
+    return s.value
+
+
+def denoise_batch(images, sigmas, params=None, outs=None, stream=None):
+    """Denoises a list of uint8 (H, W, C) CUDA tensors of any sizes with per-image sigma."""
+    lib = _lib.load()
+    torch = _torch()
+    imgs = [_hwc(t) for t in images]
+    if outs is None:
+        outs = [torch.empty(t.shape, dtype=torch.float32, device=t.device) for t in imgs]
+    arr = (_lib.CImage * len(imgs))()
+    for i, (t, s, o) in enumerate(zip(imgs, sigmas, outs)):
+        arr[i].d_in = t.data_ptr()
+        arr[i].H, arr[i].W, arr[i].C = t.shape
+        arr[i].sigma = float(s)
+        arr[i].d_out = o.data_ptr()
+    cp = HtsvdParams.of(params).c()
+    _lib.check(lib.htsvd_denoise_batch(arr, len(imgs), ctypes.byref(cp), _stream_ptr(stream)),
+               "htsvd_denoise_batch")
+    return outs
+
+
+def denoise_vjp(x, sigma, idx, w, out, grad_out, params=None, want_grad_w=True, stream=None):
+    """Vector-Jacobian product of denoise_f32 at x (grouping, bases, tau and masks held fixed)."""
+    lib = _lib.load()
+    torch = _torch()
+    x = _hwc(x)
+    H, W, C = x.shape
+    gx = torch.empty_like(x)
+    gw = torch.empty(idx.shape[0], dtype=torch.float32, device=x.device) if want_grad_w else None
+    cp = HtsvdParams.of(params).c()
+    wt = None if w is None else w.contiguous().float()
+    st = lib.htsvd_denoise_vjp(_ptr(x), H, W, C, float(sigma), ctypes.byref(cp), _ptr(idx.contiguous()), _ptr(wt),
+                               _ptr(out.contiguous()), _ptr(grad_out.contiguous()), _ptr(gx), _ptr(gw),
+                               _stream_ptr(stream))
+    _lib.check(st, "htsvd_denoise_vjp")
+    return gx, gw
+
+
+def _make_fn():
+    torch = _torch()
+
+    class HtsvdFn(torch.autograd.Function):
+        """out = Haar-tSVD(x; w) with a hand-written VJP for x and the per-group weights w.
+        The grouping, bases, tau and masks are held fixed; the backward recomputes the group
+        tensors instead of storing them."""
+
+        @staticmethod
+        def forward(ctx, x, w, sigma, params):
+            p = HtsvdParams.of(params)
+            out, info = denoise_f32(x.contiguous(), sigma, p, w=w, return_info=True)
+            ctx.save_for_backward(x, w, info["idx"], out)
+            ctx.sigma = info["sigma"]
+            ctx.params = p
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            x, w, idx, out = ctx.saved_tensors
+            gx, gw = denoise_vjp(x, ctx.sigma, idx, w, out, grad_out.contiguous(), ctx.params,
+                                 want_grad_w=ctx.needs_input_grad[1])
+            return gx, gw, None, None
+
+    return HtsvdFn
+
+
+def __getattr__(name):
+    if name == "HtsvdFn":
+        fn = _make_fn()
+        globals()["HtsvdFn"] = fn
+        return fn
+    raise AttributeError(name)

@@ -1,0 +1,615 @@
+// C ABI entry points: parameter resolution, workspace, launch sequences.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <new>
+#include <vector>
+
+#include "../../include/htsvd.h"
+#include "kernels.h"
+
+namespace htsvd {
+bool symmetric_eigenvalues(double* A, int n, double* out);
+}
+
+using namespace htsvd;
+
+namespace {
+
+// ----------------------------------------------------------------------------- parameters
+
+struct Resolved {
+    int ps, s, win, K, match_mode, agg_mode, adapt, rank_gamma, tile;
+    double tau_mult, gamma, beta;
+    int64_t max_wait;
+};
+
+htsvd_status resolve(const htsvd_params* p, int C, Resolved& r) {
+    htsvd_params z;
+    std::memset(&z, 0, sizeof(z));
+    if (!p) p = &z;
+    r.ps = p->ps > 0 ? p->ps : 8;
+    r.s = p->stride > 0 ? p->stride : 3;
+    r.win = p->window > 0 ? p->window : 18;
+    r.K = p->K > 0 ? p->K : 32;
+    r.match_mode = p->match_mode;
+    r.agg_mode = p->agg_mode;
+    r.adapt = p->adapt;
+    r.gamma = p->gcp_gamma > 0 ? p->gcp_gamma : 1.2;
+    r.beta = p->beta > 0 ? p->beta : 1.2;
+    r.rank_gamma = p->rank_gamma > 0 ? p->rank_gamma : (13 * r.K + 16) / 32;
+    r.tile = p->tile;
+    r.max_wait = p->max_wait_cycles > 0 ? p->max_wait_cycles : (int64_t)1 << 34;
+    if (p->stride < 0 || p->window < 0 || p->K < 0 || p->ps < 0) return HTSVD_ERR_INVALID_ARG;
+    if (r.K < 2 || (r.K & (r.K - 1))) return HTSVD_ERR_INVALID_ARG;
+    if (r.match_mode < 0 || r.match_mode > 3 || r.agg_mode < 0 || r.agg_mode > 1) return HTSVD_ERR_INVALID_ARG;
+    if (r.ps != PS || r.K > 32 || r.win > 64) return HTSVD_ERR_UNSUPPORTED;
+    r.tau_mult = p->tau_mult > 0 ? p->tau_mult : std::sqrt(2.0 * std::log((double)C * r.K * r.ps * r.ps));
+    return HTSVD_OK;
+}
+
+htsvd_status check_image(int H, int W, int C, const Resolved& r) {
+    if (C != 1 && C != 3) return HTSVD_ERR_INVALID_ARG;
+    if (H < r.ps || W < r.ps) return HTSVD_ERR_INVALID_ARG;
+    if ((int64_t)H * W * C >= ((int64_t)1 << 31)) return HTSVD_ERR_UNSUPPORTED;
+    Geo g = make_geo(H, W, C, r.s, r.win, r.K);
+    if ((int64_t)g.wny * g.wnx < r.K) return HTSVD_ERR_INVALID_ARG;
+    return HTSVD_OK;
+}
+
+int resolve_mode(const Resolved& r, int C) {
+    if (C == 1) return MM_GRAY;
+    switch (r.match_mode) {
+        case HTSVD_MATCH_FULL: return MM_FULL;
+        case HTSVD_MATCH_GREEN: return MM_GREEN;
+        default: return MM_GCP;
+    }
+}
+
+// ----------------------------------------------------------------------------- workspace
+
+enum Slot {
+    S_IDX, S_MOM, S_B64, S_B32, S_PART, S_FULLM, S_FULLS, S_RANKS, S_IDX2, S_Q, S_DEN, S_R, S_TMP, S_NSLOT
+};
+
+struct Workspace {
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    void* buf[S_NSLOT] = {};
+    size_t cap[S_NSLOT] = {};
+    void* hpin = nullptr;
+    size_t hcap = 0;
+};
+
+std::mutex g_mu;
+std::vector<Workspace*> g_ws;
+
+Workspace* workspace_for(cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (Workspace* w : g_ws)
+        if (w->device == dev && w->stream == s) return w;
+    Workspace* w = new (std::nothrow) Workspace();
+    if (!w) return nullptr;
+    w->device = dev;
+    w->stream = s;
+    g_ws.push_back(w);
+    return w;
+}
+
+htsvd_status ws_get(Workspace* w, int slot, size_t bytes, void** out) {
+    if (bytes == 0) bytes = 16;
+    if (w->cap[slot] < bytes) {
+        if (w->buf[slot]) {
+            cudaFree(w->buf[slot]);
+            w->buf[slot] = nullptr;
+            w->cap[slot] = 0;
+        }
+        size_t b = bytes + bytes / 8;
+        if (cudaMalloc(&w->buf[slot], b) != cudaSuccess) {
+            cudaGetLastError();
+            return HTSVD_ERR_OOM;
+        }
+        w->cap[slot] = b;
+    }
+    *out = w->buf[slot];
+    return HTSVD_OK;
+}
+
+htsvd_status ws_host(Workspace* w, size_t bytes, void** out) {
+    if (w->hcap < bytes) {
+        if (w->hpin) cudaFreeHost(w->hpin);
+        w->hpin = nullptr;
+        w->hcap = 0;
+        if (cudaMallocHost(&w->hpin, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return HTSVD_ERR_OOM;
+        }
+        w->hcap = bytes;
+    }
+    *out = w->hpin;
+    return HTSVD_OK;
+}
+
+// ----------------------------------------------------------------------------- kernel timing
+
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+
+// Brackets the launches made in its scope with events on `s` while profiling is enabled.
+struct ProfScope {
+    ProfRec r{nullptr, nullptr, nullptr};
+    cudaStream_t s;
+    ProfScope(const char* name, cudaStream_t st) : s(st) {
+        if (!g_prof_on) return;
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+            cudaGetLastError();
+            r.a = r.b = nullptr;
+            return;
+        }
+        r.name = name;
+        cudaEventRecord(r.a, s);
+    }
+    ~ProfScope() {
+        if (!r.name) return;
+        cudaEventRecord(r.b, s);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof.push_back(r);
+    }
+};
+
+#define CK(x)                                         \
+    do {                                              \
+        cudaError_t e_ = (x);                         \
+        if (e_ != cudaSuccess) return HTSVD_ERR_CUDA; \
+    } while (0)
+#define ST(x)                               \
+    do {                                    \
+        htsvd_status s_ = (x);              \
+        if (s_ != HTSVD_OK) return s_;      \
+    } while (0)
+
+// ----------------------------------------------------------------------------- tiling choices
+
+struct FilterTiling {
+    int TR, ntx, nty, FHmax, FWmax;
+};
+
+FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forced) {
+    const int cands[] = {8, 6, 5, 4, 3, 2, 1};
+    FilterTiling best{};
+    for (int TR : cands) {
+        if (forced > 0 && TR != forced) continue;
+        FilterTiling t;
+        t.TR = TR;
+        t.ntx = (g.nrx + TR - 1) / TR;
+        t.nty = (g.nry + TR - 1) / TR;
+        t.FHmax = std::min(g.H, (TR - 1) * g.s + g.wny + PS - 1);
+        t.FWmax = std::min(g.W, (TR - 1) * g.s + g.wnx + PS - 1);
+        FilterArgs fa{};
+        fa.g = g;
+        fa.FHmax = t.FHmax;
+        fa.FWmax = t.FWmax;
+        fa.img_is_float = in_bytes == 4;
+        fa.mode = mode;
+        const size_t smem = filter_smem_bytes(fa);
+        best = t;
+        if (smem > 200 * 1024) continue;
+        if (forced > 0) return t;
+        // enough tiles to fill the GPU (two per SM) unless the image is small
+        if ((int64_t)t.ntx * t.nty >= 2 * 152 || TR == 1) return t;
+    }
+    return best;
+}
+
+void choose_bm_tiles(const Geo& g, int rstep, int& TRy, int& TRx) {
+    TRy = 4;
+    TRx = 8;
+    (void)g;
+    (void)rstep;
+}
+
+// ----------------------------------------------------------------------------- pieces
+
+htsvd_status run_block_match(const uint8_t* q, const Geo& g, const Resolved& r, int rstep, int32_t* idx,
+                             cudaStream_t s) {
+    BMArgs a{};
+    a.img = q;
+    a.g = g;
+    a.mode = resolve_mode(r, g.C);
+    a.gamma2 = r.gamma * r.gamma;
+    a.rstep = rstep;
+    a.nry_s = (g.nry + rstep - 1) / rstep;
+    a.nrx_s = (g.nrx + rstep - 1) / rstep;
+    choose_bm_tiles(g, rstep, a.TRy, a.TRx);
+    a.idx = idx;
+    { ProfScope ps_("block_match", s); CK(launch_block_match(a, s)); }
+    return HTSVD_OK;
+}
+
+// Noise level from the covariance eigenvalues (host FP64). M, S: uint64 moments on the host.
+double sigma_from_moments(const unsigned long long* M, const unsigned long long* S, int d, int64_t n) {
+    std::vector<double> A((size_t)d * d), lam(d);
+    const double inv = 1.0 / (double)n;
+    std::vector<double> mu(d);
+    for (int u = 0; u < d; ++u) mu[u] = (double)S[u] / (double)n;
+    for (int u = 0; u < d; ++u)
+        for (int v = 0; v < d; ++v) A[(size_t)u * d + v] = (double)M[(size_t)u * d + v] / (double)n - mu[u] * mu[v];
+    (void)inv;
+    if (!symmetric_eigenvalues(A.data(), d, lam.data())) return -1.0;
+    std::sort(lam.begin(), lam.end());
+    int rstar = 1;
+    double sum = 0.0;
+    std::vector<double> pref(d + 1, 0.0);
+    for (int r = 1; r <= d; ++r) {
+        sum += lam[r - 1];
+        pref[r] = sum;
+        const double mean = sum / r;
+        const double med = (r & 1) ? lam[(r - 1) / 2] : 0.5 * (lam[r / 2 - 1] + lam[r / 2]);
+        if (mean <= 1.02 * med) rstar = r;
+    }
+    const double m = pref[rstar] / rstar;
+    return std::sqrt(m > 0 ? m : 0.0);
+}
+
+// Launches the moments of the quantised image and the basis solve.
+htsvd_status run_basis(Workspace* w, const uint8_t* q, const Geo& g, double** b64, float** b32, cudaStream_t s) {
+    void *mom, *p64, *p32;
+    ST(ws_get(w, S_MOM, sizeof(unsigned long long) * 2 * PS2 * g.C * g.C, &mom));
+    ST(ws_get(w, S_B64, sizeof(double) * 2 * 2 * g.C * PS2, &p64));
+    ST(ws_get(w, S_B32, sizeof(float) * 512, &p32));
+    { ProfScope ps_("moments", s); CK(launch_moments(q, g, (unsigned long long*)mom, s)); }
+    { ProfScope ps_("basis", s); CK(launch_basis((const unsigned long long*)mom, g.C, (double*)p64, (float*)p32, s)); }
+    *b64 = (double*)p64;
+    *b32 = (float*)p32;
+    return HTSVD_OK;
+}
+
+// Launches what the estimate needs (full moment, optional sampled grouping and ranks) and
+// copies it to pinned host memory; *done is recorded after the copies.
+htsvd_status launch_sigma_inputs(Workspace* w, const uint8_t* q, const Geo& g, const Resolved& r, cudaStream_t s,
+                                 void** hbuf) {
+    const int d = PS2 * g.C;
+    void *M, *S;
+    ST(ws_get(w, S_FULLM, sizeof(unsigned long long) * d * d, &M));
+    ST(ws_get(w, S_FULLS, sizeof(unsigned long long) * d, &S));
+    { ProfScope ps_("full_moment", s); CK(launch_full_moment(q, g, (unsigned long long*)M, (unsigned long long*)S, s)); }
+    const int ny8 = (g.nry + 7) / 8, nx8 = (g.nrx + 7) / 8;
+    const size_t hbytes = sizeof(unsigned long long) * (d * d + d) + sizeof(int32_t) * ny8 * nx8;
+    ST(ws_host(w, hbytes, hbuf));
+    unsigned long long* h = (unsigned long long*)*hbuf;
+    CK(cudaMemcpyAsync(h, M, sizeof(unsigned long long) * d * d, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h + (size_t)d * d, S, sizeof(unsigned long long) * d, cudaMemcpyDeviceToHost, s));
+    if (r.adapt) {
+        void *idx2, *ranks;
+        ST(ws_get(w, S_IDX2, sizeof(int32_t) * ny8 * nx8 * g.K, &idx2));
+        ST(ws_get(w, S_RANKS, sizeof(int32_t) * ny8 * nx8, &ranks));
+        ST(run_block_match(q, g, r, 8, (int32_t*)idx2, s));
+        { ProfScope ps_("group_rank", s); CK(launch_group_rank(q, g, (const int32_t*)idx2, ny8 * nx8, (int32_t*)ranks, s)); }
+        CK(cudaMemcpyAsync(h + (size_t)d * d + d, ranks, sizeof(int32_t) * ny8 * nx8, cudaMemcpyDeviceToHost, s));
+    }
+    return HTSVD_OK;
+}
+
+htsvd_status finish_sigma(const void* hbuf, const Geo& g, const Resolved& r, double* sigma) {
+    const int d = PS2 * g.C;
+    const unsigned long long* h = (const unsigned long long*)hbuf;
+    double sg = sigma_from_moments(h, h + (size_t)d * d, d, (int64_t)g.ngroups());
+    if (sg < 0) return HTSVD_ERR_CUDA;
+    if (r.adapt) {
+        const int ny8 = (g.nry + 7) / 8, nx8 = (g.nrx + 7) / 8;
+        const int32_t* ranks = (const int32_t*)(h + (size_t)d * d + d);
+        int low = 0, high = 0;
+        for (int i = 0; i < ny8 * nx8; ++i) (ranks[i] <= r.rank_gamma ? low : high)++;
+        if (low > high) sg /= r.beta;
+    }
+    *sigma = sg;
+    return HTSVD_OK;
+}
+
+struct FilterOut {
+    float* out;
+    float* den_out;
+};
+
+// Filter + reduce for the forward pass.
+htsvd_status run_forward_filter(Workspace* w, const void* img, int is_float, const Geo& g, const Resolved& r,
+                                const int32_t* idx, const double* b64, const float* b32, double tau,
+                                const float* w_in, const htsvd_params* p, float* d_out, cudaStream_t s) {
+    FilterTiling t = choose_filter_tiling(g, is_float ? 4 : 1, FM_FORWARD, r.tile);
+    FilterArgs a{};
+    a.img = img;
+    a.img_is_float = is_float;
+    a.g = g;
+    a.TR = t.TR;
+    a.ntx = t.ntx;
+    a.nty = t.nty;
+    a.FHmax = t.FHmax;
+    a.FWmax = t.FWmax;
+    a.idx = idx;
+    a.basis32 = b32;
+    a.basis64 = b64;
+    a.tau64 = tau;
+    a.tau32 = (float)tau;
+    a.band_rel = 6.103515625e-05f;          // 2^-14 of the group norm (FP32 error bound, with margin)
+    a.band_abs = (float)(tau * 2.384185791015625e-07) + 1e-6f;   // covers tau rounded to FP32
+    a.w_in = w_in;
+    a.agg_mode = r.agg_mode;
+    a.mode = FM_FORWARD;
+    a.mask_out = p ? p->d_mask_out : nullptr;
+    a.weights_out = p ? p->d_weights_out : nullptr;
+    void* part;
+    const int acc = g.C == 3 ? 4 : 2;
+    ST(ws_get(w, S_PART, sizeof(float) * (size_t)t.ntx * t.nty * t.FHmax * t.FWmax * acc, &part));
+    a.partials = (float*)part;
+    { ProfScope ps_("filter", s); CK(launch_filter(a, s)); }
+    { ProfScope ps_("reduce", s); CK(launch_reduce((float*)part, g, t.TR, t.ntx, t.nty, t.FHmax, t.FWmax, d_out, nullptr, 0, nullptr, s)); }
+    return HTSVD_OK;
+}
+
+htsvd_status denoise_impl(const void* d_in, int is_float, int H, int W, int C, double sigma, const htsvd_params* p,
+                          const float* d_w, float* d_out, int32_t* d_idx_out, cudaStream_t s) {
+    if (!d_in || !d_out) return HTSVD_ERR_INVALID_ARG;
+    Resolved r;
+    ST(resolve(p, C, r));
+    ST(check_image(H, W, C, r));
+    if (std::isnan(sigma)) return HTSVD_ERR_INVALID_ARG;
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    const Geo g = make_geo(H, W, C, r.s, r.win, r.K);
+    const int64_t N = g.ngroups();
+    const uint8_t* q = (const uint8_t*)d_in;
+    if (is_float) {
+        void* qb;
+        ST(ws_get(w, S_Q, (size_t)H * W * C, &qb));
+        { ProfScope ps_("quantize", s); CK(launch_quantize((const float*)d_in, (int64_t)H * W * C, (uint8_t*)qb, s)); }
+        q = (const uint8_t*)qb;
+    }
+    int32_t* idx = d_idx_out;
+    if (!idx) {
+        void* ib;
+        ST(ws_get(w, S_IDX, sizeof(int32_t) * N * r.K, &ib));
+        idx = (int32_t*)ib;
+    }
+    void* hbuf = nullptr;
+    if (sigma < 0) ST(launch_sigma_inputs(w, q, g, r, s, &hbuf));
+    cudaEvent_t ev = nullptr;
+    if (sigma < 0) {
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, s));
+    }
+    // Grouping and the bases do not depend on sigma: they run while the host finishes the estimate.
+    ST(run_block_match(q, g, r, 1, idx, s));
+    double* b64;
+    float* b32;
+    ST(run_basis(w, q, g, &b64, &b32, s));
+    if (p && p->d_basis_out)
+        CK(cudaMemcpyAsync(p->d_basis_out, b64, sizeof(double) * 2 * 2 * C * PS2, cudaMemcpyDeviceToDevice, s));
+    if (sigma < 0) {
+        cudaError_t e = cudaEventSynchronize(ev);
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess) return HTSVD_ERR_CUDA;
+        ST(finish_sigma(hbuf, g, r, &sigma));
+    }
+    if (p && p->h_sigma_out) *p->h_sigma_out = sigma;
+    const double tau = r.tau_mult * sigma;
+    return run_forward_filter(w, is_float ? d_in : (const void*)q, is_float, g, r, idx, b64, b32, tau, d_w, p, d_out,
+                              s);
+}
+
+}  // namespace
+
+// ============================================================================= C ABI
+
+extern "C" {
+
+htsvd_status htsvd_denoise(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, double sigma,
+                           const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t stream) {
+    return denoise_impl(d_noisy, 0, H, W, C, sigma, p, nullptr, d_out, d_idx_out, stream);
+}
+
+htsvd_status htsvd_denoise_f32(const float* d_x, int32_t H, int32_t W, int32_t C, double sigma,
+                               const htsvd_params* p, const float* d_w, float* d_out, int32_t* d_idx_out,
+                               cudaStream_t stream) {
+    return denoise_impl(d_x, 1, H, W, C, sigma, p, d_w, d_out, d_idx_out, stream);
+}
+
+htsvd_status htsvd_estimate_sigma(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, const htsvd_params* p,
+                                  double* h_sigma, cudaStream_t stream) {
+    if (!d_noisy || !h_sigma) return HTSVD_ERR_INVALID_ARG;
+    Resolved r;
+    ST(resolve(p, C, r));
+    ST(check_image(H, W, C, r));
+    Workspace* w = workspace_for(stream);
+    if (!w) return HTSVD_ERR_OOM;
+    const Geo g = make_geo(H, W, C, r.s, r.win, r.K);
+    void* hbuf;
+    ST(launch_sigma_inputs(w, d_noisy, g, r, stream, &hbuf));
+    CK(cudaStreamSynchronize(stream));
+    return finish_sigma(hbuf, g, r, h_sigma);
+}
+
+htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C, double sigma,
+                               const htsvd_params* p, const int32_t* d_idx, const float* d_w, const float* d_out,
+                               const float* d_grad_out, float* d_grad_x, float* d_grad_w, cudaStream_t s) {
+    if (!d_x || !d_idx || !d_out || !d_grad_out || !d_grad_x) return HTSVD_ERR_INVALID_ARG;
+    if (!(sigma >= 0)) return HTSVD_ERR_INVALID_ARG;
+    Resolved r;
+    ST(resolve(p, C, r));
+    ST(check_image(H, W, C, r));
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    const Geo g = make_geo(H, W, C, r.s, r.win, r.K);
+    const int64_t npix = (int64_t)H * W;
+    void *qb, *den, *rimg, *tmp;
+    ST(ws_get(w, S_Q, (size_t)npix * C, &qb));
+    ST(ws_get(w, S_DEN, sizeof(float) * npix, &den));
+    ST(ws_get(w, S_R, sizeof(float) * npix * C, &rimg));
+    ST(ws_get(w, S_TMP, sizeof(float) * npix * C, &tmp));
+    { ProfScope ps_("quantize", s); CK(launch_quantize(d_x, npix * C, (uint8_t*)qb, s)); }
+    double* b64;
+    float* b32;
+    ST(run_basis(w, (const uint8_t*)qb, g, &b64, &b32, s));
+    const double tau = r.tau_mult * sigma;
+
+    // D = sum_g w_g Scatter_g 1
+    FilterTiling td = choose_filter_tiling(g, 4, FM_DENOM, r.tile);
+    FilterArgs a{};
+    a.img = d_x;
+    a.img_is_float = 1;
+    a.g = g;
+    a.idx = d_idx;
+    a.basis32 = b32;
+    a.basis64 = b64;
+    a.tau64 = tau;
+    a.tau32 = (float)tau;
+    a.band_rel = 6.103515625e-05f;
+    a.band_abs = (float)(tau * 2.384185791015625e-07) + 1e-6f;
+    a.w_in = d_w;
+    a.agg_mode = 0;
+    a.mode = FM_DENOM;
+    a.TR = td.TR;
+    a.ntx = td.ntx;
+    a.nty = td.nty;
+    a.FHmax = td.FHmax;
+    a.FWmax = td.FWmax;
+    const int acc = C == 3 ? 4 : 2;
+    void* part;
+    ST(ws_get(w, S_PART, sizeof(float) * (size_t)td.ntx * td.nty * td.FHmax * td.FWmax * acc, &part));
+    a.partials = (float*)part;
+    { ProfScope ps_("filter", s); CK(launch_filter(a, s)); }
+    { ProfScope ps_("reduce", s); CK(launch_reduce((float*)part, g, td.TR, td.ntx, td.nty, td.FHmax, td.FWmax, (float*)tmp, (float*)den, 0,
+                     nullptr, s)); }
+    { ProfScope ps_("div", s); CK(launch_div(d_grad_out, (const float*)den, npix, C, (float*)rimg, s)); }
+
+    // adjoint filter on r = gout / D with the masks of x
+    FilterTiling ta = choose_filter_tiling(g, 4, FM_ADJOINT, r.tile);
+    a.mode = FM_ADJOINT;
+    a.TR = ta.TR;
+    a.ntx = ta.ntx;
+    a.nty = ta.nty;
+    a.FHmax = ta.FHmax;
+    a.FWmax = ta.FWmax;
+    a.r_img = (const float*)rimg;
+    a.out_img = d_out;
+    a.grad_w = d_grad_w;
+    ST(ws_get(w, S_PART, sizeof(float) * (size_t)ta.ntx * ta.nty * ta.FHmax * ta.FWmax * acc, &part));
+    a.partials = (float*)part;
+    { ProfScope ps_("filter", s); CK(launch_filter(a, s)); }
+    { ProfScope ps_("reduce", s); CK(launch_reduce((float*)part, g, ta.TR, ta.ntx, ta.nty, ta.FHmax, ta.FWmax, d_grad_x, nullptr, 1, nullptr, s)); }
+    return HTSVD_OK;
+}
+
+htsvd_status htsvd_denoise_batch(const htsvd_image* imgs, int32_t n, const htsvd_params* p, cudaStream_t s) {
+    if (n < 0 || (n > 0 && !imgs)) return HTSVD_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!(imgs[i].sigma >= 0)) return HTSVD_ERR_INVALID_ARG;
+        htsvd_params q;
+        if (p) q = *p;
+        else std::memset(&q, 0, sizeof(q));
+        q.h_sigma_out = nullptr;
+        q.d_mask_out = nullptr;
+        q.d_weights_out = nullptr;
+        q.d_basis_out = nullptr;
+        htsvd_status st = htsvd_denoise(imgs[i].d_in, imgs[i].H, imgs[i].W, imgs[i].C, imgs[i].sigma, &q,
+                                        imgs[i].d_out, nullptr, s);
+        if (st != HTSVD_OK) return st;
+    }
+    return HTSVD_OK;
+}
+
+int64_t htsvd_num_groups(int32_t H, int32_t W, const htsvd_params* p) {
+    Resolved r;
+    if (resolve(p, 1, r) != HTSVD_OK) return -1;
+    if (H < r.ps || W < r.ps) return -1;
+    return (int64_t)ref_count(H, r.s) * ref_count(W, r.s);
+}
+
+const char* htsvd_status_string(htsvd_status s) {
+    switch (s) {
+        case HTSVD_OK: return "ok";
+        case HTSVD_ERR_INVALID_ARG: return "invalid argument";
+        case HTSVD_ERR_UNSUPPORTED: return "unsupported configuration";
+        case HTSVD_ERR_CUDA: return "CUDA error";
+        case HTSVD_ERR_OOM: return "out of memory";
+        case HTSVD_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+htsvd_status htsvd_profile_enable(int32_t enable) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = enable != 0;
+    return HTSVD_OK;
+}
+
+int32_t htsvd_profile_collect(int32_t max_kernels, char* names, int32_t name_len, int64_t* launches,
+                              double* total_ms) {
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        recs.swap(g_prof);
+    }
+    std::vector<std::string> nm;
+    std::vector<int64_t> cnt;
+    std::vector<double> tot;
+    int32_t status = 0;
+    for (const ProfRec& r : recs) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            status = -1;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+        size_t i = 0;
+        while (i < nm.size() && nm[i] != r.name) ++i;
+        if (i == nm.size()) {
+            nm.push_back(r.name);
+            cnt.push_back(0);
+            tot.push_back(0.0);
+        }
+        cnt[i] += 1;
+        tot[i] += ms;
+    }
+    if (status < 0) return -1;
+    const int32_t n = (int32_t)nm.size() < max_kernels ? (int32_t)nm.size() : max_kernels;
+    for (int32_t i = 0; i < n; ++i) {
+        if (names && name_len > 0) {
+            std::strncpy(names + (size_t)i * name_len, nm[i].c_str(), name_len - 1);
+            names[(size_t)i * name_len + name_len - 1] = 0;
+        }
+        if (launches) launches[i] = cnt[i];
+        if (total_ms) total_ms[i] = tot[i];
+    }
+    return n;
+}
+
+htsvd_status htsvd_release_workspace(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HTSVD_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto it = g_ws.begin(); it != g_ws.end();) {
+        Workspace* w = *it;
+        if (w->device == dev) {
+            for (int i = 0; i < S_NSLOT; ++i)
+                if (w->buf[i]) cudaFree(w->buf[i]);
+            if (w->hpin) cudaFreeHost(w->hpin);
+            delete w;
+            it = g_ws.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return HTSVD_OK;
+}
+
+}  // extern "C"

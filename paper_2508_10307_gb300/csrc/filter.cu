@@ -1,0 +1,130 @@
+// Dispatch of the group filter, and the deterministic reduction of tile partials.
+#include "filter_impl.cuh"
+
+namespace htsvd {
+
+namespace {
+
+template <int K, int C>
+cudaError_t dispatch_mode(const FilterArgs& a, cudaStream_t s) {
+    switch (a.mode) {
+        case FM_FORWARD:
+            return a.img_is_float ? launch_filter_t<K, C, float, FM_FORWARD>(a, s)
+                                  : launch_filter_t<K, C, uint8_t, FM_FORWARD>(a, s);
+        case FM_DENOM:
+            return launch_filter_t<K, C, float, FM_DENOM>(a, s);
+        case FM_ADJOINT:
+            return a.img_is_float ? launch_filter_t<K, C, float, FM_ADJOINT>(a, s) : cudaErrorInvalidValue;
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int C>
+cudaError_t dispatch_k(const FilterArgs& a, cudaStream_t s) {
+    switch (a.g.K) {
+        case 2: return dispatch_mode<2, C>(a, s);
+        case 4: return dispatch_mode<4, C>(a, s);
+        case 8: return dispatch_mode<8, C>(a, s);
+        case 16: return dispatch_mode<16, C>(a, s);
+        case 32: return dispatch_mode<32, C>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// First tile (along one axis) whose footprint ends after p, and last tile whose footprint starts at or before p.
+__device__ inline void covering_tiles(int p, int nt, int TR, int nref, int s, int n, int npos, int wlen, int win,
+                                      int& lo, int& hi) {
+    int a = 0, b = nt - 1;
+    while (a < b) {           // smallest t with f1(t) > p
+        int m = (a + b) >> 1, f0, f1;
+        tile_span(m, TR, nref, s, n, npos, wlen, win, f0, f1);
+        if (f1 > p) b = m;
+        else a = m + 1;
+    }
+    lo = a;
+    a = 0;
+    b = nt - 1;
+    while (a < b) {           // largest t with f0(t) <= p
+        int m = (a + b + 1) >> 1, f0, f1;
+        tile_span(m, TR, nref, s, n, npos, wlen, win, f0, f1);
+        if (f0 <= p) a = m;
+        else b = m - 1;
+    }
+    hi = a;
+}
+
+template <int C>
+__global__ void reduce_kernel(const float* __restrict__ partials, Geo g, int TR, int ntx, int nty, int FHmax,
+                              int FWmax, float* __restrict__ out, float* __restrict__ den_out, int num_only,
+                              const float* __restrict__ den_in) {
+    constexpr int ACC = (C == 3) ? 4 : 2;
+    const int64_t npix = (int64_t)g.H * g.W;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(p / g.W), x = (int)(p - (int64_t)y * g.W);
+        int ylo, yhi, xlo, xhi;
+        covering_tiles(y, nty, TR, g.nry, g.s, g.H, g.npy, g.wny, g.win, ylo, yhi);
+        covering_tiles(x, ntx, TR, g.nrx, g.s, g.W, g.npx, g.wnx, g.win, xlo, xhi);
+        float v[ACC];
+#pragma unroll
+        for (int c = 0; c < ACC; ++c) v[c] = 0.f;
+        for (int ty = ylo; ty <= yhi; ++ty) {
+            int fy0, fy1;
+            tile_span(ty, TR, g.nry, g.s, g.H, g.npy, g.wny, g.win, fy0, fy1);
+            for (int tx = xlo; tx <= xhi; ++tx) {
+                int fx0, fx1;
+                tile_span(tx, TR, g.nrx, g.s, g.W, g.npx, g.wnx, g.win, fx0, fx1);
+                const float* src = partials + (((size_t)(ty * ntx + tx) * FHmax + (y - fy0)) * FWmax + (x - fx0)) * ACC;
+                if constexpr (C == 3) {
+                    const float4 q = *reinterpret_cast<const float4*>(src);
+                    v[0] += q.x; v[1] += q.y; v[2] += q.z; v[3] += q.w;
+                } else {
+                    const float2 q = *reinterpret_cast<const float2*>(src);
+                    v[0] += q.x; v[1] += q.y;
+                }
+            }
+        }
+        const float den = den_in ? den_in[p] : v[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) out[p * C + c] = num_only ? v[c] : v[c] / den;
+        if (den_out) den_out[p] = v[C];
+    }
+}
+
+__global__ void div_kernel(const float* __restrict__ gout, const float* __restrict__ den, int64_t npix, int C,
+                           float* __restrict__ r) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix * C; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = gout[i] / den[i / C];
+}
+
+}  // namespace
+
+size_t filter_smem_bytes(const FilterArgs& a) {
+    const int inb = a.img_is_float ? 4 : 1;
+    if (a.g.C == 3) return f_layout<32, 3>(a.FHmax, a.FWmax, inb, a.mode).total;
+    return f_layout<32, 1>(a.FHmax, a.FWmax, inb, a.mode).total;
+}
+
+cudaError_t launch_filter(const FilterArgs& a, cudaStream_t s) {
+    return a.g.C == 3 ? dispatch_k<3>(a, s) : dispatch_k<1>(a, s);
+}
+
+cudaError_t launch_reduce(const float* partials, const Geo& g, int TR, int ntx, int nty, int FHmax, int FWmax,
+                          float* out, float* den_out, int num_only, const float* den_in, cudaStream_t s) {
+    const int64_t npix = (int64_t)g.H * g.W;
+    int blocks = (int)((npix + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (g.C == 3)
+        reduce_kernel<3><<<blocks, 256, 0, s>>>(partials, g, TR, ntx, nty, FHmax, FWmax, out, den_out, num_only, den_in);
+    else
+        reduce_kernel<1><<<blocks, 256, 0, s>>>(partials, g, TR, ntx, nty, FHmax, FWmax, out, den_out, num_only, den_in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_div(const float* gout, const float* den, int64_t npix, int C, float* r, cudaStream_t s) {
+    int blocks = (int)((npix * C + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    div_kernel<<<blocks, 256, 0, s>>>(gout, den, npix, C, r);
+    return cudaGetLastError();
+}
+
+}  // namespace htsvd

@@ -1,0 +1,610 @@
+// Collaborative filter and aggregation (Alg. 1 Steps 2(2)-(4) and 3).
+//
+// Per group (Sec. III-B.2):
+//   S = U^T * G * V  x_4 H_K            (Eq. (forward transform); t-products evaluated per
+//                                         Fourier slice after an FFT along channels)
+//   S_t = S . [|S| >= tau]               (Eq. (hard thresholding))
+//   G^ = U * S_t * V^T  x_4 H_K^T        (Eq. (backward transform), exact inverse)
+// and every estimated patch is written back with weight w_g (Eq. (aggregation)).
+//
+// One CTA (256 threads, 8 warps) per tile of TR x TR references. The CTA stages the
+// image footprint of the tile (union of its search windows) in shared memory and keeps
+// a numerator/denominator accumulator for that footprint; groups are processed one at a
+// time, all data of a group living in shared memory / registers:
+//   A  thread (k, b): column b of patch k -> channel DFT -> Y_f = U_f^H X_f
+//   B  thread (i, k): row i -> S_f = Y_f V_f -> inverse channel DFT (real S)
+//   C  thread = fibre (i, j, c): Haar butterflies along the K patches, threshold,
+//      inverse butterflies. Coefficients whose FP32 value lies inside a guard band
+//      around tau get their keep/drop decision recomputed in FP64 (one warp per entry).
+//   D  thread (i, k): channel DFT -> Z_f = T_f V_f^H
+//   E  thread (k, b): G_f = U_f Z_f -> inverse channel DFT (real estimate)
+//   F  warp w owns footprint rows r with r mod 8 == w: it adds row (w - y_k) mod 8 of
+//      every patch k, k ascending. No atomics, fixed order: bitwise reproducible.
+// The tile's accumulator is written to a partial buffer; reduce_kernel sums the
+// overlapping tile partials in fixed tile order and divides.
+#pragma once
+#include "kernels.h"
+
+namespace htsvd {
+
+constexpr int FT_THREADS = 256;
+constexpr float F_S3H = 0.866025403784438646763723170752936183f;   // sqrt(3)/2
+constexpr float F_SQ3 = 1.73205080756887729352744634150587237f;    // sqrt(3)
+constexpr float F_R2 = 0.707106781186547524400844362104849039f;    // 1/sqrt(2)
+constexpr float F_THIRD = 0.333333333333333333333333333333333333f;
+
+template <int C>
+struct FCfg {
+    static constexpr int RWF = PS * C;                 // floats per patch row
+    static constexpr int PATCH = PS2 * C;              // floats per patch
+    static constexpr int GS = (C == 3) ? 196 : 68;     // padded stride between patches in the group buffer
+    static constexpr int ACC = (C == 3) ? 4 : 2;       // floats per footprint pixel (C numerators + 1 denominator)
+    static constexpr int NBAS = (C == 3) ? 384 : 128;  // packed FP32 basis floats
+};
+
+// Shared-memory layout (bytes), identical on host and device.
+struct FLayout {
+    int off_bas, off_gb, off_pos, off_band, off_rkeep, off_misc, off_acc, off_img, off_r, total;
+};
+template <int K, int C>
+__host__ __device__ inline FLayout f_layout(int FH, int FW, int in_bytes, int mode) {
+    using G = FCfg<C>;
+    FLayout L;
+    int o = 0;
+    L.off_bas = o; o += 512 * 4;
+    L.off_gb = o; o += K * G::GS * 4;
+    L.off_pos = o; o += 64 * 4;
+    L.off_band = o; o += 192 * 4;
+    L.off_rkeep = o; o += 192 * 4;
+    L.off_misc = o; o += 16 * 4;
+    L.off_acc = o; o += FH * FW * G::ACC * 4;
+    L.off_img = o; o += ((mode == FM_DENOM ? 0 : FH * FW * C * in_bytes) + 15) / 16 * 16;
+    L.off_r = o; o += (mode == FM_ADJOINT) ? FH * FW * C * 4 : 0;
+    L.total = o;
+    return L;
+}
+
+// In-register Haar analysis along the group mode: o = H_K a (Eq. (H_2N) applied recursively).
+template <int K>
+__device__ __forceinline__ void haar_fwd(float (&a)[K], float (&o)[K]) {
+#pragma unroll
+    for (int n = K; n > 1; n >>= 1) {
+#pragma unroll
+        for (int m = 0; m < n / 2; ++m) {
+            const float x = a[2 * m], y = a[2 * m + 1];
+            o[n / 2 + m] = (x - y) * F_R2;
+            a[m] = (x + y) * F_R2;
+        }
+    }
+    o[0] = a[0];
+}
+// Synthesis a = H_K^T o.
+template <int K>
+__device__ __forceinline__ void haar_inv(float (&o)[K], float (&a)[K]) {
+    a[0] = o[0];
+#pragma unroll
+    for (int n = 2; n <= K; n <<= 1) {
+#pragma unroll
+        for (int m = n / 2 - 1; m >= 0; --m) {
+            const float s = a[m], d = o[n / 2 + m];
+            a[2 * m] = (s + d) * F_R2;
+            a[2 * m + 1] = (s - d) * F_R2;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ float ldv(const T* p) { return (float)p[0]; }
+
+// FP64 value of one coefficient S[m][i][j][c] of the group, from the staged inputs:
+// S = T(sum_k H[m,k] P_k) with T the real t-SVD projection; returns |S| >= tau.
+template <int K, int C, typename Tin>
+__device__ bool refine_keep(int m, int e, const Tin* img_s, int FW, const int* pos, const double* __restrict__ b64,
+                            double tau64, int lane) {
+    int k0, L;
+    if (m == 0) {
+        k0 = 0;
+        L = K;
+    } else {
+        const int l = 31 - __clz(m);
+        L = K >> l;
+        k0 = (m - (1 << l)) * L;
+    }
+    const int half = (m == 0) ? L : L / 2;
+    const double h = 1.0 / sqrt((double)L);
+    const int pix = e / C, ch = e - pix * C;
+    const int i = pix / PS, j = pix % PS;
+    double s0 = 0.0, s1r = 0.0, s1i = 0.0;
+    const double s3h = 0.5 * sqrt(3.0);
+    for (int p = lane; p < PS2; p += 32) {
+        const int aa = p / PS, bb = p % PS;
+        double q[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) q[c] = 0.0;
+        for (int kk = k0; kk < k0 + L; ++kk) {
+            const Tin* src = img_s + ((pos[2 * kk] + aa) * FW + pos[2 * kk + 1] + bb) * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const double v = (double)src[c];
+                q[c] += (kk - k0 < half) ? v : -v;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) q[c] *= h;
+        const double u0 = b64[(0 * C + 0) * 2 * PS2 + 2 * (aa * PS + i)];
+        const double v0 = b64[(1 * C + 0) * 2 * PS2 + 2 * (bb * PS + j)];
+        if (C == 3) {
+            const double Q0 = q[0] + q[1] + q[2];
+            const double Q1r = q[0] - 0.5 * (q[1] + q[2]);
+            const double Q1i = s3h * (q[2] - q[1]);
+            s0 += u0 * Q0 * v0;
+            const double u1r = b64[(0 * C + 1) * 2 * PS2 + 2 * (aa * PS + i)];
+            const double u1i = b64[(0 * C + 1) * 2 * PS2 + 2 * (aa * PS + i) + 1];
+            const double v1r = b64[(1 * C + 1) * 2 * PS2 + 2 * (bb * PS + j)];
+            const double v1i = b64[(1 * C + 1) * 2 * PS2 + 2 * (bb * PS + j) + 1];
+            const double tr = u1r * Q1r + u1i * Q1i;       // conj(u1) * Q1
+            const double ti = u1r * Q1i - u1i * Q1r;
+            s1r += tr * v1r - ti * v1i;
+            s1i += tr * v1i + ti * v1r;
+        } else {
+            s0 += u0 * q[0] * v0;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1r += __shfl_xor_sync(0xffffffffu, s1r, off);
+        s1i += __shfl_xor_sync(0xffffffffu, s1i, off);
+    }
+    double S;
+    if (C == 3) {
+        const double sq3 = sqrt(3.0);
+        S = (ch == 0) ? (s0 + 2.0 * s1r) / 3.0 : (ch == 1) ? (s0 - s1r - sq3 * s1i) / 3.0 : (s0 - s1r + sq3 * s1i) / 3.0;
+    } else {
+        S = s0;
+    }
+    return fabs(S) >= tau64;
+}
+
+// Stage A: thread (k, b) -> Y_f[:, b] of patch k. Returns the sum of squares of its inputs.
+template <int K, int C, typename Tin>
+__device__ __forceinline__ float stage_a(const Tin* img_s, int FW, const int* pos, const float* bas, float* gb,
+                                         int k, int b) {
+    using G = FCfg<C>;
+    const Tin* src = img_s + (pos[2 * k] * FW + pos[2 * k + 1] + b) * C;
+    float x[PS][C];
+    float nrm = 0.f;
+#pragma unroll
+    for (int i = 0; i < PS; ++i)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            x[i][c] = ldv(src + i * FW * C + c);
+            nrm += x[i][c] * x[i][c];
+        }
+    float* dst = gb + k * G::GS + b * C;
+    if constexpr (C == 3) {
+        float X0[PS], X1r[PS], X1i[PS];
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            X0[i] = x[i][0] + x[i][1] + x[i][2];
+            X1r[i] = x[i][0] - 0.5f * (x[i][1] + x[i][2]);
+            X1i[i] = F_S3H * (x[i][2] - x[i][1]);
+        }
+        const float* U0 = bas;
+        const float* U1r = bas + 64;
+        const float* U1i = bas + 128;
+#pragma unroll
+        for (int ii = 0; ii < PS; ++ii) {
+            float y0 = 0.f, yr = 0.f, yi = 0.f;
+#pragma unroll
+            for (int a = 0; a < PS; ++a) {
+                const float u0 = U0[a * PS + ii], ur = U1r[a * PS + ii], ui = U1i[a * PS + ii];
+                y0 = fmaf(u0, X0[a], y0);
+                yr = fmaf(ur, X1r[a], fmaf(ui, X1i[a], yr));
+                yi = fmaf(ur, X1i[a], fmaf(-ui, X1r[a], yi));
+            }
+            dst[ii * G::RWF + 0] = y0;
+            dst[ii * G::RWF + 1] = yr;
+            dst[ii * G::RWF + 2] = yi;
+        }
+    } else {
+        const float* U0 = bas;
+#pragma unroll
+        for (int ii = 0; ii < PS; ++ii) {
+            float y0 = 0.f;
+#pragma unroll
+            for (int a = 0; a < PS; ++a) y0 = fmaf(U0[a * PS + ii], x[a][0], y0);
+            dst[ii * G::RWF] = y0;
+        }
+    }
+    return nrm;
+}
+
+// Stage B: thread (i, k): S = Y V, inverse channel DFT, in place on row i of patch k.
+template <int C>
+__device__ __forceinline__ void stage_b(const float* bas, float* gb, int k, int i) {
+    using G = FCfg<C>;
+    float4* row = reinterpret_cast<float4*>(gb + k * G::GS + i * G::RWF);
+    float y[G::RWF];
+#pragma unroll
+    for (int q = 0; q < G::RWF / 4; ++q) {
+        float4 v = row[q];
+        y[4 * q] = v.x; y[4 * q + 1] = v.y; y[4 * q + 2] = v.z; y[4 * q + 3] = v.w;
+    }
+    float o[G::RWF];
+    if constexpr (C == 3) {
+        const float* V0 = bas + 192;
+        const float* V1r = bas + 256;
+        const float* V1i = bas + 320;
+#pragma unroll
+        for (int j = 0; j < PS; ++j) {
+            float s0 = 0.f, sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int b = 0; b < PS; ++b) {
+                const float v0 = V0[b * PS + j], vr = V1r[b * PS + j], vi = V1i[b * PS + j];
+                const float y0 = y[3 * b], yr = y[3 * b + 1], yi = y[3 * b + 2];
+                s0 = fmaf(y0, v0, s0);
+                sr = fmaf(yr, vr, fmaf(-yi, vi, sr));
+                si = fmaf(yr, vi, fmaf(yi, vr, si));
+            }
+            o[3 * j + 0] = (s0 + 2.f * sr) * F_THIRD;
+            o[3 * j + 1] = (s0 - sr - F_SQ3 * si) * F_THIRD;
+            o[3 * j + 2] = (s0 - sr + F_SQ3 * si) * F_THIRD;
+        }
+    } else {
+        const float* V0 = bas + 64;
+#pragma unroll
+        for (int j = 0; j < PS; ++j) {
+            float s0 = 0.f;
+#pragma unroll
+            for (int b = 0; b < PS; ++b) s0 = fmaf(y[b], V0[b * PS + j], s0);
+            o[j] = s0;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < G::RWF / 4; ++q) row[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+}
+
+// Stage D: thread (i, k): channel DFT, Z = T V^H, in place on row i of patch k.
+template <int C>
+__device__ __forceinline__ void stage_d(const float* bas, float* gb, int k, int i) {
+    using G = FCfg<C>;
+    float4* row = reinterpret_cast<float4*>(gb + k * G::GS + i * G::RWF);
+    float t[G::RWF];
+#pragma unroll
+    for (int q = 0; q < G::RWF / 4; ++q) {
+        float4 v = row[q];
+        t[4 * q] = v.x; t[4 * q + 1] = v.y; t[4 * q + 2] = v.z; t[4 * q + 3] = v.w;
+    }
+    float o[G::RWF];
+    if constexpr (C == 3) {
+        float T0[PS], T1r[PS], T1i[PS];
+#pragma unroll
+        for (int j = 0; j < PS; ++j) {
+            T0[j] = t[3 * j] + t[3 * j + 1] + t[3 * j + 2];
+            T1r[j] = t[3 * j] - 0.5f * (t[3 * j + 1] + t[3 * j + 2]);
+            T1i[j] = F_S3H * (t[3 * j + 2] - t[3 * j + 1]);
+        }
+        const float* V0 = bas + 192;
+        const float* V1r = bas + 256;
+        const float* V1i = bas + 320;
+#pragma unroll
+        for (int b = 0; b < PS; ++b) {
+            float z0 = 0.f, zr = 0.f, zi = 0.f;
+#pragma unroll
+            for (int j = 0; j < PS; ++j) {
+                const float v0 = V0[b * PS + j], vr = V1r[b * PS + j], vi = V1i[b * PS + j];
+                z0 = fmaf(T0[j], v0, z0);
+                zr = fmaf(T1r[j], vr, fmaf(T1i[j], vi, zr));
+                zi = fmaf(T1i[j], vr, fmaf(-T1r[j], vi, zi));
+            }
+            o[3 * b] = z0; o[3 * b + 1] = zr; o[3 * b + 2] = zi;
+        }
+    } else {
+        const float* V0 = bas + 64;
+#pragma unroll
+        for (int b = 0; b < PS; ++b) {
+            float z = 0.f;
+#pragma unroll
+            for (int j = 0; j < PS; ++j) z = fmaf(t[j], V0[b * PS + j], z);
+            o[b] = z;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < G::RWF / 4; ++q) row[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+}
+
+// Stage E: thread (k, b): G = U Z, inverse channel DFT, in place on column b of patch k.
+template <int C>
+__device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int b) {
+    using G = FCfg<C>;
+    float* col = gb + k * G::GS + b * C;
+    if constexpr (C == 3) {
+        float Z0[PS], Zr[PS], Zi[PS];
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            Z0[i] = col[i * G::RWF];
+            Zr[i] = col[i * G::RWF + 1];
+            Zi[i] = col[i * G::RWF + 2];
+        }
+        const float* U0 = bas;
+        const float* U1r = bas + 64;
+        const float* U1i = bas + 128;
+#pragma unroll
+        for (int a = 0; a < PS; ++a) {
+            float g0 = 0.f, gr = 0.f, gi = 0.f;
+#pragma unroll
+            for (int i = 0; i < PS; ++i) {
+                const float u0 = U0[a * PS + i], ur = U1r[a * PS + i], ui = U1i[a * PS + i];
+                g0 = fmaf(u0, Z0[i], g0);
+                gr = fmaf(ur, Zr[i], fmaf(-ui, Zi[i], gr));
+                gi = fmaf(ur, Zi[i], fmaf(ui, Zr[i], gi));
+            }
+            col[a * G::RWF + 0] = (g0 + 2.f * gr) * F_THIRD;
+            col[a * G::RWF + 1] = (g0 - gr - F_SQ3 * gi) * F_THIRD;
+            col[a * G::RWF + 2] = (g0 - gr + F_SQ3 * gi) * F_THIRD;
+        }
+    } else {
+        float Z[PS];
+#pragma unroll
+        for (int i = 0; i < PS; ++i) Z[i] = col[i * G::RWF];
+        const float* U0 = bas;
+#pragma unroll
+        for (int a = 0; a < PS; ++a) {
+            float g0 = 0.f;
+#pragma unroll
+            for (int i = 0; i < PS; ++i) g0 = fmaf(U0[a * PS + i], Z[i], g0);
+            col[a * G::RWF] = g0;
+        }
+    }
+}
+
+template <int K, int C, typename Tin, int MODE>
+__global__ void __launch_bounds__(FT_THREADS, 1) filter_kernel(FilterArgs a) {
+    using G = FCfg<C>;
+    constexpr int NF = G::PATCH;                 // fibres
+    constexpr int NBW = K * NF / 32;             // bitmap words per group
+    const Geo& g = a.g;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ty = blockIdx.x / a.ntx, tx = blockIdx.x - ty * a.ntx;
+    int FY0, FY1, FX0, FX1;
+    tile_span(ty, a.TR, g.nry, g.s, g.H, g.npy, g.wny, g.win, FY0, FY1);
+    tile_span(tx, a.TR, g.nrx, g.s, g.W, g.npx, g.wnx, g.win, FX0, FX1);
+    const int FH = FY1 - FY0, FW = FX1 - FX0;
+    const FLayout L = f_layout<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), MODE);
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* bas = reinterpret_cast<float*>(smem + L.off_bas);
+    float* gb = reinterpret_cast<float*>(smem + L.off_gb);
+    int* pos = reinterpret_cast<int*>(smem + L.off_pos);
+    uint32_t* band = reinterpret_cast<uint32_t*>(smem + L.off_band);
+    uint32_t* rkeep = reinterpret_cast<uint32_t*>(smem + L.off_rkeep);
+    int* misc = reinterpret_cast<int*>(smem + L.off_misc);
+    float* acc = reinterpret_cast<float*>(smem + L.off_acc);
+    Tin* img_s = reinterpret_cast<Tin*>(smem + L.off_img);
+    float* r_s = reinterpret_cast<float*>(smem + L.off_r);
+
+    // Stage the basis, the image footprint and clear the accumulator.
+    if constexpr (MODE != FM_DENOM) {
+        for (int t = tid; t < G::NBAS; t += FT_THREADS) bas[t] = a.basis32[t];
+        const Tin* img = reinterpret_cast<const Tin*>(a.img);
+        const int rowb = FW * C;
+        for (int t = tid; t < FH * rowb; t += FT_THREADS) {
+            const int r = t / rowb, cb = t - r * rowb;
+            img_s[t] = img[((size_t)(FY0 + r) * g.W + FX0) * C + cb];
+        }
+        if constexpr (MODE == FM_ADJOINT) {
+            for (int t = tid; t < FH * rowb; t += FT_THREADS) {
+                const int r = t / rowb, cb = t - r * rowb;
+                r_s[t] = a.r_img[((size_t)(FY0 + r) * g.W + FX0) * C + cb];
+            }
+        }
+    }
+    for (int t = tid; t < FH * FW * G::ACC; t += FT_THREADS) acc[t] = 0.f;
+
+    const int iy0 = ty * a.TR, ix0 = tx * a.TR;
+    const int th = min(a.TR, g.nry - iy0), tw = min(a.TR, g.nrx - ix0);
+    for (int q = 0; q < th * tw; ++q) {
+        const int grp = (iy0 + q / tw) * g.nrx + ix0 + q % tw;
+        __syncthreads();
+        if (tid < K) {
+            // Positions come from the grouping of this geometry and lie in the footprint; a caller-given
+            // index outside it is clamped so that no access leaves the staged region.
+            const int v = a.idx[(size_t)grp * K + tid];
+            const int y = v / g.W, x = v - y * g.W;
+            pos[2 * tid] = min(max(y - FY0, 0), FH - PS);
+            pos[2 * tid + 1] = min(max(x - FX0, 0), FW - PS);
+        }
+        if (tid < NBW) {
+            band[tid] = 0u;
+            rkeep[tid] = 0u;
+        }
+        if (tid < 16) misc[tid] = 0;
+        __syncthreads();
+
+        float wg = 1.f;
+        float cx[K];          // FM_ADJOINT: coefficients at x of this thread's fibre
+        uint32_t keepb = 0;
+        if constexpr (MODE != FM_DENOM) {
+            // ---- A, B on the filtered image
+            if (tid < 8 * K) {
+                const float nrm = stage_a<K, C, Tin>(img_s, FW, pos, bas, gb, tid >> 3, tid & 7);
+                atomicAdd(reinterpret_cast<float*>(&misc[2]), nrm);
+            }
+            __syncthreads();
+            if (tid < 8 * K) stage_b<C>(bas, gb, tid % K, tid / K);
+            __syncthreads();
+            // ---- C1: Haar analysis and FP32 decisions with a guard band
+            const float nrm2 = __int_as_float(misc[2]);
+            const float delta = a.band_rel * sqrtf(nrm2) + a.band_abs;
+            float co[K];
+            uint32_t bandb = 0;
+            if (tid < NF) {
+                float fib[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) fib[k] = gb[k * G::GS + tid];
+                haar_fwd<K>(fib, co);
+#pragma unroll
+                for (int m = 0; m < K; ++m) {
+                    const float d = fabsf(co[m]) - a.tau32;
+                    if (fabsf(d) <= delta) bandb |= 1u << m;
+                    else if (d >= 0.f) keepb |= 1u << m;
+                }
+                if (bandb) {
+                    atomicAdd(&misc[0], __popc(bandb));
+#pragma unroll
+                    for (int m = 0; m < K; ++m)
+                        if ((bandb >> m) & 1u) atomicOr(&band[(m * NF + tid) >> 5], 1u << (tid & 31));
+                }
+            }
+            __syncthreads();
+            // ---- FP64 decisions inside the band (rare)
+            if (misc[0] > 0) {
+                for (int wi = warp; wi < NBW; wi += FT_THREADS / 32) {
+                    uint32_t word = band[wi];
+                    while (word) {
+                        const int bit = __ffs(word) - 1;
+                        word &= word - 1;
+                        const int ent = wi * 32 + bit;
+                        const int m = ent / NF, e = ent - m * NF;
+                        const bool keep = refine_keep<K, C, Tin>(m, e, img_s, FW, pos, a.basis64, a.tau64, lane);
+                        if (lane == 0 && keep) atomicOr(&rkeep[wi], 1u << bit);
+                    }
+                }
+                __syncthreads();
+            }
+            if (tid < NF) {
+#pragma unroll
+                for (int m = 0; m < K; ++m)
+                    if ((bandb >> m) & 1u)
+                        if ((rkeep[(m * NF + tid) >> 5] >> (tid & 31)) & 1u) keepb |= 1u << m;
+                if constexpr (MODE == FM_FORWARD) {
+                    if (a.mask_out) {
+                        uint32_t* mo = a.mask_out + (size_t)grp * NBW;
+#pragma unroll
+                        for (int m = 0; m < K; ++m) {
+                            const uint32_t w = __ballot_sync(0xffffffffu, (keepb >> m) & 1u);
+                            if (lane == 0) mo[m * (NF / 32) + warp] = w;
+                        }
+                    }
+                    atomicAdd(&misc[1], __popc(keepb));
+#pragma unroll
+                    for (int m = 0; m < K; ++m)
+                        if (!((keepb >> m) & 1u)) co[m] = 0.f;
+                    float rec[K];
+                    haar_inv<K>(co, rec);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) gb[k * G::GS + tid] = rec[k];
+                } else {
+#pragma unroll
+                    for (int m = 0; m < K; ++m) cx[m] = ((keepb >> m) & 1u) ? co[m] : 0.f;
+                }
+            }
+            __syncthreads();
+            if constexpr (MODE == FM_ADJOINT) {
+                // ---- second pass on r = gout / D with the masks of x
+                if (tid < 8 * K) {
+                    stage_a<K, C, float>(r_s, FW, pos, bas, gb, tid >> 3, tid & 7);
+                    // <Gather(r), Gather(out)> for the weight gradient
+                    const int k = tid >> 3, b = tid & 7;
+                    const float* rp = r_s + (pos[2 * k] * FW + pos[2 * k + 1] + b) * C;
+                    const int gy = pos[2 * k] + FY0, gx = pos[2 * k + 1] + FX0 + b;
+                    float dot = 0.f;
+#pragma unroll
+                    for (int i = 0; i < PS; ++i)
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            dot = fmaf(rp[i * FW * C + c], a.out_img[((size_t)(gy + i) * g.W + gx) * C + c], dot);
+                    atomicAdd(reinterpret_cast<float*>(&misc[4]), dot);
+                }
+                __syncthreads();
+                if (tid < 8 * K) stage_b<C>(bas, gb, tid % K, tid / K);
+                __syncthreads();
+                if (tid < NF) {
+                    float fib[K], cr[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) fib[k] = gb[k * G::GS + tid];
+                    haar_fwd<K>(fib, cr);
+                    float dot = 0.f;
+#pragma unroll
+                    for (int m = 0; m < K; ++m) {
+                        if (!((keepb >> m) & 1u)) cr[m] = 0.f;
+                        dot = fmaf(cr[m], cx[m], dot);
+                    }
+                    atomicAdd(reinterpret_cast<float*>(&misc[3]), dot);
+                    float rec[K];
+                    haar_inv<K>(cr, rec);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) gb[k * G::GS + tid] = rec[k];
+                }
+                __syncthreads();
+            }
+            // ---- D, E: inverse projection
+            if (tid < 8 * K) stage_d<C>(bas, gb, tid % K, tid / K);
+            __syncthreads();
+            if (tid < 8 * K) stage_e<C>(bas, gb, tid >> 3, tid & 7);
+        }
+        // ---- weight of the group
+        if (a.w_in) wg = a.w_in[grp];
+        else if (MODE == FM_FORWARD && a.agg_mode == 1) wg = 1.f / (float)max(1, misc[1]);
+        if (tid == 0) {
+            if (MODE == FM_FORWARD && a.weights_out) a.weights_out[grp] = wg;
+            if (MODE == FM_ADJOINT && a.grad_w)
+                a.grad_w[grp] = __int_as_float(misc[3]) - __int_as_float(misc[4]);
+        }
+        __syncthreads();
+        // ---- F: aggregation, warp `warp` owns footprint rows r with r % 8 == warp
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+            const int py = pos[2 * k], px = pos[2 * k + 1];
+            const int i = (warp - py) & 7;
+            const int row = py + i;
+            float* ap = acc + (row * FW + px) * G::ACC;
+            if constexpr (C == 3) {
+                if (lane < 24) {
+                    if constexpr (MODE != FM_DENOM) {
+                        const int j = lane / 3, c = lane - 3 * (lane / 3);
+                        ap[j * 4 + c] += wg * gb[k * G::GS + i * G::RWF + lane];
+                    }
+                } else if (MODE != FM_ADJOINT) {
+                    ap[(lane - 24) * 4 + 3] += wg;
+                }
+            } else {
+                if (lane < 8) {
+                    if constexpr (MODE != FM_DENOM) ap[lane * 2] += wg * gb[k * G::GS + i * G::RWF + lane];
+                } else if (lane < 16 && MODE != FM_ADJOINT) {
+                    ap[(lane - 8) * 2 + 1] += wg;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // Write the tile partial.
+    float* dst = a.partials + (size_t)blockIdx.x * a.FHmax * a.FWmax * G::ACC;
+    if constexpr (C == 3) {
+        const float4* s4 = reinterpret_cast<const float4*>(acc);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int t = tid; t < FH * FW; t += FT_THREADS) {
+            const int r = t / FW, c = t - r * FW;
+            d4[r * a.FWmax + c] = s4[t];
+        }
+    } else {
+        const float2* s2 = reinterpret_cast<const float2*>(acc);
+        float2* d2 = reinterpret_cast<float2*>(dst);
+        for (int t = tid; t < FH * FW; t += FT_THREADS) {
+            const int r = t / FW, c = t - r * FW;
+            d2[r * a.FWmax + c] = s2[t];
+        }
+    }
+}
+
+template <int K, int C, typename Tin, int MODE>
+cudaError_t launch_filter_t(const FilterArgs& a, cudaStream_t s) {
+    const FLayout L = f_layout<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), MODE);
+    auto fn = filter_kernel<K, C, Tin, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) return e;
+    fn<<<a.ntx * a.nty, FT_THREADS, L.total, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace htsvd

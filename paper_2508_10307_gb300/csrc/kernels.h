@@ -1,0 +1,82 @@
+// Internal launch interface between the C-ABI layer (api.cu) and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace htsvd {
+
+enum MatchMode { MM_GRAY = 0, MM_GCP = 1, MM_FULL = 2, MM_GREEN = 3 };
+
+// ---- block matching (bm.cu)
+struct BMArgs {
+    const uint8_t* img;
+    Geo g;
+    int mode;            // MatchMode (resolved: gray for C = 1)
+    double gamma2;       // gcp_gamma^2
+    int rstep;           // reference subsampling (1 = every reference)
+    int nry_s, nrx_s;    // references per axis after subsampling
+    int TRy, TRx;        // references per tile
+    int32_t* idx;        // out [nry_s * nrx_s][K]
+};
+size_t bm_smem_bytes(const BMArgs& a);
+cudaError_t launch_block_match(const BMArgs& a, cudaStream_t s);
+
+// ---- second moments and bases (moments.cu)
+// Row/column second moments of the reference patches, exact:
+//   R[a][a'][c][c'] = sum_r sum_b P_r[a][b][c] P_r[a'][b][c']
+//   Q[b][b'][c][c'] = sum_r sum_a P_r[a][b][c] P_r[a][b'][c']
+// stored as uint64 [2][8][8][C][C] (R then Q).
+cudaError_t launch_moments(const uint8_t* img, const Geo& g, unsigned long long* d_mom, cudaStream_t s);
+// Full second moment M[u][v] = sum_r p_r[u] p_r[v] (d = 64 C) and s[u] = sum_r p_r[u], uint64.
+cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long long* d_M,
+                               unsigned long long* d_s, cudaStream_t s);
+// FP64 eigen-solve of the per-slice row/column scatter matrices -> canonical bases.
+//   basis64: [2 (U,V)][C][8][8] complex (re, im), slice f, row a, column i.
+//   basis32: packed float slices for the filter (U0r, [U1r, U1i], V0r, [V1r, V1i]), each [a][i].
+cudaError_t launch_basis(const unsigned long long* d_mom, int C, double* d_basis64, float* d_basis32,
+                         cudaStream_t s);
+// Quantise a float image: q = clip(rint(x), 0, 255).
+cudaError_t launch_quantize(const float* x, int64_t n, uint8_t* q, cudaStream_t s);
+
+// ---- group filter and aggregation (filter.cu)
+enum FilterMode { FM_FORWARD = 0, FM_DENOM = 1, FM_ADJOINT = 2 };
+struct FilterArgs {
+    const void* img;         // uint8 or float H x W x C (the values that are filtered)
+    int img_is_float;
+    Geo g;
+    int TR, ntx, nty;        // references per tile edge, tiles per axis
+    int FHmax, FWmax;        // partial-footprint strides
+    const int32_t* idx;      // [N][K]
+    const float* basis32;
+    const double* basis64;
+    float tau32;
+    double tau64;
+    float band_rel;          // guard band: |S| within band_rel*||G||_F + band_abs of tau -> FP64 decision
+    float band_abs;
+    const float* w_in;       // optional per-group weights
+    int agg_mode;
+    float* partials;         // [ntiles][FHmax][FWmax][C+1]
+    uint32_t* mask_out;      // optional
+    float* weights_out;      // optional
+    int mode;                // FilterMode
+    // adjoint inputs
+    const float* r_img;      // (gout / D) image that is filtered with the masks of img (FM_ADJOINT)
+    const float* out_img;    // forward output (FM_ADJOINT, for the weight gradient)
+    float* grad_w;           // FM_ADJOINT, per group
+};
+size_t filter_smem_bytes(const FilterArgs& a);
+cudaError_t launch_filter(const FilterArgs& a, cudaStream_t s);
+// out[p] = sum_tiles num / sum_tiles den (deterministic tile order). If den_out is set, the
+// denominator plane is written too; if num_only, out = sum num (no division).
+cudaError_t launch_reduce(const float* partials, const Geo& g, int TR, int ntx, int nty, int FHmax, int FWmax,
+                          float* out, float* den_out, int num_only, const float* den_in, cudaStream_t s);
+// Adjoint helper: r = gout / den.
+cudaError_t launch_div(const float* gout, const float* den, int64_t npix, int C, float* r, cudaStream_t s);
+
+// ---- sigma adjustment (moments.cu)
+// Rank position a = 1 + #{f : lambda_f < lambda_{K/2}} of each sampled group (Sec. III-D).
+cudaError_t launch_group_rank(const uint8_t* img, const Geo& g, const int32_t* idx, int ngroups, int32_t* ranks,
+                              cudaStream_t s);
+
+}  // namespace htsvd

@@ -1,0 +1,441 @@
+// Second moments of the reference patches and the global t-SVD bases
+// (Alg. 1 Step 2(1); Sec. III-B.1, Eq. (BCR nonlocal SVD simplified)), plus the
+// circulant eigen-rank of sampled groups (Sec. III-D, Eq. (other eigenvalue)).
+//
+// The bases are the eigenvectors of the per-Fourier-slice row and column scatter
+// matrices of the reference patches, A_f = sum_r P_f P_f^H and B_f = sum_r P_f^H P_f,
+// with P_f the f-th slice of the FFT along the channel mode (Eqs. (FFT product),
+// (FFT third mode)). A_f and B_f follow exactly from the integer row/column moments
+//   R[a][a'][c][c'] = sum_r sum_b P[a][b][c] P[a'][b][c'],
+//   Q[b][b'][c][c'] = sum_r sum_a P[a][b][c] P[a][b'][c'],
+// as A_f[a][a'] = sum_{c,c'} w^{f(c-c')} R[a][a'][c][c'] and
+//    B_f[b][b'] = sum_{c,c'} w^{f(c'-c)} Q[b][b'][c][c'],   w = exp(-2 pi i / C).
+#include "kernels.h"
+
+namespace htsvd {
+
+namespace {
+
+// ----------------------------------------------------------------------------- moments
+
+constexpr int MOM_CHUNK = 4096;    // references per CTA: 4096 * 8 * 255^2 < 2^32
+constexpr int MOM_BATCH = 32;      // references staged at once
+
+template <int C>
+__global__ void __launch_bounds__(256) moments_kernel(const uint8_t* __restrict__ img, Geo g,
+                                                      unsigned long long* __restrict__ out) {
+    // rows[j][c][a] = 8 bytes of row a of channel c; cols[j][c][b] = 8 bytes of column b.
+    __shared__ uint32_t rows[MOM_BATCH][C][PS][2];
+    __shared__ uint32_t cols[MOM_BATCH][C][PS][2];
+    constexpr int NE = 2 * PS * PS * C * C;
+    constexpr int EPT = (NE + 255) / 256;
+    uint32_t acc[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) acc[e] = 0;
+
+    const int N = g.ngroups();
+    const int r0 = blockIdx.x * MOM_CHUNK;
+    const int r1 = min(r0 + MOM_CHUNK, N);
+    for (int rb = r0; rb < r1; rb += MOM_BATCH) {
+        const int nb = min(MOM_BATCH, r1 - rb);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb * PS2 * C; t += 256) {
+            int j = t / (PS2 * C), rem = t - j * PS2 * C;
+            int pix = rem / C, c = rem - pix * C;
+            int a = pix / PS, b = pix % PS;
+            int r = rb + j;
+            int iy = r / g.nrx, ix = r - iy * g.nrx;
+            int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
+            uint8_t v = img[((size_t)(ry + a) * g.W + rx + b) * C + c];
+            reinterpret_cast<uint8_t*>(&rows[j][c][a][0])[b] = v;
+            reinterpret_cast<uint8_t*>(&cols[j][c][b][0])[a] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            int ent = threadIdx.x + e * 256;
+            if (ent < NE) {
+                int which = ent / (PS * PS * C * C);
+                int rem = ent - which * PS * PS * C * C;
+                int u = rem / (PS * C * C);
+                rem -= u * PS * C * C;
+                int v = rem / (C * C);
+                rem -= v * C * C;
+                int c = rem / C, c2 = rem - c * C;
+                uint32_t s = 0;
+                if (which == 0) {
+                    for (int j = 0; j < nb; ++j) {
+                        s = __dp4a(rows[j][c][u][0], rows[j][c2][v][0], s);
+                        s = __dp4a(rows[j][c][u][1], rows[j][c2][v][1], s);
+                    }
+                } else {
+                    for (int j = 0; j < nb; ++j) {
+                        s = __dp4a(cols[j][c][u][0], cols[j][c2][v][0], s);
+                        s = __dp4a(cols[j][c][u][1], cols[j][c2][v][1], s);
+                    }
+                }
+                acc[e] += s;
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+        int ent = threadIdx.x + e * 256;
+        if (ent < NE && acc[e]) atomicAdd(out + ent, (unsigned long long)acc[e]);
+    }
+}
+
+// Full second moment: CTA (bx, tile) accumulates a 64x64 tile of M over a chunk of references.
+constexpr int FM_CHUNK = 2048;     // 2048 * 255^2 < 2^32
+constexpr int FM_BATCH = 64;
+
+__global__ void __launch_bounds__(256) full_moment_kernel(const uint8_t* __restrict__ img, Geo g,
+                                                          unsigned long long* __restrict__ M,
+                                                          unsigned long long* __restrict__ S) {
+    const int d = PS2 * g.C;
+    const int ntile = (d + 63) / 64;
+    const int tu = blockIdx.y / ntile, tv = blockIdx.y % ntile;
+    __shared__ uint8_t pt[FM_BATCH][3 * PS2];
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    uint32_t acc[4][4] = {};
+    uint32_t sacc = 0;
+    const int N = g.ngroups();
+    const int r0 = blockIdx.x * FM_CHUNK, r1 = min(r0 + FM_CHUNK, N);
+    for (int rb = r0; rb < r1; rb += FM_BATCH) {
+        const int nb = min(FM_BATCH, r1 - rb);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb * d; t += 256) {
+            int j = t / d, u = t - j * d;
+            int pix = u / g.C, c = u - pix * g.C;
+            int r = rb + j;
+            int iy = r / g.nrx, ix = r - iy * g.nrx;
+            int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
+            pt[j][u] = img[((size_t)(ry + pix / PS) * g.W + rx + pix % PS) * g.C + c];
+        }
+        __syncthreads();
+        for (int j = 0; j < nb; ++j) {
+            uint32_t au[4], bv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int u = tu * 64 + ty * 4 + q, v = tv * 64 + tx * 4 + q;
+                au[q] = u < d ? pt[j][u] : 0;
+                bv[q] = v < d ? pt[j][v] : 0;
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] += au[p] * bv[q];
+        }
+        if (tv == 0 && threadIdx.x < 64) {
+            int u = tu * 64 + threadIdx.x;
+            if (u < d)
+                for (int j = 0; j < nb; ++j) sacc += pt[j][u];
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int u = tu * 64 + ty * 4 + p, v = tv * 64 + tx * 4 + q;
+            if (u < d && v < d && acc[p][q]) atomicAdd(M + (size_t)u * d + v, (unsigned long long)acc[p][q]);
+        }
+    if (tv == 0 && threadIdx.x < 64) {
+        int u = tu * 64 + threadIdx.x;
+        if (u < d && sacc) atomicAdd(S + u, (unsigned long long)sacc);
+    }
+}
+
+// ----------------------------------------------------------------------------- FP64 Hermitian eigensolver
+
+// Cyclic complex Jacobi on an 8x8 Hermitian matrix held as separate real and imaginary
+// parts: each rotation first makes the pivot real with a diagonal phase e = a_pq/|a_pq|,
+// then applies a real Jacobi rotation (c, s), i.e. A <- J^H A J with
+// J[:,p] = c e_p - s conj(e) e_q and J[:,q] = s e_p + c conj(e) e_q.
+// On exit the diagonal of (Ar, Ai) holds the eigenvalues and (Vr, Vi) the eigenvectors (columns).
+__host__ __device__ void jacobi_herm8(double (*Ar)[PS], double (*Ai)[PS], double (*Vr)[PS], double (*Vi)[PS]) {
+    for (int i = 0; i < PS; ++i)
+        for (int j = 0; j < PS; ++j) {
+            Vr[i][j] = i == j ? 1.0 : 0.0;
+            Vi[i][j] = 0.0;
+        }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int i = 0; i < PS; ++i) {
+            dia += Ar[i][i] * Ar[i][i];
+            for (int j = i + 1; j < PS; ++j) off += Ar[i][j] * Ar[i][j] + Ai[i][j] * Ai[i][j];
+        }
+        if (off <= 1e-32 * dia || off == 0.0) break;
+        for (int p = 0; p < PS - 1; ++p)
+            for (int q = p + 1; q < PS; ++q) {
+                const double xr = Ar[p][q], xi = Ai[p][q];
+                const double r = sqrt(xr * xr + xi * xi);
+                const double app = Ar[p][p], aqq = Ar[q][q];
+                if (r == 0.0 || r < 1e-17 * sqrt(fabs(app * aqq))) {
+                    Ar[p][q] = Ai[p][q] = Ar[q][p] = Ai[q][p] = 0.0;
+                    continue;
+                }
+                const double er = xr / r, ei = xi / r;            // e = a_pq / |a_pq|
+                const double th = (aqq - app) / (2.0 * r);
+                double t;
+                if (fabs(th) > 1e150) t = 0.5 / th;
+                else t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                // columns p, q: a_kp <- c a_kp - s conj(e) a_kq ; a_kq <- s a_kp + c conj(e) a_kq
+                for (int k = 0; k < PS; ++k) {
+                    const double pr = Ar[k][p], pi = Ai[k][p], qr = Ar[k][q], qi = Ai[k][q];
+                    const double mr = er * qr + ei * qi, mi = er * qi - ei * qr;     // conj(e) a_kq
+                    Ar[k][p] = c * pr - sn * mr;
+                    Ai[k][p] = c * pi - sn * mi;
+                    Ar[k][q] = sn * pr + c * mr;
+                    Ai[k][q] = sn * pi + c * mi;
+                }
+                // rows p, q: a_pk <- c a_pk - s e a_qk ; a_qk <- s a_pk + c e a_qk
+                for (int k = 0; k < PS; ++k) {
+                    const double pr = Ar[p][k], pi = Ai[p][k], qr = Ar[q][k], qi = Ai[q][k];
+                    const double mr = er * qr - ei * qi, mi = er * qi + ei * qr;     // e a_qk
+                    Ar[p][k] = c * pr - sn * mr;
+                    Ai[p][k] = c * pi - sn * mi;
+                    Ar[q][k] = sn * pr + c * mr;
+                    Ai[q][k] = sn * pi + c * mi;
+                }
+                Ar[p][p] = app - t * r;
+                Ar[q][q] = aqq + t * r;
+                Ai[p][p] = Ai[q][q] = 0.0;
+                Ar[p][q] = Ai[p][q] = Ar[q][p] = Ai[q][p] = 0.0;
+                for (int k = 0; k < PS; ++k) {
+                    const double pr = Vr[k][p], pi = Vi[k][p], qr = Vr[k][q], qi = Vi[k][q];
+                    const double mr = er * qr + ei * qi, mi = er * qi - ei * qr;     // conj(e) v_kq
+                    Vr[k][p] = c * pr - sn * mr;
+                    Vi[k][p] = c * pi - sn * mi;
+                    Vr[k][q] = sn * pr + c * mr;
+                    Vi[k][q] = sn * pi + c * mi;
+                }
+            }
+    }
+}
+
+// Eigenvalues descending; each eigenvector scaled so that its largest-modulus entry
+// (lowest index within 1e-6 relative) is real and positive. Out[a][col] = (re, im).
+__host__ __device__ void canonicalise(double (*Ar)[PS], double (*Vr)[PS], double (*Vi)[PS], double (*Out)[PS][2]) {
+    int order[PS];
+    for (int i = 0; i < PS; ++i) order[i] = i;
+    for (int i = 0; i < PS; ++i)          // selection sort, descending, ties keep the lower index first
+        for (int j = i + 1; j < PS; ++j)
+            if (Ar[order[j]][order[j]] > Ar[order[i]][order[i]]) {
+                const int t = order[i];
+                order[i] = order[j];
+                order[j] = t;
+            }
+    for (int col = 0; col < PS; ++col) {
+        const int src = order[col];
+        double mod[PS], mx = 0.0;
+        for (int a = 0; a < PS; ++a) {
+            mod[a] = sqrt(Vr[a][src] * Vr[a][src] + Vi[a][src] * Vi[a][src]);
+            mx = fmax(mx, mod[a]);
+        }
+        int as = 0;
+        for (int a = 0; a < PS; ++a)
+            if (mod[a] >= mx * (1.0 - 1e-6)) {
+                as = a;
+                break;
+            }
+        const double hr = Vr[as][src] / mod[as], hi = -Vi[as][src] / mod[as];     // conj(v_a) / |v_a|
+        for (int a = 0; a < PS; ++a) {
+            Out[a][col][0] = Vr[a][src] * hr - Vi[a][src] * hi;
+            Out[a][col][1] = Vr[a][src] * hi + Vi[a][src] * hr;
+        }
+        Out[as][col][1] = 0.0;
+    }
+}
+
+// Scatter matrix of slice f from the integer moments (rows: which = 0, columns: which = 1),
+// then its canonical eigenvectors.
+// work: 4 * PS * PS doubles of scratch (Ar, Ai, Vr, Vi).
+__host__ __device__ void slice_basis(const unsigned long long* mom, int C, int which, int f, double* work,
+                                     double (*Out)[PS][2]) {
+    double (*Ar)[PS] = reinterpret_cast<double (*)[PS]>(work);
+    double (*Ai)[PS] = reinterpret_cast<double (*)[PS]>(work + PS2);
+    double (*Vr)[PS] = reinterpret_cast<double (*)[PS]>(work + 2 * PS2);
+    double (*Vi)[PS] = reinterpret_cast<double (*)[PS]>(work + 3 * PS2);
+    const unsigned long long* M = mom + (size_t)which * PS * PS * C * C;
+    const double s32 = 0.5 * sqrt(3.0);
+    for (int u = 0; u < PS; ++u)
+        for (int v = 0; v < PS; ++v) {
+            double accr = 0.0, acci = 0.0;
+            for (int c = 0; c < C; ++c)
+                for (int c2 = 0; c2 < C; ++c2) {
+                    const double m = (double)M[((u * PS + v) * C + c) * C + c2];
+                    // phase w^{f d}, d = c - c2 for rows and c2 - c for columns, w = exp(-2 pi i / C)
+                    const int d = which == 0 ? (c - c2) : (c2 - c);
+                    const int k = ((f * d) % C + C) % C;
+                    double phr = 1.0, phi = 0.0;
+                    if (C == 3 && k == 1) { phr = -0.5; phi = -s32; }
+                    if (C == 3 && k == 2) { phr = -0.5; phi = s32; }
+                    accr += m * phr;
+                    acci += m * phi;
+                }
+            Ar[u][v] = accr;
+            Ai[u][v] = u == v ? 0.0 : acci;
+        }
+    jacobi_herm8(Ar, Ai, Vr, Vi);
+    canonicalise(Ar, Vr, Vi, Out);
+}
+
+// One thread per (U or V, slice f) problem, f = 0 .. C/2.
+__global__ void basis_kernel(const unsigned long long* __restrict__ mom, int C, double* __restrict__ b64,
+                             float* __restrict__ b32) {
+    __shared__ double Res[4][PS][PS][2];
+    __shared__ double work[4][4 * PS2];
+    const int nf = C / 2 + 1;
+    const int t = threadIdx.x;
+    if (t < 2 * nf) slice_basis(mom, C, t / nf, t % nf, work[t], Res[t]);
+    __syncthreads();
+    // Write FP64 slices (conjugate slices C - f for f > C/2) and the packed FP32 copies.
+    for (int e = threadIdx.x; e < 2 * C * PS2; e += blockDim.x) {
+        const int which = e / (C * PS2), rem = e - which * C * PS2;
+        const int f = rem / PS2, ai = rem - f * PS2;
+        const int fs = f <= C / 2 ? f : C - f;
+        const double* v = Res[which * nf + fs][ai / PS][ai % PS];
+        b64[2 * e] = v[0];
+        b64[2 * e + 1] = f != fs ? -v[1] : v[1];
+    }
+    // packed FP32: per which: slice0 re [64]; for C = 3 also slice1 re [64], slice1 im [64]
+    const int per = (C == 3) ? 3 * PS2 : PS2;
+    for (int e = threadIdx.x; e < 2 * per; e += blockDim.x) {
+        const int which = e / per, rem = e - which * per;
+        const int part = rem / PS2, ai = rem - part * PS2;
+        const double* v = Res[which * nf + (part == 0 ? 0 : 1)][ai / PS][ai % PS];
+        b32[e] = (float)(part == 2 ? v[1] : v[0]);
+    }
+}
+
+__global__ void quantize_kernel(const float* __restrict__ x, int64_t n, uint8_t* __restrict__ q) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = rintf(x[i]);
+        v = fminf(fmaxf(v, 0.0f), 255.0f);
+        q[i] = (uint8_t)v;
+    }
+}
+
+// lambda_f = || sum_m p_m exp(-2 pi i f m / K) ||^2 over the full-channel patch vectors of a
+// group (the eigenvalues of circ(G) circ(G)^T), then the rank of lambda_{K/2}. FP64, one CTA per group.
+__global__ void __launch_bounds__(256) group_rank_kernel(const uint8_t* __restrict__ img, Geo g,
+                                                         const int32_t* __restrict__ idx,
+                                                         int32_t* __restrict__ ranks) {
+    const int grp = blockIdx.x;
+    const int K = g.K;
+    const int d = PS2 * g.C;
+    __shared__ uint8_t pv[32][3 * PS2];
+    __shared__ double tc[32], ts[32];
+    __shared__ double part[256];
+    for (int t = threadIdx.x; t < K * d; t += blockDim.x) {
+        const int m = t / d, u = t - m * d;
+        const int pix = u / g.C, c = u - pix * g.C;
+        const int v = idx[(size_t)grp * K + m];
+        const int y = v / g.W, x = v - y * g.W;
+        pv[m][u] = img[((size_t)(y + pix / PS) * g.W + x + pix % PS) * g.C + c];
+    }
+    if (threadIdx.x < K) {
+        double sn, cs;
+        sincospi(-2.0 * threadIdx.x / K, &sn, &cs);
+        tc[threadIdx.x] = cs;
+        ts[threadIdx.x] = sn;
+    }
+    __syncthreads();
+    const int nsl = blockDim.x / K;
+    const int f = threadIdx.x % K, sl = threadIdx.x / K;
+    double s = 0.0;
+    if (sl < nsl)
+        for (int u = sl; u < d; u += nsl) {
+            double re = 0.0, im = 0.0;
+            for (int m = 0; m < K; ++m) {
+                const int k = (f * m) % K;
+                re += pv[m][u] * tc[k];
+                im += pv[m][u] * ts[k];
+            }
+            s += re * re + im * im;
+        }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double tot = 0.0;
+        for (int q = 0; q < nsl; ++q) tot += part[q * K + threadIdx.x];
+        part[threadIdx.x] = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 1;
+        for (int ff = 0; ff < K; ++ff)
+            if (part[ff] < part[K / 2]) ++a;
+        ranks[grp] = a;
+    }
+}
+
+}  // namespace
+
+// Host copy of the per-slice basis computation (used by the CPU tests of the eigensolver).
+extern "C" void htsvd_internal_slice_basis(const unsigned long long* mom, int C, int which, int f, double* out) {
+    double R[PS][PS][2], work[4 * PS2];
+    slice_basis(mom, C, which, f, work, R);
+    for (int a = 0; a < PS2; ++a) {
+        out[2 * a] = R[a / PS][a % PS][0];
+        out[2 * a + 1] = R[a / PS][a % PS][1];
+    }
+}
+
+// Internal hooks for device-side checks of the moments and the basis solve.
+extern "C" int htsvd_internal_moments(const uint8_t* d_img, int H, int W, int C, int stride,
+                                      unsigned long long* d_mom) {
+    Geo g = make_geo(H, W, C, stride, 8, 2);
+    if (launch_moments(d_img, g, d_mom, 0) != cudaSuccess) return 1;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
+}
+extern "C" int htsvd_internal_basis(const unsigned long long* d_mom, int C, double* d_b64, float* d_b32) {
+    if (launch_basis(d_mom, C, d_b64, d_b32, 0) != cudaSuccess) return 1;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
+}
+
+cudaError_t launch_moments(const uint8_t* img, const Geo& g, unsigned long long* d_mom, cudaStream_t s) {
+    const int n = g.ngroups();
+    const int blocks = (n + MOM_CHUNK - 1) / MOM_CHUNK;
+    cudaError_t e = cudaMemsetAsync(d_mom, 0, sizeof(unsigned long long) * 2 * PS2 * g.C * g.C, s);
+    if (e != cudaSuccess) return e;
+    if (g.C == 3) moments_kernel<3><<<blocks, 256, 0, s>>>(img, g, d_mom);
+    else moments_kernel<1><<<blocks, 256, 0, s>>>(img, g, d_mom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long long* d_M, unsigned long long* d_s,
+                               cudaStream_t s) {
+    const int d = PS2 * g.C;
+    cudaError_t e = cudaMemsetAsync(d_M, 0, sizeof(unsigned long long) * d * d, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_s, 0, sizeof(unsigned long long) * d, s);
+    if (e != cudaSuccess) return e;
+    const int n = g.ngroups();
+    const int nt = (d + 63) / 64;
+    dim3 grid((n + FM_CHUNK - 1) / FM_CHUNK, nt * nt);
+    full_moment_kernel<<<grid, 256, 0, s>>>(img, g, d_M, d_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_basis(const unsigned long long* d_mom, int C, double* d_basis64, float* d_basis32, cudaStream_t s) {
+    basis_kernel<<<1, 64, 0, s>>>(d_mom, C, d_basis64, d_basis32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quantize(const float* x, int64_t n, uint8_t* q, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    quantize_kernel<<<blocks, 256, 0, s>>>(x, n, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_rank(const uint8_t* img, const Geo& g, const int32_t* idx, int ngroups, int32_t* ranks,
+                              cudaStream_t s) {
+    if (ngroups <= 0) return cudaSuccess;
+    group_rank_kernel<<<ngroups, 256, 0, s>>>(img, g, idx, ranks);
+    return cudaGetLastError();
+}
+
+}  // namespace htsvd

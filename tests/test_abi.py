@@ -1,0 +1,69 @@
+"""The C-ABI library loads and exports every symbol include/htsvd.h declares (CPU only);
+argument errors are reported before any device work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2508_10307_gb300 as H
+from paper_2508_10307_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "htsvd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(htsvd_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for n in ["htsvd_denoise", "htsvd_denoise_f32", "htsvd_estimate_sigma", "htsvd_denoise_batch",
+              "htsvd_denoise_vjp", "htsvd_num_groups", "htsvd_status_string", "htsvd_release_workspace"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = H.load_library()
+    for n in _declared():
+        assert hasattr(lib, n), n
+    assert set(_lib.EXPORTED) == set(_declared())
+
+
+def test_num_groups_matches_reference_grid():
+    assert H.num_groups(128, 128, dict(stride=3)) == 41 * 41
+    assert H.num_groups(512, 512, dict(stride=2)) == 253 * 253
+    assert H.num_groups(2160, 3840, dict(stride=3)) == 719 * 1279
+    assert H.num_groups(7, 100, None) == -1
+
+
+def test_status_strings():
+    lib = H.load_library()
+    assert lib.htsvd_status_string(0) == b"ok"
+    assert lib.htsvd_status_string(1) == b"invalid argument"
+
+
+def _call_denoise(H_, W_, C, params, ptr=1):
+    lib = H.load_library()
+    cp = H.HtsvdParams.of(params).c()
+    return lib.htsvd_denoise(ctypes.c_void_p(ptr), H_, W_, C, 10.0, ctypes.byref(cp), ctypes.c_void_p(ptr), None,
+                             None)
+
+
+@pytest.mark.parametrize("shape,params,code", [
+    ((7, 40, 3), dict(), 1),                   # smaller than a patch
+    ((40, 40, 2), dict(), 1),                  # C not 1 or 3
+    ((40, 40, 3), dict(K=12), 1),              # K not a power of two
+    ((40, 40, 3), dict(ps=4), 2),              # only ps = 8 is built
+    ((40, 40, 3), dict(K=64), 2),              # K > 32 not built
+    ((40, 40, 3), dict(window=65), 2),         # window > 64 not built
+    ((9, 9, 1), dict(K=8, window=3), 1),       # fewer than K candidates in the window
+])
+def test_invalid_arguments_are_rejected_on_the_host(shape, params, code):
+    assert _call_denoise(*shape, params) == code
+
+
+def test_null_pointers_rejected():
+    assert _call_denoise(40, 40, 3, dict(), ptr=0) == 1

@@ -1,0 +1,166 @@
+"""GPU path vs the FP64 oracle through the C ABI (needs a GB300 and the built library).
+
+Bar: match indices and threshold masks bit-exact (masks: except coefficients the oracle
+itself finds within 1e-9 of tau, expected none); pixels within 1e-3 on the [0, 255]
+scale; PSNR within 0.01 dB; basis within 1e-9.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import htsvd_oracle as O
+from paper_2508_10307_gb300 import synth
+from tests._common import PIX_TOL, PSNR_TOL, max_abs, oracle_run, pack_masks, psnr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2508_10307_gb300 as H  # noqa: E402
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _run_gpu(noisy, sigma, prm, **kw):
+    out, info = H.denoise(_dev(noisy), sigma, prm, return_info=True, masks=True, weights=True, basis=True, **kw)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in info.items()}
+
+
+def _basis_from_gpu(b):
+    z = b[..., 0] + 1j * b[..., 1]            # (2, C, 8, 8)
+    return z[0], z[1]
+
+
+def _compare(noisy, sigma, prm, r, clean=None):
+    out, info = _run_gpu(noisy, sigma, prm)
+    # grouping
+    np.testing.assert_array_equal(info["idx"].astype(np.int64), r.idx)
+    # bases
+    U, V = _basis_from_gpu(info["basis"])
+    assert np.abs(U - r.U).max() < 1e-9 and np.abs(V - r.V).max() < 1e-9
+    # masks
+    om = pack_masks(r.masks)
+    gm = info["masks"].view(np.uint32)[:, :om.shape[1]]
+    diff = np.nonzero(om != gm)
+    bad = 0
+    if diff[0].size:
+        amb = {(int(g), int(i)) for g, i in r.ambiguous}
+        for g, wd in zip(*diff):
+            x = int(om[g, wd]) ^ int(gm[g, wd])
+            for b in range(32):
+                if (x >> b) & 1 and (int(g), int(wd) * 32 + b) not in amb:
+                    bad += 1
+    assert bad == 0, f"{bad} mask bits differ outside the ambiguity band"
+    # pixels
+    err = max_abs(out, r.out)
+    assert err <= PIX_TOL, f"max abs pixel error {err}"
+    if clean is not None:
+        assert abs(psnr(out, clean) - psnr(r.out, clean)) <= PSNR_TOL
+    return out, info
+
+
+def test_gray128_parity():
+    clean, noisy, sigma, prm, r = oracle_run("gray128")
+    out, info = _compare(noisy, sigma, prm, r, clean)
+    assert psnr(out, clean) > psnr(noisy, clean) + 6
+
+
+def test_rgb512_parity_with_estimated_sigma():
+    clean, noisy, sigma, prm, r = oracle_run("rgb512")
+    out, info = _compare(noisy, None, prm, r, clean)
+    assert abs(info["sigma"] - sigma) <= 1e-9 * sigma
+    assert psnr(out, clean) > psnr(noisy, clean) + 6
+
+
+@pytest.mark.parametrize("shape,prm,sigma", [
+    ((37, 45, 3), dict(ps=8, stride=3, window=11, K=8), 20.0),          # ragged tail in both axes
+    ((50, 29, 1), dict(ps=8, stride=4, window=9, K=16), 15.0),
+    ((20, 26, 3), dict(ps=8, stride=2, window=31, K=32), 30.0),         # image smaller than the window
+    ((64, 70, 3), dict(ps=8, stride=5, window=17, K=4, match_mode="full"), 25.0),
+    ((64, 48, 3), dict(ps=8, stride=3, window=15, K=16, agg_mode="sparsity"), 25.0),
+    ((33, 40, 3), dict(ps=8, stride=1, window=7, K=2), 10.0),
+])
+def test_small_images_parity(shape, prm, sigma):
+    Hh, Ww, C = shape
+    clean = synth.clean_image(Hh, Ww, C, 77)
+    noisy = synth.add_gaussian(clean, sigma, 77)
+    r = O.denoise(noisy, sigma, prm, keep_masks=True)
+    out, info = _compare(noisy, sigma, prm, r)
+    if prm.get("agg_mode") == "sparsity":
+        # w_g = 1 / max(1, #kept): the kept counts are integers and must agree exactly
+        np.testing.assert_array_equal(np.rint(1.0 / info["weights"]), np.rint(1.0 / r.weights))
+
+
+def test_tied_distances_lowest_index():
+    tile = np.random.default_rng(3).integers(0, 256, size=(8, 8, 3), dtype=np.uint8)
+    noisy = np.ascontiguousarray(np.tile(tile, (6, 6, 1)))
+    prm = dict(ps=8, stride=4, window=21, K=16)
+    r = O.denoise(noisy, 20.0, prm, keep_masks=True)
+    _compare(noisy, 20.0, prm, r)
+
+
+def test_zero_threshold_is_identity_on_gpu():
+    clean, noisy, sigma, prm = synth.workload_rgb512()
+    out = H.denoise(_dev(noisy), 0.0, prm).cpu().numpy()
+    assert max_abs(out, noisy) <= 2e-3
+
+
+def test_huge_threshold_gives_zero():
+    _, noisy, _, prm = synth.workload_gray128()
+    out = H.denoise(_dev(noisy), 1e30, prm).cpu().numpy()
+    assert np.abs(out).max() == 0.0
+
+
+def test_constant_image():
+    img = np.full((40, 40, 3), 91, dtype=np.uint8)
+    out = H.denoise(_dev(img), 25.0, dict(ps=8, stride=3, window=9, K=8)).cpu().numpy()
+    assert max_abs(out, 91.0) <= PIX_TOL
+
+
+def test_deterministic_bitwise():
+    _, noisy, sigma, prm = synth.workload_gray128()
+    a = H.denoise(_dev(noisy), sigma, prm).cpu().numpy()
+    b = H.denoise(_dev(noisy), sigma, prm).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_estimate_sigma_matches_oracle():
+    clean, noisy, sigma, prm, r = oracle_run("rgb512")
+    s = H.estimate_sigma(_dev(noisy), prm)
+    assert abs(s - sigma) <= 1e-9 * sigma
+
+
+def test_estimate_sigma_adaptive_matches_oracle():
+    clean = synth.clean_image(160, 192, 3, 5)
+    noisy = synth.add_gaussian(clean, 35.0, 5)
+    prm = dict(ps=8, stride=3, window=15, K=32, adapt=True)
+    s_or, det = O.estimate_sigma(noisy, prm, return_details=True)
+    s = H.estimate_sigma(_dev(noisy), prm)
+    assert abs(s - s_or) <= 1e-9 * s_or
+
+
+def test_float_input_matches_oracle():
+    clean = synth.clean_image(64, 72, 3, 9)
+    x = synth.add_gaussian_float(clean, 25.0, 9)
+    prm = dict(ps=8, stride=3, window=15, K=16)
+    r = O.denoise(x, 25.0, prm, keep_masks=True)
+    out, info = H.denoise_f32(_dev(x), 25.0, prm, return_info=True)
+    np.testing.assert_array_equal(info["idx"].cpu().numpy().astype(np.int64), r.idx)
+    assert max_abs(out.cpu().numpy(), r.out) <= PIX_TOL
+
+
+def test_batch_equals_single_calls():
+    shapes = [(64, 80), (96, 40), (48, 48)]
+    imgs, sig = [], []
+    for j, (h, w) in enumerate(shapes):
+        c, n = synth.batch_image(j, h, w, 15.0 + 10 * j)
+        imgs.append(_dev(n))
+        sig.append(15.0 + 10 * j)
+    prm = dict(ps=8, stride=3, window=31, K=32)
+    outs = H.denoise_batch(imgs, sig, prm)
+    for t, s, o in zip(imgs, sig, outs):
+        ref = H.denoise(t, s, prm)
+        assert torch.equal(ref, o)
