@@ -132,6 +132,27 @@ htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C
                                const float* d_out, const float* d_grad_out, float* d_grad_x,
                                float* d_grad_w, cudaStream_t stream);
 
+/* Size of the fixed device array used by htsvd_denoise_noalloc. */
+#define HTSVD_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Alg. 1 on a uint8 image without any device-memory allocation (the paper has no
+ * counterpart: this serves callers that must not allocate). Hosts that reserve all device
+ * memory in their own pool, or loops that cannot afford the device-wide synchronisation
+ * cudaFree implies, cannot let a library call cudaMalloc/cudaFree; this call runs the
+ * same kernels as htsvd_denoise but keeps every temporary (match indices, moments,
+ * bases, tile partials) in one array of HTSVD_NOALLOC_SCRATCH_BYTES (32 MiB) that the
+ * library declares in device memory. Every GPU that loads the library holds that array
+ * until the process exits.
+ * sigma must be >= 0 (no estimation). The other arguments are as in htsvd_denoise.
+ * Images whose temporaries do not fit the array return HTSVD_ERR_INVALID_ARG before any
+ * device work (at stride 3, window 18, K 32 the array holds RGB images up to 677 x 677).
+ * The first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture. All calls share the one
+ * array and it keeps the last call's contents: calls that can overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
+htsvd_status htsvd_denoise_noalloc(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, double sigma,
+                                   const htsvd_params* p, float* d_out, cudaStream_t stream);
+
 /* Number of groups (reference patches) of an H x W image, or -1 on bad arguments. */
 int64_t htsvd_num_groups(int32_t H, int32_t W, const htsvd_params* p);
 
