@@ -78,6 +78,8 @@ typedef struct htsvd_params {
     float*    d_weights_out; /* DEVICE: per-group aggregation weights actually used */
     double*   d_basis_out;   /* DEVICE: 2*C*ps*ps complex values (re, im): U_F slices then V_F slices,
                                 each slice row-major [a][i] (column i = i-th eigenvector) */
+    float*    d_coef_out;    /* DEVICE: FP32 coefficients S before thresholding, K*ps*ps*C floats per group,
+                                same index as the mask bits (for accuracy checks) */
 } htsvd_params;
 
 /* One image of a batch. */

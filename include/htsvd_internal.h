@@ -1,0 +1,34 @@
+/*
+ * htsvd_internal.h — test hooks of libhtsvd (not part of the stable API).
+ *
+ * They expose single steps of the path so that tests can check them in isolation.
+ */
+#ifndef HTSVD_INTERNAL_H
+#define HTSVD_INTERNAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* HOST computation of one global-basis slice (Sec. III-B.1): from the integer row (which = 0)
+ * or column (which = 1) moments `mom` ([2][8][8][C][C] uint64, host memory), the slice-f scatter
+ * matrix and its canonical eigenvectors, written to out[64][2] (row-major [a][i], re/im).
+ * Runs the same rotation sequence as the device solver. No errors are reported. */
+void htsvd_internal_slice_basis(const unsigned long long* mom, int C, int which, int f, double* out);
+
+/* DEVICE: integer row/column moments of the reference patches of a uint8 image (d_img) with the
+ * given grid stride into d_mom (2*64*C*C uint64, device); synchronises the device.
+ * Returns 0 on success, 1 on a CUDA error. */
+int htsvd_internal_moments(const uint8_t* d_img, int H, int W, int C, int stride, unsigned long long* d_mom);
+
+/* DEVICE: basis solve from device moments; d_b64 receives 2*2*C*64 doubles (see d_basis_out of
+ * htsvd_params), d_b32 512 floats (the filter's packed FP32 copy); synchronises the device.
+ * Returns 0 on success, 1 on a CUDA error. */
+int htsvd_internal_basis(const unsigned long long* d_mom, int C, double* d_b64, float* d_b32);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HTSVD_INTERNAL_H */

@@ -90,7 +90,7 @@ def num_groups(H: int, W: int, params=None) -> int:
     return int(lib.htsvd_num_groups(H, W, ctypes.byref(cp)))
 
 
-def _outputs(x, p, params, want_idx, want_masks, want_weights, want_basis):
+def _outputs(x, p, params, want_idx, want_masks, want_weights, want_basis, want_coeffs=False):
     torch = _torch()
     H, W, C = x.shape
     n = num_groups(H, W, p)
@@ -106,11 +106,14 @@ def _outputs(x, p, params, want_idx, want_masks, want_weights, want_basis):
     if want_basis:
         info["basis"] = torch.empty((2, C, 8, 8, 2), dtype=torch.float64, device=x.device)
         params.d_basis_out = info["basis"].data_ptr()
+    if want_coeffs:
+        info["coeffs"] = torch.empty((n, p.K, 8, 8, C), dtype=torch.float32, device=x.device)
+        params.d_coef_out = info["coeffs"].data_ptr()
     return out, idx, info
 
 
 def denoise(noisy, sigma=None, params=None, *, return_info=False, masks=False, weights=False, basis=False,
-            stream=None):
+            coeffs=False, stream=None):
     """Alg. 1 on a uint8 (H, W[, C]) CUDA tensor. sigma=None estimates it on the device.
     Returns the float32 (H, W, C) estimate, or (estimate, info) with return_info."""
     lib = _lib.load()
@@ -121,7 +124,7 @@ def denoise(noisy, sigma=None, params=None, *, return_info=False, masks=False, w
     cp = p.c()
     sig_out = ctypes.c_double(-1.0)
     cp.h_sigma_out = ctypes.pointer(sig_out)
-    out, idx, info = _outputs(x, p, cp, return_info, masks, weights, basis)
+    out, idx, info = _outputs(x, p, cp, return_info, masks, weights, basis, coeffs)
     H, W, C = x.shape
     st = lib.htsvd_denoise(_ptr(x), H, W, C, -1.0 if sigma is None else float(sigma), ctypes.byref(cp),
                            _ptr(out), _ptr(idx), _stream_ptr(stream))

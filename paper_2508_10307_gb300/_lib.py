@@ -34,6 +34,7 @@ class CParams(ctypes.Structure):
         ("d_mask_out", ctypes.c_void_p),
         ("d_weights_out", ctypes.c_void_p),
         ("d_basis_out", ctypes.c_void_p),
+        ("d_coef_out", ctypes.c_void_p),
     ]
 
 

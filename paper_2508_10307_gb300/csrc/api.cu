@@ -339,13 +339,14 @@ htsvd_status run_forward_filter(Workspace* w, const void* img, int is_float, con
     a.basis64 = b64;
     a.tau64 = tau;
     a.tau32 = (float)tau;
-    a.band_rel = 6.103515625e-05f;          // 2^-14 of the group norm (FP32 error bound, with margin)
-    a.band_abs = (float)(tau * 2.384185791015625e-07) + 1e-6f;   // covers tau rounded to FP32
+    a.band_rel = kBandRel;
+    a.band_abs = (float)(tau * kBandTau) + 1e-6f;
     a.w_in = w_in;
     a.agg_mode = r.agg_mode;
     a.mode = FM_FORWARD;
     a.mask_out = p ? p->d_mask_out : nullptr;
     a.weights_out = p ? p->d_weights_out : nullptr;
+    a.coef_out = p ? p->d_coef_out : nullptr;
     void* part;
     const int acc = g.C == 3 ? 4 : 2;
     ST(ws_get(w, S_PART, sizeof(float) * (size_t)t.ntx * t.nty * t.FHmax * t.FWmax * acc, &part));
@@ -471,8 +472,8 @@ htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C
     a.basis64 = b64;
     a.tau64 = tau;
     a.tau32 = (float)tau;
-    a.band_rel = 6.103515625e-05f;
-    a.band_abs = (float)(tau * 2.384185791015625e-07) + 1e-6f;
+    a.band_rel = kBandRel;
+    a.band_abs = (float)(tau * kBandTau) + 1e-6f;
     a.w_in = d_w;
     a.agg_mode = 0;
     a.mode = FM_DENOM;
@@ -519,6 +520,7 @@ htsvd_status htsvd_denoise_batch(const htsvd_image* imgs, int32_t n, const htsvd
         q.d_mask_out = nullptr;
         q.d_weights_out = nullptr;
         q.d_basis_out = nullptr;
+        q.d_coef_out = nullptr;
         htsvd_status st = htsvd_denoise(imgs[i].d_in, imgs[i].H, imgs[i].W, imgs[i].C, imgs[i].sigma, &q,
                                         imgs[i].d_out, nullptr, s);
         if (st != HTSVD_OK) return st;

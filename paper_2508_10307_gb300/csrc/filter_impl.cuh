@@ -96,8 +96,17 @@ __device__ __forceinline__ void haar_inv(float (&o)[K], float (&a)[K]) {
 template <typename T>
 __device__ __forceinline__ float ldv(const T* p) { return (float)p[0]; }
 
+// Eight consecutive floats of a 32-byte aligned shared-memory row (two 128-bit loads).
+__device__ __forceinline__ void load8(const float* p, float (&r)[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+    r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+}
+
 // FP64 value of one coefficient S[m][i][j][c] of the group, from the staged inputs:
 // S = T(sum_k H[m,k] P_k) with T the real t-SVD projection; returns |S| >= tau.
+// Lane l handles the pixels (a, b) = l and l + 32 of the combined patch Q = sum_k H[m,k] P_k;
+// for uint8 inputs the signed sum of the patches is exact in int32.
 template <int K, int C, typename Tin>
 __device__ bool refine_keep(int m, int e, const Tin* img_s, int FW, const int* pos, const double* __restrict__ b64,
                             double tau64, int lane) {
@@ -116,24 +125,39 @@ __device__ bool refine_keep(int m, int e, const Tin* img_s, int FW, const int* p
     const int i = pix / PS, j = pix % PS;
     double s0 = 0.0, s1r = 0.0, s1i = 0.0;
     const double s3h = 0.5 * sqrt(3.0);
-    for (int p = lane; p < PS2; p += 32) {
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+        const int p = lane + 32 * rep;
         const int aa = p / PS, bb = p % PS;
         double q[C];
+        if constexpr (sizeof(Tin) == 1) {
+            int qi[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) q[c] = 0.0;
-        for (int kk = k0; kk < k0 + L; ++kk) {
-            const Tin* src = img_s + ((pos[2 * kk] + aa) * FW + pos[2 * kk + 1] + bb) * C;
+            for (int c = 0; c < C; ++c) qi[c] = 0;
+            for (int kk = k0; kk < k0 + L; ++kk) {
+                const Tin* src = img_s + ((pos[2 * kk] + aa) * FW + pos[2 * kk + 1] + bb) * C;
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const double v = (double)src[c];
-                q[c] += (kk - k0 < half) ? v : -v;
+                for (int c = 0; c < C; ++c) qi[c] += (kk - k0 < half) ? (int)src[c] : -(int)src[c];
             }
-        }
 #pragma unroll
-        for (int c = 0; c < C; ++c) q[c] *= h;
+            for (int c = 0; c < C; ++c) q[c] = (double)qi[c] * h;
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) q[c] = 0.0;
+            for (int kk = k0; kk < k0 + L; ++kk) {
+                const Tin* src = img_s + ((pos[2 * kk] + aa) * FW + pos[2 * kk + 1] + bb) * C;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const double v = (double)src[c];
+                    q[c] += (kk - k0 < half) ? v : -v;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) q[c] *= h;
+        }
         const double u0 = b64[(0 * C + 0) * 2 * PS2 + 2 * (aa * PS + i)];
         const double v0 = b64[(1 * C + 0) * 2 * PS2 + 2 * (bb * PS + j)];
-        if (C == 3) {
+        if constexpr (C == 3) {
             const double Q0 = q[0] + q[1] + q[2];
             const double Q1r = q[0] - 0.5 * (q[1] + q[2]);
             const double Q1i = s3h * (q[2] - q[1]);
@@ -153,11 +177,13 @@ __device__ bool refine_keep(int m, int e, const Tin* img_s, int FW, const int* p
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-        s1r += __shfl_xor_sync(0xffffffffu, s1r, off);
-        s1i += __shfl_xor_sync(0xffffffffu, s1i, off);
+        if constexpr (C == 3) {
+            s1r += __shfl_xor_sync(0xffffffffu, s1r, off);
+            s1i += __shfl_xor_sync(0xffffffffu, s1i, off);
+        }
     }
     double S;
-    if (C == 3) {
+    if constexpr (C == 3) {
         const double sq3 = sqrt(3.0);
         S = (ch == 0) ? (s0 + 2.0 * s1r) / 3.0 : (ch == 1) ? (s0 - s1r - sq3 * s1i) / 3.0 : (s0 - s1r + sq3 * s1i) / 3.0;
     } else {
@@ -166,7 +192,10 @@ __device__ bool refine_keep(int m, int e, const Tin* img_s, int FW, const int* p
     return fabs(S) >= tau64;
 }
 
-// Stage A: thread (k, b) -> Y_f[:, b] of patch k. Returns the sum of squares of its inputs.
+// Basis rows in shared memory (each [a][i], row a = 8 consecutive floats):
+// C = 3: U0 at 0, U1r at 64, U1i at 128, V0 at 192, V1r at 256, V1i at 320; C = 1: U0 at 0, V0 at 64.
+
+// Stage A: thread (k, b) -> Y_f[:, b] = U_f^H X_f[:, b] of patch k. Returns the sum of squares of its inputs.
 template <int K, int C, typename Tin>
 __device__ __forceinline__ float stage_a(const Tin* img_s, int FW, const int* pos, const float* bas, float* gb,
                                          int k, int b) {
@@ -179,48 +208,53 @@ __device__ __forceinline__ float stage_a(const Tin* img_s, int FW, const int* po
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             x[i][c] = ldv(src + i * FW * C + c);
-            nrm += x[i][c] * x[i][c];
+            nrm = fmaf(x[i][c], x[i][c], nrm);
         }
     float* dst = gb + k * G::GS + b * C;
     if constexpr (C == 3) {
-        float X0[PS], X1r[PS], X1i[PS];
+        float y0[PS], yr[PS], yi[PS];
 #pragma unroll
-        for (int i = 0; i < PS; ++i) {
-            X0[i] = x[i][0] + x[i][1] + x[i][2];
-            X1r[i] = x[i][0] - 0.5f * (x[i][1] + x[i][2]);
-            X1i[i] = F_S3H * (x[i][2] - x[i][1]);
+        for (int ii = 0; ii < PS; ++ii) y0[ii] = yr[ii] = yi[ii] = 0.f;
+#pragma unroll
+        for (int a = 0; a < PS; ++a) {
+            const float X0 = x[a][0] + x[a][1] + x[a][2];
+            const float X1r = x[a][0] - 0.5f * (x[a][1] + x[a][2]);
+            const float X1i = F_S3H * (x[a][2] - x[a][1]);
+            float u0[8], ur[8], ui[8];
+            load8(bas + a * PS, u0);
+            load8(bas + 64 + a * PS, ur);
+            load8(bas + 128 + a * PS, ui);
+#pragma unroll
+            for (int ii = 0; ii < PS; ++ii) {
+                y0[ii] = fmaf(u0[ii], X0, y0[ii]);
+                yr[ii] = fmaf(ur[ii], X1r, fmaf(ui[ii], X1i, yr[ii]));
+                yi[ii] = fmaf(ur[ii], X1i, fmaf(-ui[ii], X1r, yi[ii]));
+            }
         }
-        const float* U0 = bas;
-        const float* U1r = bas + 64;
-        const float* U1i = bas + 128;
 #pragma unroll
         for (int ii = 0; ii < PS; ++ii) {
-            float y0 = 0.f, yr = 0.f, yi = 0.f;
-#pragma unroll
-            for (int a = 0; a < PS; ++a) {
-                const float u0 = U0[a * PS + ii], ur = U1r[a * PS + ii], ui = U1i[a * PS + ii];
-                y0 = fmaf(u0, X0[a], y0);
-                yr = fmaf(ur, X1r[a], fmaf(ui, X1i[a], yr));
-                yi = fmaf(ur, X1i[a], fmaf(-ui, X1r[a], yi));
-            }
-            dst[ii * G::RWF + 0] = y0;
-            dst[ii * G::RWF + 1] = yr;
-            dst[ii * G::RWF + 2] = yi;
+            dst[ii * G::RWF + 0] = y0[ii];
+            dst[ii * G::RWF + 1] = yr[ii];
+            dst[ii * G::RWF + 2] = yi[ii];
         }
     } else {
-        const float* U0 = bas;
+        float y0[PS];
 #pragma unroll
-        for (int ii = 0; ii < PS; ++ii) {
-            float y0 = 0.f;
+        for (int ii = 0; ii < PS; ++ii) y0[ii] = 0.f;
 #pragma unroll
-            for (int a = 0; a < PS; ++a) y0 = fmaf(U0[a * PS + ii], x[a][0], y0);
-            dst[ii * G::RWF] = y0;
+        for (int a = 0; a < PS; ++a) {
+            float u0[8];
+            load8(bas + a * PS, u0);
+#pragma unroll
+            for (int ii = 0; ii < PS; ++ii) y0[ii] = fmaf(u0[ii], x[a][0], y0[ii]);
         }
+#pragma unroll
+        for (int ii = 0; ii < PS; ++ii) dst[ii * G::RWF] = y0[ii];
     }
     return nrm;
 }
 
-// Stage B: thread (i, k): S = Y V, inverse channel DFT, in place on row i of patch k.
+// Stage B: thread (i, k): S_f[i, :] = Y_f[i, :] V_f, inverse channel DFT, in place on row i of patch k.
 template <int C>
 __device__ __forceinline__ void stage_b(const float* bas, float* gb, int k, int i) {
     using G = FCfg<C>;
@@ -233,39 +267,45 @@ __device__ __forceinline__ void stage_b(const float* bas, float* gb, int k, int 
     }
     float o[G::RWF];
     if constexpr (C == 3) {
-        const float* V0 = bas + 192;
-        const float* V1r = bas + 256;
-        const float* V1i = bas + 320;
+        float s0[PS], sr[PS], si[PS];
+#pragma unroll
+        for (int j = 0; j < PS; ++j) s0[j] = sr[j] = si[j] = 0.f;
+#pragma unroll
+        for (int b = 0; b < PS; ++b) {
+            float v0[8], vr[8], vi[8];
+            load8(bas + 192 + b * PS, v0);
+            load8(bas + 256 + b * PS, vr);
+            load8(bas + 320 + b * PS, vi);
+            const float y0 = y[3 * b], yr = y[3 * b + 1], yi = y[3 * b + 2];
+#pragma unroll
+            for (int j = 0; j < PS; ++j) {
+                s0[j] = fmaf(y0, v0[j], s0[j]);
+                sr[j] = fmaf(yr, vr[j], fmaf(-yi, vi[j], sr[j]));
+                si[j] = fmaf(yr, vi[j], fmaf(yi, vr[j], si[j]));
+            }
+        }
 #pragma unroll
         for (int j = 0; j < PS; ++j) {
-            float s0 = 0.f, sr = 0.f, si = 0.f;
-#pragma unroll
-            for (int b = 0; b < PS; ++b) {
-                const float v0 = V0[b * PS + j], vr = V1r[b * PS + j], vi = V1i[b * PS + j];
-                const float y0 = y[3 * b], yr = y[3 * b + 1], yi = y[3 * b + 2];
-                s0 = fmaf(y0, v0, s0);
-                sr = fmaf(yr, vr, fmaf(-yi, vi, sr));
-                si = fmaf(yr, vi, fmaf(yi, vr, si));
-            }
-            o[3 * j + 0] = (s0 + 2.f * sr) * F_THIRD;
-            o[3 * j + 1] = (s0 - sr - F_SQ3 * si) * F_THIRD;
-            o[3 * j + 2] = (s0 - sr + F_SQ3 * si) * F_THIRD;
+            o[3 * j + 0] = (s0[j] + 2.f * sr[j]) * F_THIRD;
+            o[3 * j + 1] = (s0[j] - sr[j] - F_SQ3 * si[j]) * F_THIRD;
+            o[3 * j + 2] = (s0[j] - sr[j] + F_SQ3 * si[j]) * F_THIRD;
         }
     } else {
-        const float* V0 = bas + 64;
 #pragma unroll
-        for (int j = 0; j < PS; ++j) {
-            float s0 = 0.f;
+        for (int j = 0; j < PS; ++j) o[j] = 0.f;
 #pragma unroll
-            for (int b = 0; b < PS; ++b) s0 = fmaf(y[b], V0[b * PS + j], s0);
-            o[j] = s0;
+        for (int b = 0; b < PS; ++b) {
+            float v0[8];
+            load8(bas + 64 + b * PS, v0);
+#pragma unroll
+            for (int j = 0; j < PS; ++j) o[j] = fmaf(y[b], v0[j], o[j]);
         }
     }
 #pragma unroll
     for (int q = 0; q < G::RWF / 4; ++q) row[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
 }
 
-// Stage D: thread (i, k): channel DFT, Z = T V^H, in place on row i of patch k.
+// Stage D: thread (i, k): channel DFT, Z_f[i, :] = T_f[i, :] V_f^H, in place on row i of patch k.
 template <int C>
 __device__ __forceinline__ void stage_d(const float* bas, float* gb, int k, int i) {
     using G = FCfg<C>;
@@ -285,28 +325,29 @@ __device__ __forceinline__ void stage_d(const float* bas, float* gb, int k, int 
             T1r[j] = t[3 * j] - 0.5f * (t[3 * j + 1] + t[3 * j + 2]);
             T1i[j] = F_S3H * (t[3 * j + 2] - t[3 * j + 1]);
         }
-        const float* V0 = bas + 192;
-        const float* V1r = bas + 256;
-        const float* V1i = bas + 320;
 #pragma unroll
         for (int b = 0; b < PS; ++b) {
+            float v0[8], vr[8], vi[8];
+            load8(bas + 192 + b * PS, v0);
+            load8(bas + 256 + b * PS, vr);
+            load8(bas + 320 + b * PS, vi);
             float z0 = 0.f, zr = 0.f, zi = 0.f;
 #pragma unroll
             for (int j = 0; j < PS; ++j) {
-                const float v0 = V0[b * PS + j], vr = V1r[b * PS + j], vi = V1i[b * PS + j];
-                z0 = fmaf(T0[j], v0, z0);
-                zr = fmaf(T1r[j], vr, fmaf(T1i[j], vi, zr));
-                zi = fmaf(T1i[j], vr, fmaf(-T1r[j], vi, zi));
+                z0 = fmaf(T0[j], v0[j], z0);
+                zr = fmaf(T1r[j], vr[j], fmaf(T1i[j], vi[j], zr));
+                zi = fmaf(T1i[j], vr[j], fmaf(-T1r[j], vi[j], zi));
             }
             o[3 * b] = z0; o[3 * b + 1] = zr; o[3 * b + 2] = zi;
         }
     } else {
-        const float* V0 = bas + 64;
 #pragma unroll
         for (int b = 0; b < PS; ++b) {
+            float v0[8];
+            load8(bas + 64 + b * PS, v0);
             float z = 0.f;
 #pragma unroll
-            for (int j = 0; j < PS; ++j) z = fmaf(t[j], V0[b * PS + j], z);
+            for (int j = 0; j < PS; ++j) z = fmaf(t[j], v0[j], z);
             o[b] = z;
         }
     }
@@ -314,7 +355,7 @@ __device__ __forceinline__ void stage_d(const float* bas, float* gb, int k, int 
     for (int q = 0; q < G::RWF / 4; ++q) row[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
 }
 
-// Stage E: thread (k, b): G = U Z, inverse channel DFT, in place on column b of patch k.
+// Stage E: thread (k, b): G_f[:, b] = U_f Z_f[:, b], inverse channel DFT, in place on column b of patch k.
 template <int C>
 __device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int b) {
     using G = FCfg<C>;
@@ -327,18 +368,18 @@ __device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int 
             Zr[i] = col[i * G::RWF + 1];
             Zi[i] = col[i * G::RWF + 2];
         }
-        const float* U0 = bas;
-        const float* U1r = bas + 64;
-        const float* U1i = bas + 128;
 #pragma unroll
         for (int a = 0; a < PS; ++a) {
+            float u0[8], ur[8], ui[8];
+            load8(bas + a * PS, u0);
+            load8(bas + 64 + a * PS, ur);
+            load8(bas + 128 + a * PS, ui);
             float g0 = 0.f, gr = 0.f, gi = 0.f;
 #pragma unroll
             for (int i = 0; i < PS; ++i) {
-                const float u0 = U0[a * PS + i], ur = U1r[a * PS + i], ui = U1i[a * PS + i];
-                g0 = fmaf(u0, Z0[i], g0);
-                gr = fmaf(ur, Zr[i], fmaf(-ui, Zi[i], gr));
-                gi = fmaf(ur, Zi[i], fmaf(ui, Zr[i], gi));
+                g0 = fmaf(u0[i], Z0[i], g0);
+                gr = fmaf(ur[i], Zr[i], fmaf(-ui[i], Zi[i], gr));
+                gi = fmaf(ur[i], Zi[i], fmaf(ui[i], Zr[i], gi));
             }
             col[a * G::RWF + 0] = (g0 + 2.f * gr) * F_THIRD;
             col[a * G::RWF + 1] = (g0 - gr - F_SQ3 * gi) * F_THIRD;
@@ -348,19 +389,20 @@ __device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int 
         float Z[PS];
 #pragma unroll
         for (int i = 0; i < PS; ++i) Z[i] = col[i * G::RWF];
-        const float* U0 = bas;
 #pragma unroll
         for (int a = 0; a < PS; ++a) {
+            float u0[8];
+            load8(bas + a * PS, u0);
             float g0 = 0.f;
 #pragma unroll
-            for (int i = 0; i < PS; ++i) g0 = fmaf(U0[a * PS + i], Z[i], g0);
+            for (int i = 0; i < PS; ++i) g0 = fmaf(u0[i], Z[i], g0);
             col[a * G::RWF] = g0;
         }
     }
 }
 
 template <int K, int C, typename Tin, int MODE>
-__global__ void __launch_bounds__(FT_THREADS, 1) filter_kernel(FilterArgs a) {
+__global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
     using G = FCfg<C>;
     constexpr int NF = G::PATCH;                 // fibres
     constexpr int NBW = K * NF / 32;             // bitmap words per group
@@ -443,6 +485,11 @@ __global__ void __launch_bounds__(FT_THREADS, 1) filter_kernel(FilterArgs a) {
 #pragma unroll
                 for (int k = 0; k < K; ++k) fib[k] = gb[k * G::GS + tid];
                 haar_fwd<K>(fib, co);
+                if (MODE == FM_FORWARD && a.coef_out) {
+                    float* cdst = a.coef_out + (size_t)grp * K * NF;
+#pragma unroll
+                    for (int m = 0; m < K; ++m) cdst[m * NF + tid] = co[m];
+                }
 #pragma unroll
                 for (int m = 0; m < K; ++m) {
                     const float d = fabsf(co[m]) - a.tau32;

@@ -41,6 +41,12 @@ cudaError_t launch_quantize(const float* x, int64_t n, uint8_t* q, cudaStream_t 
 
 // ---- group filter and aggregation (filter.cu)
 enum FilterMode { FM_FORWARD = 0, FM_DENOM = 1, FM_ADJOINT = 2 };
+
+// Guard band of the threshold decision: a coefficient whose FP32 value lies within
+// kBandRel * ||G||_F + kBandTau * tau of tau is decided again in FP64 (||G||_F: Frobenius
+// norm of the group's inputs; kBandTau covers tau rounded to FP32).
+constexpr float kBandRel = 3.814697265625e-06f;       // 2^-18
+constexpr double kBandTau = 2.384185791015625e-07;    // 2^-22
 struct FilterArgs {
     const void* img;         // uint8 or float H x W x C (the values that are filtered)
     int img_is_float;
@@ -59,6 +65,7 @@ struct FilterArgs {
     float* partials;         // [ntiles][FHmax][FWmax][C+1]
     uint32_t* mask_out;      // optional
     float* weights_out;      // optional
+    float* coef_out;         // optional FP32 coefficients, K*64*C per group (accuracy checks)
     int mode;                // FilterMode
     // adjoint inputs
     const float* r_img;      // (gout / D) image that is filtered with the masks of img (FM_ADJOINT)

@@ -18,7 +18,7 @@ namespace {
 
 // ----------------------------------------------------------------------------- moments
 
-constexpr int MOM_CHUNK = 4096;    // references per CTA: 4096 * 8 * 255^2 < 2^32
+constexpr int MOM_CHUNK = 256;     // references per CTA (uint32 partials: 256 * 8 * 255^2 < 2^32)
 constexpr int MOM_BATCH = 32;      // references staged at once
 
 template <int C>
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) moments_kernel(const uint8_t* __restrict_
 }
 
 // Full second moment: CTA (bx, tile) accumulates a 64x64 tile of M over a chunk of references.
-constexpr int FM_CHUNK = 2048;     // 2048 * 255^2 < 2^32
+constexpr int FM_CHUNK = 512;      // references per CTA (512 * 255^2 < 2^32)
 constexpr int FM_BATCH = 64;
 
 __global__ void __launch_bounds__(256) full_moment_kernel(const uint8_t* __restrict__ img, Geo g,
@@ -281,14 +281,112 @@ __host__ __device__ void slice_basis(const unsigned long long* mom, int C, int w
     canonicalise(Ar, Vr, Vi, Out);
 }
 
-// One thread per (U or V, slice f) problem, f = 0 .. C/2.
+// Device form of the same solver: one warp per problem, lanes 0..7 update row/column k = lane of a
+// rotation in parallel; the matrices live in shared memory. Same rotations, same order.
+__device__ void jacobi_herm8_warp(double (*Ar)[PS], double (*Ai)[PS], double (*Vr)[PS], double (*Vi)[PS], int lane) {
+    if (lane < PS)
+        for (int j = 0; j < PS; ++j) {
+            Vr[lane][j] = lane == j ? 1.0 : 0.0;
+            Vi[lane][j] = 0.0;
+        }
+    __syncwarp();
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int i = 0; i < PS; ++i) {
+            dia += Ar[i][i] * Ar[i][i];
+            for (int j = i + 1; j < PS; ++j) off += Ar[i][j] * Ar[i][j] + Ai[i][j] * Ai[i][j];
+        }
+        if (off <= 1e-32 * dia || off == 0.0) break;
+        for (int p = 0; p < PS - 1; ++p)
+            for (int q = p + 1; q < PS; ++q) {
+                const double xr = Ar[p][q], xi = Ai[p][q];
+                const double r = sqrt(xr * xr + xi * xi);
+                const double app = Ar[p][p], aqq = Ar[q][q];
+                __syncwarp();
+                if (r == 0.0 || r < 1e-17 * sqrt(fabs(app * aqq))) {
+                    if (lane == 0) Ar[p][q] = Ai[p][q] = Ar[q][p] = Ai[q][p] = 0.0;
+                    __syncwarp();
+                    continue;
+                }
+                const double er = xr / r, ei = xi / r;
+                const double th = (aqq - app) / (2.0 * r);
+                double t;
+                if (fabs(th) > 1e150) t = 0.5 / th;
+                else t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                if (lane < PS) {
+                    const int k = lane;
+                    const double pr = Ar[k][p], pi = Ai[k][p], qr = Ar[k][q], qi = Ai[k][q];
+                    const double mr = er * qr + ei * qi, mi = er * qi - ei * qr;
+                    Ar[k][p] = c * pr - sn * mr;
+                    Ai[k][p] = c * pi - sn * mi;
+                    Ar[k][q] = sn * pr + c * mr;
+                    Ai[k][q] = sn * pi + c * mi;
+                }
+                __syncwarp();
+                if (lane < PS) {
+                    const int k = lane;
+                    const double pr = Ar[p][k], pi = Ai[p][k], qr = Ar[q][k], qi = Ai[q][k];
+                    const double mr = er * qr - ei * qi, mi = er * qi + ei * qr;
+                    Ar[p][k] = c * pr - sn * mr;
+                    Ai[p][k] = c * pi - sn * mi;
+                    Ar[q][k] = sn * pr + c * mr;
+                    Ai[q][k] = sn * pi + c * mi;
+                    const double vpr = Vr[k][p], vpi = Vi[k][p], vqr = Vr[k][q], vqi = Vi[k][q];
+                    const double nr = er * vqr + ei * vqi, ni = er * vqi - ei * vqr;
+                    Vr[k][p] = c * vpr - sn * nr;
+                    Vi[k][p] = c * vpi - sn * ni;
+                    Vr[k][q] = sn * vpr + c * nr;
+                    Vi[k][q] = sn * vpi + c * ni;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    Ar[p][p] = app - t * r;
+                    Ar[q][q] = aqq + t * r;
+                    Ai[p][p] = Ai[q][q] = 0.0;
+                    Ar[p][q] = Ai[p][q] = Ar[q][p] = Ai[q][p] = 0.0;
+                }
+                __syncwarp();
+            }
+    }
+}
+
+// One warp per (U or V, slice f) problem, f = 0 .. C/2.
 __global__ void basis_kernel(const unsigned long long* __restrict__ mom, int C, double* __restrict__ b64,
                              float* __restrict__ b32) {
     __shared__ double Res[4][PS][PS][2];
     __shared__ double work[4][4 * PS2];
     const int nf = C / 2 + 1;
-    const int t = threadIdx.x;
-    if (t < 2 * nf) slice_basis(mom, C, t / nf, t % nf, work[t], Res[t]);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < 2 * nf) {
+        const int which = w / nf, f = w % nf;
+        double (*Ar)[PS] = reinterpret_cast<double (*)[PS]>(work[w]);
+        double (*Ai)[PS] = reinterpret_cast<double (*)[PS]>(work[w] + PS2);
+        double (*Vr)[PS] = reinterpret_cast<double (*)[PS]>(work[w] + 2 * PS2);
+        double (*Vi)[PS] = reinterpret_cast<double (*)[PS]>(work[w] + 3 * PS2);
+        const unsigned long long* M = mom + (size_t)which * PS * PS * C * C;
+        const double s32 = 0.5 * sqrt(3.0);
+        for (int e = lane; e < PS2; e += 32) {
+            const int u = e / PS, v = e % PS;
+            double accr = 0.0, acci = 0.0;
+            for (int c = 0; c < C; ++c)
+                for (int c2 = 0; c2 < C; ++c2) {
+                    const double m = (double)M[((u * PS + v) * C + c) * C + c2];
+                    const int d = which == 0 ? (c - c2) : (c2 - c);
+                    const int k = ((f * d) % C + C) % C;
+                    double phr = 1.0, phi = 0.0;
+                    if (C == 3 && k == 1) { phr = -0.5; phi = -s32; }
+                    if (C == 3 && k == 2) { phr = -0.5; phi = s32; }
+                    accr += m * phr;
+                    acci += m * phi;
+                }
+            Ar[u][v] = accr;
+            Ai[u][v] = u == v ? 0.0 : acci;
+        }
+        __syncwarp();
+        jacobi_herm8_warp(Ar, Ai, Vr, Vi, lane);
+        if (lane == 0) canonicalise(Ar, Vr, Vi, Res[w]);
+    }
     __syncthreads();
     // Write FP64 slices (conjugate slices C - f for f > C/2) and the packed FP32 copies.
     for (int e = threadIdx.x; e < 2 * C * PS2; e += blockDim.x) {
@@ -419,7 +517,7 @@ cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long l
 }
 
 cudaError_t launch_basis(const unsigned long long* d_mom, int C, double* d_basis64, float* d_basis32, cudaStream_t s) {
-    basis_kernel<<<1, 64, 0, s>>>(d_mom, C, d_basis64, d_basis32);
+    basis_kernel<<<1, 128, 0, s>>>(d_mom, C, d_basis64, d_basis32);
     return cudaGetLastError();
 }
 

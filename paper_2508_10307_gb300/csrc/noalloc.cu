@@ -130,8 +130,8 @@ extern "C" htsvd_status htsvd_denoise_noalloc(const uint8_t* d_noisy, int32_t H,
     fa.basis64 = b64;
     fa.tau64 = tau;
     fa.tau32 = (float)tau;
-    fa.band_rel = 6.103515625e-05f;
-    fa.band_abs = (float)(tau * 2.384185791015625e-07) + 1e-6f;
+    fa.band_rel = kBandRel;
+    fa.band_abs = (float)(tau * kBandTau) + 1e-6f;
     fa.w_in = nullptr;
     fa.agg_mode = p->agg_mode;
     fa.partials = part;

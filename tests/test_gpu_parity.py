@@ -164,3 +164,25 @@ def test_batch_equals_single_calls():
     for t, s, o in zip(imgs, sig, outs):
         ref = H.denoise(t, s, prm)
         assert torch.equal(ref, o)
+
+
+BAND_REL = 2.0 ** -18     # guard band of the threshold decision, relative to ||G||_F (kernels.h kBandRel)
+
+
+@pytest.mark.parametrize("key", ["gray128", "rgb512"])
+def test_fp32_coefficient_error_is_well_inside_the_guard_band(key):
+    """The FP32 coefficients decide keep/drop outside the band, so their error against the
+    FP64 coefficients of the oracle must stay far below band * ||G||_F on the workloads."""
+    clean, noisy, sigma, prm, r = oracle_run(key)
+    out, info = H.denoise(_dev(noisy), sigma, prm, return_info=True, coeffs=True)
+    coef = info["coeffs"].cpu().numpy()
+    p = O.Params.of(prm)
+    Hk = O.haar_matrix(p.K)
+    rng = np.random.default_rng(0)
+    sample = rng.choice(len(r.idx), size=min(2048, len(r.idx)), replace=False)
+    G = O.gather_groups(noisy, r.idx[sample], p.ps)
+    S = O.forward_transform(G, r.U, r.V, Hk)
+    nrm = np.sqrt((G.reshape(len(sample), -1) ** 2).sum(axis=1))
+    err = np.abs(coef[sample].astype(np.float64) - S).reshape(len(sample), -1).max(axis=1)
+    worst = float((err / nrm).max())
+    assert worst <= BAND_REL / 8, f"max |S32 - S64| / ||G|| = {worst:.3e}"
