@@ -81,6 +81,9 @@ struct Workspace {
     size_t cap[S_NSLOT] = {};
     void* hpin = nullptr;
     size_t hcap = 0;
+    cudaStream_t side = nullptr;          // moments + basis run here (highest priority), concurrently with
+                                          // block matching
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 std::mutex g_mu;
@@ -116,6 +119,20 @@ htsvd_status ws_get(Workspace* w, int slot, size_t bytes, void** out) {
         w->cap[slot] = b;
     }
     *out = w->buf[slot];
+    return HTSVD_OK;
+}
+
+// Side stream and fork/join events of a workspace, created on first use.
+htsvd_status ws_side(Workspace* w) {
+    if (w->side) return HTSVD_OK;
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);       // hi: numerically lowest = most urgent
+    if (cudaStreamCreateWithPriority(&w->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return HTSVD_ERR_CUDA;
+    }
     return HTSVD_OK;
 }
 
@@ -387,11 +404,17 @@ htsvd_status denoise_impl(const void* d_in, int is_float, int H, int W, int C, d
         CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         CK(cudaEventRecord(ev, s));
     }
-    // Grouping and the bases do not depend on sigma: they run while the host finishes the estimate.
-    ST(run_block_match(q, g, r, 1, idx, s));
+    // Grouping and the bases do not depend on sigma: they run while the host finishes the estimate,
+    // the bases on the side stream concurrently with block matching (joined before the filter).
+    ST(ws_side(w));
+    CK(cudaEventRecord(w->ev_fork, s));
+    CK(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
     double* b64;
     float* b32;
-    ST(run_basis(w, q, g, &b64, &b32, s));
+    ST(run_basis(w, q, g, &b64, &b32, w->side));
+    CK(cudaEventRecord(w->ev_join, w->side));
+    ST(run_block_match(q, g, r, 1, idx, s));
+    CK(cudaStreamWaitEvent(s, w->ev_join, 0));
     if (p && p->d_basis_out)
         CK(cudaMemcpyAsync(p->d_basis_out, b64, sizeof(double) * 2 * 2 * C * PS2, cudaMemcpyDeviceToDevice, s));
     if (sigma < 0) {
@@ -605,6 +628,9 @@ htsvd_status htsvd_release_workspace(void) {
             for (int i = 0; i < S_NSLOT; ++i)
                 if (w->buf[i]) cudaFree(w->buf[i]);
             if (w->hpin) cudaFreeHost(w->hpin);
+            if (w->side) cudaStreamDestroy(w->side);
+            if (w->ev_fork) cudaEventDestroy(w->ev_fork);
+            if (w->ev_join) cudaEventDestroy(w->ev_join);
             delete w;
             it = g_ws.erase(it);
         } else {

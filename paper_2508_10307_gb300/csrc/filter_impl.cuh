@@ -35,9 +35,12 @@ constexpr float F_THIRD = 0.333333333333333333333333333333333333f;
 
 template <int C>
 struct FCfg {
-    static constexpr int RWF = PS * C;                 // floats per patch row
-    static constexpr int PATCH = PS2 * C;              // floats per patch
-    static constexpr int GS = (C == 3) ? 196 : 68;     // padded stride between patches in the group buffer
+    static constexpr int RWF = PS * C;                 // floats of data per patch row
+    static constexpr int ROW = (C == 3) ? 28 : 12;     // padded row stride: an odd number of 16-byte units,
+                                                       // so the 128-bit row loads of 8 consecutive rows hit
+                                                       // distinct bank groups
+    static constexpr int PATCH = PS2 * C;              // floats per patch (fibres of the Haar stage)
+    static constexpr int GS = (C == 3) ? 228 : 100;    // stride between patches (odd number of 16-byte units)
     static constexpr int ACC = (C == 3) ? 4 : 2;       // floats per footprint pixel (C numerators + 1 denominator)
     static constexpr int NBAS = (C == 3) ? 384 : 128;  // packed FP32 basis floats
 };
@@ -233,9 +236,9 @@ __device__ __forceinline__ float stage_a(const Tin* img_s, int FW, const int* po
         }
 #pragma unroll
         for (int ii = 0; ii < PS; ++ii) {
-            dst[ii * G::RWF + 0] = y0[ii];
-            dst[ii * G::RWF + 1] = yr[ii];
-            dst[ii * G::RWF + 2] = yi[ii];
+            dst[ii * G::ROW + 0] = y0[ii];
+            dst[ii * G::ROW + 1] = yr[ii];
+            dst[ii * G::ROW + 2] = yi[ii];
         }
     } else {
         float y0[PS];
@@ -249,7 +252,7 @@ __device__ __forceinline__ float stage_a(const Tin* img_s, int FW, const int* po
             for (int ii = 0; ii < PS; ++ii) y0[ii] = fmaf(u0[ii], x[a][0], y0[ii]);
         }
 #pragma unroll
-        for (int ii = 0; ii < PS; ++ii) dst[ii * G::RWF] = y0[ii];
+        for (int ii = 0; ii < PS; ++ii) dst[ii * G::ROW] = y0[ii];
     }
     return nrm;
 }
@@ -258,7 +261,7 @@ __device__ __forceinline__ float stage_a(const Tin* img_s, int FW, const int* po
 template <int C>
 __device__ __forceinline__ void stage_b(const float* bas, float* gb, int k, int i) {
     using G = FCfg<C>;
-    float4* row = reinterpret_cast<float4*>(gb + k * G::GS + i * G::RWF);
+    float4* row = reinterpret_cast<float4*>(gb + k * G::GS + i * G::ROW);
     float y[G::RWF];
 #pragma unroll
     for (int q = 0; q < G::RWF / 4; ++q) {
@@ -309,7 +312,7 @@ __device__ __forceinline__ void stage_b(const float* bas, float* gb, int k, int 
 template <int C>
 __device__ __forceinline__ void stage_d(const float* bas, float* gb, int k, int i) {
     using G = FCfg<C>;
-    float4* row = reinterpret_cast<float4*>(gb + k * G::GS + i * G::RWF);
+    float4* row = reinterpret_cast<float4*>(gb + k * G::GS + i * G::ROW);
     float t[G::RWF];
 #pragma unroll
     for (int q = 0; q < G::RWF / 4; ++q) {
@@ -364,9 +367,9 @@ __device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int 
         float Z0[PS], Zr[PS], Zi[PS];
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
-            Z0[i] = col[i * G::RWF];
-            Zr[i] = col[i * G::RWF + 1];
-            Zi[i] = col[i * G::RWF + 2];
+            Z0[i] = col[i * G::ROW];
+            Zr[i] = col[i * G::ROW + 1];
+            Zi[i] = col[i * G::ROW + 2];
         }
 #pragma unroll
         for (int a = 0; a < PS; ++a) {
@@ -381,14 +384,14 @@ __device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int 
                 gr = fmaf(ur[i], Zr[i], fmaf(-ui[i], Zi[i], gr));
                 gi = fmaf(ur[i], Zi[i], fmaf(ui[i], Zr[i], gi));
             }
-            col[a * G::RWF + 0] = (g0 + 2.f * gr) * F_THIRD;
-            col[a * G::RWF + 1] = (g0 - gr - F_SQ3 * gi) * F_THIRD;
-            col[a * G::RWF + 2] = (g0 - gr + F_SQ3 * gi) * F_THIRD;
+            col[a * G::ROW + 0] = (g0 + 2.f * gr) * F_THIRD;
+            col[a * G::ROW + 1] = (g0 - gr - F_SQ3 * gi) * F_THIRD;
+            col[a * G::ROW + 2] = (g0 - gr + F_SQ3 * gi) * F_THIRD;
         }
     } else {
         float Z[PS];
 #pragma unroll
-        for (int i = 0; i < PS; ++i) Z[i] = col[i * G::RWF];
+        for (int i = 0; i < PS; ++i) Z[i] = col[i * G::ROW];
 #pragma unroll
         for (int a = 0; a < PS; ++a) {
             float u0[8];
@@ -396,7 +399,7 @@ __device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int 
             float g0 = 0.f;
 #pragma unroll
             for (int i = 0; i < PS; ++i) g0 = fmaf(u0[i], Z[i], g0);
-            col[a * G::RWF] = g0;
+            col[a * G::ROW] = g0;
         }
     }
 }
@@ -406,6 +409,8 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
     using G = FCfg<C>;
     constexpr int NF = G::PATCH;                 // fibres
     constexpr int NBW = K * NF / 32;             // bitmap words per group
+    // lanes that run the per-patch stages (threads 0 .. 8K-1; K = 2 fills half a warp)
+    constexpr unsigned kAB = (8 * K >= 32) ? 0xffffffffu : ((1u << (8 * K)) - 1u);
     const Geo& g = a.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ty = blockIdx.x / a.ntx, tx = blockIdx.x - ty * a.ntx;
@@ -468,22 +473,34 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
         uint32_t keepb = 0;
         if constexpr (MODE != FM_DENOM) {
             // ---- A, B on the filtered image
+            // A and B of patch k run on threads 8k..8k+7 of one warp: a warp barrier orders them.
             if (tid < 8 * K) {
                 const float nrm = stage_a<K, C, Tin>(img_s, FW, pos, bas, gb, tid >> 3, tid & 7);
-                atomicAdd(reinterpret_cast<float*>(&misc[2]), nrm);
+                // ||G||_F^2: a warp sum first (exact in int for uint8 inputs), one shared atomic per warp
+                if constexpr (sizeof(Tin) == 1) {
+                    const int wsum = __reduce_add_sync(kAB, (int)nrm);
+                    if (lane == 0) atomicAdd(&misc[5], wsum);
+                } else {
+                    float v = nrm;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kAB, v, off);
+                    if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[2]), v);
+                }
+                __syncwarp(kAB);
+                stage_b<C>(bas, gb, tid >> 3, tid & 7);
             }
             __syncthreads();
-            if (tid < 8 * K) stage_b<C>(bas, gb, tid % K, tid / K);
-            __syncthreads();
             // ---- C1: Haar analysis and FP32 decisions with a guard band
-            const float nrm2 = __int_as_float(misc[2]);
+            const float nrm2 = sizeof(Tin) == 1 ? (float)misc[5] : __int_as_float(misc[2]);
             const float delta = a.band_rel * sqrtf(nrm2) + a.band_abs;
             float co[K];
             uint32_t bandb = 0;
+            // fibre tid = (i*8 + j)*C + c lives at row i, column offset j*C + c of every patch
+            const int foff = (tid / G::RWF) * G::ROW + (tid % G::RWF);
             if (tid < NF) {
                 float fib[K];
 #pragma unroll
-                for (int k = 0; k < K; ++k) fib[k] = gb[k * G::GS + tid];
+                for (int k = 0; k < K; ++k) fib[k] = gb[k * G::GS + foff];
                 haar_fwd<K>(fib, co);
                 if (MODE == FM_FORWARD && a.coef_out) {
                     float* cdst = a.coef_out + (size_t)grp * K * NF;
@@ -533,14 +550,17 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
                             if (lane == 0) mo[m * (NF / 32) + warp] = w;
                         }
                     }
-                    atomicAdd(&misc[1], __popc(keepb));
+                    {
+                        const int wk = __reduce_add_sync(0xffffffffu, __popc(keepb));
+                        if (lane == 0) atomicAdd(&misc[1], wk);
+                    }
 #pragma unroll
                     for (int m = 0; m < K; ++m)
                         if (!((keepb >> m) & 1u)) co[m] = 0.f;
                     float rec[K];
                     haar_inv<K>(co, rec);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) gb[k * G::GS + tid] = rec[k];
+                    for (int k = 0; k < K; ++k) gb[k * G::GS + foff] = rec[k];
                 } else {
 #pragma unroll
                     for (int m = 0; m < K; ++m) cx[m] = ((keepb >> m) & 1u) ? co[m] : 0.f;
@@ -551,6 +571,8 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
                 // ---- second pass on r = gout / D with the masks of x
                 if (tid < 8 * K) {
                     stage_a<K, C, float>(r_s, FW, pos, bas, gb, tid >> 3, tid & 7);
+                    __syncwarp(kAB);
+                    stage_b<C>(bas, gb, tid >> 3, tid & 7);
                     // <Gather(r), Gather(out)> for the weight gradient
                     const int k = tid >> 3, b = tid & 7;
                     const float* rp = r_s + (pos[2 * k] * FW + pos[2 * k + 1] + b) * C;
@@ -561,15 +583,15 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
 #pragma unroll
                         for (int c = 0; c < C; ++c)
                             dot = fmaf(rp[i * FW * C + c], a.out_img[((size_t)(gy + i) * g.W + gx) * C + c], dot);
-                    atomicAdd(reinterpret_cast<float*>(&misc[4]), dot);
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(kAB, dot, off);
+                    if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[4]), dot);
                 }
-                __syncthreads();
-                if (tid < 8 * K) stage_b<C>(bas, gb, tid % K, tid / K);
                 __syncthreads();
                 if (tid < NF) {
                     float fib[K], cr[K];
 #pragma unroll
-                    for (int k = 0; k < K; ++k) fib[k] = gb[k * G::GS + tid];
+                    for (int k = 0; k < K; ++k) fib[k] = gb[k * G::GS + foff];
                     haar_fwd<K>(fib, cr);
                     float dot = 0.f;
 #pragma unroll
@@ -577,18 +599,22 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
                         if (!((keepb >> m) & 1u)) cr[m] = 0.f;
                         dot = fmaf(cr[m], cx[m], dot);
                     }
-                    atomicAdd(reinterpret_cast<float*>(&misc[3]), dot);
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+                    if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[3]), dot);
                     float rec[K];
                     haar_inv<K>(cr, rec);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) gb[k * G::GS + tid] = rec[k];
+                    for (int k = 0; k < K; ++k) gb[k * G::GS + foff] = rec[k];
                 }
                 __syncthreads();
             }
-            // ---- D, E: inverse projection
-            if (tid < 8 * K) stage_d<C>(bas, gb, tid % K, tid / K);
-            __syncthreads();
-            if (tid < 8 * K) stage_e<C>(bas, gb, tid >> 3, tid & 7);
+            // ---- D, E: inverse projection (patch k on threads 8k..8k+7 of one warp)
+            if (tid < 8 * K) {
+                stage_d<C>(bas, gb, tid >> 3, tid & 7);
+                __syncwarp(kAB);
+                stage_e<C>(bas, gb, tid >> 3, tid & 7);
+            }
         }
         // ---- weight of the group
         if (a.w_in) wg = a.w_in[grp];
@@ -610,14 +636,14 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
                 if (lane < 24) {
                     if constexpr (MODE != FM_DENOM) {
                         const int j = lane / 3, c = lane - 3 * (lane / 3);
-                        ap[j * 4 + c] += wg * gb[k * G::GS + i * G::RWF + lane];
+                        ap[j * 4 + c] += wg * gb[k * G::GS + i * G::ROW + lane];
                     }
                 } else if (MODE != FM_ADJOINT) {
                     ap[(lane - 24) * 4 + 3] += wg;
                 }
             } else {
                 if (lane < 8) {
-                    if constexpr (MODE != FM_DENOM) ap[lane * 2] += wg * gb[k * G::GS + i * G::RWF + lane];
+                    if constexpr (MODE != FM_DENOM) ap[lane * 2] += wg * gb[k * G::GS + i * G::ROW + lane];
                 } else if (lane < 16 && MODE != FM_ADJOINT) {
                     ap[(lane - 8) * 2 + 1] += wg;
                 }

@@ -86,8 +86,11 @@ __global__ void __launch_bounds__(256) moments_kernel(const uint8_t* __restrict_
 }
 
 // Full second moment: CTA (bx, tile) accumulates a 64x64 tile of M over a chunk of references.
+// The patch values of 4 consecutive references are packed per 32-bit word ([u][ref/4]), so one
+// dp4a adds the products of 4 references; each thread owns a 4x4 block of the tile.
 constexpr int FM_CHUNK = 512;      // references per CTA (512 * 255^2 < 2^32)
-constexpr int FM_BATCH = 64;
+constexpr int FM_BATCH = 64;       // references staged at once
+constexpr int FM_WPAD = FM_BATCH / 4 + 1;
 
 __global__ void __launch_bounds__(256) full_moment_kernel(const uint8_t* __restrict__ img, Geo g,
                                                           unsigned long long* __restrict__ M,
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(256) full_moment_kernel(const uint8_t* __restr
     const int d = PS2 * g.C;
     const int ntile = (d + 63) / 64;
     const int tu = blockIdx.y / ntile, tv = blockIdx.y % ntile;
-    __shared__ uint8_t pt[FM_BATCH][3 * PS2];
+    __shared__ uint32_t pk[3 * PS2][FM_WPAD];
     const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
     uint32_t acc[4][4] = {};
     uint32_t sacc = 0;
@@ -104,43 +107,48 @@ __global__ void __launch_bounds__(256) full_moment_kernel(const uint8_t* __restr
     for (int rb = r0; rb < r1; rb += FM_BATCH) {
         const int nb = min(FM_BATCH, r1 - rb);
         __syncthreads();
-        for (int t = threadIdx.x; t < nb * d; t += 256) {
-            int j = t / d, u = t - j * d;
-            int pix = u / g.C, c = u - pix * g.C;
-            int r = rb + j;
-            int iy = r / g.nrx, ix = r - iy * g.nrx;
-            int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
-            pt[j][u] = img[((size_t)(ry + pix / PS) * g.W + rx + pix % PS) * g.C + c];
+        for (int t = threadIdx.x; t < FM_BATCH * d; t += 256) {
+            const int j = t / d, u = t - j * d;
+            uint8_t v = 0;
+            if (j < nb) {
+                const int pix = u / g.C, c = u - pix * g.C;
+                const int r = rb + j;
+                const int iy = r / g.nrx, ix = r - iy * g.nrx;
+                const int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
+                v = img[((size_t)(ry + pix / PS) * g.W + rx + pix % PS) * g.C + c];
+            }
+            reinterpret_cast<uint8_t*>(&pk[u][j >> 2])[j & 3] = v;
         }
         __syncthreads();
-        for (int j = 0; j < nb; ++j) {
+        const int nw = (nb + 3) >> 2;
+        for (int jw = 0; jw < nw; ++jw) {
             uint32_t au[4], bv[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                int u = tu * 64 + ty * 4 + q, v = tv * 64 + tx * 4 + q;
-                au[q] = u < d ? pt[j][u] : 0;
-                bv[q] = v < d ? pt[j][v] : 0;
+                const int u = tu * 64 + ty * 4 + q, v = tv * 64 + tx * 4 + q;
+                au[q] = u < d ? pk[u][jw] : 0u;
+                bv[q] = v < d ? pk[v][jw] : 0u;
             }
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] += au[p] * bv[q];
+                for (int q = 0; q < 4; ++q) acc[p][q] = __dp4a(au[p], bv[q], acc[p][q]);
         }
         if (tv == 0 && threadIdx.x < 64) {
-            int u = tu * 64 + threadIdx.x;
+            const int u = tu * 64 + threadIdx.x;
             if (u < d)
-                for (int j = 0; j < nb; ++j) sacc += pt[j][u];
+                for (int jw = 0; jw < nw; ++jw) sacc = __dp4a(pk[u][jw], 0x01010101u, sacc);
         }
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            int u = tu * 64 + ty * 4 + p, v = tv * 64 + tx * 4 + q;
+            const int u = tu * 64 + ty * 4 + p, v = tv * 64 + tx * 4 + q;
             if (u < d && v < d && acc[p][q]) atomicAdd(M + (size_t)u * d + v, (unsigned long long)acc[p][q]);
         }
     if (tv == 0 && threadIdx.x < 64) {
-        int u = tu * 64 + threadIdx.x;
+        const int u = tu * 64 + threadIdx.x;
         if (u < d && sacc) atomicAdd(S + u, (unsigned long long)sacc);
     }
 }
