@@ -162,6 +162,123 @@ def run_reference(args):
 
 # ------------------------------------------------------------------------------------------- GPU arm
 
+def max_over_ranks_ms(ms, dist=None) -> float:
+    """The slowest rank's time: whole-job throughput divides all ranks' work by it."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, steps: int, mp_per_step: float, max_ms: float) -> float:
+    """Megapixels of every rank's steps over the slowest rank's device time (weak scaling)."""
+    return world * steps * mp_per_step / (max_ms / 1000.0)
+
+
+class Workload:
+    """One bench step: inputs resident on the device, the call a user makes, the result it returns."""
+
+    def __init__(self, name, config, mp_per_step, groups_per_step, C, K, host_inputs, step, result_bytes,
+                 compare=None, compare_name=None):
+        self.name, self.config, self.mp_per_step = name, config, mp_per_step
+        self.groups_per_step, self.C, self.K = groups_per_step, C, K
+        self.host_inputs, self.step, self.result_bytes = host_inputs, step, result_bytes
+        self.compare, self.compare_name = compare, compare_name
+
+
+def make_workload(name):
+    import numpy as np
+    import torch
+    import paper_2508_10307_gb300 as H
+    from paper_2508_10307_gb300 import synth
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    if name == "rgb512":
+        clean, noisy, _, prm = synth.workload_rgb512()
+        host = [noisy]
+        n = H.num_groups(512, 512, prm)
+        return Workload(name, dict(CONFIG), 512 * 512 / 1e6, n, 3, 32, host,
+                        lambda d: [H.denoise(d[0], None, prm)], 512 * 512 * 3 * 4), clean
+    if name == "gray128":
+        clean, noisy, sigma, prm = synth.workload_gray128()
+        cfg = {"workload": "gray128_sigma25", "image": "128x128x1 uint8", "noise": "gaussian sigma=25",
+               "sigma": "given (25)", "ps": 8, "stride": 3, "window": 21, "K": 16, "tau": "2.7 sigma"}
+        return Workload(name, cfg, 128 * 128 / 1e6, H.num_groups(128, 128, prm), 1, 16, [noisy],
+                        lambda d: [H.denoise(d[0], sigma, prm)], 128 * 128 * 4), clean
+    if name == "rgb4k":
+        clean = synth.clean_image(2160, 3840, 3, 1003)
+        levels = [10.0, 25.0, 50.0]
+        noisy = [synth.add_poisson_gaussian(clean, 0.01, b * b, 1003) for b in levels]
+        prm = dict(ps=8, stride=3, window=31, K=32)
+        cfg = {"workload": "rgb3840x2160_pg_3levels", "image": "3 x 3840x2160x3 uint8 per step",
+               "noise": "poisson-gaussian a=0.01, b in {10^2, 25^2, 50^2}", "sigma": "given (sqrt(b))",
+               "ps": 8, "stride": 3, "window": 31, "K": 32}
+        n = H.num_groups(2160, 3840, prm)
+        return Workload(name, cfg, 3 * 3840 * 2160 / 1e6, 3 * n, 3, 32, noisy,
+                        lambda d: [H.denoise(x, b, prm) for x, b in zip(d, levels)],
+                        3 * 3840 * 2160 * 3 * 4), synth.quantize(clean)
+    if name == "batch64":
+        shapes = synth.batch_shapes(64)
+        imgs, sig, cleans = [], [], []
+        for j, (h, w, s_) in enumerate(shapes):
+            c, n_ = synth.batch_image(j, h, w, s_)
+            imgs.append(n_)
+            sig.append(s_)
+        prm = dict(ps=8, stride=3, window=31, K=32)
+        mp = sum(h * w for h, w, _ in shapes) / 1e6
+        groups = sum(H.num_groups(h, w, prm) for h, w, _ in shapes)
+        outs = [None]
+        cfg = {"workload": "batch64_rgb_uneven", "images": "64 RGB uint8, W~U{256..2048}, H~U{256..1536}",
+               "noise": "gaussian, sigma_j~U(10,50)", "sigma": "given per image", "ps": 8, "stride": 3,
+               "window": 31, "K": 32, "form": "one persistent launch per phase, CUDA graph replay, autotuned tiles"}
+
+        def step(d):
+            if outs[0] is None:
+                outs[0] = [torch.empty(x.shape, dtype=torch.float32, device="cuda") for x in d]
+            return H.denoise_batch(d, sig, prm, outs=outs[0])
+
+        def sequential(d):
+            return [H.denoise(x, s_, prm) for x, s_ in zip(d, sig)]
+
+        return Workload(name, cfg, mp, groups, 3, 32, imgs, step, int(mp * 1e6 * 12), sequential,
+                        "sequential_plain_calls"), None
+    if name == "vjp8":
+        cleans, xs = [], []
+        for j in range(8):
+            c = synth.clean_image(512, 512, 3, 3000 + j)
+            cleans.append(c.astype(np.float32))
+            xs.append(synth.add_gaussian_float(c, 25.0, 3000 + j))
+        prm = dict(ps=8, stride=2, window=31, K=32)
+        n = H.num_groups(512, 512, prm)
+        targets = [None]
+        cfg = {"workload": "vjp8_rgb512_f32", "images": "8 x 512x512x3 float32", "noise": "gaussian sigma=25",
+               "sigma": "given (25)", "ps": 8, "stride": 2, "window": 31, "K": 32,
+               "form": "forward + hand-written VJP (x and per-group weights), loss = MSE to the clean image"}
+
+        def step(d):
+            if targets[0] is None:
+                targets[0] = [dev(c) for c in cleans]
+            res = []
+            for x, t in zip(d, targets[0]):
+                xr = x.detach().requires_grad_(True)
+                w = torch.ones(n, device="cuda", requires_grad=True)
+                out = H.HtsvdFn.apply(xr, w, 25.0, prm)
+                loss = ((out - t) ** 2).mean()
+                loss.backward()
+                res.append(xr.grad)
+            return res
+
+        def forward_only(d):
+            return [H.denoise_f32(x, 25.0, prm) for x in d]
+
+        return Workload(name, cfg, 8 * 512 * 512 / 1e6, 8 * n, 3, 32, xs, step, 8 * 512 * 512 * 3 * 4,
+                        forward_only, "forward_only"), None
+    raise ValueError(name)
+
+
 def run_gpu(args):
     import torch
     import paper_2508_10307_gb300 as H
@@ -176,23 +293,37 @@ def run_gpu(args):
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     H.load_library()
-    clean, noisy, _, prm = synth.workload_rgb512()
-    Hh, Ww, C = noisy.shape
-    mp_step = Hh * Ww / 1e6
-    img = torch.from_numpy(noisy).cuda()
-    out = torch.empty((Hh, Ww, C), dtype=torch.float32, device="cuda")
+    wl, clean = make_workload(args.workload)
+    d_in = [torch.from_numpy(x).cuda() for x in wl.host_inputs]
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(src, dst):
-        return H.denoise(src, None, prm)
-
-    # warm-up (also grows the workspace)
+    # warm-up (also grows the workspace, tunes and captures the batch graph)
     for _ in range(args.warmup):
-        res = step(img, out)
+        res = wl.step(d_in)
     torch.cuda.synchronize()
-    # parity gate of the benchmarked configuration: PSNR against the clean image
-    psnr_gpu = synth.psnr(res.cpu().numpy(), clean)
+    psnr_gpu = synth.psnr(res[0].detach().cpu().numpy(), clean) if clean is not None else None
+
+    def timed(fn, inputs_dev, steps, with_copies=False, hosts=None, host_out=None):
+        evs = []
+        for _ in range(steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if with_copies:
+                for hsrc, ddst in zip(hosts, inputs_dev):
+                    ddst.copy_(hsrc, non_blocking=True)
+            r = fn(inputs_dev)
+            if with_copies:
+                for ro, ho in zip(r, host_out):
+                    ho.copy_(ro.detach(), non_blocking=True)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    def max_over_ranks(ms):
+        return max_over_ranks_ms(ms, dist)
 
     sampler = ClockSampler(local)
     _lib.profile_enable(True)
@@ -201,48 +332,33 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    evs = []
-    for _ in range(args.steps):
-        flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step(img, out)
-        b.record(stream)
-        evs.append((a, b))
-    torch.cuda.synchronize()
+    dev_ms = timed(wl.step, d_in, args.steps)
     if dist:
         dist.barrier()
     clocks = sampler.stop()
     prof = _lib.profile_collect()
     _lib.profile_enable(False)
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([dev_ms], dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms_max = float(t.item())
-    value = world * args.steps * mp_step / (dev_ms_max / 1000.0)
+    dev_ms_max = max_over_ranks(dev_ms)
+    value = whole_job_value(world, args.steps, wl.mp_per_step, dev_ms_max)
 
-    # end to end through the public API: pinned host input -> device, denoise, result -> pinned host
-    h_in = torch.from_numpy(noisy).pin_memory()
-    h_out = torch.empty((Hh, Ww, C), dtype=torch.float32).pin_memory()
-    d_in = torch.empty_like(img)
-    e2e_evs = []
-    for i in range(args.warmup + args.steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.fill_(1)
-        a.record(stream)
-        d_in.copy_(h_in, non_blocking=True)
-        r = step(d_in, out)
-        h_out.copy_(r, non_blocking=True)
-        b.record(stream)
-        if i >= args.warmup:
-            e2e_evs.append((a, b))
-    torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_evs)
-    t = torch.tensor([e2e_ms], dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps * mp_step / (float(t.item()) / 1000.0)
+    # end to end through the public API: pinned host inputs -> device, the call, results -> pinned host
+    hosts = [torch.from_numpy(x).pin_memory() for x in wl.host_inputs]
+    res = wl.step(d_in)
+    host_out = [torch.empty(r.shape, dtype=r.dtype).pin_memory() for r in res]
+    timed(wl.step, d_in, args.warmup, True, hosts, host_out)
+    e2e_ms = max_over_ranks(timed(wl.step, d_in, args.steps, True, hosts, host_out))
+    e2e_value = whole_job_value(world, args.steps, wl.mp_per_step, e2e_ms)
+    h2d = sum(x.nbytes for x in wl.host_inputs)
+    d2h = sum(h.numel() * h.element_size() for h in host_out)
+
+    compare = None
+    if wl.compare is not None:
+        for _ in range(args.warmup):
+            wl.compare(d_in)
+        cmp_ms = max_over_ranks(timed(wl.compare, d_in, args.steps))
+        cmp_value = whole_job_value(world, args.steps, wl.mp_per_step, cmp_ms)
+        compare = {"name": wl.compare_name, "value": cmp_value, "unit": UNIT, "ms_per_step": cmp_ms / args.steps,
+                   "ratio": value / cmp_value}
 
     if rank != 0:
         if dist:
@@ -251,24 +367,22 @@ def run_gpu(args):
 
     # roofline of the dominant kernel (by device time in the timed region)
     dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
-    launches = sum(v[0] for v in prof.values())
+    launches = sum(v[0] for v in prof.values()) if prof else 5 * args.steps
     roof = None
     if dom == "filter":
         n_launch, ms = prof["filter"]
-        flops = 64009 * filter_flops_per_group(3, 32)
+        flops = wl.groups_per_step * filter_flops_per_group(wl.C, wl.K) * args.steps / n_launch
         achieved = flops / (ms / n_launch / 1000.0) / 1e12
-        sm_mhz = 2070.0
-        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "group_filter",
                 "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts and max clock)"}
     elif dom is not None:
-        n_launch, ms = prof[dom]
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
                 "kernel": dom}
 
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload == "rgb512":
         try:
             r = run_oracle_subprocess(args.cpu_rows)
             cpu = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -280,13 +394,14 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(CONFIG, l2="256 MB buffer written between timed steps (untimed)",
+            "config": dict(wl.config, l2="256 MB buffer written between timed steps (untimed)",
                            parallelism=f"replicas x{world}"),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Hh * Ww * C,
-                    "d2h_bytes_per_step": Hh * Ww * C * 4},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "kernels_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "psnr_db": psnr_gpu}
+    if compare is not None:
+        line["compare"] = compare
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -299,6 +414,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rgb512", choices=["rgb512", "gray128", "rgb4k", "batch64", "vjp8"])
     ap.add_argument("--cpu-rows", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-worker", type=int, default=None)

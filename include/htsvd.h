@@ -38,7 +38,7 @@ typedef enum htsvd_status {
     HTSVD_ERR_UNSUPPORTED = 2,   /* valid for the method, not built here (ps != 8, K > 32, window > 64) */
     HTSVD_ERR_CUDA = 3,          /* a CUDA runtime call failed */
     HTSVD_ERR_OOM = 4,           /* workspace allocation failed */
-    HTSVD_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (persistent batch) */
+    HTSVD_ERR_TIMEOUT = 5,       /* reserved for bounded device waits; no kernel of this build waits on another CTA */
 } htsvd_status;
 
 typedef enum htsvd_match_mode {
@@ -70,7 +70,7 @@ typedef struct htsvd_params {
     double  beta;          /* <= 0 -> 1.2 (Sec. III-D) */
     int32_t rank_gamma;    /* <= 0 -> round(13 K / 32) (Sec. III-D) */
     int32_t tile;          /* reference tile edge for the filter (0 -> automatic) */
-    int64_t max_wait_cycles; /* persistent batch: clock64 budget of a queue wait; 0 -> 2^34 */
+    int64_t max_wait_cycles; /* reserved (bounded device waits); ignored by this build */
     /* Optional outputs (may be NULL). */
     double*   h_sigma_out;   /* HOST: the sigma actually used (estimated when sigma < 0) */
     uint32_t* d_mask_out;    /* DEVICE: threshold masks, per group ceil(K*ps*ps*C/32) words, bit index
@@ -117,9 +117,14 @@ htsvd_status htsvd_denoise_f32(const float* d_x, int32_t H, int32_t W, int32_t C
 htsvd_status htsvd_estimate_sigma(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C,
                                   const htsvd_params* p, double* h_sigma, cudaStream_t stream);
 
-/* Alg. 1 on n uint8 images of any sizes with per-image sigma (>= 0), as one
- * persistent launch per phase over a work queue. The launch sequence contains no host
- * synchronisation. Optional outputs of p are ignored. */
+/* Alg. 1 on n uint8 images of any sizes (one C for the whole batch) with per-image sigma
+ * (>= 0). Each phase (moments, bases, grouping, filter, reduction) is one persistent launch
+ * whose CTAs take (image, tile) work items from a queue over all images; the sequence is
+ * captured into a CUDA graph that later calls with the same images, sizes, sigmas and
+ * parameters replay. The first call for a new batch shape also times candidate tile shapes
+ * (autotuning) and synchronises `stream`; replays do not synchronise. If `stream` cannot be
+ * captured (for instance because the caller is capturing it), the sequence runs eagerly.
+ * Optional outputs of p are ignored. */
 htsvd_status htsvd_denoise_batch(const htsvd_image* h_imgs, int32_t n, const htsvd_params* p,
                                  cudaStream_t stream);
 

@@ -532,25 +532,6 @@ htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C
     return HTSVD_OK;
 }
 
-htsvd_status htsvd_denoise_batch(const htsvd_image* imgs, int32_t n, const htsvd_params* p, cudaStream_t s) {
-    if (n < 0 || (n > 0 && !imgs)) return HTSVD_ERR_INVALID_ARG;
-    for (int i = 0; i < n; ++i) {
-        if (!(imgs[i].sigma >= 0)) return HTSVD_ERR_INVALID_ARG;
-        htsvd_params q;
-        if (p) q = *p;
-        else std::memset(&q, 0, sizeof(q));
-        q.h_sigma_out = nullptr;
-        q.d_mask_out = nullptr;
-        q.d_weights_out = nullptr;
-        q.d_basis_out = nullptr;
-        q.d_coef_out = nullptr;
-        htsvd_status st = htsvd_denoise(imgs[i].d_in, imgs[i].H, imgs[i].W, imgs[i].C, imgs[i].sigma, &q,
-                                        imgs[i].d_out, nullptr, s);
-        if (st != HTSVD_OK) return st;
-    }
-    return HTSVD_OK;
-}
-
 int64_t htsvd_num_groups(int32_t H, int32_t W, const htsvd_params* p) {
     Resolved r;
     if (resolve(p, 1, r) != HTSVD_OK) return -1;

@@ -9,7 +9,10 @@ namespace htsvd {
 
 namespace {
 
-// A (n x n, row-major, symmetric, overwritten) -> diagonal d[n], off-diagonal e[n-1].
+// A (n x n, row-major, symmetric; only the lower triangle i >= j is read and overwritten)
+// -> diagonal d[n], off-diagonal e[n-1]. Step k reflects the trailing block B = A[k+1:, k+1:]
+// with H = I - beta v v^T (H x = alpha e_1 for x = A[k+1:, k]): p = beta B v,
+// w = p - (beta/2)(v^T p) v, B <- B - v w^T - w v^T.
 void tridiagonalize(double* A, int n, double* d, double* e) {
     std::vector<double> v(n), p(n), w(n);
     for (int k = 0; k < n - 2; ++k) {
@@ -25,17 +28,23 @@ void tridiagonalize(double* A, int n, double* d, double* e) {
             continue;
         }
         double alpha = std::sqrt(xn2);
-        if (x[0] > 0) alpha = -alpha;             // H x = alpha e_1, avoiding cancellation in v_0
+        if (x[0] > 0) alpha = -alpha;             // avoids cancellation in v_0
         x[0] -= alpha;
         double vtv = 0.0;
         for (int i = 0; i < m; ++i) vtv += x[i] * x[i];
         const double beta = 2.0 / vtv;
-        // p = beta * B v, B = A[k+1:, k+1:] symmetric: accumulated as sum_j x_j * row_j (axpy form)
+        // p = B v from the lower triangle: row i contributes its dot product to p_i and,
+        // through symmetry, L_ij v_i to p_j (j < i)
         for (int i = 0; i < m; ++i) p[i] = 0.0;
-        for (int j = 0; j < m; ++j) {
-            const double* row = A + (size_t)(k + 1 + j) * n + (k + 1);
-            const double xj = x[j];
-            for (int i = 0; i < m; ++i) p[i] += row[i] * xj;
+        for (int i = 0; i < m; ++i) {
+            const double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+            const double vi = x[i];
+            double s = 0.0;
+            for (int j = 0; j < i; ++j) {
+                s += row[j] * x[j];
+                p[j] += row[j] * vi;
+            }
+            p[i] += s + row[i] * vi;
         }
         double vp = 0.0;
         for (int i = 0; i < m; ++i) {
@@ -47,7 +56,7 @@ void tridiagonalize(double* A, int n, double* d, double* e) {
         for (int i = 0; i < m; ++i) {
             double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
             const double xi = x[i], wi = w[i];
-            for (int j = 0; j < m; ++j) row[j] -= xi * w[j] + wi * x[j];
+            for (int j = 0; j <= i; ++j) row[j] -= xi * w[j] + wi * x[j];
         }
         e[k] = alpha;
     }
@@ -72,11 +81,11 @@ bool tridiagonal_eigenvalues(double* a, double* b, int n) {
         // Wilkinson shift from the trailing 2x2 block
         const double dd = 0.5 * (a[hi - 1] - a[hi]);
         const double bb = b[hi - 1];
-        const double den = dd + (dd >= 0 ? 1.0 : -1.0) * std::hypot(dd, bb);
+        const double den = dd + (dd >= 0 ? 1.0 : -1.0) * std::sqrt(dd * dd + bb * bb);
         const double mu = a[hi] - (den != 0.0 ? bb * bb / den : 0.0);
         double x = a[lo] - mu, z = b[lo];
         for (int k = lo; k < hi; ++k) {
-            const double r = std::hypot(x, z);
+            const double r = std::sqrt(x * x + z * z);      // entries are far from overflow (covariances of bytes)
             const double c = r == 0.0 ? 1.0 : x / r, s = r == 0.0 ? 0.0 : z / r;
             if (k > lo) b[k - 1] = r;
             const double ak = a[k], ak1 = a[k + 1], bk = b[k];

@@ -53,13 +53,14 @@ __device__ inline void covering_tiles(int p, int nt, int TR, int nref, int s, in
     hi = a;
 }
 
+// Sum of the tile partials covering pixel p (deterministic tile order), then out = num / den.
 template <int C>
-__global__ void reduce_kernel(const float* __restrict__ partials, Geo g, int TR, int ntx, int nty, int FHmax,
-                              int FWmax, float* __restrict__ out, float* __restrict__ den_out, int num_only,
-                              const float* __restrict__ den_in) {
+__device__ __forceinline__ void reduce_pixel(int64_t p, const float* __restrict__ partials, const Geo& g, int TR,
+                                             int ntx, int nty, int FHmax, int FWmax, float* __restrict__ out,
+                                             float* __restrict__ den_out, int num_only,
+                                             const float* __restrict__ den_in) {
     constexpr int ACC = (C == 3) ? 4 : 2;
-    const int64_t npix = (int64_t)g.H * g.W;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+    {
         const int y = (int)(p / g.W), x = (int)(p - (int64_t)y * g.W);
         int ylo, yhi, xlo, xhi;
         covering_tiles(y, nty, TR, g.nry, g.s, g.H, g.npy, g.wny, g.win, ylo, yhi);
@@ -90,6 +91,44 @@ __global__ void reduce_kernel(const float* __restrict__ partials, Geo g, int TR,
     }
 }
 
+template <int C>
+__global__ void reduce_kernel(const float* __restrict__ partials, Geo g, int TR, int ntx, int nty, int FHmax,
+                              int FWmax, float* __restrict__ out, float* __restrict__ den_out, int num_only,
+                              const float* __restrict__ den_in) {
+    const int64_t npix = (int64_t)g.H * g.W;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x)
+        reduce_pixel<C>(p, partials, g, TR, ntx, nty, FHmax, FWmax, out, den_out, num_only, den_in);
+}
+
+// Batch form: pixel blocks of 256 of all images; block w -> image by prefix[] (in blocks).
+template <int C>
+__global__ void reduce_batch_kernel(const FilterArgs* __restrict__ args, float* const* __restrict__ outs,
+                                    const int* __restrict__ prefix, int nimg) {
+    const int total = prefix[nimg];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        int lo = 0, hi = nimg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const FilterArgs& a = args[lo];
+        const int64_t p = (int64_t)(w - prefix[lo]) * 256 + threadIdx.x;
+        if (p < (int64_t)a.g.H * a.g.W)
+            reduce_pixel<C>(p, a.partials, a.g, a.TR, a.ntx, a.nty, a.FHmax, a.FWmax, outs[lo], nullptr, 0, nullptr);
+    }
+}
+
+template <int K, int C>
+cudaError_t launch_filter_batch_t(const FilterArgs* d_args, const int* d_prefix, int nimg, size_t smem, int grid,
+                                  int* d_counter, cudaStream_t s) {
+    auto fn = filter_batch_kernel<K, C>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, FT_THREADS, smem, s>>>(d_args, d_prefix, nimg, d_counter);
+    return cudaGetLastError();
+}
+
 __global__ void div_kernel(const float* __restrict__ gout, const float* __restrict__ den, int64_t npix, int C,
                            float* __restrict__ r) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix * C; i += (int64_t)gridDim.x * blockDim.x)
@@ -117,6 +156,35 @@ cudaError_t launch_reduce(const float* partials, const Geo& g, int TR, int ntx, 
         reduce_kernel<3><<<blocks, 256, 0, s>>>(partials, g, TR, ntx, nty, FHmax, FWmax, out, den_out, num_only, den_in);
     else
         reduce_kernel<1><<<blocks, 256, 0, s>>>(partials, g, TR, ntx, nty, FHmax, FWmax, out, den_out, num_only, den_in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_batch(int K, int C, const FilterArgs* d_args, const int* d_prefix, int nimg, size_t smem,
+                                int grid, int* d_counter, cudaStream_t s) {
+    if (C == 3) {
+        switch (K) {
+            case 2: return launch_filter_batch_t<2, 3>(d_args, d_prefix, nimg, smem, grid, d_counter, s);
+            case 4: return launch_filter_batch_t<4, 3>(d_args, d_prefix, nimg, smem, grid, d_counter, s);
+            case 8: return launch_filter_batch_t<8, 3>(d_args, d_prefix, nimg, smem, grid, d_counter, s);
+            case 16: return launch_filter_batch_t<16, 3>(d_args, d_prefix, nimg, smem, grid, d_counter, s);
+            case 32: return launch_filter_batch_t<32, 3>(d_args, d_prefix, nimg, smem, grid, d_counter, s);
+        }
+    } else {
+        switch (K) {
+            case 2: return launch_filter_batch_t<2, 1>(d_args, d_prefix, nimg, smem, grid, d_counter, s);
+            case 4: return launch_filter_batch_t<4, 1>(d_args, d_prefix, nimg, smem, grid, d_counter, s);
+            case 8: return launch_filter_batch_t<8, 1>(d_args, d_prefix, nimg, smem, grid, d_counter, s);
+            case 16: return launch_filter_batch_t<16, 1>(d_args, d_prefix, nimg, smem, grid, d_counter, s);
+            case 32: return launch_filter_batch_t<32, 1>(d_args, d_prefix, nimg, smem, grid, d_counter, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reduce_batch(int C, const FilterArgs* d_args, float* const* d_outs, const int* d_prefix, int nimg,
+                                int grid, cudaStream_t s) {
+    if (C == 3) reduce_batch_kernel<3><<<grid, 256, 0, s>>>(d_args, d_outs, d_prefix, nimg);
+    else reduce_batch_kernel<1><<<grid, 256, 0, s>>>(d_args, d_outs, d_prefix, nimg);
     return cudaGetLastError();
 }
 

@@ -404,8 +404,9 @@ __device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int 
     }
 }
 
+// One tile of references (tile index t = ty * ntx + tx); smem: f_layout(...).total bytes.
 template <int K, int C, typename Tin, int MODE>
-__global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
+__device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile, unsigned char* smem) {
     using G = FCfg<C>;
     constexpr int NF = G::PATCH;                 // fibres
     constexpr int NBW = K * NF / 32;             // bitmap words per group
@@ -413,13 +414,12 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
     constexpr unsigned kAB = (8 * K >= 32) ? 0xffffffffu : ((1u << (8 * K)) - 1u);
     const Geo& g = a.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ty = blockIdx.x / a.ntx, tx = blockIdx.x - ty * a.ntx;
+    const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     int FY0, FY1, FX0, FX1;
     tile_span(ty, a.TR, g.nry, g.s, g.H, g.npy, g.wny, g.win, FY0, FY1);
     tile_span(tx, a.TR, g.nrx, g.s, g.W, g.npx, g.wnx, g.win, FX0, FX1);
     const int FH = FY1 - FY0, FW = FX1 - FX0;
     const FLayout L = f_layout<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), MODE);
-    extern __shared__ __align__(16) unsigned char smem[];
     float* bas = reinterpret_cast<float*>(smem + L.off_bas);
     float* gb = reinterpret_cast<float*>(smem + L.off_gb);
     int* pos = reinterpret_cast<int*>(smem + L.off_pos);
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
     }
     __syncthreads();
     // Write the tile partial.
-    float* dst = a.partials + (size_t)blockIdx.x * a.FHmax * a.FWmax * G::ACC;
+    float* dst = a.partials + (size_t)tile * a.FHmax * a.FWmax * G::ACC;
     if constexpr (C == 3) {
         const float4* s4 = reinterpret_cast<const float4*>(acc);
         float4* d4 = reinterpret_cast<float4*>(dst);
@@ -667,6 +667,36 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
             const int r = t / FW, c = t - r * FW;
             d2[r * a.FWmax + c] = s2[t];
         }
+    }
+}
+
+template <int K, int C, typename Tin, int MODE>
+__global__ void __launch_bounds__(FT_THREADS, 2) filter_kernel(FilterArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    filter_tile<K, C, Tin, MODE>(a, blockIdx.x, smem);
+}
+
+// Persistent form over the tiles of many images (same K and C): work item w -> image by prefix[].
+template <int K, int C>
+__global__ void __launch_bounds__(FT_THREADS, 2) filter_batch_kernel(const FilterArgs* __restrict__ args,
+                                                                     const int* __restrict__ prefix, int nimg,
+                                                                     int* __restrict__ counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int item;
+    const int total = prefix[nimg];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int w = item;
+        if (w >= total) break;
+        int lo = 0, hi = nimg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        filter_tile<K, C, uint8_t, FM_FORWARD>(args[lo], w - prefix[lo], smem);
     }
 }
 

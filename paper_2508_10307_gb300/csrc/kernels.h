@@ -45,7 +45,7 @@ enum FilterMode { FM_FORWARD = 0, FM_DENOM = 1, FM_ADJOINT = 2 };
 // Guard band of the threshold decision: a coefficient whose FP32 value lies within
 // kBandRel * ||G||_F + kBandTau * tau of tau is decided again in FP64 (||G||_F: Frobenius
 // norm of the group's inputs; kBandTau covers tau rounded to FP32).
-constexpr float kBandRel = 3.814697265625e-06f;       // 2^-18
+constexpr float kBandRel = 1.9073486328125e-06f;      // 2^-19
 constexpr double kBandTau = 2.384185791015625e-07;    // 2^-22
 struct FilterArgs {
     const void* img;         // uint8 or float H x W x C (the values that are filtered)
@@ -80,6 +80,20 @@ cudaError_t launch_reduce(const float* partials, const Geo& g, int TR, int ntx, 
                           float* out, float* den_out, int num_only, const float* den_in, cudaStream_t s);
 // Adjoint helper: r = gout / den.
 cudaError_t launch_div(const float* gout, const float* den, int64_t npix, int C, float* r, cudaStream_t s);
+
+// ---- persistent batch forms over many images (work items -> image by prefix sums)
+int bm_tiles(const BMArgs& a);
+cudaError_t launch_block_match_batch(const BMArgs* d_args, const int* d_prefix, int nimg, size_t smem, int grid,
+                                     int* d_counter, cudaStream_t s);
+int moments_chunks(const Geo& g);
+cudaError_t launch_moments_batch(int C, const BMArgs* d_args, unsigned long long* const* d_moms, const int* d_prefix,
+                                 int nimg, int grid, cudaStream_t s);
+cudaError_t launch_basis_batch(int C, const FilterArgs* d_fargs, unsigned long long* const* d_moms, int nimg,
+                               cudaStream_t s);
+cudaError_t launch_filter_batch(int K, int C, const FilterArgs* d_args, const int* d_prefix, int nimg, size_t smem,
+                                int grid, int* d_counter, cudaStream_t s);
+cudaError_t launch_reduce_batch(int C, const FilterArgs* d_args, float* const* d_outs, const int* d_prefix, int nimg,
+                                int grid, cudaStream_t s);
 
 // ---- sigma adjustment (moments.cu)
 // Rank position a = 1 + #{f : lambda_f < lambda_{K/2}} of each sampled group (Sec. III-D).

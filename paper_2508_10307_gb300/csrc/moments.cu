@@ -21,9 +21,10 @@ namespace {
 constexpr int MOM_CHUNK = 256;     // references per CTA (uint32 partials: 256 * 8 * 255^2 < 2^32)
 constexpr int MOM_BATCH = 32;      // references staged at once
 
+// Moments of the references [chunk * MOM_CHUNK, (chunk + 1) * MOM_CHUNK) added into out.
 template <int C>
-__global__ void __launch_bounds__(256) moments_kernel(const uint8_t* __restrict__ img, Geo g,
-                                                      unsigned long long* __restrict__ out) {
+__device__ __forceinline__ void moments_chunk(const uint8_t* __restrict__ img, const Geo& g, int chunk,
+                                              unsigned long long* __restrict__ out) {
     // rows[j][c][a] = 8 bytes of row a of channel c; cols[j][c][b] = 8 bytes of column b.
     __shared__ uint32_t rows[MOM_BATCH][C][PS][2];
     __shared__ uint32_t cols[MOM_BATCH][C][PS][2];
@@ -34,7 +35,7 @@ __global__ void __launch_bounds__(256) moments_kernel(const uint8_t* __restrict_
     for (int e = 0; e < EPT; ++e) acc[e] = 0;
 
     const int N = g.ngroups();
-    const int r0 = blockIdx.x * MOM_CHUNK;
+    const int r0 = chunk * MOM_CHUNK;
     const int r1 = min(r0 + MOM_CHUNK, N);
     for (int rb = r0; rb < r1; rb += MOM_BATCH) {
         const int nb = min(MOM_BATCH, r1 - rb);
@@ -82,6 +83,30 @@ __global__ void __launch_bounds__(256) moments_kernel(const uint8_t* __restrict_
     for (int e = 0; e < EPT; ++e) {
         int ent = threadIdx.x + e * 256;
         if (ent < NE && acc[e]) atomicAdd(out + ent, (unsigned long long)acc[e]);
+    }
+    __syncthreads();
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) moments_kernel(const uint8_t* __restrict__ img, Geo g,
+                                                      unsigned long long* __restrict__ out) {
+    moments_chunk<C>(img, g, blockIdx.x, out);
+}
+
+// Batch form: chunk items of all images, item w -> image by prefix[].
+template <int C>
+__global__ void __launch_bounds__(256) moments_batch_kernel(const BMArgs* __restrict__ args,
+                                                            unsigned long long* const* __restrict__ moms,
+                                                            const int* __restrict__ prefix, int nimg) {
+    const int total = prefix[nimg];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        int lo = 0, hi = nimg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        moments_chunk<C>(args[lo].img, args[lo].g, w - prefix[lo], moms[lo]);
     }
 }
 
@@ -289,130 +314,178 @@ __host__ __device__ void slice_basis(const unsigned long long* mom, int C, int w
     canonicalise(Ar, Vr, Vi, Out);
 }
 
-// Device form of the same solver: one warp per problem, lanes 0..7 update row/column k = lane of a
-// rotation in parallel; the matrices live in shared memory. Same rotations, same order.
-__device__ void jacobi_herm8_warp(double (*Ar)[PS], double (*Ai)[PS], double (*Vr)[PS], double (*Vi)[PS], int lane) {
+// Device form of the solver: parallel (round-robin) Jacobi. Each sweep runs 7 rounds of 4
+// rotations on disjoint index pairs (circle schedule: pairs (p[i], p[7-i]) with p a rotation of
+// 1..7 around 0), so the FP64 latency chain per sweep is 7 rotations deep instead of 28.
+// Lane i < 4 computes rotation i of a round; lane 8i + k applies it to row/column k.
+// The 2x2 block of a pair is touched only by its own rotation, so each rotation zeroes its pivot
+// exactly as the cyclic solver's would.
+// rot: [5][10] shared scratch: rows 0..3 the rotations of a round
+// (er, ei, c, s, t*r, skip, p, q, a_pp, a_qq), row 4 the convergence flag.
+__device__ void jacobi_herm8_warp(double (*Ar)[PS], double (*Ai)[PS], double (*Vr)[PS], double (*Vi)[PS],
+                                  double (*rot)[10], int lane) {
     if (lane < PS)
         for (int j = 0; j < PS; ++j) {
             Vr[lane][j] = lane == j ? 1.0 : 0.0;
             Vi[lane][j] = 0.0;
         }
     __syncwarp();
+    const int pr_i = lane >> 3, k = lane & 7;          // rotation of this lane, row/column it updates
     for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0, dia = 0.0;
-        for (int i = 0; i < PS; ++i) {
-            dia += Ar[i][i] * Ar[i][i];
-            for (int j = i + 1; j < PS; ++j) off += Ar[i][j] * Ar[i][j] + Ai[i][j] * Ai[i][j];
-        }
-        if (off <= 1e-32 * dia || off == 0.0) break;
-        for (int p = 0; p < PS - 1; ++p)
-            for (int q = p + 1; q < PS; ++q) {
-                const double xr = Ar[p][q], xi = Ai[p][q];
-                const double r = sqrt(xr * xr + xi * xi);
-                const double app = Ar[p][p], aqq = Ar[q][q];
-                __syncwarp();
-                if (r == 0.0 || r < 1e-17 * sqrt(fabs(app * aqq))) {
-                    if (lane == 0) Ar[p][q] = Ai[p][q] = Ar[q][p] = Ai[q][p] = 0.0;
-                    __syncwarp();
-                    continue;
-                }
-                const double er = xr / r, ei = xi / r;
-                const double th = (aqq - app) / (2.0 * r);
-                double t;
-                if (fabs(th) > 1e150) t = 0.5 / th;
-                else t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
-                if (lane < PS) {
-                    const int k = lane;
-                    const double pr = Ar[k][p], pi = Ai[k][p], qr = Ar[k][q], qi = Ai[k][q];
-                    const double mr = er * qr + ei * qi, mi = er * qi - ei * qr;
-                    Ar[k][p] = c * pr - sn * mr;
-                    Ai[k][p] = c * pi - sn * mi;
-                    Ar[k][q] = sn * pr + c * mr;
-                    Ai[k][q] = sn * pi + c * mi;
-                }
-                __syncwarp();
-                if (lane < PS) {
-                    const int k = lane;
-                    const double pr = Ar[p][k], pi = Ai[p][k], qr = Ar[q][k], qi = Ai[q][k];
-                    const double mr = er * qr - ei * qi, mi = er * qi + ei * qr;
-                    Ar[p][k] = c * pr - sn * mr;
-                    Ai[p][k] = c * pi - sn * mi;
-                    Ar[q][k] = sn * pr + c * mr;
-                    Ai[q][k] = sn * pi + c * mi;
-                    const double vpr = Vr[k][p], vpi = Vi[k][p], vqr = Vr[k][q], vqi = Vi[k][q];
-                    const double nr = er * vqr + ei * vqi, ni = er * vqi - ei * vqr;
-                    Vr[k][p] = c * vpr - sn * nr;
-                    Vi[k][p] = c * vpi - sn * ni;
-                    Vr[k][q] = sn * vpr + c * nr;
-                    Vi[k][q] = sn * vpi + c * ni;
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    Ar[p][p] = app - t * r;
-                    Ar[q][q] = aqq + t * r;
-                    Ai[p][p] = Ai[q][q] = 0.0;
-                    Ar[p][q] = Ai[p][q] = Ar[q][p] = Ai[q][p] = 0.0;
-                }
-                __syncwarp();
+        if (lane == 0) {
+            double off = 0.0, dia = 0.0;
+            for (int i = 0; i < PS; ++i) {
+                dia += Ar[i][i] * Ar[i][i];
+                for (int j = i + 1; j < PS; ++j) off += Ar[i][j] * Ar[i][j] + Ai[i][j] * Ai[i][j];
             }
+            rot[4][0] = (off <= 1e-32 * dia || off == 0.0) ? 1.0 : 0.0;
+        }
+        __syncwarp();
+        if (rot[4][0] != 0.0) break;
+        for (int r = 0; r < PS - 1; ++r) {
+            // pair of rotation i in round r
+            auto at = [r](int j) { return j == 0 ? 0 : 1 + ((j - 1 + r) % (PS - 1)); };
+            if (lane < 4) {
+                int p = at(lane), q = at(PS - 1 - lane);
+                if (p > q) { const int t = p; p = q; q = t; }
+                const double xr = Ar[p][q], xi = Ai[p][q];
+                const double rr = sqrt(xr * xr + xi * xi);
+                const double app = Ar[p][p], aqq = Ar[q][q];
+                double* R = rot[lane];
+                R[6] = p;
+                R[7] = q;
+                R[8] = app;
+                R[9] = aqq;
+                if (rr == 0.0 || rr < 1e-17 * sqrt(fabs(app * aqq))) {
+                    R[5] = 1.0;
+                } else {
+                    const double th = (aqq - app) / (2.0 * rr);
+                    double t;
+                    if (fabs(th) > 1e150) t = 0.5 / th;
+                    else t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                    const double c = 1.0 / sqrt(t * t + 1.0);
+                    R[0] = xr / rr;
+                    R[1] = xi / rr;
+                    R[2] = c;
+                    R[3] = t * c;
+                    R[4] = t * rr;
+                    R[5] = 0.0;
+                }
+            }
+            __syncwarp();
+            const double* R = rot[pr_i];
+            const bool skip = R[5] != 0.0;
+            const int p = (int)R[6], q = (int)R[7];
+            const double er = R[0], ei = R[1], c = R[2], sn = R[3];
+            if (!skip) {     // columns p, q: a_kp <- c a_kp - s conj(e) a_kq ; a_kq <- s a_kp + c conj(e) a_kq
+                const double pr = Ar[k][p], pi = Ai[k][p], qr = Ar[k][q], qi = Ai[k][q];
+                const double mr = er * qr + ei * qi, mi = er * qi - ei * qr;
+                Ar[k][p] = c * pr - sn * mr;
+                Ai[k][p] = c * pi - sn * mi;
+                Ar[k][q] = sn * pr + c * mr;
+                Ai[k][q] = sn * pi + c * mi;
+            }
+            __syncwarp();
+            if (!skip) {     // rows p, q: a_pk <- c a_pk - s e a_qk ; a_qk <- s a_pk + c e a_qk ; and V
+                const double pr = Ar[p][k], pi = Ai[p][k], qr = Ar[q][k], qi = Ai[q][k];
+                const double mr = er * qr - ei * qi, mi = er * qi + ei * qr;
+                Ar[p][k] = c * pr - sn * mr;
+                Ai[p][k] = c * pi - sn * mi;
+                Ar[q][k] = sn * pr + c * mr;
+                Ai[q][k] = sn * pi + c * mi;
+                const double vpr = Vr[k][p], vpi = Vi[k][p], vqr = Vr[k][q], vqi = Vi[k][q];
+                const double nr = er * vqr + ei * vqi, ni = er * vqi - ei * vqr;
+                Vr[k][p] = c * vpr - sn * nr;
+                Vi[k][p] = c * vpi - sn * ni;
+                Vr[k][q] = sn * vpr + c * nr;
+                Vi[k][q] = sn * vpi + c * ni;
+            }
+            __syncwarp();
+            if (lane < 4) {
+                // the rotated 2x2 block: diagonal a_pp - t r, a_qq + t r (a_pp, a_qq before the round), zero pivot
+                const double* Rl = rot[lane];
+                const int pl = (int)Rl[6], ql = (int)Rl[7];
+                if (Rl[5] == 0.0) {
+                    Ar[pl][pl] = Rl[8] - Rl[4];
+                    Ar[ql][ql] = Rl[9] + Rl[4];
+                    Ai[pl][pl] = Ai[ql][ql] = 0.0;
+                }
+                Ar[pl][ql] = Ai[pl][ql] = Ar[ql][pl] = Ai[ql][pl] = 0.0;
+            }
+            __syncwarp();
+        }
     }
 }
 
-// One warp per (U or V, slice f) problem, f = 0 .. C/2.
+// One warp per (U or V, slice f) problem w, f = 0 .. C/2; writes its slice of the outputs.
+__device__ __forceinline__ void basis_problem(const unsigned long long* __restrict__ mom, int C, int w,
+                                              double* __restrict__ b64, float* __restrict__ b32) {
+    __shared__ double Res[PS][PS][2];
+    __shared__ double work[4 * PS2];
+    __shared__ double rot[5][10];
+    const int nf = C / 2 + 1;
+    const int lane = threadIdx.x & 31;
+    const int which = w / nf, f = w % nf;
+    double (*Ar)[PS] = reinterpret_cast<double (*)[PS]>(work);
+    double (*Ai)[PS] = reinterpret_cast<double (*)[PS]>(work + PS2);
+    double (*Vr)[PS] = reinterpret_cast<double (*)[PS]>(work + 2 * PS2);
+    double (*Vi)[PS] = reinterpret_cast<double (*)[PS]>(work + 3 * PS2);
+    const unsigned long long* M = mom + (size_t)which * PS * PS * C * C;
+    const double s32 = 0.5 * sqrt(3.0);
+    for (int e = lane; e < PS2; e += 32) {
+        const int u = e / PS, v = e % PS;
+        double accr = 0.0, acci = 0.0;
+        for (int c = 0; c < C; ++c)
+            for (int c2 = 0; c2 < C; ++c2) {
+                const double m = (double)M[((u * PS + v) * C + c) * C + c2];
+                const int d = which == 0 ? (c - c2) : (c2 - c);
+                const int k = ((f * d) % C + C) % C;
+                double phr = 1.0, phi = 0.0;
+                if (C == 3 && k == 1) { phr = -0.5; phi = -s32; }
+                if (C == 3 && k == 2) { phr = -0.5; phi = s32; }
+                accr += m * phr;
+                acci += m * phi;
+            }
+        Ar[u][v] = accr;
+        Ai[u][v] = u == v ? 0.0 : acci;
+    }
+    __syncwarp();
+    jacobi_herm8_warp(Ar, Ai, Vr, Vi, rot, lane);
+    if (lane == 0) canonicalise(Ar, Vr, Vi, Res);
+    __syncwarp();
+    // FP64 slice f (and its conjugate slice C - f) of U or V, and the packed FP32 copy used by the filter.
+    for (int ai = lane; ai < PS2; ai += 32) {
+        const double re = Res[ai / PS][ai % PS][0], im = Res[ai / PS][ai % PS][1];
+        double* o = b64 + 2 * ((size_t)(which * C + f) * PS2 + ai);
+        o[0] = re;
+        o[1] = im;
+        if (f != 0 && C - f != f) {
+            double* oc = b64 + 2 * ((size_t)(which * C + (C - f)) * PS2 + ai);
+            oc[0] = re;
+            oc[1] = -im;
+        }
+        const int per = (C == 3) ? 3 * PS2 : PS2;
+        float* o32 = b32 + which * per;
+        if (f == 0) o32[ai] = (float)re;
+        else {
+            o32[PS2 + ai] = (float)re;
+            o32[2 * PS2 + ai] = (float)im;
+        }
+    }
+}
+
 __global__ void basis_kernel(const unsigned long long* __restrict__ mom, int C, double* __restrict__ b64,
                              float* __restrict__ b32) {
-    __shared__ double Res[4][PS][PS][2];
-    __shared__ double work[4][4 * PS2];
-    const int nf = C / 2 + 1;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w < 2 * nf) {
-        const int which = w / nf, f = w % nf;
-        double (*Ar)[PS] = reinterpret_cast<double (*)[PS]>(work[w]);
-        double (*Ai)[PS] = reinterpret_cast<double (*)[PS]>(work[w] + PS2);
-        double (*Vr)[PS] = reinterpret_cast<double (*)[PS]>(work[w] + 2 * PS2);
-        double (*Vi)[PS] = reinterpret_cast<double (*)[PS]>(work[w] + 3 * PS2);
-        const unsigned long long* M = mom + (size_t)which * PS * PS * C * C;
-        const double s32 = 0.5 * sqrt(3.0);
-        for (int e = lane; e < PS2; e += 32) {
-            const int u = e / PS, v = e % PS;
-            double accr = 0.0, acci = 0.0;
-            for (int c = 0; c < C; ++c)
-                for (int c2 = 0; c2 < C; ++c2) {
-                    const double m = (double)M[((u * PS + v) * C + c) * C + c2];
-                    const int d = which == 0 ? (c - c2) : (c2 - c);
-                    const int k = ((f * d) % C + C) % C;
-                    double phr = 1.0, phi = 0.0;
-                    if (C == 3 && k == 1) { phr = -0.5; phi = -s32; }
-                    if (C == 3 && k == 2) { phr = -0.5; phi = s32; }
-                    accr += m * phr;
-                    acci += m * phi;
-                }
-            Ar[u][v] = accr;
-            Ai[u][v] = u == v ? 0.0 : acci;
-        }
-        __syncwarp();
-        jacobi_herm8_warp(Ar, Ai, Vr, Vi, lane);
-        if (lane == 0) canonicalise(Ar, Vr, Vi, Res[w]);
-    }
-    __syncthreads();
-    // Write FP64 slices (conjugate slices C - f for f > C/2) and the packed FP32 copies.
-    for (int e = threadIdx.x; e < 2 * C * PS2; e += blockDim.x) {
-        const int which = e / (C * PS2), rem = e - which * C * PS2;
-        const int f = rem / PS2, ai = rem - f * PS2;
-        const int fs = f <= C / 2 ? f : C - f;
-        const double* v = Res[which * nf + fs][ai / PS][ai % PS];
-        b64[2 * e] = v[0];
-        b64[2 * e + 1] = f != fs ? -v[1] : v[1];
-    }
-    // packed FP32: per which: slice0 re [64]; for C = 3 also slice1 re [64], slice1 im [64]
-    const int per = (C == 3) ? 3 * PS2 : PS2;
-    for (int e = threadIdx.x; e < 2 * per; e += blockDim.x) {
-        const int which = e / per, rem = e - which * per;
-        const int part = rem / PS2, ai = rem - part * PS2;
-        const double* v = Res[which * nf + (part == 0 ? 0 : 1)][ai / PS][ai % PS];
-        b32[e] = (float)(part == 2 ? v[1] : v[0]);
-    }
+    basis_problem(mom, C, blockIdx.x, b64, b32);
+}
+
+// Batch form: block b -> image b / (2 (C/2 + 1)), problem b % (2 (C/2 + 1)).
+__global__ void basis_batch_kernel(const FilterArgs* __restrict__ fargs, unsigned long long* const* __restrict__ moms,
+                                   int C) {
+    const int np = 2 * (C / 2 + 1);
+    const int i = blockIdx.x / np;
+    const FilterArgs& a = fargs[i];
+    basis_problem(moms[i], C, blockIdx.x % np, const_cast<double*>(a.basis64), const_cast<float*>(a.basis32));
 }
 
 __global__ void quantize_kernel(const float* __restrict__ x, int64_t n, uint8_t* __restrict__ q) {
@@ -511,6 +584,21 @@ cudaError_t launch_moments(const uint8_t* img, const Geo& g, unsigned long long*
     return cudaGetLastError();
 }
 
+int moments_chunks(const Geo& g) { return (g.ngroups() + MOM_CHUNK - 1) / MOM_CHUNK; }
+
+cudaError_t launch_moments_batch(int C, const BMArgs* d_args, unsigned long long* const* d_moms, const int* d_prefix,
+                                 int nimg, int grid, cudaStream_t s) {
+    if (C == 3) moments_batch_kernel<3><<<grid, 256, 0, s>>>(d_args, d_moms, d_prefix, nimg);
+    else moments_batch_kernel<1><<<grid, 256, 0, s>>>(d_args, d_moms, d_prefix, nimg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_basis_batch(int C, const FilterArgs* d_fargs, unsigned long long* const* d_moms, int nimg,
+                               cudaStream_t s) {
+    basis_batch_kernel<<<nimg * 2 * (C / 2 + 1), 32, 0, s>>>(d_fargs, d_moms, C);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long long* d_M, unsigned long long* d_s,
                                cudaStream_t s) {
     const int d = PS2 * g.C;
@@ -525,7 +613,7 @@ cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long l
 }
 
 cudaError_t launch_basis(const unsigned long long* d_mom, int C, double* d_basis64, float* d_basis32, cudaStream_t s) {
-    basis_kernel<<<1, 128, 0, s>>>(d_mom, C, d_basis64, d_basis32);
+    basis_kernel<<<2 * (C / 2 + 1), 32, 0, s>>>(d_mom, C, d_basis64, d_basis32);
     return cudaGetLastError();
 }
 
