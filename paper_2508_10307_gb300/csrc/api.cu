@@ -201,8 +201,11 @@ struct FilterTiling {
 };
 
 FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forced) {
+    // The largest tile whose shared memory lets two CTAs share an SM (228 KB, 1 KB reserved per CTA)
+    // and that still gives two tiles per SM; failing that, the largest that fits at all.
     const int cands[] = {8, 6, 5, 4, 3, 2, 1};
-    FilterTiling best{};
+    FilterTiling fit2{}, fit1{};
+    bool have2 = false, have1 = false;
     for (int TR : cands) {
         if (forced > 0 && TR != forced) continue;
         FilterTiling t;
@@ -218,13 +221,15 @@ FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forc
         fa.img_is_float = in_bytes == 4;
         fa.mode = mode;
         const size_t smem = filter_smem_bytes(fa);
-        best = t;
-        if (smem > 200 * 1024) continue;
         if (forced > 0) return t;
-        // enough tiles to fill the GPU (two per SM) unless the image is small
-        if ((int64_t)t.ntx * t.nty >= 2 * 152 || TR == 1) return t;
+        if (smem <= 112 * 1024) {
+            if (!have2) fit2 = t, have2 = true;
+            if ((int64_t)t.ntx * t.nty >= 2 * 152) return t;
+        } else if (smem <= 200 * 1024 && !have1) {
+            fit1 = t, have1 = true;
+        }
     }
-    return best;
+    return have2 ? fit2 : fit1;
 }
 
 void choose_bm_tiles(const Geo& g, int rstep, int& TRy, int& TRx) {

@@ -124,6 +124,7 @@ cudaError_t launch_filter_batch_t(const FilterArgs* d_args, const int* d_prefix,
                                   int* d_counter, cudaStream_t s) {
     auto fn = filter_batch_kernel<K, C>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     fn<<<grid, FT_THREADS, smem, s>>>(d_args, d_prefix, nimg, d_counter);
     return cudaGetLastError();
@@ -139,6 +140,9 @@ __global__ void div_kernel(const float* __restrict__ gout, const float* __restri
 
 size_t filter_smem_bytes(const FilterArgs& a) {
     const int inb = a.img_is_float ? 4 : 1;
+    if (a.mode == FM_FORWARD)
+        return a.g.C == 3 ? f_layout_fwd<32, 3>(a.FHmax, a.FWmax, inb).total
+                          : f_layout_fwd<32, 1>(a.FHmax, a.FWmax, inb).total;
     if (a.g.C == 3) return f_layout<32, 3>(a.FHmax, a.FWmax, inb, a.mode).total;
     return f_layout<32, 1>(a.FHmax, a.FWmax, inb, a.mode).total;
 }

@@ -67,6 +67,26 @@ __host__ __device__ inline FLayout f_layout(int FH, int FW, int in_bytes, int mo
     return L;
 }
 
+// Shared-memory layout of the pipelined forward filter: two group buffers, two position and
+// counter sets (group q+1 is projected while group q is aggregated), no band bitmaps.
+template <int K, int C>
+__host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes) {
+    using G = FCfg<C>;
+    FLayout L;
+    int o = 0;
+    L.off_bas = o; o += 512 * 4;
+    L.off_gb = o; o += 2 * K * G::GS * 4;
+    L.off_pos = o; o += 2 * 64 * 4;
+    L.off_band = o;
+    L.off_rkeep = o;
+    L.off_misc = o; o += 2 * 16 * 4;
+    L.off_acc = o; o += FH * FW * G::ACC * 4;
+    L.off_img = o; o += (FH * FW * C * in_bytes + 15) / 16 * 16;
+    L.off_r = o;
+    L.total = o;
+    return L;
+}
+
 // In-register Haar analysis along the group mode: o = H_K a (Eq. (H_2N) applied recursively).
 template <int K>
 __device__ __forceinline__ void haar_fwd(float (&a)[K], float (&o)[K]) {
@@ -404,9 +424,204 @@ __device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int 
     }
 }
 
-// One tile of references (tile index t = ty * ntx + tx); smem: f_layout(...).total bytes.
+// Forward filter of one tile, software-pipelined over its groups with three CTA barriers per
+// group: [C(q)] | [D, E(q); positions of q+1] | [F(q) aggregation and A, B(q+1) projections].
+// Guard-band entries are re-decided in FP64 by the warp that owns the fibre (no CTA barrier).
+template <int K, int C, typename Tin>
+__device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int tile, unsigned char* smem) {
+    using G = FCfg<C>;
+    constexpr int NF = G::PATCH;
+    constexpr int NBW = K * NF / 32;
+    constexpr unsigned kAB = (8 * K >= 32) ? 0xffffffffu : ((1u << (8 * K)) - 1u);
+    const Geo& g = a.g;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+    int FY0, FY1, FX0, FX1;
+    tile_span(ty, a.TR, g.nry, g.s, g.H, g.npy, g.wny, g.win, FY0, FY1);
+    tile_span(tx, a.TR, g.nrx, g.s, g.W, g.npx, g.wnx, g.win, FX0, FX1);
+    const int FH = FY1 - FY0, FW = FX1 - FX0;
+    const FLayout L = f_layout_fwd<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin));
+    float* bas = reinterpret_cast<float*>(smem + L.off_bas);
+    float* gbb = reinterpret_cast<float*>(smem + L.off_gb);
+    int* posb = reinterpret_cast<int*>(smem + L.off_pos);
+    int* miscb = reinterpret_cast<int*>(smem + L.off_misc);
+    float* acc = reinterpret_cast<float*>(smem + L.off_acc);
+    Tin* img_s = reinterpret_cast<Tin*>(smem + L.off_img);
+
+    for (int t = tid; t < G::NBAS; t += FT_THREADS) bas[t] = a.basis32[t];
+    {
+        const Tin* img = reinterpret_cast<const Tin*>(a.img);
+        const int rowb = FW * C;
+        for (int t = tid; t < FH * rowb; t += FT_THREADS) {
+            const int r = t / rowb, cb = t - r * rowb;
+            img_s[t] = img[((size_t)(FY0 + r) * g.W + FX0) * C + cb];
+        }
+    }
+    for (int t = tid; t < FH * FW * G::ACC; t += FT_THREADS) acc[t] = 0.f;
+
+    const int iy0 = ty * a.TR, ix0 = tx * a.TR;
+    const int th = min(a.TR, g.nry - iy0), tw = min(a.TR, g.nrx - ix0);
+    const int ngr = th * tw;
+    auto group_of = [&](int q) { return (iy0 + q / tw) * g.nrx + ix0 + q % tw; };
+    // Positions come from the grouping of this geometry and lie in the footprint; a caller-given
+    // index outside it is clamped so that no access leaves the staged region.
+    auto load_pos = [&](int q, int* pos) {
+        if (tid < K) {
+            const int v = a.idx[(size_t)group_of(q) * K + tid];
+            const int y = v / g.W, x = v - y * g.W;
+            pos[2 * tid] = min(max(y - FY0, 0), FH - PS);
+            pos[2 * tid + 1] = min(max(x - FX0, 0), FW - PS);
+        }
+    };
+    // A, B of group q into buffer gbq; ||G||_F^2 into misc[5] (uint8, exact) or misc[2] (float)
+    auto project = [&](float* gbq, const int* pos, int* misc) {
+        if (tid < 8 * K) {
+            const float nrm = stage_a<K, C, Tin>(img_s, FW, pos, bas, gbq, tid >> 3, tid & 7);
+            if constexpr (sizeof(Tin) == 1) {
+                const int wsum = __reduce_add_sync(kAB, (int)nrm);
+                if (lane == 0) atomicAdd(&misc[5], wsum);
+            } else {
+                float v = nrm;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kAB, v, off);
+                if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[2]), v);
+            }
+            __syncwarp(kAB);
+            stage_b<C>(bas, gbq, tid >> 3, tid & 7);
+        }
+    };
+
+    load_pos(0, posb);
+    if (tid < 32) miscb[tid] = 0;
+    __syncthreads();
+    project(gbb, posb, miscb);
+    __syncthreads();
+
+    for (int q = 0; q < ngr; ++q) {
+        const int buf = q & 1;
+        const int grp = group_of(q);
+        float* gbq = gbb + buf * K * G::GS;
+        const int* pos = posb + buf * 64;
+        int* misc = miscb + buf * 16;
+
+        // ---- C: Haar analysis, threshold (FP64 inside the guard band), synthesis
+        if (tid < NF) {
+            const int foff = (tid / G::RWF) * G::ROW + (tid % G::RWF);
+            const float nrm2 = sizeof(Tin) == 1 ? (float)misc[5] : __int_as_float(misc[2]);
+            const float delta = a.band_rel * sqrtf(nrm2) + a.band_abs;
+            float fib[K], co[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) fib[k] = gbq[k * G::GS + foff];
+            haar_fwd<K>(fib, co);
+            if (a.coef_out) {
+                float* cdst = a.coef_out + (size_t)grp * K * NF;
+#pragma unroll
+                for (int m = 0; m < K; ++m) cdst[m * NF + tid] = co[m];
+            }
+            uint32_t keepb = 0, bandb = 0;
+#pragma unroll
+            for (int m = 0; m < K; ++m) {
+                const float d = fabsf(co[m]) - a.tau32;
+                if (fabsf(d) <= delta) bandb |= 1u << m;
+                else if (d >= 0.f) keepb |= 1u << m;
+            }
+            unsigned anyb = __ballot_sync(0xffffffffu, bandb != 0u);
+            while (anyb) {
+                const int l = __ffs(anyb) - 1;
+                anyb &= anyb - 1;
+                uint32_t bb = __shfl_sync(0xffffffffu, bandb, l);
+                while (bb) {
+                    const int m = __ffs(bb) - 1;
+                    bb &= bb - 1;
+                    const bool keep = refine_keep<K, C, Tin>(m, warp * 32 + l, img_s, FW, pos, a.basis64, a.tau64, lane);
+                    if (lane == l && keep) keepb |= 1u << m;
+                }
+            }
+            if (a.mask_out) {
+                uint32_t* mo = a.mask_out + (size_t)grp * NBW;
+#pragma unroll
+                for (int m = 0; m < K; ++m) {
+                    const uint32_t w = __ballot_sync(0xffffffffu, (keepb >> m) & 1u);
+                    if (lane == 0) mo[m * (NF / 32) + warp] = w;
+                }
+            }
+            {
+                const int wk = __reduce_add_sync(0xffffffffu, __popc(keepb));
+                if (lane == 0) atomicAdd(&misc[1], wk);
+            }
+#pragma unroll
+            for (int m = 0; m < K; ++m)
+                if (!((keepb >> m) & 1u)) co[m] = 0.f;
+            float rec[K];
+            haar_inv<K>(co, rec);
+#pragma unroll
+            for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = rec[k];
+        }
+        __syncthreads();
+        // ---- D, E: inverse projection; positions and counters of the next group
+        if (tid < 8 * K) {
+            stage_d<C>(bas, gbq, tid >> 3, tid & 7);
+            __syncwarp(kAB);
+            stage_e<C>(bas, gbq, tid >> 3, tid & 7);
+        }
+        if (q + 1 < ngr) {
+            load_pos(q + 1, posb + (buf ^ 1) * 64);
+            if (tid < 16) miscb[(buf ^ 1) * 16 + tid] = 0;
+        }
+        __syncthreads();
+        // ---- F(q): aggregation (warp `warp` owns footprint rows r with r % 8 == warp) ...
+        float wg = 1.f;
+        if (a.w_in) wg = a.w_in[grp];
+        else if (a.agg_mode == 1) wg = 1.f / (float)max(1, misc[1]);
+        if (tid == 0 && a.weights_out) a.weights_out[grp] = wg;
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+            const int py = pos[2 * k], px = pos[2 * k + 1];
+            const int i = (warp - py) & 7;
+            float* ap = acc + ((py + i) * FW + px) * G::ACC;
+            if constexpr (C == 3) {
+                if (lane < 24) {
+                    const int j = lane / 3, c = lane - 3 * (lane / 3);
+                    ap[j * 4 + c] += wg * gbq[k * G::GS + i * G::ROW + lane];
+                } else {
+                    ap[(lane - 24) * 4 + 3] += wg;
+                }
+            } else {
+                if (lane < 8) ap[lane * 2] += wg * gbq[k * G::GS + i * G::ROW + lane];
+                else if (lane < 16) ap[(lane - 8) * 2 + 1] += wg;
+            }
+        }
+        // ... overlapped with A, B(q+1) into the other buffer
+        if (q + 1 < ngr) project(gbb + (buf ^ 1) * K * G::GS, posb + (buf ^ 1) * 64, miscb + (buf ^ 1) * 16);
+        __syncthreads();
+    }
+    // Write the tile partial.
+    float* dst = a.partials + (size_t)tile * a.FHmax * a.FWmax * G::ACC;
+    if constexpr (C == 3) {
+        const float4* s4 = reinterpret_cast<const float4*>(acc);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int t = tid; t < FH * FW; t += FT_THREADS) {
+            const int r = t / FW, c = t - r * FW;
+            d4[r * a.FWmax + c] = s4[t];
+        }
+    } else {
+        const float2* s2 = reinterpret_cast<const float2*>(acc);
+        float2* d2 = reinterpret_cast<float2*>(dst);
+        for (int t = tid; t < FH * FW; t += FT_THREADS) {
+            const int r = t / FW, c = t - r * FW;
+            d2[r * a.FWmax + c] = s2[t];
+        }
+    }
+}
+
+// One tile of references (tile index t = ty * ntx + tx); smem: f_layout(...).total bytes
+// (f_layout_fwd for the forward mode).
 template <int K, int C, typename Tin, int MODE>
 __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile, unsigned char* smem) {
+    if constexpr (MODE == FM_FORWARD) {
+        filter_tile_fwd<K, C, Tin>(a, tile, smem);
+        return;
+    }
     using G = FCfg<C>;
     constexpr int NF = G::PATCH;                 // fibres
     constexpr int NBW = K * NF / 32;             // bitmap words per group
@@ -702,9 +917,11 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_batch_kernel(const Filte
 
 template <int K, int C, typename Tin, int MODE>
 cudaError_t launch_filter_t(const FilterArgs& a, cudaStream_t s) {
-    const FLayout L = f_layout<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), MODE);
+    const FLayout L = MODE == FM_FORWARD ? f_layout_fwd<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin))
+                                         : f_layout<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), MODE);
     auto fn = filter_kernel<K, C, Tin, MODE>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     fn<<<a.ntx * a.nty, FT_THREADS, L.total, s>>>(a);
     return cudaGetLastError();
