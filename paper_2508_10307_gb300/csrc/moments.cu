@@ -132,17 +132,21 @@ __global__ void __launch_bounds__(256) full_moment_kernel(const uint8_t* __restr
     for (int rb = r0; rb < r1; rb += FM_BATCH) {
         const int nb = min(FM_BATCH, r1 - rb);
         __syncthreads();
-        for (int t = threadIdx.x; t < FM_BATCH * d; t += 256) {
-            const int j = t / d, u = t - j * d;
-            uint8_t v = 0;
+        // (reference j, patch row i): the row's 8*C bytes are contiguous in the image and land on
+        // entries u = i*8*C + b of the packed matrix
+        const int rowb = PS * g.C;
+        for (int t = threadIdx.x; t < FM_BATCH * PS; t += 256) {
+            const int j = t >> 3, i = t & 7;
+            uint8_t* dst = reinterpret_cast<uint8_t*>(&pk[i * rowb][0]) + (j >> 2) * 4 + (j & 3);
             if (j < nb) {
-                const int pix = u / g.C, c = u - pix * g.C;
                 const int r = rb + j;
                 const int iy = r / g.nrx, ix = r - iy * g.nrx;
                 const int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
-                v = img[((size_t)(ry + pix / PS) * g.W + rx + pix % PS) * g.C + c];
+                const uint8_t* src = img + ((size_t)(ry + i) * g.W + rx) * g.C;
+                for (int b = 0; b < rowb; ++b) dst[b * FM_WPAD * 4] = src[b];
+            } else {
+                for (int b = 0; b < rowb; ++b) dst[b * FM_WPAD * 4] = 0;
             }
-            reinterpret_cast<uint8_t*>(&pk[u][j >> 2])[j & 3] = v;
         }
         __syncthreads();
         const int nw = (nb + 3) >> 2;
