@@ -338,6 +338,8 @@ def run_gpu(args):
     clocks = sampler.stop()
     prof = _lib.profile_collect()
     _lib.profile_enable(False)
+    host_steps = {k: v for k, v in prof.items() if k.endswith("_host")}     # wall-clock host steps, not launches
+    prof = {k: v for k, v in prof.items() if k not in host_steps}
     dev_ms_max = max_over_ranks(dev_ms)
     value = whole_job_value(world, args.steps, wl.mp_per_step, dev_ms_max)
 
@@ -399,6 +401,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "kernels_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+            "host_ms": {k: {"calls": v[0], "ms": v[1]} for k, v in host_steps.items()},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "psnr_db": psnr_gpu}
     if compare is not None:
         line["compare"] = compare

@@ -171,7 +171,9 @@ const char* htsvd_status_string(htsvd_status s);
  * htsvd_profile_collect waits for the recorded events and writes, for up to max_kernels
  * kernel names, the name (NUL-terminated, name_len bytes per entry, HOST), the number of
  * launches and their total device time in ms (HOST arrays); it then clears the record and
- * returns the number of entries written, or -1 if an event could not be read. */
+ * returns the number of entries written, or -1 if an event could not be read. The host part
+ * of the noise-level estimate (the covariance eigenvalues) is recorded as "sigma_host" with
+ * its wall-clock time. */
 htsvd_status htsvd_profile_enable(int32_t enable);
 int32_t htsvd_profile_collect(int32_t max_kernels, char* names, int32_t name_len, int64_t* launches,
                               double* total_ms);

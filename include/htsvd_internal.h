@@ -28,6 +28,15 @@ int htsvd_internal_moments(const uint8_t* d_img, int H, int W, int C, int stride
  * Returns 0 on success, 1 on a CUDA error. */
 int htsvd_internal_basis(const unsigned long long* d_mom, int C, double* d_b64, float* d_b32);
 
+/* HOST noise level of Sec. III-D from the integer patch moments of the reference patches:
+ * M (d x d uint64, sum over references of x x^T) and S (d uint64, sum of x), n references,
+ * d = 64 C (patch entries in (row, column, channel) order). The covariance M/n - (S/n)(S/n)^T
+ * is reduced to tridiagonal form and its eigenvalues found by shifted QR (FP64); if lam is not
+ * NULL it receives the d eigenvalues in ascending order (host). Returns sigma, or -1 on a bad
+ * argument or if the iteration did not converge. */
+double htsvd_internal_sigma_from_moments(const unsigned long long* M, const unsigned long long* S, int d, int64_t n,
+                                         double* lam);
+
 #ifdef __cplusplus
 }
 #endif

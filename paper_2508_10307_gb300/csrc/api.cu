@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <chrono>
 #include <mutex>
 #include <string>
 #include <new>
@@ -156,6 +157,7 @@ htsvd_status ws_host(Workspace* w, size_t bytes, void** out) {
 struct ProfRec {
     const char* name;
     cudaEvent_t a, b;
+    double host_ms;       // >= 0: a host step timed with the wall clock (no events)
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
@@ -163,7 +165,7 @@ std::vector<ProfRec> g_prof;
 
 // Brackets the launches made in its scope with events on `s` while profiling is enabled.
 struct ProfScope {
-    ProfRec r{nullptr, nullptr, nullptr};
+    ProfRec r{nullptr, nullptr, nullptr, -1.0};
     cudaStream_t s;
     ProfScope(const char* name, cudaStream_t st) : s(st) {
         if (!g_prof_on) return;
@@ -180,6 +182,21 @@ struct ProfScope {
         cudaEventRecord(r.b, s);
         std::lock_guard<std::mutex> lk(g_prof_mu);
         g_prof.push_back(r);
+    }
+};
+
+// Wall-clock timing of a host step, recorded under `name` while profiling is enabled.
+struct HostProfScope {
+    const char* name;
+    std::chrono::steady_clock::time_point t0;
+    explicit HostProfScope(const char* n) : name(g_prof_on ? n : nullptr) {
+        if (name) t0 = std::chrono::steady_clock::now();
+    }
+    ~HostProfScope() {
+        if (!name) return;
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof.push_back(ProfRec{name, nullptr, nullptr, ms});
     }
 };
 
@@ -258,16 +275,16 @@ htsvd_status run_block_match(const uint8_t* q, const Geo& g, const Resolved& r, 
 }
 
 // Noise level from the covariance eigenvalues (host FP64). M, S: uint64 moments on the host.
-double sigma_from_moments(const unsigned long long* M, const unsigned long long* S, int d, int64_t n) {
+double sigma_from_moments(const unsigned long long* M, const unsigned long long* S, int d, int64_t n,
+                          double* lam_out = nullptr) {
     std::vector<double> A((size_t)d * d), lam(d);
-    const double inv = 1.0 / (double)n;
     std::vector<double> mu(d);
     for (int u = 0; u < d; ++u) mu[u] = (double)S[u] / (double)n;
-    for (int u = 0; u < d; ++u)
-        for (int v = 0; v < d; ++v) A[(size_t)u * d + v] = (double)M[(size_t)u * d + v] / (double)n - mu[u] * mu[v];
-    (void)inv;
+    for (int u = 0; u < d; ++u)          // lower triangle: all the eigensolver reads
+        for (int v = 0; v <= u; ++v) A[(size_t)u * d + v] = (double)M[(size_t)u * d + v] / (double)n - mu[u] * mu[v];
     if (!symmetric_eigenvalues(A.data(), d, lam.data())) return -1.0;
     std::sort(lam.begin(), lam.end());
+    if (lam_out) std::copy(lam.begin(), lam.end(), lam_out);
     int rstar = 1;
     double sum = 0.0;
     std::vector<double> pref(d + 1, 0.0);
@@ -324,7 +341,11 @@ htsvd_status launch_sigma_inputs(Workspace* w, const uint8_t* q, const Geo& g, c
 htsvd_status finish_sigma(const void* hbuf, const Geo& g, const Resolved& r, double* sigma) {
     const int d = PS2 * g.C;
     const unsigned long long* h = (const unsigned long long*)hbuf;
-    double sg = sigma_from_moments(h, h + (size_t)d * d, d, (int64_t)g.ngroups());
+    double sg;
+    {
+        HostProfScope hp_("sigma_host");
+        sg = sigma_from_moments(h, h + (size_t)d * d, d, (int64_t)g.ngroups());
+    }
     if (sg < 0) return HTSVD_ERR_CUDA;
     if (r.adapt) {
         const int ny8 = (g.nry + 7) / 8, nx8 = (g.nrx + 7) / 8;
@@ -439,6 +460,12 @@ htsvd_status denoise_impl(const void* d_in, int is_float, int H, int W, int C, d
 // ============================================================================= C ABI
 
 extern "C" {
+
+double htsvd_internal_sigma_from_moments(const unsigned long long* M, const unsigned long long* S, int d, int64_t n,
+                                         double* lam) {
+    if (!M || !S || d < 1 || n < 1) return -1.0;
+    return sigma_from_moments(M, S, d, n, lam);
+}
 
 htsvd_status htsvd_denoise(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, double sigma,
                            const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t stream) {
@@ -575,12 +602,16 @@ int32_t htsvd_profile_collect(int32_t max_kernels, char* names, int32_t name_len
     int32_t status = 0;
     for (const ProfRec& r : recs) {
         float ms = 0.f;
-        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
-            cudaGetLastError();
-            status = -1;
+        if (r.host_ms >= 0) {
+            ms = (float)r.host_ms;
+        } else {
+            if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+                cudaGetLastError();
+                status = -1;
+            }
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
         }
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
         size_t i = 0;
         while (i < nm.size() && nm[i] != r.name) ++i;
         if (i == nm.size()) {

@@ -1,7 +1,8 @@
 // Host FP64 eigenvalues of a small dense symmetric matrix (the d x d patch covariance of
 // the noise-level estimate, d = 64 C). Householder reduction to tridiagonal form, then
-// implicit symmetric QR steps with a Wilkinson shift and deflation (Golub & Van Loan,
-// "Matrix Computations", Sec. 8.3). Eigenvalues only.
+// implicit-shift QR with a Wilkinson shift and deflation (Golub & Van Loan, "Matrix
+// Computations", Secs. 8.3.1 and 8.3.5), carried out on the squared off-diagonal entries so
+// that no square root is taken inside the chase. Eigenvalues only.
 #include <cmath>
 #include <vector>
 
@@ -12,92 +13,140 @@ namespace {
 // A (n x n, row-major, symmetric; only the lower triangle i >= j is read and overwritten)
 // -> diagonal d[n], off-diagonal e[n-1]. Step k reflects the trailing block B = A[k+1:, k+1:]
 // with H = I - beta v v^T (H x = alpha e_1 for x = A[k+1:, k]): p = beta B v,
-// w = p - (beta/2)(v^T p) v, B <- B - v w^T - w v^T.
+// w = p - (beta/2)(v^T p) v, B <- B - v w^T - w v^T. The rank-2 update of step k is deferred
+// and applied to each row of the trailing triangle in the same pass that forms p of step k+1,
+// so the triangle is read and written once per step.
 void tridiagonalize(double* A, int n, double* d, double* e) {
-    std::vector<double> v(n), p(n), w(n);
-    for (int k = 0; k < n - 2; ++k) {
-        const int m = n - k - 1;                  // size of the trailing block
-        double* x = &v[0];
+    std::vector<double> vb(n, 0.0), wb(n, 0.0), v(n), p(n);     // (vb, wb): deferred update, absolute indices
+    bool pending = false;
+    for (int k = 0; k < n; ++k) {
+        if (pending) {                                            // column k, rows k..n-1
+            const double vk = vb[k], wk = wb[k];
+            for (int i = k; i < n; ++i) A[(size_t)i * n + k] -= vb[i] * wk + wb[i] * vk;
+        }
+        d[k] = A[(size_t)k * n + k];
+        if (k >= n - 2) continue;                                 // the last 2x2 block needs no reflector
+        const int m = n - k - 1;
         double xn2 = 0.0;
         for (int i = 0; i < m; ++i) {
-            x[i] = A[(size_t)(k + 1 + i) * n + k];
-            xn2 += x[i] * x[i];
+            v[i] = A[(size_t)(k + 1 + i) * n + k];
+            xn2 += v[i] * v[i];
         }
-        if (xn2 == 0.0) {
-            e[k] = 0.0;
-            continue;
+        double alpha = 0.0, beta = 0.0;
+        if (xn2 != 0.0) {
+            alpha = std::sqrt(xn2);
+            if (v[0] > 0) alpha = -alpha;                         // avoids cancellation in v_0
+            v[0] -= alpha;
+            double vtv = 0.0;
+            for (int i = 0; i < m; ++i) vtv += v[i] * v[i];
+            beta = 2.0 / vtv;
         }
-        double alpha = std::sqrt(xn2);
-        if (x[0] > 0) alpha = -alpha;             // avoids cancellation in v_0
-        x[0] -= alpha;
-        double vtv = 0.0;
-        for (int i = 0; i < m; ++i) vtv += x[i] * x[i];
-        const double beta = 2.0 / vtv;
-        // p = B v from the lower triangle: row i contributes its dot product to p_i and,
-        // through symmetry, L_ij v_i to p_j (j < i)
+        e[k] = alpha;
+        // one pass over the trailing lower triangle: deferred update of row i, then its part of
+        // p = B v (row i gives its dot product to p_i and, by symmetry, L_ij v_i to p_j, j < i)
+        const double* vo = vb.data() + k + 1;
+        const double* wo = wb.data() + k + 1;
         for (int i = 0; i < m; ++i) p[i] = 0.0;
         for (int i = 0; i < m; ++i) {
-            const double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
-            const double vi = x[i];
-            double s = 0.0;
-            for (int j = 0; j < i; ++j) {
-                s += row[j] * x[j];
-                p[j] += row[j] * vi;
+            double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+            const double vi = v[i], voi = vo[i], woi = wo[i];
+            double s0 = 0.0, s1 = 0.0;                            // two partial sums: two dependency chains
+            int j = 0;
+            if (pending) {
+                for (; j + 2 <= i; j += 2) {
+                    const double r0 = row[j] - (voi * wo[j] + woi * vo[j]);
+                    const double r1 = row[j + 1] - (voi * wo[j + 1] + woi * vo[j + 1]);
+                    row[j] = r0;
+                    row[j + 1] = r1;
+                    s0 += r0 * v[j];
+                    s1 += r1 * v[j + 1];
+                    p[j] += r0 * vi;
+                    p[j + 1] += r1 * vi;
+                }
+                for (; j < i; ++j) {
+                    const double r0 = row[j] - (voi * wo[j] + woi * vo[j]);
+                    row[j] = r0;
+                    s0 += r0 * v[j];
+                    p[j] += r0 * vi;
+                }
+                row[i] -= voi * wo[i] + woi * vo[i];
+            } else {
+                for (; j + 2 <= i; j += 2) {
+                    s0 += row[j] * v[j];
+                    s1 += row[j + 1] * v[j + 1];
+                    p[j] += row[j] * vi;
+                    p[j + 1] += row[j + 1] * vi;
+                }
+                for (; j < i; ++j) {
+                    s0 += row[j] * v[j];
+                    p[j] += row[j] * vi;
+                }
             }
-            p[i] += s + row[i] * vi;
+            p[i] += (s0 + s1) + row[i] * vi;
         }
         double vp = 0.0;
         for (int i = 0; i < m; ++i) {
             p[i] *= beta;
-            vp += x[i] * p[i];
+            vp += v[i] * p[i];
         }
         const double Kc = 0.5 * beta * vp;
-        for (int i = 0; i < m; ++i) w[i] = p[i] - Kc * x[i];
+        vb[k] = wb[k] = 0.0;
         for (int i = 0; i < m; ++i) {
-            double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
-            const double xi = x[i], wi = w[i];
-            for (int j = 0; j <= i; ++j) row[j] -= xi * w[j] + wi * x[j];
+            vb[k + 1 + i] = v[i];
+            wb[k + 1 + i] = p[i] - Kc * v[i];
         }
-        e[k] = alpha;
+        pending = beta != 0.0;
     }
-    for (int i = 0; i < n; ++i) d[i] = A[(size_t)i * n + i];
     if (n >= 2) e[n - 2] = A[(size_t)(n - 1) * n + (n - 2)];
 }
 
-// Eigenvalues of the symmetric tridiagonal (a, b) in place in a.
-bool tridiagonal_eigenvalues(double* a, double* b, int n) {
-    const double eps = 2.220446049250313e-16;
+// Eigenvalues of the symmetric tridiagonal matrix (a, e2) in place in a, where e2 holds the
+// SQUARES of the off-diagonal entries. One shifted QR step T - mu I = QR, T' = RQ + mu I with
+// Givens rotations (c_k, s_k), written with gamma_k = c_{k-1} pi_k (pi_k: the k-th pivot of R
+// before rotation k, c_0 = 1):
+//   r_k^2 = pi_k^2 + b_k^2,  c_k^2 = pi_k^2 / r_k^2,  s_k^2 = b_k^2 / r_k^2,
+//   gamma_{k+1} = c_k^2 (a_{k+1} - mu) - s_k^2 gamma_k,   a'_k = gamma_k + a_{k+1} - gamma_{k+1},
+//   b'_{k-1}^2 = s_{k-1}^2 r_k^2,   pi_{k+1}^2 = gamma_{k+1}^2 / c_k^2 (= c_{k-1}^2 b_k^2 if c_k = 0),
+// and at the end of the segment a'_hi = mu + gamma_hi, b'_{hi-1}^2 = s_{hi-1}^2 pi_hi^2.
+bool tridiagonal_eigenvalues(double* a, double* e2, int n) {
+    const double eps = 2.220446049250313e-16, eps2 = eps * eps;
+    auto negligible = [&](int k) {
+        const double t = std::fabs(a[k]) + std::fabs(a[k + 1]);
+        return e2[k] <= eps2 * t * t;
+    };
     int iter = 0;
     int hi = n - 1;
     while (hi > 0) {
-        if (std::fabs(b[hi - 1]) <= eps * (std::fabs(a[hi - 1]) + std::fabs(a[hi]))) {
-            b[hi - 1] = 0.0;
+        if (negligible(hi - 1)) {
+            e2[hi - 1] = 0.0;
             --hi;
             continue;
         }
         int lo = hi - 1;
-        while (lo > 0 && std::fabs(b[lo - 1]) > eps * (std::fabs(a[lo - 1]) + std::fabs(a[lo]))) --lo;
+        while (lo > 0 && !negligible(lo - 1)) --lo;
         if (++iter > 60 * n) return false;
-        // Wilkinson shift from the trailing 2x2 block
+        // Wilkinson shift: the eigenvalue of the trailing 2x2 block nearer to a_hi
         const double dd = 0.5 * (a[hi - 1] - a[hi]);
-        const double bb = b[hi - 1];
-        const double den = dd + (dd >= 0 ? 1.0 : -1.0) * std::sqrt(dd * dd + bb * bb);
-        const double mu = a[hi] - (den != 0.0 ? bb * bb / den : 0.0);
-        double x = a[lo] - mu, z = b[lo];
+        const double bb = e2[hi - 1];
+        const double den = dd + (dd >= 0 ? 1.0 : -1.0) * std::sqrt(dd * dd + bb);
+        const double mu = a[hi] - (den != 0.0 ? bb / den : 0.0);
+        double gam = a[lo] - mu, pi2 = gam * gam, c2p = 1.0, s2p = 0.0;
         for (int k = lo; k < hi; ++k) {
-            const double r = std::sqrt(x * x + z * z);      // entries are far from overflow (covariances of bytes)
-            const double c = r == 0.0 ? 1.0 : x / r, s = r == 0.0 ? 0.0 : z / r;
-            if (k > lo) b[k - 1] = r;
-            const double ak = a[k], ak1 = a[k + 1], bk = b[k];
-            a[k] = c * c * ak + 2.0 * c * s * bk + s * s * ak1;
-            a[k + 1] = s * s * ak - 2.0 * c * s * bk + c * c * ak1;
-            b[k] = c * s * (ak1 - ak) + (c * c - s * s) * bk;
-            if (k + 1 < hi) {
-                x = b[k];
-                z = s * b[k + 1];
-                b[k + 1] = c * b[k + 1];
-            }
+            const double b2 = e2[k];
+            const double r2 = pi2 + b2;
+            if (k > lo) e2[k - 1] = s2p * r2;
+            // the three quotients depend only on pi2 and b2; 1/c2 is taken directly so that the
+            // next pivot does not wait for c2
+            const double c2 = pi2 / r2, s2 = b2 / r2, inv_c2 = r2 / pi2;
+            const double gn = c2 * (a[k + 1] - mu) - s2 * gam;
+            a[k] = gam + (a[k + 1] - gn);
+            pi2 = pi2 != 0.0 ? gn * gn * inv_c2 : c2p * b2;
+            c2p = c2;
+            s2p = s2;
+            gam = gn;
         }
+        e2[hi - 1] = s2p * pi2;
+        a[hi] = mu + gam;
     }
     return true;
 }
@@ -109,6 +158,7 @@ bool tridiagonal_eigenvalues(double* a, double* b, int n) {
 bool symmetric_eigenvalues(double* A, int n, double* out) {
     std::vector<double> e(n > 1 ? n - 1 : 1, 0.0);
     tridiagonalize(A, n, out, e.data());
+    for (double& x : e) x *= x;
     return tridiagonal_eigenvalues(out, e.data(), n);
 }
 

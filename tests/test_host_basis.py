@@ -34,3 +34,44 @@ def test_host_slice_basis_matches_oracle(C, shape, stride):
             lib.htsvd_internal_slice_basis(mom.ctypes.data, C, which, f, out.ctypes.data)
             z = (out[0::2] + 1j * out[1::2]).reshape(8, 8)
             assert np.abs(z - ref[f]).max() < 1e-9
+
+
+def _sigma_hook():
+    lib = H.load_library()
+    f = lib.htsvd_internal_sigma_from_moments
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
+    f.restype = ctypes.c_double
+    return f
+
+
+@pytest.mark.parametrize("C,shape,stride,kind", [(3, (64, 72), 3, "natural"), (1, (80, 64), 2, "natural"),
+                                                 (3, (40, 48), 1, "flat"), (1, (48, 40), 2, "constant")])
+def test_host_sigma_eigenvalues_match_oracle(C, shape, stride, kind):
+    """Host tridiagonal-QR eigenvalues of the patch covariance and the sigma rule (Sec. III-D)
+    against numpy's eigvalsh and the oracle's estimate, from exact integer moments."""
+    f = _sigma_hook()
+    if kind == "constant":
+        noisy = np.full(shape + (C,), 117, np.uint8)
+    else:
+        clean = synth.clean_image(shape[0], shape[1], C, 5)
+        if kind == "flat":     # low-rank signal: the covariance is dominated by few directions
+            clean = np.repeat(clean[:, :1, :], shape[1], axis=1)
+        noisy = synth.add_gaussian(clean, 12.0, 5)
+    p = O.Params(ps=8, stride=stride, window=15, K=16)
+    P = O.reference_patches(noisy, p).reshape(-1, 64 * C).astype(np.int64)
+    M = np.ascontiguousarray((P.T @ P).astype(np.uint64))
+    S = np.ascontiguousarray(P.sum(axis=0).astype(np.uint64))
+    lam = np.zeros(64 * C)
+    sig = f(M.ctypes.data, S.ctypes.data, 64 * C, P.shape[0], lam.ctypes.data)
+    ref = np.linalg.eigvalsh(O.patch_covariance(noisy, p))
+    scale = max(np.abs(ref).max(), 1.0)
+    assert np.abs(lam - np.sort(ref)).max() <= 1e-10 * scale
+    assert sig == pytest.approx(O.estimate_sigma(noisy, p), rel=1e-9, abs=1e-9)
+
+
+def test_host_sigma_rejects_bad_args():
+    f = _sigma_hook()
+    M = np.zeros((64, 64), np.uint64)
+    S = np.zeros(64, np.uint64)
+    assert f(M.ctypes.data, S.ctypes.data, 64, 0, None) == -1.0
+    assert f(None, S.ctypes.data, 64, 5, None) == -1.0
