@@ -269,6 +269,7 @@ htsvd_status run_block_match(const uint8_t* q, const Geo& g, const Resolved& r, 
     a.nry_s = (g.nry + rstep - 1) / rstep;
     a.nrx_s = (g.nrx + rstep - 1) / rstep;
     choose_bm_tiles(g, rstep, a.TRy, a.TRx);
+    bm_fit_tiles(a);
     a.idx = idx;
     { ProfScope ps_("block_match", s); CK(launch_block_match(a, s)); }
     return HTSVD_OK;

@@ -141,6 +141,7 @@ htsvd_status make_plan(const htsvd_image* imgs, int n, const htsvd_params* p, co
         b.nrx_s = g.nrx;
         b.TRy = t.bmy;
         b.TRx = t.bmx;
+        bm_fit_tiles(b);
         FilterArgs f{};
         f.img = im.d_in;
         f.img_is_float = 0;

@@ -1,17 +1,22 @@
 // Block matching (grouping, Alg. 1 Step 1; Sec. III-A, Eq. (GCP distance)).
 //
 // One CTA per tile of references; the match planes of the tile's union of search windows
-// are staged in shared memory. One warp per reference. Each lane scores 4 horizontally
-// adjacent candidates (8 lanes cover a window row of up to 32 candidates, 4 rows per step;
-// wider windows use 16 lanes per row, 2 rows per step):
-//  - byte planes (gray, G, or R, G, B in full mode): 4 pixels per instruction with
-//    __vabsdiffu4 and __dp4a on words funnel-shifted to the candidate's alignment;
-//  - the R+G+B plane of the "average" branch (values up to 765): FP32 differences and
-//    squares summed two rows at a time (each partial sum < 2^24, so exact) and converted to
-//    int32 before the final sum.
-// Both give the exact integer SSD. Keys (SSD << 32 | y*W + x) are merged into a warp-wide
-// sorted list (lane l holds the l-th smallest), so ties break by the lowest linear index.
-// Slot 0 of every group is the reference itself.
+// are staged in shared memory, together with the 8x8 box sums of their squares at every
+// candidate position (S_vv). One warp per reference. The exact integer SSD of a candidate v
+// against the reference r is
+//     SSD = S_vv(v) - 2 <v, r> + S_vv(r),
+// so per candidate only the cross term <v, r> is accumulated:
+//  - byte planes (gray, G, or R, G, B in full mode): __dp4a on words shifted to the
+//    candidate's alignment (4 pixels per instruction);
+//  - the R+G+B plane of the "average" branch (values up to 765): FP32 products summed two
+//    rows at a time (each partial sum < 2^24, so exact) and converted to int32.
+// Lane layout: lane (g, q) owns the candidate columns 4q .. 4q+3 of a strip of R consecutive
+// candidate rows; each staged image row is loaded once and used for every candidate row of the
+// strip it overlaps (reference row i = image row - candidate row).
+// Keys (SSD << 32 | y*W + x) below the warp's current threshold (the (K-1)-th smallest key
+// merged so far) are appended to a per-warp buffer; 32 buffered keys at a time are sorted and
+// merged into the warp-wide sorted list (lane l holds the l-th smallest). Ties therefore break
+// by the lowest linear index. Slot 0 of every group is the reference itself.
 #include "kernels.h"
 
 namespace htsvd {
@@ -19,7 +24,11 @@ namespace htsvd {
 namespace {
 
 constexpr int BM_THREADS = 256;
-constexpr int BM_PAD = 16;          // zero bytes after each staged byte row (funnel-shift over-read)
+constexpr int BM_WARPS = BM_THREADS / 32;
+constexpr int BM_PAD = 16;          // zero bytes after each staged byte row (shifted-word over-read)
+constexpr int BM_BUF = 64;          // per-warp key buffer (< 32 left after a merge + 32 appended)
+constexpr int BM_FR = 4;            // candidate rows per strip on the R+G+B plane
+constexpr unsigned FULL = 0xffffffffu;
 
 struct Region {
     int y0, x0, h, w;
@@ -41,14 +50,38 @@ __host__ __device__ inline int byte_planes(int mode, int C) {
     if (C == 1) return 1;
     return mode == MM_FULL ? 3 : 1;       // gray | G (green and GCP) | R, G, B (full)
 }
+__host__ __device__ inline bool uses_sum_plane(int mode, int C) { return C == 3 && mode == MM_GCP; }
 __host__ __device__ inline int bytes_pitch(int w) { return ((w + BM_PAD) + 3) & ~3; }
 
-// Bytes [u, u + 4) of the 16-byte little-endian window w0..w3, u in [0, 7].
-__device__ __forceinline__ uint32_t window4(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, int u) {
-    const uint32_t lo = u < 4 ? w0 : w1;
-    const uint32_t mi = u < 4 ? w1 : w2;
-    return __funnelshift_r(lo, mi, 8 * (u & 3));
-    (void)w3;
+// Shared-memory layout of a region of h x w pixels (h, w >= ps).
+struct BmLayout {
+    size_t bytes, fplane, svv, warp, total;
+};
+__host__ __device__ inline size_t a16(size_t o) { return (o + 15) & ~(size_t)15; }
+__host__ __device__ inline BmLayout bm_layout(int h, int w, int nb, bool sum_plane) {
+    BmLayout L;
+    size_t o = 0;
+    L.bytes = o;
+    o = a16(o + (size_t)nb * h * bytes_pitch(w));            // nb byte planes [h][pitch]
+    L.fplane = o;
+    if (sum_plane) o = a16(o + sizeof(float) * h * w);       // R+G+B plane [h][w]
+    L.svv = o;
+    o = a16(o + sizeof(int) * (sum_plane ? 2 : 1) * (size_t)(h - PS + 1) * (w - PS + 1));   // S_vv [h-7][w-7]
+    L.warp = o;
+    o += (size_t)BM_WARPS * (BM_BUF * sizeof(unsigned long long) + PS2 * sizeof(float));
+    L.total = o;
+    return L;
+}
+
+// Candidate rows per lane strip on the byte planes: the cheaper of 4 and 8 by loads (R + 7 rows)
+// and products (8 R row pairs) per chunk of 32/qpr strips; 4 when three planes are matched
+// (the reference words of three planes stay in registers).
+__host__ __device__ inline int bm_strip_rows(const Geo& g, int nb) {
+    if (nb == 3) return 4;
+    const int qpr = (g.wnx + 3) / 4, G = 32 / qpr;
+    const int c8 = (g.wny + G * 8 - 1) / (G * 8) * ((8 + PS - 1) * 13 + 8 * PS * 8);
+    const int c4 = (g.wny + G * 4 - 1) / (G * 4) * ((4 + PS - 1) * 13 + 4 * PS * 8);
+    return c8 <= c4 ? 8 : 4;
 }
 
 // Bitonic sort of one key per lane, ascending across the warp.
@@ -57,44 +90,240 @@ __device__ __forceinline__ unsigned long long warp_sort_asc(unsigned long long v
     for (int k = 2; k <= 32; k <<= 1)
 #pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
+            const unsigned long long o = __shfl_xor_sync(FULL, v, j);
             const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
             v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
         }
     return v;
 }
 
-// Merges the key of every lane into the warp's sorted list (lane l: l-th smallest; the
-// K-1 smallest keys seen so far are in lanes 0..K-2). Few passing keys are inserted one by
-// one; many are sorted and merged with the list in one bitonic pass.
-__device__ __forceinline__ void merge_keys(unsigned long long key, unsigned long long& list, int K, int lane) {
-    unsigned long long thr = __shfl_sync(0xffffffffu, list, K - 2);
-    unsigned pass = __ballot_sync(0xffffffffu, key < thr);
-    if (__popc(pass) > 4) {
-        const unsigned long long b = warp_sort_asc(key, lane);
-        const unsigned long long br = __shfl_sync(0xffffffffu, b, 31 - lane);
-        unsigned long long v = br < list ? br : list;     // bitonic: the 32 smallest of both lists
+// Top-(K-1) selection state of one warp: the sorted list (lane l: l-th smallest key merged so
+// far), its (K-1)-th key as the admission threshold, and the buffer of admitted keys.
+struct Select {
+    unsigned long long list, thr;
+    unsigned long long* buf;
+    int cnt;
+};
+
+struct MergeOut {
+    unsigned long long list, thr;
+    int cnt;
+};
+
+// Merges the first min(cnt, 32) buffered keys into the list and moves the rest down. Kept out
+// of line: it runs a few times per reference, while its call sites are many (one per offered
+// register), and inlining it everywhere overflows the instruction cache.
+__device__ __noinline__ MergeOut sel_merge_fn(unsigned long long list, unsigned long long* buf, int cnt, int K,
+                                              int lane) {
+    __syncwarp();
+    const int n = cnt < 32 ? cnt : 32;
+    const unsigned long long k = lane < n ? buf[lane] : ~0ull;
+    const unsigned long long b = warp_sort_asc(k, lane);
+    const unsigned long long br = __shfl_sync(FULL, b, 31 - lane);
+    unsigned long long v = br < list ? br : list;           // bitonic: the 32 smallest of both lists
 #pragma unroll
-        for (int j = 16; j > 0; j >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
-            v = ((lane & j) == 0) ? (o < v ? o : v) : (o > v ? o : v);
-        }
-        list = v;
-        return;
+    for (int j = 16; j > 0; j >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(FULL, v, j);
+        v = ((lane & j) == 0) ? (o < v ? o : v) : (o > v ? o : v);
     }
-    while (pass) {
-        const int src = __ffs(pass) - 1;
-        pass &= pass - 1;
-        const unsigned long long kk = __shfl_sync(0xffffffffu, key, src);
-        thr = __shfl_sync(0xffffffffu, list, K - 2);
-        if (kk < thr) {
-            const unsigned gt = __ballot_sync(0xffffffffu, list > kk);
-            const int pos = __ffs(gt) - 1;
-            const unsigned long long prev = __shfl_up_sync(0xffffffffu, list, 1);
-            if (lane == pos) list = kk;
-            else if (lane > pos) list = prev;
+    MergeOut m;
+    m.list = v;
+    m.thr = __shfl_sync(FULL, v, K - 2);
+    const int rest = cnt - n;
+    unsigned long long t = 0;
+    if (lane < rest) t = buf[32 + lane];
+    __syncwarp();
+    if (lane < rest) buf[lane] = t;
+    __syncwarp();
+    m.cnt = rest;
+    return m;
+}
+
+__device__ __forceinline__ void sel_merge(Select& S, int K, int lane) {
+    const MergeOut m = sel_merge_fn(S.list, S.buf, S.cnt, K, lane);
+    S.list = m.list;
+    S.thr = m.thr;
+    S.cnt = m.cnt;
+}
+
+// Offers one key per lane: keys below the threshold are appended to the buffer.
+__device__ __forceinline__ void sel_offer(Select& S, unsigned long long key, int K, int lane) {
+    const bool p = key < S.thr;
+    const unsigned pass = __ballot_sync(FULL, p);
+    if (!pass) return;
+    if (p) S.buf[S.cnt + __popc(pass & ((1u << lane) - 1u))] = key;
+    S.cnt += __popc(pass);
+    if (S.cnt >= 32) sel_merge(S, K, lane);
+}
+
+// Per-reference geometry shared by both distance paths.
+struct RefCtx {
+    int ry, rx, wy0, wx0;
+    int oy, ox;            // window origin in region coordinates
+    int wv;                // S_vv pitch (candidate positions per region row)
+};
+
+__device__ __forceinline__ unsigned long long make_key(int ssd, int py, int px, int W) {
+    return ((unsigned long long)(unsigned)ssd << 32) | (unsigned)(py * W + px);
+}
+
+// Byte planes: cross terms of the candidates of the lane's strips, keys offered per strip.
+template <int R, int NB>
+__device__ __forceinline__ void match_bytes(const BMArgs& a, const Region& Rg, const uint8_t* bp, int P8,
+                                            const int* svv, const RefCtx& c, Select& S, int lane) {
+    const Geo& g = a.g;
+    const int qpr = (g.wnx + 3) / 4, G = 32 / qpr;
+    const int sg = lane / qpr, q = lane - sg * qpr;
+    const bool active = sg < G;
+    const int cx0 = 4 * q;
+    // reference rows: two words per plane and row
+    uint32_t rw[NB][PS][2];
+#pragma unroll
+    for (int p = 0; p < NB; ++p) {
+        const uint8_t* pl = bp + (size_t)p * Rg.h * P8;
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            const int bo = (c.ry - Rg.y0 + i) * P8 + (c.rx - Rg.x0);
+            const uint32_t* wp = reinterpret_cast<const uint32_t*>(pl + (bo & ~3));
+            const int u = 8 * (bo & 3);
+            const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
+            rw[p][i][0] = __funnelshift_r(w0, w1, u);
+            rw[p][i][1] = __funnelshift_r(w1, w2, u);
         }
     }
+    const int srr = svv[(c.ry - Rg.y0) * c.wv + (c.rx - Rg.x0)];
+    const int sh = 8 * (c.ox & 3);                            // byte offset of every candidate word in a row
+    const int last_row = g.wny + PS - 2;                      // last window row any valid candidate reads
+    // warp-uniform chunk count (every lane offers the same number of keys); idle lanes and strips
+    // past the window offer none
+    const int nch = (g.wny + G * R - 1) / (G * R);
+    for (int ch = 0; ch < nch; ++ch) {
+        const int cy0 = (ch * G + sg) * R;
+        const bool run = active && cy0 < g.wny;
+        uint32_t acc[R][4];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) acc[k][s] = 0u;
+        if (run) {
+#pragma unroll
+            for (int t = 0; t < R + PS - 1; ++t) {
+                const int rr = min(cy0 + t, last_row);
+#pragma unroll
+                for (int p = 0; p < NB; ++p) {
+                    const uint8_t* pl = bp + (size_t)p * Rg.h * P8;
+                    const uint32_t* wp =
+                        reinterpret_cast<const uint32_t*>(pl + (((c.oy + rr) * P8 + c.ox + cx0) & ~3));
+                    const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2], w3 = wp[3];
+                    const uint32_t a0 = __funnelshift_r(w0, w1, sh);
+                    const uint32_t a1 = __funnelshift_r(w1, w2, sh);
+                    const uint32_t a2 = __funnelshift_r(w2, w3, sh);
+                    uint32_t lo[4], hi[4];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        lo[s] = s == 0 ? a0 : __funnelshift_r(a0, a1, 8 * s);
+                        hi[s] = s == 0 ? a1 : __funnelshift_r(a1, a2, 8 * s);
+                    }
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        const int i = t - k;                  // reference row met by candidate row k
+                        if (i < 0 || i >= PS) continue;
+#pragma unroll
+                        for (int s = 0; s < 4; ++s) {
+                            acc[k][s] = __dp4a(lo[s], rw[p][i][0], acc[k][s]);
+                            acc[k][s] = __dp4a(hi[s], rw[p][i][1], acc[k][s]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int cy = cy0 + k, cx = cx0 + s;
+                unsigned long long key = ~0ull;
+                if (run && cy < g.wny && cx < g.wnx) {
+                    const int py = c.wy0 + cy, px = c.wx0 + cx;
+                    if (py != c.ry || px != c.rx)
+                        key = make_key(svv[(c.oy + cy) * c.wv + c.ox + cx] + srr - 2 * (int)acc[k][s], py, px, g.W);
+                }
+                sel_offer(S, key, g.K, lane);
+            }
+    }
+}
+
+// R+G+B plane: exact cross terms from FP32 partial sums over two reference rows.
+__device__ __forceinline__ void match_sum_plane(const BMArgs& a, const Region& Rg, const float* sp,
+                                                const int* svv2, float* rvw, const RefCtx& c, Select& S,
+                                                int lane) {
+    const Geo& g = a.g;
+    constexpr int R = BM_FR;
+    const int qpr = (g.wnx + 3) / 4, G = 32 / qpr;
+    const int sg = lane / qpr, q = lane - sg * qpr;
+    const bool active = sg < G;
+    const int cx0 = 4 * q;
+    // the reference patch, for broadcast reads
+    for (int e = lane; e < PS2; e += 32) rvw[e] = sp[(c.ry - Rg.y0 + e / PS) * Rg.w + (c.rx - Rg.x0) + e % PS];
+    __syncwarp();
+    const int srr = svv2[(c.ry - Rg.y0) * c.wv + (c.rx - Rg.x0)];
+    const int last_row = g.wny + PS - 2;
+    const int maxc = Rg.w - 1 - c.ox;          // clamp of the columns of idle candidates beyond the window
+    const int nch = (g.wny + G * R - 1) / (G * R);           // warp-uniform, as on the byte planes
+    for (int ch = 0; ch < nch; ++ch) {
+        const int cy0 = (ch * G + sg) * R;
+        const bool run = active && cy0 < g.wny;
+        int acc[R][4];
+        float part[R][4];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                acc[k][s] = 0;
+                part[k][s] = 0.f;
+            }
+        if (run) {
+#pragma unroll
+            for (int t = 0; t < R + PS - 1; ++t) {
+                const int rr = min(cy0 + t, last_row);
+                const float* row = sp + (c.oy + rr) * Rg.w + c.ox;
+                float v[PS + 3];
+#pragma unroll
+                for (int j = 0; j < PS + 3; ++j) v[j] = row[min(cx0 + j, maxc)];
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const int i = t - k;
+                    if (i < 0 || i >= PS) continue;
+                    const float4 r0 = reinterpret_cast<const float4*>(rvw + i * PS)[0];
+                    const float4 r1 = reinterpret_cast<const float4*>(rvw + i * PS)[1];
+                    const float rv[PS] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+#pragma unroll
+                        for (int j = 0; j < PS; ++j) part[k][s] = fmaf(v[s + j], rv[j], part[k][s]);
+                        if (i & 1) {
+                            acc[k][s] += __float2int_rn(part[k][s]);
+                            part[k][s] = 0.f;
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int cy = cy0 + k, cx = cx0 + s;
+                unsigned long long key = ~0ull;
+                if (run && cy < g.wny && cx < g.wnx) {
+                    const int py = c.wy0 + cy, px = c.wx0 + cx;
+                    if (py != c.ry || px != c.rx)
+                        key = make_key(svv2[(c.oy + cy) * c.wv + c.ox + cx] + srr - 2 * acc[k][s], py, px, g.W);
+                }
+                sel_offer(S, key, g.K, lane);
+            }
+    }
+    __syncwarp();
 }
 
 // Grouping of one tile (by, bx) of references; bsm: bm_smem_bytes(a) of shared memory.
@@ -102,178 +331,139 @@ __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigne
     const Geo& g = a.g;
     const int iy0 = by * a.TRy, ix0 = bx * a.TRx;
     const int iy1 = min(iy0 + a.TRy, a.nry_s) - 1, ix1 = min(ix0 + a.TRx, a.nrx_s) - 1;
-    const Region R = bm_region(a, iy0, iy1, ix0, ix1);
+    const Region Rg = bm_region(a, iy0, iy1, ix0, ix1);
     const int nb = byte_planes(a.mode, g.C);
-    const int P8 = bytes_pitch(R.w);
-    const bool gcp = g.C == 3 && a.mode == MM_GCP;
-    uint8_t* bp = bsm;                                              // nb byte planes [R.h][P8]
-    float* sp = reinterpret_cast<float*>(bsm + (((size_t)nb * R.h * P8 + 15) & ~(size_t)15));   // R+G+B plane
+    const bool gcp = uses_sum_plane(a.mode, g.C);
+    const int P8 = bytes_pitch(Rg.w);
+    const BmLayout L = bm_layout(Rg.h, Rg.w, nb, gcp);
+    uint8_t* bp = bsm + L.bytes;                                     // nb byte planes [h][P8]
+    float* sp = reinterpret_cast<float*>(bsm + L.fplane);            // R+G+B plane [h][w]
+    int* svv = reinterpret_cast<int*>(bsm + L.svv);                  // S_vv [nsv][h-7][w-7]
+    const int hv = Rg.h - PS + 1, wv = Rg.w - PS + 1;
 
     // Stage the planes of the region (byte rows zero-padded).
-    for (int t = threadIdx.x; t < R.h * P8; t += BM_THREADS) {
-        const int r = t / P8, c = t - r * P8;
-        if (c < R.w) {
-            const uint8_t* px = a.img + ((size_t)(R.y0 + r) * g.W + (R.x0 + c)) * g.C;
+    for (int t = threadIdx.x; t < Rg.h * P8; t += BM_THREADS) {
+        const int r = t / P8, cc = t - r * P8;
+        if (cc < Rg.w) {
+            const uint8_t* px = a.img + ((size_t)(Rg.y0 + r) * g.W + (Rg.x0 + cc)) * g.C;
             if (g.C == 1) {
                 bp[t] = px[0];
             } else if (a.mode == MM_FULL) {
                 bp[t] = px[0];
-                bp[(size_t)R.h * P8 + t] = px[1];
-                bp[(size_t)2 * R.h * P8 + t] = px[2];
+                bp[(size_t)Rg.h * P8 + t] = px[1];
+                bp[(size_t)2 * Rg.h * P8 + t] = px[2];
             } else {
                 bp[t] = px[1];
-                if (gcp) sp[r * R.w + c] = (float)((int)px[0] + (int)px[1] + (int)px[2]);
+                if (gcp) sp[r * Rg.w + cc] = (float)((int)px[0] + (int)px[1] + (int)px[2]);
             }
         } else {
-            for (int p = 0; p < nb; ++p) bp[(size_t)p * R.h * P8 + t] = 0;
+            for (int p = 0; p < nb; ++p) bp[(size_t)p * Rg.h * P8 + t] = 0;
+        }
+    }
+    __syncthreads();
+    // S_vv: 8x8 box sums of the squared plane values (summed over the byte planes; the R+G+B
+    // plane separately). Work item (plane, block of 8 output rows, column x).
+    {
+        const int nyc = (hv + PS - 1) / PS;
+        const int nsv = gcp ? 2 : 1;
+        for (int it = threadIdx.x; it < nsv * nyc * wv; it += BM_THREADS) {
+            const int pl = it / (nyc * wv);
+            const int rem = it - pl * nyc * wv;
+            const int yc = rem / wv, x = rem - yc * wv;
+            const int y0 = yc * PS;
+            int hs[2 * PS - 1];
+#pragma unroll
+            for (int t = 0; t < 2 * PS - 1; ++t) {
+                int v = 0;
+                const int r = y0 + t;
+                if (r < Rg.h) {
+                    if (pl == 0) {
+                        for (int p = 0; p < nb; ++p) {
+                            const uint8_t* rowp = bp + (size_t)p * Rg.h * P8 + (size_t)r * P8 + x;
+#pragma unroll
+                            for (int j = 0; j < PS; ++j) v += (int)rowp[j] * (int)rowp[j];
+                        }
+                    } else {
+                        const float* rowp = sp + r * Rg.w + x;
+#pragma unroll
+                        for (int j = 0; j < PS; ++j) {
+                            const int u = (int)rowp[j];
+                            v += u * u;
+                        }
+                    }
+                }
+                hs[t] = v;
+            }
+            int* out = svv + (size_t)pl * hv * wv;
+#pragma unroll
+            for (int o = 0; o < PS; ++o) {
+                if (y0 + o < hv) {
+                    int sum = 0;
+#pragma unroll
+                    for (int i = 0; i < PS; ++i) sum += hs[o + i];
+                    out[(y0 + o) * wv + x] = sum;
+                }
+            }
         }
     }
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // lane -> (window row within the step, candidate quad): 8 quads (32 columns) per row for windows up to
-    // 32 wide, else 16 quads (64 columns) per row
-    const int qpr = g.wnx > 32 ? 16 : 8;
-    const int rps = 32 / qpr;
-    const int sub = lane / qpr, q = lane % qpr;
+    unsigned char* wbase = bsm + L.warp + (size_t)warp * (BM_BUF * sizeof(unsigned long long) + PS2 * sizeof(float));
+    unsigned long long* buf = reinterpret_cast<unsigned long long*>(wbase);
+    float* rvw = reinterpret_cast<float*>(wbase + BM_BUF * sizeof(unsigned long long));
     const int tw = ix1 - ix0 + 1;
     const int nt = (iy1 - iy0 + 1) * tw;
     const int K = g.K;
-    for (int t = warp; t < nt; t += BM_THREADS / 32) {
+    const int R = bm_strip_rows(g, nb);
+    for (int t = warp; t < nt; t += BM_WARPS) {
         const int iy = iy0 + t / tw, ix = ix0 + t % tw;
-        const int ry = ref_pos(iy * a.rstep, g.s, g.H), rx = ref_pos(ix * a.rstep, g.s, g.W);
-        const int wy0 = win_start(ry, g.npy, g.win), wx0 = win_start(rx, g.npx, g.win);
+        RefCtx c;
+        c.ry = ref_pos(iy * a.rstep, g.s, g.H);
+        c.rx = ref_pos(ix * a.rstep, g.s, g.W);
+        c.wy0 = win_start(c.ry, g.npy, g.win);
+        c.wx0 = win_start(c.rx, g.npx, g.win);
+        c.oy = c.wy0 - Rg.y0;
+        c.ox = c.wx0 - Rg.x0;
+        c.wv = wv;
 
         // Plane choice (Eq. GCP distance on the reference patch).
         bool green = true;
         if (gcp) {
             int r2 = 0, g2 = 0, b2 = 0;
             for (int pi = lane; pi < PS2; pi += 32) {
-                const uint8_t* px = a.img + ((size_t)(ry + pi / PS) * g.W + rx + pi % PS) * 3;
+                const uint8_t* px = a.img + ((size_t)(c.ry + pi / PS) * g.W + c.rx + pi % PS) * 3;
                 const int rr = px[0], gg = px[1], bb = px[2];
                 r2 += rr * rr;
                 g2 += gg * gg;
                 b2 += bb * bb;
             }
-            r2 = __reduce_add_sync(0xffffffffu, r2);
-            g2 = __reduce_add_sync(0xffffffffu, g2);
-            b2 = __reduce_add_sync(0xffffffffu, b2);
+            r2 = __reduce_add_sync(FULL, r2);
+            g2 = __reduce_add_sync(FULL, g2);
+            b2 = __reduce_add_sync(FULL, b2);
             const double lhs = a.gamma2 * (double)g2;
             green = (lhs >= (double)r2) && (lhs >= (double)b2);
         }
 
-        unsigned long long list = ~0ull;       // lane l: l-th smallest key so far
-        const int cx0 = 4 * q;
-        const bool quad_ok = cx0 < g.wnx;
-        if (green) {
-            // reference rows as two words per plane and row
-            uint32_t rw[3][PS][2];
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                if (p >= nb) break;
-                const uint8_t* pl = bp + (size_t)p * R.h * P8;
-#pragma unroll
-                for (int i = 0; i < PS; ++i) {
-                    const int bo = (ry - R.y0 + i) * P8 + (rx - R.x0);
-                    const uint32_t* wp = reinterpret_cast<const uint32_t*>(pl + (bo & ~3));
-                    const int u = bo & 3;
-                    const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
-                    rw[p][i][0] = __funnelshift_r(w0, w1, 8 * u);
-                    rw[p][i][1] = __funnelshift_r(w1, w2, 8 * u);
-                }
-            }
-            for (int ybase = 0; ybase < g.wny; ybase += rps) {
-                const int cy = ybase + sub;
-                uint32_t acc[4] = {0u, 0u, 0u, 0u};
-                const bool ok = quad_ok && cy < g.wny;
-                if (ok) {
-#pragma unroll
-                    for (int p = 0; p < 3; ++p) {
-                        if (p >= nb) break;
-                        const uint8_t* pl = bp + (size_t)p * R.h * P8;
-#pragma unroll
-                        for (int i = 0; i < PS; ++i) {
-                            const int bo = (wy0 + cy - R.y0 + i) * P8 + (wx0 - R.x0) + cx0;
-                            const uint32_t* wp = reinterpret_cast<const uint32_t*>(pl + (bo & ~3));
-                            const int sh = bo & 3;
-                            const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2], w3 = wp[3];
-#pragma unroll
-                            for (int s = 0; s < 4; ++s) {
-                                const int u = sh + s;
-                                const uint32_t lo = window4(w0, w1, w2, w3, u);
-                                const uint32_t hi = window4(w1, w2, w3, w3, u);
-                                const uint32_t d0 = __vabsdiffu4(lo, rw[p][i][0]);
-                                const uint32_t d1 = __vabsdiffu4(hi, rw[p][i][1]);
-                                acc[s] = __dp4a(d0, d0, acc[s]);
-                                acc[s] = __dp4a(d1, d1, acc[s]);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    unsigned long long key = ~0ull;
-                    const int cx = cx0 + s;
-                    if (ok && cx < g.wnx) {
-                        const int py = wy0 + cy, px = wx0 + cx;
-                        if (py != ry || px != rx)
-                            key = ((unsigned long long)acc[s] << 32) | (unsigned)(py * g.W + px);
-                    }
-                    merge_keys(key, list, K, lane);
-                }
-            }
+        Select S;
+        S.list = ~0ull;
+        S.thr = ~0ull;
+        S.buf = buf;
+        S.cnt = 0;
+        if (!green) {
+            match_sum_plane(a, Rg, sp, svv + (size_t)hv * wv, rvw, c, S, lane);
+        } else if (nb == 3) {
+            match_bytes<4, 3>(a, Rg, bp, P8, svv, c, S, lane);
+        } else if (R == 8) {
+            match_bytes<8, 1>(a, Rg, bp, P8, svv, c, S, lane);
         } else {
-            // R+G+B plane: exact integer SSD via FP32 partial sums of two rows
-            float rv[PS][PS];
-#pragma unroll
-            for (int i = 0; i < PS; ++i)
-#pragma unroll
-                for (int j = 0; j < PS; ++j) rv[i][j] = sp[(ry - R.y0 + i) * R.w + (rx - R.x0) + j];
-            for (int ybase = 0; ybase < g.wny; ybase += rps) {
-                const int cy = ybase + sub;
-                int acc[4] = {0, 0, 0, 0};
-                const bool ok = quad_ok && cy < g.wny;
-                if (ok) {
-                    // columns cx0 .. cx0 + 10 of the rows; clamp reads of candidates beyond the window
-                    const int maxc = R.w - 1 - (wx0 - R.x0);
-#pragma unroll
-                    for (int i2 = 0; i2 < PS; i2 += 2) {
-                        float part[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int ii = 0; ii < 2; ++ii) {
-                            const int i = i2 + ii;
-                            const float* row = sp + (wy0 + cy - R.y0 + i) * R.w + (wx0 - R.x0);
-                            float v[PS + 3];
-#pragma unroll
-                            for (int c = 0; c < PS + 3; ++c) v[c] = row[min(cx0 + c, maxc)];
-#pragma unroll
-                            for (int s = 0; s < 4; ++s)
-#pragma unroll
-                                for (int j = 0; j < PS; ++j) {
-                                    const float d = v[s + j] - rv[i][j];
-                                    part[s] = fmaf(d, d, part[s]);
-                                }
-                        }
-#pragma unroll
-                        for (int s = 0; s < 4; ++s) acc[s] += __float2int_rn(part[s]);
-                    }
-                }
-#pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    unsigned long long key = ~0ull;
-                    const int cx = cx0 + s;
-                    if (ok && cx < g.wnx) {
-                        const int py = wy0 + cy, px = wx0 + cx;
-                        if (py != ry || px != rx)
-                            key = ((unsigned long long)(unsigned)acc[s] << 32) | (unsigned)(py * g.W + px);
-                    }
-                    merge_keys(key, list, K, lane);
-                }
-            }
+            match_bytes<4, 1>(a, Rg, bp, P8, svv, c, S, lane);
         }
+        if (S.cnt > 0) sel_merge(S, K, lane);
         int32_t* out = a.idx + (size_t)(iy * a.nrx_s + ix) * K;
-        if (lane == 0) out[0] = ry * g.W + rx;
-        if (lane < K - 1) out[1 + lane] = (int32_t)(unsigned)(list & 0xffffffffull);
+        if (lane == 0) out[0] = c.ry * g.W + c.rx;
+        if (lane < K - 1) out[1 + lane] = (int32_t)(unsigned)(S.list & 0xffffffffull);
+        __syncwarp();
     }
 }
 
@@ -308,6 +498,9 @@ __global__ void __launch_bounds__(BM_THREADS, 2) block_match_batch_kernel(const 
     }
 }
 
+constexpr size_t BM_SMEM_TARGET = 100 * 1024;    // leaves room for two CTAs per SM
+constexpr size_t BM_SMEM_MAX = 227 * 1024;
+
 }  // namespace
 
 size_t bm_smem_bytes(const BMArgs& a) {
@@ -317,9 +510,14 @@ size_t bm_smem_bytes(const BMArgs& a) {
     int hx = (a.TRx - 1) * a.rstep * g.s + g.wnx + PS - 1;
     if (hy > g.H) hy = g.H;
     if (hx > g.W) hx = g.W;
-    const size_t bytes = (size_t)byte_planes(a.mode, g.C) * hy * bytes_pitch(hx);
-    const bool gcp = g.C == 3 && a.mode == MM_GCP;
-    return ((bytes + 15) & ~(size_t)15) + (gcp ? (size_t)hy * hx * sizeof(float) : 0);
+    return bm_layout(hy, hx, byte_planes(a.mode, g.C), uses_sum_plane(a.mode, g.C)).total;
+}
+
+void bm_fit_tiles(BMArgs& a) {
+    while (bm_smem_bytes(a) > BM_SMEM_TARGET && (a.TRx > 1 || a.TRy > 1)) {
+        if (a.TRx >= a.TRy) a.TRx = (a.TRx + 1) / 2;
+        else a.TRy = (a.TRy + 1) / 2;
+    }
 }
 
 int bm_tiles(const BMArgs& a) {
@@ -328,6 +526,7 @@ int bm_tiles(const BMArgs& a) {
 
 cudaError_t launch_block_match_batch(const BMArgs* d_args, const int* d_prefix, int nimg, size_t smem, int grid,
                                      int* d_counter, cudaStream_t s) {
+    if (smem > BM_SMEM_MAX) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(block_match_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -337,6 +536,7 @@ cudaError_t launch_block_match_batch(const BMArgs* d_args, const int* d_prefix, 
 
 cudaError_t launch_block_match(const BMArgs& a, cudaStream_t s) {
     size_t smem = bm_smem_bytes(a);
+    if (smem > BM_SMEM_MAX) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(block_match_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

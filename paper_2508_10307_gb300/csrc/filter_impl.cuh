@@ -40,7 +40,9 @@ struct FCfg {
                                                        // so the 128-bit row loads of 8 consecutive rows hit
                                                        // distinct bank groups
     static constexpr int PATCH = PS2 * C;              // floats per patch (fibres of the Haar stage)
-    static constexpr int GS = (C == 3) ? 228 : 100;    // stride between patches (odd number of 16-byte units)
+    static constexpr int GS = (C == 3) ? 232 : 104;    // stride between patches, = 8 (mod 32) words: the column
+                                                       // accesses of stages A and E (lanes = 4 patches x 8
+                                                       // columns) then fall on 32 distinct banks
     static constexpr int ACC = (C == 3) ? 4 : 2;       // floats per footprint pixel (C numerators + 1 denominator)
     static constexpr int NBAS = (C == 3) ? 384 : 128;  // packed FP32 basis floats
 };
@@ -465,14 +467,14 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     auto group_of = [&](int q) { return (iy0 + q / tw) * g.nrx + ix0 + q % tw; };
     // Positions come from the grouping of this geometry and lie in the footprint; a caller-given
     // index outside it is clamped so that no access leaves the staged region.
-    auto load_pos = [&](int q, int* pos) {
+    auto store_pos = [&](int v, int* pos) {
         if (tid < K) {
-            const int v = a.idx[(size_t)group_of(q) * K + tid];
             const int y = v / g.W, x = v - y * g.W;
             pos[2 * tid] = min(max(y - FY0, 0), FH - PS);
             pos[2 * tid + 1] = min(max(x - FX0, 0), FW - PS);
         }
     };
+    auto fetch_idx = [&](int q) { return tid < K ? a.idx[(size_t)group_of(q) * K + tid] : 0; };
     // A, B of group q into buffer gbq; ||G||_F^2 into misc[5] (uint8, exact) or misc[2] (float)
     auto project = [&](float* gbq, const int* pos, int* misc) {
         if (tid < 8 * K) {
@@ -491,13 +493,15 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         }
     };
 
-    load_pos(0, posb);
+    store_pos(fetch_idx(0), posb);
     if (tid < 32) miscb[tid] = 0;
     __syncthreads();
     project(gbb, posb, miscb);
     __syncthreads();
 
     for (int q = 0; q < ngr; ++q) {
+        // the next group's indices: loaded here, stored after the C phase hides their latency
+        const int next_idx = q + 1 < ngr ? fetch_idx(q + 1) : 0;
         const int buf = q & 1;
         const int grp = group_of(q);
         float* gbq = gbb + buf * K * G::GS;
@@ -565,7 +569,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
             stage_e<C>(bas, gbq, tid >> 3, tid & 7);
         }
         if (q + 1 < ngr) {
-            load_pos(q + 1, posb + (buf ^ 1) * 64);
+            store_pos(next_idx, posb + (buf ^ 1) * 64);
             if (tid < 16) miscb[(buf ^ 1) * 16 + tid] = 0;
         }
         __syncthreads();

@@ -20,6 +20,8 @@ struct BMArgs {
     int32_t* idx;        // out [nry_s * nrx_s][K]
 };
 size_t bm_smem_bytes(const BMArgs& a);
+// Halves the tile (TRx, TRy) until its shared-memory footprint leaves room for two CTAs per SM.
+void bm_fit_tiles(BMArgs& a);
 cudaError_t launch_block_match(const BMArgs& a, cudaStream_t s);
 
 // ---- second moments and bases (moments.cu)

@@ -113,6 +113,7 @@ extern "C" htsvd_status htsvd_denoise_noalloc(const uint8_t* d_noisy, int32_t H,
     ba.nrx_s = g.nrx;
     ba.TRy = 4;
     ba.TRx = 8;
+    bm_fit_tiles(ba);
     ba.idx = idx;
     if (launch_block_match(ba, stream) != cudaSuccess) return HTSVD_ERR_CUDA;
     // launch_moments clears the moment accumulators (left over from the previous call) first.
