@@ -89,33 +89,69 @@ __host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes) {
     return L;
 }
 
-// In-register Haar analysis along the group mode: o = H_K a (Eq. (H_2N) applied recursively).
+// Haar analysis along the group mode, o = H_K a (Eq. (H_2N) applied recursively), in place on
+// one array: at the level of length n the values sit at stride K/n, so the detail o[n/2 + m]
+// lands in slot (2m+1) K/n and the approximation o[0] in slot 0.
+// Calls f(mo, slot) for every coefficient o[mo] and its slot in the in-place array. Each level
+// is its own template instance, so every loop has a constant trip count, unrolls fully, and
+// every index is a compile-time constant: the array stays in registers.
+template <int K>
+__host__ __device__ constexpr int haar_levels() { return K <= 1 ? 0 : 1 + haar_levels<K / 2>(); }
+template <int K, int L, typename F>
+__device__ __forceinline__ void haar_each_level(F& f) {       // level L: n = 2^(L+1), details o[2^L + m]
+    if constexpr (L >= 0) {
+        haar_each_level<K, L - 1>(f);
+#pragma unroll
+        for (int m = 0; m < (1 << L); ++m) f((1 << L) + m, (2 * m + 1) * (K >> (L + 1)));
+    }
+}
+template <int K, typename F>
+__device__ __forceinline__ void haar_for_each(F&& f) {
+    f(0, 0);
+    haar_each_level<K, haar_levels<K>() - 1>(f);
+}
+template <int K, int L>
+__device__ __forceinline__ void haar_fwd_level(float (&v)[K]) {  // levels L, L-1, ..., 0 (n = K first)
+    if constexpr (L >= 0) {
+        constexpr int st = K >> (L + 1);
+#pragma unroll
+        for (int m = 0; m < (1 << L); ++m) {
+            const float x = v[2 * m * st], y = v[(2 * m + 1) * st];
+            v[(2 * m + 1) * st] = (x - y) * F_R2;
+            v[2 * m * st] = (x + y) * F_R2;
+        }
+        haar_fwd_level<K, L - 1>(v);
+    }
+}
+template <int K, int L>
+__device__ __forceinline__ void haar_inv_level(float (&v)[K]) {  // levels L, L+1, ..., (n = 2 first)
+    if constexpr ((2 << L) <= K) {
+        constexpr int st = K >> (L + 1);
+#pragma unroll
+        for (int m = (1 << L) - 1; m >= 0; --m) {
+            const float sa = v[2 * m * st], d = v[(2 * m + 1) * st];
+            v[2 * m * st] = (sa + d) * F_R2;
+            v[(2 * m + 1) * st] = (sa - d) * F_R2;
+        }
+        haar_inv_level<K, L + 1>(v);
+    }
+}
+template <int K>
+__device__ __forceinline__ void haar_fwd_inplace(float (&v)[K]) { haar_fwd_level<K, haar_levels<K>() - 1>(v); }
+template <int K>
+__device__ __forceinline__ void haar_inv_inplace(float (&v)[K]) { haar_inv_level<K, 0>(v); }
+
+// Two-array forms: o = H_K a (Eq. (H_2N) applied recursively; a is overwritten) and its
+// synthesis a = H_K^T o (o is overwritten), with o in the natural coefficient order.
 template <int K>
 __device__ __forceinline__ void haar_fwd(float (&a)[K], float (&o)[K]) {
-#pragma unroll
-    for (int n = K; n > 1; n >>= 1) {
-#pragma unroll
-        for (int m = 0; m < n / 2; ++m) {
-            const float x = a[2 * m], y = a[2 * m + 1];
-            o[n / 2 + m] = (x - y) * F_R2;
-            a[m] = (x + y) * F_R2;
-        }
-    }
-    o[0] = a[0];
+    haar_fwd_inplace<K>(a);
+    haar_for_each<K>([&](int m, int sl) { o[m] = a[sl]; });
 }
-// Synthesis a = H_K^T o.
 template <int K>
 __device__ __forceinline__ void haar_inv(float (&o)[K], float (&a)[K]) {
-    a[0] = o[0];
-#pragma unroll
-    for (int n = 2; n <= K; n <<= 1) {
-#pragma unroll
-        for (int m = n / 2 - 1; m >= 0; --m) {
-            const float s = a[m], d = o[n / 2 + m];
-            a[2 * m] = (s + d) * F_R2;
-            a[2 * m + 1] = (s - d) * F_R2;
-        }
-    }
+    haar_for_each<K>([&](int m, int sl) { a[sl] = o[m]; });
+    haar_inv_inplace<K>(a);
 }
 
 template <typename T>
@@ -133,8 +169,8 @@ __device__ __forceinline__ void load8(const float* p, float (&r)[8]) {
 // Lane l handles the pixels (a, b) = l and l + 32 of the combined patch Q = sum_k H[m,k] P_k;
 // for uint8 inputs the signed sum of the patches is exact in int32.
 template <int K, int C, typename Tin>
-__device__ bool refine_keep(int m, int e, const Tin* img_s, int FW, const int* pos, const double* __restrict__ b64,
-                            double tau64, int lane) {
+__device__ __forceinline__ bool refine_keep(int m, int e, const Tin* img_s, int FW, const int* pos,
+                                            const double* __restrict__ b64, double tau64, int lane) {
     int k0, L;
     if (m == 0) {
         k0 = 0;
@@ -159,10 +195,15 @@ __device__ bool refine_keep(int m, int e, const Tin* img_s, int FW, const int* p
             int qi[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) qi[c] = 0;
-            for (int kk = k0; kk < k0 + L; ++kk) {
-                const Tin* src = img_s + ((pos[2 * kk] + aa) * FW + pos[2 * kk + 1] + bb) * C;
+            for (int kk = k0; kk < k0 + L; kk += 2) {        // L is even: two independent loads per step
+                const Tin* s0p = img_s + ((pos[2 * kk] + aa) * FW + pos[2 * kk + 1] + bb) * C;
+                const Tin* s1p = img_s + ((pos[2 * kk + 2] + aa) * FW + pos[2 * kk + 3] + bb) * C;
+                const bool p0 = kk - k0 < half, p1 = kk + 1 - k0 < half;
 #pragma unroll
-                for (int c = 0; c < C; ++c) qi[c] += (kk - k0 < half) ? (int)src[c] : -(int)src[c];
+                for (int c = 0; c < C; ++c) {
+                    const int x0 = (int)s0p[c], x1 = (int)s1p[c];
+                    qi[c] += (p0 ? x0 : -x0) + (p1 ? x1 : -x1);
+                }
             }
 #pragma unroll
             for (int c = 0; c < C; ++c) q[c] = (double)qi[c] * h;
@@ -199,14 +240,8 @@ __device__ bool refine_keep(int m, int e, const Tin* img_s, int FW, const int* p
             s0 += u0 * q[0] * v0;
         }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-        if constexpr (C == 3) {
-            s1r += __shfl_xor_sync(0xffffffffu, s1r, off);
-            s1i += __shfl_xor_sync(0xffffffffu, s1i, off);
-        }
-    }
+    // the requested channel is a fixed linear combination of the three slice sums: combine per
+    // lane, then reduce one value
     double S;
     if constexpr (C == 3) {
         const double sq3 = sqrt(3.0);
@@ -214,6 +249,8 @@ __device__ bool refine_keep(int m, int e, const Tin* img_s, int FW, const int* p
     } else {
         S = s0;
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) S += __shfl_xor_sync(0xffffffffu, S, off);
     return fabs(S) >= tau64;
 }
 
@@ -509,38 +546,8 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         int* misc = miscb + buf * 16;
 
         // ---- C: Haar analysis, threshold (FP64 inside the guard band), synthesis
-        if (tid < NF) {
-            const int foff = (tid / G::RWF) * G::ROW + (tid % G::RWF);
-            const float nrm2 = sizeof(Tin) == 1 ? (float)misc[5] : __int_as_float(misc[2]);
-            const float delta = a.band_rel * sqrtf(nrm2) + a.band_abs;
-            float fib[K], co[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) fib[k] = gbq[k * G::GS + foff];
-            haar_fwd<K>(fib, co);
-            if (a.coef_out) {
-                float* cdst = a.coef_out + (size_t)grp * K * NF;
-#pragma unroll
-                for (int m = 0; m < K; ++m) cdst[m * NF + tid] = co[m];
-            }
-            uint32_t keepb = 0, bandb = 0;
-#pragma unroll
-            for (int m = 0; m < K; ++m) {
-                const float d = fabsf(co[m]) - a.tau32;
-                if (fabsf(d) <= delta) bandb |= 1u << m;
-                else if (d >= 0.f) keepb |= 1u << m;
-            }
-            unsigned anyb = __ballot_sync(0xffffffffu, bandb != 0u);
-            while (anyb) {
-                const int l = __ffs(anyb) - 1;
-                anyb &= anyb - 1;
-                uint32_t bb = __shfl_sync(0xffffffffu, bandb, l);
-                while (bb) {
-                    const int m = __ffs(bb) - 1;
-                    bb &= bb - 1;
-                    const bool keep = refine_keep<K, C, Tin>(m, warp * 32 + l, img_s, FW, pos, a.basis64, a.tau64, lane);
-                    if (lane == l && keep) keepb |= 1u << m;
-                }
-            }
+        // final keep decisions of the warp's fibres: optional mask output, kept count
+        auto keep_finish = [&](uint32_t keepb) {
             if (a.mask_out) {
                 uint32_t* mo = a.mask_out + (size_t)grp * NBW;
 #pragma unroll
@@ -549,17 +556,72 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                     if (lane == 0) mo[m * (NF / 32) + warp] = w;
                 }
             }
+            const int wk = __reduce_add_sync(0xffffffffu, __popc(keepb));
+            if (lane == 0) atomicAdd(&misc[1], wk);
+        };
+        if (tid < NF) {
+            const int foff = (tid / G::RWF) * G::ROW + (tid % G::RWF);
+            const float nrm2 = sizeof(Tin) == 1 ? (float)misc[5] : __int_as_float(misc[2]);
+            const float delta = a.band_rel * sqrtf(nrm2) + a.band_abs;
+            // (the rare guard-band path finishes the fibre in a scope of its own, with a second
+            // array reloaded from shared memory, so that no K-register array is live across the
+            // FP64 refinement loop: that would push the array to local memory)
+            uint32_t keepb = 0, bandb = 0;
+            unsigned anyb;
             {
-                const int wk = __reduce_add_sync(0xffffffffu, __popc(keepb));
-                if (lane == 0) atomicAdd(&misc[1], wk);
+                float v[K];                               // fibre, then its coefficients (haar_for_each slots)
+#pragma unroll
+                for (int k = 0; k < K; ++k) v[k] = gbq[k * G::GS + foff];
+                haar_fwd_inplace<K>(v);
+                if (a.coef_out) {
+                    float* cdst = a.coef_out + (size_t)grp * K * NF;
+                    haar_for_each<K>([&](int m, int sl) { cdst[m * NF + tid] = v[sl]; });
+                }
+                haar_for_each<K>([&](int m, int sl) {
+                    const float d = fabsf(v[sl]) - a.tau32;
+                    if (fabsf(d) <= delta) bandb |= 1u << m;
+                    else if (d >= 0.f) keepb |= 1u << m;
+                });
+                anyb = __ballot_sync(0xffffffffu, bandb != 0u);
+                if (!anyb) {
+                    keep_finish(keepb);
+                    haar_for_each<K>([&](int m, int sl) {
+                        if (!((keepb >> m) & 1u)) v[sl] = 0.f;
+                    });
+                    haar_inv_inplace<K>(v);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = v[k];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = v[k];    // park the coefficients
+                }
             }
+            if (anyb) {                                   // warp-uniform
+                __syncwarp();
+                do {
+                    const int l = __ffs(anyb) - 1;
+                    anyb &= anyb - 1;
+                    uint32_t bb = __shfl_sync(0xffffffffu, bandb, l);
+                    while (bb) {
+                        const int m = __ffs(bb) - 1;
+                        bb &= bb - 1;
+                        const bool keep =
+                            refine_keep<K, C, Tin>(m, warp * 32 + l, img_s, FW, pos, a.basis64, a.tau64, lane);
+                        if (lane == l && keep) keepb |= 1u << m;
+                    }
+                } while (anyb);
+                __syncwarp();
+                keep_finish(keepb);
+                float w[K];
 #pragma unroll
-            for (int m = 0; m < K; ++m)
-                if (!((keepb >> m) & 1u)) co[m] = 0.f;
-            float rec[K];
-            haar_inv<K>(co, rec);
+                for (int k = 0; k < K; ++k) w[k] = gbq[k * G::GS + foff];
+                haar_for_each<K>([&](int m, int sl) {
+                    if (!((keepb >> m) & 1u)) w[sl] = 0.f;
+                });
+                haar_inv_inplace<K>(w);
 #pragma unroll
-            for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = rec[k];
+                for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = w[k];
+            }
         }
         __syncthreads();
         // ---- D, E: inverse projection; positions and counters of the next group
