@@ -10,12 +10,21 @@ namespace htsvd {
 
 namespace {
 
+// Two doubles as one vector value (GCC vector extension: SIMD on any target, no intrinsics).
+typedef double v2d __attribute__((vector_size(16)));
+inline v2d ld2(const double* p) {
+    v2d r;
+    __builtin_memcpy(&r, p, sizeof(r));
+    return r;
+}
+inline void st2(double* p, v2d x) { __builtin_memcpy(p, &x, sizeof(x)); }
+
 // A (n x n, row-major, symmetric; only the lower triangle i >= j is read and overwritten)
 // -> diagonal d[n], off-diagonal e[n-1]. Step k reflects the trailing block B = A[k+1:, k+1:]
 // with H = I - beta v v^T (H x = alpha e_1 for x = A[k+1:, k]): p = beta B v,
 // w = p - (beta/2)(v^T p) v, B <- B - v w^T - w v^T. The rank-2 update of step k is deferred
 // and applied to each row of the trailing triangle in the same pass that forms p of step k+1,
-// so the triangle is read and written once per step.
+// so the triangle is read and written once per step; the pass runs on two-double vectors.
 void tridiagonalize(double* A, int n, double* d, double* e) {
     std::vector<double> vb(n, 0.0), wb(n, 0.0), v(n), p(n);     // (vb, wb): deferred update, absolute indices
     bool pending = false;
@@ -50,39 +59,42 @@ void tridiagonalize(double* A, int n, double* d, double* e) {
         for (int i = 0; i < m; ++i) {
             double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
             const double vi = v[i], voi = vo[i], woi = wo[i];
-            double s0 = 0.0, s1 = 0.0;                            // two partial sums: two dependency chains
+            const v2d VI = {vi, vi}, VOI = {voi, voi}, WOI = {woi, woi};
+            v2d S0 = {0.0, 0.0}, S1 = {0.0, 0.0};                // four partial sums of the dot product
+            double s = 0.0;
             int j = 0;
             if (pending) {
-                for (; j + 2 <= i; j += 2) {
-                    const double r0 = row[j] - (voi * wo[j] + woi * vo[j]);
-                    const double r1 = row[j + 1] - (voi * wo[j + 1] + woi * vo[j + 1]);
-                    row[j] = r0;
-                    row[j + 1] = r1;
-                    s0 += r0 * v[j];
-                    s1 += r1 * v[j + 1];
-                    p[j] += r0 * vi;
-                    p[j + 1] += r1 * vi;
+                for (; j + 4 <= i; j += 4) {
+                    const v2d r0 = ld2(row + j) - (VOI * ld2(wo + j) + WOI * ld2(vo + j));
+                    const v2d r1 = ld2(row + j + 2) - (VOI * ld2(wo + j + 2) + WOI * ld2(vo + j + 2));
+                    st2(row + j, r0);
+                    st2(row + j + 2, r1);
+                    S0 += r0 * ld2(v.data() + j);
+                    S1 += r1 * ld2(v.data() + j + 2);
+                    st2(p.data() + j, ld2(p.data() + j) + r0 * VI);
+                    st2(p.data() + j + 2, ld2(p.data() + j + 2) + r1 * VI);
                 }
                 for (; j < i; ++j) {
                     const double r0 = row[j] - (voi * wo[j] + woi * vo[j]);
                     row[j] = r0;
-                    s0 += r0 * v[j];
+                    s += r0 * v[j];
                     p[j] += r0 * vi;
                 }
                 row[i] -= voi * wo[i] + woi * vo[i];
             } else {
-                for (; j + 2 <= i; j += 2) {
-                    s0 += row[j] * v[j];
-                    s1 += row[j + 1] * v[j + 1];
-                    p[j] += row[j] * vi;
-                    p[j + 1] += row[j + 1] * vi;
+                for (; j + 4 <= i; j += 4) {
+                    const v2d r0 = ld2(row + j), r1 = ld2(row + j + 2);
+                    S0 += r0 * ld2(v.data() + j);
+                    S1 += r1 * ld2(v.data() + j + 2);
+                    st2(p.data() + j, ld2(p.data() + j) + r0 * VI);
+                    st2(p.data() + j + 2, ld2(p.data() + j + 2) + r1 * VI);
                 }
                 for (; j < i; ++j) {
-                    s0 += row[j] * v[j];
+                    s += row[j] * v[j];
                     p[j] += row[j] * vi;
                 }
             }
-            p[i] += (s0 + s1) + row[i] * vi;
+            p[i] += (((S0[0] + S0[1]) + (S1[0] + S1[1])) + s) + row[i] * vi;
         }
         double vp = 0.0;
         for (int i = 0; i < m; ++i) {
