@@ -56,7 +56,7 @@ __host__ __device__ inline FLayout f_layout(int FH, int FW, int in_bytes, int mo
     using G = FCfg<C>;
     FLayout L;
     int o = 0;
-    L.off_bas = o; o += 512 * 4;
+    L.off_bas = o; o += 2 * 384 * 4;           // basis rows, then the transposed copies
     L.off_gb = o; o += K * G::GS * 4;
     L.off_pos = o; o += 64 * 4;
     L.off_band = o; o += 192 * 4;
@@ -76,7 +76,7 @@ __host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes) {
     using G = FCfg<C>;
     FLayout L;
     int o = 0;
-    L.off_bas = o; o += 512 * 4;
+    L.off_bas = o; o += 2 * 384 * 4;           // basis rows, then the transposed copies
     L.off_gb = o; o += 2 * K * G::GS * 4;
     L.off_pos = o; o += 2 * 64 * 4;
     L.off_band = o;
@@ -367,7 +367,21 @@ __device__ __forceinline__ void stage_b(const float* bas, float* gb, int k, int 
     for (int q = 0; q < G::RWF / 4; ++q) row[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
 }
 
+// Copies the packed FP32 basis into shared memory, followed by the transpose of each 8x8 block
+// (at NBAS): stages D and E read the bases by columns, as outer products.
+template <int C>
+__device__ __forceinline__ void stage_basis(const float* __restrict__ src, float* bas, int tid) {
+    using G = FCfg<C>;
+    for (int t = tid; t < G::NBAS; t += FT_THREADS) {
+        const float x = src[t];
+        bas[t] = x;
+        bas[G::NBAS + (t & ~63) + (t & 7) * PS + ((t >> 3) & 7)] = x;
+    }
+}
+
 // Stage D: thread (i, k): channel DFT, Z_f[i, :] = T_f[i, :] V_f^H, in place on row i of patch k.
+// Outer-product order (column j of T_f times row j of the transposed basis) keeps 3 x 8
+// independent accumulators; each output sums its terms in the same order as a dot product.
 template <int C>
 __device__ __forceinline__ void stage_d(const float* bas, float* gb, int k, int i) {
     using G = FCfg<C>;
@@ -378,39 +392,41 @@ __device__ __forceinline__ void stage_d(const float* bas, float* gb, int k, int 
         float4 v = row[q];
         t[4 * q] = v.x; t[4 * q + 1] = v.y; t[4 * q + 2] = v.z; t[4 * q + 3] = v.w;
     }
+    const float* bt = bas + G::NBAS;          // transposed blocks
     float o[G::RWF];
     if constexpr (C == 3) {
-        float T0[PS], T1r[PS], T1i[PS];
+        float z0[PS], zr[PS], zi[PS];
+#pragma unroll
+        for (int b = 0; b < PS; ++b) z0[b] = zr[b] = zi[b] = 0.f;
 #pragma unroll
         for (int j = 0; j < PS; ++j) {
-            T0[j] = t[3 * j] + t[3 * j + 1] + t[3 * j + 2];
-            T1r[j] = t[3 * j] - 0.5f * (t[3 * j + 1] + t[3 * j + 2]);
-            T1i[j] = F_S3H * (t[3 * j + 2] - t[3 * j + 1]);
+            const float T0 = t[3 * j] + t[3 * j + 1] + t[3 * j + 2];
+            const float T1r = t[3 * j] - 0.5f * (t[3 * j + 1] + t[3 * j + 2]);
+            const float T1i = F_S3H * (t[3 * j + 2] - t[3 * j + 1]);
+            float v0[8], vr[8], vi[8];                // column j of V_0, V_1 (re, im)
+            load8(bt + 192 + j * PS, v0);
+            load8(bt + 256 + j * PS, vr);
+            load8(bt + 320 + j * PS, vi);
+#pragma unroll
+            for (int b = 0; b < PS; ++b) {
+                z0[b] = fmaf(T0, v0[b], z0[b]);
+                zr[b] = fmaf(T1r, vr[b], fmaf(T1i, vi[b], zr[b]));
+                zi[b] = fmaf(T1i, vr[b], fmaf(-T1r, vi[b], zi[b]));
+            }
         }
 #pragma unroll
         for (int b = 0; b < PS; ++b) {
-            float v0[8], vr[8], vi[8];
-            load8(bas + 192 + b * PS, v0);
-            load8(bas + 256 + b * PS, vr);
-            load8(bas + 320 + b * PS, vi);
-            float z0 = 0.f, zr = 0.f, zi = 0.f;
-#pragma unroll
-            for (int j = 0; j < PS; ++j) {
-                z0 = fmaf(T0[j], v0[j], z0);
-                zr = fmaf(T1r[j], vr[j], fmaf(T1i[j], vi[j], zr));
-                zi = fmaf(T1i[j], vr[j], fmaf(-T1r[j], vi[j], zi));
-            }
-            o[3 * b] = z0; o[3 * b + 1] = zr; o[3 * b + 2] = zi;
+            o[3 * b] = z0[b]; o[3 * b + 1] = zr[b]; o[3 * b + 2] = zi[b];
         }
     } else {
 #pragma unroll
-        for (int b = 0; b < PS; ++b) {
-            float v0[8];
-            load8(bas + 64 + b * PS, v0);
-            float z = 0.f;
+        for (int b = 0; b < PS; ++b) o[b] = 0.f;
 #pragma unroll
-            for (int j = 0; j < PS; ++j) z = fmaf(t[j], v0[j], z);
-            o[b] = z;
+        for (int j = 0; j < PS; ++j) {
+            float v0[8];
+            load8(bt + 64 + j * PS, v0);
+#pragma unroll
+            for (int b = 0; b < PS; ++b) o[b] = fmaf(t[j], v0[b], o[b]);
         }
     }
 #pragma unroll
@@ -418,48 +434,50 @@ __device__ __forceinline__ void stage_d(const float* bas, float* gb, int k, int 
 }
 
 // Stage E: thread (k, b): G_f[:, b] = U_f Z_f[:, b], inverse channel DFT, in place on column b of patch k.
+// Outer-product order as in stage D.
 template <int C>
 __device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int b) {
     using G = FCfg<C>;
     float* col = gb + k * G::GS + b * C;
+    const float* bt = bas + G::NBAS;
     if constexpr (C == 3) {
-        float Z0[PS], Zr[PS], Zi[PS];
+        float g0[PS], gr[PS], gi[PS];
+#pragma unroll
+        for (int a = 0; a < PS; ++a) g0[a] = gr[a] = gi[a] = 0.f;
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
-            Z0[i] = col[i * G::ROW];
-            Zr[i] = col[i * G::ROW + 1];
-            Zi[i] = col[i * G::ROW + 2];
+            const float Z0 = col[i * G::ROW], Zr = col[i * G::ROW + 1], Zi = col[i * G::ROW + 2];
+            float u0[8], ur[8], ui[8];                // column i of U_0, U_1 (re, im)
+            load8(bt + i * PS, u0);
+            load8(bt + 64 + i * PS, ur);
+            load8(bt + 128 + i * PS, ui);
+#pragma unroll
+            for (int a = 0; a < PS; ++a) {
+                g0[a] = fmaf(u0[a], Z0, g0[a]);
+                gr[a] = fmaf(ur[a], Zr, fmaf(-ui[a], Zi, gr[a]));
+                gi[a] = fmaf(ur[a], Zi, fmaf(ui[a], Zr, gi[a]));
+            }
         }
 #pragma unroll
         for (int a = 0; a < PS; ++a) {
-            float u0[8], ur[8], ui[8];
-            load8(bas + a * PS, u0);
-            load8(bas + 64 + a * PS, ur);
-            load8(bas + 128 + a * PS, ui);
-            float g0 = 0.f, gr = 0.f, gi = 0.f;
-#pragma unroll
-            for (int i = 0; i < PS; ++i) {
-                g0 = fmaf(u0[i], Z0[i], g0);
-                gr = fmaf(ur[i], Zr[i], fmaf(-ui[i], Zi[i], gr));
-                gi = fmaf(ur[i], Zi[i], fmaf(ui[i], Zr[i], gi));
-            }
-            col[a * G::ROW + 0] = (g0 + 2.f * gr) * F_THIRD;
-            col[a * G::ROW + 1] = (g0 - gr - F_SQ3 * gi) * F_THIRD;
-            col[a * G::ROW + 2] = (g0 - gr + F_SQ3 * gi) * F_THIRD;
+            col[a * G::ROW + 0] = (g0[a] + 2.f * gr[a]) * F_THIRD;
+            col[a * G::ROW + 1] = (g0[a] - gr[a] - F_SQ3 * gi[a]) * F_THIRD;
+            col[a * G::ROW + 2] = (g0[a] - gr[a] + F_SQ3 * gi[a]) * F_THIRD;
         }
     } else {
-        float Z[PS];
+        float g0[PS];
 #pragma unroll
-        for (int i = 0; i < PS; ++i) Z[i] = col[i * G::ROW];
+        for (int a = 0; a < PS; ++a) g0[a] = 0.f;
 #pragma unroll
-        for (int a = 0; a < PS; ++a) {
+        for (int i = 0; i < PS; ++i) {
+            const float Z = col[i * G::ROW];
             float u0[8];
-            load8(bas + a * PS, u0);
-            float g0 = 0.f;
+            load8(bt + i * PS, u0);
 #pragma unroll
-            for (int i = 0; i < PS; ++i) g0 = fmaf(u0[i], Z[i], g0);
-            col[a * G::ROW] = g0;
+            for (int a = 0; a < PS; ++a) g0[a] = fmaf(u0[a], Z, g0[a]);
         }
+#pragma unroll
+        for (int a = 0; a < PS; ++a) col[a * G::ROW] = g0[a];
     }
 }
 
@@ -487,7 +505,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     float* acc = reinterpret_cast<float*>(smem + L.off_acc);
     Tin* img_s = reinterpret_cast<Tin*>(smem + L.off_img);
 
-    for (int t = tid; t < G::NBAS; t += FT_THREADS) bas[t] = a.basis32[t];
+    stage_basis<C>(a.basis32, bas, tid);
     {
         const Tin* img = reinterpret_cast<const Tin*>(a.img);
         const int rowb = FW * C;
@@ -640,21 +658,30 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         if (a.w_in) wg = a.w_in[grp];
         else if (a.agg_mode == 1) wg = 1.f / (float)max(1, misc[1]);
         if (tid == 0 && a.weights_out) a.weights_out[grp] = wg;
-#pragma unroll 1
-        for (int k = 0; k < K; ++k) {
-            const int py = pos[2 * k], px = pos[2 * k + 1];
-            const int i = (warp - py) & 7;
-            float* ap = acc + ((py + i) * FW + px) * G::ACC;
-            if constexpr (C == 3) {
-                if (lane < 24) {
-                    const int j = lane / 3, c = lane - 3 * (lane / 3);
-                    ap[j * 4 + c] += wg * gbq[k * G::GS + i * G::ROW + lane];
-                } else {
-                    ap[(lane - 24) * 4 + 3] += wg;
+        {
+            // lane k precomputes, for patch k, the offsets of the row that this warp adds (its
+            // footprint row r has r % 8 == warp) in the accumulator and in the group buffer; the
+            // loop broadcasts them. Lane roles: C = 3: 24 numerator lanes (pixel j, channel c) and
+            // 8 weight lanes; C = 1: 8 and 8.
+            int my_aoff = 0, my_goff = 0;
+            if (lane < K) {
+                const int py = pos[2 * lane], px = pos[2 * lane + 1];
+                const int i = (warp - py) & 7;
+                my_aoff = ((py + i) * FW + px) * G::ACC;
+                my_goff = lane * G::GS + i * G::ROW;
+            }
+            constexpr int NV = PS * C;                // numerator lanes
+            const bool num = lane < NV, act = lane < NV + PS;
+            const int lofs = num ? (lane / C) * G::ACC + (lane % C) : (lane - NV) * G::ACC + C;
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) {
+                const int aoff = __shfl_sync(0xffffffffu, my_aoff, k);
+                const int goff = __shfl_sync(0xffffffffu, my_goff, k);
+                if (act) {
+                    const float x = num ? gbq[goff + lane] : 1.f;
+                    acc[aoff + lofs] += wg * x;
                 }
-            } else {
-                if (lane < 8) ap[lane * 2] += wg * gbq[k * G::GS + i * G::ROW + lane];
-                else if (lane < 16) ap[(lane - 8) * 2 + 1] += wg;
+                __syncwarp();                         // orders the read-modify-writes of patches k, k+1
             }
         }
         // ... overlapped with A, B(q+1) into the other buffer
@@ -713,7 +740,7 @@ __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile,
 
     // Stage the basis, the image footprint and clear the accumulator.
     if constexpr (MODE != FM_DENOM) {
-        for (int t = tid; t < G::NBAS; t += FT_THREADS) bas[t] = a.basis32[t];
+        stage_basis<C>(a.basis32, bas, tid);
         const Tin* img = reinterpret_cast<const Tin*>(a.img);
         const int rowb = FW * C;
         for (int t = tid; t < FH * rowb; t += FT_THREADS) {
