@@ -44,6 +44,7 @@ htsvd_status resolve(const htsvd_params* p, int C, Resolved& r) {
     r.tile = p->tile;
     r.max_wait = p->max_wait_cycles > 0 ? p->max_wait_cycles : (int64_t)1 << 34;
     if (p->stride < 0 || p->window < 0 || p->K < 0 || p->ps < 0) return HTSVD_ERR_INVALID_ARG;
+    if (p->tile < 0 || p->tile > 16) return HTSVD_ERR_INVALID_ARG;
     if (r.K < 2 || (r.K & (r.K - 1))) return HTSVD_ERR_INVALID_ARG;
     if (r.match_mode < 0 || r.match_mode > 3 || r.agg_mode < 0 || r.agg_mode > 1) return HTSVD_ERR_INVALID_ARG;
     if (r.ps != PS || r.K > 32 || r.win > 64) return HTSVD_ERR_UNSUPPORTED;
@@ -218,13 +219,30 @@ struct FilterTiling {
 };
 
 FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forced) {
-    // The largest tile whose shared memory lets two CTAs share an SM (228 KB, 1 KB reserved per CTA)
-    // and that still gives two tiles per SM; failing that, the largest that fits at all.
-    const int cands[] = {8, 6, 5, 4, 3, 2, 1};
-    FilterTiling fit2{}, fit1{};
-    bool have2 = false, have1 = false;
+    // Among the tiles whose shared memory lets two CTAs share an SM (228 KB, 1 KB reserved per
+    // CTA): the largest that still gives 8 waves of two CTAs per SM (the last, partial wave then
+    // costs little), else the largest with one such wave, else the largest that fits at all. A
+    // forced edge is taken as given if its shared memory fits a CTA (TR = 0 returned otherwise).
+    const int cands[] = {8, 7, 6, 5, 4, 3, 2, 1};
+    FilterTiling fit2{}, fit1{}, wave1{};
+    bool have2 = false, have1 = false, havew = false;
+    if (forced > 0) {
+        FilterTiling t{};
+        t.TR = forced;
+        t.ntx = (g.nrx + forced - 1) / forced;
+        t.nty = (g.nry + forced - 1) / forced;
+        t.FHmax = std::min(g.H, (forced - 1) * g.s + g.wny + PS - 1);
+        t.FWmax = std::min(g.W, (forced - 1) * g.s + g.wnx + PS - 1);
+        FilterArgs fa{};
+        fa.g = g;
+        fa.FHmax = t.FHmax;
+        fa.FWmax = t.FWmax;
+        fa.img_is_float = in_bytes == 4;
+        fa.mode = mode;
+        if (filter_smem_bytes(fa) > 227 * 1024) t.TR = 0;
+        return t;
+    }
     for (int TR : cands) {
-        if (forced > 0 && TR != forced) continue;
         FilterTiling t;
         t.TR = TR;
         t.ntx = (g.nrx + TR - 1) / TR;
@@ -238,15 +256,16 @@ FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forc
         fa.img_is_float = in_bytes == 4;
         fa.mode = mode;
         const size_t smem = filter_smem_bytes(fa);
-        if (forced > 0) return t;
         if (smem <= 112 * 1024) {
+            const int64_t tiles = (int64_t)t.ntx * t.nty;
             if (!have2) fit2 = t, have2 = true;
-            if ((int64_t)t.ntx * t.nty >= 2 * 152) return t;
+            if (tiles >= 8 * 2 * 152) return t;
+            if (tiles >= 2 * 152 && !havew) wave1 = t, havew = true;
         } else if (smem <= 200 * 1024 && !have1) {
             fit1 = t, have1 = true;
         }
     }
-    return have2 ? fit2 : fit1;
+    return havew ? wave1 : have2 ? fit2 : fit1;
 }
 
 void choose_bm_tiles(const Geo& g, int rstep, int& TRy, int& TRx) {
@@ -369,6 +388,7 @@ htsvd_status run_forward_filter(Workspace* w, const void* img, int is_float, con
                                 const int32_t* idx, const double* b64, const float* b32, double tau,
                                 const float* w_in, const htsvd_params* p, float* d_out, cudaStream_t s) {
     FilterTiling t = choose_filter_tiling(g, is_float ? 4 : 1, FM_FORWARD, r.tile);
+    if (t.TR == 0) return HTSVD_ERR_UNSUPPORTED;
     FilterArgs a{};
     a.img = img;
     a.img_is_float = is_float;
@@ -519,6 +539,7 @@ htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C
 
     // D = sum_g w_g Scatter_g 1
     FilterTiling td = choose_filter_tiling(g, 4, FM_DENOM, r.tile);
+    if (td.TR == 0) return HTSVD_ERR_UNSUPPORTED;
     FilterArgs a{};
     a.img = d_x;
     a.img_is_float = 1;
@@ -549,6 +570,7 @@ htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C
 
     // adjoint filter on r = gout / D with the masks of x
     FilterTiling ta = choose_filter_tiling(g, 4, FM_ADJOINT, r.tile);
+    if (ta.TR == 0) return HTSVD_ERR_UNSUPPORTED;
     a.mode = FM_ADJOINT;
     a.TR = ta.TR;
     a.ntx = ta.ntx;

@@ -64,6 +64,8 @@ def _call_denoise(H_, W_, C, params, ptr=1):
     ((40, 40, 3), dict(K=64), 2),              # K > 32 not built
     ((40, 40, 3), dict(window=65), 2),         # window > 64 not built
     ((9, 9, 1), dict(K=8, window=3), 1),       # fewer than K candidates in the window
+    ((40, 40, 3), dict(tile=17), 1),           # filter tile edge out of range
+    ((40, 40, 3), dict(tile=-1), 1),
 ])
 def test_invalid_arguments_are_rejected_on_the_host(shape, params, code):
     assert _call_denoise(*shape, params) == code

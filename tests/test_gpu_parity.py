@@ -82,12 +82,15 @@ def test_rgb512_parity_with_estimated_sigma():
     ((64, 70, 3), dict(ps=8, stride=5, window=17, K=4, match_mode="full"), 25.0),
     ((64, 48, 3), dict(ps=8, stride=3, window=15, K=16, agg_mode="sparsity"), 25.0),
     ((33, 40, 3), dict(ps=8, stride=1, window=7, K=2), 10.0),
+    ((61, 75, 3), dict(ps=8, stride=3, window=15, K=16, tile=7), 20.0),  # forced filter tiles (ragged)
+    ((47, 52, 1), dict(ps=8, stride=2, window=13, K=8, tile=3), 20.0),
 ])
 def test_small_images_parity(shape, prm, sigma):
     Hh, Ww, C = shape
     clean = synth.clean_image(Hh, Ww, C, 77)
     noisy = synth.add_gaussian(clean, sigma, 77)
-    r = O.denoise(noisy, sigma, prm, keep_masks=True)
+    # the filter tile is a launch choice of the GPU path: the oracle has no such parameter
+    r = O.denoise(noisy, sigma, {k: v for k, v in prm.items() if k != "tile"}, keep_masks=True)
     out, info = _compare(noisy, sigma, prm, r)
     if prm.get("agg_mode") == "sparsity":
         # w_g = 1 / max(1, #kept): the kept counts are integers and must agree exactly
