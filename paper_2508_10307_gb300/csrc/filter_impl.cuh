@@ -548,6 +548,24 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         }
     };
 
+    // Fibre of this thread in the C phase: thread (w, l) takes the w-th fibre (in patch-row order)
+    // whose group-buffer column falls on bank l, so the 32 fibres of a warp use 32 distinct banks
+    // (each bank holds NF/32 fibres: the rows start ROW words apart and cover RWF words).
+    int fib = -1, foff = 0;
+    if (tid < NF) {
+        for (int i = 0, cnt = 0; i < PS && fib < 0; ++i) {
+            const int e = (lane - G::ROW * i) & 31;
+            if (e < G::RWF) {
+                if (cnt == warp) fib = i * G::RWF + e;
+                ++cnt;
+            }
+        }
+        foff = (fib / G::RWF) * G::ROW + (fib % G::RWF);
+    }
+    auto clear_masks = [&](int q) {                     // mask words of group q, before its C phase
+        if (a.mask_out && tid < NBW) a.mask_out[(size_t)group_of(q) * NBW + tid] = 0u;
+    };
+    clear_masks(0);
     store_pos(fetch_idx(0), posb);
     if (tid < 32) miscb[tid] = 0;
     __syncthreads();
@@ -566,19 +584,17 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         // ---- C: Haar analysis, threshold (FP64 inside the guard band), synthesis
         // final keep decisions of the warp's fibres: optional mask output, kept count
         auto keep_finish = [&](uint32_t keepb) {
-            if (a.mask_out) {
+            if (a.mask_out) {                             // words cleared a phase earlier
                 uint32_t* mo = a.mask_out + (size_t)grp * NBW;
-#pragma unroll
-                for (int m = 0; m < K; ++m) {
-                    const uint32_t w = __ballot_sync(0xffffffffu, (keepb >> m) & 1u);
-                    if (lane == 0) mo[m * (NF / 32) + warp] = w;
+                for (uint32_t b = keepb; b; b &= b - 1) {
+                    const int m = __ffs(b) - 1;
+                    atomicOr(&mo[m * (NF / 32) + (fib >> 5)], 1u << (fib & 31));
                 }
             }
             const int wk = __reduce_add_sync(0xffffffffu, __popc(keepb));
             if (lane == 0) atomicAdd(&misc[1], wk);
         };
         if (tid < NF) {
-            const int foff = (tid / G::RWF) * G::ROW + (tid % G::RWF);
             const float nrm2 = sizeof(Tin) == 1 ? (float)misc[5] : __int_as_float(misc[2]);
             const float delta = a.band_rel * sqrtf(nrm2) + a.band_abs;
             // (the rare guard-band path finishes the fibre in a scope of its own, with a second
@@ -593,7 +609,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 haar_fwd_inplace<K>(v);
                 if (a.coef_out) {
                     float* cdst = a.coef_out + (size_t)grp * K * NF;
-                    haar_for_each<K>([&](int m, int sl) { cdst[m * NF + tid] = v[sl]; });
+                    haar_for_each<K>([&](int m, int sl) { cdst[m * NF + fib] = v[sl]; });
                 }
                 haar_for_each<K>([&](int m, int sl) {
                     const float d = fabsf(v[sl]) - a.tau32;
@@ -620,11 +636,11 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                     const int l = __ffs(anyb) - 1;
                     anyb &= anyb - 1;
                     uint32_t bb = __shfl_sync(0xffffffffu, bandb, l);
+                    const int fl = __shfl_sync(0xffffffffu, fib, l);
                     while (bb) {
                         const int m = __ffs(bb) - 1;
                         bb &= bb - 1;
-                        const bool keep =
-                            refine_keep<K, C, Tin>(m, warp * 32 + l, img_s, FW, pos, a.basis64, a.tau64, lane);
+                        const bool keep = refine_keep<K, C, Tin>(m, fl, img_s, FW, pos, a.basis64, a.tau64, lane);
                         if (lane == l && keep) keepb |= 1u << m;
                     }
                 } while (anyb);
@@ -651,6 +667,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         if (q + 1 < ngr) {
             store_pos(next_idx, posb + (buf ^ 1) * 64);
             if (tid < 16) miscb[(buf ^ 1) * 16 + tid] = 0;
+            clear_masks(q + 1);
         }
         __syncthreads();
         // ---- F(q): aggregation (warp `warp` owns footprint rows r with r % 8 == warp) ...

@@ -112,41 +112,52 @@ __global__ void __launch_bounds__(256) moments_batch_kernel(const BMArgs* __rest
 
 // Full second moment: CTA (bx, tile) accumulates a 64x64 tile of M over a chunk of references.
 // The patch values of 4 consecutive references are packed per 32-bit word ([u][ref/4]), so one
-// dp4a adds the products of 4 references; each thread owns a 4x4 block of the tile.
-constexpr int FM_CHUNK = 512;      // references per CTA (512 * 255^2 < 2^32)
-constexpr int FM_BATCH = 64;       // references staged at once
+// dp4a adds the products of 4 references; each thread owns a 4x4 block of the tile. M is
+// symmetric: only the tiles on and below the diagonal (tu >= tv) are formed, and readers use the
+// lower triangle u >= v.
+constexpr int FM_CHUNK_MAX = 16384;    // references per CTA at most (16384 * 255^2 < 2^32)
+constexpr int FM_BATCH = 64;           // references staged at once
 constexpr int FM_WPAD = FM_BATCH / 4 + 1;
 
-__global__ void __launch_bounds__(256) full_moment_kernel(const uint8_t* __restrict__ img, Geo g,
+template <int C>
+__global__ void __launch_bounds__(256) full_moment_kernel(const uint8_t* __restrict__ img, Geo g, int chunk,
                                                           unsigned long long* __restrict__ M,
                                                           unsigned long long* __restrict__ S) {
-    const int d = PS2 * g.C;
-    const int ntile = (d + 63) / 64;
-    const int tu = blockIdx.y / ntile, tv = blockIdx.y % ntile;
+    constexpr int d = PS2 * C;
+    constexpr int ROWB = PS * C;                 // bytes of one patch row
+    int tu = 0, tv = blockIdx.y;                 // blockIdx.y -> (tu, tv), tu >= tv, row-major
+    while (tv > tu) {
+        tv -= tu + 1;
+        ++tu;
+    }
     __shared__ uint32_t pk[3 * PS2][FM_WPAD];
     const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
     uint32_t acc[4][4] = {};
     uint32_t sacc = 0;
     const int N = g.ngroups();
-    const int r0 = blockIdx.x * FM_CHUNK, r1 = min(r0 + FM_CHUNK, N);
+    const int r0 = blockIdx.x * chunk, r1 = min(r0 + chunk, N);
     for (int rb = r0; rb < r1; rb += FM_BATCH) {
         const int nb = min(FM_BATCH, r1 - rb);
         __syncthreads();
         // (reference j, patch row i): the row's 8*C bytes are contiguous in the image and land on
-        // entries u = i*8*C + b of the packed matrix
-        const int rowb = PS * g.C;
+        // entries u = i*8*C + b of the packed matrix (all loads of a row issued together)
         for (int t = threadIdx.x; t < FM_BATCH * PS; t += 256) {
             const int j = t >> 3, i = t & 7;
-            uint8_t* dst = reinterpret_cast<uint8_t*>(&pk[i * rowb][0]) + (j >> 2) * 4 + (j & 3);
+            uint8_t* dst = reinterpret_cast<uint8_t*>(&pk[i * ROWB][0]) + (j >> 2) * 4 + (j & 3);
+            uint8_t v[ROWB];
             if (j < nb) {
                 const int r = rb + j;
                 const int iy = r / g.nrx, ix = r - iy * g.nrx;
                 const int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
-                const uint8_t* src = img + ((size_t)(ry + i) * g.W + rx) * g.C;
-                for (int b = 0; b < rowb; ++b) dst[b * FM_WPAD * 4] = src[b];
+                const uint8_t* src = img + ((size_t)(ry + i) * g.W + rx) * C;
+#pragma unroll
+                for (int b = 0; b < ROWB; ++b) v[b] = src[b];
             } else {
-                for (int b = 0; b < rowb; ++b) dst[b * FM_WPAD * 4] = 0;
+#pragma unroll
+                for (int b = 0; b < ROWB; ++b) v[b] = 0;
             }
+#pragma unroll
+            for (int b = 0; b < ROWB; ++b) dst[b * FM_WPAD * 4] = v[b];
         }
         __syncthreads();
         const int nw = (nb + 3) >> 2;
@@ -611,8 +622,16 @@ cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long l
     if (e != cudaSuccess) return e;
     const int n = g.ngroups();
     const int nt = (d + 63) / 64;
-    dim3 grid((n + FM_CHUNK - 1) / FM_CHUNK, nt * nt);
-    full_moment_kernel<<<grid, 256, 0, s>>>(img, g, d_M, d_s);
+    const int ntiles = nt * (nt + 1) / 2;                       // tiles on and below the diagonal
+    // chunks of whole staging batches, about four CTAs per SM in total
+    int nchunk = (4 * 152 + ntiles - 1) / ntiles;
+    const int nbatch = (n + FM_BATCH - 1) / FM_BATCH;
+    if (nchunk > nbatch) nchunk = nbatch;
+    int chunk = (nbatch + nchunk - 1) / nchunk * FM_BATCH;
+    if (chunk > FM_CHUNK_MAX) chunk = FM_CHUNK_MAX;
+    dim3 grid((n + chunk - 1) / chunk, ntiles);
+    if (g.C == 3) full_moment_kernel<3><<<grid, 256, 0, s>>>(img, g, chunk, d_M, d_s);
+    else full_moment_kernel<1><<<grid, 256, 0, s>>>(img, g, chunk, d_M, d_s);
     return cudaGetLastError();
 }
 
