@@ -181,7 +181,9 @@ __device__ __forceinline__ bool refine_keep(int m, int e, const Tin* img_s, int 
         k0 = (m - (1 << l)) * L;
     }
     const int half = (m == 0) ? L : L / 2;
-    const double h = 1.0 / sqrt((double)L);
+    // 1/sqrt(L) for L = 2^e: a power of two, times 1/sqrt(2) when e is odd
+    const int e2 = 31 - __clz(L);
+    const double h = ldexp((e2 & 1) ? 0.70710678118654752440 : 1.0, -(e2 >> 1));
     const int pix = e / C, ch = e - pix * C;
     const int i = pix / PS, j = pix % PS;
     double s0 = 0.0, s1r = 0.0, s1i = 0.0;
@@ -195,9 +197,11 @@ __device__ __forceinline__ bool refine_keep(int m, int e, const Tin* img_s, int 
             int qi[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) qi[c] = 0;
-            for (int kk = k0; kk < k0 + L; kk += 2) {        // L is even: two independent loads per step
-                const Tin* s0p = img_s + ((pos[2 * kk] + aa) * FW + pos[2 * kk + 1] + bb) * C;
-                const Tin* s1p = img_s + ((pos[2 * kk + 2] + aa) * FW + pos[2 * kk + 3] + bb) * C;
+            // L is even and k0 a multiple of L: the positions of patches kk, kk+1 are one aligned int4
+            for (int kk = k0; kk < k0 + L; kk += 2) {
+                const int4 pp = *reinterpret_cast<const int4*>(pos + 2 * kk);
+                const Tin* s0p = img_s + ((pp.x + aa) * FW + pp.y + bb) * C;
+                const Tin* s1p = img_s + ((pp.z + aa) * FW + pp.w + bb) * C;
                 const bool p0 = kk - k0 < half, p1 = kk + 1 - k0 < half;
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
@@ -245,7 +249,9 @@ __device__ __forceinline__ bool refine_keep(int m, int e, const Tin* img_s, int 
     double S;
     if constexpr (C == 3) {
         const double sq3 = sqrt(3.0);
-        S = (ch == 0) ? (s0 + 2.0 * s1r) / 3.0 : (ch == 1) ? (s0 - s1r - sq3 * s1i) / 3.0 : (s0 - s1r + sq3 * s1i) / 3.0;
+        const double third = 1.0 / 3.0;
+        S = (ch == 0) ? (s0 + 2.0 * s1r) * third : (ch == 1) ? (s0 - s1r - sq3 * s1i) * third
+                                                              : (s0 - s1r + sq3 * s1i) * third;
     } else {
         S = s0;
     }
