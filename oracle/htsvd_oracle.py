@@ -44,6 +44,10 @@ Readings where the paper is silent or ambiguous (each is listed in the design doc):
      sigma by beta.
   R12 float inputs: matching, bases and sigma use q = clip(rint(x)); the
      transforms use x.
+  R15 A-Haar-tSVD (Alg. 2) subimages: each axis of length n is cut into
+     t = max(1, floor(n / n_sub)) parts with boundaries floor(i n / t), so every
+     subimage is at least n_sub long; each subimage gets its own noise estimate
+     (R10, with R11 when adapt is set) and is denoised on its own (Alg. 1).
 
 Parity pins for every function are in tests/test_oracle_pins.py.
 """
@@ -551,3 +555,31 @@ def estimate_sigma(x: np.ndarray, params=None, return_details=False):
             sigma = sigma / p.beta
         det.update(ranks=np.array(ranks), low=low, high=high)
     return (sigma, det) if return_details else sigma
+
+
+# --------------------------------------------------------------------------- A-Haar-tSVD (Alg. 2)
+
+def subimage_bounds(n: int, n_sub: int) -> list[tuple[int, int]]:
+    """Reading R15: t = max(1, floor(n / n_sub)) parts of one axis, boundaries floor(i n / t)."""
+    t = max(1, n // n_sub)
+    return [((i * n) // t, ((i + 1) * n) // t) for i in range(t)]
+
+
+def a_haar_tsvd(x: np.ndarray, sub_h: int, sub_w: int, params=None):
+    """Alg. 2 (A-Haar-tSVD) with the eigenvalue noise estimate (R10, R11) in place of the CNN:
+    Step 1 estimates sigma per subimage, Step 2 denoises each subimage with Alg. 1 at its sigma.
+    Returns (output (H, W, C) float64, per-subimage sigmas in row-major subimage order)."""
+    p = Params.of(params)
+    if x.ndim == 2:
+        x = x[:, :, None]
+    H, Wd, C = x.shape
+    out = np.zeros((H, Wd, C))
+    sigmas = []
+    for (y0, y1) in subimage_bounds(H, sub_h):
+        for (x0, x1) in subimage_bounds(Wd, sub_w):
+            sub = np.ascontiguousarray(x[y0:y1, x0:x1])
+            sg = estimate_sigma(sub, p)
+            sigmas.append(sg)
+            out[y0:y1, x0:x1] = denoise(sub, sg, p).out
+    return out, np.array(sigmas)
+

@@ -399,3 +399,40 @@ def test_frozen_map_gradients_match_central_differences():
         e[g] = h
         fd = (L(x, w + e) - L(x, w - e)) / (2 * h)
         assert abs(fd - gw[g]) < 1e-6 * max(1, abs(fd))
+
+
+# ---------------------------------------------------------------- A-Haar-tSVD (Alg. 2), reading R15
+
+@pytest.mark.parametrize("n,sub", [(100, 30), (64, 64), (50, 64), (129, 8), (512, 256)])
+def test_subimage_bounds_tile_the_axis(n, sub):
+    b = O.subimage_bounds(n, sub)
+    assert b[0][0] == 0 and b[-1][1] == n
+    assert all(b[i][1] == b[i + 1][0] for i in range(len(b) - 1))
+    assert len(b) == max(1, n // sub)
+    if n >= sub:
+        assert all(e - s >= sub for s, e in b)
+
+
+def test_a_haar_tsvd_single_subimage_is_alg1_with_estimated_sigma():
+    """With one subimage, Alg. 2 is Alg. 1 at the image's own estimate."""
+    x = synth.add_gaussian(synth.clean_image(40, 48, 3, 21), 15.0, 21)
+    p = dict(ps=8, stride=4, window=9, K=8, adapt=True)
+    out, sig = O.a_haar_tsvd(x, 64, 64, p)
+    s0 = O.estimate_sigma(x, p)
+    assert sig.shape == (1,) and sig[0] == s0
+    np.testing.assert_array_equal(out, O.denoise(x, s0, p).out)
+
+
+def test_a_haar_tsvd_estimates_each_subimage_on_its_own():
+    """Left half sigma 6, right half sigma 30: the two subimage estimates follow their own
+    noise, and each output half is Alg. 1 on that half alone at its estimate."""
+    clean = synth.clean_image(96, 192, 1, 22)
+    left = synth.add_gaussian(clean[:, :96], 6.0, 22)
+    right = synth.add_gaussian(clean[:, 96:], 30.0, 23)
+    x = np.ascontiguousarray(np.concatenate([left, right], axis=1))
+    p = dict(ps=8, stride=2, window=11, K=8)
+    out, sig = O.a_haar_tsvd(x, 96, 96, p)
+    assert sig.shape == (2,)
+    # (clipping to [0, 255] and the small sample bias the high-noise estimate low)
+    assert 4.0 < sig[0] < 8.5 and 20.0 < sig[1] < 36.0 and sig[1] > 3.0 * sig[0]
+    np.testing.assert_array_equal(out[:, 96:], O.denoise(np.ascontiguousarray(x[:, 96:]), sig[1], p).out)
