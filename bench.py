@@ -276,6 +276,22 @@ def make_workload(name):
 
         return Workload(name, cfg, 8 * 512 * 512 / 1e6, 8 * n, 3, 32, xs, step, 8 * 512 * 512 * 3 * 4,
                         forward_only, "forward_only"), None
+    if name == "adaptive512":
+        clean, noisy, _, prm = synth.workload_rgb512()
+        prm = dict(prm, adapt=True)
+        sub = (256, 256)
+        cfg = {"workload": "a_haar_tsvd_rgb512_sub256", "image": "512x512x3 uint8",
+               "noise": "poisson-gaussian a=0.01 b=15^2", "subimages": "2 x 2 of 256x256",
+               "sigma": "estimated per subimage (eigenvalue rule + eigen-rank vote)", "ps": 8, "stride": 2,
+               "window": 31, "K": 32, "form": "Alg. 2: one host sync, subimages denoised as one batch"}
+        n = H.num_groups(256, 256, prm) * 4
+
+        def plain(d):
+            return [H.denoise(d[0], None, dict(prm, adapt=False))]
+
+        return Workload(name, cfg, 512 * 512 / 1e6, n, 3, 32, [noisy],
+                        lambda d: [H.denoise_adaptive(d[0], sub, prm)], 512 * 512 * 3 * 4, plain,
+                        "plain_single_sigma"), clean
     raise ValueError(name)
 
 
@@ -417,7 +433,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="rgb512", choices=["rgb512", "gray128", "rgb4k", "batch64", "vjp8"])
+    ap.add_argument("--workload", default="rgb512", choices=["rgb512", "gray128", "rgb4k", "batch64", "vjp8", "adaptive512"])
     ap.add_argument("--cpu-rows", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-worker", type=int, default=None)

@@ -117,6 +117,21 @@ htsvd_status htsvd_denoise_f32(const float* d_x, int32_t H, int32_t W, int32_t C
 htsvd_status htsvd_estimate_sigma(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C,
                                   const htsvd_params* p, double* h_sigma, cudaStream_t stream);
 
+/* A-Haar-tSVD (Alg. 2), with the patch-covariance eigenvalue estimate (and, when p->adapt is
+ * set, the eigen-rank vote of Eq. (adjust noise level)) in place of the paper's CNN estimator.
+ * The uint8 image d_noisy (H x W x C, DEVICE) is cut into subimages: each axis of length n into
+ * t = max(1, n / n_sub) parts with boundaries floor(i n / t), so every part is at least n_sub
+ * long (sub_h, sub_w >= 1). Step 1 estimates sigma per subimage; Step 2 denoises every
+ * subimage on its own (Alg. 1, its own grouping, bases and threshold) at that sigma, all in one
+ * batched pass (htsvd_denoise_batch), and writes it into d_out (H x W x C float32, DEVICE).
+ * h_sigmas (HOST, may be NULL) receives the subimage sigmas in row-major subimage order.
+ * Synchronises `stream` once (host eigenvalue step). Errors: INVALID_ARG for a null pointer,
+ * sub_h or sub_w < 1, or a subimage that fails the checks of htsvd_denoise; optional outputs of p
+ * are ignored. */
+htsvd_status htsvd_denoise_adaptive(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, int32_t sub_h,
+                                    int32_t sub_w, const htsvd_params* p, float* d_out, double* h_sigmas,
+                                    cudaStream_t stream);
+
 /* Alg. 1 on n uint8 images of any sizes (one C for the whole batch) with per-image sigma
  * (>= 0). Each phase (moments, bases, grouping, filter, reduction) is one persistent launch
  * whose CTAs take (image, tile) work items from a queue over all images; the sequence is

@@ -11,8 +11,8 @@ from dataclasses import dataclass, fields
 
 from . import _lib
 
-__all__ = ["HtsvdParams", "denoise", "denoise_f32", "estimate_sigma", "denoise_batch", "denoise_vjp",
-           "num_groups", "HtsvdFn", "load_library"]
+__all__ = ["HtsvdParams", "denoise", "denoise_f32", "estimate_sigma", "denoise_batch", "denoise_adaptive",
+           "denoise_vjp", "num_groups", "HtsvdFn", "load_library"]
 
 _MATCH = {"auto": 0, "gcp": 1, "full": 2, "green": 3}
 _AGG = {"uniform": 0, "sparsity": 1}
@@ -190,6 +190,32 @@ def denoise_batch(images, sigmas, params=None, outs=None, stream=None):
     _lib.check(lib.htsvd_denoise_batch(arr, len(imgs), ctypes.byref(cp), _stream_ptr(stream)),
                "htsvd_denoise_batch")
     return outs
+
+
+def subimage_bounds(n: int, n_sub: int):
+    """Subimage boundaries of one axis used by denoise_adaptive: t = max(1, n // n_sub) parts,
+    boundaries floor(i n / t)."""
+    t = max(1, n // n_sub)
+    return [((i * n) // t, ((i + 1) * n) // t) for i in range(t)]
+
+
+def denoise_adaptive(noisy, sub=(256, 256), params=None, *, return_sigmas=False, stream=None):
+    """A-Haar-tSVD (Alg. 2) on a uint8 (H, W[, C]) CUDA tensor: per-subimage noise estimates
+    (eigenvalue rule; the eigen-rank vote when params.adapt) and per-subimage denoising.
+    Returns the float32 (H, W, C) estimate, and the subimage sigmas (row-major) if asked."""
+    lib = _lib.load()
+    torch = _torch()
+    x = _hwc(noisy)
+    if x.dtype != torch.uint8:
+        raise TypeError("denoise_adaptive expects uint8")
+    H, W, C = x.shape
+    cp = HtsvdParams.of(params).c()
+    out = torch.empty((H, W, C), dtype=torch.float32, device=x.device)
+    n = len(subimage_bounds(H, int(sub[0]))) * len(subimage_bounds(W, int(sub[1])))
+    sig = (ctypes.c_double * n)()
+    _lib.check(lib.htsvd_denoise_adaptive(_ptr(x), H, W, C, int(sub[0]), int(sub[1]), ctypes.byref(cp), _ptr(out),
+                                          sig, _stream_ptr(stream)), "htsvd_denoise_adaptive")
+    return (out, [float(v) for v in sig]) if return_sigmas else out
 
 
 def denoise_vjp(x, sigma, idx, w, out, grad_out, params=None, want_grad_w=True, stream=None):

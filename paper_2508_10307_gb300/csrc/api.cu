@@ -5,6 +5,7 @@
 #include <chrono>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <new>
 #include <vector>
 
@@ -73,7 +74,8 @@ int resolve_mode(const Resolved& r, int C) {
 // ----------------------------------------------------------------------------- workspace
 
 enum Slot {
-    S_IDX, S_MOM, S_B64, S_B32, S_PART, S_FULLM, S_FULLS, S_RANKS, S_IDX2, S_Q, S_DEN, S_R, S_TMP, S_NSLOT
+    S_IDX, S_MOM, S_B64, S_B32, S_PART, S_FULLM, S_FULLS, S_RANKS, S_IDX2, S_Q, S_DEN, S_R, S_TMP,
+    S_AIN, S_AOUT, S_NSLOT           // S_AIN, S_AOUT: subimages of htsvd_denoise_adaptive
 };
 
 struct Workspace {
@@ -334,17 +336,23 @@ htsvd_status run_basis(Workspace* w, const uint8_t* q, const Geo& g, double** b6
 
 // Launches what the estimate needs (full moment, optional sampled grouping and ranks) and
 // copies it to pinned host memory; *done is recorded after the copies.
-htsvd_status launch_sigma_inputs(Workspace* w, const uint8_t* q, const Geo& g, const Resolved& r, cudaStream_t s,
-                                 void** hbuf) {
+// Host bytes of the estimate's inputs: moment M (d x d), sums S (d), rank votes of the sampled groups.
+size_t sigma_host_bytes(const Geo& g) {
+    const int d = PS2 * g.C;
+    const int ny8 = (g.nry + 7) / 8, nx8 = (g.nrx + 7) / 8;
+    return sizeof(unsigned long long) * ((size_t)d * d + d) + sizeof(int32_t) * ny8 * nx8;
+}
+
+// Launches what the estimate needs (full moment, optional sampled grouping and ranks) and copies
+// it to the pinned host memory at h (sigma_host_bytes(g) bytes).
+htsvd_status enqueue_sigma_inputs(Workspace* w, const uint8_t* q, const Geo& g, const Resolved& r, cudaStream_t s,
+                                  unsigned long long* h) {
     const int d = PS2 * g.C;
     void *M, *S;
     ST(ws_get(w, S_FULLM, sizeof(unsigned long long) * d * d, &M));
     ST(ws_get(w, S_FULLS, sizeof(unsigned long long) * d, &S));
     { ProfScope ps_("full_moment", s); CK(launch_full_moment(q, g, (unsigned long long*)M, (unsigned long long*)S, s)); }
     const int ny8 = (g.nry + 7) / 8, nx8 = (g.nrx + 7) / 8;
-    const size_t hbytes = sizeof(unsigned long long) * (d * d + d) + sizeof(int32_t) * ny8 * nx8;
-    ST(ws_host(w, hbytes, hbuf));
-    unsigned long long* h = (unsigned long long*)*hbuf;
     CK(cudaMemcpyAsync(h, M, sizeof(unsigned long long) * d * d, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h + (size_t)d * d, S, sizeof(unsigned long long) * d, cudaMemcpyDeviceToHost, s));
     if (r.adapt) {
@@ -356,6 +364,12 @@ htsvd_status launch_sigma_inputs(Workspace* w, const uint8_t* q, const Geo& g, c
         CK(cudaMemcpyAsync(h + (size_t)d * d + d, ranks, sizeof(int32_t) * ny8 * nx8, cudaMemcpyDeviceToHost, s));
     }
     return HTSVD_OK;
+}
+
+htsvd_status launch_sigma_inputs(Workspace* w, const uint8_t* q, const Geo& g, const Resolved& r, cudaStream_t s,
+                                 void** hbuf) {
+    ST(ws_host(w, sigma_host_bytes(g), hbuf));
+    return enqueue_sigma_inputs(w, q, g, r, s, (unsigned long long*)*hbuf);
 }
 
 htsvd_status finish_sigma(const void* hbuf, const Geo& g, const Resolved& r, double* sigma) {
@@ -512,6 +526,99 @@ htsvd_status htsvd_estimate_sigma(const uint8_t* d_noisy, int32_t H, int32_t W, 
     ST(launch_sigma_inputs(w, d_noisy, g, r, stream, &hbuf));
     CK(cudaStreamSynchronize(stream));
     return finish_sigma(hbuf, g, r, h_sigma);
+}
+
+htsvd_status htsvd_denoise_adaptive(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, int32_t sub_h,
+                                    int32_t sub_w, const htsvd_params* p, float* d_out, double* h_sigmas,
+                                    cudaStream_t s) {
+    if (!d_noisy || !d_out || sub_h < 1 || sub_w < 1) return HTSVD_ERR_INVALID_ARG;
+    Resolved r;
+    ST(resolve(p, C, r));
+    ST(check_image(H, W, C, r));
+    // subimage bounds per axis: t = max(1, n / n_sub) parts, boundaries floor(i n / t)
+    auto bounds = [](int n, int sub) {
+        const int t = std::max(1, n / sub);
+        std::vector<int> b(t + 1);
+        for (int i = 0; i <= t; ++i) b[i] = (int)(((int64_t)i * n) / t);
+        return b;
+    };
+    const std::vector<int> by = bounds(H, sub_h), bx = bounds(W, sub_w);
+    const int ny = (int)by.size() - 1, nx = (int)bx.size() - 1, n = ny * nx;
+    struct Tile {
+        int y0, x0, h, w;
+        Geo g;
+        size_t in_off, out_off, h_off;
+    };
+    std::vector<Tile> tiles(n);
+    size_t in_bytes = 0, out_bytes = 0, h_bytes = 0;
+    for (int t = 0; t < n; ++t) {
+        Tile& T = tiles[t];
+        T.y0 = by[t / nx];
+        T.x0 = bx[t % nx];
+        T.h = by[t / nx + 1] - T.y0;
+        T.w = bx[t % nx + 1] - T.x0;
+        ST(check_image(T.h, T.w, C, r));
+        T.g = make_geo(T.h, T.w, C, r.s, r.win, r.K);
+        T.in_off = in_bytes;
+        T.out_off = out_bytes;
+        T.h_off = h_bytes;
+        in_bytes += ((size_t)T.h * T.w * C + 255) & ~(size_t)255;
+        out_bytes += (sizeof(float) * T.h * T.w * C + 255) & ~(size_t)255;
+        h_bytes += (sigma_host_bytes(T.g) + 15) & ~(size_t)15;
+    }
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    void *vin, *vout, *vh;
+    ST(ws_get(w, S_AIN, in_bytes, &vin));
+    ST(ws_get(w, S_AOUT, out_bytes, &vout));
+    ST(ws_host(w, h_bytes, &vh));
+    uint8_t* tin = (uint8_t*)vin;
+    unsigned char* tout = (unsigned char*)vout;
+    unsigned char* hb = (unsigned char*)vh;
+    // Step 1 (Alg. 2): copy each subimage out and launch the inputs of its noise estimate
+    for (const Tile& T : tiles) {
+        CK(cudaMemcpy2DAsync(tin + T.in_off, (size_t)T.w * C, d_noisy + ((size_t)T.y0 * W + T.x0) * C, (size_t)W * C,
+                             (size_t)T.w * C, T.h, cudaMemcpyDeviceToDevice, s));
+        ST(enqueue_sigma_inputs(w, tin + T.in_off, T.g, r, s, (unsigned long long*)(hb + T.h_off)));
+    }
+    CK(cudaStreamSynchronize(s));
+    // host eigenvalue problems of the subimages are independent: a few threads share them
+    std::vector<double> sig(n, 0.0);
+    std::vector<htsvd_status> st(n, HTSVD_OK);
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int nth = std::max(1, std::min(n, (int)std::min(8u, hw > 1 ? hw / 2 : 1u)));
+        auto work = [&](int k) {
+            for (int t = k; t < n; t += nth) st[t] = finish_sigma(hb + tiles[t].h_off, tiles[t].g, r, &sig[t]);
+        };
+        std::vector<std::thread> th;
+        try {
+            for (int k = 1; k < nth; ++k) th.emplace_back(work, k);
+        } catch (...) {
+        }
+        work(0);
+        for (int k = 1; k < nth; ++k)
+            if (k - 1 >= (int)th.size()) work(k);
+        for (auto& x : th) x.join();
+    }
+    for (int t = 0; t < n; ++t) ST(st[t]);
+    if (h_sigmas)
+        for (int t = 0; t < n; ++t) h_sigmas[t] = sig[t];
+    // Step 2: all subimages in one batched pass, each at its own sigma; then back into place
+    std::vector<htsvd_image> imgs(n);
+    for (int t = 0; t < n; ++t) {
+        imgs[t].d_in = tin + tiles[t].in_off;
+        imgs[t].H = tiles[t].h;
+        imgs[t].W = tiles[t].w;
+        imgs[t].C = C;
+        imgs[t].sigma = sig[t];
+        imgs[t].d_out = (float*)(tout + tiles[t].out_off);
+    }
+    ST(htsvd_denoise_batch(imgs.data(), n, p, s));
+    for (const Tile& T : tiles)
+        CK(cudaMemcpy2DAsync(d_out + ((size_t)T.y0 * W + T.x0) * C, sizeof(float) * W * C, tout + T.out_off,
+                             sizeof(float) * T.w * C, sizeof(float) * T.w * C, T.h, cudaMemcpyDeviceToDevice, s));
+    return HTSVD_OK;
 }
 
 htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C, double sigma,

@@ -73,3 +73,19 @@ def test_invalid_arguments_are_rejected_on_the_host(shape, params, code):
 
 def test_null_pointers_rejected():
     assert _call_denoise(40, 40, 3, dict(), ptr=0) == 1
+
+
+def test_adaptive_rejects_bad_subimage_sizes_on_the_host():
+    lib = H.load_library()
+    cp = H.HtsvdParams().c()
+    for sub_h, sub_w in ((0, 16), (16, 0), (-3, 16)):
+        assert lib.htsvd_denoise_adaptive(ctypes.c_void_p(1), 64, 64, 3, sub_h, sub_w, ctypes.byref(cp),
+                                          ctypes.c_void_p(1), None, None) == 1
+    assert lib.htsvd_denoise_adaptive(None, 64, 64, 3, 32, 32, ctypes.byref(cp), ctypes.c_void_p(1), None,
+                                      None) == 1
+
+
+@pytest.mark.parametrize("n,sub", [(512, 256), (100, 30), (50, 64), (129, 8), (2160, 256)])
+def test_subimage_bounds_match_the_oracle_reading(n, sub):
+    from oracle import htsvd_oracle as O
+    assert H.subimage_bounds(n, sub) == O.subimage_bounds(n, sub)
