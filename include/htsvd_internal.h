@@ -7,6 +7,7 @@
 #define HTSVD_INTERNAL_H
 
 #include <stdint.h>
+#include "htsvd.h"
 
 #ifdef __cplusplus
 extern "C" {
@@ -36,6 +37,14 @@ int htsvd_internal_basis(const unsigned long long* d_mom, int C, double* d_b64, 
  * argument or if the iteration did not converge. */
 double htsvd_internal_sigma_from_moments(const unsigned long long* M, const unsigned long long* S, int d, int64_t n,
                                          double* lam);
+
+/* DEVICE + HOST: the eigen-rank vote inputs of Sec. III-D for a uint8 image (d_img, DEVICE):
+ * grouping of every 8th reference per axis, then for each such group the rank
+ * a = 1 + #{f : lambda_f < lambda_{K/2}} of its circulant eigenvalues, written row-major to
+ * h_ranks (HOST, max_ranks entries). Synchronises the device. Returns the number of groups, or
+ * -1 on a bad argument, too small an array or a CUDA error. */
+int32_t htsvd_internal_sampled_ranks(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const htsvd_params* p,
+                                     int32_t* h_ranks, int32_t max_ranks);
 
 #ifdef __cplusplus
 }

@@ -496,6 +496,25 @@ htsvd_status denoise_impl(const void* d_in, int is_float, int H, int W, int C, d
 
 extern "C" {
 
+int32_t htsvd_internal_sampled_ranks(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const htsvd_params* p,
+                                     int32_t* h_ranks, int32_t max_ranks) {
+    Resolved r;
+    if (!d_img || !h_ranks || resolve(p, C, r) != HTSVD_OK || check_image(H, W, C, r) != HTSVD_OK) return -1;
+    const Geo g = make_geo(H, W, C, r.s, r.win, r.K);
+    const int ny8 = (g.nry + 7) / 8, nx8 = (g.nrx + 7) / 8, n = ny8 * nx8;
+    if (n > max_ranks) return -1;
+    Workspace* w = workspace_for(nullptr);
+    if (!w) return -1;
+    void *idx2, *ranks;
+    if (ws_get(w, S_IDX2, sizeof(int32_t) * n * g.K, &idx2) != HTSVD_OK ||
+        ws_get(w, S_RANKS, sizeof(int32_t) * n, &ranks) != HTSVD_OK)
+        return -1;
+    if (run_block_match(d_img, g, r, 8, (int32_t*)idx2, nullptr) != HTSVD_OK) return -1;
+    if (launch_group_rank(d_img, g, (const int32_t*)idx2, n, (int32_t*)ranks, nullptr) != cudaSuccess) return -1;
+    if (cudaMemcpy(h_ranks, ranks, sizeof(int32_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    return n;
+}
+
 double htsvd_internal_sigma_from_moments(const unsigned long long* M, const unsigned long long* S, int d, int64_t n,
                                          double* lam) {
     if (!M || !S || d < 1 || n < 1) return -1.0;

@@ -513,15 +513,23 @@ __global__ void quantize_kernel(const float* __restrict__ x, int64_t n, uint8_t*
 
 // lambda_f = || sum_m p_m exp(-2 pi i f m / K) ||^2 over the full-channel patch vectors of a
 // group (the eigenvalues of circ(G) circ(G)^T), then the rank of lambda_{K/2}. FP64, one CTA per group.
+// Rank of lambda_{K/2} among the circulant eigenvalues lambda_f = sum_u |sum_m p_m[u] w^{-fm}|^2
+// of one sampled group (Sec. III-D; the group is real, so lambda_{K-f} = lambda_f and only
+// f = 0 .. K/2 are formed). lambda_{K/2} = sum_u (sum_m (-1)^m p_m[u])^2 is an exact integer. The
+// others are formed in FP32 together with an absolute error bound, and any lambda_f whose bound
+// reaches lambda_{K/2} is recomputed in FP64 before the comparison.
 __global__ void __launch_bounds__(256) group_rank_kernel(const uint8_t* __restrict__ img, Geo g,
                                                          const int32_t* __restrict__ idx,
                                                          int32_t* __restrict__ ranks) {
     const int grp = blockIdx.x;
     const int K = g.K;
     const int d = PS2 * g.C;
+    const int NFQ = K / 2 + 1;                  // f = 0 .. K/2
     __shared__ uint8_t pv[32][3 * PS2];
-    __shared__ double tc[32], ts[32];
-    __shared__ double part[256];
+    __shared__ float tcf[32], tsf[32];
+    __shared__ float lam32[17], bnd[17];
+    __shared__ unsigned long long half_sq;
+    __shared__ double lam64, tc64[32], ts64[32];
     for (int t = threadIdx.x; t < K * d; t += blockDim.x) {
         const int m = t / d, u = t - m * d;
         const int pix = u / g.C, c = u - pix * g.C;
@@ -530,39 +538,86 @@ __global__ void __launch_bounds__(256) group_rank_kernel(const uint8_t* __restri
         pv[m][u] = img[((size_t)(y + pix / PS) * g.W + x + pix % PS) * g.C + c];
     }
     if (threadIdx.x < K) {
-        double sn, cs;
-        sincospi(-2.0 * threadIdx.x / K, &sn, &cs);
-        tc[threadIdx.x] = cs;
-        ts[threadIdx.x] = sn;
+        float sn, cs;
+        sincospif(-2.0f * threadIdx.x / K, &sn, &cs);
+        tcf[threadIdx.x] = cs;
+        tsf[threadIdx.x] = sn;
     }
+    if (threadIdx.x < NFQ) lam32[threadIdx.x] = bnd[threadIdx.x] = 0.f;
+    if (threadIdx.x == 0) half_sq = 0ull;
     __syncthreads();
-    const int nsl = blockDim.x / K;
-    const int f = threadIdx.x % K, sl = threadIdx.x / K;
-    double s = 0.0;
-    if (sl < nsl)
-        for (int u = sl; u < d; u += nsl) {
-            double re = 0.0, im = 0.0;
-            for (int m = 0; m < K; ++m) {
-                const int k = (f * m) % K;
-                re += pv[m][u] * tc[k];
-                im += pv[m][u] * ts[k];
-            }
-            s += re * re + im * im;
+    const int lane = threadIdx.x & 31;
+    // exact lambda_{K/2}
+    {
+        unsigned long long acc = 0ull;
+        for (int u = threadIdx.x; u < d; u += blockDim.x) {
+            int a = 0;
+            for (int m = 0; m < K; ++m) a += (m & 1) ? -(int)pv[m][u] : (int)pv[m][u];
+            acc += (unsigned long long)((long long)a * a);
         }
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x < K) {
-        double tot = 0.0;
-        for (int q = 0; q < nsl; ++q) tot += part[q * K + threadIdx.x];
-        part[threadIdx.x] = tot;
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0 && acc) atomicAdd(&half_sq, acc);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int a = 1;
-        for (int ff = 0; ff < K; ++ff)
-            if (part[ff] < part[K / 2]) ++a;
-        ranks[grp] = a;
+    // FP32 lambda_f, f < K/2, and a bound on its error: |X| <= 255 K per entry, each of the K
+    // products and sums rounds by at most 2^-24 of that and the twiddle by 2^-24 of 255, so each
+    // of Re, Im is off by at most e = 2 K 255 K 2^-24; |X|^2 then by 2 sqrt(2) e |X| + 2 e^2.
+    // thread t: frequency t % (K/2), entries u = t / (K/2), + 256/(K/2), ... (partial sums per thread,
+    // one shared atomic per thread and frequency)
+    {
+        const float e = 2.f * K * 255.f * K * 5.9604645e-8f;
+        const int nf = NFQ - 1, f = threadIdx.x % nf, u0 = threadIdx.x / nf, du = blockDim.x / nf;
+        float lsum = 0.f, bsum = 0.f;
+        if (u0 < du)
+            for (int u = u0; u < d; u += du) {
+                float re = 0.f, im = 0.f;
+                for (int m = 0; m < K; ++m) {
+                    const int k = (f * m) & (K - 1);
+                    re = fmaf((float)pv[m][u], tcf[k], re);
+                    im = fmaf((float)pv[m][u], tsf[k], im);
+                }
+                const float mag2 = re * re + im * im;
+                lsum += mag2;
+                bsum += 2.8284272f * e * sqrtf(mag2) + 2.f * e * e + 1e-6f * mag2;
+            }
+        if (u0 < du) {
+            atomicAdd(&lam32[f], lsum);
+            atomicAdd(&bnd[f], bsum);
+        }
     }
+    if (threadIdx.x < K) sincospi(-2.0 * threadIdx.x / K, &ts64[threadIdx.x], &tc64[threadIdx.x]);
+    __syncthreads();
+    const double lh = (double)half_sq;
+    // count lambda_f < lambda_{K/2} over all K frequencies (f and K - f count twice)
+    int a = 1;
+    for (int f = 0; f < NFQ - 1; ++f) {
+        const int mult = (f == 0) ? 1 : 2;
+        // summing the (positive) terms of lambda_f in FP32 adds at most 2^-24 relative per term:
+        // 3e-5 covers the 192 terms with room to spare
+        const double l32 = (double)lam32[f], b = 2.0 * (double)bnd[f] + 3e-5 * fabs(l32);
+        if (l32 + b < lh) {
+            a += mult;
+        } else if (l32 - b < lh) {
+            // too close to decide in FP32: lambda_f in FP64
+            if (threadIdx.x == 0) lam64 = 0.0;
+            __syncthreads();
+            double part = 0.0;
+            for (int u = threadIdx.x; u < d; u += blockDim.x) {
+                double re = 0.0, im = 0.0;
+                for (int m = 0; m < K; ++m) {
+                    const int k = (f * m) & (K - 1);
+                    re += pv[m][u] * tc64[k];
+                    im += pv[m][u] * ts64[k];
+                }
+                part += re * re + im * im;
+            }
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            if (lane == 0 && part != 0.0) atomicAdd(&lam64, part);
+            __syncthreads();
+            if (lam64 < lh) a += mult;
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) ranks[grp] = a;
 }
 
 }  // namespace

@@ -181,3 +181,30 @@ def test_batch_rejects_mixed_channels():
     b = _dev(np.zeros((32, 32, 1), dtype=np.uint8))
     with pytest.raises(RuntimeError):
         H.denoise_batch([a, b], [10.0, 10.0], dict(ps=8, stride=3, window=9, K=8))
+
+
+@pytest.mark.parametrize("shape,prm,sigma", [
+    ((96, 120, 3), dict(ps=8, stride=2, window=15, K=32), 20.0),
+    ((80, 64, 1), dict(ps=8, stride=1, window=13, K=16), 35.0),
+    ((72, 72, 3), dict(ps=8, stride=3, window=11, K=8), 8.0),
+])
+def test_sampled_group_ranks_match_oracle(shape, prm, sigma):
+    """Eigen-rank of lambda_{K/2} among the circulant eigenvalues of every 8th group per axis
+    (Sec. III-D), element by element against the oracle."""
+    import ctypes
+    import torch
+    import paper_2508_10307_gb300 as H
+    Hh, Ww, C = shape
+    noisy = synth.add_gaussian(synth.clean_image(Hh, Ww, C, 53), sigma, 53)
+    _, det = O.estimate_sigma(noisy, dict(prm, adapt=True), return_details=True)
+    lib = H.load_library()
+    f = lib.htsvd_internal_sampled_ranks
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_int32]
+    f.restype = ctypes.c_int32
+    cp = H.HtsvdParams.of(prm).c()
+    x = torch.from_numpy(noisy).cuda()
+    out = np.zeros(4096, np.int32)
+    n = f(x.data_ptr(), Hh, Ww, C, ctypes.addressof(cp), out.ctypes.data, out.size)
+    assert n == det["ranks"].size
+    np.testing.assert_array_equal(out[:n], det["ranks"])
