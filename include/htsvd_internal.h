@@ -16,7 +16,8 @@ extern "C" {
 /* HOST computation of one global-basis slice (Sec. III-B.1): from the integer row (which = 0)
  * or column (which = 1) moments `mom` ([2][8][8][C][C] uint64, host memory), the slice-f scatter
  * matrix and its canonical eigenvectors, written to out[64][2] (row-major [a][i], re/im).
- * Runs the same rotation sequence as the device solver. No errors are reported. */
+ * Uses the same complex Jacobi method as the device solver (cyclic pair order here, round-robin
+ * order on the device), so the two agree to rounding. No errors are reported. */
 void htsvd_internal_slice_basis(const unsigned long long* mom, int C, int which, int f, double* out);
 
 /* DEVICE: integer row/column moments of the reference patches of a uint8 image (d_img) with the

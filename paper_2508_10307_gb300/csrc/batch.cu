@@ -289,13 +289,14 @@ Tuning autotune(BatchCache* c, const htsvd_image* imgs, int n, const htsvd_param
         cudaGetLastError();
         return best;
     }
-    const int trs[] = {4, 6, 8};
+    // five filter tile edges; the three grouping tile shapes are tried alongside the first three
+    const int trs[] = {5, 4, 6, 8, 7};
     const int bms[][2] = {{4, 8}, {2, 16}, {8, 8}};
-    for (int ti = 0; ti < 3; ++ti) {
+    for (int ti = 0; ti < 5; ++ti) {
         Tuning t;
         t.TR = trs[ti];
-        t.bmy = bms[ti][0];
-        t.bmx = bms[ti][1];
+        t.bmy = bms[ti % 3][0];
+        t.bmx = bms[ti % 3][1];
         Plan P;
         if (prepare(c, imgs, n, p, t, P) != HTSVD_OK) continue;
         // bases and grouping first (the filter needs both), then time grouping and filter separately

@@ -364,23 +364,26 @@ __device__ void jacobi_herm8_warp(double (*Ar)[PS], double (*Ai)[PS], double (*V
                 int p = at(lane), q = at(PS - 1 - lane);
                 if (p > q) { const int t = p; p = q; q = t; }
                 const double xr = Ar[p][q], xi = Ai[p][q];
-                const double rr = sqrt(xr * xr + xi * xi);
+                const double r2 = xr * xr + xi * xi;
                 const double app = Ar[p][p], aqq = Ar[q][q];
                 double* R = rot[lane];
                 R[6] = p;
                 R[7] = q;
                 R[8] = app;
                 R[9] = aqq;
-                if (rr == 0.0 || rr < 1e-17 * sqrt(fabs(app * aqq))) {
+                // FP64 division and square root are long sequences on this GPU: |a_pq|, its phase and
+                // theta share one reciprocal square root, c takes another
+                if (r2 == 0.0 || r2 < 1e-34 * fabs(app * aqq)) {
                     R[5] = 1.0;
                 } else {
-                    const double th = (aqq - app) / (2.0 * rr);
+                    const double ir = rsqrt(r2), rr = r2 * ir;
+                    const double th = 0.5 * (aqq - app) * ir;
                     double t;
                     if (fabs(th) > 1e150) t = 0.5 / th;
                     else t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                    const double c = 1.0 / sqrt(t * t + 1.0);
-                    R[0] = xr / rr;
-                    R[1] = xi / rr;
+                    const double c = rsqrt(t * t + 1.0);
+                    R[0] = xr * ir;
+                    R[1] = xi * ir;
                     R[2] = c;
                     R[3] = t * c;
                     R[4] = t * rr;
