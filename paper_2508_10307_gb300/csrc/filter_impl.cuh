@@ -13,13 +13,16 @@
 // time, all data of a group living in shared memory / registers:
 //   A  thread (k, b): column b of patch k -> channel DFT -> Y_f = U_f^H X_f
 //   B  thread (i, k): row i -> S_f = Y_f V_f -> inverse channel DFT (real S)
-//   C  thread = fibre (i, j, c): Haar butterflies along the K patches, threshold,
-//      inverse butterflies. Coefficients whose FP32 value lies inside a guard band
-//      around tau get their keep/drop decision recomputed in FP64 (one warp per entry).
-//   D  thread (i, k): channel DFT -> Z_f = T_f V_f^H
-//   E  thread (k, b): G_f = U_f Z_f -> inverse channel DFT (real estimate)
+//   C  thread = fibre (i, j, c): Haar butterflies along the K patches (in place, one register
+//      array), threshold, inverse butterflies. Coefficients whose FP32 value lies inside a
+//      guard band around tau get their keep/drop decision recomputed in FP64 (one warp per
+//      entry). In the forward mode each warp's 32 fibres sit on 32 distinct banks.
+//   D  thread (i, k): channel DFT -> Z_f = T_f V_f^H   (outer products, transposed basis)
+//   E  thread (k, b): G_f = U_f Z_f -> inverse channel DFT (real estimate), likewise
 //   F  warp w owns footprint rows r with r mod 8 == w: it adds row (w - y_k) mod 8 of
 //      every patch k, k ascending. No atomics, fixed order: bitwise reproducible.
+// The forward mode (filter_tile_fwd) pipelines these over the tile's groups with two group
+// buffers and three CTA barriers per group: [C(q)] | [D, E(q)] | [F(q) with A, B(q+1)].
 // The tile's accumulator is written to a partial buffer; reduce_kernel sums the
 // overlapping tile partials in fixed tile order and divides.
 #pragma once
