@@ -83,6 +83,10 @@ def test_rgb512_parity_with_estimated_sigma():
     ((64, 48, 3), dict(ps=8, stride=3, window=15, K=16, agg_mode="sparsity"), 25.0),
     ((33, 40, 3), dict(ps=8, stride=1, window=7, K=2), 10.0),
     ((61, 75, 3), dict(ps=8, stride=3, window=15, K=16, tile=7), 20.0),  # forced filter tiles (ragged)
+    # windows wider than 32: 9..16 candidate quads per lane row, 2 or 3 strips per warp
+    ((72, 88, 3), dict(ps=8, stride=5, window=45, K=16), 20.0),
+    ((80, 80, 1), dict(ps=8, stride=6, window=64, K=32), 25.0),                # the largest window built
+    ((64, 72, 3), dict(ps=8, stride=5, window=37, K=8, match_mode="full"), 20.0),
     ((47, 52, 1), dict(ps=8, stride=2, window=13, K=8, tile=3), 20.0),
 ])
 def test_small_images_parity(shape, prm, sigma):
