@@ -144,19 +144,6 @@ __device__ __forceinline__ void haar_fwd_inplace(float (&v)[K]) { haar_fwd_level
 template <int K>
 __device__ __forceinline__ void haar_inv_inplace(float (&v)[K]) { haar_inv_level<K, 0>(v); }
 
-// Two-array forms: o = H_K a (Eq. (H_2N) applied recursively; a is overwritten) and its
-// synthesis a = H_K^T o (o is overwritten), with o in the natural coefficient order.
-template <int K>
-__device__ __forceinline__ void haar_fwd(float (&a)[K], float (&o)[K]) {
-    haar_fwd_inplace<K>(a);
-    haar_for_each<K>([&](int m, int sl) { o[m] = a[sl]; });
-}
-template <int K>
-__device__ __forceinline__ void haar_inv(float (&o)[K], float (&a)[K]) {
-    haar_for_each<K>([&](int m, int sl) { a[sl] = o[m]; });
-    haar_inv_inplace<K>(a);
-}
-
 template <typename T>
 __device__ __forceinline__ float ldv(const T* p) { return (float)p[0]; }
 
@@ -827,26 +814,19 @@ __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile,
             // ---- C1: Haar analysis and FP32 decisions with a guard band
             const float nrm2 = sizeof(Tin) == 1 ? (float)misc[5] : __int_as_float(misc[2]);
             const float delta = a.band_rel * sqrtf(nrm2) + a.band_abs;
-            float co[K];
+            float co[K];          // fibre, then its coefficients in place (haar_for_each slots)
             uint32_t bandb = 0;
             // fibre tid = (i*8 + j)*C + c lives at row i, column offset j*C + c of every patch
             const int foff = (tid / G::RWF) * G::ROW + (tid % G::RWF);
             if (tid < NF) {
-                float fib[K];
 #pragma unroll
-                for (int k = 0; k < K; ++k) fib[k] = gb[k * G::GS + foff];
-                haar_fwd<K>(fib, co);
-                if (MODE == FM_FORWARD && a.coef_out) {
-                    float* cdst = a.coef_out + (size_t)grp * K * NF;
-#pragma unroll
-                    for (int m = 0; m < K; ++m) cdst[m * NF + tid] = co[m];
-                }
-#pragma unroll
-                for (int m = 0; m < K; ++m) {
-                    const float d = fabsf(co[m]) - a.tau32;
+                for (int k = 0; k < K; ++k) co[k] = gb[k * G::GS + foff];
+                haar_fwd_inplace<K>(co);
+                haar_for_each<K>([&](int m, int sl) {
+                    const float d = fabsf(co[sl]) - a.tau32;
                     if (fabsf(d) <= delta) bandb |= 1u << m;
                     else if (d >= 0.f) keepb |= 1u << m;
-                }
+                });
                 if (bandb) {
                     atomicAdd(&misc[0], __popc(bandb));
 #pragma unroll
@@ -875,30 +855,9 @@ __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile,
                 for (int m = 0; m < K; ++m)
                     if ((bandb >> m) & 1u)
                         if ((rkeep[(m * NF + tid) >> 5] >> (tid & 31)) & 1u) keepb |= 1u << m;
-                if constexpr (MODE == FM_FORWARD) {
-                    if (a.mask_out) {
-                        uint32_t* mo = a.mask_out + (size_t)grp * NBW;
-#pragma unroll
-                        for (int m = 0; m < K; ++m) {
-                            const uint32_t w = __ballot_sync(0xffffffffu, (keepb >> m) & 1u);
-                            if (lane == 0) mo[m * (NF / 32) + warp] = w;
-                        }
-                    }
-                    {
-                        const int wk = __reduce_add_sync(0xffffffffu, __popc(keepb));
-                        if (lane == 0) atomicAdd(&misc[1], wk);
-                    }
-#pragma unroll
-                    for (int m = 0; m < K; ++m)
-                        if (!((keepb >> m) & 1u)) co[m] = 0.f;
-                    float rec[K];
-                    haar_inv<K>(co, rec);
-#pragma unroll
-                    for (int k = 0; k < K; ++k) gb[k * G::GS + foff] = rec[k];
-                } else {
-#pragma unroll
-                    for (int m = 0; m < K; ++m) cx[m] = ((keepb >> m) & 1u) ? co[m] : 0.f;
-                }
+                // (the forward mode runs in filter_tile_fwd; here only the adjoint keeps the
+                // kept coefficients at x, for the weight gradient)
+                haar_for_each<K>([&](int m, int sl) { cx[sl] = ((keepb >> m) & 1u) ? co[sl] : 0.f; });
             }
             __syncthreads();
             if constexpr (MODE == FM_ADJOINT) {
@@ -923,23 +882,21 @@ __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile,
                 }
                 __syncthreads();
                 if (tid < NF) {
-                    float fib[K], cr[K];
+                    float cr[K];      // fibre of the r pass, then its coefficients in place
 #pragma unroll
-                    for (int k = 0; k < K; ++k) fib[k] = gb[k * G::GS + foff];
-                    haar_fwd<K>(fib, cr);
+                    for (int k = 0; k < K; ++k) cr[k] = gb[k * G::GS + foff];
+                    haar_fwd_inplace<K>(cr);
                     float dot = 0.f;
-#pragma unroll
-                    for (int m = 0; m < K; ++m) {
-                        if (!((keepb >> m) & 1u)) cr[m] = 0.f;
-                        dot = fmaf(cr[m], cx[m], dot);
-                    }
+                    haar_for_each<K>([&](int m, int sl) {
+                        if (!((keepb >> m) & 1u)) cr[sl] = 0.f;
+                        dot = fmaf(cr[sl], cx[sl], dot);
+                    });
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
                     if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[3]), dot);
-                    float rec[K];
-                    haar_inv<K>(cr, rec);
+                    haar_inv_inplace<K>(cr);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) gb[k * G::GS + foff] = rec[k];
+                    for (int k = 0; k < K; ++k) gb[k * G::GS + foff] = cr[k];
                 }
                 __syncthreads();
             }
