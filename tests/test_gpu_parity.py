@@ -212,3 +212,37 @@ def test_sampled_group_ranks_match_oracle(shape, prm, sigma):
     n = f(x.data_ptr(), Hh, Ww, C, ctypes.addressof(cp), out.ctypes.data, out.size)
     assert n == det["ranks"].size
     np.testing.assert_array_equal(out[:n], det["ranks"])
+
+
+BAND_REL = 2.0 ** -19     # guard band of the threshold decision, relative to ||G||_F (kBandRel in kernels.h)
+
+
+def _coefficient_errors(key):
+    """FP32 coefficients of the GPU path against the oracle's FP64 coefficients on sampled groups:
+    (|S32 - S64| [n, K, 64*C], ||G||_F [n], ||G restricted to the Haar support of row m||_F [n, K])."""
+    clean, noisy, sigma, prm, r = oracle_run(key)
+    out, info = H.denoise(_dev(noisy), sigma, prm, return_info=True, coeffs=True)
+    coef = info["coeffs"].cpu().numpy()
+    p = O.Params.of(prm)
+    Hk = O.haar_matrix(p.K)
+    rng = np.random.default_rng(0)
+    sample = rng.choice(len(r.idx), size=min(2048, len(r.idx)), replace=False)
+    G = O.gather_groups(noisy, r.idx[sample], p.ps).astype(np.float64)
+    S = O.forward_transform(G, r.U, r.V, Hk)
+    n = len(sample)
+    err = np.abs(coef[sample].astype(np.float64) - S).reshape(n, p.K, -1)
+    pk = (G.reshape(n, p.K, -1) ** 2).sum(axis=2)              # squared norm per patch (group order)
+    supp = (np.abs(Hk) > 0).astype(np.float64)                 # [m, k]: patch k in the support of row m
+    return err, np.sqrt(pk.sum(axis=1)), np.sqrt(pk @ supp.T)
+
+
+@pytest.mark.parametrize("key", ["gray128", "rgb512"])
+def test_fp32_coefficient_error_is_well_inside_the_guard_band(key):
+    """Outside the guard band the FP32 coefficients decide keep/drop, so their error against the
+    oracle's FP64 coefficients must stay well below band * ||G||_F, and below band * ||G_m||_F with
+    G_m the patches in the Haar support of the coefficient's row."""
+    err, nrm, nrm_m = _coefficient_errors(key)
+    worst = float((err.max(axis=2) / nrm[:, None]).max())
+    worst_m = float((err.max(axis=2) / nrm_m).max())
+    assert worst <= BAND_REL / 4, f"max |S32 - S64| / ||G|| = {worst:.3e}"
+    assert worst_m <= BAND_REL / 4, f"max |S32 - S64| / ||G_m|| = {worst_m:.3e}"
