@@ -82,7 +82,7 @@ __host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes) {
     L.off_bas = o; o += 2 * 384 * 4;           // basis rows, then the transposed copies
     L.off_gb = o; o += 2 * K * G::GS * 4;
     L.off_pos = o; o += 2 * 64 * 4;
-    L.off_band = o;
+    L.off_band = o; o += 2 * 32 * 4;           // per-patch squared norms of the two groups in flight
     L.off_rkeep = o;
     L.off_misc = o; o += 2 * 16 * 4;
     L.off_acc = o; o += FH * FW * G::ACC * 4;
@@ -498,6 +498,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     float* gbb = reinterpret_cast<float*>(smem + L.off_gb);
     int* posb = reinterpret_cast<int*>(smem + L.off_pos);
     int* miscb = reinterpret_cast<int*>(smem + L.off_misc);
+    float* pnb = reinterpret_cast<float*>(smem + L.off_band);
     float* acc = reinterpret_cast<float*>(smem + L.off_acc);
     Tin* img_s = reinterpret_cast<Tin*>(smem + L.off_img);
 
@@ -526,10 +527,18 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         }
     };
     auto fetch_idx = [&](int q) { return tid < K ? a.idx[(size_t)group_of(q) * K + tid] : 0; };
-    // A, B of group q into buffer gbq; ||G||_F^2 into misc[5] (uint8, exact) or misc[2] (float)
-    auto project = [&](float* gbq, const int* pos, int* misc) {
+    // A, B of group q into buffer gbq; ||G||_F^2 into misc[5] (uint8, exact) or misc[2] (float), and
+    // the squared norm of each patch into pn[k]
+    auto project = [&](float* gbq, const int* pos, int* misc, float* pn) {
         if (tid < 8 * K) {
             const float nrm = stage_a<K, C, Tin>(img_s, FW, pos, bas, gbq, tid >> 3, tid & 7);
+            {
+                float pk = nrm;                           // the 8 columns of patch k are 8 adjacent lanes
+                pk += __shfl_xor_sync(kAB, pk, 1);
+                pk += __shfl_xor_sync(kAB, pk, 2);
+                pk += __shfl_xor_sync(kAB, pk, 4);
+                if ((tid & 7) == 0) pn[tid >> 3] = pk;
+            }
             if constexpr (sizeof(Tin) == 1) {
                 const int wsum = __reduce_add_sync(kAB, (int)nrm);
                 if (lane == 0) atomicAdd(&misc[5], wsum);
@@ -565,7 +574,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     store_pos(fetch_idx(0), posb);
     if (tid < 32) miscb[tid] = 0;
     __syncthreads();
-    project(gbb, posb, miscb);
+    project(gbb, posb, miscb, pnb);
     __syncthreads();
 
     for (int q = 0; q < ngr; ++q) {
@@ -576,6 +585,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         float* gbq = gbb + buf * K * G::GS;
         const int* pos = posb + buf * 64;
         int* misc = miscb + buf * 16;
+        const float* pn = pnb + buf * 32;
 
         // ---- C: Haar analysis, threshold (FP64 inside the guard band), synthesis
         // final keep decisions of the warp's fibres: optional mask output, kept count
@@ -607,11 +617,32 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                     float* cdst = a.coef_out + (size_t)grp * K * NF;
                     haar_for_each<K>([&](int m, int sl) { cdst[m * NF + fib] = v[sl]; });
                 }
+                float dlast = 0.f;
+                int mlast = 0;
                 haar_for_each<K>([&](int m, int sl) {
                     const float d = fabsf(v[sl]) - a.tau32;
-                    if (fabsf(d) <= delta) bandb |= 1u << m;
-                    else if (d >= 0.f) keepb |= 1u << m;
+                    if (fabsf(d) <= delta) {
+                        bandb |= 1u << m;
+                        dlast = d;
+                        mlast = m;
+                    } else if (d >= 0.f) {
+                        keepb |= 1u << m;
+                    }
                 });
+                if (bandb != 0u && (bandb & (bandb - 1u)) == 0u) {
+                    // one entry inside the group-wide band (the usual case): the FP32 error of row m
+                    // only involves the patches of its Haar support (L = K / 2^level patches from k0),
+                    // so the band narrows to their norm
+                    const int m = mlast;
+                    const int lv = m == 0 ? 0 : 31 - __clz(m);
+                    const int L = m == 0 ? K : K >> lv, k0 = m == 0 ? 0 : (m - (1 << lv)) * L;
+                    float sq = 0.f;
+                    for (int k = k0; k < k0 + L; ++k) sq += pn[k];
+                    if (fabsf(dlast) > a.band_rel * sqrtf(sq) + a.band_abs) {
+                        bandb = 0u;
+                        if (dlast >= 0.f) keepb |= 1u << m;
+                    }
+                }
                 anyb = __ballot_sync(0xffffffffu, bandb != 0u);
                 if (!anyb) {
                     keep_finish(keepb);
@@ -698,7 +729,8 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
             }
         }
         // ... overlapped with A, B(q+1) into the other buffer
-        if (q + 1 < ngr) project(gbb + (buf ^ 1) * K * G::GS, posb + (buf ^ 1) * 64, miscb + (buf ^ 1) * 16);
+        if (q + 1 < ngr)
+            project(gbb + (buf ^ 1) * K * G::GS, posb + (buf ^ 1) * 64, miscb + (buf ^ 1) * 16, pnb + (buf ^ 1) * 32);
         __syncthreads();
     }
     // Write the tile partial.
