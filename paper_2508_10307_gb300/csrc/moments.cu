@@ -296,6 +296,48 @@ __host__ __device__ void canonicalise(double (*Ar)[PS], double (*Vr)[PS], double
     }
 }
 
+// Device form of canonicalise for one warp: lane 0 orders the eigenvalues (the same selection
+// sort), then lane c < 8 treats output column c. The largest-modulus entry is found on squared
+// moduli and the phase takes one reciprocal square root (FP64 square root and division are long
+// sequences on this GPU).
+__device__ void canonicalise_warp(double (*Ar)[PS], double (*Vr)[PS], double (*Vi)[PS], double (*Out)[PS][2],
+                                  int* order, int lane) {
+    if (lane == 0) {
+        for (int i = 0; i < PS; ++i) order[i] = i;
+        for (int i = 0; i < PS; ++i)          // selection sort, descending, as in canonicalise
+            for (int j = i + 1; j < PS; ++j)
+                if (Ar[order[j]][order[j]] > Ar[order[i]][order[i]]) {
+                    const int t = order[i];
+                    order[i] = order[j];
+                    order[j] = t;
+                }
+    }
+    __syncwarp();
+    if (lane < PS) {
+        const int col = lane, src = order[col];
+        double mod2[PS], mx2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < PS; ++a) {
+            mod2[a] = Vr[a][src] * Vr[a][src] + Vi[a][src] * Vi[a][src];
+            mx2 = fmax(mx2, mod2[a]);
+        }
+        const double lim = mx2 * ((1.0 - 1e-6) * (1.0 - 1e-6));   // |v_a| >= (1 - 1e-6) max |v|
+        int as = PS - 1;
+#pragma unroll
+        for (int a = PS - 1; a >= 0; --a)
+            if (mod2[a] >= lim) as = a;
+        const double inv = rsqrt(mod2[as]);
+        const double hr = Vr[as][src] * inv, hi = -Vi[as][src] * inv;     // conj(v_a) / |v_a|
+#pragma unroll
+        for (int a = 0; a < PS; ++a) {
+            Out[a][col][0] = Vr[a][src] * hr - Vi[a][src] * hi;
+            Out[a][col][1] = Vr[a][src] * hi + Vi[a][src] * hr;
+        }
+        Out[as][col][1] = 0.0;
+    }
+    __syncwarp();
+}
+
 // Scatter matrix of slice f from the integer moments (rows: which = 0, columns: which = 1),
 // then its canonical eigenvectors.
 // work: 4 * PS * PS doubles of scratch (Ar, Ai, Vr, Vi).
@@ -346,17 +388,26 @@ __device__ void jacobi_herm8_warp(double (*Ar)[PS], double (*Ai)[PS], double (*V
         }
     __syncwarp();
     const int pr_i = lane >> 3, k = lane & 7;          // rotation of this lane, row/column it updates
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        if (lane == 0) {
-            double off = 0.0, dia = 0.0;
-            for (int i = 0; i < PS; ++i) {
-                dia += Ar[i][i] * Ar[i][i];
-                for (int j = i + 1; j < PS; ++j) off += Ar[i][j] * Ar[i][j] + Ai[i][j] * Ai[i][j];
-            }
-            rot[4][0] = (off <= 1e-32 * dia || off == 0.0) ? 1.0 : 0.0;
+    // lane l < 28 holds the off-diagonal pair (oi, oj), oi < oj, of the convergence test
+    int oi = 0, oj = 0;
+    if (lane < PS * (PS - 1) / 2) {
+        int rem = lane;
+        while (rem >= PS - 1 - oi) {
+            rem -= PS - 1 - oi;
+            ++oi;
         }
+        oj = oi + 1 + rem;
+    }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = lane < PS * (PS - 1) / 2 ? Ar[oi][oj] * Ar[oi][oj] + Ai[oi][oj] * Ai[oi][oj] : 0.0;
+        double dia = lane < PS ? Ar[lane][lane] * Ar[lane][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            dia += __shfl_xor_sync(0xffffffffu, dia, o);
+        }
+        if (off <= 1e-32 * dia || off == 0.0) break;      // same value in every lane
         __syncwarp();
-        if (rot[4][0] != 0.0) break;
         for (int r = 0; r < PS - 1; ++r) {
             // pair of rotation i in round r
             auto at = [r](int j) { return j == 0 ? 0 : 1 + ((j - 1 + r) % (PS - 1)); };
@@ -469,8 +520,8 @@ __device__ __forceinline__ void basis_problem(const unsigned long long* __restri
     }
     __syncwarp();
     jacobi_herm8_warp(Ar, Ai, Vr, Vi, rot, lane);
-    if (lane == 0) canonicalise(Ar, Vr, Vi, Res);
-    __syncwarp();
+    __shared__ int order[PS];
+    canonicalise_warp(Ar, Vr, Vi, Res, order, lane);
     // FP64 slice f (and its conjugate slice C - f) of U or V, and the packed FP32 copy used by the filter.
     for (int ai = lane; ai < PS2; ai += 32) {
         const double re = Res[ai / PS][ai % PS][0], im = Res[ai / PS][ai % PS][1];
