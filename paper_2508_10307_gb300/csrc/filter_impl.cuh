@@ -105,12 +105,13 @@ __device__ __forceinline__ void haar_each_level(F& f) {       // level L: n = 2^
     if constexpr (L >= 0) {
         haar_each_level<K, L - 1>(f);
 #pragma unroll
-        for (int m = 0; m < (1 << L); ++m) f((1 << L) + m, (2 * m + 1) * (K >> (L + 1)));
+        for (int m = 0; m < (1 << L); ++m) f((1 << L) + m, (2 * m + 1) * (K >> (L + 1)), K >> L);
     }
 }
+// f(mo, slot, support): support = number of patches the row of o[mo] combines (K for mo = 0 and 1).
 template <int K, typename F>
 __device__ __forceinline__ void haar_for_each(F&& f) {
-    f(0, 0);
+    f(0, 0, K);
     haar_each_level<K, haar_levels<K>() - 1>(f);
 }
 template <int K, int L>
@@ -139,10 +140,42 @@ __device__ __forceinline__ void haar_inv_level(float (&v)[K]) {  // levels L, L+
         haar_inv_level<K, L + 1>(v);
     }
 }
+// Unnormalised forms (sums and differences only): the coefficient of row m comes out multiplied by
+// sqrt(L_m), L_m its support, and synthesis of coefficients scaled by 1 / L_m gives H_K^T o.
+template <int K, int L>
+__device__ __forceinline__ void haar_fwd_level_sum(float (&v)[K]) {
+    if constexpr (L >= 0) {
+        constexpr int st = K >> (L + 1);
+#pragma unroll
+        for (int m = 0; m < (1 << L); ++m) {
+            const float x = v[2 * m * st], y = v[(2 * m + 1) * st];
+            v[(2 * m + 1) * st] = x - y;
+            v[2 * m * st] = x + y;
+        }
+        haar_fwd_level_sum<K, L - 1>(v);
+    }
+}
+template <int K, int L>
+__device__ __forceinline__ void haar_inv_level_sum(float (&v)[K]) {
+    if constexpr ((2 << L) <= K) {
+        constexpr int st = K >> (L + 1);
+#pragma unroll
+        for (int m = (1 << L) - 1; m >= 0; --m) {
+            const float sa = v[2 * m * st], d = v[(2 * m + 1) * st];
+            v[2 * m * st] = sa + d;
+            v[(2 * m + 1) * st] = sa - d;
+        }
+        haar_inv_level_sum<K, L + 1>(v);
+    }
+}
 template <int K>
 __device__ __forceinline__ void haar_fwd_inplace(float (&v)[K]) { haar_fwd_level<K, haar_levels<K>() - 1>(v); }
 template <int K>
 __device__ __forceinline__ void haar_inv_inplace(float (&v)[K]) { haar_inv_level<K, 0>(v); }
+template <int K>
+__device__ __forceinline__ void haar_fwd_sum(float (&v)[K]) { haar_fwd_level_sum<K, haar_levels<K>() - 1>(v); }
+template <int K>
+__device__ __forceinline__ void haar_inv_sum(float (&v)[K]) { haar_inv_level_sum<K, 0>(v); }
 
 template <typename T>
 __device__ __forceinline__ float ldv(const T* p) { return (float)p[0]; }
@@ -608,20 +641,24 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
             // FP64 refinement loop: that would push the array to local memory)
             uint32_t keepb = 0, bandb = 0;
             unsigned anyb;
+            // The Haar transform runs unnormalised (sums and differences): row m's coefficient is
+            // sqrt(L_m) times the normalised one, so threshold and band scale by sqrt(L_m) (one pair of
+            // values per support size L = 2^j) and kept coefficients by 1 / L_m before synthesis.
             {
                 float v[K];                               // fibre, then its coefficients (haar_for_each slots)
 #pragma unroll
                 for (int k = 0; k < K; ++k) v[k] = gbq[k * G::GS + foff];
-                haar_fwd_inplace<K>(v);
+                haar_fwd_sum<K>(v);
                 if (a.coef_out) {
                     float* cdst = a.coef_out + (size_t)grp * K * NF;
-                    haar_for_each<K>([&](int m, int sl) { cdst[m * NF + fib] = v[sl]; });
+                    haar_for_each<K>([&](int m, int sl, int L) { cdst[m * NF + fib] = v[sl] * rsqrtf((float)L); });
                 }
                 float dlast = 0.f;
                 int mlast = 0;
-                haar_for_each<K>([&](int m, int sl) {
-                    const float d = fabsf(v[sl]) - a.tau32;
-                    if (fabsf(d) <= delta) {
+                haar_for_each<K>([&](int m, int sl, int L) {
+                    const float r = sqrtf((float)L);      // folds to a constant once unrolled
+                    const float d = fmaf(-a.tau32, r, fabsf(v[sl]));
+                    if (fabsf(d) <= delta * r) {
                         bandb |= 1u << m;
                         dlast = d;
                         mlast = m;
@@ -638,7 +675,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                     const int L = m == 0 ? K : K >> lv, k0 = m == 0 ? 0 : (m - (1 << lv)) * L;
                     float sq = 0.f;
                     for (int k = k0; k < k0 + L; ++k) sq += pn[k];
-                    if (fabsf(dlast) > a.band_rel * sqrtf(sq) + a.band_abs) {
+                    if (fabsf(dlast) > (a.band_rel * sqrtf(sq) + a.band_abs) * sqrtf((float)L)) {
                         bandb = 0u;
                         if (dlast >= 0.f) keepb |= 1u << m;
                     }
@@ -646,10 +683,10 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 anyb = __ballot_sync(0xffffffffu, bandb != 0u);
                 if (!anyb) {
                     keep_finish(keepb);
-                    haar_for_each<K>([&](int m, int sl) {
-                        if (!((keepb >> m) & 1u)) v[sl] = 0.f;
+                    haar_for_each<K>([&](int m, int sl, int L) {
+                        v[sl] = ((keepb >> m) & 1u) ? v[sl] * (1.f / (float)L) : 0.f;
                     });
-                    haar_inv_inplace<K>(v);
+                    haar_inv_sum<K>(v);
 #pragma unroll
                     for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = v[k];
                 } else {
@@ -676,10 +713,10 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 float w[K];
 #pragma unroll
                 for (int k = 0; k < K; ++k) w[k] = gbq[k * G::GS + foff];
-                haar_for_each<K>([&](int m, int sl) {
-                    if (!((keepb >> m) & 1u)) w[sl] = 0.f;
+                haar_for_each<K>([&](int m, int sl, int L) {
+                    w[sl] = ((keepb >> m) & 1u) ? w[sl] * (1.f / (float)L) : 0.f;
                 });
-                haar_inv_inplace<K>(w);
+                haar_inv_sum<K>(w);
 #pragma unroll
                 for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = w[k];
             }
@@ -854,7 +891,7 @@ __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile,
 #pragma unroll
                 for (int k = 0; k < K; ++k) co[k] = gb[k * G::GS + foff];
                 haar_fwd_inplace<K>(co);
-                haar_for_each<K>([&](int m, int sl) {
+                haar_for_each<K>([&](int m, int sl, int) {
                     const float d = fabsf(co[sl]) - a.tau32;
                     if (fabsf(d) <= delta) bandb |= 1u << m;
                     else if (d >= 0.f) keepb |= 1u << m;
@@ -889,7 +926,7 @@ __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile,
                         if ((rkeep[(m * NF + tid) >> 5] >> (tid & 31)) & 1u) keepb |= 1u << m;
                 // (the forward mode runs in filter_tile_fwd; here only the adjoint keeps the
                 // kept coefficients at x, for the weight gradient)
-                haar_for_each<K>([&](int m, int sl) { cx[sl] = ((keepb >> m) & 1u) ? co[sl] : 0.f; });
+                haar_for_each<K>([&](int m, int sl, int) { cx[sl] = ((keepb >> m) & 1u) ? co[sl] : 0.f; });
             }
             __syncthreads();
             if constexpr (MODE == FM_ADJOINT) {
@@ -919,7 +956,7 @@ __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile,
                     for (int k = 0; k < K; ++k) cr[k] = gb[k * G::GS + foff];
                     haar_fwd_inplace<K>(cr);
                     float dot = 0.f;
-                    haar_for_each<K>([&](int m, int sl) {
+                    haar_for_each<K>([&](int m, int sl, int) {
                         if (!((keepb >> m) & 1u)) cr[sl] = 0.f;
                         dot = fmaf(cr[sl], cx[sl], dot);
                     });
