@@ -72,8 +72,8 @@ __host__ __device__ inline FLayout f_layout(int FH, int FW, int in_bytes, int mo
     return L;
 }
 
-// Shared-memory layout of the pipelined forward filter: two group buffers, two position and
-// counter sets (group q+1 is projected while group q is aggregated), no band bitmaps.
+// Shared-memory layout of the pipelined forward filter: two group buffers (group q+1 is projected
+// while group q is inverted and aggregated), three position and counter sets, no band bitmaps.
 template <int K, int C>
 __host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes) {
     using G = FCfg<C>;
@@ -81,10 +81,10 @@ __host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes) {
     int o = 0;
     L.off_bas = o; o += 2 * 384 * 4;           // basis rows, then the transposed copies
     L.off_gb = o; o += 2 * K * G::GS * 4;
-    L.off_pos = o; o += 2 * 64 * 4;
+    L.off_pos = o; o += 3 * 64 * 4;            // positions of three groups (q, q+1, q+2)
     L.off_band = o; o += 2 * 32 * 4;           // per-patch squared norms of the two groups in flight
     L.off_rkeep = o;
-    L.off_misc = o; o += 2 * 16 * 4;
+    L.off_misc = o; o += 3 * 16 * 4;
     L.off_acc = o; o += FH * FW * G::ACC * 4;
     L.off_img = o; o += (FH * FW * C * in_bytes + 15) / 16 * 16;
     L.off_r = o;
@@ -510,15 +510,347 @@ __device__ __forceinline__ void stage_e(const float* bas, float* gb, int k, int 
     }
 }
 
-// Forward filter of one tile, software-pipelined over its groups with three CTA barriers per
-// group: [C(q)] | [D, E(q); positions of q+1] | [F(q) aggregation and A, B(q+1) projections].
-// Guard-band entries are re-decided in FP64 by the warp that owns the fibre (no CTA barrier).
+// Two-wide forms of stages A, B, D, E for the pipelined forward filter: thread (k, p), p < 4, owns
+// columns 2p, 2p+1 (A, E) or rows r0(p), r0(p) + 2 (B, D) of patch k, so each basis value read
+// from shared memory feeds two columns or rows. Each output sums its terms in the same order as
+// the one-wide forms. Row pairs start at r0 in {0, 1, 4, 5}: with a patch stride of 8 (mod 32)
+// words and row strides of 28 (C = 3) or 12 (C = 1) words, the 128-bit row accesses of a quarter
+// warp (2 patches x 4 row pairs) fall on 8 distinct bank groups; the 64-bit column-pair accesses
+// of a half warp (4 patches x 4 column pairs) on 32 distinct banks.
+__device__ __forceinline__ int row_pair_first(int p) { return (p & 1) + 4 * (p >> 1); }
+
+// Stage A, two columns. Returns the sum of squares of the thread's inputs.
+template <int K, int C, typename Tin>
+__device__ __forceinline__ float stage_a2(const Tin* img_s, int FW, const int* pos, const float* bas, float* gb,
+                                          int k, int p) {
+    using G = FCfg<C>;
+    const Tin* src = img_s + (pos[2 * k] * FW + pos[2 * k + 1] + 2 * p) * C;
+    float* dst = gb + k * G::GS + 2 * p * C;
+    float nrm = 0.f;
+    if constexpr (C == 3) {
+        float y0[2][PS], yr[2][PS], yi[2][PS];
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+#pragma unroll
+            for (int ii = 0; ii < PS; ++ii) y0[w][ii] = yr[w][ii] = yi[w][ii] = 0.f;
+#pragma unroll 1
+        for (int a = 0; a < PS; ++a) {
+            float X0[2], X1r[2], X1i[2];
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                const float x0 = ldv(src + a * FW * C + w * C), x1 = ldv(src + a * FW * C + w * C + 1),
+                            x2 = ldv(src + a * FW * C + w * C + 2);
+                nrm = fmaf(x0, x0, nrm);
+                nrm = fmaf(x1, x1, nrm);
+                nrm = fmaf(x2, x2, nrm);
+                X0[w] = x0 + x1 + x2;
+                X1r[w] = x0 - 0.5f * (x1 + x2);
+                X1i[w] = F_S3H * (x2 - x1);
+            }
+            float u0[8], ur[8], ui[8];
+            load8(bas + a * PS, u0);
+            load8(bas + 64 + a * PS, ur);
+            load8(bas + 128 + a * PS, ui);
+#pragma unroll
+            for (int ii = 0; ii < PS; ++ii)
+#pragma unroll
+                for (int w = 0; w < 2; ++w) {
+                    y0[w][ii] = fmaf(u0[ii], X0[w], y0[w][ii]);
+                    yr[w][ii] = fmaf(ur[ii], X1r[w], fmaf(ui[ii], X1i[w], yr[w][ii]));
+                    yi[w][ii] = fmaf(ur[ii], X1i[w], fmaf(-ui[ii], X1r[w], yi[w][ii]));
+                }
+        }
+#pragma unroll
+        for (int ii = 0; ii < PS; ++ii) {
+            float2* d = reinterpret_cast<float2*>(dst + ii * G::ROW);
+            d[0] = make_float2(y0[0][ii], yr[0][ii]);
+            d[1] = make_float2(yi[0][ii], y0[1][ii]);
+            d[2] = make_float2(yr[1][ii], yi[1][ii]);
+        }
+    } else {
+        float y0[2][PS];
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+#pragma unroll
+            for (int ii = 0; ii < PS; ++ii) y0[w][ii] = 0.f;
+#pragma unroll 1
+        for (int a = 0; a < PS; ++a) {
+            const float x0 = ldv(src + a * FW), x1 = ldv(src + a * FW + 1);
+            nrm = fmaf(x0, x0, nrm);
+            nrm = fmaf(x1, x1, nrm);
+            float u0[8];
+            load8(bas + a * PS, u0);
+#pragma unroll
+            for (int ii = 0; ii < PS; ++ii) {
+                y0[0][ii] = fmaf(u0[ii], x0, y0[0][ii]);
+                y0[1][ii] = fmaf(u0[ii], x1, y0[1][ii]);
+            }
+        }
+#pragma unroll
+        for (int ii = 0; ii < PS; ++ii)
+            *reinterpret_cast<float2*>(dst + ii * G::ROW) = make_float2(y0[0][ii], y0[1][ii]);
+    }
+    return nrm;
+}
+
+// Six consecutive floats 6*bb .. 6*bb+5 of a 16-byte aligned C = 3 row (one 128-bit and one 64-bit
+// load); odd = bb & 1, a constant at every call site once the loops unroll.
+__device__ __forceinline__ void load6(const float* row, int bb, int odd, float (&r)[6]) {
+    if (odd == 0) {
+        const float4 a = *reinterpret_cast<const float4*>(row + 6 * bb);
+        const float2 b = *reinterpret_cast<const float2*>(row + 6 * bb + 4);
+        r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w; r[4] = b.x; r[5] = b.y;
+    } else {
+        const float2 a = *reinterpret_cast<const float2*>(row + 6 * bb);
+        const float4 b = *reinterpret_cast<const float4*>(row + 6 * bb + 2);
+        r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y; r[4] = b.z; r[5] = b.w;
+    }
+}
+
+// Stage B, two rows (S_f[i, :] = Y_f[i, :] V_f, inverse channel DFT).
+template <int C>
+__device__ __forceinline__ void stage_b2(const float* bas, float* gb, int k, int p) {
+    using G = FCfg<C>;
+    const int r0 = row_pair_first(p);
+    float* rows[2] = {gb + k * G::GS + r0 * G::ROW, gb + k * G::GS + (r0 + 2) * G::ROW};
+    if constexpr (C == 3) {
+        float s0[2][PS], sr[2][PS], si[2][PS];
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+#pragma unroll
+            for (int j = 0; j < PS; ++j) s0[w][j] = sr[w][j] = si[w][j] = 0.f;
+#pragma unroll 1
+        for (int bb2 = 0; bb2 < PS / 2; bb2 += 2)
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+            const int bb = bb2 + par;
+            float y[2][6];
+            load6(rows[0], bb, par, y[0]);
+            load6(rows[1], bb, par, y[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int b = 2 * bb + h;
+                float v0[8], vr[8], vi[8];
+                load8(bas + 192 + b * PS, v0);
+                load8(bas + 256 + b * PS, vr);
+                load8(bas + 320 + b * PS, vi);
+#pragma unroll
+                for (int j = 0; j < PS; ++j)
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        const float y0 = y[w][3 * h], yr = y[w][3 * h + 1], yi = y[w][3 * h + 2];
+                        s0[w][j] = fmaf(y0, v0[j], s0[w][j]);
+                        sr[w][j] = fmaf(yr, vr[j], fmaf(-yi, vi[j], sr[w][j]));
+                        si[w][j] = fmaf(yr, vi[j], fmaf(yi, vr[j], si[w][j]));
+                    }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            float o[G::RWF];
+#pragma unroll
+            for (int j = 0; j < PS; ++j) {
+                o[3 * j + 0] = (s0[w][j] + 2.f * sr[w][j]) * F_THIRD;
+                o[3 * j + 1] = (s0[w][j] - sr[w][j] - F_SQ3 * si[w][j]) * F_THIRD;
+                o[3 * j + 2] = (s0[w][j] - sr[w][j] + F_SQ3 * si[w][j]) * F_THIRD;
+            }
+            float4* r4 = reinterpret_cast<float4*>(rows[w]);
+#pragma unroll
+            for (int q = 0; q < G::RWF / 4; ++q) r4[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        }
+    } else {
+        float y[2][PS], o[2][PS];
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            load8(rows[w], y[w]);
+#pragma unroll
+            for (int j = 0; j < PS; ++j) o[w][j] = 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < PS; ++b) {
+            float v0[8];
+            load8(bas + 64 + b * PS, v0);
+#pragma unroll
+            for (int j = 0; j < PS; ++j)
+#pragma unroll
+                for (int w = 0; w < 2; ++w) o[w][j] = fmaf(y[w][b], v0[j], o[w][j]);
+        }
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            float4* r4 = reinterpret_cast<float4*>(rows[w]);
+            r4[0] = make_float4(o[w][0], o[w][1], o[w][2], o[w][3]);
+            r4[1] = make_float4(o[w][4], o[w][5], o[w][6], o[w][7]);
+        }
+    }
+}
+
+// Stage D, two rows (channel DFT, Z_f[i, :] = T_f[i, :] V_f^H), outer-product order.
+template <int C>
+__device__ __forceinline__ void stage_d2(const float* bas, float* gb, int k, int p) {
+    using G = FCfg<C>;
+    const int r0 = row_pair_first(p);
+    float* rows[2] = {gb + k * G::GS + r0 * G::ROW, gb + k * G::GS + (r0 + 2) * G::ROW};
+    const float* bt = bas + G::NBAS;
+    if constexpr (C == 3) {
+        float z0[2][PS], zr[2][PS], zi[2][PS];
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+#pragma unroll
+            for (int b = 0; b < PS; ++b) z0[w][b] = zr[w][b] = zi[w][b] = 0.f;
+#pragma unroll 1
+        for (int jj2 = 0; jj2 < PS / 2; jj2 += 2)
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+            const int jj = jj2 + par;
+            float t[2][6];
+            load6(rows[0], jj, par, t[0]);
+            load6(rows[1], jj, par, t[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = 2 * jj + h;
+                float T0[2], T1r[2], T1i[2];
+#pragma unroll
+                for (int w = 0; w < 2; ++w) {
+                    const float t0 = t[w][3 * h], t1 = t[w][3 * h + 1], t2 = t[w][3 * h + 2];
+                    T0[w] = t0 + t1 + t2;
+                    T1r[w] = t0 - 0.5f * (t1 + t2);
+                    T1i[w] = F_S3H * (t2 - t1);
+                }
+                float v0[8], vr[8], vi[8];
+                load8(bt + 192 + j * PS, v0);
+                load8(bt + 256 + j * PS, vr);
+                load8(bt + 320 + j * PS, vi);
+#pragma unroll
+                for (int b = 0; b < PS; ++b)
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        z0[w][b] = fmaf(T0[w], v0[b], z0[w][b]);
+                        zr[w][b] = fmaf(T1r[w], vr[b], fmaf(T1i[w], vi[b], zr[w][b]));
+                        zi[w][b] = fmaf(T1i[w], vr[b], fmaf(-T1r[w], vi[b], zi[w][b]));
+                    }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            float4* r4 = reinterpret_cast<float4*>(rows[w]);
+#pragma unroll
+            for (int q = 0; q < G::RWF / 4; ++q) {
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int n = 4 * q + e, b = n / 3, c = n % 3;
+                    o[e] = c == 0 ? z0[w][b] : (c == 1 ? zr[w][b] : zi[w][b]);
+                }
+                r4[q] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+    } else {
+        float t[2][PS], o[2][PS];
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            load8(rows[w], t[w]);
+#pragma unroll
+            for (int b = 0; b < PS; ++b) o[w][b] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < PS; ++j) {
+            float v0[8];
+            load8(bt + 64 + j * PS, v0);
+#pragma unroll
+            for (int b = 0; b < PS; ++b)
+#pragma unroll
+                for (int w = 0; w < 2; ++w) o[w][b] = fmaf(t[w][j], v0[b], o[w][b]);
+        }
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            float4* r4 = reinterpret_cast<float4*>(rows[w]);
+            r4[0] = make_float4(o[w][0], o[w][1], o[w][2], o[w][3]);
+            r4[1] = make_float4(o[w][4], o[w][5], o[w][6], o[w][7]);
+        }
+    }
+}
+
+// Stage E, two columns (G_f[:, b] = U_f Z_f[:, b], inverse channel DFT), outer-product order.
+template <int C>
+__device__ __forceinline__ void stage_e2(const float* bas, float* gb, int k, int p) {
+    using G = FCfg<C>;
+    float* col = gb + k * G::GS + 2 * p * C;
+    const float* bt = bas + G::NBAS;
+    if constexpr (C == 3) {
+        float g0[2][PS], gr[2][PS], gi[2][PS];
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+#pragma unroll
+            for (int a = 0; a < PS; ++a) g0[w][a] = gr[w][a] = gi[w][a] = 0.f;
+#pragma unroll 1
+        for (int i = 0; i < PS; ++i) {
+            const float2* z2 = reinterpret_cast<const float2*>(col + i * G::ROW);
+            const float2 za = z2[0], zb = z2[1], zc = z2[2];
+            const float Z0[2] = {za.x, zb.y}, Zr[2] = {za.y, zc.x}, Zi[2] = {zb.x, zc.y};
+            float u0[8], ur[8], ui[8];
+            load8(bt + i * PS, u0);
+            load8(bt + 64 + i * PS, ur);
+            load8(bt + 128 + i * PS, ui);
+#pragma unroll
+            for (int a = 0; a < PS; ++a)
+#pragma unroll
+                for (int w = 0; w < 2; ++w) {
+                    g0[w][a] = fmaf(u0[a], Z0[w], g0[w][a]);
+                    gr[w][a] = fmaf(ur[a], Zr[w], fmaf(-ui[a], Zi[w], gr[w][a]));
+                    gi[w][a] = fmaf(ur[a], Zi[w], fmaf(ui[a], Zr[w], gi[w][a]));
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < PS; ++a) {
+            float o[6];
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                o[3 * w + 0] = (g0[w][a] + 2.f * gr[w][a]) * F_THIRD;
+                o[3 * w + 1] = (g0[w][a] - gr[w][a] - F_SQ3 * gi[w][a]) * F_THIRD;
+                o[3 * w + 2] = (g0[w][a] - gr[w][a] + F_SQ3 * gi[w][a]) * F_THIRD;
+            }
+            float2* d = reinterpret_cast<float2*>(col + a * G::ROW);
+            d[0] = make_float2(o[0], o[1]);
+            d[1] = make_float2(o[2], o[3]);
+            d[2] = make_float2(o[4], o[5]);
+        }
+    } else {
+        float g0[2][PS];
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+#pragma unroll
+            for (int a = 0; a < PS; ++a) g0[w][a] = 0.f;
+#pragma unroll 1
+        for (int i = 0; i < PS; ++i) {
+            const float2 z = *reinterpret_cast<const float2*>(col + i * G::ROW);
+            float u0[8];
+            load8(bt + i * PS, u0);
+#pragma unroll
+            for (int a = 0; a < PS; ++a) {
+                g0[0][a] = fmaf(u0[a], z.x, g0[0][a]);
+                g0[1][a] = fmaf(u0[a], z.y, g0[1][a]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < PS; ++a)
+            *reinterpret_cast<float2*>(col + a * G::ROW) = make_float2(g0[0][a], g0[1][a]);
+    }
+}
+
+// Forward filter of one tile, software-pipelined over its groups with two CTA barriers per group:
+// [D, E(q) on the first half of the CTA | A, B(q+1) on the second half] then [F(q) aggregation,
+// C(q+1) Haar/threshold/synthesis]. Group buffers alternate; positions and counters rotate over
+// three slots (those of q+2 are written while q and q+1 are in flight). Guard-band entries are
+// re-decided in FP64 by the warp that owns the fibre (no CTA barrier).
 template <int K, int C, typename Tin>
 __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int tile, unsigned char* smem) {
     using G = FCfg<C>;
     constexpr int NF = G::PATCH;
     constexpr int NBW = K * NF / 32;
-    constexpr unsigned kAB = (8 * K >= 32) ? 0xffffffffu : ((1u << (8 * K)) - 1u);
+    constexpr int NU = 4 * K;                    // threads of a two-wide stage: K patches x 4
+    constexpr int AB0 = FT_THREADS / 2;          // first thread of the A, B half
+    static_assert(NU <= AB0, "two-wide stages need 4K <= half the CTA");
+    constexpr unsigned kU = (NU >= 32) ? 0xffffffffu : ((1u << NU) - 1u);
     const Geo& g = a.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
@@ -560,30 +892,35 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         }
     };
     auto fetch_idx = [&](int q) { return tid < K ? a.idx[(size_t)group_of(q) * K + tid] : 0; };
-    // A, B of group q into buffer gbq; ||G||_F^2 into misc[5] (uint8, exact) or misc[2] (float), and
-    // the squared norm of each patch into pn[k]
-    auto project = [&](float* gbq, const int* pos, int* misc, float* pn) {
-        if (tid < 8 * K) {
-            const float nrm = stage_a<K, C, Tin>(img_s, FW, pos, bas, gbq, tid >> 3, tid & 7);
-            {
-                float pk = nrm;                           // the 8 columns of patch k are 8 adjacent lanes
-                pk += __shfl_xor_sync(kAB, pk, 1);
-                pk += __shfl_xor_sync(kAB, pk, 2);
-                pk += __shfl_xor_sync(kAB, pk, 4);
-                if ((tid & 7) == 0) pn[tid >> 3] = pk;
-            }
-            if constexpr (sizeof(Tin) == 1) {
-                const int wsum = __reduce_add_sync(kAB, (int)nrm);
-                if (lane == 0) atomicAdd(&misc[5], wsum);
-            } else {
-                float v = nrm;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kAB, v, off);
-                if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[2]), v);
-            }
-            __syncwarp(kAB);
-            stage_b<C>(bas, gbq, tid >> 3, tid & 7);
+    // slots: group buffer and patch norms alternate, positions and counters rotate over three
+    auto gb_of = [&](int q) { return gbb + (q & 1) * K * G::GS; };
+    auto pn_of = [&](int q) { return pnb + (q & 1) * 32; };
+    auto pos_of = [&](int q) { return posb + (q % 3) * 64; };
+    auto misc_of = [&](int q) { return miscb + (q % 3) * 16; };
+    // A, B of group q by thread u < NU of the second half; ||G||_F^2 into misc[5] (uint8, exact) or
+    // misc[2] (float), and the squared norm of each patch into pn[k]
+    auto project = [&](int u, int q) {
+        float* gbq = gb_of(q);
+        int* misc = misc_of(q);
+        const float nrm = stage_a2<K, C, Tin>(img_s, FW, pos_of(q), bas, gbq, u >> 2, u & 3);
+        {
+            float pk = nrm;                               // the 4 column pairs of patch k are 4 adjacent lanes
+            pk += __shfl_xor_sync(kU, pk, 1);
+            pk += __shfl_xor_sync(kU, pk, 2);
+            if ((u & 3) == 0) pn_of(q)[u >> 2] = pk;
         }
+        if constexpr (sizeof(Tin) == 1) {
+            const int wsum = __reduce_add_sync(kU, (int)nrm);
+            if (lane == 0) atomicAdd(&misc[5], wsum);
+        } else {
+            float v = nrm;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                if (off < NU) v += __shfl_xor_sync(kU, v, off);
+            if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[2]), v);
+        }
+        __syncwarp(kU);                                   // stage B reads the rows the 4 lanes of patch k wrote
+        stage_b2<C>(bas, gbq, u >> 2, u & 3);
     };
 
     // Fibre of this thread in the C phase: thread (w, l) takes the w-th fibre (in patch-row order)
@@ -603,24 +940,14 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     auto clear_masks = [&](int q) {                     // mask words of group q, before its C phase
         if (a.mask_out && tid < NBW) a.mask_out[(size_t)group_of(q) * NBW + tid] = 0u;
     };
-    clear_masks(0);
-    store_pos(fetch_idx(0), posb);
-    if (tid < 32) miscb[tid] = 0;
-    __syncthreads();
-    project(gbb, posb, miscb, pnb);
-    __syncthreads();
 
-    for (int q = 0; q < ngr; ++q) {
-        // the next group's indices: loaded here, stored after the C phase hides their latency
-        const int next_idx = q + 1 < ngr ? fetch_idx(q + 1) : 0;
-        const int buf = q & 1;
+    // C(q): Haar analysis, threshold (FP64 inside the guard band), synthesis, by the NF fibre threads
+    auto phase_c = [&](const int q) {
         const int grp = group_of(q);
-        float* gbq = gbb + buf * K * G::GS;
-        const int* pos = posb + buf * 64;
-        int* misc = miscb + buf * 16;
-        const float* pn = pnb + buf * 32;
-
-        // ---- C: Haar analysis, threshold (FP64 inside the guard band), synthesis
+        float* gbq = gb_of(q);
+        const int* pos = pos_of(q);
+        int* misc = misc_of(q);
+        const float* pn = pn_of(q);
         // final keep decisions of the warp's fibres: optional mask output, kept count
         auto keep_finish = [&](uint32_t keepb) {
             if (a.mask_out) {                             // words cleared a phase earlier
@@ -721,53 +1048,71 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = w[k];
             }
         }
-        __syncthreads();
-        // ---- D, E: inverse projection; positions and counters of the next group
-        if (tid < 8 * K) {
-            stage_d<C>(bas, gbq, tid >> 3, tid & 7);
-            __syncwarp(kAB);
-            stage_e<C>(bas, gbq, tid >> 3, tid & 7);
+    };
+
+    // iteration q: [D, E(q) | A, B(q+1)] then [F(q), C(q+1)]; q = -1 only projects and thresholds group 0
+    store_pos(fetch_idx(0), pos_of(0));
+    if (tid < 48) miscb[tid] = 0;
+    __syncthreads();
+
+    for (int q = -1; q < ngr; ++q) {
+        // indices of group q+2: loaded here, stored at the end of the second phase
+        const int next_idx = q + 2 < ngr ? fetch_idx(q + 2) : 0;
+
+        // ---- D, E(q) (inverse projection) on the first half | A, B(q+1) on the second half
+        if (q >= 0 && tid < NU) {
+            float* gbq = gb_of(q);
+            stage_d2<C>(bas, gbq, tid >> 2, tid & 3);
+            __syncwarp(kU);
+            stage_e2<C>(bas, gbq, tid >> 2, tid & 3);
+        } else if (tid >= AB0 && tid < AB0 + NU && q + 1 < ngr) {
+            project(tid - AB0, q + 1);
         }
-        if (q + 1 < ngr) {
-            store_pos(next_idx, posb + (buf ^ 1) * 64);
-            if (tid < 16) miscb[(buf ^ 1) * 16 + tid] = 0;
-            clear_masks(q + 1);
-        }
+        if (q + 1 < ngr) clear_masks(q + 1);
         __syncthreads();
-        // ---- F(q): aggregation (warp `warp` owns footprint rows r with r % 8 == warp) ...
-        float wg = 1.f;
-        if (a.w_in) wg = a.w_in[grp];
-        else if (a.agg_mode == 1) wg = 1.f / (float)max(1, misc[1]);
-        if (tid == 0 && a.weights_out) a.weights_out[grp] = wg;
-        {
-            // lane k precomputes, for patch k, the offsets of the row that this warp adds (its
-            // footprint row r has r % 8 == warp) in the accumulator and in the group buffer; the
-            // loop broadcasts them. Lane roles: C = 3: 24 numerator lanes (pixel j, channel c) and
-            // 8 weight lanes; C = 1: 8 and 8.
-            int my_aoff = 0, my_goff = 0;
-            if (lane < K) {
-                const int py = pos[2 * lane], px = pos[2 * lane + 1];
-                const int i = (warp - py) & 7;
-                my_aoff = ((py + i) * FW + px) * G::ACC;
-                my_goff = lane * G::GS + i * G::ROW;
-            }
-            constexpr int NV = PS * C;                // numerator lanes
-            const bool num = lane < NV, act = lane < NV + PS;
-            const int lofs = num ? (lane / C) * G::ACC + (lane % C) : (lane - NV) * G::ACC + C;
-#pragma unroll 4
-            for (int k = 0; k < K; ++k) {
-                const int aoff = __shfl_sync(0xffffffffu, my_aoff, k);
-                const int goff = __shfl_sync(0xffffffffu, my_goff, k);
-                if (act) {
-                    const float x = num ? gbq[goff + lane] : 1.f;
-                    acc[aoff + lofs] += wg * x;
+        if (q >= 0) {
+            const int grp = group_of(q);
+            const float* gbq = gb_of(q);
+            const int* pos = pos_of(q);
+            const int* misc = misc_of(q);
+            // ---- F(q): aggregation (warp `warp` owns footprint rows r with r % 8 == warp) ...
+            float wg = 1.f;
+            if (a.w_in) wg = a.w_in[grp];
+            else if (a.agg_mode == 1) wg = 1.f / (float)max(1, misc[1]);
+            if (tid == 0 && a.weights_out) a.weights_out[grp] = wg;
+            {
+                // lane k precomputes, for patch k, the offsets of the row that this warp adds (its
+                // footprint row r has r % 8 == warp) in the accumulator and in the group buffer; the
+                // loop broadcasts them. Lane roles: C = 3: 24 numerator lanes (pixel j, channel c) and
+                // 8 weight lanes; C = 1: 8 and 8.
+                int my_aoff = 0, my_goff = 0;
+                if (lane < K) {
+                    const int py = pos[2 * lane], px = pos[2 * lane + 1];
+                    const int i = (warp - py) & 7;
+                    my_aoff = ((py + i) * FW + px) * G::ACC;
+                    my_goff = lane * G::GS + i * G::ROW;
                 }
-                __syncwarp();                         // orders the read-modify-writes of patches k, k+1
+                constexpr int NV = PS * C;                // numerator lanes
+                const bool num = lane < NV, act = lane < NV + PS;
+                const int lofs = num ? (lane / C) * G::ACC + (lane % C) : (lane - NV) * G::ACC + C;
+#pragma unroll 4
+                for (int k = 0; k < K; ++k) {
+                    const int aoff = __shfl_sync(0xffffffffu, my_aoff, k);
+                    const int goff = __shfl_sync(0xffffffffu, my_goff, k);
+                    if (act) {
+                        const float x = num ? gbq[goff + lane] : 1.f;
+                        acc[aoff + lofs] += wg * x;
+                    }
+                    __syncwarp();                         // orders the read-modify-writes of patches k, k+1
+                }
             }
         }
-        // ... overlapped with A, B(q+1) into the other buffer
-        if (q + 1 < ngr)
-            project(gbb + (buf ^ 1) * K * G::GS, posb + (buf ^ 1) * 64, miscb + (buf ^ 1) * 16, pnb + (buf ^ 1) * 32);
+        // ... then C(q+1); positions and counters of q+2 into the slot that q-1 used
+        if (q + 1 < ngr) phase_c(q + 1);
+        if (q + 2 < ngr) {
+            store_pos(next_idx, pos_of(q + 2));
+            if (tid < 16) misc_of(q + 2)[tid] = 0;
+        }
         __syncthreads();
     }
     // Write the tile partial.
