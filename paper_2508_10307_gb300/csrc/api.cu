@@ -321,13 +321,22 @@ double sigma_from_moments(const unsigned long long* M, const unsigned long long*
     return std::sqrt(m > 0 ? m : 0.0);
 }
 
-// Launches the moments of the quantised image and the basis solve.
-htsvd_status run_basis(Workspace* w, const uint8_t* q, const Geo& g, double** b64, float** b32, cudaStream_t s) {
+// Launches the moments of the quantised image and the basis solve. With fullM (the full second
+// moment of the same references, already formed on this stream's predecessors) the row and
+// column moments are summed from it instead of re-read from the image.
+htsvd_status run_basis(Workspace* w, const uint8_t* q, const Geo& g, double** b64, float** b32, cudaStream_t s,
+                       const unsigned long long* fullM = nullptr) {
     void *mom, *p64, *p32;
     ST(ws_get(w, S_MOM, sizeof(unsigned long long) * 2 * PS2 * g.C * g.C, &mom));
     ST(ws_get(w, S_B64, sizeof(double) * 2 * 2 * g.C * PS2, &p64));
     ST(ws_get(w, S_B32, sizeof(float) * 512, &p32));
-    { ProfScope ps_("moments", s); CK(launch_moments(q, g, (unsigned long long*)mom, s)); }
+    if (fullM) {
+        ProfScope ps_("moments_from_full", s);
+        CK(launch_moments_from_full(fullM, g.C, (unsigned long long*)mom, s));
+    } else {
+        ProfScope ps_("moments", s);
+        CK(launch_moments(q, g, (unsigned long long*)mom, s));
+    }
     { ProfScope ps_("basis", s); CK(launch_basis((const unsigned long long*)mom, g.C, (double*)p64, (float*)p32, s)); }
     *b64 = (double*)p64;
     *b32 = (float*)p32;
@@ -472,7 +481,9 @@ htsvd_status denoise_impl(const void* d_in, int is_float, int H, int W, int C, d
     CK(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
     double* b64;
     float* b32;
-    ST(run_basis(w, q, g, &b64, &b32, w->side));
+    void* fullM = nullptr;
+    if (sigma < 0) ST(ws_get(w, S_FULLM, sizeof(unsigned long long) * PS2 * C * PS2 * C, &fullM));
+    ST(run_basis(w, q, g, &b64, &b32, w->side, (const unsigned long long*)fullM));
     CK(cudaEventRecord(w->ev_join, w->side));
     ST(run_block_match(q, g, r, 1, idx, s));
     CK(cudaStreamWaitEvent(s, w->ev_join, 0));

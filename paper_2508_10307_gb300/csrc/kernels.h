@@ -30,6 +30,9 @@ cudaError_t launch_block_match(const BMArgs& a, cudaStream_t s);
 //   Q[b][b'][c][c'] = sum_r sum_a P_r[a][b][c] P_r[a][b'][c']
 // stored as uint64 [2][8][8][C][C] (R then Q).
 cudaError_t launch_moments(const uint8_t* img, const Geo& g, unsigned long long* d_mom, cudaStream_t s);
+// Row and column moments derived exactly from the full second moment (lower triangle) that
+// launch_full_moment wrote; replaces launch_moments where the full moment is already formed.
+cudaError_t launch_moments_from_full(const unsigned long long* d_M, int C, unsigned long long* d_mom, cudaStream_t s);
 // Full second moment M[u][v] = sum_r p_r[u] p_r[v] (d = 64 C) and s[u] = sum_r p_r[u], uint64.
 cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long long* d_M,
                                unsigned long long* d_s, cudaStream_t s);

@@ -110,6 +110,35 @@ __global__ void __launch_bounds__(256) moments_batch_kernel(const BMArgs* __rest
     }
 }
 
+// Row and column moments from the full second moment M (entry u = a*8C + b*C + c of the packed
+// patch; lower triangle u >= v filled): R[a][a'][c][c'] = sum_b M[(a,b,c)][(a',b,c')] and
+// Q[b][b'][c][c'] = sum_a M[(a,b,c)][(a,b',c')]. Integer sums, so the result equals the direct
+// moments exactly. One thread per entry, written (not added) in the layout of moments_chunk.
+template <int C>
+__global__ void __launch_bounds__(256) moments_from_full_kernel(const unsigned long long* __restrict__ M,
+                                                                unsigned long long* __restrict__ out) {
+    constexpr int d = PS2 * C;
+    constexpr int NE = 2 * PS * PS * C * C;
+    const int ent = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ent >= NE) return;
+    const int which = ent / (PS * PS * C * C);
+    int rem = ent - which * PS * PS * C * C;
+    const int u = rem / (PS * C * C);
+    rem -= u * PS * C * C;
+    const int v = rem / (C * C);
+    rem -= v * C * C;
+    const int c = rem / C, c2 = rem - c * C;
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int t = 0; t < PS; ++t) {
+        // which 0: rows (a, a') = (u, v), summed over the column t; which 1: columns (b, b') = (u, v), over the row t
+        const int i = which == 0 ? u * PS * C + t * C + c : t * PS * C + u * C + c;
+        const int j = which == 0 ? v * PS * C + t * C + c2 : t * PS * C + v * C + c2;
+        sum += i >= j ? M[(size_t)i * d + j] : M[(size_t)j * d + i];
+    }
+    out[ent] = sum;
+}
+
 // Full second moment: CTA (bx, tile) accumulates a 64x64 tile of M over a chunk of references.
 // The patch values of 4 consecutive references are packed per 32-bit word ([u][ref/4]), so one
 // dp4a adds the products of 4 references; each thread owns a 4x4 block of the tile. M is
@@ -720,6 +749,13 @@ cudaError_t launch_moments_batch(int C, const BMArgs* d_args, unsigned long long
 cudaError_t launch_basis_batch(int C, const FilterArgs* d_fargs, unsigned long long* const* d_moms, int nimg,
                                cudaStream_t s) {
     basis_batch_kernel<<<nimg * 2 * (C / 2 + 1), 32, 0, s>>>(d_fargs, d_moms, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_from_full(const unsigned long long* d_M, int C, unsigned long long* d_mom, cudaStream_t s) {
+    const int ne = 2 * PS2 * C * C;
+    if (C == 3) moments_from_full_kernel<3><<<(ne + 255) / 256, 256, 0, s>>>(d_M, d_mom);
+    else moments_from_full_kernel<1><<<(ne + 255) / 256, 256, 0, s>>>(d_M, d_mom);
     return cudaGetLastError();
 }
 

@@ -134,6 +134,21 @@ def test_deterministic_bitwise():
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("shape,prm", [
+    ((96, 80, 3), dict(ps=8, stride=3, window=15, K=16)),
+    ((70, 90, 1), dict(ps=8, stride=2, window=13, K=8)),
+])
+def test_bases_from_the_full_moment_equal_the_direct_ones(shape, prm):
+    # with sigma estimated the row/column moments are summed from the full second moment; with
+    # sigma given they are read from the image: both are exact integer sums, so the bases agree bitwise
+    img = synth.quantize(synth.add_gaussian(synth.clean_image(*shape, seed=77), 20.0, seed=78))
+    x = _dev(img)
+    _, est = H.denoise(x, None, prm, return_info=True, basis=True)
+    _, giv = H.denoise(x, 20.0, prm, return_info=True, basis=True)
+    torch.cuda.synchronize()
+    assert torch.equal(est["basis"], giv["basis"])
+
+
 def test_estimate_sigma_matches_oracle():
     clean, noisy, sigma, prm, r = oracle_run("rgb512")
     s = H.estimate_sigma(_dev(noisy), prm)
