@@ -24,7 +24,8 @@ inline void st2(double* p, v2d x) { __builtin_memcpy(p, &x, sizeof(x)); }
 // with H = I - beta v v^T (H x = alpha e_1 for x = A[k+1:, k]): p = beta B v,
 // w = p - (beta/2)(v^T p) v, B <- B - v w^T - w v^T. The rank-2 update of step k is deferred
 // and applied to each row of the trailing triangle in the same pass that forms p of step k+1,
-// so the triangle is read and written once per step; the pass runs on two-double vectors.
+// so the triangle is read and written once per step; the pass runs on two-double vectors, two
+// rows at a time.
 void tridiagonalize(double* A, int n, double* d, double* e) {
     std::vector<double> vb(n, 0.0), wb(n, 0.0), v(n), p(n);     // (vb, wb): deferred update, absolute indices
     bool pending = false;
@@ -52,49 +53,73 @@ void tridiagonalize(double* A, int n, double* d, double* e) {
         }
         e[k] = alpha;
         // one pass over the trailing lower triangle: deferred update of row i, then its part of
-        // p = B v (row i gives its dot product to p_i and, by symmetry, L_ij v_i to p_j, j < i)
+        // p = B v (row i gives its dot product to p_i and, by symmetry, L_ij v_i to p_j, j < i).
+        // Rows go in pairs (i, i+1) so that each load of v, p and the deferred (vb, wb) serves both.
         const double* vo = vb.data() + k + 1;
         const double* wo = wb.data() + k + 1;
-        for (int i = 0; i < m; ++i) p[i] = 0.0;
-        for (int i = 0; i < m; ++i) {
-            double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
-            const double vi = v[i], voi = vo[i], woi = wo[i];
-            const v2d VI = {vi, vi}, VOI = {voi, voi}, WOI = {woi, woi};
-            v2d S0 = {0.0, 0.0}, S1 = {0.0, 0.0};                // four partial sums of the dot product
-            double s = 0.0;
+        const double* vv = v.data();
+        double* pp = p.data();
+        for (int i = 0; i < m; ++i) pp[i] = 0.0;
+        const double pend = pending ? 1.0 : 0.0;     // the deferred update is zero at the first step
+        int i = 0;
+        for (; i + 2 <= m; i += 2) {
+            double* ra = A + (size_t)(k + 1 + i) * n + (k + 1);
+            double* rb = ra + n;
+            const double va = vv[i], vb1 = vv[i + 1];
+            const double voa = pend * vo[i], woa = pend * wo[i], vob = pend * vo[i + 1], wob = pend * wo[i + 1];
+            const v2d VA = {va, va}, VB = {vb1, vb1};
+            const v2d VOA = {voa, voa}, WOA = {woa, woa}, VOB = {vob, vob}, WOB = {wob, wob};
+            v2d Sa0 = {0.0, 0.0}, Sa1 = {0.0, 0.0}, Sb0 = {0.0, 0.0}, Sb1 = {0.0, 0.0};
+            double sa = 0.0, sb = 0.0;
             int j = 0;
-            if (pending) {
-                for (; j + 4 <= i; j += 4) {
-                    const v2d r0 = ld2(row + j) - (VOI * ld2(wo + j) + WOI * ld2(vo + j));
-                    const v2d r1 = ld2(row + j + 2) - (VOI * ld2(wo + j + 2) + WOI * ld2(vo + j + 2));
-                    st2(row + j, r0);
-                    st2(row + j + 2, r1);
-                    S0 += r0 * ld2(v.data() + j);
-                    S1 += r1 * ld2(v.data() + j + 2);
-                    st2(p.data() + j, ld2(p.data() + j) + r0 * VI);
-                    st2(p.data() + j + 2, ld2(p.data() + j + 2) + r1 * VI);
-                }
-                for (; j < i; ++j) {
-                    const double r0 = row[j] - (voi * wo[j] + woi * vo[j]);
-                    row[j] = r0;
-                    s += r0 * v[j];
-                    p[j] += r0 * vi;
-                }
-                row[i] -= voi * wo[i] + woi * vo[i];
-            } else {
-                for (; j + 4 <= i; j += 4) {
-                    const v2d r0 = ld2(row + j), r1 = ld2(row + j + 2);
-                    S0 += r0 * ld2(v.data() + j);
-                    S1 += r1 * ld2(v.data() + j + 2);
-                    st2(p.data() + j, ld2(p.data() + j) + r0 * VI);
-                    st2(p.data() + j + 2, ld2(p.data() + j + 2) + r1 * VI);
-                }
-                for (; j < i; ++j) {
-                    s += row[j] * v[j];
-                    p[j] += row[j] * vi;
-                }
+            for (; j + 4 <= i; j += 4) {
+                const v2d w0 = ld2(wo + j), w1 = ld2(wo + j + 2), o0 = ld2(vo + j), o1 = ld2(vo + j + 2);
+                const v2d x0 = ld2(vv + j), x1 = ld2(vv + j + 2);
+                const v2d a0 = ld2(ra + j) - (VOA * w0 + WOA * o0), a1 = ld2(ra + j + 2) - (VOA * w1 + WOA * o1);
+                const v2d b0 = ld2(rb + j) - (VOB * w0 + WOB * o0), b1 = ld2(rb + j + 2) - (VOB * w1 + WOB * o1);
+                st2(ra + j, a0);
+                st2(ra + j + 2, a1);
+                st2(rb + j, b0);
+                st2(rb + j + 2, b1);
+                Sa0 += a0 * x0;
+                Sa1 += a1 * x1;
+                Sb0 += b0 * x0;
+                Sb1 += b1 * x1;
+                st2(pp + j, ld2(pp + j) + (a0 * VA + b0 * VB));
+                st2(pp + j + 2, ld2(pp + j + 2) + (a1 * VA + b1 * VB));
             }
-            p[i] += (((S0[0] + S0[1]) + (S1[0] + S1[1])) + s) + row[i] * vi;
+            for (; j < i; ++j) {
+                const double a0 = ra[j] - (voa * wo[j] + woa * vo[j]);
+                const double b0 = rb[j] - (vob * wo[j] + wob * vo[j]);
+                ra[j] = a0;
+                rb[j] = b0;
+                sa += a0 * vv[j];
+                sb += b0 * vv[j];
+                pp[j] += a0 * va + b0 * vb1;
+            }
+            // column i: the diagonal of row i and the last off-diagonal entry of row i+1
+            const double da = ra[i] - (voa * wo[i] + woa * vo[i]);
+            const double bi = rb[i] - (vob * wo[i] + wob * vo[i]);
+            ra[i] = da;
+            rb[i] = bi;
+            const double db = rb[i + 1] - (vob * wo[i + 1] + wob * vo[i + 1]);
+            rb[i + 1] = db;
+            sb += bi * va;
+            pp[i] += (((Sa0[0] + Sa0[1]) + (Sa1[0] + Sa1[1])) + sa) + da * va + bi * vb1;
+            pp[i + 1] += (((Sb0[0] + Sb0[1]) + (Sb1[0] + Sb1[1])) + sb) + db * vb1;
+        }
+        for (; i < m; ++i) {                                      // the last row when m is odd
+            double* row = A + (size_t)(k + 1 + i) * n + (k + 1);
+            const double vi = vv[i], voi = pend * vo[i], woi = pend * wo[i];
+            double s = 0.0;
+            for (int j = 0; j < i; ++j) {
+                const double r0 = row[j] - (voi * wo[j] + woi * vo[j]);
+                row[j] = r0;
+                s += r0 * vv[j];
+                pp[j] += r0 * vi;
+            }
+            row[i] -= voi * wo[i] + woi * vo[i];
+            pp[i] += s + row[i] * vi;
         }
         double vp = 0.0;
         for (int i = 0; i < m; ++i) {
@@ -120,6 +145,9 @@ void tridiagonalize(double* A, int n, double* d, double* e) {
 //   gamma_{k+1} = c_k^2 (a_{k+1} - mu) - s_k^2 gamma_k,   a'_k = gamma_k + a_{k+1} - gamma_{k+1},
 //   b'_{k-1}^2 = s_{k-1}^2 r_k^2,   pi_{k+1}^2 = gamma_{k+1}^2 / c_k^2 (= c_{k-1}^2 b_k^2 if c_k = 0),
 // and at the end of the segment a'_hi = mu + gamma_hi, b'_{hi-1}^2 = s_{hi-1}^2 pi_hi^2.
+// The chase is one long dependency chain through pi_k^2, so it is evaluated with a single
+// division on that chain: with nu = pi_k^2 (a_{k+1} - mu) - b_k^2 gamma_k, gamma_{k+1} = nu / r_k^2
+// and pi_{k+1}^2 = nu^2 / (r_k^2 pi_k^2); the other quotients are off the chain.
 bool tridiagonal_eigenvalues(double* a, double* e2, int n) {
     const double eps = 2.220446049250313e-16, eps2 = eps * eps;
     auto negligible = [&](int k) {
@@ -147,12 +175,11 @@ bool tridiagonal_eigenvalues(double* a, double* e2, int n) {
             const double b2 = e2[k];
             const double r2 = pi2 + b2;
             if (k > lo) e2[k - 1] = s2p * r2;
-            // the three quotients depend only on pi2 and b2; 1/c2 is taken directly so that the
-            // next pivot does not wait for c2
-            const double c2 = pi2 / r2, s2 = b2 / r2, inv_c2 = r2 / pi2;
-            const double gn = c2 * (a[k + 1] - mu) - s2 * gam;
+            const double nu = pi2 * (a[k + 1] - mu) - b2 * gam;
+            const double gn = nu / r2;
+            const double c2 = pi2 / r2, s2 = b2 / r2;
             a[k] = gam + (a[k + 1] - gn);
-            pi2 = pi2 != 0.0 ? gn * gn * inv_c2 : c2p * b2;
+            pi2 = pi2 != 0.0 ? (nu * nu) / (r2 * pi2) : c2p * b2;
             c2p = c2;
             s2p = s2;
             gam = gn;
