@@ -42,6 +42,11 @@ def _params():
     return prm
 
 
+# DRAM bytes (read + write) of one launch of the forward filter kernel, from one ncu capture of
+# the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); workloads not captured: None.
+FILTER_DRAM_BYTES = {"rgb512": 9.065472e6 + 26.100480e6}
+
+
 def filter_flops_per_group(C: int, K: int) -> int:
     """Algorithmic FP32 flops of one group in the structured per-Fourier-slice form:
     t-SVD projections (per patch and direction: 10,240 for C=3, 2,048 for C=1), channel DFTs
@@ -393,7 +398,7 @@ def run_gpu(args):
         achieved = flops / (ms / n_launch / 1000.0) / 1e12
         peak = NUM_SMS * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "group_filter",
+                "traffic": FILTER_DRAM_BYTES.get(args.workload), "kernel": "group_filter",
                 "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts and max clock)"}
     elif dom is not None:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
