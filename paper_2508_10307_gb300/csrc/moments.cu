@@ -168,25 +168,56 @@ __global__ void __launch_bounds__(256) full_moment_kernel(const uint8_t* __restr
     for (int rb = r0; rb < r1; rb += FM_BATCH) {
         const int nb = min(FM_BATCH, r1 - rb);
         __syncthreads();
-        // (reference j, patch row i): the row's 8*C bytes are contiguous in the image and land on
-        // entries u = i*8*C + b of the packed matrix (all loads of a row issued together)
-        for (int t = threadIdx.x; t < FM_BATCH * PS; t += 256) {
-            const int j = t >> 3, i = t & 7;
-            uint8_t* dst = reinterpret_cast<uint8_t*>(&pk[i * ROWB][0]) + (j >> 2) * 4 + (j & 3);
-            uint8_t v[ROWB];
-            if (j < nb) {
-                const int r = rb + j;
-                const int iy = r / g.nrx, ix = r - iy * g.nrx;
-                const int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
-                const uint8_t* src = img + ((size_t)(ry + i) * g.W + rx) * C;
+        // Task (quad jq, patch row i, part h): the part's HB bytes of row i of references 4jq..4jq+3
+        // (contiguous in the image) are read as aligned 32-bit words, shifted into place, and
+        // transposed 4 x 4 so that word (u, jq) holds byte u of the four references. Only rows that
+        // meet this CTA's two 64-row blocks are staged (the others are never read here).
+        {
+            constexpr int HB = ROWB / 2;              // bytes per part: 12 (C = 3) or 4 (C = 1)
+            constexpr int NWD = HB / 4;               // whole words per part
+            const int t = threadIdx.x;
+            const int h = t & 1, i = (t >> 1) & 7, jq = t >> 4;
+            const int u0 = i * ROWB + h * HB;
+            const bool need = (u0 < tu * 64 + 64 && u0 + HB > tu * 64) || (u0 < tv * 64 + 64 && u0 + HB > tv * 64);
+            if (jq < FM_BATCH / 4 && need) {
+                uint32_t al[4][NWD];                  // [reference][word] aligned row bytes
 #pragma unroll
-                for (int b = 0; b < ROWB; ++b) v[b] = src[b];
-            } else {
+                for (int q = 0; q < 4; ++q) {
+                    const int j = jq * 4 + q;
 #pragma unroll
-                for (int b = 0; b < ROWB; ++b) v[b] = 0;
+                    for (int wd = 0; wd < NWD; ++wd) al[q][wd] = 0u;
+                    if (j < nb) {
+                        const int r = rb + j;
+                        const int iy = r / g.nrx, ix = r - iy * g.nrx;
+                        const int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
+                        // alignment from the absolute address: the image may start at any byte
+                        const uintptr_t a = reinterpret_cast<uintptr_t>(img + ((size_t)(ry + i) * g.W + rx) * C + h * HB);
+                        const int o = (int)(a & 3);
+                        // every word read holds at least one byte of the part, so none leaves the image's
+                        // aligned words
+                        const uint32_t* w = reinterpret_cast<const uint32_t*>(a - o);
+                        uint32_t wv[NWD + 1];
+#pragma unroll
+                        for (int wd = 0; wd < NWD; ++wd) wv[wd] = w[wd];
+                        // the word after the part holds needed bytes only when the part is unaligned
+                        wv[NWD] = o ? w[NWD] : 0u;
+#pragma unroll
+                        for (int wd = 0; wd < NWD; ++wd) al[q][wd] = __funnelshift_r(wv[wd], wv[wd + 1], 8 * o);
+                    }
+                }
+#pragma unroll
+                for (int wd = 0; wd < NWD; ++wd) {
+                    const uint32_t lo01 = __byte_perm(al[0][wd], al[1][wd], 0x5140u);
+                    const uint32_t hi01 = __byte_perm(al[0][wd], al[1][wd], 0x7362u);
+                    const uint32_t lo23 = __byte_perm(al[2][wd], al[3][wd], 0x5140u);
+                    const uint32_t hi23 = __byte_perm(al[2][wd], al[3][wd], 0x7362u);
+                    const int u = u0 + wd * 4;
+                    pk[u + 0][jq] = __byte_perm(lo01, lo23, 0x5410u);
+                    pk[u + 1][jq] = __byte_perm(lo01, lo23, 0x7632u);
+                    pk[u + 2][jq] = __byte_perm(hi01, hi23, 0x5410u);
+                    pk[u + 3][jq] = __byte_perm(hi01, hi23, 0x7632u);
+                }
             }
-#pragma unroll
-            for (int b = 0; b < ROWB; ++b) dst[b * FM_WPAD * 4] = v[b];
         }
         __syncthreads();
         const int nw = (nb + 3) >> 2;
