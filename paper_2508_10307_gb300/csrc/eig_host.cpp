@@ -137,6 +137,37 @@ void tridiagonalize(double* A, int n, double* d, double* e) {
     if (n >= 2) e[n - 2] = A[(size_t)(n - 1) * n + (n - 2)];
 }
 
+// State of one QR sweep in flight over the segment [lo, hi] with shift mu.
+struct Sweep {
+    double mu, gam, pi2, c2p, s2p;
+};
+
+// Step k of a sweep (k = lo starts it): reads a[k+1], e2[k]; writes a[k] and e2[k-1].
+inline void sweep_step(double* a, double* e2, int lo, int k, Sweep& S) {
+    if (k == lo) {
+        S.gam = a[lo] - S.mu;
+        S.pi2 = S.gam * S.gam;
+        S.c2p = 1.0;
+        S.s2p = 0.0;
+    }
+    const double b2 = e2[k];
+    const double r2 = S.pi2 + b2;
+    if (k > lo) e2[k - 1] = S.s2p * r2;
+    const double nu = S.pi2 * (a[k + 1] - S.mu) - b2 * S.gam;
+    const double gn = nu / r2;
+    const double c2 = S.pi2 / r2, s2 = b2 / r2;
+    a[k] = S.gam + (a[k + 1] - gn);
+    S.pi2 = S.pi2 != 0.0 ? (nu * nu) / (r2 * S.pi2) : S.c2p * b2;
+    S.c2p = c2;
+    S.s2p = s2;
+    S.gam = gn;
+}
+
+inline void sweep_end(double* a, double* e2, int hi, const Sweep& S) {
+    e2[hi - 1] = S.s2p * S.pi2;
+    a[hi] = S.mu + S.gam;
+}
+
 // Eigenvalues of the symmetric tridiagonal matrix (a, e2) in place in a, where e2 holds the
 // SQUARES of the off-diagonal entries. One shifted QR step T - mu I = QR, T' = RQ + mu I with
 // Givens rotations (c_k, s_k), written with gamma_k = c_{k-1} pi_k (pi_k: the k-th pivot of R
@@ -147,7 +178,9 @@ void tridiagonalize(double* A, int n, double* d, double* e) {
 // and at the end of the segment a'_hi = mu + gamma_hi, b'_{hi-1}^2 = s_{hi-1}^2 pi_hi^2.
 // The chase is one long dependency chain through pi_k^2, so it is evaluated with a single
 // division on that chain: with nu = pi_k^2 (a_{k+1} - mu) - b_k^2 gamma_k, gamma_{k+1} = nu / r_k^2
-// and pi_{k+1}^2 = nu^2 / (r_k^2 pi_k^2); the other quotients are off the chain.
+// and pi_{k+1}^2 = nu^2 / (r_k^2 pi_k^2); the other quotients are off the chain. Segments of four
+// or more run two sweeps at once (shifts: both eigenvalues of the trailing 2x2 block), one
+// trailing the other, so that two independent chains share the core.
 bool tridiagonal_eigenvalues(double* a, double* e2, int n) {
     const double eps = 2.220446049250313e-16, eps2 = eps * eps;
     auto negligible = [&](int k) {
@@ -170,22 +203,22 @@ bool tridiagonal_eigenvalues(double* a, double* e2, int n) {
         const double bb = e2[hi - 1];
         const double den = dd + (dd >= 0 ? 1.0 : -1.0) * std::sqrt(dd * dd + bb);
         const double mu = a[hi] - (den != 0.0 ? bb / den : 0.0);
-        double gam = a[lo] - mu, pi2 = gam * gam, c2p = 1.0, s2p = 0.0;
-        for (int k = lo; k < hi; ++k) {
-            const double b2 = e2[k];
-            const double r2 = pi2 + b2;
-            if (k > lo) e2[k - 1] = s2p * r2;
-            const double nu = pi2 * (a[k + 1] - mu) - b2 * gam;
-            const double gn = nu / r2;
-            const double c2 = pi2 / r2, s2 = b2 / r2;
-            a[k] = gam + (a[k + 1] - gn);
-            pi2 = pi2 != 0.0 ? (nu * nu) / (r2 * pi2) : c2p * b2;
-            c2p = c2;
-            s2p = s2;
-            gam = gn;
+        Sweep s1{mu, 0.0, 0.0, 0.0, 0.0};
+        if (hi - lo < 3) {
+            for (int k = lo; k < hi; ++k) sweep_step(a, e2, lo, k, s1);
+            sweep_end(a, e2, hi, s1);
+            continue;
         }
-        e2[hi - 1] = s2p * pi2;
-        a[hi] = mu + gam;
+        // Two sweeps in flight: the second, shifted by the block's other eigenvalue, trails the
+        // first by two positions (step k reads a[k+1] and e2[k], which the first sweep finished at
+        // its step k+1), so the two dependency chains overlap.
+        Sweep s2{(a[hi - 1] + a[hi]) - mu, 0.0, 0.0, 0.0, 0.0};
+        for (int t = lo; t < hi + 2; ++t) {
+            if (t < hi) sweep_step(a, e2, lo, t, s1);
+            else if (t == hi) sweep_end(a, e2, hi, s1);
+            if (t - 2 >= lo) sweep_step(a, e2, lo, t - 2, s2);
+        }
+        sweep_end(a, e2, hi, s2);
     }
     return true;
 }
