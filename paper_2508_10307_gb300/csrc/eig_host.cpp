@@ -25,7 +25,9 @@ inline void st2(double* p, v2d x) { __builtin_memcpy(p, &x, sizeof(x)); }
 // w = p - (beta/2)(v^T p) v, B <- B - v w^T - w v^T. The rank-2 update of step k is deferred
 // and applied to each row of the trailing triangle in the same pass that forms p of step k+1,
 // so the triangle is read and written once per step; the pass runs on two-double vectors, two
-// rows at a time.
+// rows at a time. Its expressions are chains of multiply-adds (r - v w - w' v', p + a v + b v'), so
+// that each entry costs four fused operations per row where a compiler contracts them: the pass
+// is bound by floating-point issue, not by memory.
 void tridiagonalize(double* A, int n, double* d, double* e) {
     std::vector<double> vb(n, 0.0), wb(n, 0.0), v(n), p(n);     // (vb, wb): deferred update, absolute indices
     bool pending = false;
@@ -75,8 +77,8 @@ void tridiagonalize(double* A, int n, double* d, double* e) {
             for (; j + 4 <= i; j += 4) {
                 const v2d w0 = ld2(wo + j), w1 = ld2(wo + j + 2), o0 = ld2(vo + j), o1 = ld2(vo + j + 2);
                 const v2d x0 = ld2(vv + j), x1 = ld2(vv + j + 2);
-                const v2d a0 = ld2(ra + j) - (VOA * w0 + WOA * o0), a1 = ld2(ra + j + 2) - (VOA * w1 + WOA * o1);
-                const v2d b0 = ld2(rb + j) - (VOB * w0 + WOB * o0), b1 = ld2(rb + j + 2) - (VOB * w1 + WOB * o1);
+                const v2d a0 = (ld2(ra + j) - VOA * w0) - WOA * o0, a1 = (ld2(ra + j + 2) - VOA * w1) - WOA * o1;
+                const v2d b0 = (ld2(rb + j) - VOB * w0) - WOB * o0, b1 = (ld2(rb + j + 2) - VOB * w1) - WOB * o1;
                 st2(ra + j, a0);
                 st2(ra + j + 2, a1);
                 st2(rb + j, b0);
@@ -85,8 +87,8 @@ void tridiagonalize(double* A, int n, double* d, double* e) {
                 Sa1 += a1 * x1;
                 Sb0 += b0 * x0;
                 Sb1 += b1 * x1;
-                st2(pp + j, ld2(pp + j) + (a0 * VA + b0 * VB));
-                st2(pp + j + 2, ld2(pp + j + 2) + (a1 * VA + b1 * VB));
+                st2(pp + j, (ld2(pp + j) + a0 * VA) + b0 * VB);
+                st2(pp + j + 2, (ld2(pp + j + 2) + a1 * VA) + b1 * VB);
             }
             for (; j < i; ++j) {
                 const double a0 = ra[j] - (voa * wo[j] + woa * vo[j]);
