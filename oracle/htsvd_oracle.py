@@ -48,6 +48,14 @@ Readings where the paper is silent or ambiguous (each is listed in the design doc):
      t = max(1, floor(n / n_sub)) parts with boundaries floor(i n / t), so every
      subimage is at least n_sub long; each subimage gets its own noise estimate
      (R10, with R11 when adapt is set) and is denoised on its own (Alg. 1).
+  R16 video (Sec. IV, real-world color video denoising; the paper states only that
+     the patch search covers space and time and that the noise estimate runs frame
+     by frame): output frame t is Alg. 1 on frame t with frame t's own bases (R6)
+     and sigma; the candidates of a reference of frame t are the positions of its
+     spatial window (R4) in every frame max(0, t-T) .. min(F-1, t+T), the
+     reference itself excluded, compared on the plane its own patch selects (R1,
+     R2 on frame t); keys (SSD, f*H*W + y*W + x), ties -> lowest global index;
+     only the estimated patches that lie in frame t are aggregated into it.
 
 Parity pins for every function are in tests/test_oracle_pins.py.
 """
@@ -583,3 +591,161 @@ def a_haar_tsvd(x: np.ndarray, sub_h: int, sub_w: int, params=None):
             out[y0:y1, x0:x1] = denoise(sub, sg, p).out
     return out, np.array(sigmas)
 
+
+# --------------------------------------------------------------------------- video (Sec. IV, reading R16)
+
+def _match_plane_ssd_pair(ref_planes, cand_planes, ry, rxs, y0, ny, x0s, nx, ps):
+    """As _match_plane_ssd, with the reference patches taken from ref_planes and the candidates
+    from cand_planes (another frame): (n, ny, nx) int64."""
+    ssd = np.zeros((len(rxs), ny, nx), dtype=np.int64)
+    cols = x0s[:, None] + np.arange(nx)[None, :]
+    for rp, cp in zip(ref_planes, cand_planes):
+        cand = sliding_window_view(cp, (ps, ps))[y0:y0 + ny][:, cols]     # (ny, n, nx, i, j)
+        ref = sliding_window_view(rp, (ps, ps))[ry, rxs]                 # (n, i, j)
+        d = cand - ref[None, :, None]
+        ssd += np.einsum("ynxij,ynxij->nyx", d, d)
+    return ssd
+
+
+def _guide_planes(img: np.ndarray, mode: str):
+    """The integer planes of one frame for each matching mode: (byte planes, R+G+B plane)."""
+    x = img.astype(np.int64)
+    C = x.shape[2]
+    if mode == "full":
+        return [x[:, :, c] for c in range(C)], None
+    if C == 1:
+        return [x[:, :, 0]], None
+    return [x[:, :, 1]], x[:, :, 0] + x[:, :, 1] + x[:, :, 2]
+
+
+def _match_row_video(video: np.ndarray, t: int, ry: int, rxs: np.ndarray, p: Params, T: int):
+    """Reading R16: groups of the references (ry, rxs[n]) of frame t over frames t-T..t+T."""
+    F, H, Wd, C = video.shape
+    ps, K = p.ps, p.K
+    y0, ny = window_range(ry, H, ps, p.window)
+    xw = [window_range(int(rx), Wd, ps, p.window) for rx in rxs]
+    x0s = np.array([a for a, _ in xw], dtype=np.int64)
+    nx = xw[0][1]
+    mode = p.match_mode
+    if mode == "auto":
+        mode = "gray" if C == 1 else "gcp"
+    n = len(rxs)
+    if mode == "full" or C == 1 or mode == "gray":
+        green = np.ones(n, dtype=bool) if mode != "full" else np.zeros(n, dtype=bool)
+    else:
+        green = np.array([gcp_uses_green(video[t], ry, int(rx), ps, p.gcp_gamma) for rx in rxs])
+    rb, rs = _guide_planes(video[t], mode)
+    if mode == "gray" and C == 3:
+        rb = [video[t].astype(np.int64)[:, :, 1]]
+    f0, f1 = max(0, t - T), min(F - 1, t + T)
+    ssds, lins = [], []
+    for f in range(f0, f1 + 1):
+        cb, cs = _guide_planes(video[f], mode)
+        if mode == "gray" and C == 3:
+            cb = [video[f].astype(np.int64)[:, :, 1]]
+        sb = _match_plane_ssd_pair(rb, cb, ry, rxs, y0, ny, x0s, nx, ps)
+        if rs is not None and mode == "gcp":
+            ss = _match_plane_ssd_pair([rs], [cs], ry, rxs, y0, ny, x0s, nx, ps)
+            sb = np.where(green[:, None, None], sb, ss)
+        lin = (f * H * Wd + (y0 + np.arange(ny))[None, :, None] * Wd
+               + (x0s[:, None, None] + np.arange(nx)[None, None, :]))
+        ssds.append(sb.reshape(n, -1))
+        lins.append(np.broadcast_to(lin, sb.shape).reshape(n, -1))
+    ssd = np.concatenate(ssds, axis=1)
+    lin = np.concatenate(lins, axis=1)
+    ref_lin = t * H * Wd + ry * Wd + rxs
+    if ssd.shape[1] - 1 < K - 1:
+        raise ValueError("search window holds fewer than K candidates")
+    idx = np.empty((n, K), dtype=np.int64)
+    for r in range(n):
+        keep = lin[r] != ref_lin[r]
+        cl, cs = lin[r][keep], ssd[r][keep]
+        order = np.lexsort((cl, cs))[:K - 1]                 # ascending SSD, ties -> lowest global index
+        idx[r, 0] = ref_lin[r]
+        idx[r, 1:] = cl[order]
+    return idx, green
+
+
+def block_match_video(video: np.ndarray, t: int, params=None, T: int = 1):
+    """Reading R16 for every reference patch of frame t (row-major reference grid): global
+    indices f*H*W + y*W + x (N_ref, K), slot 0 the reference, and the per-reference green flags."""
+    p = Params.of(params)
+    if video.ndim == 3:
+        video = video[..., None]
+    F, H, Wd, C = video.shape
+    ys = reference_positions(H, p.ps, p.stride)
+    xs = reference_positions(Wd, p.ps, p.stride)
+    rows = [_match_row_video(video, t, int(ry), xs, p, T) for ry in ys]
+    return np.concatenate([r[0] for r in rows]), np.concatenate([r[1] for r in rows])
+
+
+def gather_groups_video(xv: np.ndarray, idx: np.ndarray, ps: int) -> np.ndarray:
+    """Stack the K patches named by global indices f*H*W + y*W + x: (n, K, ps, ps, C) float64."""
+    F, H, Wd, C = xv.shape
+    views = sliding_window_view(xv.astype(np.float64), (ps, ps), axis=(1, 2))    # [f, y, x, C, i, j]
+    f, rem = idx // (H * Wd), idx % (H * Wd)
+    g = views[f, rem // Wd, rem % Wd]                                              # [n, K, C, i, j]
+    return np.ascontiguousarray(np.moveaxis(g, 2, -1))
+
+
+def aggregate_frame(shape, t: int, idx: np.ndarray, Ghat: np.ndarray, w: np.ndarray, ps: int):
+    """Eq. (aggregation) restricted to frame t (reading R16): the estimated patches whose global
+    index lies in frame t are written back with their group's weight; the others are dropped."""
+    H, Wd, C = shape
+    inf = (idx // (H * Wd)) == t
+    loc = idx % (H * Wd)
+    g_i, k_i = np.nonzero(inf)
+    yy, xx = loc[g_i, k_i] // Wd, loc[g_i, k_i] % Wd
+    ii, jj = np.mgrid[0:ps, 0:ps]
+    pix = ((yy[:, None, None] + ii) * Wd + (xx[:, None, None] + jj)).ravel()
+    wg = w[g_i]
+    num = np.stack([np.bincount(pix, weights=(Ghat[g_i, k_i, :, :, c] * wg[:, None, None]).ravel(),
+                                minlength=H * Wd) for c in range(C)], axis=-1).reshape(H, Wd, C)
+    den = np.bincount(pix, weights=np.broadcast_to(wg[:, None, None], (wg.size, ps, ps)).ravel(),
+                      minlength=H * Wd).reshape(H, Wd)
+    return num, den
+
+
+def denoise_video(video: np.ndarray, sigma=None, params=None, T: int = 1, *, keep_masks=False, chunk=2048):
+    """Reading R16: a uint8 clip (F, H, W, C) denoised frame by frame with spatio-temporal grouping.
+    sigma None -> estimated per frame (R10, R11); else used for every frame.
+    Returns (output (F, H, W, C) float64, per-frame Results with global idx, masks and ambiguity)."""
+    p = Params.of(params)
+    if video.ndim == 3:
+        video = video[..., None]
+    F, H, Wd, C = video.shape
+    xv = video.astype(np.float64)
+    Hk = haar_matrix(p.K)
+    out = np.zeros((F, H, Wd, C))
+    results = []
+    for t in range(F):
+        frame = video[t]
+        sg = estimate_sigma(frame, p) if sigma is None else float(sigma)
+        idx, _ = block_match_video(video, t, p, T)
+        U, V, _, _ = global_basis(reference_patches(frame, p))
+        tau = tau_multiplier(p, C) * sg
+        n = idx.shape[0]
+        num = np.zeros((H, Wd, C))
+        den = np.zeros((H, Wd))
+        masks = np.zeros((n, p.K, p.ps, p.ps, C), dtype=bool) if keep_masks else None
+        w_out = np.ones(n)
+        amb = []
+        for a in range(0, n, chunk):
+            b = min(n, a + chunk)
+            G = gather_groups_video(xv, idx[a:b], p.ps)
+            S = forward_transform(G, U, V, Hk)
+            m = hard_threshold_mask(S, tau)
+            near = np.nonzero(np.abs(np.abs(S.reshape(b - a, -1)) - tau) <= 1e-9 * max(tau, 1.0))
+            amb.extend(zip((near[0] + a).tolist(), near[1].tolist()))
+            if p.agg_mode == "sparsity":
+                w_out[a:b] = 1.0 / np.maximum(1, m.reshape(b - a, -1).sum(axis=1))
+            Ghat = inverse_transform(S * m, U, V, Hk)
+            nu, de = aggregate_frame((H, Wd, C), t, idx[a:b], Ghat, w_out[a:b], p.ps)
+            num += nu
+            den += de
+            if keep_masks:
+                masks[a:b] = m
+        out[t] = num / den[:, :, None]
+        results.append(Result(out=out[t], idx=idx, tau=tau, U=U, V=V, weights=w_out, masks=masks, den=den,
+                              ambiguous=np.array(amb, dtype=np.int64).reshape(-1, 2), extra={"sigma": sg}))
+    return out, results

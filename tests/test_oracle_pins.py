@@ -436,3 +436,100 @@ def test_a_haar_tsvd_estimates_each_subimage_on_its_own():
     # (clipping to [0, 255] and the small sample bias the high-noise estimate low)
     assert 4.0 < sig[0] < 8.5 and 20.0 < sig[1] < 36.0 and sig[1] > 3.0 * sig[0]
     np.testing.assert_array_equal(out[:, 96:], O.denoise(np.ascontiguousarray(x[:, 96:]), sig[1], p).out)
+
+
+# ---------------------------------------------------------------- video (reading R16)
+
+def _clip(F, H, W, C, seed, sigma=15.0):
+    return np.stack([synth.add_gaussian(synth.clean_image(H, W, C, seed=seed), sigma, seed=seed + 100 + t)
+                     for t in range(F)])
+
+
+@pytest.mark.parametrize("C", [3, 1])
+def test_video_without_temporal_search_is_the_image_denoiser_per_frame(C):
+    clip = _clip(3, 24, 20, C, seed=5)
+    prm = dict(ps=8, stride=3, window=9, K=8)
+    out, res = O.denoise_video(clip, 20.0, prm, T=0)
+    for t in range(3):
+        r = O.denoise(clip[t], 20.0, prm)
+        assert np.array_equal(out[t], r.out)
+        assert np.array_equal(res[t].idx - t * 24 * 20, r.idx)
+
+
+@pytest.mark.parametrize("C,mode", [(3, "gcp"), (3, "full"), (1, "auto")])
+def test_video_grouping_against_brute_force(C, mode):
+    """Every candidate of every frame in reach enumerated with plain loops: SSD on the plane the
+    reference patch selects, keys (SSD, global index), the reference itself excluded."""
+    F, H, W, ps = 3, 15, 13, 8
+    clip = _clip(F, H, W, C, seed=9, sigma=30.0)
+    prm = O.Params.of(dict(ps=ps, stride=3, window=5, K=6, match_mode=mode))
+    T = 1
+    for t in range(F):
+        idx, green = O.block_match_video(clip, t, prm, T)
+        ys = O.reference_positions(H, ps, 3)
+        xs = O.reference_positions(W, ps, 3)
+        n = 0
+        for ry in ys:
+            for rx in xs:
+                y0, ny = O.window_range(int(ry), H, ps, 5)
+                x0, nx = O.window_range(int(rx), W, ps, 5)
+                x = clip.astype(np.int64)
+                ref = x[t, ry:ry + ps, rx:rx + ps, :]
+                if C == 1:
+                    planes = [0]
+                    use_sum = False
+                elif mode == "full":
+                    planes, use_sum = [0, 1, 2], False
+                else:
+                    g2 = int((ref[:, :, 1] ** 2).sum())
+                    r2, b2 = int((ref[:, :, 0] ** 2).sum()), int((ref[:, :, 2] ** 2).sum())
+                    gg = 1.2 * 1.2
+                    use_sum = not (gg * g2 >= r2 and gg * g2 >= b2)
+                    planes = [1]
+                keys = []
+                for f in range(max(0, t - T), min(F - 1, t + T) + 1):
+                    for y in range(y0, y0 + ny):
+                        for xx in range(x0, x0 + nx):
+                            if f == t and y == ry and xx == rx:
+                                continue
+                            cand = x[f, y:y + ps, xx:xx + ps, :]
+                            if use_sum:
+                                d = int(((cand.sum(axis=2) - ref.sum(axis=2)) ** 2).sum())
+                            else:
+                                d = sum(int(((cand[:, :, c] - ref[:, :, c]) ** 2).sum()) for c in planes)
+                            keys.append((d, f * H * W + y * W + xx))
+                keys.sort()
+                want = [t * H * W + ry * W + rx] + [k[1] for k in keys[:5]]
+                assert list(idx[n]) == want, (t, ry, rx)
+                n += 1
+
+
+def test_video_output_depends_only_on_frames_in_reach():
+    clip = _clip(5, 20, 18, 3, seed=21)
+    prm = dict(ps=8, stride=3, window=7, K=8)
+    a, _ = O.denoise_video(clip, 18.0, prm, T=1)
+    other = clip.copy()
+    other[4] = synth.add_gaussian(synth.clean_image(20, 18, 3, seed=99), 18.0, seed=7)
+    b, _ = O.denoise_video(other, 18.0, prm, T=1)
+    for t in range(3):                                  # frames 0..2 cannot reach frame 4
+        assert np.array_equal(a[t], b[t])
+    assert not np.array_equal(a[3], b[3])
+
+
+def test_video_zero_threshold_reproduces_the_clip():
+    clip = _clip(3, 20, 18, 3, seed=31)
+    out, _ = O.denoise_video(clip, 0.0, dict(ps=8, stride=3, window=7, K=8), T=1)
+    np.testing.assert_allclose(out, clip.astype(np.float64), rtol=0, atol=1e-9)
+
+
+def test_video_static_clip_groups_the_reference_copies_first():
+    """With identical frames the reference's own copies in frames t-1 and t+1 have distance 0,
+    the smallest possible, and come first in global-index order (a textured noisy frame has no
+    other zero-distance candidate)."""
+    frame = synth.add_gaussian(synth.clean_image(24, 22, 3, seed=41), 25.0, seed=42)
+    clip = np.stack([frame] * 3)
+    H, W = 24, 22
+    idx, _ = O.block_match_video(clip, 1, dict(ps=8, stride=3, window=9, K=8), T=1)
+    ref = idx[:, 0] - H * W
+    np.testing.assert_array_equal(idx[:, 1], ref)                # frame 0 copy
+    np.testing.assert_array_equal(idx[:, 2], ref + 2 * H * W)    # frame 2 copy
