@@ -109,6 +109,23 @@ htsvd_status htsvd_denoise_f32(const float* d_x, int32_t H, int32_t W, int32_t C
                                const htsvd_params* p, const float* d_w, float* d_out, int32_t* d_idx_out,
                                cudaStream_t stream);
 
+/* Color video (Sec. IV, real-world color video denoising: the patch search covers space and
+ * time, the noise estimate runs frame by frame). d_video: F frames of H x W x C uint8, frame-major
+ * (DEVICE); d_out: the same shape in float32 (DEVICE). Output frame t is Alg. 1 on frame t with
+ * frame t's own global bases and sigma (estimated from frame t when sigma < 0, else sigma for
+ * every frame), except that grouping searches the spatial window in frames t - T .. t + T
+ * (clipped to the clip) and only the patches lying in frame t are aggregated into it. Group
+ * indices are global, f * H * W + y * W + x; ties break towards the lowest. T = 0 gives
+ * htsvd_denoise on every frame. d_idx_out (DEVICE, may be NULL): the groups of every frame,
+ * F x N_groups x K int32 (frame-major, each frame as htsvd_denoise's d_idx_out). h_sigmas (HOST,
+ * may be NULL) receives the F sigmas used.
+ * Synchronises `stream` once per frame when sigma is estimated. Errors: INVALID_ARG for a null
+ * pointer, F < 1, T < 0 or a frame that fails the checks of htsvd_denoise; UNSUPPORTED when
+ * F * H * W reaches 2^31; optional outputs of p are ignored. */
+htsvd_status htsvd_denoise_video(const uint8_t* d_video, int32_t F, int32_t H, int32_t W, int32_t C, int32_t T,
+                                 double sigma, const htsvd_params* p, float* d_out, int32_t* d_idx_out,
+                                 double* h_sigmas, cudaStream_t stream);
+
 /* Noise level from the eigenvalues of the covariance of the reference patches:
  * ascending eigenvalues l_1..l_d, r* = max{r : mean(l_1..r) <= 1.02 median(l_1..r)},
  * sigma = sqrt(mean(l_1..r*)). With p->adapt the eigen-rank vote of Sec. III-D,

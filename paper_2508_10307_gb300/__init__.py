@@ -12,7 +12,7 @@ from dataclasses import dataclass, fields
 from . import _lib
 
 __all__ = ["HtsvdParams", "denoise", "denoise_f32", "estimate_sigma", "denoise_batch", "denoise_adaptive",
-           "denoise_vjp", "num_groups", "HtsvdFn", "load_library"]
+           "denoise_video", "denoise_vjp", "num_groups", "HtsvdFn", "load_library"]
 
 _MATCH = {"auto": 0, "gcp": 1, "full": 2, "green": 3}
 _AGG = {"uniform": 0, "sparsity": 1}
@@ -216,6 +216,30 @@ def denoise_adaptive(noisy, sub=(256, 256), params=None, *, return_sigmas=False,
     _lib.check(lib.htsvd_denoise_adaptive(_ptr(x), H, W, C, int(sub[0]), int(sub[1]), ctypes.byref(cp), _ptr(out),
                                           sig, _stream_ptr(stream)), "htsvd_denoise_adaptive")
     return (out, [float(v) for v in sig]) if return_sigmas else out
+
+
+def denoise_video(frames, sigma=None, params=None, *, T=1, return_info=False, stream=None):
+    """A clip of uint8 frames (F, H, W[, C]) on the GPU, frame by frame with spatio-temporal grouping
+    over frames t-T..t+T; sigma=None estimates it per frame. Returns float32 (F, H, W, C), or
+    (estimate, info) with return_info: info["idx"] (F, N, K) global group indices, info["sigmas"]."""
+    lib = _lib.load()
+    torch = _torch()
+    v = frames if frames.dim() == 4 else frames.unsqueeze(-1)
+    if v.dtype != torch.uint8:
+        raise TypeError("denoise_video expects uint8")
+    v = v.contiguous()
+    F, H, W, C = v.shape
+    p = HtsvdParams.of(params)
+    out = torch.empty((F, H, W, C), dtype=torch.float32, device=v.device)
+    idx = torch.empty((F, num_groups(H, W, p), p.K), dtype=torch.int32, device=v.device) if return_info else None
+    cp = p.c()
+    sig = (ctypes.c_double * F)()
+    _lib.check(lib.htsvd_denoise_video(_ptr(v), F, H, W, C, int(T), -1.0 if sigma is None else float(sigma),
+                                       ctypes.byref(cp), _ptr(out), _ptr(idx), sig, _stream_ptr(stream)),
+               "htsvd_denoise_video")
+    if return_info:
+        return out, {"idx": idx, "sigmas": [float(s) for s in sig]}
+    return out
 
 
 def denoise_vjp(x, sigma, idx, w, out, grad_out, params=None, want_grad_w=True, stream=None):

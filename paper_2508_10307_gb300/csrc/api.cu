@@ -220,7 +220,7 @@ struct FilterTiling {
     int TR, ntx, nty, FHmax, FWmax;
 };
 
-FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forced) {
+FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forced, int nfr = 1) {
     // Among the tiles whose shared memory lets two CTAs share an SM (228 KB, 1 KB reserved per
     // CTA): the largest that still gives 8 waves of two CTAs per SM (the last, partial wave then
     // costs little), else the largest with one such wave, else the largest that fits at all. A
@@ -241,6 +241,7 @@ FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forc
         fa.FWmax = t.FWmax;
         fa.img_is_float = in_bytes == 4;
         fa.mode = mode;
+        fa.nfr = nfr;
         if (filter_smem_bytes(fa) > 227 * 1024) t.TR = 0;
         return t;
     }
@@ -257,6 +258,7 @@ FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forc
         fa.FWmax = t.FWmax;
         fa.img_is_float = in_bytes == 4;
         fa.mode = mode;
+        fa.nfr = nfr;
         const size_t smem = filter_smem_bytes(fa);
         if (smem <= 112 * 1024) {
             const int64_t tiles = (int64_t)t.ntx * t.nty;
@@ -279,10 +281,25 @@ void choose_bm_tiles(const Geo& g, int rstep, int& TRy, int& TRx) {
 
 // ----------------------------------------------------------------------------- pieces
 
+// Spatio-temporal context of one output frame of a clip: candidate frames f0 .. f0 + nfr - 1 of
+// vid (fstride bytes apart), reference frame fref.
+struct VideoCtx {
+    const uint8_t* vid;
+    long long fstride;
+    int f0, nfr, fref;
+};
+
 htsvd_status run_block_match(const uint8_t* q, const Geo& g, const Resolved& r, int rstep, int32_t* idx,
-                             cudaStream_t s) {
+                             cudaStream_t s, const VideoCtx* vc = nullptr) {
     BMArgs a{};
     a.img = q;
+    if (vc) {
+        a.vid = vc->vid;
+        a.fstride = vc->fstride;
+        a.f0 = vc->f0;
+        a.nfr = vc->nfr;
+        a.fref = vc->fref;
+    }
     a.g = g;
     a.mode = resolve_mode(r, g.C);
     a.gamma2 = r.gamma * r.gamma;
@@ -409,8 +426,10 @@ struct FilterOut {
 // Filter + reduce for the forward pass.
 htsvd_status run_forward_filter(Workspace* w, const void* img, int is_float, const Geo& g, const Resolved& r,
                                 const int32_t* idx, const double* b64, const float* b32, double tau,
-                                const float* w_in, const htsvd_params* p, float* d_out, cudaStream_t s) {
-    FilterTiling t = choose_filter_tiling(g, is_float ? 4 : 1, FM_FORWARD, r.tile);
+                                const float* w_in, const htsvd_params* p, float* d_out, cudaStream_t s,
+                                const VideoCtx* vc = nullptr) {
+    const int mode = vc ? FM_VIDEO : FM_FORWARD;
+    FilterTiling t = choose_filter_tiling(g, is_float ? 4 : 1, mode, r.tile, vc ? vc->nfr : 1);
     if (t.TR == 0) return HTSVD_ERR_UNSUPPORTED;
     FilterArgs a{};
     a.img = img;
@@ -430,7 +449,14 @@ htsvd_status run_forward_filter(Workspace* w, const void* img, int is_float, con
     a.band_abs = (float)(tau * kBandTau) + 1e-6f;
     a.w_in = w_in;
     a.agg_mode = r.agg_mode;
-    a.mode = FM_FORWARD;
+    a.mode = mode;
+    if (vc) {
+        a.vid = vc->vid;
+        a.fstride = vc->fstride;                  // uint8 elements = bytes
+        a.f0 = vc->f0;
+        a.nfr = vc->nfr;
+        a.fref = vc->fref;
+    }
     a.mask_out = p ? p->d_mask_out : nullptr;
     a.weights_out = p ? p->d_weights_out : nullptr;
     a.coef_out = p ? p->d_coef_out : nullptr;
@@ -501,6 +527,62 @@ htsvd_status denoise_impl(const void* d_in, int is_float, int H, int W, int C, d
                               s);
 }
 
+// A clip, frame by frame (real-world color video denoising, Sec. IV): output frame t is Alg. 1 on
+// frame t (its own sigma, estimated or given, and its own global bases), except that grouping
+// searches the spatial window in frames t - T .. t + T and only the patches lying in frame t are
+// aggregated into it.
+htsvd_status video_impl(const uint8_t* d_vid, int F, int H, int W, int C, int T, double sigma,
+                        const htsvd_params* p, float* d_out, int32_t* d_idx_out, double* h_sigmas, cudaStream_t s) {
+    if (!d_vid || !d_out || F < 1 || T < 0) return HTSVD_ERR_INVALID_ARG;
+    Resolved r;
+    ST(resolve(p, C, r));
+    ST(check_image(H, W, C, r));
+    if (std::isnan(sigma)) return HTSVD_ERR_INVALID_ARG;
+    if ((int64_t)F * H * W >= ((int64_t)1 << 31)) return HTSVD_ERR_UNSUPPORTED;   // int32 global indices
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    const Geo g = make_geo(H, W, C, r.s, r.win, r.K);
+    const int64_t N = g.ngroups();
+    const long long fr = (long long)H * W * C;
+    void* ib = nullptr;
+    if (!d_idx_out) ST(ws_get(w, S_IDX, sizeof(int32_t) * N * r.K, &ib));
+    ST(ws_side(w));
+    for (int t = 0; t < F; ++t) {
+        int32_t* idx = d_idx_out ? d_idx_out + (size_t)t * N * r.K : (int32_t*)ib;
+        const uint8_t* q = d_vid + t * fr;
+        double sg = sigma;
+        void* hbuf = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (sg < 0) {
+            ST(launch_sigma_inputs(w, q, g, r, s, &hbuf));
+            CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            CK(cudaEventRecord(ev, s));
+        }
+        CK(cudaEventRecord(w->ev_fork, s));
+        CK(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
+        double* b64;
+        float* b32;
+        void* fullM = nullptr;
+        if (sg < 0) ST(ws_get(w, S_FULLM, sizeof(unsigned long long) * PS2 * C * PS2 * C, &fullM));
+        ST(run_basis(w, q, g, &b64, &b32, w->side, (const unsigned long long*)fullM));
+        CK(cudaEventRecord(w->ev_join, w->side));
+        const int f0 = std::max(0, t - T), f1 = std::min(F - 1, t + T);
+        const VideoCtx vc{d_vid, fr, f0, f1 - f0 + 1, t};
+        ST(run_block_match(q, g, r, 1, idx, s, &vc));
+        CK(cudaStreamWaitEvent(s, w->ev_join, 0));
+        if (sg < 0) {
+            cudaError_t e = cudaEventSynchronize(ev);
+            cudaEventDestroy(ev);
+            if (e != cudaSuccess) return HTSVD_ERR_CUDA;
+            ST(finish_sigma(hbuf, g, r, &sg));
+        }
+        if (h_sigmas) h_sigmas[t] = sg;
+        ST(run_forward_filter(w, q, 0, g, r, idx, b64, b32, r.tau_mult * sg, nullptr, nullptr, d_out + t * fr, s,
+                              &vc));
+    }
+    return HTSVD_OK;
+}
+
 }  // namespace
 
 // ============================================================================= C ABI
@@ -535,6 +617,12 @@ double htsvd_internal_sigma_from_moments(const unsigned long long* M, const unsi
 htsvd_status htsvd_denoise(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, double sigma,
                            const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t stream) {
     return denoise_impl(d_noisy, 0, H, W, C, sigma, p, nullptr, d_out, d_idx_out, stream);
+}
+
+htsvd_status htsvd_denoise_video(const uint8_t* d_video, int32_t F, int32_t H, int32_t W, int32_t C, int32_t T,
+                                 double sigma, const htsvd_params* p, float* d_out, int32_t* d_idx_out,
+                                 double* h_sigmas, cudaStream_t stream) {
+    return video_impl(d_video, F, H, W, C, T, sigma, p, d_out, d_idx_out, h_sigmas, stream);
 }
 
 htsvd_status htsvd_denoise_f32(const float* d_x, int32_t H, int32_t W, int32_t C, double sigma,

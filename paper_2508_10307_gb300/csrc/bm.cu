@@ -53,20 +53,25 @@ __host__ __device__ inline int byte_planes(int mode, int C) {
 __host__ __device__ inline bool uses_sum_plane(int mode, int C) { return C == 3 && mode == MM_GCP; }
 __host__ __device__ inline int bytes_pitch(int w) { return ((w + BM_PAD) + 3) & ~3; }
 
-// Shared-memory layout of a region of h x w pixels (h, w >= ps).
+// Shared-memory layout of a region of h x w pixels (h, w >= ps) staged from nfr frames: each
+// section holds one block per frame, the blocks sz_* bytes apart.
 struct BmLayout {
     size_t bytes, fplane, svv, warp, total;
+    size_t sz_bytes, sz_fplane, sz_svv;
 };
 __host__ __device__ inline size_t a16(size_t o) { return (o + 15) & ~(size_t)15; }
-__host__ __device__ inline BmLayout bm_layout(int h, int w, int nb, bool sum_plane) {
+__host__ __device__ inline BmLayout bm_layout(int h, int w, int nb, bool sum_plane, int nfr = 1) {
     BmLayout L;
+    L.sz_bytes = a16((size_t)nb * h * bytes_pitch(w));                                  // nb byte planes [h][pitch]
+    L.sz_fplane = sum_plane ? a16(sizeof(float) * h * w) : 0;                          // R+G+B plane [h][w]
+    L.sz_svv = a16(sizeof(int) * (sum_plane ? 2 : 1) * (size_t)(h - PS + 1) * (w - PS + 1));   // S_vv [h-7][w-7]
     size_t o = 0;
     L.bytes = o;
-    o = a16(o + (size_t)nb * h * bytes_pitch(w));            // nb byte planes [h][pitch]
+    o += nfr * L.sz_bytes;
     L.fplane = o;
-    if (sum_plane) o = a16(o + sizeof(float) * h * w);       // R+G+B plane [h][w]
+    o += nfr * L.sz_fplane;
     L.svv = o;
-    o = a16(o + sizeof(int) * (sum_plane ? 2 : 1) * (size_t)(h - PS + 1) * (w - PS + 1));   // S_vv [h-7][w-7]
+    o += nfr * L.sz_svv;
     L.warp = o;
     o += (size_t)BM_WARPS * (BM_BUF * sizeof(unsigned long long) + PS2 * sizeof(float));
     L.total = o;
@@ -163,14 +168,18 @@ struct RefCtx {
     int wv;                // S_vv pitch (candidate positions per region row)
 };
 
-__device__ __forceinline__ unsigned long long make_key(int ssd, int py, int px, int W) {
-    return ((unsigned long long)(unsigned)ssd << 32) | (unsigned)(py * W + px);
+__device__ __forceinline__ unsigned long long make_key(int ssd, int py, int px, int W, unsigned koff) {
+    return ((unsigned long long)(unsigned)ssd << 32) | (koff + (unsigned)(py * W + px));
 }
 
 // Byte planes: cross terms of the candidates of the lane's strips, keys offered per strip.
+// bp, svv: the candidate frame's byte planes and box sums; rbp, srr: the reference frame's planes
+// and the reference's own box sum; koff: index offset of the candidate frame; self: the candidate
+// frame is the reference frame (its reference position is not a candidate).
 template <int R, int NB>
-__device__ __forceinline__ void match_bytes(const BMArgs& a, const Region& Rg, const uint8_t* bp, int P8,
-                                            const int* svv, const RefCtx& c, Select& S, int lane) {
+__device__ __forceinline__ void match_bytes(const BMArgs& a, const Region& Rg, const uint8_t* bp,
+                                            const uint8_t* rbp, int P8, const int* svv, int srr,
+                                            const RefCtx& c, Select& S, int lane, unsigned koff, bool self) {
     const Geo& g = a.g;
     const int qpr = (g.wnx + 3) / 4, G = 32 / qpr;
     const int sg = lane / qpr, q = lane - sg * qpr;
@@ -180,7 +189,7 @@ __device__ __forceinline__ void match_bytes(const BMArgs& a, const Region& Rg, c
     uint32_t rw[NB][PS][2];
 #pragma unroll
     for (int p = 0; p < NB; ++p) {
-        const uint8_t* pl = bp + (size_t)p * Rg.h * P8;
+        const uint8_t* pl = rbp + (size_t)p * Rg.h * P8;
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
             const int bo = (c.ry - Rg.y0 + i) * P8 + (c.rx - Rg.x0);
@@ -191,7 +200,6 @@ __device__ __forceinline__ void match_bytes(const BMArgs& a, const Region& Rg, c
             rw[p][i][1] = __funnelshift_r(w1, w2, u);
         }
     }
-    const int srr = svv[(c.ry - Rg.y0) * c.wv + (c.rx - Rg.x0)];
     const int sh = 8 * (c.ox & 3);                            // byte offset of every candidate word in a row
     const int last_row = g.wny + PS - 2;                      // last window row any valid candidate reads
     // warp-uniform chunk count (every lane offers the same number of keys); idle lanes and strips
@@ -245,8 +253,9 @@ __device__ __forceinline__ void match_bytes(const BMArgs& a, const Region& Rg, c
                 unsigned long long key = ~0ull;
                 if (run && cy < g.wny && cx < g.wnx) {
                     const int py = c.wy0 + cy, px = c.wx0 + cx;
-                    if (py != c.ry || px != c.rx)
-                        key = make_key(svv[(c.oy + cy) * c.wv + c.ox + cx] + srr - 2 * (int)acc[k][s], py, px, g.W);
+                    if (!self || py != c.ry || px != c.rx)
+                        key = make_key(svv[(c.oy + cy) * c.wv + c.ox + cx] + srr - 2 * (int)acc[k][s], py, px, g.W,
+                                       koff);
                 }
                 sel_offer(S, key, g.K, lane);
             }
@@ -254,9 +263,11 @@ __device__ __forceinline__ void match_bytes(const BMArgs& a, const Region& Rg, c
 }
 
 // R+G+B plane: exact cross terms from FP32 partial sums over two reference rows.
+// sp, svv2: the candidate frame's R+G+B plane and box sums; rsp, srr: the reference frame's plane
+// and the reference's box sum; koff, self as for the byte planes.
 __device__ __forceinline__ void match_sum_plane(const BMArgs& a, const Region& Rg, const float* sp,
-                                                const int* svv2, float* rvw, const RefCtx& c, Select& S,
-                                                int lane) {
+                                                const float* rsp, const int* svv2, int srr, float* rvw,
+                                                const RefCtx& c, Select& S, int lane, unsigned koff, bool self) {
     const Geo& g = a.g;
     constexpr int R = BM_FR;
     const int qpr = (g.wnx + 3) / 4, G = 32 / qpr;
@@ -264,9 +275,9 @@ __device__ __forceinline__ void match_sum_plane(const BMArgs& a, const Region& R
     const bool active = sg < G;
     const int cx0 = 4 * q;
     // the reference patch, for broadcast reads
-    for (int e = lane; e < PS2; e += 32) rvw[e] = sp[(c.ry - Rg.y0 + e / PS) * Rg.w + (c.rx - Rg.x0) + e % PS];
+    __syncwarp();                              // rvw of the previous frame or reference is read
+    for (int e = lane; e < PS2; e += 32) rvw[e] = rsp[(c.ry - Rg.y0 + e / PS) * Rg.w + (c.rx - Rg.x0) + e % PS];
     __syncwarp();
-    const int srr = svv2[(c.ry - Rg.y0) * c.wv + (c.rx - Rg.x0)];
     const int last_row = g.wny + PS - 2;
     const int maxc = Rg.w - 1 - c.ox;          // clamp of the columns of idle candidates beyond the window
     const int nch = (g.wny + G * R - 1) / (G * R);           // warp-uniform, as on the byte planes
@@ -317,8 +328,9 @@ __device__ __forceinline__ void match_sum_plane(const BMArgs& a, const Region& R
                 unsigned long long key = ~0ull;
                 if (run && cy < g.wny && cx < g.wnx) {
                     const int py = c.wy0 + cy, px = c.wx0 + cx;
-                    if (py != c.ry || px != c.rx)
-                        key = make_key(svv2[(c.oy + cy) * c.wv + c.ox + cx] + srr - 2 * acc[k][s], py, px, g.W);
+                    if (!self || py != c.ry || px != c.rx)
+                        key = make_key(svv2[(c.oy + cy) * c.wv + c.ox + cx] + srr - 2 * acc[k][s], py, px, g.W,
+                                       koff);
                 }
                 sel_offer(S, key, g.K, lane);
             }
@@ -327,6 +339,9 @@ __device__ __forceinline__ void match_sum_plane(const BMArgs& a, const Region& R
 }
 
 // Grouping of one tile (by, bx) of references; bsm: bm_smem_bytes(a) of shared memory.
+// MF: spatio-temporal search over a.nfr frames (a separate instantiation, so that the image
+// kernels carry no frame loop).
+template <bool MF>
 __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigned char* bsm) {
     const Geo& g = a.g;
     const int iy0 = by * a.TRy, ix0 = bx * a.TRx;
@@ -335,29 +350,37 @@ __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigne
     const int nb = byte_planes(a.mode, g.C);
     const bool gcp = uses_sum_plane(a.mode, g.C);
     const int P8 = bytes_pitch(Rg.w);
-    const BmLayout L = bm_layout(Rg.h, Rg.w, nb, gcp);
-    uint8_t* bp = bsm + L.bytes;                                     // nb byte planes [h][P8]
-    float* sp = reinterpret_cast<float*>(bsm + L.fplane);            // R+G+B plane [h][w]
-    int* svv = reinterpret_cast<int*>(bsm + L.svv);                  // S_vv [nsv][h-7][w-7]
+    const int nfr = MF ? a.nfr : 1;                                  // frames searched
+    const BmLayout L = bm_layout(Rg.h, Rg.w, nb, gcp, nfr);
     const int hv = Rg.h - PS + 1, wv = Rg.w - PS + 1;
+    // frame slot fs: nb byte planes [h][P8], R+G+B plane [h][w], S_vv [nsv][h-7][w-7]
+    auto planes_of = [&](int fs) { return bsm + L.bytes + fs * L.sz_bytes; };
+    auto sum_of = [&](int fs) { return reinterpret_cast<float*>(bsm + L.fplane + fs * L.sz_fplane); };
+    auto svv_of = [&](int fs) { return reinterpret_cast<int*>(bsm + L.svv + fs * L.sz_svv); };
+    const int fsref = MF ? a.fref - a.f0 : 0;                         // slot of the reference frame
 
-    // Stage the planes of the region (byte rows zero-padded).
-    for (int t = threadIdx.x; t < Rg.h * P8; t += BM_THREADS) {
-        const int r = t / P8, cc = t - r * P8;
+    // Stage the planes of the region of every frame (byte rows zero-padded).
+    for (int t = threadIdx.x; t < nfr * Rg.h * P8; t += BM_THREADS) {
+        const int fs = t / (Rg.h * P8), tt = t - fs * (Rg.h * P8);
+        const int r = tt / P8, cc = tt - r * P8;
+        uint8_t* bp = planes_of(fs);
+        float* sp = sum_of(fs);
+        const uint8_t* frame = MF ? a.vid + (size_t)(a.f0 + fs) * a.fstride : a.img;
+        const int t_ = tt;
         if (cc < Rg.w) {
-            const uint8_t* px = a.img + ((size_t)(Rg.y0 + r) * g.W + (Rg.x0 + cc)) * g.C;
+            const uint8_t* px = frame + ((size_t)(Rg.y0 + r) * g.W + (Rg.x0 + cc)) * g.C;
             if (g.C == 1) {
-                bp[t] = px[0];
+                bp[t_] = px[0];
             } else if (a.mode == MM_FULL) {
-                bp[t] = px[0];
-                bp[(size_t)Rg.h * P8 + t] = px[1];
-                bp[(size_t)2 * Rg.h * P8 + t] = px[2];
+                bp[t_] = px[0];
+                bp[(size_t)Rg.h * P8 + t_] = px[1];
+                bp[(size_t)2 * Rg.h * P8 + t_] = px[2];
             } else {
-                bp[t] = px[1];
+                bp[t_] = px[1];
                 if (gcp) sp[r * Rg.w + cc] = (float)((int)px[0] + (int)px[1] + (int)px[2]);
             }
         } else {
-            for (int p = 0; p < nb; ++p) bp[(size_t)p * Rg.h * P8 + t] = 0;
+            for (int p = 0; p < nb; ++p) bp[(size_t)p * Rg.h * P8 + t_] = 0;
         }
     }
     __syncthreads();
@@ -366,7 +389,11 @@ __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigne
     {
         const int nyc = (hv + PS - 1) / PS;
         const int nsv = gcp ? 2 : 1;
-        for (int it = threadIdx.x; it < nsv * nyc * wv; it += BM_THREADS) {
+        for (int it0 = threadIdx.x; it0 < nfr * nsv * nyc * wv; it0 += BM_THREADS) {
+            const int fs = it0 / (nsv * nyc * wv), it = it0 - fs * (nsv * nyc * wv);
+            const uint8_t* bp = planes_of(fs);
+            const float* sp = sum_of(fs);
+            int* svv = svv_of(fs);
             const int pl = it / (nyc * wv);
             const int rem = it - pl * nyc * wv;
             const int yc = rem / wv, x = rem - yc * wv;
@@ -450,18 +477,29 @@ __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigne
         S.thr = ~0ull;
         S.buf = buf;
         S.cnt = 0;
-        if (!green) {
-            match_sum_plane(a, Rg, sp, svv + (size_t)hv * wv, rvw, c, S, lane);
-        } else if (nb == 3) {
-            match_bytes<4, 3>(a, Rg, bp, P8, svv, c, S, lane);
-        } else if (R == 8) {
-            match_bytes<8, 1>(a, Rg, bp, P8, svv, c, S, lane);
-        } else {
-            match_bytes<4, 1>(a, Rg, bp, P8, svv, c, S, lane);
+        // the reference patch and its box sums come from the reference frame's slot
+        const uint8_t* rbp = planes_of(fsref);
+        const float* rsp = sum_of(fsref);
+        const int* rsvv = svv_of(fsref);
+        const int rsrr = rsvv[(size_t)(green ? 0 : hv * wv) + (c.ry - Rg.y0) * wv + (c.rx - Rg.x0)];
+        for (int fs = 0; fs < nfr; ++fs) {
+            const unsigned koff = MF ? (unsigned)(a.f0 + fs) * (unsigned)(g.H * g.W) : 0u;
+            const bool self = fs == fsref;
+            const uint8_t* bp = planes_of(fs);
+            const int* svv = svv_of(fs);
+            if (!green) {
+                match_sum_plane(a, Rg, sum_of(fs), rsp, svv + (size_t)hv * wv, rsrr, rvw, c, S, lane, koff, self);
+            } else if (nb == 3) {
+                match_bytes<4, 3>(a, Rg, bp, rbp, P8, svv, rsrr, c, S, lane, koff, self);
+            } else if (R == 8) {
+                match_bytes<8, 1>(a, Rg, bp, rbp, P8, svv, rsrr, c, S, lane, koff, self);
+            } else {
+                match_bytes<4, 1>(a, Rg, bp, rbp, P8, svv, rsrr, c, S, lane, koff, self);
+            }
         }
         if (S.cnt > 0) sel_merge(S, K, lane);
         int32_t* out = a.idx + (size_t)(iy * a.nrx_s + ix) * K;
-        if (lane == 0) out[0] = c.ry * g.W + c.rx;
+        if (lane == 0) out[0] = (MF ? a.fref * g.H * g.W : 0) + c.ry * g.W + c.rx;
         if (lane < K - 1) out[1 + lane] = (int32_t)(unsigned)(S.list & 0xffffffffull);
         __syncwarp();
     }
@@ -469,7 +507,12 @@ __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigne
 
 __global__ void __launch_bounds__(BM_THREADS, 2) block_match_kernel(BMArgs a) {
     extern __shared__ __align__(16) unsigned char bsm[];
-    bm_tile(a, blockIdx.y, blockIdx.x, bsm);
+    bm_tile<false>(a, blockIdx.y, blockIdx.x, bsm);
+}
+
+__global__ void __launch_bounds__(BM_THREADS, 2) block_match_video_kernel(BMArgs a) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    bm_tile<true>(a, blockIdx.y, blockIdx.x, bsm);
 }
 
 // Persistent form over the tiles of many images: work item w -> image by prefix[], then tile.
@@ -494,7 +537,7 @@ __global__ void __launch_bounds__(BM_THREADS, 2) block_match_batch_kernel(const 
         const BMArgs& a = args[lo];
         const int t = w - prefix[lo];
         const int ntx = (a.nrx_s + a.TRx - 1) / a.TRx;
-        bm_tile(a, t / ntx, t % ntx, bsm);
+        bm_tile<false>(a, t / ntx, t % ntx, bsm);
     }
 }
 
@@ -510,7 +553,7 @@ size_t bm_smem_bytes(const BMArgs& a) {
     int hx = (a.TRx - 1) * a.rstep * g.s + g.wnx + PS - 1;
     if (hy > g.H) hy = g.H;
     if (hx > g.W) hx = g.W;
-    return bm_layout(hy, hx, byte_planes(a.mode, g.C), uses_sum_plane(a.mode, g.C)).total;
+    return bm_layout(hy, hx, byte_planes(a.mode, g.C), uses_sum_plane(a.mode, g.C), a.nfr > 0 ? a.nfr : 1).total;
 }
 
 void bm_fit_tiles(BMArgs& a) {
@@ -537,13 +580,13 @@ cudaError_t launch_block_match_batch(const BMArgs* d_args, const int* d_prefix, 
 cudaError_t launch_block_match(const BMArgs& a, cudaStream_t s) {
     size_t smem = bm_smem_bytes(a);
     if (smem > BM_SMEM_MAX) return cudaErrorInvalidValue;
+    auto fn = a.nfr > 0 ? block_match_video_kernel : block_match_kernel;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(block_match_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((a.nrx_s + a.TRx - 1) / a.TRx, (a.nry_s + a.TRy - 1) / a.TRy);
-    block_match_kernel<<<grid, BM_THREADS, smem, s>>>(a);
+    fn<<<grid, BM_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 

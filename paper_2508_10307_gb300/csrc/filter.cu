@@ -15,6 +15,8 @@ cudaError_t dispatch_mode(const FilterArgs& a, cudaStream_t s) {
             return launch_filter_t<K, C, float, FM_DENOM>(a, s);
         case FM_ADJOINT:
             return a.img_is_float ? launch_filter_t<K, C, float, FM_ADJOINT>(a, s) : cudaErrorInvalidValue;
+        case FM_VIDEO:
+            return a.img_is_float || a.nfr < 1 ? cudaErrorInvalidValue : launch_filter_t<K, C, uint8_t, FM_VIDEO>(a, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -140,9 +142,11 @@ __global__ void div_kernel(const float* __restrict__ gout, const float* __restri
 
 size_t filter_smem_bytes(const FilterArgs& a) {
     const int inb = a.img_is_float ? 4 : 1;
-    if (a.mode == FM_FORWARD)
-        return a.g.C == 3 ? f_layout_fwd<32, 3>(a.FHmax, a.FWmax, inb).total
-                          : f_layout_fwd<32, 1>(a.FHmax, a.FWmax, inb).total;
+    if (a.mode == FM_FORWARD || a.mode == FM_VIDEO) {
+        const int nfr = a.mode == FM_VIDEO && a.nfr > 0 ? a.nfr : 1;
+        return a.g.C == 3 ? f_layout_fwd<32, 3>(a.FHmax, a.FWmax, inb, nfr).total
+                          : f_layout_fwd<32, 1>(a.FHmax, a.FWmax, inb, nfr).total;
+    }
     if (a.g.C == 3) return f_layout<32, 3>(a.FHmax, a.FWmax, inb, a.mode).total;
     return f_layout<32, 1>(a.FHmax, a.FWmax, inb, a.mode).total;
 }

@@ -75,7 +75,7 @@ __host__ __device__ inline FLayout f_layout(int FH, int FW, int in_bytes, int mo
 // Shared-memory layout of the pipelined forward filter: two group buffers (group q+1 is projected
 // while group q is inverted and aggregated), three position and counter sets, no band bitmaps.
 template <int K, int C>
-__host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes) {
+__host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes, int nfr = 1) {
     using G = FCfg<C>;
     FLayout L;
     int o = 0;
@@ -86,7 +86,7 @@ __host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes) {
     L.off_rkeep = o;
     L.off_misc = o; o += 3 * 16 * 4;
     L.off_acc = o; o += FH * FW * G::ACC * 4;
-    L.off_img = o; o += (FH * FW * C * in_bytes + 15) / 16 * 16;
+    L.off_img = o; o += (nfr * FH * FW * C * in_bytes + 15) / 16 * 16;   // footprints of nfr frames, stacked
     L.off_r = o;
     L.total = o;
     return L;
@@ -842,7 +842,11 @@ __device__ __forceinline__ void stage_e2(const float* bas, float* gb, int k, int
 // C(q+1) Haar/threshold/synthesis]. Group buffers alternate; positions and counters rotate over
 // three slots (those of q+2 are written while q and q+1 are in flight). Guard-band entries are
 // re-decided in FP64 by the warp that owns the fibre (no CTA barrier).
-template <int K, int C, typename Tin>
+// MF: video groups (FM_VIDEO). The footprints of the clip's frames f0 .. f0 + nfr - 1 are staged
+// one above the other, the reference frame's first (slot 0, rows [0, FH)), the others after it in
+// frame order; a patch's staged row is slot * FH + its row in the footprint, so every stage reads
+// it as in one image, and the aggregation adds the slot-0 patches only.
+template <int K, int C, typename Tin, bool MF>
 __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int tile, unsigned char* smem) {
     using G = FCfg<C>;
     constexpr int NF = G::PATCH;
@@ -858,7 +862,8 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     tile_span(ty, a.TR, g.nry, g.s, g.H, g.npy, g.wny, g.win, FY0, FY1);
     tile_span(tx, a.TR, g.nrx, g.s, g.W, g.npx, g.wnx, g.win, FX0, FX1);
     const int FH = FY1 - FY0, FW = FX1 - FX0;
-    const FLayout L = f_layout_fwd<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin));
+    const int nfr = MF ? a.nfr : 1;
+    const FLayout L = f_layout_fwd<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), nfr);
     float* bas = reinterpret_cast<float*>(smem + L.off_bas);
     float* gbb = reinterpret_cast<float*>(smem + L.off_gb);
     int* posb = reinterpret_cast<int*>(smem + L.off_pos);
@@ -866,13 +871,21 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     float* pnb = reinterpret_cast<float*>(smem + L.off_band);
     float* acc = reinterpret_cast<float*>(smem + L.off_acc);
     Tin* img_s = reinterpret_cast<Tin*>(smem + L.off_img);
+    // frame of staging slot sl (slot 0: the reference frame, then the others in order)
+    auto slot_frame = [&](int sl) {
+        if (!MF) return 0;
+        const int f = a.f0 + sl - 1;
+        return sl == 0 ? a.fref : (f >= a.fref ? f + 1 : f);
+    };
 
     stage_basis<C>(a.basis32, bas, tid);
     {
-        const Tin* img = reinterpret_cast<const Tin*>(a.img);
         const int rowb = FW * C;
-        for (int t = tid; t < FH * rowb; t += FT_THREADS) {
-            const int r = t / rowb, cb = t - r * rowb;
+        for (int t = tid; t < nfr * FH * rowb; t += FT_THREADS) {
+            const int sl = t / (FH * rowb), tt = t - sl * (FH * rowb);
+            const int r = tt / rowb, cb = tt - r * rowb;
+            const Tin* img = MF ? reinterpret_cast<const Tin*>(a.vid) + (size_t)slot_frame(sl) * a.fstride
+                                : reinterpret_cast<const Tin*>(a.img);
             img_s[t] = img[((size_t)(FY0 + r) * g.W + FX0) * C + cb];
         }
     }
@@ -886,8 +899,15 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     // index outside it is clamped so that no access leaves the staged region.
     auto store_pos = [&](int v, int* pos) {
         if (tid < K) {
+            int sl = 0;
+            if (MF) {                                 // frame -> staging slot (clamped to the staged frames)
+                const int hw = g.H * g.W;
+                const int f = min(max(v / hw, a.f0), a.f0 + a.nfr - 1);
+                v = max(v - (v / hw) * hw, 0);
+                sl = f == a.fref ? 0 : (f < a.fref ? f - a.f0 + 1 : f - a.f0);
+            }
             const int y = v / g.W, x = v - y * g.W;
-            pos[2 * tid] = min(max(y - FY0, 0), FH - PS);
+            pos[2 * tid] = sl * FH + min(max(y - FY0, 0), FH - PS);
             pos[2 * tid + 1] = min(max(x - FX0, 0), FW - PS);
         }
     };
@@ -1091,6 +1111,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                     const int i = (warp - py) & 7;
                     my_aoff = ((py + i) * FW + px) * G::ACC;
                     my_goff = lane * G::GS + i * G::ROW;
+                    if (MF && py >= FH) my_aoff = -1;     // a patch of another frame: not aggregated here
                 }
                 constexpr int NV = PS * C;                // numerator lanes
                 const bool num = lane < NV, act = lane < NV + PS;
@@ -1099,7 +1120,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 for (int k = 0; k < K; ++k) {
                     const int aoff = __shfl_sync(0xffffffffu, my_aoff, k);
                     const int goff = __shfl_sync(0xffffffffu, my_goff, k);
-                    if (act) {
+                    if (act && (!MF || aoff >= 0)) {
                         const float x = num ? gbq[goff + lane] : 1.f;
                         acc[aoff + lofs] += wg * x;
                     }
@@ -1138,8 +1159,8 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
 // (f_layout_fwd for the forward mode).
 template <int K, int C, typename Tin, int MODE>
 __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile, unsigned char* smem) {
-    if constexpr (MODE == FM_FORWARD) {
-        filter_tile_fwd<K, C, Tin>(a, tile, smem);
+    if constexpr (MODE == FM_FORWARD || MODE == FM_VIDEO) {
+        filter_tile_fwd<K, C, Tin, MODE == FM_VIDEO>(a, tile, smem);
         return;
     }
     using G = FCfg<C>;
@@ -1408,6 +1429,7 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_batch_kernel(const Filte
 template <int K, int C, typename Tin, int MODE>
 cudaError_t launch_filter_t(const FilterArgs& a, cudaStream_t s) {
     const FLayout L = MODE == FM_FORWARD ? f_layout_fwd<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin))
+                      : MODE == FM_VIDEO ? f_layout_fwd<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), a.nfr)
                                          : f_layout<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), MODE);
     auto fn = filter_kernel<K, C, Tin, MODE>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);

@@ -18,6 +18,12 @@ struct BMArgs {
     int nry_s, nrx_s;    // references per axis after subsampling
     int TRy, TRx;        // references per tile
     int32_t* idx;        // out [nry_s * nrx_s][K]
+    // Spatio-temporal search (video): candidates also come from frames f0 .. f0 + nfr - 1 of the
+    // clip at vid (frame stride fstride bytes); img is frame fref. Indices are global,
+    // f * H * W + y * W + x. nfr = 0 (the default) searches img alone, with frame-local indices.
+    const uint8_t* vid;
+    long long fstride;
+    int f0, nfr, fref;
 };
 size_t bm_smem_bytes(const BMArgs& a);
 // Halves the tile (TRx, TRy) until its shared-memory footprint leaves room for two CTAs per SM.
@@ -45,7 +51,7 @@ cudaError_t launch_basis(const unsigned long long* d_mom, int C, double* d_basis
 cudaError_t launch_quantize(const float* x, int64_t n, uint8_t* q, cudaStream_t s);
 
 // ---- group filter and aggregation (filter.cu)
-enum FilterMode { FM_FORWARD = 0, FM_DENOM = 1, FM_ADJOINT = 2 };
+enum FilterMode { FM_FORWARD = 0, FM_DENOM = 1, FM_ADJOINT = 2, FM_VIDEO = 3 };
 
 // Guard band of the threshold decision: a coefficient whose FP32 value lies within
 // kBandRel * ||G||_F + kBandTau * tau of tau is decided again in FP64 (||G||_F: Frobenius
@@ -76,6 +82,12 @@ struct FilterArgs {
     const float* r_img;      // (gout / D) image that is filtered with the masks of img (FM_ADJOINT)
     const float* out_img;    // forward output (FM_ADJOINT, for the weight gradient)
     float* grad_w;           // FM_ADJOINT, per group
+    // FM_VIDEO (forward over a clip, uint8): groups of frame fref may hold patches of frames
+    // f0 .. f0 + nfr - 1 of vid (frame stride fstride elements, indices f * H * W + y * W + x);
+    // only the patches of frame fref are aggregated. img is frame fref.
+    const void* vid;
+    long long fstride;
+    int f0, nfr, fref;
 };
 size_t filter_smem_bytes(const FilterArgs& a);
 cudaError_t launch_filter(const FilterArgs& a, cudaStream_t s);

@@ -89,3 +89,16 @@ def test_adaptive_rejects_bad_subimage_sizes_on_the_host():
 def test_subimage_bounds_match_the_oracle_reading(n, sub):
     from oracle import htsvd_oracle as O
     assert H.subimage_bounds(n, sub) == O.subimage_bounds(n, sub)
+
+
+def test_video_rejects_bad_arguments_on_the_host():
+    lib = H.load_library()
+    cp = H.HtsvdParams().c()
+    dp = ctypes.c_void_p(1)
+    call = lambda vid, F, T: lib.htsvd_denoise_video(vid, F, 64, 64, 3, T, 10.0, ctypes.byref(cp), dp, None, None,
+                                                     None)
+    assert call(dp, 0, 1) == 1                 # no frames
+    assert call(dp, 3, -1) == 1                # negative temporal radius
+    assert call(None, 3, 1) == 1               # null clip
+    assert lib.htsvd_denoise_video(dp, 3, 64, 64, 2, 1, 10.0, ctypes.byref(cp), dp, None, None, None) == 1
+
