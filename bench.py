@@ -297,6 +297,25 @@ def make_workload(name):
         return Workload(name, cfg, 512 * 512 / 1e6, n, 3, 32, [noisy],
                         lambda d: [H.denoise_adaptive(d[0], sub, prm)], 512 * 512 * 3 * 4, plain,
                         "plain_single_sigma"), clean
+    if name == "video1080":
+        F, Hh, Ww, T = 4, 1080, 1920, 1
+        base = synth.clean_image(Hh, Ww + F, 3, 4001)
+        clip = np.stack([synth.add_poisson_gaussian(np.ascontiguousarray(base[:, t:t + Ww]), 0.01, 15.0 ** 2,
+                                                    4001 + 17 * t) for t in range(F)])
+        prm = dict(ps=8, stride=3, window=31, K=32)
+        cfg = {"workload": "video_rgb1920x1080x4_T1", "clip": "4 frames of 1920x1080x3 uint8, content drifting "
+               "one pixel per frame", "noise": "poisson-gaussian a=0.01 b=15^2, fresh per frame",
+               "sigma": "estimated per frame", "ps": 8, "stride": 3, "window": 31, "K": 32,
+               "temporal_radius": T, "form": "frame by frame, grouping over frames t-1..t+1"}
+        n = H.num_groups(Hh, Ww, prm)
+
+        def frame_by_frame(d):
+            return [H.denoise_video(d[0], None, prm, T=0)]
+
+        clean = np.stack([synth.quantize(base[:, t:t + Ww]) for t in range(F)])
+        return Workload(name, cfg, F * Hh * Ww / 1e6, F * n, 3, 32, [clip],
+                        lambda d: [H.denoise_video(d[0], None, prm, T=T)], F * Hh * Ww * 3 * 4, frame_by_frame,
+                        "frame_by_frame_no_temporal_search"), clean
     raise ValueError(name)
 
 
@@ -438,7 +457,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="rgb512", choices=["rgb512", "gray128", "rgb4k", "batch64", "vjp8", "adaptive512"])
+    ap.add_argument("--workload", default="rgb512", choices=["rgb512", "gray128", "rgb4k", "batch64", "vjp8", "adaptive512",
+                                                      "video1080"])
     ap.add_argument("--cpu-rows", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-worker", type=int, default=None)
