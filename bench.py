@@ -316,6 +316,24 @@ def make_workload(name):
         return Workload(name, cfg, F * Hh * Ww / 1e6, F * n, 3, 32, [clip],
                         lambda d: [H.denoise_video(d[0], None, prm, T=T)], F * Hh * Ww * 3 * 4, frame_by_frame,
                         "frame_by_frame_no_temporal_search"), clean
+    if name == "sweep512":
+        clean, noisy, _, prm = synth.workload_rgb512()
+        mults = [1.8, 2.1, 2.4, 2.7, 3.0, 3.3, 3.6, 3.9]
+        cfg = {"workload": "tau_sweep_rgb512_x8", "image": "512x512x3 uint8", "noise": "poisson-gaussian a=0.01 b=15^2",
+               "sigma": "estimated once", "tau_mults": mults, "ps": 8, "stride": 2, "window": 31, "K": 32,
+               "form": "grouping, bases, sigma and noisy coefficients once; threshold, synthesis and aggregation "
+                       "per tau (the step's MP count is 8 outputs)"}
+        n = H.num_groups(512, 512, prm)
+        sig = [None]
+
+        def plain(d):
+            if sig[0] is None:
+                sig[0] = H.estimate_sigma(d[0], prm)
+            return [H.denoise(d[0], sig[0], dict(prm, tau_mult=m)) for m in mults]
+
+        return Workload(name, cfg, len(mults) * 512 * 512 / 1e6, len(mults) * n, 3, 32, [noisy],
+                        lambda d: [H.denoise_tau_sweep(d[0], mults, None, prm)], len(mults) * 512 * 512 * 3 * 4,
+                        plain, "separate_calls_per_tau"), None
     raise ValueError(name)
 
 
@@ -458,7 +476,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rgb512", choices=["rgb512", "gray128", "rgb4k", "batch64", "vjp8", "adaptive512",
-                                                      "video1080"])
+                                                      "video1080", "sweep512"])
     ap.add_argument("--cpu-rows", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-worker", type=int, default=None)

@@ -126,6 +126,18 @@ htsvd_status htsvd_denoise_video(const uint8_t* d_video, int32_t F, int32_t H, i
                                  double sigma, const htsvd_params* p, float* d_out, int32_t* d_idx_out,
                                  double* h_sigmas, cudaStream_t stream);
 
+/* A sweep of thresholds (parameter tuning, Sec. III-E: the grouping and the noisy coefficients
+ * are computed once and cached). d_noisy: H x W x C uint8 (DEVICE); h_tau_mults: n_tau >= 1
+ * threshold multipliers (HOST, each finite and >= 0); d_outs: n_tau x H x W x C float32 (DEVICE).
+ * Output i equals htsvd_denoise at tau = h_tau_mults[i] * sigma (sigma < 0: estimated once,
+ * returned in h_sigma, HOST, may be NULL). The cache takes N_groups x K x 64 C floats of device
+ * memory in the stream's workspace. Errors: INVALID_ARG for a null pointer, n_tau < 1, a negative or
+ * non-finite multiplier, or an image that fails the checks of htsvd_denoise; UNSUPPORTED for
+ * K < 8; optional outputs of p are ignored. Synchronises `stream` once when sigma is estimated. */
+htsvd_status htsvd_denoise_tau_sweep(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, double sigma,
+                                     const double* h_tau_mults, int32_t n_tau, const htsvd_params* p,
+                                     float* d_outs, double* h_sigma, cudaStream_t stream);
+
 /* Noise level from the eigenvalues of the covariance of the reference patches:
  * ascending eigenvalues l_1..l_d, r* = max{r : mean(l_1..r) <= 1.02 median(l_1..r)},
  * sigma = sqrt(mean(l_1..r*)). With p->adapt the eigen-rank vote of Sec. III-D,

@@ -12,7 +12,7 @@ from dataclasses import dataclass, fields
 from . import _lib
 
 __all__ = ["HtsvdParams", "denoise", "denoise_f32", "estimate_sigma", "denoise_batch", "denoise_adaptive",
-           "denoise_video", "denoise_vjp", "num_groups", "HtsvdFn", "load_library"]
+           "denoise_video", "denoise_tau_sweep", "denoise_vjp", "num_groups", "HtsvdFn", "load_library"]
 
 _MATCH = {"auto": 0, "gcp": 1, "full": 2, "green": 3}
 _AGG = {"uniform": 0, "sparsity": 1}
@@ -240,6 +240,25 @@ def denoise_video(frames, sigma=None, params=None, *, T=1, return_info=False, st
     if return_info:
         return out, {"idx": idx, "sigmas": [float(s) for s in sig]}
     return out
+
+
+def denoise_tau_sweep(noisy, tau_mults, sigma=None, params=None, *, return_sigma=False, stream=None):
+    """Alg. 1 on a uint8 (H, W[, C]) CUDA tensor at every tau = tau_mults[i] * sigma, with the grouping,
+    bases, sigma and noisy coefficients computed once. Returns float32 (n, H, W, C)."""
+    lib = _lib.load()
+    torch = _torch()
+    x = _hwc(noisy)
+    if x.dtype != torch.uint8:
+        raise TypeError("denoise_tau_sweep expects uint8")
+    H, W, C = x.shape
+    m = [float(t) for t in tau_mults]
+    outs = torch.empty((len(m), H, W, C), dtype=torch.float32, device=x.device)
+    cp = HtsvdParams.of(params).c()
+    sig = ctypes.c_double(-1.0)
+    _lib.check(lib.htsvd_denoise_tau_sweep(_ptr(x), H, W, C, -1.0 if sigma is None else float(sigma),
+                                           (ctypes.c_double * len(m))(*m), len(m), ctypes.byref(cp), _ptr(outs),
+                                           ctypes.byref(sig), _stream_ptr(stream)), "htsvd_denoise_tau_sweep")
+    return (outs, sig.value) if return_sigma else outs
 
 
 def denoise_vjp(x, sigma, idx, w, out, grad_out, params=None, want_grad_w=True, stream=None):

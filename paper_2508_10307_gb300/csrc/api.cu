@@ -75,7 +75,9 @@ int resolve_mode(const Resolved& r, int C) {
 
 enum Slot {
     S_IDX, S_MOM, S_B64, S_B32, S_PART, S_FULLM, S_FULLS, S_RANKS, S_IDX2, S_Q, S_DEN, S_R, S_TMP,
-    S_AIN, S_AOUT, S_NSLOT           // S_AIN, S_AOUT: subimages of htsvd_denoise_adaptive
+    S_AIN, S_AOUT,                   // S_AIN, S_AOUT: subimages of htsvd_denoise_adaptive
+    S_COEF, S_CPN, S_CNRM,           // coefficient cache of htsvd_denoise_tau_sweep
+    S_NSLOT
 };
 
 struct Workspace {
@@ -424,11 +426,19 @@ struct FilterOut {
 };
 
 // Filter + reduce for the forward pass.
+// Coefficient cache of the noisy groups (FM_ANALYZE writes it, FM_SYNTH reads it).
+struct CoefCache {
+    float* coef;
+    float* pn;
+    int* nrm;
+    int mode;                // FM_ANALYZE or FM_SYNTH
+};
+
 htsvd_status run_forward_filter(Workspace* w, const void* img, int is_float, const Geo& g, const Resolved& r,
                                 const int32_t* idx, const double* b64, const float* b32, double tau,
                                 const float* w_in, const htsvd_params* p, float* d_out, cudaStream_t s,
-                                const VideoCtx* vc = nullptr) {
-    const int mode = vc ? FM_VIDEO : FM_FORWARD;
+                                const VideoCtx* vc = nullptr, const CoefCache* cc = nullptr) {
+    const int mode = vc ? FM_VIDEO : cc ? cc->mode : FM_FORWARD;
     FilterTiling t = choose_filter_tiling(g, is_float ? 4 : 1, mode, r.tile, vc ? vc->nfr : 1);
     if (t.TR == 0) return HTSVD_ERR_UNSUPPORTED;
     FilterArgs a{};
@@ -457,6 +467,11 @@ htsvd_status run_forward_filter(Workspace* w, const void* img, int is_float, con
         a.nfr = vc->nfr;
         a.fref = vc->fref;
     }
+    if (cc) {
+        a.cache_coef = cc->coef;
+        a.cache_pn = cc->pn;
+        a.cache_nrm = cc->nrm;
+    }
     a.mask_out = p ? p->d_mask_out : nullptr;
     a.weights_out = p ? p->d_weights_out : nullptr;
     a.coef_out = p ? p->d_coef_out : nullptr;
@@ -464,7 +479,12 @@ htsvd_status run_forward_filter(Workspace* w, const void* img, int is_float, con
     const int acc = g.C == 3 ? 4 : 2;
     ST(ws_get(w, S_PART, sizeof(float) * (size_t)t.ntx * t.nty * t.FHmax * t.FWmax * acc, &part));
     a.partials = (float*)part;
-    { ProfScope ps_("filter", s); CK(launch_filter(a, s)); }
+    if (mode == FM_ANALYZE) {
+        ProfScope ps_("filter_analyze", s);
+        CK(launch_filter(a, s));
+        return HTSVD_OK;
+    }
+    { ProfScope ps_(mode == FM_SYNTH ? "filter_synth" : "filter", s); CK(launch_filter(a, s)); }
     { ProfScope ps_("reduce", s); CK(launch_reduce((float*)part, g, t.TR, t.ntx, t.nty, t.FHmax, t.FWmax, d_out, nullptr, 0, nullptr, s)); }
     return HTSVD_OK;
 }
@@ -583,6 +603,65 @@ htsvd_status video_impl(const uint8_t* d_vid, int F, int H, int W, int C, int T,
     return HTSVD_OK;
 }
 
+// A sweep of thresholds over one image with the grouping, bases, sigma and the noisy group
+// coefficients computed once and cached (the speed-up of parameter tuning that Sec. III-E
+// points to): output i is Alg. 1 at tau = tau_mults[i] * sigma.
+htsvd_status sweep_impl(const uint8_t* d_in, int H, int W, int C, double sigma, const double* tau_mults, int n_tau,
+                        const htsvd_params* p, float* d_outs, double* h_sigma, cudaStream_t s) {
+    if (!d_in || !d_outs || !tau_mults || n_tau < 1) return HTSVD_ERR_INVALID_ARG;
+    for (int i = 0; i < n_tau; ++i)
+        if (!(tau_mults[i] >= 0.0) || std::isinf(tau_mults[i])) return HTSVD_ERR_INVALID_ARG;
+    Resolved r;
+    ST(resolve(p, C, r));
+    ST(check_image(H, W, C, r));
+    if (std::isnan(sigma)) return HTSVD_ERR_INVALID_ARG;
+    if (r.K < 8) return HTSVD_ERR_UNSUPPORTED;
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    const Geo g = make_geo(H, W, C, r.s, r.win, r.K);
+    const int64_t N = g.ngroups();
+    void *ib, *cc, *cp, *cn;
+    ST(ws_get(w, S_IDX, sizeof(int32_t) * N * r.K, &ib));
+    ST(ws_get(w, S_COEF, sizeof(float) * (size_t)N * r.K * PS2 * C, &cc));
+    ST(ws_get(w, S_CPN, sizeof(float) * (size_t)N * 32, &cp));
+    ST(ws_get(w, S_CNRM, sizeof(int) * (size_t)N, &cn));
+    int32_t* idx = (int32_t*)ib;
+    void* hbuf = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (sigma < 0) {
+        ST(launch_sigma_inputs(w, d_in, g, r, s, &hbuf));
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, s));
+    }
+    ST(ws_side(w));
+    CK(cudaEventRecord(w->ev_fork, s));
+    CK(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
+    double* b64;
+    float* b32;
+    void* fullM = nullptr;
+    if (sigma < 0) ST(ws_get(w, S_FULLM, sizeof(unsigned long long) * PS2 * C * PS2 * C, &fullM));
+    ST(run_basis(w, d_in, g, &b64, &b32, w->side, (const unsigned long long*)fullM));
+    CK(cudaEventRecord(w->ev_join, w->side));
+    ST(run_block_match(d_in, g, r, 1, idx, s));
+    CK(cudaStreamWaitEvent(s, w->ev_join, 0));
+    // the noisy coefficients (tau plays no part in the analysis)
+    CoefCache cache{(float*)cc, (float*)cp, (int*)cn, FM_ANALYZE};
+    ST(run_forward_filter(w, d_in, 0, g, r, idx, b64, b32, 0.0, nullptr, nullptr, nullptr, s, nullptr, &cache));
+    if (sigma < 0) {
+        cudaError_t e = cudaEventSynchronize(ev);
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess) return HTSVD_ERR_CUDA;
+        ST(finish_sigma(hbuf, g, r, &sigma));
+    }
+    if (h_sigma) *h_sigma = sigma;
+    cache.mode = FM_SYNTH;
+    const size_t img = (size_t)H * W * C;
+    for (int i = 0; i < n_tau; ++i)
+        ST(run_forward_filter(w, d_in, 0, g, r, idx, b64, b32, tau_mults[i] * sigma, nullptr, nullptr,
+                              d_outs + i * img, s, nullptr, &cache));
+    return HTSVD_OK;
+}
+
 }  // namespace
 
 // ============================================================================= C ABI
@@ -623,6 +702,12 @@ htsvd_status htsvd_denoise_video(const uint8_t* d_video, int32_t F, int32_t H, i
                                  double sigma, const htsvd_params* p, float* d_out, int32_t* d_idx_out,
                                  double* h_sigmas, cudaStream_t stream) {
     return video_impl(d_video, F, H, W, C, T, sigma, p, d_out, d_idx_out, h_sigmas, stream);
+}
+
+htsvd_status htsvd_denoise_tau_sweep(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, double sigma,
+                                     const double* h_tau_mults, int32_t n_tau, const htsvd_params* p,
+                                     float* d_outs, double* h_sigma, cudaStream_t stream) {
+    return sweep_impl(d_noisy, H, W, C, sigma, h_tau_mults, n_tau, p, d_outs, h_sigma, stream);
 }
 
 htsvd_status htsvd_denoise_f32(const float* d_x, int32_t H, int32_t W, int32_t C, double sigma,

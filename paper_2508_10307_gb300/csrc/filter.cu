@@ -17,6 +17,14 @@ cudaError_t dispatch_mode(const FilterArgs& a, cudaStream_t s) {
             return a.img_is_float ? launch_filter_t<K, C, float, FM_ADJOINT>(a, s) : cudaErrorInvalidValue;
         case FM_VIDEO:
             return a.img_is_float || a.nfr < 1 ? cudaErrorInvalidValue : launch_filter_t<K, C, uint8_t, FM_VIDEO>(a, s);
+        case FM_ANALYZE:
+        case FM_SYNTH:
+            if constexpr (K >= 8) {
+                if (a.img_is_float) return cudaErrorInvalidValue;
+                return a.mode == FM_ANALYZE ? launch_filter_t<K, C, uint8_t, FM_ANALYZE>(a, s)
+                                            : launch_filter_t<K, C, uint8_t, FM_SYNTH>(a, s);
+            }
+            return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
 }
@@ -142,7 +150,7 @@ __global__ void div_kernel(const float* __restrict__ gout, const float* __restri
 
 size_t filter_smem_bytes(const FilterArgs& a) {
     const int inb = a.img_is_float ? 4 : 1;
-    if (a.mode == FM_FORWARD || a.mode == FM_VIDEO) {
+    if (a.mode == FM_FORWARD || a.mode == FM_VIDEO || a.mode == FM_ANALYZE || a.mode == FM_SYNTH) {
         const int nfr = a.mode == FM_VIDEO && a.nfr > 0 ? a.nfr : 1;
         return a.g.C == 3 ? f_layout_fwd<32, 3>(a.FHmax, a.FWmax, inb, nfr).total
                           : f_layout_fwd<32, 1>(a.FHmax, a.FWmax, inb, nfr).total;

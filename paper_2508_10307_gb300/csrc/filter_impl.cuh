@@ -846,7 +846,10 @@ __device__ __forceinline__ void stage_e2(const float* bas, float* gb, int k, int
 // one above the other, the reference frame's first (slot 0, rows [0, FH)), the others after it in
 // frame order; a patch's staged row is slot * FH + its row in the footprint, so every stage reads
 // it as in one image, and the aggregation adds the slot-0 patches only.
-template <int K, int C, typename Tin, bool MF>
+// VAR: 0 the whole filter; 1 (FM_ANALYZE) projections and Haar analysis only, the coefficients,
+// patch norms and ||G||_F^2 written to the cache; 2 (FM_SYNTH) the cached coefficients loaded in
+// place of the projections, then threshold, synthesis and aggregation as in the whole filter.
+template <int K, int C, typename Tin, bool MF, int VAR = 0>
 __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int tile, unsigned char* smem) {
     using G = FCfg<C>;
     constexpr int NF = G::PATCH;
@@ -980,6 +983,10 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
             const int wk = __reduce_add_sync(0xffffffffu, __popc(keepb));
             if (lane == 0) atomicAdd(&misc[1], wk);
         };
+        if constexpr (VAR == 1) {                     // per-patch norms and ||G||_F^2 of the group
+            if (tid < K) a.cache_pn[(size_t)grp * 32 + tid] = pn[tid];
+            if (tid == 0) a.cache_nrm[grp] = sizeof(Tin) == 1 ? misc[5] : misc[2];
+        }
         if (tid < NF) {
             const float nrm2 = sizeof(Tin) == 1 ? (float)misc[5] : __int_as_float(misc[2]);
             const float delta = a.band_rel * sqrtf(nrm2) + a.band_abs;
@@ -995,7 +1002,13 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 float v[K];                               // fibre, then its coefficients (haar_for_each slots)
 #pragma unroll
                 for (int k = 0; k < K; ++k) v[k] = gbq[k * G::GS + foff];
-                haar_fwd_sum<K>(v);
+                if constexpr (VAR != 2) haar_fwd_sum<K>(v);
+                if constexpr (VAR == 1) {                 // analysis only: cache the coefficients
+                    float* cdst = a.cache_coef + (size_t)grp * K * NF + fib;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) cdst[(size_t)k * NF] = v[k];
+                    return;
+                }
                 if (a.coef_out) {
                     float* cdst = a.coef_out + (size_t)grp * K * NF;
                     haar_for_each<K>([&](int m, int sl, int L) { cdst[m * NF + fib] = v[sl] * rsqrtf((float)L); });
@@ -1081,16 +1094,33 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
 
         // ---- D, E(q) (inverse projection) on the first half | A, B(q+1) on the second half
         if (q >= 0 && tid < NU) {
-            float* gbq = gb_of(q);
-            stage_d2<C>(bas, gbq, tid >> 2, tid & 3);
-            __syncwarp(kU);
-            stage_e2<C>(bas, gbq, tid >> 2, tid & 3);
+            if constexpr (VAR != 1) {
+                float* gbq = gb_of(q);
+                stage_d2<C>(bas, gbq, tid >> 2, tid & 3);
+                __syncwarp(kU);
+                stage_e2<C>(bas, gbq, tid >> 2, tid & 3);
+            }
         } else if (tid >= AB0 && tid < AB0 + NU && q + 1 < ngr) {
-            project(tid - AB0, q + 1);
+            if constexpr (VAR == 2) {
+                // the cached coefficients of group q+1, four fibres per 128-bit word (64 C fibres per
+                // slot; a run of four never crosses a patch row)
+                const int u = tid - AB0;
+                const int g1 = group_of(q + 1);
+                const float4* src = reinterpret_cast<const float4*>(a.cache_coef + (size_t)g1 * K * NF);
+                float* gbn = gb_of(q + 1);
+                for (int e4 = u; e4 < K * NF / 4; e4 += NU) {
+                    const int k = e4 / (NF / 4), fb = 4 * (e4 - k * (NF / 4));
+                    *reinterpret_cast<float4*>(gbn + k * G::GS + (fb / G::RWF) * G::ROW + fb % G::RWF) = src[e4];
+                }
+                if (u < K) pn_of(q + 1)[u] = a.cache_pn[(size_t)g1 * 32 + u];
+                if (u == 0) misc_of(q + 1)[sizeof(Tin) == 1 ? 5 : 2] = a.cache_nrm[g1];
+            } else {
+                project(tid - AB0, q + 1);
+            }
         }
         if (q + 1 < ngr) clear_masks(q + 1);
         __syncthreads();
-        if (q >= 0) {
+        if (VAR != 1 && q >= 0) {
             const int grp = group_of(q);
             const float* gbq = gb_of(q);
             const int* pos = pos_of(q);
@@ -1136,6 +1166,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         }
         __syncthreads();
     }
+    if constexpr (VAR == 1) return;                   // analysis only: nothing aggregated
     // Write the tile partial.
     float* dst = a.partials + (size_t)tile * a.FHmax * a.FWmax * G::ACC;
     if constexpr (C == 3) {
@@ -1161,6 +1192,10 @@ template <int K, int C, typename Tin, int MODE>
 __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile, unsigned char* smem) {
     if constexpr (MODE == FM_FORWARD || MODE == FM_VIDEO) {
         filter_tile_fwd<K, C, Tin, MODE == FM_VIDEO>(a, tile, smem);
+        return;
+    }
+    if constexpr (MODE == FM_ANALYZE || MODE == FM_SYNTH) {
+        filter_tile_fwd<K, C, Tin, false, MODE == FM_ANALYZE ? 1 : 2>(a, tile, smem);
         return;
     }
     using G = FCfg<C>;
@@ -1428,7 +1463,8 @@ __global__ void __launch_bounds__(FT_THREADS, 2) filter_batch_kernel(const Filte
 
 template <int K, int C, typename Tin, int MODE>
 cudaError_t launch_filter_t(const FilterArgs& a, cudaStream_t s) {
-    const FLayout L = MODE == FM_FORWARD ? f_layout_fwd<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin))
+    const FLayout L = (MODE == FM_FORWARD || MODE == FM_ANALYZE || MODE == FM_SYNTH)
+                          ? f_layout_fwd<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin))
                       : MODE == FM_VIDEO ? f_layout_fwd<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), a.nfr)
                                          : f_layout<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), MODE);
     auto fn = filter_kernel<K, C, Tin, MODE>;

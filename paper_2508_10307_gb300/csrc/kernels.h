@@ -51,7 +51,7 @@ cudaError_t launch_basis(const unsigned long long* d_mom, int C, double* d_basis
 cudaError_t launch_quantize(const float* x, int64_t n, uint8_t* q, cudaStream_t s);
 
 // ---- group filter and aggregation (filter.cu)
-enum FilterMode { FM_FORWARD = 0, FM_DENOM = 1, FM_ADJOINT = 2, FM_VIDEO = 3 };
+enum FilterMode { FM_FORWARD = 0, FM_DENOM = 1, FM_ADJOINT = 2, FM_VIDEO = 3, FM_ANALYZE = 4, FM_SYNTH = 5 };
 
 // Guard band of the threshold decision: a coefficient whose FP32 value lies within
 // kBandRel * ||G||_F + kBandTau * tau of tau is decided again in FP64 (||G||_F: Frobenius
@@ -88,6 +88,13 @@ struct FilterArgs {
     const void* vid;
     long long fstride;
     int f0, nfr, fref;
+    // Coefficient cache of the noisy groups (threshold sweeps): FM_ANALYZE writes, FM_SYNTH reads
+    // the Haar-domain coefficients of every group ([N][K][64 C] floats, unnormalised Haar, slot
+    // order of the in-place transform), the per-patch squared norms ([N][32]) and ||G||_F^2 ([N],
+    // the filter's own integer or float-bit representation).
+    float* cache_coef;
+    float* cache_pn;
+    int* cache_nrm;
 };
 size_t filter_smem_bytes(const FilterArgs& a);
 cudaError_t launch_filter(const FilterArgs& a, cudaStream_t s);

@@ -102,3 +102,19 @@ def test_video_rejects_bad_arguments_on_the_host():
     assert call(None, 3, 1) == 1               # null clip
     assert lib.htsvd_denoise_video(dp, 3, 64, 64, 2, 1, 10.0, ctypes.byref(cp), dp, None, None, None) == 1
 
+
+def test_tau_sweep_rejects_bad_arguments_on_the_host():
+    lib = H.load_library()
+    dp = ctypes.c_void_p(1)
+    ok = (ctypes.c_double * 2)(1.0, 2.0)
+    bad = (ctypes.c_double * 2)(1.0, -2.0)
+
+    def call(mults, n, params=None):
+        cp = H.HtsvdParams.of(params).c()
+        return lib.htsvd_denoise_tau_sweep(dp, 64, 64, 3, 10.0, mults, n, ctypes.byref(cp), dp, None, None)
+
+    assert call(ok, 0) == 1                    # no thresholds
+    assert call(bad, 2) == 1                   # negative multiplier
+    assert call(None, 2) == 1                  # null list
+    assert call(ok, 2, dict(K=4)) == 2         # cached coefficients need K >= 8
+
