@@ -56,6 +56,12 @@ Readings where the paper is silent or ambiguous (each is listed in the design doc):
      reference itself excluded, compared on the plane its own patch selects (R1,
      R2 on frame t); keys (SSD, f*H*W + y*W + x), ties -> lowest global index;
      only the estimated patches that lie in frame t are aggregated into it.
+  R17 threshold selection by Stein's unbiased risk estimate (the paper only notes that tuning is
+     sped up by caching indices and coefficients, Sec. III-E): for each multiplier m,
+     f = Alg. 1 at tau = m sigma on a float image y (R13), n = H W C,
+     SURE(m) = ||f - y||^2 / n - sigma^2 + (2 sigma^2 / n) b^T J^T b, with J the Jacobian of the
+     frozen-mask map at y (R14; the hard threshold's jump terms are not counted) and b a caller-given
+     probe (a Rademacher vector makes b^T J b an unbiased estimate of trace J).
 
 Parity pins for every function are in tests/test_oracle_pins.py.
 """
@@ -749,3 +755,26 @@ def denoise_video(video: np.ndarray, sigma=None, params=None, T: int = 1, *, kee
         results.append(Result(out=out[t], idx=idx, tau=tau, U=U, V=V, weights=w_out, masks=masks, den=den,
                               ambiguous=np.array(amb, dtype=np.int64).reshape(-1, 2), extra={"sigma": sg}))
     return out, results
+
+
+# --------------------------------------------------------------------------- threshold selection (reading R17)
+
+def sure(x: np.ndarray, sigma: float, tau_mults, probe: np.ndarray, params=None) -> np.ndarray:
+    """Reading R17: SURE(m) for every multiplier m, the divergence through the frozen-mask adjoint
+    applied to the probe. x: float (H, W, C) image on the [0, 255] scale; probe: same shape."""
+    p = Params.of(params)
+    if x.ndim == 2:
+        x = x[:, :, None]
+    if probe.ndim == 2:
+        probe = probe[:, :, None]
+    xf = x.astype(np.float64)
+    b = probe.astype(np.float64)
+    n = xf.size
+    res = []
+    for m in tau_mults:
+        pm = Params.of(dict(p.__dict__, tau_mult=float(m)))
+        r = denoise(xf, sigma, pm, keep_masks=True)
+        gx, _ = denoise_fixed_vjp(xf, b, r.idx, r.masks, r.U, r.V, r.weights, pm.ps)
+        res.append(((r.out - xf) ** 2).sum() / n - sigma ** 2 + 2.0 * sigma ** 2 / n * float((b * gx).sum()))
+    return np.array(res)
+

@@ -533,3 +533,42 @@ def test_video_static_clip_groups_the_reference_copies_first():
     ref = idx[:, 0] - H * W
     np.testing.assert_array_equal(idx[:, 1], ref)                # frame 0 copy
     np.testing.assert_array_equal(idx[:, 2], ref + 2 * H * W)    # frame 2 copy
+
+
+# ---------------------------------------------------------------- SURE threshold selection (reading R17)
+
+def _probe(shape, seed):
+    return np.random.default_rng(seed).choice([-1.0, 1.0], size=shape)
+
+
+def test_sure_closed_forms_at_zero_and_infinite_threshold():
+    """tau = 0 keeps every coefficient: f(y) = y and J = I, so SURE = -sigma^2 + 2 sigma^2 b^T b / n
+    = sigma^2 for a +-1 probe. A threshold above every coefficient gives f = 0 and J = 0, so
+    SURE = ||y||^2 / n - sigma^2."""
+    y = synth.add_gaussian_float(synth.clean_image(24, 26, 3, 61), 20.0, 62)
+    prm = dict(ps=8, stride=3, window=7, K=8)
+    b = _probe(y.shape, 63)
+    s0, sbig = O.sure(y, 20.0, [1e-12, 1e6], b, prm)
+    assert s0 == pytest.approx(20.0 ** 2, rel=1e-9)
+    assert sbig == pytest.approx((y.astype(np.float64) ** 2).mean() - 20.0 ** 2, rel=1e-12)
+
+
+def test_sure_divergence_is_the_trace_of_the_frozen_map():
+    """Summing b^T J^T b over the unit probes e_i gives trace J, computed here column by column from
+    the frozen-mask map itself (a linear map in its input)."""
+    y = synth.add_gaussian_float(synth.clean_image(12, 12, 1, 71), 25.0, 72)
+    prm = O.Params.of(dict(ps=8, stride=2, window=5, K=4, tau_mult=2.0))
+    r = O.denoise(y, 25.0, prm, keep_masks=True)
+    n = y.size
+    tr_cols = 0.0
+    tr_vjp = 0.0
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        e = e.reshape(y.shape[0], y.shape[1], 1)
+        col, _ = O.denoise_fixed(e, r.idx, r.masks, r.U, r.V, r.weights, prm.ps)
+        tr_cols += col.ravel()[i]
+        gx, _ = O.denoise_fixed_vjp(y, e, r.idx, r.masks, r.U, r.V, r.weights, prm.ps)
+        tr_vjp += gx.ravel()[i]
+    assert tr_vjp == pytest.approx(tr_cols, rel=1e-10)
+    assert 0.0 < tr_cols < n
