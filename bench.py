@@ -334,6 +334,28 @@ def make_workload(name):
         return Workload(name, cfg, len(mults) * 512 * 512 / 1e6, len(mults) * n, 3, 32, [noisy],
                         lambda d: [H.denoise_tau_sweep(d[0], mults, None, prm)], len(mults) * 512 * 512 * 3 * 4,
                         plain, "separate_calls_per_tau"), None
+    if name == "sure512":
+        clean = synth.clean_image(512, 512, 3, 5001)
+        y = synth.add_gaussian_float(clean, 25.0, 5001).astype(np.float32)
+        probe = np.random.default_rng(5002).choice([-1.0, 1.0], size=y.shape).astype(np.float32)
+        prm = dict(ps=8, stride=2, window=31, K=32)
+        mults = [1.8, 2.4, 3.0, 3.6]
+        cfg = {"workload": "sure_rgb512_f32_x4", "image": "512x512x3 float32", "noise": "gaussian sigma=25",
+               "sigma": "given (25)", "tau_mults": mults, "ps": 8, "stride": 2, "window": 31, "K": 32,
+               "form": "per multiplier: forward, frozen-mask VJP of a +-1 probe, FP64 sums (MP count: 4 images)"}
+        n = H.num_groups(512, 512, prm)
+        pb = [None]
+
+        def step(d):
+            if pb[0] is None:
+                pb[0] = dev(probe)
+            return [torch.tensor(H.sure(d[0], 25.0, mults, pb[0], prm))]
+
+        def forward_only(d):
+            return [H.denoise_f32(d[0], 25.0, dict(prm, tau_mult=m)) for m in mults]
+
+        return Workload(name, cfg, len(mults) * 512 * 512 / 1e6, len(mults) * n, 3, 32, [y], step, 8 * len(mults),
+                        forward_only, "forward_only_per_tau"), None
     raise ValueError(name)
 
 
@@ -476,7 +498,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rgb512", choices=["rgb512", "gray128", "rgb4k", "batch64", "vjp8", "adaptive512",
-                                                      "video1080", "sweep512"])
+                                                      "video1080", "sweep512", "sure512"])
     ap.add_argument("--cpu-rows", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-worker", type=int, default=None)

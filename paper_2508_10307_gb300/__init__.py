@@ -12,7 +12,7 @@ from dataclasses import dataclass, fields
 from . import _lib
 
 __all__ = ["HtsvdParams", "denoise", "denoise_f32", "estimate_sigma", "denoise_batch", "denoise_adaptive",
-           "denoise_video", "denoise_tau_sweep", "denoise_vjp", "num_groups", "HtsvdFn", "load_library"]
+           "denoise_video", "denoise_tau_sweep", "sure", "denoise_vjp", "num_groups", "HtsvdFn", "load_library"]
 
 _MATCH = {"auto": 0, "gcp": 1, "full": 2, "green": 3}
 _AGG = {"uniform": 0, "sparsity": 1}
@@ -259,6 +259,25 @@ def denoise_tau_sweep(noisy, tau_mults, sigma=None, params=None, *, return_sigma
                                            (ctypes.c_double * len(m))(*m), len(m), ctypes.byref(cp), _ptr(outs),
                                            ctypes.byref(sig), _stream_ptr(stream)), "htsvd_denoise_tau_sweep")
     return (outs, sig.value) if return_sigma else outs
+
+
+def sure(y, sigma, tau_mults, probe, params=None, stream=None):
+    """SURE of each threshold multiplier on a float32 (H, W[, C]) CUDA image y, with the divergence
+    through the frozen-mask VJP applied to probe (same shape; e.g. a +-1 Rademacher vector).
+    Returns a list of floats; synchronises the stream."""
+    lib = _lib.load()
+    torch = _torch()
+    x = _hwc(y)
+    if x.dtype != torch.float32:
+        raise TypeError("sure expects float32")
+    b = _hwc(probe).contiguous().float()
+    H, W, C = x.shape
+    m = [float(t) for t in tau_mults]
+    res = (ctypes.c_double * len(m))()
+    cp = HtsvdParams.of(params).c()
+    _lib.check(lib.htsvd_sure(_ptr(x.contiguous()), H, W, C, float(sigma), (ctypes.c_double * len(m))(*m), len(m),
+                              _ptr(b), ctypes.byref(cp), res, _stream_ptr(stream)), "htsvd_sure")
+    return [float(v) for v in res]
 
 
 def denoise_vjp(x, sigma, idx, w, out, grad_out, params=None, want_grad_w=True, stream=None):

@@ -13,7 +13,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "OOM"
 EXPORTED = ["htsvd_denoise", "htsvd_denoise_f32", "htsvd_estimate_sigma", "htsvd_denoise_batch",
             "htsvd_denoise_vjp", "htsvd_num_groups", "htsvd_status_string", "htsvd_release_workspace",
             "htsvd_profile_enable", "htsvd_profile_collect", "htsvd_denoise_noalloc", "htsvd_denoise_adaptive",
-            "htsvd_denoise_video", "htsvd_denoise_tau_sweep"]
+            "htsvd_denoise_video", "htsvd_denoise_tau_sweep", "htsvd_sure"]
 
 
 class CParams(ctypes.Structure):
@@ -78,6 +78,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                         vp]
     lib.htsvd_denoise_tau_sweep.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(ctypes.c_double), i32, P, vp,
                                             ctypes.POINTER(ctypes.c_double), vp]
+    lib.htsvd_sure.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(ctypes.c_double), i32, vp, P,
+                               ctypes.POINTER(ctypes.c_double), vp]
     lib.htsvd_num_groups.argtypes = [i32, i32, P]
     lib.htsvd_num_groups.restype = ctypes.c_int64
     lib.htsvd_status_string.argtypes = [ctypes.c_int]
@@ -90,7 +92,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.htsvd_profile_collect.restype = i32
     for name in ["htsvd_denoise", "htsvd_denoise_f32", "htsvd_estimate_sigma", "htsvd_denoise_batch",
                  "htsvd_denoise_vjp", "htsvd_release_workspace", "htsvd_denoise_noalloc", "htsvd_denoise_adaptive",
-                 "htsvd_denoise_video", "htsvd_denoise_tau_sweep"]:
+                 "htsvd_denoise_video", "htsvd_denoise_tau_sweep", "htsvd_sure"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

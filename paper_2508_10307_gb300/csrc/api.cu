@@ -77,6 +77,7 @@ enum Slot {
     S_IDX, S_MOM, S_B64, S_B32, S_PART, S_FULLM, S_FULLS, S_RANKS, S_IDX2, S_Q, S_DEN, S_R, S_TMP,
     S_AIN, S_AOUT,                   // S_AIN, S_AOUT: subimages of htsvd_denoise_adaptive
     S_COEF, S_CPN, S_CNRM,           // coefficient cache of htsvd_denoise_tau_sweep
+    S_SOUT, S_SGX, S_SIDX, S_SRED,   // htsvd_sure: estimate, adjoint, grouping, reduction terms
     S_NSLOT
 };
 
@@ -894,6 +895,52 @@ htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C
     a.partials = (float*)part;
     { ProfScope ps_("filter", s); CK(launch_filter(a, s)); }
     { ProfScope ps_("reduce", s); CK(launch_reduce((float*)part, g, ta.TR, ta.ntx, ta.nty, ta.FHmax, ta.FWmax, d_grad_x, nullptr, 1, nullptr, s)); }
+    return HTSVD_OK;
+}
+
+htsvd_status htsvd_sure(const float* d_y, int32_t H, int32_t W, int32_t C, double sigma, const double* h_tau_mults,
+                        int32_t n_tau, const float* d_probe, const htsvd_params* p, double* h_sure,
+                        cudaStream_t s) {
+    if (!d_y || !d_probe || !h_tau_mults || !h_sure || n_tau < 1) return HTSVD_ERR_INVALID_ARG;
+    if (!(sigma > 0) || std::isinf(sigma)) return HTSVD_ERR_INVALID_ARG;
+    for (int i = 0; i < n_tau; ++i)
+        if (!(h_tau_mults[i] > 0.0) || std::isinf(h_tau_mults[i])) return HTSVD_ERR_INVALID_ARG;
+    Resolved r;
+    ST(resolve(p, C, r));
+    ST(check_image(H, W, C, r));
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    const int64_t n = (int64_t)H * W * C;
+    const Geo g = make_geo(H, W, C, r.s, r.win, r.K);
+    void *out, *gx, *idx, *red;
+    ST(ws_get(w, S_SOUT, sizeof(float) * n, &out));
+    ST(ws_get(w, S_SGX, sizeof(float) * n, &gx));
+    ST(ws_get(w, S_SIDX, sizeof(int32_t) * g.ngroups() * r.K, &idx));
+    ST(ws_get(w, S_SRED, sizeof(double) * (sure_scratch_doubles() + 2 * (size_t)n_tau), &red));
+    double* scratch = (double*)red;
+    double* terms = scratch + sure_scratch_doubles();
+    htsvd_params pm;
+    if (p) pm = *p;
+    else std::memset(&pm, 0, sizeof(pm));
+    pm.h_sigma_out = nullptr;
+    pm.d_mask_out = nullptr;
+    pm.d_weights_out = nullptr;
+    pm.d_basis_out = nullptr;
+    pm.d_coef_out = nullptr;
+    for (int i = 0; i < n_tau; ++i) {
+        pm.tau_mult = h_tau_mults[i];
+        // f = Alg. 1 at tau = m sigma, then J^T b through the frozen-mask adjoint, then the two sums
+        ST(denoise_impl(d_y, 1, H, W, C, sigma, &pm, nullptr, (float*)out, (int32_t*)idx, s));
+        ST(htsvd_denoise_vjp(d_y, H, W, C, sigma, &pm, (const int32_t*)idx, nullptr, (const float*)out, d_probe,
+                             (float*)gx, nullptr, s));
+        { ProfScope ps_("sure_terms", s); CK(launch_sure_terms((const float*)out, d_y, d_probe, (const float*)gx, n,
+                                                               scratch, terms + 2 * i, s)); }
+    }
+    std::vector<double> h(2 * (size_t)n_tau);
+    CK(cudaMemcpyAsync(h.data(), terms, sizeof(double) * 2 * n_tau, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < n_tau; ++i)
+        h_sure[i] = h[2 * i] / (double)n - sigma * sigma + 2.0 * sigma * sigma / (double)n * h[2 * i + 1];
     return HTSVD_OK;
 }
 

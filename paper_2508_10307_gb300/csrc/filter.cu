@@ -146,7 +146,61 @@ __global__ void div_kernel(const float* __restrict__ gout, const float* __restri
         r[i] = gout[i] / den[i / C];
 }
 
+// SURE terms: block b sums (out - x)^2 and probe * g over a strided range in FP64, then a tree in
+// shared memory; part[2b], part[2b+1]. Fixed order, so the result is reproducible.
+constexpr int SURE_THREADS = 256;
+constexpr int SURE_BLOCKS = 304;
+
+__global__ void __launch_bounds__(SURE_THREADS) sure_terms_kernel(const float* __restrict__ out,
+                                                                  const float* __restrict__ x,
+                                                                  const float* __restrict__ b,
+                                                                  const float* __restrict__ g, int64_t n,
+                                                                  double* __restrict__ part) {
+    __shared__ double s1[SURE_THREADS], s2[SURE_THREADS];
+    double a1 = 0.0, a2 = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)SURE_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * SURE_THREADS) {
+        const double d = (double)out[i] - (double)x[i];
+        a1 += d * d;
+        a2 += (double)b[i] * (double)g[i];
+    }
+    s1[threadIdx.x] = a1;
+    s2[threadIdx.x] = a2;
+    __syncthreads();
+    for (int h = SURE_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s1[threadIdx.x] += s1[threadIdx.x + h];
+            s2[threadIdx.x] += s2[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s1[0];
+        part[2 * blockIdx.x + 1] = s2[0];
+    }
+}
+
+__global__ void sure_sum_kernel(const double* __restrict__ part, int nb, double* __restrict__ res) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            a1 += part[2 * i];
+            a2 += part[2 * i + 1];
+        }
+        res[0] = a1;
+        res[1] = a2;
+    }
+}
+
 }  // namespace
+
+size_t sure_scratch_doubles() { return 2 * (size_t)SURE_BLOCKS; }
+
+cudaError_t launch_sure_terms(const float* out, const float* x, const float* b, const float* g, int64_t n,
+                              double* scratch, double* res, cudaStream_t s) {
+    sure_terms_kernel<<<SURE_BLOCKS, SURE_THREADS, 0, s>>>(out, x, b, g, n, scratch);
+    sure_sum_kernel<<<1, 32, 0, s>>>(scratch, SURE_BLOCKS, res);
+    return cudaGetLastError();
+}
 
 size_t filter_smem_bytes(const FilterArgs& a) {
     const int inb = a.img_is_float ? 4 : 1;

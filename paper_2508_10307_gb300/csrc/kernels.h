@@ -102,6 +102,11 @@ cudaError_t launch_filter(const FilterArgs& a, cudaStream_t s);
 // denominator plane is written too; if num_only, out = sum num (no division).
 cudaError_t launch_reduce(const float* partials, const Geo& g, int TR, int ntx, int nty, int FHmax, int FWmax,
                           float* out, float* den_out, int num_only, const float* den_in, cudaStream_t s);
+// SURE terms in FP64: res[0] = sum (out - x)^2, res[1] = sum b * g over n floats (deterministic
+// two-level reduction; scratch: sure_scratch_doubles() doubles).
+size_t sure_scratch_doubles();
+cudaError_t launch_sure_terms(const float* out, const float* x, const float* b, const float* g, int64_t n,
+                              double* scratch, double* res, cudaStream_t s);
 // Adjoint helper: r = gout / den.
 cudaError_t launch_div(const float* gout, const float* den, int64_t npix, int C, float* r, cudaStream_t s);
 

@@ -118,3 +118,18 @@ def test_tau_sweep_rejects_bad_arguments_on_the_host():
     assert call(None, 2) == 1                  # null list
     assert call(ok, 2, dict(K=4)) == 2         # cached coefficients need K >= 8
 
+
+def test_sure_rejects_bad_arguments_on_the_host():
+    lib = H.load_library()
+    dp = ctypes.c_void_p(1)
+    cp = H.HtsvdParams().c()
+    res = (ctypes.c_double * 2)()
+    ok = (ctypes.c_double * 2)(1.0, 2.0)
+    zero = (ctypes.c_double * 2)(1.0, 0.0)
+    call = lambda sigma, m, n, probe=dp: lib.htsvd_sure(dp, 64, 64, 3, sigma, m, n, probe, ctypes.byref(cp), res,
+                                                         None)
+    assert call(10.0, ok, 0) == 1              # no thresholds
+    assert call(0.0, ok, 2) == 1               # sigma must be positive
+    assert call(10.0, zero, 2) == 1            # multipliers must be positive
+    assert call(10.0, ok, 2, None) == 1        # no probe
+

@@ -1,0 +1,34 @@
+"""SURE threshold selection through the C ABI against the oracle (reading R17)."""
+import numpy as np
+import pytest
+
+from oracle import htsvd_oracle as O
+from paper_2508_10307_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2508_10307_gb300 as H  # noqa: E402
+
+
+@pytest.mark.parametrize("shape,prm,sigma", [
+    ((48, 56, 3), dict(ps=8, stride=3, window=11, K=16), 20.0),
+    ((40, 44, 1), dict(ps=8, stride=2, window=9, K=8), 25.0),
+])
+def test_sure_matches_oracle(shape, prm, sigma):
+    y = synth.add_gaussian_float(synth.clean_image(*shape, 801), sigma, 802).astype(np.float32)
+    b = np.random.default_rng(803).choice([-1.0, 1.0], size=y.shape).astype(np.float32)
+    mults = [1.6, 2.2, 2.8, 3.6]
+    ref = O.sure(y.astype(np.float64), sigma, mults, b.astype(np.float64), prm)
+    got = np.array(H.sure(torch.from_numpy(y).cuda(), sigma, mults, torch.from_numpy(b).cuda(), prm))
+    # FP32 estimates within 1e-3 per pixel move each term by far less than 1e-3 of sigma^2
+    np.testing.assert_allclose(got, ref, rtol=1e-3, atol=1e-3 * sigma ** 2)
+    assert int(np.argmin(got)) == int(np.argmin(ref))
+
+
+def test_sure_of_a_vanishing_threshold_is_sigma_squared():
+    y = synth.add_gaussian_float(synth.clean_image(40, 48, 3, 811), 15.0, 812).astype(np.float32)
+    b = np.random.default_rng(813).choice([-1.0, 1.0], size=y.shape).astype(np.float32)
+    (s,) = H.sure(torch.from_numpy(y).cuda(), 15.0, [1e-9], torch.from_numpy(b).cuda(),
+                  dict(ps=8, stride=3, window=9, K=8))
+    assert s == pytest.approx(15.0 ** 2, rel=1e-4)
