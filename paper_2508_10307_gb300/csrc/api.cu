@@ -311,6 +311,7 @@ htsvd_status run_block_match(const uint8_t* q, const Geo& g, const Resolved& r, 
     a.nrx_s = (g.nrx + rstep - 1) / rstep;
     choose_bm_tiles(g, rstep, a.TRy, a.TRx);
     bm_fit_tiles(a);
+    if (bm_smem_bytes(a) > 227 * 1024) return HTSVD_ERR_UNSUPPORTED;   // e.g. too many frames in reach
     a.idx = idx;
     { ProfScope ps_("block_match", s); CK(launch_block_match(a, s)); }
     return HTSVD_OK;
