@@ -40,16 +40,57 @@ __device__ __forceinline__ void moments_chunk(const uint8_t* __restrict__ img, c
     for (int rb = r0; rb < r1; rb += MOM_BATCH) {
         const int nb = min(MOM_BATCH, r1 - rb);
         __syncthreads();
-        for (int t = threadIdx.x; t < nb * PS2 * C; t += 256) {
-            int j = t / (PS2 * C), rem = t - j * PS2 * C;
-            int pix = rem / C, c = rem - pix * C;
-            int a = pix / PS, b = pix % PS;
-            int r = rb + j;
-            int iy = r / g.nrx, ix = r - iy * g.nrx;
-            int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
-            uint8_t v = img[((size_t)(ry + a) * g.W + rx + b) * C + c];
-            reinterpret_cast<uint8_t*>(&rows[j][c][a][0])[b] = v;
-            reinterpret_cast<uint8_t*>(&cols[j][c][b][0])[a] = v;
+        // rows: task (reference j, patch row a) reads the row's 8 C bytes as aligned 32-bit words
+        // (alignment from the absolute address), shifts them into place and splits the channels
+        for (int t = threadIdx.x; t < nb * PS; t += 256) {
+            const int j = t >> 3, a = t & 7;
+            const int r = rb + j;
+            const int iy = r / g.nrx, ix = r - iy * g.nrx;
+            const int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
+            constexpr int NW = 2 * C;                 // words of one patch row
+            const uintptr_t ad = reinterpret_cast<uintptr_t>(img + ((size_t)(ry + a) * g.W + rx) * C);
+            const int o = (int)(ad & 3);
+            // every word read holds at least one byte of the row, so none leaves the image's aligned words
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(ad - o);
+            uint32_t wv[NW + 1], al[NW];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) wv[k] = w[k];
+            wv[NW] = o ? w[NW] : 0u;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) al[k] = __funnelshift_r(wv[k], wv[k + 1], 8 * o);
+            if constexpr (C == 1) {
+                rows[j][0][a][0] = al[0];
+                rows[j][0][a][1] = al[1];
+            } else {
+                // channel c, pixels 4h .. 4h+3: bytes 12h + c + 3i (i = 0..3) of the row
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint32_t v = 0u;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int pb = 12 * h + c + 3 * i;
+                            v |= ((al[pb >> 2] >> (8 * (pb & 3))) & 0xffu) << (8 * i);
+                        }
+                        rows[j][c][a][h] = v;
+                    }
+            }
+        }
+        __syncthreads();
+        // columns: block (j, c, word w of the column = rows 4w..4w+3, word h of the row = columns
+        // 4h..4h+3) is a 4 x 4 byte transpose of four row words
+        for (int t = threadIdx.x; t < nb * C * 4; t += 256) {
+            const int j = t / (C * 4), rem = t - j * C * 4;
+            const int c = rem >> 2, w = (rem >> 1) & 1, h = rem & 1;
+            const uint32_t r0 = rows[j][c][4 * w + 0][h], r1 = rows[j][c][4 * w + 1][h];
+            const uint32_t r2 = rows[j][c][4 * w + 2][h], r3 = rows[j][c][4 * w + 3][h];
+            const uint32_t lo01 = __byte_perm(r0, r1, 0x5140u), hi01 = __byte_perm(r0, r1, 0x7362u);
+            const uint32_t lo23 = __byte_perm(r2, r3, 0x5140u), hi23 = __byte_perm(r2, r3, 0x7362u);
+            cols[j][c][4 * h + 0][w] = __byte_perm(lo01, lo23, 0x5410u);
+            cols[j][c][4 * h + 1][w] = __byte_perm(lo01, lo23, 0x7632u);
+            cols[j][c][4 * h + 2][w] = __byte_perm(hi01, hi23, 0x5410u);
+            cols[j][c][4 * h + 3][w] = __byte_perm(hi01, hi23, 0x7632u);
         }
         __syncthreads();
 #pragma unroll
