@@ -78,17 +78,6 @@ __host__ __device__ inline BmLayout bm_layout(int h, int w, int nb, bool sum_pla
     return L;
 }
 
-// Candidate rows per lane strip on the byte planes: the cheaper of 4 and 8 by loads (R + 7 rows)
-// and products (8 R row pairs) per chunk of 32/qpr strips; 4 when three planes are matched
-// (the reference words of three planes stay in registers).
-__host__ __device__ inline int bm_strip_rows(const Geo& g, int nb) {
-    if (nb == 3) return 4;
-    const int qpr = (g.wnx + 3) / 4, G = 32 / qpr;
-    const int c8 = (g.wny + G * 8 - 1) / (G * 8) * ((8 + PS - 1) * 13 + 8 * PS * 8);
-    const int c4 = (g.wny + G * 4 - 1) / (G * 4) * ((4 + PS - 1) * 13 + 4 * PS * 8);
-    return c8 <= c4 ? 8 : 4;
-}
-
 // Bitonic sort of one key per lane, ascending across the warp.
 __device__ __forceinline__ unsigned long long warp_sort_asc(unsigned long long v, int lane) {
 #pragma unroll
@@ -442,7 +431,6 @@ __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigne
     const int tw = ix1 - ix0 + 1;
     const int nt = (iy1 - iy0 + 1) * tw;
     const int K = g.K;
-    const int R = bm_strip_rows(g, nb);
     for (int t = warp; t < nt; t += BM_WARPS) {
         const int iy = iy0 + t / tw, ix = ix0 + t % tw;
         RefCtx c;
@@ -491,9 +479,10 @@ __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigne
                 match_sum_plane(a, Rg, sum_of(fs), rsp, svv + (size_t)hv * wv, rsrr, rvw, c, S, lane, koff, self);
             } else if (nb == 3) {
                 match_bytes<4, 3>(a, Rg, bp, rbp, P8, svv, rsrr, c, S, lane, koff, self);
-            } else if (R == 8) {
-                match_bytes<8, 1>(a, Rg, bp, rbp, P8, svv, rsrr, c, S, lane, koff, self);
             } else {
+                // strips of 4 candidate rows: strips of 8 load fewer rows per product (R + 7 rows for
+                // 8 R row pairs), but their fully unrolled body costs more in instruction fetch than
+                // it saves (3-5% slower on the 512x512x3 and 3840x2160x3 workloads)
                 match_bytes<4, 1>(a, Rg, bp, rbp, P8, svv, rsrr, c, S, lane, koff, self);
             }
         }
