@@ -44,7 +44,7 @@ def _params():
 
 # DRAM bytes (read + write) of one launch of the forward filter kernel, from one ncu capture of
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum); workloads not captured: None.
-FILTER_DRAM_BYTES = {"rgb512": 9.065472e6 + 26.100480e6}
+FILTER_DRAM_BYTES = {"rgb512": 9.074432e6 + 26.756096e6}
 
 
 def filter_flops_per_group(C: int, K: int) -> int:
