@@ -10,7 +10,7 @@
 //    candidate's alignment (4 pixels per instruction);
 //  - the R+G+B plane of the "average" branch (values up to 765): FP32 products summed two
 //    rows at a time (each partial sum < 2^24, so exact) and converted to int32.
-// Lane layout: lane (g, q) owns the candidate columns 4q .. 4q+3 of a strip of R consecutive
+// Lane layout: lane (g, q) owns the candidate columns 4q .. 4q+3 of a strip of R = 4 consecutive
 // candidate rows; each staged image row is loaded once and used for every candidate row of the
 // strip it overlaps (reference row i = image row - candidate row).
 // Keys (SSD << 32 | y*W + x) below the warp's current threshold (the (K-1)-th smallest key

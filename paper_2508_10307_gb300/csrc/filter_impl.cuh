@@ -22,7 +22,10 @@
 //   F  warp w owns footprint rows r with r mod 8 == w: it adds row (w - y_k) mod 8 of
 //      every patch k, k ascending. No atomics, fixed order: bitwise reproducible.
 // The forward mode (filter_tile_fwd) pipelines these over the tile's groups with two group
-// buffers and three CTA barriers per group: [C(q)] | [D, E(q)] | [F(q) with A, B(q+1)].
+// buffers and two CTA barriers per group: [D, E(q) on warps 0-3 | A, B(q+1) on warps 4-7], then
+// [F(q), C(q+1)]; there each thread of A, B, D, E owns two columns or two rows of a patch. The
+// same routine serves video groups (stacked frame footprints) and the analysis / synthesis passes
+// of a threshold sweep; the sequential routine (filter_tile) serves the VJP's passes.
 // The tile's accumulator is written to a partial buffer; reduce_kernel sums the
 // overlapping tile partials in fixed tile order and divides.
 #pragma once
@@ -1264,7 +1267,9 @@ __device__ __forceinline__ void filter_tile(const FilterArgs& a, const int tile,
         uint32_t keepb = 0;
         if constexpr (MODE != FM_DENOM) {
             // ---- A, B on the filtered image
-            // A and B of patch k run on threads 8k..8k+7 of one warp: a warp barrier orders them.
+            // A and B of patch k run on threads 8k..8k+7 of one warp (one column or row per thread;
+            // the two-wide forms spill here, where the x coefficients stay live): a warp barrier
+            // orders them.
             if (tid < 8 * K) {
                 const float nrm = stage_a<K, C, Tin>(img_s, FW, pos, bas, gb, tid >> 3, tid & 7);
                 // ||G||_F^2: a warp sum first (exact in int for uint8 inputs), one shared atomic per warp
