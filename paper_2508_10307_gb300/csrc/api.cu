@@ -491,6 +491,15 @@ htsvd_status run_forward_filter(Workspace* w, const void* img, int is_float, con
     return HTSVD_OK;
 }
 
+// Owns the event that marks the estimate's inputs on the host's side of a call; destroyed on
+// every return path.
+struct HostEvent {
+    cudaEvent_t ev = nullptr;
+    ~HostEvent() {
+        if (ev) cudaEventDestroy(ev);
+    }
+};
+
 htsvd_status denoise_impl(const void* d_in, int is_float, int H, int W, int C, double sigma, const htsvd_params* p,
                           const float* d_w, float* d_out, int32_t* d_idx_out, cudaStream_t s) {
     if (!d_in || !d_out) return HTSVD_ERR_INVALID_ARG;
@@ -517,10 +526,10 @@ htsvd_status denoise_impl(const void* d_in, int is_float, int H, int W, int C, d
     }
     void* hbuf = nullptr;
     if (sigma < 0) ST(launch_sigma_inputs(w, q, g, r, s, &hbuf));
-    cudaEvent_t ev = nullptr;
+    HostEvent hev;
     if (sigma < 0) {
-        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        CK(cudaEventRecord(ev, s));
+        CK(cudaEventCreateWithFlags(&hev.ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(hev.ev, s));
     }
     // Grouping and the bases do not depend on sigma: they run while the host finishes the estimate,
     // the bases on the side stream concurrently with block matching (joined before the filter).
@@ -538,9 +547,7 @@ htsvd_status denoise_impl(const void* d_in, int is_float, int H, int W, int C, d
     if (p && p->d_basis_out)
         CK(cudaMemcpyAsync(p->d_basis_out, b64, sizeof(double) * 2 * 2 * C * PS2, cudaMemcpyDeviceToDevice, s));
     if (sigma < 0) {
-        cudaError_t e = cudaEventSynchronize(ev);
-        cudaEventDestroy(ev);
-        if (e != cudaSuccess) return HTSVD_ERR_CUDA;
+        if (cudaEventSynchronize(hev.ev) != cudaSuccess) return HTSVD_ERR_CUDA;
         ST(finish_sigma(hbuf, g, r, &sigma));
     }
     if (p && p->h_sigma_out) *p->h_sigma_out = sigma;
@@ -574,11 +581,11 @@ htsvd_status video_impl(const uint8_t* d_vid, int F, int H, int W, int C, int T,
         const uint8_t* q = d_vid + t * fr;
         double sg = sigma;
         void* hbuf = nullptr;
-        cudaEvent_t ev = nullptr;
+        HostEvent hev;
         if (sg < 0) {
             ST(launch_sigma_inputs(w, q, g, r, s, &hbuf));
-            CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-            CK(cudaEventRecord(ev, s));
+            CK(cudaEventCreateWithFlags(&hev.ev, cudaEventDisableTiming));
+            CK(cudaEventRecord(hev.ev, s));
         }
         CK(cudaEventRecord(w->ev_fork, s));
         CK(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
@@ -593,9 +600,7 @@ htsvd_status video_impl(const uint8_t* d_vid, int F, int H, int W, int C, int T,
         ST(run_block_match(q, g, r, 1, idx, s, &vc));
         CK(cudaStreamWaitEvent(s, w->ev_join, 0));
         if (sg < 0) {
-            cudaError_t e = cudaEventSynchronize(ev);
-            cudaEventDestroy(ev);
-            if (e != cudaSuccess) return HTSVD_ERR_CUDA;
+            if (cudaEventSynchronize(hev.ev) != cudaSuccess) return HTSVD_ERR_CUDA;
             ST(finish_sigma(hbuf, g, r, &sg));
         }
         if (h_sigmas) h_sigmas[t] = sg;
@@ -629,11 +634,11 @@ htsvd_status sweep_impl(const uint8_t* d_in, int H, int W, int C, double sigma, 
     ST(ws_get(w, S_CNRM, sizeof(int) * (size_t)N, &cn));
     int32_t* idx = (int32_t*)ib;
     void* hbuf = nullptr;
-    cudaEvent_t ev = nullptr;
+    HostEvent hev;
     if (sigma < 0) {
         ST(launch_sigma_inputs(w, d_in, g, r, s, &hbuf));
-        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        CK(cudaEventRecord(ev, s));
+        CK(cudaEventCreateWithFlags(&hev.ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(hev.ev, s));
     }
     ST(ws_side(w));
     CK(cudaEventRecord(w->ev_fork, s));
@@ -650,9 +655,7 @@ htsvd_status sweep_impl(const uint8_t* d_in, int H, int W, int C, double sigma, 
     CoefCache cache{(float*)cc, (float*)cp, (int*)cn, FM_ANALYZE};
     ST(run_forward_filter(w, d_in, 0, g, r, idx, b64, b32, 0.0, nullptr, nullptr, nullptr, s, nullptr, &cache));
     if (sigma < 0) {
-        cudaError_t e = cudaEventSynchronize(ev);
-        cudaEventDestroy(ev);
-        if (e != cudaSuccess) return HTSVD_ERR_CUDA;
+        if (cudaEventSynchronize(hev.ev) != cudaSuccess) return HTSVD_ERR_CUDA;
         ST(finish_sigma(hbuf, g, r, &sigma));
     }
     if (h_sigma) *h_sigma = sigma;
