@@ -17,7 +17,7 @@ definition states:
 * circulant eigen-analysis and sigma adjustment         -- Sec. III-D, Eqs. (other eigenvalue), (adjust noise level)
 * eigenvalue noise-level estimate (patch-covariance rule, used in place of the paper's CNN)
 
-Readings where the paper is silent or ambiguous (each is listed in the design doc):
+Readings where the paper is silent or ambiguous:
   R1 distance = exact integer SSD on the chosen plane; the "avg" branch uses the
      R+G+B sum plane (SSD = 9x the SSD of the average, same order).
   R2 the GCP test is evaluated on the reference patch with raw L2 norms, in
