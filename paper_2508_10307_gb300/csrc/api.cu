@@ -667,6 +667,68 @@ htsvd_status sweep_impl(const uint8_t* d_in, int H, int W, int C, double sigma, 
     return HTSVD_OK;
 }
 
+// The VJP's device passes with grouping and bases given (FP64 b64 and packed FP32 b32): the
+// denominator D, r = gout / D, and the adjoint filter on r with the masks of x at tau.
+htsvd_status vjp_core(Workspace* w, const float* d_x, const Geo& g, const Resolved& r, const int32_t* d_idx,
+                      const float* d_w, const double* b64, const float* b32, double tau, const float* d_out,
+                      const float* d_grad_out, float* d_grad_x, float* d_grad_w, cudaStream_t s) {
+    const int C = g.C;
+    const int64_t npix = (int64_t)g.H * g.W;
+    void *den, *rimg, *tmp;
+    ST(ws_get(w, S_DEN, sizeof(float) * npix, &den));
+    ST(ws_get(w, S_R, sizeof(float) * npix * C, &rimg));
+    ST(ws_get(w, S_TMP, sizeof(float) * npix * C, &tmp));
+
+    // D = sum_g w_g Scatter_g 1
+    FilterTiling td = choose_filter_tiling(g, 4, FM_DENOM, r.tile);
+    if (td.TR == 0) return HTSVD_ERR_UNSUPPORTED;
+    FilterArgs a{};
+    a.img = d_x;
+    a.img_is_float = 1;
+    a.g = g;
+    a.idx = d_idx;
+    a.basis32 = b32;
+    a.basis64 = b64;
+    a.tau64 = tau;
+    a.tau32 = (float)tau;
+    a.band_rel = kBandRel;
+    a.band_abs = (float)(tau * kBandTau) + 1e-6f;
+    a.w_in = d_w;
+    a.agg_mode = 0;
+    a.mode = FM_DENOM;
+    a.TR = td.TR;
+    a.ntx = td.ntx;
+    a.nty = td.nty;
+    a.FHmax = td.FHmax;
+    a.FWmax = td.FWmax;
+    const int acc = C == 3 ? 4 : 2;
+    void* part;
+    ST(ws_get(w, S_PART, sizeof(float) * (size_t)td.ntx * td.nty * td.FHmax * td.FWmax * acc, &part));
+    a.partials = (float*)part;
+    { ProfScope ps_("filter", s); CK(launch_filter(a, s)); }
+    { ProfScope ps_("reduce", s); CK(launch_reduce((float*)part, g, td.TR, td.ntx, td.nty, td.FHmax, td.FWmax, (float*)tmp, (float*)den, 0,
+                     nullptr, s)); }
+    { ProfScope ps_("div", s); CK(launch_div(d_grad_out, (const float*)den, npix, C, (float*)rimg, s)); }
+
+    // adjoint filter on r = gout / D with the masks of x
+    FilterTiling ta = choose_filter_tiling(g, 4, FM_ADJOINT, r.tile);
+    if (ta.TR == 0) return HTSVD_ERR_UNSUPPORTED;
+    a.mode = FM_ADJOINT;
+    a.TR = ta.TR;
+    a.ntx = ta.ntx;
+    a.nty = ta.nty;
+    a.FHmax = ta.FHmax;
+    a.FWmax = ta.FWmax;
+    a.r_img = (const float*)rimg;
+    a.out_img = d_out;
+    a.grad_w = d_grad_w;
+    ST(ws_get(w, S_PART, sizeof(float) * (size_t)ta.ntx * ta.nty * ta.FHmax * ta.FWmax * acc, &part));
+    a.partials = (float*)part;
+    { ProfScope ps_("filter", s); CK(launch_filter(a, s)); }
+    { ProfScope ps_("reduce", s); CK(launch_reduce((float*)part, g, ta.TR, ta.ntx, ta.nty, ta.FHmax, ta.FWmax, d_grad_x, nullptr, 1, nullptr, s)); }
+    return HTSVD_OK;
+}
+
 }  // namespace
 
 // ============================================================================= C ABI
@@ -841,65 +903,14 @@ htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C
     if (!w) return HTSVD_ERR_OOM;
     const Geo g = make_geo(H, W, C, r.s, r.win, r.K);
     const int64_t npix = (int64_t)H * W;
-    void *qb, *den, *rimg, *tmp;
+    void* qb;
     ST(ws_get(w, S_Q, (size_t)npix * C, &qb));
-    ST(ws_get(w, S_DEN, sizeof(float) * npix, &den));
-    ST(ws_get(w, S_R, sizeof(float) * npix * C, &rimg));
-    ST(ws_get(w, S_TMP, sizeof(float) * npix * C, &tmp));
     { ProfScope ps_("quantize", s); CK(launch_quantize(d_x, npix * C, (uint8_t*)qb, s)); }
     double* b64;
     float* b32;
     ST(run_basis(w, (const uint8_t*)qb, g, &b64, &b32, s));
-    const double tau = r.tau_mult * sigma;
-
-    // D = sum_g w_g Scatter_g 1
-    FilterTiling td = choose_filter_tiling(g, 4, FM_DENOM, r.tile);
-    if (td.TR == 0) return HTSVD_ERR_UNSUPPORTED;
-    FilterArgs a{};
-    a.img = d_x;
-    a.img_is_float = 1;
-    a.g = g;
-    a.idx = d_idx;
-    a.basis32 = b32;
-    a.basis64 = b64;
-    a.tau64 = tau;
-    a.tau32 = (float)tau;
-    a.band_rel = kBandRel;
-    a.band_abs = (float)(tau * kBandTau) + 1e-6f;
-    a.w_in = d_w;
-    a.agg_mode = 0;
-    a.mode = FM_DENOM;
-    a.TR = td.TR;
-    a.ntx = td.ntx;
-    a.nty = td.nty;
-    a.FHmax = td.FHmax;
-    a.FWmax = td.FWmax;
-    const int acc = C == 3 ? 4 : 2;
-    void* part;
-    ST(ws_get(w, S_PART, sizeof(float) * (size_t)td.ntx * td.nty * td.FHmax * td.FWmax * acc, &part));
-    a.partials = (float*)part;
-    { ProfScope ps_("filter", s); CK(launch_filter(a, s)); }
-    { ProfScope ps_("reduce", s); CK(launch_reduce((float*)part, g, td.TR, td.ntx, td.nty, td.FHmax, td.FWmax, (float*)tmp, (float*)den, 0,
-                     nullptr, s)); }
-    { ProfScope ps_("div", s); CK(launch_div(d_grad_out, (const float*)den, npix, C, (float*)rimg, s)); }
-
-    // adjoint filter on r = gout / D with the masks of x
-    FilterTiling ta = choose_filter_tiling(g, 4, FM_ADJOINT, r.tile);
-    if (ta.TR == 0) return HTSVD_ERR_UNSUPPORTED;
-    a.mode = FM_ADJOINT;
-    a.TR = ta.TR;
-    a.ntx = ta.ntx;
-    a.nty = ta.nty;
-    a.FHmax = ta.FHmax;
-    a.FWmax = ta.FWmax;
-    a.r_img = (const float*)rimg;
-    a.out_img = d_out;
-    a.grad_w = d_grad_w;
-    ST(ws_get(w, S_PART, sizeof(float) * (size_t)ta.ntx * ta.nty * ta.FHmax * ta.FWmax * acc, &part));
-    a.partials = (float*)part;
-    { ProfScope ps_("filter", s); CK(launch_filter(a, s)); }
-    { ProfScope ps_("reduce", s); CK(launch_reduce((float*)part, g, ta.TR, ta.ntx, ta.nty, ta.FHmax, ta.FWmax, d_grad_x, nullptr, 1, nullptr, s)); }
-    return HTSVD_OK;
+    return vjp_core(w, d_x, g, r, d_idx, d_w, b64, b32, r.tau_mult * sigma, d_out, d_grad_out, d_grad_x, d_grad_w,
+                    s);
 }
 
 htsvd_status htsvd_sure(const float* d_y, int32_t H, int32_t W, int32_t C, double sigma, const double* h_tau_mults,
@@ -931,12 +942,24 @@ htsvd_status htsvd_sure(const float* d_y, int32_t H, int32_t W, int32_t C, doubl
     pm.d_weights_out = nullptr;
     pm.d_basis_out = nullptr;
     pm.d_coef_out = nullptr;
+    // grouping and bases of the rounded image, shared by every multiplier
+    void* qb;
+    ST(ws_get(w, S_Q, (size_t)n, &qb));
+    { ProfScope ps_("quantize", s); CK(launch_quantize(d_y, n, (uint8_t*)qb, s)); }
+    double* b64;
+    float* b32;
+    ST(run_basis(w, (const uint8_t*)qb, g, &b64, &b32, s));
+    ST(run_block_match((const uint8_t*)qb, g, r, 1, (int32_t*)idx, s));
     for (int i = 0; i < n_tau; ++i) {
         pm.tau_mult = h_tau_mults[i];
+        Resolved ri;
+        ST(resolve(&pm, C, ri));
+        const double tau = ri.tau_mult * sigma;
         // f = Alg. 1 at tau = m sigma, then J^T b through the frozen-mask adjoint, then the two sums
-        ST(denoise_impl(d_y, 1, H, W, C, sigma, &pm, nullptr, (float*)out, (int32_t*)idx, s));
-        ST(htsvd_denoise_vjp(d_y, H, W, C, sigma, &pm, (const int32_t*)idx, nullptr, (const float*)out, d_probe,
-                             (float*)gx, nullptr, s));
+        ST(run_forward_filter(w, d_y, 1, g, ri, (const int32_t*)idx, b64, b32, tau, nullptr, nullptr, (float*)out,
+                              s));
+        ST(vjp_core(w, d_y, g, ri, (const int32_t*)idx, nullptr, b64, b32, tau, (const float*)out, d_probe,
+                    (float*)gx, nullptr, s));
         { ProfScope ps_("sure_terms", s); CK(launch_sure_terms((const float*)out, d_y, d_probe, (const float*)gx, n,
                                                                scratch, terms + 2 * i, s)); }
     }
