@@ -38,7 +38,7 @@ typedef enum htsvd_status {
     HTSVD_ERR_UNSUPPORTED = 2,   /* valid for the method, not built here (ps != 8, K > 32, window > 64) */
     HTSVD_ERR_CUDA = 3,          /* a CUDA runtime call failed */
     HTSVD_ERR_OOM = 4,           /* workspace allocation failed */
-    HTSVD_ERR_TIMEOUT = 5,       /* reserved for bounded device waits; no kernel of this build waits on another CTA */
+    HTSVD_ERR_TIMEOUT = 5,       /* reserved for bounded device waits; no kernel of this library waits on another CTA */
 } htsvd_status;
 
 typedef enum htsvd_match_mode {
@@ -70,7 +70,7 @@ typedef struct htsvd_params {
     double  beta;          /* <= 0 -> 1.2 (Sec. III-D) */
     int32_t rank_gamma;    /* <= 0 -> round(13 K / 32) (Sec. III-D) */
     int32_t tile;          /* reference tile edge for the filter (0 -> automatic) */
-    int64_t max_wait_cycles; /* reserved (bounded device waits); ignored by this build */
+    int64_t max_wait_cycles; /* reserved (bounded device waits); ignored: no kernel of this library waits on another CTA */
     /* Optional outputs (may be NULL). */
     double*   h_sigma_out;   /* HOST: the sigma actually used (estimated when sigma < 0) */
     uint32_t* d_mask_out;    /* DEVICE: threshold masks, per group ceil(K*ps*ps*C/32) words, bit index
