@@ -59,9 +59,14 @@ Readings where the paper is silent or ambiguous:
   R17 threshold selection by Stein's unbiased risk estimate (the paper only notes that tuning is
      sped up by caching indices and coefficients, Sec. III-E): for each multiplier m,
      f = Alg. 1 at tau = m sigma on a float image y (R13), n = H W C,
-     SURE(m) = ||f - y||^2 / n - sigma^2 + (2 sigma^2 / n) b^T J^T b, with J the Jacobian of the
-     frozen-mask map at y (R14; the hard threshold's jump terms are not counted) and b a caller-given
-     probe (a Rademacher vector makes b^T J b an unbiased estimate of trace J).
+     SURE(m) = ||f - y||^2 / n - sigma^2 + (2 sigma^2 / n) div, b a caller-given probe (a Rademacher
+     vector makes b^T J b an unbiased estimate of trace J). With a step eps > 0 the divergence is the
+     Monte-Carlo finite difference of the whole denoiser (Ramani, Blu and Unser, 2008),
+     div = b^T (f(z) - f(y)) / eps with z = y + eps b rounded to float32 as the device forms it
+     (round(eps), then round(eps b), then round(y + eps b)); f(z) regroups and re-solves the bases,
+     so the threshold's jumps and the bases' dependence on y are counted. With eps = 0 it is
+     b^T J^T b, J the Jacobian of the frozen-mask map at y (R14), which counts neither: hard
+     thresholding makes that form biased low (the jump terms grow as tau falls).
 
 Parity pins for every function are in tests/test_oracle_pins.py.
 """
@@ -759,9 +764,10 @@ def denoise_video(video: np.ndarray, sigma=None, params=None, T: int = 1, *, kee
 
 # --------------------------------------------------------------------------- threshold selection (reading R17)
 
-def sure(x: np.ndarray, sigma: float, tau_mults, probe: np.ndarray, params=None) -> np.ndarray:
-    """Reading R17: SURE(m) for every multiplier m, the divergence through the frozen-mask adjoint
-    applied to the probe. x: float (H, W, C) image on the [0, 255] scale; probe: same shape."""
+def sure(x: np.ndarray, sigma: float, tau_mults, probe: np.ndarray, params=None, eps: float = 0.0) -> np.ndarray:
+    """Reading R17: SURE(m) for every multiplier m. x: float (H, W, C) image on the [0, 255] scale
+    (float32 values); probe: same shape. eps > 0: the divergence is the finite difference of the
+    whole denoiser along the probe; eps = 0: the frozen-mask adjoint applied to the probe."""
     p = Params.of(params)
     if x.ndim == 2:
         x = x[:, :, None]
@@ -770,11 +776,19 @@ def sure(x: np.ndarray, sigma: float, tau_mults, probe: np.ndarray, params=None)
     xf = x.astype(np.float64)
     b = probe.astype(np.float64)
     n = xf.size
+    z = None
+    if eps > 0:
+        # the perturbed image in float32, each operation rounded once
+        z = (x.astype(np.float32) + np.float32(eps) * probe.astype(np.float32)).astype(np.float64)
     res = []
     for m in tau_mults:
         pm = Params.of(dict(p.__dict__, tau_mult=float(m)))
-        r = denoise(xf, sigma, pm, keep_masks=True)
-        gx, _ = denoise_fixed_vjp(xf, b, r.idx, r.masks, r.U, r.V, r.weights, pm.ps)
-        res.append(((r.out - xf) ** 2).sum() / n - sigma ** 2 + 2.0 * sigma ** 2 / n * float((b * gx).sum()))
+        r = denoise(xf, sigma, pm, keep_masks=eps == 0)
+        if eps > 0:
+            div = float((b * (denoise(z, sigma, pm).out - r.out)).sum()) / eps
+        else:
+            gx, _ = denoise_fixed_vjp(xf, b, r.idx, r.masks, r.U, r.V, r.weights, pm.ps)
+            div = float((b * gx).sum())
+        res.append(((r.out - xf) ** 2).sum() / n - sigma ** 2 + 2.0 * sigma ** 2 / n * div)
     return np.array(res)
 

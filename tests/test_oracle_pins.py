@@ -551,6 +551,29 @@ def test_sure_closed_forms_at_zero_and_infinite_threshold():
     s0, sbig = O.sure(y, 20.0, [1e-12, 1e6], b, prm)
     assert s0 == pytest.approx(20.0 ** 2, rel=1e-9)
     assert sbig == pytest.approx((y.astype(np.float64) ** 2).mean() - 20.0 ** 2, rel=1e-12)
+    # finite-difference form: f(z) = z at tau = 0, so the divergence is b^T (z - y) / eps = n up to
+    # the float32 rounding of z (|z - y - eps b| <= 2^-24 |z| per entry)
+    s0, sbig = O.sure(y, 20.0, [1e-12, 1e6], b, prm, eps=2.0)
+    assert s0 == pytest.approx(20.0 ** 2, rel=1e-5)
+    assert sbig == pytest.approx((y.astype(np.float64) ** 2).mean() - 20.0 ** 2, rel=1e-12)
+
+
+def test_sure_finite_difference_tracks_the_true_risk():
+    """Stein's lemma: on Gaussian noise the expectation of SURE is the mean squared error against the
+    clean image. The finite-difference form counts the threshold's jumps and the bases' dependence
+    on y and lands within 15% of the error; the frozen-mask form counts neither and falls below it."""
+    x = synth.clean_image(64, 64, 3, 101).astype(np.float64)
+    y = synth.add_gaussian_float(synth.clean_image(64, 64, 3, 101), 20.0, 102)
+    b = _probe(y.shape, 103)
+    prm = dict(ps=8, stride=3, window=9, K=16)
+    ms = [1.5, 2.7]
+    fd = O.sure(y, 20.0, ms, b, prm, eps=2.0)
+    frozen = O.sure(y, 20.0, ms, b, prm)
+    for m, a, c in zip(ms, fd, frozen):
+        mse = ((O.denoise(y.astype(np.float64), 20.0, O.Params.of(dict(prm, tau_mult=m))).out - x) ** 2).mean()
+        assert a == pytest.approx(mse, rel=0.15)
+        assert c < mse
+    assert fd[1] < fd[0]     # the larger threshold is the better one here, and SURE says so
 
 
 def test_sure_divergence_is_the_trace_of_the_frozen_map():
