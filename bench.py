@@ -343,7 +343,8 @@ def make_workload(name):
         mults = [1.8, 2.4, 3.0, 3.6]
         cfg = {"workload": "sure_rgb512_f32_x4", "image": "512x512x3 float32", "noise": "gaussian sigma=25",
                "sigma": "given (25)", "tau_mults": mults, "ps": 8, "stride": 2, "window": 31, "K": 32,
-               "form": "per multiplier: forward, frozen-mask VJP of a +-1 probe, FP64 sums (MP count: 4 images)"}
+               "form": "finite-difference divergence along a +-1 probe, eps = sigma/10: grouping and bases of y and of "
+                       "y + eps probe once each, two forward passes per multiplier, FP64 sums (MP count: 4 images)"}
         n = H.num_groups(512, 512, prm)
         pb = [None]
 

@@ -140,16 +140,21 @@ htsvd_status htsvd_denoise_tau_sweep(const uint8_t* d_noisy, int32_t H, int32_t 
 
 /* Threshold selection by Stein's unbiased risk estimate (tuning, Sec. III-E). For each multiplier
  * m = h_tau_mults[i] > 0: f = htsvd_denoise_f32 at tau = m * sigma on d_y (H x W x C float32 on the
- * [0, 255] scale, DEVICE), n = H W C, and
- *   h_sure[i] = ||f - y||^2 / n - sigma^2 + (2 sigma^2 / n) b^T J^T b,
- * with J^T b the vector-Jacobian product of htsvd_denoise_vjp (grouping, bases, tau and masks held
- * fixed; the hard threshold's jump terms are not counted) and b = d_probe (H x W x C float32,
- * DEVICE; a +-1 Rademacher vector makes b^T J b an unbiased estimate of trace J). Sums in FP64.
- * sigma > 0 is required. h_sure: n_tau doubles (HOST). Synchronises `stream`. Errors: INVALID_ARG
- * for a null pointer, n_tau < 1, sigma or a multiplier not positive and finite, or an image that
- * fails the checks of htsvd_denoise; optional outputs of p are ignored. */
+ * [0, 255] scale, DEVICE), n = H W C, b = d_probe (H x W x C float32, DEVICE; a +-1 Rademacher
+ * vector makes the divergence below an unbiased estimate of trace J), and
+ *   h_sure[i] = ||f - y||^2 / n - sigma^2 + (2 sigma^2 / n) div.
+ * eps > 0: div = b^T (f(z) - f(y)) / eps, the Monte-Carlo finite difference of the whole denoiser
+ * (Ramani, Blu and Unser, 2008) with z = y + eps b formed in float32, each operation rounded once;
+ * f(z) groups and solves the bases of z, so the hard threshold's jumps and the bases' dependence
+ * on y are counted (eps about sigma / 10 suits the [0, 255] scale). eps = 0: div = b^T J^T b with
+ * J^T b the vector-Jacobian product of htsvd_denoise_vjp (grouping, bases, tau and masks held
+ * fixed), which counts neither and so falls below the true risk. Sums in FP64. sigma > 0 is
+ * required. h_sure: n_tau doubles (HOST). Synchronises `stream`. Errors: INVALID_ARG for a null
+ * pointer, n_tau < 1, sigma or a multiplier not positive and finite, eps negative, not finite or
+ * vanishing in float32, or an image that fails the checks of htsvd_denoise; optional outputs of p
+ * are ignored. */
 htsvd_status htsvd_sure(const float* d_y, int32_t H, int32_t W, int32_t C, double sigma, const double* h_tau_mults,
-                        int32_t n_tau, const float* d_probe, const htsvd_params* p, double* h_sure,
+                        int32_t n_tau, const float* d_probe, double eps, const htsvd_params* p, double* h_sure,
                         cudaStream_t stream);
 
 /* Noise level from the eigenvalues of the covariance of the reference patches:

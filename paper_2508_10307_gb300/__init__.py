@@ -261,10 +261,12 @@ def denoise_tau_sweep(noisy, tau_mults, sigma=None, params=None, *, return_sigma
     return (outs, sig.value) if return_sigma else outs
 
 
-def sure(y, sigma, tau_mults, probe, params=None, stream=None):
-    """SURE of each threshold multiplier on a float32 (H, W[, C]) CUDA image y, with the divergence
-    through the frozen-mask VJP applied to probe (same shape; e.g. a +-1 Rademacher vector).
-    Returns a list of floats; synchronises the stream."""
+def sure(y, sigma, tau_mults, probe, params=None, eps=None, stream=None):
+    """SURE of each threshold multiplier on a float32 (H, W[, C]) CUDA image y along probe (same
+    shape; e.g. a +-1 Rademacher vector). eps > 0 (default sigma / 10): the divergence is the finite
+    difference of the whole denoiser at y + eps * probe; eps = 0: the frozen-mask VJP applied to
+    probe (biased low: it omits the threshold's jumps). Returns a list of floats; synchronises the
+    stream."""
     lib = _lib.load()
     torch = _torch()
     x = _hwc(y)
@@ -275,8 +277,9 @@ def sure(y, sigma, tau_mults, probe, params=None, stream=None):
     m = [float(t) for t in tau_mults]
     res = (ctypes.c_double * len(m))()
     cp = HtsvdParams.of(params).c()
+    e = 0.1 * float(sigma) if eps is None else float(eps)
     _lib.check(lib.htsvd_sure(_ptr(x.contiguous()), H, W, C, float(sigma), (ctypes.c_double * len(m))(*m), len(m),
-                              _ptr(b), ctypes.byref(cp), res, _stream_ptr(stream)), "htsvd_sure")
+                              _ptr(b), e, ctypes.byref(cp), res, _stream_ptr(stream)), "htsvd_sure")
     return [float(v) for v in res]
 
 

@@ -78,7 +78,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                         vp]
     lib.htsvd_denoise_tau_sweep.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(ctypes.c_double), i32, P, vp,
                                             ctypes.POINTER(ctypes.c_double), vp]
-    lib.htsvd_sure.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(ctypes.c_double), i32, vp, P,
+    lib.htsvd_sure.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(ctypes.c_double), i32, vp, dbl, P,
                                ctypes.POINTER(ctypes.c_double), vp]
     lib.htsvd_num_groups.argtypes = [i32, i32, P]
     lib.htsvd_num_groups.restype = ctypes.c_int64

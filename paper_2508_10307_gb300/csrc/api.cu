@@ -77,7 +77,7 @@ enum Slot {
     S_IDX, S_MOM, S_B64, S_B32, S_PART, S_FULLM, S_FULLS, S_RANKS, S_IDX2, S_Q, S_DEN, S_R, S_TMP,
     S_AIN, S_AOUT,                   // S_AIN, S_AOUT: subimages of htsvd_denoise_adaptive
     S_COEF, S_CPN, S_CNRM,           // coefficient cache of htsvd_denoise_tau_sweep
-    S_SOUT, S_SGX, S_SIDX, S_SRED,   // htsvd_sure: estimate, adjoint, grouping, reduction terms
+    S_SOUT, S_SGX, S_SIDX, S_SRED,   // htsvd_sure: estimate, adjoint or perturbed image, grouping, sums
     S_NSLOT
 };
 
@@ -914,10 +914,11 @@ htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C
 }
 
 htsvd_status htsvd_sure(const float* d_y, int32_t H, int32_t W, int32_t C, double sigma, const double* h_tau_mults,
-                        int32_t n_tau, const float* d_probe, const htsvd_params* p, double* h_sure,
+                        int32_t n_tau, const float* d_probe, double eps, const htsvd_params* p, double* h_sure,
                         cudaStream_t s) {
     if (!d_y || !d_probe || !h_tau_mults || !h_sure || n_tau < 1) return HTSVD_ERR_INVALID_ARG;
     if (!(sigma > 0) || std::isinf(sigma)) return HTSVD_ERR_INVALID_ARG;
+    if (!(eps >= 0.0) || (eps > 0.0 && !(std::isfinite((float)eps) && (float)eps > 0.0f))) return HTSVD_ERR_INVALID_ARG;
     for (int i = 0; i < n_tau; ++i)
         if (!(h_tau_mults[i] > 0.0) || std::isinf(h_tau_mults[i])) return HTSVD_ERR_INVALID_ARG;
     Resolved r;
@@ -927,13 +928,14 @@ htsvd_status htsvd_sure(const float* d_y, int32_t H, int32_t W, int32_t C, doubl
     if (!w) return HTSVD_ERR_OOM;
     const int64_t n = (int64_t)H * W * C;
     const Geo g = make_geo(H, W, C, r.s, r.win, r.K);
+    const bool fd = eps > 0.0;
     void *out, *gx, *idx, *red;
     ST(ws_get(w, S_SOUT, sizeof(float) * n, &out));
-    ST(ws_get(w, S_SGX, sizeof(float) * n, &gx));
+    ST(ws_get(w, S_SGX, sizeof(float) * n, &gx));     // J^T b (eps = 0) or the perturbed image z (eps > 0)
     ST(ws_get(w, S_SIDX, sizeof(int32_t) * g.ngroups() * r.K, &idx));
-    ST(ws_get(w, S_SRED, sizeof(double) * (sure_scratch_doubles() + 2 * (size_t)n_tau), &red));
+    ST(ws_get(w, S_SRED, sizeof(double) * (sure_scratch_doubles() + 4 * (size_t)n_tau), &red));
     double* scratch = (double*)red;
-    double* terms = scratch + sure_scratch_doubles();
+    double* terms = scratch + sure_scratch_doubles();   // per multiplier: |f - y|^2, b.g, then b.f(z) (fd)
     htsvd_params pm;
     if (p) pm = *p;
     else std::memset(&pm, 0, sizeof(pm));
@@ -942,32 +944,52 @@ htsvd_status htsvd_sure(const float* d_y, int32_t H, int32_t W, int32_t C, doubl
     pm.d_weights_out = nullptr;
     pm.d_basis_out = nullptr;
     pm.d_coef_out = nullptr;
-    // grouping and bases of the rounded image, shared by every multiplier
-    void* qb;
-    ST(ws_get(w, S_Q, (size_t)n, &qb));
-    { ProfScope ps_("quantize", s); CK(launch_quantize(d_y, n, (uint8_t*)qb, s)); }
-    double* b64;
-    float* b32;
-    ST(run_basis(w, (const uint8_t*)qb, g, &b64, &b32, s));
-    ST(run_block_match((const uint8_t*)qb, g, r, 1, (int32_t*)idx, s));
+    std::vector<Resolved> rs((size_t)n_tau);
     for (int i = 0; i < n_tau; ++i) {
         pm.tau_mult = h_tau_mults[i];
-        Resolved ri;
-        ST(resolve(&pm, C, ri));
-        const double tau = ri.tau_mult * sigma;
-        // f = Alg. 1 at tau = m sigma, then J^T b through the frozen-mask adjoint, then the two sums
-        ST(run_forward_filter(w, d_y, 1, g, ri, (const int32_t*)idx, b64, b32, tau, nullptr, nullptr, (float*)out,
-                              s));
-        ST(vjp_core(w, d_y, g, ri, (const int32_t*)idx, nullptr, b64, b32, tau, (const float*)out, d_probe,
-                    (float*)gx, nullptr, s));
-        { ProfScope ps_("sure_terms", s); CK(launch_sure_terms((const float*)out, d_y, d_probe, (const float*)gx, n,
-                                                               scratch, terms + 2 * i, s)); }
+        ST(resolve(&pm, C, rs[i]));
     }
-    std::vector<double> h(2 * (size_t)n_tau);
-    CK(cudaMemcpyAsync(h.data(), terms, sizeof(double) * 2 * n_tau, cudaMemcpyDeviceToHost, s));
+    void* qb;
+    ST(ws_get(w, S_Q, (size_t)n, &qb));
+    // Pass 0 denoises y at every multiplier; with eps > 0 pass 1 denoises z = y + eps b. Each pass
+    // groups and solves the bases of its own rounded image once, shared by every multiplier.
+    const int passes = fd ? 2 : 1;
+    for (int pass = 0; pass < passes; ++pass) {
+        const float* img = d_y;
+        if (pass == 1) {
+            ProfScope ps_("perturb", s);
+            CK(launch_perturb(d_y, d_probe, (float)eps, n, (float*)gx, s));
+            img = (const float*)gx;
+        }
+        { ProfScope ps_("quantize", s); CK(launch_quantize(img, n, (uint8_t*)qb, s)); }
+        double* b64;
+        float* b32;
+        ST(run_basis(w, (const uint8_t*)qb, g, &b64, &b32, s));
+        ST(run_block_match((const uint8_t*)qb, g, r, 1, (int32_t*)idx, s));
+        for (int i = 0; i < n_tau; ++i) {
+            const Resolved& ri = rs[i];
+            const double tau = ri.tau_mult * sigma;
+            ST(run_forward_filter(w, img, 1, g, ri, (const int32_t*)idx, b64, b32, tau, nullptr, nullptr,
+                                  (float*)out, s));
+            const float* gv = (const float*)out;        // fd: b.f(y) in pass 0, b.f(z) in pass 1
+            if (!fd) {
+                // J^T b through the frozen-mask adjoint
+                ST(vjp_core(w, d_y, g, ri, (const int32_t*)idx, nullptr, b64, b32, tau, (const float*)out, d_probe,
+                            (float*)gx, nullptr, s));
+                gv = (const float*)gx;
+            }
+            ProfScope ps_("sure_terms", s);
+            CK(launch_sure_terms((const float*)out, img, d_probe, gv, n, scratch, terms + 4 * i + 2 * pass, s));
+        }
+    }
+    std::vector<double> h(4 * (size_t)n_tau);
+    CK(cudaMemcpyAsync(h.data(), terms, sizeof(double) * 4 * n_tau, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    for (int i = 0; i < n_tau; ++i)
-        h_sure[i] = h[2 * i] / (double)n - sigma * sigma + 2.0 * sigma * sigma / (double)n * h[2 * i + 1];
+    for (int i = 0; i < n_tau; ++i) {
+        const double* t = &h[4 * (size_t)i];
+        const double div = fd ? (t[3] - t[1]) / eps : t[1];
+        h_sure[i] = t[0] / (double)n - sigma * sigma + 2.0 * sigma * sigma / (double)n * div;
+    }
     return HTSVD_OK;
 }
 

@@ -191,9 +191,25 @@ __global__ void sure_sum_kernel(const double* __restrict__ part, int nb, double*
     }
 }
 
+// z = y + eps b in float32 with each operation rounded once (no contraction into an FMA), so the
+// perturbed image is the one a host forms with IEEE single arithmetic.
+__global__ void perturb_kernel(const float* __restrict__ y, const float* __restrict__ b, float eps, int64_t n,
+                               float* __restrict__ z) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = __fadd_rn(y[i], __fmul_rn(eps, b[i]));
+}
+
 }  // namespace
 
 size_t sure_scratch_doubles() { return 2 * (size_t)SURE_BLOCKS; }
+
+cudaError_t launch_perturb(const float* y, const float* b, float eps, int64_t n, float* z, cudaStream_t s) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    perturb_kernel<<<(int)blocks, 256, 0, s>>>(y, b, eps, n, z);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sure_terms(const float* out, const float* x, const float* b, const float* g, int64_t n,
                               double* scratch, double* res, cudaStream_t s) {

@@ -102,6 +102,8 @@ cudaError_t launch_filter(const FilterArgs& a, cudaStream_t s);
 // denominator plane is written too; if num_only, out = sum num (no division).
 cudaError_t launch_reduce(const float* partials, const Geo& g, int TR, int ntx, int nty, int FHmax, int FWmax,
                           float* out, float* den_out, int num_only, const float* den_in, cudaStream_t s);
+// z = y + eps b over n floats, each operation rounded once (the finite-difference SURE's perturbed image).
+cudaError_t launch_perturb(const float* y, const float* b, float eps, int64_t n, float* z, cudaStream_t s);
 // SURE terms in FP64: res[0] = sum (out - x)^2, res[1] = sum b * g over n floats (deterministic
 // two-level reduction; scratch: sure_scratch_doubles() doubles).
 size_t sure_scratch_doubles();

@@ -126,9 +126,12 @@ def test_sure_rejects_bad_arguments_on_the_host():
     res = (ctypes.c_double * 2)()
     ok = (ctypes.c_double * 2)(1.0, 2.0)
     zero = (ctypes.c_double * 2)(1.0, 0.0)
-    call = lambda sigma, m, n, probe=dp: lib.htsvd_sure(dp, 64, 64, 3, sigma, m, n, probe, ctypes.byref(cp), res,
-                                                         None)
+    call = lambda sigma, m, n, probe=dp, eps=1.0: lib.htsvd_sure(dp, 64, 64, 3, sigma, m, n, probe, eps,
+                                                                  ctypes.byref(cp), res, None)
     assert call(10.0, ok, 0) == 1              # no thresholds
+    assert call(10.0, ok, 2, eps=-1.0) == 1    # negative step
+    assert call(10.0, ok, 2, eps=1e300) == 1   # step not finite in float32
+    assert call(10.0, ok, 2, eps=1e-60) == 1   # step vanishing in float32
     assert call(0.0, ok, 2) == 1               # sigma must be positive
     assert call(10.0, zero, 2) == 1            # multipliers must be positive
     assert call(10.0, ok, 2, None) == 1        # no probe
