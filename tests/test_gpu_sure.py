@@ -39,7 +39,9 @@ def test_sure_of_a_vanishing_threshold_is_sigma_squared(eps):
 def test_finite_difference_sure_tracks_the_error_against_the_clean_image():
     """Stein's lemma at a size the oracle does not reach quickly: on Gaussian noise the
     finite-difference SURE of the device path stays close to the device path's own mean squared
-    error against the clean image, and both pick the same threshold."""
+    error against the clean image, and both pick the same threshold. SURE is itself an estimate:
+    the realisation's noise energy ||y - x||^2 / n - sigma^2 enters every value alike (standard
+    deviation sigma^2 sqrt(2 / n), 2.0 here), so the bound is 5% plus three of those."""
     clean = synth.clean_image(256, 256, 3, 821)
     y = synth.add_gaussian_float(clean, 25.0, 822).astype(np.float32)
     b = np.random.default_rng(823).choice([-1.0, 1.0], size=y.shape).astype(np.float32)
@@ -49,5 +51,5 @@ def test_finite_difference_sure_tracks_the_error_against_the_clean_image():
     got = np.array(H.sure(dy, 25.0, mults, torch.from_numpy(b).cuda(), prm, eps=2.5))
     x = torch.from_numpy(clean.astype(np.float32)).cuda()
     mse = np.array([float(((H.denoise_f32(dy, 25.0, dict(prm, tau_mult=m)) - x) ** 2).mean()) for m in mults])
-    np.testing.assert_allclose(got, mse, rtol=0.08)
+    np.testing.assert_allclose(got, mse, rtol=0.05, atol=3 * 25.0 ** 2 * np.sqrt(2 / y.size))
     assert int(np.argmin(got)) == int(np.argmin(mse))
