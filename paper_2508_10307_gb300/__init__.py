@@ -84,6 +84,20 @@ def _hwc(x):
     return x
 
 
+def _need(t, name, shape, dtype, like=None):
+    """Checks a buffer the library reads or writes through a bare pointer: its shape (it sets how far
+    the kernels index), dtype, contiguity and device. Returns t."""
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if not t.is_cuda or (like is not None and t.device != like.device):
+        raise ValueError(f"{name}: expected a CUDA tensor on {like.device if like is not None else 'the GPU'}")
+    return t
+
+
 def num_groups(H: int, W: int, params=None) -> int:
     lib = _lib.load()
     cp = HtsvdParams.of(params).c()
@@ -149,7 +163,7 @@ def denoise_f32(x, sigma=None, params=None, *, w=None, return_info=False, masks=
     cp.h_sigma_out = ctypes.pointer(sig_out)
     out, idx, info = _outputs(x, p, cp, True, masks, weights, basis)
     H, W, C = x.shape
-    wt = None if w is None else w.contiguous().float()
+    wt = None if w is None else _need(w.contiguous().float(), "w", (idx.shape[0],), torch.float32, x)
     st = lib.htsvd_denoise_f32(_ptr(x), H, W, C, -1.0 if sigma is None else float(sigma), ctypes.byref(cp),
                                _ptr(wt), _ptr(out), _ptr(idx), _stream_ptr(stream))
     _lib.check(st, "htsvd_denoise_f32")
@@ -164,6 +178,8 @@ def estimate_sigma(noisy, params=None, stream=None) -> float:
     the eigen-rank vote of Sec. III-D). Synchronises the stream."""
     lib = _lib.load()
     x = _hwc(noisy)
+    if x.dtype != _torch().uint8:
+        raise TypeError("estimate_sigma expects uint8")
     p = HtsvdParams.of(params)
     cp = p.c()
     s = ctypes.c_double(0.0)
@@ -178,8 +194,18 @@ def denoise_batch(images, sigmas, params=None, outs=None, stream=None):
     lib = _lib.load()
     torch = _torch()
     imgs = [_hwc(t) for t in images]
+    sigmas = list(sigmas)
+    if len(sigmas) != len(imgs):
+        raise ValueError(f"denoise_batch: {len(imgs)} images but {len(sigmas)} sigmas")
+    for t in imgs:
+        if t.dtype != torch.uint8:
+            raise TypeError("denoise_batch expects uint8 images")
     if outs is None:
         outs = [torch.empty(t.shape, dtype=torch.float32, device=t.device) for t in imgs]
+    if len(outs) != len(imgs):
+        raise ValueError(f"denoise_batch: {len(imgs)} images but {len(outs)} outputs")
+    for i, (t, o) in enumerate(zip(imgs, outs)):
+        _need(o if o.dim() == 3 else o.unsqueeze(-1), f"outs[{i}]", t.shape, torch.float32, t)
     arr = (_lib.CImage * len(imgs))()
     for i, (t, s, o) in enumerate(zip(imgs, sigmas, outs)):
         arr[i].d_in = t.data_ptr()
@@ -225,6 +251,8 @@ def denoise_video(frames, sigma=None, params=None, *, T=1, return_info=False, st
     lib = _lib.load()
     torch = _torch()
     v = frames if frames.dim() == 4 else frames.unsqueeze(-1)
+    if v.dim() != 4 or not v.is_cuda:
+        raise ValueError("denoise_video expects a CUDA tensor of shape (F, H, W) or (F, H, W, C)")
     if v.dtype != torch.uint8:
         raise TypeError("denoise_video expects uint8")
     v = v.contiguous()
@@ -272,7 +300,7 @@ def sure(y, sigma, tau_mults, probe, params=None, eps=None, stream=None):
     x = _hwc(y)
     if x.dtype != torch.float32:
         raise TypeError("sure expects float32")
-    b = _hwc(probe).contiguous().float()
+    b = _need(probe if probe.dim() == 3 else probe.unsqueeze(-1), "probe", x.shape, torch.float32, x)
     H, W, C = x.shape
     m = [float(t) for t in tau_mults]
     res = (ctypes.c_double * len(m))()
@@ -288,14 +316,21 @@ def denoise_vjp(x, sigma, idx, w, out, grad_out, params=None, want_grad_w=True, 
     lib = _lib.load()
     torch = _torch()
     x = _hwc(x)
+    if x.dtype != torch.float32:
+        raise TypeError("denoise_vjp expects float32")
     H, W, C = x.shape
+    p = HtsvdParams.of(params)
+    n = num_groups(H, W, p)
+    idx = _need(idx.contiguous(), "idx", (n, p.K), torch.int32, x)
+    out = _need(out.contiguous().view(x.shape) if out.numel() == x.numel() else out, "out", x.shape, torch.float32, x)
+    grad_out = _need(grad_out.contiguous().view(x.shape) if grad_out.numel() == x.numel() else grad_out,
+                     "grad_out", x.shape, torch.float32, x)
     gx = torch.empty_like(x)
-    gw = torch.empty(idx.shape[0], dtype=torch.float32, device=x.device) if want_grad_w else None
-    cp = HtsvdParams.of(params).c()
-    wt = None if w is None else w.contiguous().float()
-    st = lib.htsvd_denoise_vjp(_ptr(x), H, W, C, float(sigma), ctypes.byref(cp), _ptr(idx.contiguous()), _ptr(wt),
-                               _ptr(out.contiguous()), _ptr(grad_out.contiguous()), _ptr(gx), _ptr(gw),
-                               _stream_ptr(stream))
+    gw = torch.empty(n, dtype=torch.float32, device=x.device) if want_grad_w else None
+    cp = p.c()
+    wt = None if w is None else _need(w.contiguous().float(), "w", (n,), torch.float32, x)
+    st = lib.htsvd_denoise_vjp(_ptr(x), H, W, C, float(sigma), ctypes.byref(cp), _ptr(idx), _ptr(wt),
+                               _ptr(out), _ptr(grad_out), _ptr(gx), _ptr(gw), _stream_ptr(stream))
     _lib.check(st, "htsvd_denoise_vjp")
     return gx, gw
 

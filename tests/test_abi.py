@@ -136,3 +136,19 @@ def test_sure_rejects_bad_arguments_on_the_host():
     assert call(10.0, zero, 2) == 1            # multipliers must be positive
     assert call(10.0, ok, 2, None) == 1        # no probe
 
+
+
+def test_binding_checks_buffers_before_they_reach_the_library():
+    """The C ABI takes bare pointers; the binding checks shape, dtype, layout and device of every
+    buffer the kernels index, so a wrong buffer raises instead of being read out of bounds."""
+    torch = pytest.importorskip("torch")
+    from paper_2508_10307_gb300 import _need
+    t = torch.zeros((4, 5, 3), dtype=torch.float32)
+    with pytest.raises(ValueError, match="probe: expected shape"):
+        _need(t, "probe", (4, 5, 1), torch.float32)
+    with pytest.raises(TypeError, match="w: expected"):
+        _need(t, "w", (4, 5, 3), torch.int32)
+    with pytest.raises(ValueError, match="contiguous"):
+        _need(t.transpose(0, 1), "out", (5, 4, 3), torch.float32)
+    with pytest.raises(ValueError, match="CUDA"):
+        _need(t, "grad_out", (4, 5, 3), torch.float32)     # a host tensor never reaches the library
