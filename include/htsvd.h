@@ -18,8 +18,10 @@
  *    candidates of its search window by (SSD, linear index) ascending.
  *  - Calls are asynchronous on `stream` except where a host result is
  *    returned (documented per call). The library owns a workspace cached per
- *    (device, stream); it grows with cudaMalloc on first use at a size and is
- *    never touched by two calls on the same stream at once.
+ *    (device, stream); it grows with cudaMalloc on first use at a size. Calls
+ *    on different streams may run from different host threads at once; calls
+ *    on one stream share its workspace, so host threads that issue them must
+ *    serialise them (stream order then keeps their kernels apart).
  *  - No exceptions cross this ABI; every call returns an htsvd_status.
  */
 #ifndef HTSVD_H
