@@ -67,6 +67,12 @@ Readings where the paper is silent or ambiguous:
      so the threshold's jumps and the bases' dependence on y are counted. With eps = 0 it is
      b^T J^T b, J the Jacobian of the frozen-mask map at y (R14), which counts neither: hard
      thresholding makes that form biased low (the jump terms grow as tau falls).
+  R18 hyperspectral cubes (Sec. III-E, extension to other imaging; Sec. IV, real-world HSI
+     denoising): an H x W x N cube is Alg. 1 with C = N, so a patch is a ps x ps x N tube and the
+     t-SVD runs along the band mode (N Fourier slices); the paper is silent on matching for HSI,
+     so 'auto' matching takes the SSD over all bands (exact integers); tau = sigma sqrt(2 ln(N K
+     ps^2)) (Sec. IV-A with c = N, as R9). The paper's band-mean noise estimate goes through its
+     CNN, so for cubes sigma is an input.
 
 Parity pins for every function are in tests/test_oracle_pins.py.
 """
@@ -154,6 +160,17 @@ def window_range(r: int, n: int, ps: int, W: int) -> tuple[int, int]:
 
 # --------------------------------------------------------------------------- grouping (Sec. III-A)
 
+def resolve_match_mode(mode: str, C: int) -> str:
+    """The matching mode used for a C-channel image: 'auto' is the gray plane for one channel, the
+    GCP choice (Eq. GCP distance) for RGB and, reading R18, the SSD over all bands for a
+    hyperspectral cube. The GCP and green-plane modes name RGB planes and need C in {1, 3}."""
+    if mode == "auto":
+        return "gray" if C == 1 else ("gcp" if C == 3 else "full")
+    if mode in ("gcp", "gray") and C not in (1, 3):
+        raise ValueError(f"match mode {mode!r} needs 1 or 3 channels, got {C}")
+    return mode
+
+
 def match_planes(img: np.ndarray):
     """Integer planes the distance of Eq. (GCP distance) is taken on.
     Returns (green_or_gray, rgb_sum); rgb_sum is None for one channel."""
@@ -196,9 +213,7 @@ def _match_row(img: np.ndarray, ry: int, rxs: np.ndarray, p: Params):
     nx = xw[0][1]
     if ny * nx < K:
         raise ValueError("search window holds fewer than K candidates")
-    mode = p.match_mode
-    if mode == "auto":
-        mode = "gray" if C == 1 else "gcp"
+    mode = resolve_match_mode(p.match_mode, C)
     x = img.astype(np.int64)
     n = len(rxs)
     if mode == "full":
@@ -637,9 +652,7 @@ def _match_row_video(video: np.ndarray, t: int, ry: int, rxs: np.ndarray, p: Par
     xw = [window_range(int(rx), Wd, ps, p.window) for rx in rxs]
     x0s = np.array([a for a, _ in xw], dtype=np.int64)
     nx = xw[0][1]
-    mode = p.match_mode
-    if mode == "auto":
-        mode = "gray" if C == 1 else "gcp"
+    mode = resolve_match_mode(p.match_mode, C)
     n = len(rxs)
     if mode == "full" or C == 1 or mode == "gray":
         green = np.ones(n, dtype=bool) if mode != "full" else np.zeros(n, dtype=bool)

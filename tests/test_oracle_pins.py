@@ -595,3 +595,70 @@ def test_sure_divergence_is_the_trace_of_the_frozen_map():
         tr_vjp += gx.ravel()[i]
     assert tr_vjp == pytest.approx(tr_cols, rel=1e-10)
     assert 0.0 < tr_cols < n
+
+
+# ---------------------------------------------------------------- hyperspectral cubes (reading R18)
+
+def _cube(H, W, N, seed, sigma=12.0):
+    """A smooth cube whose bands are affine in one clean image, plus Gaussian noise, as uint8."""
+    rng = np.random.default_rng(seed)
+    g = synth.clean_image(H, W, 1, seed)[:, :, 0].astype(np.float64)
+    cube = np.stack([g * (0.6 + 0.08 * b) + 9.0 * b for b in range(N)], axis=2)
+    return np.clip(np.rint(cube + rng.normal(0.0, sigma, cube.shape)), 0, 255).astype(np.uint8)
+
+
+def test_hsi_auto_matching_is_the_ssd_over_all_bands():
+    img = np.random.default_rng(31).integers(0, 256, size=(13, 15, 5), dtype=np.uint8)
+    p = O.Params(ps=4, stride=3, window=6, K=8)
+    idx, _ = O.block_match(img, p)
+    H, W, N = img.shape
+    im = img.astype(int).tolist()
+    n = 0
+    for ry in O.reference_positions(H, 4, 3):
+        for rx in O.reference_positions(W, 4, 3):
+            ry, rx = int(ry), int(rx)
+            ys = range(min(max(ry - 2, 0), H - 4 - 5), min(max(ry - 2, 0), H - 4 - 5) + 6)
+            xs = range(min(max(rx - 2, 0), W - 4 - 5), min(max(rx - 2, 0), W - 4 - 5) + 6)
+            keys = []
+            for y in ys:
+                for x in xs:
+                    if (y, x) != (ry, rx):
+                        d = sum((im[ry + i][rx + j][b] - im[y + i][x + j][b]) ** 2
+                                for i in range(4) for j in range(4) for b in range(N))
+                        keys.append((d, y * W + x))
+            keys.sort()
+            assert list(idx[n]) == [ry * W + rx] + [k[1] for k in keys[:7]]
+            n += 1
+
+
+def test_hsi_denoiser_commutes_with_a_cyclic_shift_of_the_bands():
+    """The t-SVD is built on circulant structure along the band mode: a cyclic shift of the bands
+    multiplies every Fourier slice by a phase, which leaves the scatter matrices and so the bases
+    unchanged, and the inverse band transform turns the phase back into the shift."""
+    y = _cube(30, 34, 6, 41)
+    prm = dict(ps=8, stride=3, window=9, K=8, tau_mult=2.7)
+    a = O.denoise(y, 12.0, prm).out
+    for s in (1, 4):
+        b = O.denoise(np.roll(y, s, axis=2), 12.0, prm).out
+        assert np.abs(b - np.roll(a, s, axis=2)).max() <= 1e-9
+
+
+def test_hsi_identical_bands_reduce_to_the_gray_denoiser():
+    """N equal bands put all energy in Fourier slice 0, whose scatter matrices are N^2 times the gray
+    ones (same bases), and the inverse band transform returns the gray coefficients in every band;
+    the all-band SSD is N times the gray SSD (same groups). With one multiplier for both, every band
+    of the result is the gray result."""
+    g = _cube(28, 31, 1, 43)
+    prm = dict(ps=8, stride=3, window=9, K=8, tau_mult=2.7)
+    r1 = O.denoise(g, 12.0, prm).out
+    rN = O.denoise(np.repeat(g, 5, axis=2), 12.0, prm).out
+    assert np.abs(rN - np.repeat(r1, 5, axis=2)).max() <= 1e-9
+
+
+def test_hsi_zero_threshold_is_the_identity_and_rgb_modes_refuse_cubes():
+    y = _cube(24, 26, 7, 47)
+    out = O.denoise(y, 12.0, dict(ps=8, stride=3, window=7, K=4, tau_mult=1e-12)).out
+    assert np.abs(out - y).max() <= 1e-9
+    for mode in ("gcp", "gray"):
+        with pytest.raises(ValueError):
+            O.block_match(y, O.Params(ps=8, stride=3, window=7, K=4, match_mode=mode))
