@@ -1,4 +1,5 @@
-// Dispatch of the group filter, and the deterministic reduction of tile partials.
+// Dispatch of the group filter, the deterministic reduction of tile partials, and the small kernels
+// of the SURE path (perturbed image, FP64 sums).
 #include "filter_impl.cuh"
 
 namespace htsvd {
