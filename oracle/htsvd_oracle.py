@@ -28,26 +28,30 @@ Readings where the paper is silent or ambiguous:
   R5 slot 0 is the reference; slots 1..K-1 are the K-1 smallest (SSD, y*W+x)
      keys among the other candidates (ties -> lowest linear index).
   R6 global bases: per Fourier slice f, U_f = eigenvectors of sum_r P_f P_f^H,
-     V_f = eigenvectors of sum_r P_f^H P_f (uncentred, reference patches),
-     eigenvalues descending, each eigenvector's largest-modulus entry made real
-     positive (ties within 1e-6 relative -> lowest index); slice C-f := conj(slice f).
-  R7 coefficients along the group mode are H_K applied to each K-fibre
+     V_f = eigenvectors of sum_r P_f^H P_f (uncentred, reference patches);
+     slice C-f := conj(slice f).
+  R7 eigenvector convention: eigenvalues descending, each eigenvector's
+     largest-modulus entry made real positive (ties within 1e-6 relative ->
+     lowest index).
+  R8 coefficients along the group mode are H_K applied to each K-fibre
      (U_Haar = H_K^T); the inverse is H_K^T.
-  R8 tau = tau_mult * sigma; tau_mult <= 0 means sqrt(2 ln(C K ps^2)); the
+  R9 tau = tau_mult * sigma; tau_mult <= 0 means sqrt(2 ln(C K ps^2)); the
      threshold applies to every coefficient and |S| == tau is kept.
-  R9 aggregation weights: 1 per group (uniform), or 1/max(1, #kept) (sparsity),
+  R10 aggregation weights: 1 per group (uniform), or 1/max(1, #kept) (sparsity),
      or caller-given per-group weights.
-  R10 noise estimate: covariance of reference patches, ascending eigenvalues,
+  R11 noise estimate: covariance of reference patches, ascending eigenvalues,
      r* = max{r : mean(l_1..r) <= 1.02 median(l_1..r)}, sigma = sqrt(mean(l_1..r*)).
-  R11 adaptive adjustment: groups of every 8th reference per axis; rank
+  R12 adaptive adjustment: groups of every 8th reference per axis; rank
      a = 1 + #{f : lambda_f < lambda_{K/2}}; majority of a <= gamma_rank divides
      sigma by beta.
-  R12 float inputs: matching, bases and sigma use q = clip(rint(x)); the
+  R13 float inputs: matching, bases and sigma use q = clip(rint(x)); the
      transforms use x.
+  R14 vector-Jacobian product: grouping, bases, tau and masks held fixed (masks
+     taken at x), so the map is linear in x and its adjoint is the transposed chain.
   R15 A-Haar-tSVD (Alg. 2) subimages: each axis of length n is cut into
      t = max(1, floor(n / n_sub)) parts with boundaries floor(i n / t), so every
      subimage is at least n_sub long; each subimage gets its own noise estimate
-     (R10, with R11 when adapt is set) and is denoised on its own (Alg. 1).
+     (R11, with R12 when adapt is set) and is denoised on its own (Alg. 1).
   R16 video (Sec. IV, real-world color video denoising; the paper states only that
      the patch search covers space and time and that the noise estimate runs frame
      by frame): output frame t is Alg. 1 on frame t with frame t's own bases (R6)
@@ -315,7 +319,7 @@ def t_product_fft(A: np.ndarray, B: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------- global bases (Sec. III-B.1)
 
 def canonical_eigvecs(A: np.ndarray):
-    """Eigenpairs of a Hermitian matrix, eigenvalues descending, each eigenvector scaled by a
+    """Reading R7: eigenpairs of a Hermitian matrix, eigenvalues descending, each eigenvector scaled by a
     unit phase so its largest-modulus entry (lowest index within 1e-6 relative) is real positive."""
     w, Q = np.linalg.eigh(A)
     w, Q = w[::-1].copy(), Q[:, ::-1].copy()
@@ -388,7 +392,7 @@ def forward_transform(G: np.ndarray, U, V, H: np.ndarray) -> np.ndarray:
 
 
 def inverse_transform(S: np.ndarray, U, V, H: np.ndarray) -> np.ndarray:
-    """Eq. (backward transform) read as the exact inverse (reading R7): x_4 H_K^T then U * . * V^T."""
+    """Eq. (backward transform) read as the exact inverse (reading R8): x_4 H_K^T then U * . * V^T."""
     T = np.moveaxis(np.tensordot(H.T, S, axes=([1], [-4])), 0, -4)   # sum_m H[m, k] S_m
     return patch_inverse(T, U, V)
 
@@ -441,7 +445,7 @@ def denoise(x: np.ndarray, sigma: float, params=None, *, idx=None, weights=None,
     """Alg. 1: grouping, global bases, forward transform, hard threshold, inverse, aggregation.
 
     x: (H, W, C) uint8 or float image on the [0, 255] scale.  For float input the matching and the
-    bases use the quantised image (reading R12) and the transforms use x itself."""
+    bases use the quantised image (reading R13) and the transforms use x itself."""
     p = Params.of(params)
     if x.ndim == 2:
         x = x[:, :, None]
@@ -487,7 +491,7 @@ def denoise(x: np.ndarray, sigma: float, params=None, *, idx=None, weights=None,
 # --------------------------------------------------------------------------- frozen-mask linear map and its adjoint
 
 def denoise_fixed(x: np.ndarray, idx: np.ndarray, masks: np.ndarray, U, V, w: np.ndarray, ps: int):
-    """The denoiser with grouping, bases and masks held fixed: out = N(x) / D,
+    """Reading R14: the denoiser with grouping, bases and masks held fixed: out = N(x) / D,
     N(x) = sum_g w_g Scatter_g T^-1 (M_g . T Gather_g x), D = sum_g w_g Scatter_g 1.  Linear in x."""
     if x.ndim == 2:
         x = x[:, :, None]
@@ -502,7 +506,7 @@ def denoise_fixed(x: np.ndarray, idx: np.ndarray, masks: np.ndarray, U, V, w: np
 
 def denoise_fixed_vjp(x: np.ndarray, gout: np.ndarray, idx: np.ndarray, masks: np.ndarray, U, V,
                       w: np.ndarray, ps: int):
-    """Adjoint of denoise_fixed at x for cotangent gout.
+    """Reading R14: adjoint of denoise_fixed at x for cotangent gout.
     d/dx  = sum_g w_g Gather_g^T T^T (M_g . T Gather_g (gout / D))
     d/dw_g = sum over g's patches of (gout/D)[q] * (Ghat_g[q] - out[q])."""
     if x.ndim == 2:
@@ -524,7 +528,7 @@ def denoise_fixed_vjp(x: np.ndarray, gout: np.ndarray, idx: np.ndarray, masks: n
     return gx, gw
 
 
-# --------------------------------------------------------------------------- noise level (Sec. III-D + reading R10/R11)
+# --------------------------------------------------------------------------- noise level (Sec. III-D + reading R11/R12)
 
 def patch_covariance(q: np.ndarray, p: Params) -> np.ndarray:
     P = reference_patches(q, p).reshape(-1, p.ps * p.ps * q.shape[2])
@@ -533,7 +537,7 @@ def patch_covariance(q: np.ndarray, p: Params) -> np.ndarray:
 
 
 def sigma_from_eigenvalues(lam: np.ndarray) -> float:
-    """Reading R10: the largest leading run of ascending eigenvalues whose mean stays within 2% of
+    """Reading R11: the largest leading run of ascending eigenvalues whose mean stays within 2% of
     its median is taken as the noise subspace; sigma = sqrt(mean of that run)."""
     lam = np.sort(lam)
     rstar = 1
@@ -560,8 +564,8 @@ def rank_position(G: np.ndarray) -> int:
 
 
 def estimate_sigma(x: np.ndarray, params=None, return_details=False):
-    """Noise level from the patch covariance (reading R10), optionally adjusted by the
-    eigen-rank vote of Eq. (adjust noise level) over sampled groups (reading R11)."""
+    """Noise level from the patch covariance (reading R11), optionally adjusted by the
+    eigen-rank vote of Eq. (adjust noise level) over sampled groups (reading R12)."""
     p = Params.of(params)
     if x.ndim == 2:
         x = x[:, :, None]
@@ -600,7 +604,7 @@ def subimage_bounds(n: int, n_sub: int) -> list[tuple[int, int]]:
 
 
 def a_haar_tsvd(x: np.ndarray, sub_h: int, sub_w: int, params=None):
-    """Alg. 2 (A-Haar-tSVD) with the eigenvalue noise estimate (R10, R11) in place of the CNN:
+    """Alg. 2 (A-Haar-tSVD) with the eigenvalue noise estimate (R11, R12) in place of the CNN:
     Step 1 estimates sigma per subimage, Step 2 denoises each subimage with Alg. 1 at its sigma.
     Returns (output (H, W, C) float64, per-subimage sigmas in row-major subimage order)."""
     p = Params.of(params)
@@ -732,7 +736,7 @@ def aggregate_frame(shape, t: int, idx: np.ndarray, Ghat: np.ndarray, w: np.ndar
 
 def denoise_video(video: np.ndarray, sigma=None, params=None, T: int = 1, *, keep_masks=False, chunk=2048):
     """Reading R16: a uint8 clip (F, H, W, C) denoised frame by frame with spatio-temporal grouping.
-    sigma None -> estimated per frame (R10, R11); else used for every frame.
+    sigma None -> estimated per frame (R11, R12); else used for every frame.
     Returns (output (F, H, W, C) float64, per-frame Results with global idx, masks and ambiguity)."""
     p = Params.of(params)
     if video.ndim == 3:
