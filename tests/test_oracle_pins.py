@@ -347,15 +347,65 @@ def test_sigma_rule_on_constructed_spectrum():
     assert abs(O.sigma_from_eigenvalues(lam) - 2.0) < 1e-12
 
 
-def test_adaptive_vote_direction():
-    clean = synth.clean_image(96, 96, 3, 21)
-    noisy = synth.add_gaussian(clean, 40.0, 21)
-    s0, d = O.estimate_sigma(noisy, dict(ps=8, stride=3, window=15, K=32, adapt=True), return_details=True)
-    assert d["low"] + d["high"] == len(d["ranks"]) > 0
-    if d["low"] > d["high"]:
-        assert abs(s0 - d["sigma_est"] / 1.2) < 1e-12
-    else:
-        assert s0 == d["sigma_est"]
+def _ramp_zone_image(n=256, stride=4, seed=5):
+    """Gray image for the vote-direction pin, high side: random texture everywhere except a 14 x 14 zone
+    around every sampled reference (every 8th reference per axis) holding I = 20 + x' + 17 y' in zone
+    coordinates. Window 7 (offsets -3..3) keeps every candidate patch of a sampled reference inside its
+    zone, where a candidate at offset (dy, dx) is the reference patch plus the constant dx + 17 dy, so
+    its SSD is 64 (dx + 17 dy)^2: the three nearest are dx = -1, +1, -2 in that order (equal SSD ->
+    lowest index), dy = 0. The texture elsewhere makes the patch covariance full rank (sigma_est > 0)."""
+    rng = np.random.default_rng(seed)
+    img = rng.integers(0, 256, size=(n, n)).astype(np.int64)
+    ys = O.reference_positions(n, 8, stride)[::8]
+    for Y0 in ys:
+        for X0 in ys:
+            y0, x0 = int(Y0) - 3, int(X0) - 3
+            for y in range(max(0, y0), min(n, y0 + 14)):
+                for x in range(max(0, x0), min(n, x0 + 14)):
+                    img[y, x] = 20 + (x - x0) + 17 * (y - y0)
+    return img.astype(np.uint8)[:, :, None]
+
+
+def test_adaptive_vote_divides_when_every_group_ranks_low():
+    """Eq. (adjust noise level): sigma_hat = sigma_est / beta when a <= gamma wins the vote. An image tiled
+    with one random 8 x 8 texture has, in a window of 25, at least 3 x 3 exact copies of every reference
+    patch, so with K = 8 every group is 8 identical patches: lambda_f = 0 for f != 0, hence
+    a = 1 + #{f : lambda_f < lambda_4 = 0} = 1 <= gamma = round(13 * 8 / 32) = 3 for every sampled group."""
+    tex = np.random.default_rng(11).integers(0, 256, size=(8, 8)).astype(np.uint8)
+    img = np.tile(tex, (8, 8))[:, :, None]
+    prm = dict(ps=8, stride=3, window=25, K=8)
+    p = O.Params.of(prm)
+    for ry in O.reference_positions(64, 8, 3)[::8]:
+        for rx in O.reference_positions(64, 8, 3)[::8]:
+            idx, _, _ = O.block_match_one(img, int(ry), int(rx), p)
+            G = O.gather_groups(img, idx[None], 8)[0]
+            assert (G == G[0]).all()                      # 8 identical patches
+    s_est = O.estimate_sigma(img, prm)
+    s_hat, d = O.estimate_sigma(img, dict(prm, adapt=True), return_details=True)
+    assert s_est > 1.0
+    assert (d["ranks"] == 1).all() and d["high"] == 0
+    assert s_hat == s_est / 1.2
+
+
+def test_adaptive_vote_keeps_sigma_when_groups_rank_high():
+    """High side of Eq. (adjust noise level): with K = 4 an interior sampled group is p, p - 1, p + 1, p - 2
+    (constants added to one patch p; see _ramp_zone_image), so lambda_2 = 64 (0 + 1 + 1 + 2)^2 = 1024
+    exceeds lambda_1 = lambda_3 = 64 ((0 - 1)^2 + (-1 + 2)^2) = 128 and a >= 3 > gamma = round(13 * 4 / 32)
+    = 2. Only the sampled references on the first row or column (window clamped at the border) can rank
+    low, so a > gamma wins the vote and sigma is left as estimated."""
+    img = _ramp_zone_image()
+    prm = dict(ps=8, stride=4, window=7, K=4)
+    p = O.Params.of(prm)
+    idx, _, _ = O.block_match_one(img, 32, 32, p)
+    assert (idx - (32 * 256 + 32)).tolist() == [0, -1, 1, -2]
+    lam = O.circulant_eigenvalues(O.gather_groups(img, idx[None], 8)[0])
+    assert abs(lam[2] - 1024.0) < 1e-6 and abs(lam[1] - 128.0) < 1e-6 and abs(lam[3] - 128.0) < 1e-6
+    s_est = O.estimate_sigma(img, prm)
+    s_hat, d = O.estimate_sigma(img, dict(prm, adapt=True), return_details=True)
+    assert s_est > 1.0
+    n_border = 2 * 8 - 1                                 # sampled references with y = 0 or x = 0
+    assert d["high"] >= len(d["ranks"]) - n_border > d["low"]
+    assert s_hat == s_est
 
 
 # ---------------------------------------------------------------- frozen-mask map and its adjoint
