@@ -40,7 +40,9 @@ typedef enum htsvd_status {
     HTSVD_ERR_UNSUPPORTED = 2,   /* valid for the method, not built here (ps != 8, K > 32, window > 64) */
     HTSVD_ERR_CUDA = 3,          /* a CUDA runtime call failed */
     HTSVD_ERR_OOM = 4,           /* workspace allocation failed */
-    HTSVD_ERR_TIMEOUT = 5,       /* reserved for bounded device waits; no kernel of this library waits on another CTA */
+    HTSVD_ERR_TIMEOUT = 5,       /* reserved: no kernel of this library waits on another CTA, so no call returns it */
+    HTSVD_ERR_DEGENERATE_BASIS = 6, /* strict mode only: a global-basis slice has a relative eigen-gap below 1e-9,
+                                       so its eigenvectors (and the coefficients) are not unique (Sec. III-B.1) */
 } htsvd_status;
 
 typedef enum htsvd_match_mode {
@@ -71,8 +73,7 @@ typedef struct htsvd_params {
     int32_t adapt;         /* sigma estimation: apply the eigen-rank vote of Eq. (adjust noise level) */
     double  beta;          /* <= 0 -> 1.2 (Sec. III-D) */
     int32_t rank_gamma;    /* <= 0 -> round(13 K / 32) (Sec. III-D) */
-    int32_t tile;          /* reference tile edge for the filter (0 -> automatic) */
-    int64_t max_wait_cycles; /* reserved (bounded device waits); ignored: no kernel of this library waits on another CTA */
+    int32_t tile;          /* reference tile edge for the filter (0 -> automatic), at most 16 */
     /* Optional outputs (may be NULL). */
     double*   h_sigma_out;   /* HOST: the sigma actually used (estimated when sigma < 0) */
     uint32_t* d_mask_out;    /* DEVICE: threshold masks, per group ceil(K*ps*ps*C/32) words, bit index
@@ -82,6 +83,15 @@ typedef struct htsvd_params {
                                 each slice row-major [a][i] (column i = i-th eigenvector) */
     float*    d_coef_out;    /* DEVICE: FP32 coefficients S before thresholding, K*ps*ps*C floats per group,
                                 same index as the mask bits (for accuracy checks) */
+    /* Eigen-gap check of the global bases (Sec. III-B.1: the bases are eigenvectors of the per-slice
+     * scatter matrices; where two eigenvalues coincide the eigenvectors, and so the thresholded
+     * coefficients, are not unique). The gap of a slice is min_i |l_i - l_{i+1}| / |l_max| over its
+     * eigenvalues; the check takes the smallest over all U and V slices. Either field makes the call
+     * synchronise `stream` once after the basis solve. Honoured by htsvd_denoise, htsvd_denoise_f32 and
+     * htsvd_denoise_noalloc. */
+    int32_t   strict_basis;  /* nonzero: return HTSVD_ERR_DEGENERATE_BASIS (before the filter runs, d_out
+                                unwritten) when that gap is below 1e-9; zero: no check (production) */
+    double*   h_basis_gap_out; /* HOST (may be NULL): receives that smallest relative gap */
 } htsvd_params;
 
 /* One image of a batch. */
@@ -206,22 +216,31 @@ htsvd_status htsvd_denoise_vjp(const float* d_x, int32_t H, int32_t W, int32_t C
 
 /* Size of the fixed device array used by htsvd_denoise_noalloc. */
 #define HTSVD_NOALLOC_SCRATCH_BYTES (32u << 20)
+/* Square RGB edges that array holds at stride 3, window 18, K 32 on a 152-SM GB300 (see below). */
+#define HTSVD_NOALLOC_SAME_TILES_RGB_EDGE 305
+#define HTSVD_NOALLOC_MAX_RGB_EDGE 821
 
-/* Alg. 1 on a uint8 image without any device-memory allocation (the paper has no
- * counterpart: this serves callers that must not allocate). Hosts that reserve all device
- * memory in their own pool, or loops that cannot afford the device-wide synchronisation
- * cudaFree implies, cannot let a library call cudaMalloc/cudaFree; this call runs the
- * same kernels as htsvd_denoise but keeps every temporary (match indices, moments,
- * bases, tile partials) in one array of HTSVD_NOALLOC_SCRATCH_BYTES (32 MiB) that the
- * library declares in device memory. Every GPU that loads the library holds that array
- * until the process exits.
- * sigma must be >= 0 (no estimation). The other arguments are as in htsvd_denoise.
- * Images whose temporaries do not fit the array return HTSVD_ERR_INVALID_ARG before any
- * device work (at stride 3, window 18, K 32 the array holds RGB images up to 677 x 677).
- * The first call on a device looks up the array's device address (with that device
- * current); make that first call before any stream capture. All calls share the one
- * array and it keeps the last call's contents: calls that can overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller. */
+/* The plain uint8 denoiser of htsvd_denoise, without any device-memory allocation. The paper has
+ * no counterpart: this call serves callers that must not let a library allocate. A host whose own
+ * caching allocator has reserved the device memory cannot have a library call cudaMalloc behind it,
+ * and a latency-bound processing loop cannot take the device-wide synchronisation that cudaFree
+ * implies. This call runs the same kernels as htsvd_denoise with the same parameter checks; it takes
+ * the same filter tiles (so the same output, bit for bit) whenever their tile partials fit, else the
+ * largest tile edge whose shared memory fits a CTA (equal output up to rounding order). It keeps
+ * every temporary (match indices, moments, bases, eigen-gaps, tile partials) in one array of
+ * HTSVD_NOALLOC_SCRATCH_BYTES (32 MiB) that the
+ * library declares in device memory; every GPU that loads the library holds that array until the
+ * process exits. It calls no cudaMalloc, cudaFree or allocating library routine.
+ * sigma must be given (>= 0, finite); there is no estimation and no d_idx_out. Every field of p is
+ * honoured as in htsvd_denoise (optional outputs, tile, strict_basis, h_basis_gap_out).
+ * Images whose temporaries do not fit the array return HTSVD_ERR_INVALID_ARG before any device work.
+ * At stride 3, window 18, K 32 on a 152-SM GB300, square RGB images up to
+ * HTSVD_NOALLOC_SAME_TILES_RGB_EDGE take the tiles of htsvd_denoise and images up to
+ * HTSVD_NOALLOC_MAX_RGB_EDGE fit at all (htsvd_internal_noalloc_bytes gives the need of any size).
+ * The first call on a device looks up the array's device address (with that device current); make
+ * that first call before any stream capture. All calls share the one array and it keeps the last
+ * call's contents (each call clears what it accumulates); calls that can overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the caller. */
 htsvd_status htsvd_denoise_noalloc(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, double sigma,
                                    const htsvd_params* p, float* d_out, cudaStream_t stream);
 

@@ -47,6 +47,18 @@ double htsvd_internal_sigma_from_moments(const unsigned long long* M, const unsi
 int32_t htsvd_internal_sampled_ranks(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const htsvd_params* p,
                                      int32_t* h_ranks, int32_t max_ranks);
 
+/* Bytes of the static scratch array that htsvd_denoise_noalloc would use for an H x W x C image
+ * with parameters p on the current device (the filter tiles depend on its SM count), or -1 when
+ * the arguments fail the checks of htsvd_denoise. Host only; launches nothing. */
+int64_t htsvd_internal_noalloc_bytes(int32_t H, int32_t W, int32_t C, const htsvd_params* p);
+
+/* DEVICE probe of an arithmetic pipe's issue rate on the current device: 2 CTAs of 512 threads per
+ * SM, each thread running 8 independent chains of one instruction for 32 * iters steps (op 0: FP32
+ * fused multiply-add, 1: 32-bit integer multiply-add, 2: 4-way byte dot product with accumulate).
+ * Returns the mean over SMs of operations per SM clock (clock64 spans per SM), or -1 on a bad
+ * argument or a CUDA error. Synchronises the device; allocates two small buffers. */
+double htsvd_internal_alu_probe(int32_t op, int32_t iters);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,9 @@ Readings where the paper is silent or ambiguous:
      slice C-f := conj(slice f).
   R7 eigenvector convention: eigenvalues descending, each eigenvector's
      largest-modulus entry made real positive (ties within 1e-6 relative ->
-     lowest index).
+     lowest index). Where two eigenvalues of a slice lie within 1e-9 of each other
+     (relative to the largest) the eigenvectors are not unique; strict mode raises
+     DegenerateBasis there (a test mode: without it the call proceeds).
   R8 coefficients along the group mode are H_K applied to each K-fibre
      (U_Haar = H_K^T); the inverse is H_K^T.
   R9 tau = tau_mult * sigma; tau_mult <= 0 means sqrt(2 ln(C K ps^2)); the
@@ -104,6 +106,7 @@ class Params:
     adapt: bool = False            # Sec. III-D adjustment
     beta: float = 1.2
     rank_gamma: int = 0            # 0 -> round(13 K / 32)
+    strict_basis: bool = False     # raise DegenerateBasis when a basis slice has coinciding eigenvalues
 
     @staticmethod
     def of(d: dict | "Params" | None) -> "Params":
@@ -356,9 +359,23 @@ def global_basis(ref_patches: np.ndarray):
 
 
 def basis_gap(lam: np.ndarray) -> float:
-    """Smallest relative gap between consecutive eigenvalues (degeneracy check of reading R6)."""
+    """Smallest relative gap between consecutive eigenvalues (degeneracy check of reading R7)."""
     top = max(abs(lam.max()), 1e-300)
     return float(np.min(np.abs(np.diff(np.sort(lam)))) / top) if lam.size > 1 else 1.0
+
+
+DEGENERATE_GAP = 1e-9
+
+
+class DegenerateBasis(ValueError):
+    """Reading R7: two eigenvalues of a basis slice lie within DEGENERATE_GAP (relative to the largest), so
+    the slice's eigenvectors, and with them the coefficients that are thresholded, are not unique."""
+
+
+def global_basis_gap(lu: np.ndarray, lv: np.ndarray) -> float:
+    """Smallest basis_gap over the U and V slices f = 0 .. C // 2 (slices C - f repeat f)."""
+    C = lu.shape[0]
+    return min(min(basis_gap(lu[f]), basis_gap(lv[f])) for f in range(C // 2 + 1))
 
 
 # --------------------------------------------------------------------------- group transform (Sec. III-B.2)
@@ -441,11 +458,12 @@ def _as_quantised(x: np.ndarray) -> np.ndarray:
 
 
 def denoise(x: np.ndarray, sigma: float, params=None, *, idx=None, weights=None,
-            keep_masks=False, keep_coeffs=False, chunk=2048, tau=None) -> Result:
+            keep_masks=False, keep_coeffs=False, chunk=2048, tau=None, basis=None) -> Result:
     """Alg. 1: grouping, global bases, forward transform, hard threshold, inverse, aggregation.
 
     x: (H, W, C) uint8 or float image on the [0, 255] scale.  For float input the matching and the
-    bases use the quantised image (reading R13) and the transforms use x itself."""
+    bases use the quantised image (reading R13) and the transforms use x itself.  idx restricts the
+    filter to the given groups; basis = global_basis(...) of this image skips its recomputation."""
     p = Params.of(params)
     if x.ndim == 2:
         x = x[:, :, None]
@@ -453,7 +471,10 @@ def denoise(x: np.ndarray, sigma: float, params=None, *, idx=None, weights=None,
     q = _as_quantised(x)
     if idx is None:
         idx, _ = block_match(q, p)
-    U, V, _, _ = global_basis(reference_patches(q, p))
+    U, V, lu, lv = global_basis(reference_patches(q, p)) if basis is None else basis
+    gap = global_basis_gap(lu, lv)
+    if p.strict_basis and not gap >= DEGENERATE_GAP:
+        raise DegenerateBasis(f"smallest relative eigen-gap {gap:.3g} < {DEGENERATE_GAP:g}")
     Hk = haar_matrix(p.K)
     if tau is None:
         tau = tau_multiplier(p, C) * float(sigma)
@@ -485,7 +506,8 @@ def denoise(x: np.ndarray, sigma: float, params=None, *, idx=None, weights=None,
             coeffs[a:b] = np.abs(S)
     out = num / den[:, :, None]
     return Result(out=out, idx=idx, tau=tau, U=U, V=V, weights=w_out, masks=masks,
-                  coeffs=coeffs, den=den, ambiguous=np.array(amb, dtype=np.int64).reshape(-1, 2))
+                  coeffs=coeffs, den=den, ambiguous=np.array(amb, dtype=np.int64).reshape(-1, 2),
+                  extra={"basis_gap": gap})
 
 
 # --------------------------------------------------------------------------- frozen-mask linear map and its adjoint

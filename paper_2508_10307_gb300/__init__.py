@@ -33,6 +33,7 @@ class HtsvdParams:
     beta: float = 1.2
     rank_gamma: int = 0
     tile: int = 0
+    strict_basis: bool = False      # fail with DEGENERATE_BASIS when a basis slice's eigen-gap is below 1e-9
 
     @staticmethod
     def of(p) -> "HtsvdParams":
@@ -54,6 +55,7 @@ class HtsvdParams:
         cp.beta = float(self.beta)
         cp.rank_gamma = int(self.rank_gamma)
         cp.tile = int(self.tile)
+        cp.strict_basis = int(bool(self.strict_basis))
         return cp
 
 
@@ -127,9 +129,10 @@ def _outputs(x, p, params, want_idx, want_masks, want_weights, want_basis, want_
 
 
 def denoise(noisy, sigma=None, params=None, *, return_info=False, masks=False, weights=False, basis=False,
-            coeffs=False, stream=None):
+            coeffs=False, basis_gap=False, stream=None):
     """Alg. 1 on a uint8 (H, W[, C]) CUDA tensor. sigma=None estimates it on the device.
-    Returns the float32 (H, W, C) estimate, or (estimate, info) with return_info."""
+    Returns the float32 (H, W, C) estimate, or (estimate, info) with return_info; basis_gap=True adds
+    info["basis_gap"], the smallest relative eigen-gap of the basis slices (synchronises)."""
     lib = _lib.load()
     x = _hwc(noisy)
     if x.dtype != _torch().uint8:
@@ -138,6 +141,9 @@ def denoise(noisy, sigma=None, params=None, *, return_info=False, masks=False, w
     cp = p.c()
     sig_out = ctypes.c_double(-1.0)
     cp.h_sigma_out = ctypes.pointer(sig_out)
+    gap_out = ctypes.c_double(-1.0)
+    if basis_gap:
+        cp.h_basis_gap_out = ctypes.pointer(gap_out)
     out, idx, info = _outputs(x, p, cp, return_info, masks, weights, basis, coeffs)
     H, W, C = x.shape
     st = lib.htsvd_denoise(_ptr(x), H, W, C, -1.0 if sigma is None else float(sigma), ctypes.byref(cp),
@@ -145,6 +151,8 @@ def denoise(noisy, sigma=None, params=None, *, return_info=False, masks=False, w
     _lib.check(st, "htsvd_denoise")
     if return_info:
         info.update(idx=idx, sigma=sig_out.value)
+        if basis_gap:
+            info["basis_gap"] = gap_out.value
         return out, info
     return out
 

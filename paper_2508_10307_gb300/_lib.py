@@ -8,7 +8,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libhtsvd.so")
 
 HTSVD_OK = 0
-STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "OOM", 5: "TIMEOUT"}
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "OOM", 5: "TIMEOUT", 6: "DEGENERATE_BASIS"}
+HTSVD_ERR_DEGENERATE_BASIS = 6
 
 EXPORTED = ["htsvd_denoise", "htsvd_denoise_f32", "htsvd_estimate_sigma", "htsvd_denoise_batch",
             "htsvd_denoise_vjp", "htsvd_num_groups", "htsvd_status_string", "htsvd_release_workspace",
@@ -30,12 +31,13 @@ class CParams(ctypes.Structure):
         ("beta", ctypes.c_double),
         ("rank_gamma", ctypes.c_int32),
         ("tile", ctypes.c_int32),
-        ("max_wait_cycles", ctypes.c_int64),
         ("h_sigma_out", ctypes.POINTER(ctypes.c_double)),
         ("d_mask_out", ctypes.c_void_p),
         ("d_weights_out", ctypes.c_void_p),
         ("d_basis_out", ctypes.c_void_p),
         ("d_coef_out", ctypes.c_void_p),
+        ("strict_basis", ctypes.c_int32),
+        ("h_basis_gap_out", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -55,6 +57,10 @@ _lib = None
 
 class HtsvdError(RuntimeError):
     pass
+
+
+class DegenerateBasisError(HtsvdError):
+    """A global-basis slice has coinciding eigenvalues (strict mode)."""
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -80,6 +86,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                             ctypes.POINTER(ctypes.c_double), vp]
     lib.htsvd_sure.argtypes = [vp, i32, i32, i32, dbl, ctypes.POINTER(ctypes.c_double), i32, vp, dbl, P,
                                ctypes.POINTER(ctypes.c_double), vp]
+    lib.htsvd_internal_alu_probe.argtypes = [i32, i32]
+    lib.htsvd_internal_alu_probe.restype = ctypes.c_double
+    lib.htsvd_internal_noalloc_bytes.argtypes = [i32, i32, i32, P]
+    lib.htsvd_internal_noalloc_bytes.restype = ctypes.c_int64
     lib.htsvd_num_groups.argtypes = [i32, i32, P]
     lib.htsvd_num_groups.restype = ctypes.c_int64
     lib.htsvd_status_string.argtypes = [ctypes.c_int]
@@ -101,7 +111,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 def check(status: int, what: str) -> None:
     if status != HTSVD_OK:
         msg = _lib.htsvd_status_string(status).decode() if _lib is not None else ""
-        raise HtsvdError(f"{what} failed: {STATUS_NAMES.get(status, status)} ({msg})")
+        cls = DegenerateBasisError if status == HTSVD_ERR_DEGENERATE_BASIS else HtsvdError
+        raise cls(f"{what} failed: {STATUS_NAMES.get(status, status)} ({msg})")
 
 
 def profile_enable(on: bool) -> None:

@@ -11,6 +11,7 @@
 
 #include "../../include/htsvd.h"
 #include "kernels.h"
+#include "host_plan.h"
 
 namespace htsvd {
 bool symmetric_eigenvalues(double* A, int n, double* out);
@@ -18,15 +19,9 @@ bool symmetric_eigenvalues(double* A, int n, double* out);
 
 using namespace htsvd;
 
-namespace {
+namespace htsvd {
 
 // ----------------------------------------------------------------------------- parameters
-
-struct Resolved {
-    int ps, s, win, K, match_mode, agg_mode, adapt, rank_gamma, tile;
-    double tau_mult, gamma, beta;
-    int64_t max_wait;
-};
 
 htsvd_status resolve(const htsvd_params* p, int C, Resolved& r) {
     htsvd_params z;
@@ -43,7 +38,7 @@ htsvd_status resolve(const htsvd_params* p, int C, Resolved& r) {
     r.beta = p->beta > 0 ? p->beta : 1.2;
     r.rank_gamma = p->rank_gamma > 0 ? p->rank_gamma : (13 * r.K + 16) / 32;
     r.tile = p->tile;
-    r.max_wait = p->max_wait_cycles > 0 ? p->max_wait_cycles : (int64_t)1 << 34;
+    r.strict_basis = p->strict_basis != 0 || p->h_basis_gap_out != nullptr;
     if (p->stride < 0 || p->window < 0 || p->K < 0 || p->ps < 0) return HTSVD_ERR_INVALID_ARG;
     if (p->tile < 0 || p->tile > 16) return HTSVD_ERR_INVALID_ARG;
     if (r.K < 2 || (r.K & (r.K - 1))) return HTSVD_ERR_INVALID_ARG;
@@ -71,6 +66,65 @@ int resolve_mode(const Resolved& r, int C) {
     }
 }
 
+// ----------------------------------------------------------------------------- tiling choices
+
+FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forced, int nfr) {
+    // Among the tiles whose shared memory lets two CTAs share an SM (228 KB, 1 KB reserved per
+    // CTA): the largest that still gives 8 waves of two CTAs per SM (the last, partial wave then
+    // costs little), else the largest with one such wave, else the largest that fits at all. A
+    // forced edge is taken as given if its shared memory fits a CTA (TR = 0 returned otherwise).
+    const int cands[] = {8, 7, 6, 5, 4, 3, 2, 1};
+    const int64_t nsm = device_sm_count();
+    FilterTiling fit2{}, fit1{}, wave1{};
+    bool have2 = false, have1 = false, havew = false;
+    if (forced > 0) {
+        FilterTiling t{};
+        t.TR = forced;
+        t.ntx = (g.nrx + forced - 1) / forced;
+        t.nty = (g.nry + forced - 1) / forced;
+        t.FHmax = std::min(g.H, (forced - 1) * g.s + g.wny + PS - 1);
+        t.FWmax = std::min(g.W, (forced - 1) * g.s + g.wnx + PS - 1);
+        FilterArgs fa{};
+        fa.g = g;
+        fa.FHmax = t.FHmax;
+        fa.FWmax = t.FWmax;
+        fa.img_is_float = in_bytes == 4;
+        fa.mode = mode;
+        fa.nfr = nfr;
+        if (filter_smem_bytes(fa) > 227 * 1024) t.TR = 0;
+        return t;
+    }
+    for (int TR : cands) {
+        FilterTiling t;
+        t.TR = TR;
+        t.ntx = (g.nrx + TR - 1) / TR;
+        t.nty = (g.nry + TR - 1) / TR;
+        t.FHmax = std::min(g.H, (TR - 1) * g.s + g.wny + PS - 1);
+        t.FWmax = std::min(g.W, (TR - 1) * g.s + g.wnx + PS - 1);
+        FilterArgs fa{};
+        fa.g = g;
+        fa.FHmax = t.FHmax;
+        fa.FWmax = t.FWmax;
+        fa.img_is_float = in_bytes == 4;
+        fa.mode = mode;
+        fa.nfr = nfr;
+        const size_t smem = filter_smem_bytes(fa);
+        if (smem <= 112 * 1024) {
+            const int64_t tiles = (int64_t)t.ntx * t.nty;
+            if (!have2) fit2 = t, have2 = true;
+            if (tiles >= 8 * 2 * nsm) return t;
+            if (tiles >= 2 * nsm && !havew) wave1 = t, havew = true;
+        } else if (smem <= 200 * 1024 && !have1) {
+            fit1 = t, have1 = true;
+        }
+    }
+    return havew ? wave1 : have2 ? fit2 : fit1;
+}
+
+}  // namespace htsvd
+
+namespace {
+
 // ----------------------------------------------------------------------------- workspace
 
 enum Slot {
@@ -78,6 +132,7 @@ enum Slot {
     S_AIN, S_AOUT,                   // S_AIN, S_AOUT: subimages of htsvd_denoise_adaptive
     S_COEF, S_CPN, S_CNRM,           // coefficient cache of htsvd_denoise_tau_sweep
     S_SOUT, S_SGX, S_SIDX, S_SRED,   // htsvd_sure: estimate, adjoint or perturbed image, grouping, sums
+    S_GAP,                           // eigen-gaps of the basis slices (strict mode)
     S_NSLOT
 };
 
@@ -217,64 +272,6 @@ struct HostProfScope {
         if (s_ != HTSVD_OK) return s_;      \
     } while (0)
 
-// ----------------------------------------------------------------------------- tiling choices
-
-struct FilterTiling {
-    int TR, ntx, nty, FHmax, FWmax;
-};
-
-FilterTiling choose_filter_tiling(const Geo& g, int in_bytes, int mode, int forced, int nfr = 1) {
-    // Among the tiles whose shared memory lets two CTAs share an SM (228 KB, 1 KB reserved per
-    // CTA): the largest that still gives 8 waves of two CTAs per SM (the last, partial wave then
-    // costs little), else the largest with one such wave, else the largest that fits at all. A
-    // forced edge is taken as given if its shared memory fits a CTA (TR = 0 returned otherwise).
-    const int cands[] = {8, 7, 6, 5, 4, 3, 2, 1};
-    FilterTiling fit2{}, fit1{}, wave1{};
-    bool have2 = false, have1 = false, havew = false;
-    if (forced > 0) {
-        FilterTiling t{};
-        t.TR = forced;
-        t.ntx = (g.nrx + forced - 1) / forced;
-        t.nty = (g.nry + forced - 1) / forced;
-        t.FHmax = std::min(g.H, (forced - 1) * g.s + g.wny + PS - 1);
-        t.FWmax = std::min(g.W, (forced - 1) * g.s + g.wnx + PS - 1);
-        FilterArgs fa{};
-        fa.g = g;
-        fa.FHmax = t.FHmax;
-        fa.FWmax = t.FWmax;
-        fa.img_is_float = in_bytes == 4;
-        fa.mode = mode;
-        fa.nfr = nfr;
-        if (filter_smem_bytes(fa) > 227 * 1024) t.TR = 0;
-        return t;
-    }
-    for (int TR : cands) {
-        FilterTiling t;
-        t.TR = TR;
-        t.ntx = (g.nrx + TR - 1) / TR;
-        t.nty = (g.nry + TR - 1) / TR;
-        t.FHmax = std::min(g.H, (TR - 1) * g.s + g.wny + PS - 1);
-        t.FWmax = std::min(g.W, (TR - 1) * g.s + g.wnx + PS - 1);
-        FilterArgs fa{};
-        fa.g = g;
-        fa.FHmax = t.FHmax;
-        fa.FWmax = t.FWmax;
-        fa.img_is_float = in_bytes == 4;
-        fa.mode = mode;
-        fa.nfr = nfr;
-        const size_t smem = filter_smem_bytes(fa);
-        if (smem <= 112 * 1024) {
-            const int64_t tiles = (int64_t)t.ntx * t.nty;
-            if (!have2) fit2 = t, have2 = true;
-            if (tiles >= 8 * 2 * 152) return t;
-            if (tiles >= 2 * 152 && !havew) wave1 = t, havew = true;
-        } else if (smem <= 200 * 1024 && !have1) {
-            fit1 = t, have1 = true;
-        }
-    }
-    return havew ? wave1 : have2 ? fit2 : fit1;
-}
-
 void choose_bm_tiles(const Geo& g, int rstep, int& TRy, int& TRx) {
     TRy = 4;
     TRx = 8;
@@ -346,7 +343,7 @@ double sigma_from_moments(const unsigned long long* M, const unsigned long long*
 // moment of the same references, already formed on this stream's predecessors) the row and
 // column moments are summed from it instead of re-read from the image.
 htsvd_status run_basis(Workspace* w, const uint8_t* q, const Geo& g, double** b64, float** b32, cudaStream_t s,
-                       const unsigned long long* fullM = nullptr) {
+                       const unsigned long long* fullM = nullptr, double* d_gap = nullptr) {
     void *mom, *p64, *p32;
     ST(ws_get(w, S_MOM, sizeof(unsigned long long) * 2 * PS2 * g.C * g.C, &mom));
     ST(ws_get(w, S_B64, sizeof(double) * 2 * 2 * g.C * PS2, &p64));
@@ -358,9 +355,24 @@ htsvd_status run_basis(Workspace* w, const uint8_t* q, const Geo& g, double** b6
         ProfScope ps_("moments", s);
         CK(launch_moments(q, g, (unsigned long long*)mom, s));
     }
-    { ProfScope ps_("basis", s); CK(launch_basis((const unsigned long long*)mom, g.C, (double*)p64, (float*)p32, s)); }
+    { ProfScope ps_("basis", s); CK(launch_basis((const unsigned long long*)mom, g.C, (double*)p64, (float*)p32, s, d_gap)); }
     *b64 = (double*)p64;
     *b32 = (float*)p32;
+    return HTSVD_OK;
+}
+
+// Strict-mode eigen-gap check: waits for the per-slice gaps of the basis solve (queued on s), writes
+// the smallest to p->h_basis_gap_out and fails with DEGENERATE_BASIS below kDegenerateGap when
+// p->strict_basis is set.
+htsvd_status check_basis_gap(const double* d_gap, int C, const htsvd_params* p, cudaStream_t s) {
+    double h[8];
+    const int n = basis_problems(C);
+    CK(cudaMemcpyAsync(h, d_gap, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double m = h[0];
+    for (int i = 1; i < n; ++i) m = std::min(m, h[i]);
+    if (p->h_basis_gap_out) *p->h_basis_gap_out = m;
+    if (p->strict_basis && !(m >= kDegenerateGap)) return HTSVD_ERR_DEGENERATE_BASIS;
     return HTSVD_OK;
 }
 
@@ -540,12 +552,15 @@ htsvd_status denoise_impl(const void* d_in, int is_float, int H, int W, int C, d
     float* b32;
     void* fullM = nullptr;
     if (sigma < 0) ST(ws_get(w, S_FULLM, sizeof(unsigned long long) * PS2 * C * PS2 * C, &fullM));
-    ST(run_basis(w, q, g, &b64, &b32, w->side, (const unsigned long long*)fullM));
+    void* gap = nullptr;
+    if (r.strict_basis) ST(ws_get(w, S_GAP, sizeof(double) * basis_problems(C), &gap));
+    ST(run_basis(w, q, g, &b64, &b32, w->side, (const unsigned long long*)fullM, (double*)gap));
     CK(cudaEventRecord(w->ev_join, w->side));
     ST(run_block_match(q, g, r, 1, idx, s));
     CK(cudaStreamWaitEvent(s, w->ev_join, 0));
     if (p && p->d_basis_out)
         CK(cudaMemcpyAsync(p->d_basis_out, b64, sizeof(double) * 2 * 2 * C * PS2, cudaMemcpyDeviceToDevice, s));
+    if (r.strict_basis) ST(check_basis_gap((const double*)gap, C, p, s));
     if (sigma < 0) {
         if (cudaEventSynchronize(hev.ev) != cudaSuccess) return HTSVD_ERR_CUDA;
         ST(finish_sigma(hbuf, g, r, &sigma));
@@ -1008,6 +1023,7 @@ const char* htsvd_status_string(htsvd_status s) {
         case HTSVD_ERR_CUDA: return "CUDA error";
         case HTSVD_ERR_OOM: return "out of memory";
         case HTSVD_ERR_TIMEOUT: return "device wait timed out";
+        case HTSVD_ERR_DEGENERATE_BASIS: return "degenerate basis: two eigenvalues of a basis slice coincide";
     }
     return "unknown status";
 }

@@ -253,7 +253,7 @@ htsvd_status enqueue(BatchCache* c, const Plan& P, cudaStream_t s, int phase_mas
     int* ctr = reinterpret_cast<int*>(d + L.ctr);
     BCK(cudaMemcpyAsync(d, c->hdesc, L.total, cudaMemcpyHostToDevice, s));
     BCK(cudaMemsetAsync(c->dev, 0, P.mom_bytes, s));
-    const int nsm = 152;
+    const int nsm = device_sm_count();
     BCK(cudaEventRecord(c->ev_fork, s));
     BCK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     if (phase_mask & 1) BCK(launch_moments_batch(P.C, dbm, dmom, pmom, P.n, std::min(P.p_mom[P.n], nsm * 8), c->side));

@@ -204,9 +204,28 @@ __global__ void perturb_kernel(const float* __restrict__ y, const float* __restr
 
 size_t sure_scratch_doubles() { return 2 * (size_t)SURE_BLOCKS; }
 
+int device_sm_count() {
+    constexpr int kMaxDev = 64;
+    static int cached[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (cached[dev] <= 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            return 1;
+        }
+        cached[dev] = n;          // benign race: every writer stores the same value
+    }
+    return cached[dev];
+}
+
 cudaError_t launch_perturb(const float* y, const float* b, float eps, int64_t n, float* z, cudaStream_t s) {
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
     if (blocks < 1) blocks = 1;
     perturb_kernel<<<(int)blocks, 256, 0, s>>>(y, b, eps, n, z);
     return cudaGetLastError();
@@ -238,7 +257,7 @@ cudaError_t launch_reduce(const float* partials, const Geo& g, int TR, int ntx, 
                           float* out, float* den_out, int num_only, const float* den_in, cudaStream_t s) {
     const int64_t npix = (int64_t)g.H * g.W;
     int blocks = (int)((npix + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
     if (g.C == 3)
         reduce_kernel<3><<<blocks, 256, 0, s>>>(partials, g, TR, ntx, nty, FHmax, FWmax, out, den_out, num_only, den_in);
     else
@@ -277,7 +296,7 @@ cudaError_t launch_reduce_batch(int C, const FilterArgs* d_args, float* const* d
 
 cudaError_t launch_div(const float* gout, const float* den, int64_t npix, int C, float* r, cudaStream_t s) {
     int blocks = (int)((npix * C + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
     div_kernel<<<blocks, 256, 0, s>>>(gout, den, npix, C, r);
     return cudaGetLastError();
 }

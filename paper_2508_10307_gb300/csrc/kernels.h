@@ -8,6 +8,10 @@ namespace htsvd {
 
 enum MatchMode { MM_GRAY = 0, MM_GCP = 1, MM_FULL = 2, MM_GREEN = 3 };
 
+// Streaming multiprocessors of the calling thread's current device (cudaDevAttrMultiProcessorCount,
+// looked up once per device); grids and wave counts are sized from it.
+int device_sm_count();
+
 // ---- block matching (bm.cu)
 struct BMArgs {
     const uint8_t* img;
@@ -45,8 +49,11 @@ cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long l
 // FP64 eigen-solve of the per-slice row/column scatter matrices -> canonical bases.
 //   basis64: [2 (U,V)][C][8][8] complex (re, im), slice f, row a, column i.
 //   basis32: packed float slices for the filter (U0r, [U1r, U1i], V0r, [V1r, V1i]), each [a][i].
+//   gap (optional): per solved problem (U slices f = 0 .. C/2, then V slices; basis_problems(C) of them)
+//   the smallest gap between consecutive eigenvalues relative to the largest eigenvalue.
+inline int basis_problems(int C) { return 2 * (C / 2 + 1); }
 cudaError_t launch_basis(const unsigned long long* d_mom, int C, double* d_basis64, float* d_basis32,
-                         cudaStream_t s);
+                         cudaStream_t s, double* d_gap = nullptr);
 // Quantise a float image: q = clip(rint(x), 0, 255).
 cudaError_t launch_quantize(const float* x, int64_t n, uint8_t* q, cudaStream_t s);
 

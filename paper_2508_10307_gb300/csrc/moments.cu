@@ -589,7 +589,8 @@ __device__ void jacobi_herm8_warp(double (*Ar)[PS], double (*Ai)[PS], double (*V
 
 // One warp per (U or V, slice f) problem w, f = 0 .. C/2; writes its slice of the outputs.
 __device__ __forceinline__ void basis_problem(const unsigned long long* __restrict__ mom, int C, int w,
-                                              double* __restrict__ b64, float* __restrict__ b32) {
+                                              double* __restrict__ b64, float* __restrict__ b32,
+                                              double* __restrict__ gap_out) {
     __shared__ double Res[PS][PS][2];
     __shared__ double work[4 * PS2];
     __shared__ double rot[5][10];
@@ -623,6 +624,12 @@ __device__ __forceinline__ void basis_problem(const unsigned long long* __restri
     jacobi_herm8_warp(Ar, Ai, Vr, Vi, rot, lane);
     __shared__ int order[PS];
     canonicalise_warp(Ar, Vr, Vi, Res, order, lane);
+    if (gap_out && lane == 0) {
+        // smallest gap between consecutive eigenvalues (descending order) relative to the largest
+        double gmin = fabs(Ar[order[0]][order[0]] - Ar[order[1]][order[1]]);
+        for (int i = 1; i + 1 < PS; ++i) gmin = fmin(gmin, fabs(Ar[order[i]][order[i]] - Ar[order[i + 1]][order[i + 1]]));
+        gap_out[w] = gmin / fmax(fabs(Ar[order[0]][order[0]]), 1e-300);
+    }
     // FP64 slice f (and its conjugate slice C - f) of U or V, and the packed FP32 copy used by the filter.
     for (int ai = lane; ai < PS2; ai += 32) {
         const double re = Res[ai / PS][ai % PS][0], im = Res[ai / PS][ai % PS][1];
@@ -645,8 +652,8 @@ __device__ __forceinline__ void basis_problem(const unsigned long long* __restri
 }
 
 __global__ void basis_kernel(const unsigned long long* __restrict__ mom, int C, double* __restrict__ b64,
-                             float* __restrict__ b32) {
-    basis_problem(mom, C, blockIdx.x, b64, b32);
+                             float* __restrict__ b32, double* __restrict__ gap) {
+    basis_problem(mom, C, blockIdx.x, b64, b32, gap);
 }
 
 // Batch form: block b -> image b / (2 (C/2 + 1)), problem b % (2 (C/2 + 1)).
@@ -655,7 +662,7 @@ __global__ void basis_batch_kernel(const FilterArgs* __restrict__ fargs, unsigne
     const int np = 2 * (C / 2 + 1);
     const int i = blockIdx.x / np;
     const FilterArgs& a = fargs[i];
-    basis_problem(moms[i], C, blockIdx.x % np, const_cast<double*>(a.basis64), const_cast<float*>(a.basis32));
+    basis_problem(moms[i], C, blockIdx.x % np, const_cast<double*>(a.basis64), const_cast<float*>(a.basis32), nullptr);
 }
 
 __global__ void quantize_kernel(const float* __restrict__ x, int64_t n, uint8_t* __restrict__ q) {
@@ -841,7 +848,7 @@ cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long l
     const int nt = (d + 63) / 64;
     const int ntiles = nt * (nt + 1) / 2;                       // tiles on and below the diagonal
     // chunks of whole staging batches, about four CTAs per SM in total
-    int nchunk = (4 * 152 + ntiles - 1) / ntiles;
+    int nchunk = (4 * device_sm_count() + ntiles - 1) / ntiles;
     const int nbatch = (n + FM_BATCH - 1) / FM_BATCH;
     if (nchunk > nbatch) nchunk = nbatch;
     int chunk = (nbatch + nchunk - 1) / nchunk * FM_BATCH;
@@ -852,8 +859,9 @@ cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long l
     return cudaGetLastError();
 }
 
-cudaError_t launch_basis(const unsigned long long* d_mom, int C, double* d_basis64, float* d_basis32, cudaStream_t s) {
-    basis_kernel<<<2 * (C / 2 + 1), 32, 0, s>>>(d_mom, C, d_basis64, d_basis32);
+cudaError_t launch_basis(const unsigned long long* d_mom, int C, double* d_basis64, float* d_basis32, cudaStream_t s,
+                         double* d_gap) {
+    basis_kernel<<<2 * (C / 2 + 1), 32, 0, s>>>(d_mom, C, d_basis64, d_basis32, d_gap);
     return cudaGetLastError();
 }
 

@@ -4,14 +4,17 @@
 // application whose own caching allocator has reserved the device memory (a library
 // allocating behind it can fail or fragment that pool), and latency-bound processing
 // loops in which the implicit device synchronisation of cudaFree would stall other
-// streams. This entry point runs the same kernels as htsvd_denoise but takes every
-// temporary buffer (match indices, moments, bases, tile partials) from one fixed array
-// in device memory that the library declares statically; it calls no allocator at all.
+// streams. This entry point runs the same kernels as htsvd_denoise, with the same parameter
+// checks and the same filter tiles (so the same output), but takes every temporary buffer
+// (match indices, moments, bases, eigen-gaps, tile partials) from one fixed array in device
+// memory that the library declares statically; it calls no allocator at all.
 #include <cmath>
 #include <cstring>
 #include <mutex>
 
 #include "../../include/htsvd.h"
+#include "../../include/htsvd_internal.h"
+#include "host_plan.h"
 #include "kernels.h"
 
 using namespace htsvd;
@@ -45,87 +48,121 @@ htsvd_status scratch_address(void** out) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-}  // namespace
+// Carve-up of the scratch array for one call (byte offsets), from the resolved parameters.
+struct Carve {
+    Geo g;
+    FilterTiling t;
+    size_t o_idx, o_mom, o_b64, o_b32, o_gap, o_part, total;
+};
 
-extern "C" htsvd_status htsvd_denoise_noalloc(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, double sigma,
-                                              const htsvd_params* p, float* d_out, cudaStream_t stream) {
-    if (!d_noisy || !d_out || !(sigma >= 0)) return HTSVD_ERR_INVALID_ARG;
-    htsvd_params z;
-    std::memset(&z, 0, sizeof(z));
-    if (!p) p = &z;
-    const int ps = p->ps > 0 ? p->ps : 8, s = p->stride > 0 ? p->stride : 3;
-    const int win = p->window > 0 ? p->window : 18, K = p->K > 0 ? p->K : 32;
-    if (p->ps < 0 || p->stride < 0 || p->window < 0 || p->K < 0) return HTSVD_ERR_INVALID_ARG;
-    if (K < 2 || (K & (K - 1)) || (C != 1 && C != 3) || H < ps || W < ps) return HTSVD_ERR_INVALID_ARG;
-    if (p->match_mode < 0 || p->match_mode > 3 || p->agg_mode < 0 || p->agg_mode > 1) return HTSVD_ERR_INVALID_ARG;
-    if (ps != PS || K > 32 || win > 64) return HTSVD_ERR_UNSUPPORTED;
-    const Geo g = make_geo(H, W, C, s, win, K);
-    if ((int64_t)g.wny * g.wnx < K) return HTSVD_ERR_INVALID_ARG;
-    const double gamma = p->gcp_gamma > 0 ? p->gcp_gamma : 1.2;
-    const double mult = p->tau_mult > 0 ? p->tau_mult : std::sqrt(2.0 * std::log((double)C * K * ps * ps));
-    const double tau = mult * sigma;
-
-    // Tile edge for the filter: the largest of these whose shared memory fits.
-    const int cands[] = {8, 6, 4, 2, 1};
-    FilterArgs fa{};
-    int TR = 1;
-    for (int c : cands) {
-        fa.g = g;
-        fa.FHmax = (c - 1) * s + g.wny + PS - 1 < H ? (c - 1) * s + g.wny + PS - 1 : H;
-        fa.FWmax = (c - 1) * s + g.wnx + PS - 1 < W ? (c - 1) * s + g.wnx + PS - 1 : W;
-        fa.img_is_float = 0;
-        fa.mode = FM_FORWARD;
-        if (filter_smem_bytes(fa) <= 200 * 1024) {
-            TR = c;
+htsvd_status plan(int H, int W, int C, const htsvd_params* p, Resolved& r, Carve& c) {
+    htsvd_status st = resolve(p, C, r);
+    if (st != HTSVD_OK) return st;
+    if ((st = check_image(H, W, C, r)) != HTSVD_OK) return st;
+    c.g = make_geo(H, W, C, r.s, r.win, r.K);
+    auto carve = [&](const FilterTiling& t) {
+        const size_t n = (size_t)c.g.ngroups();
+        size_t o = 0;
+        c.t = t;
+        c.o_idx = o; o += align256(sizeof(int32_t) * n * r.K);
+        c.o_mom = o; o += align256(sizeof(unsigned long long) * 2 * PS2 * C * C);
+        c.o_b64 = o; o += align256(sizeof(double) * 2 * 2 * C * PS2);
+        c.o_b32 = o; o += align256(sizeof(float) * 512);
+        c.o_gap = o; o += align256(sizeof(double) * basis_problems(C));
+        c.o_part = o; o += align256(sizeof(float) * (size_t)t.ntx * t.nty * t.FHmax * t.FWmax * (C == 3 ? 4 : 2));
+        c.total = o;
+    };
+    // the tiles of htsvd_denoise; if their partials do not fit the array (and no edge is forced), the
+    // largest edge whose shared memory fits a CTA (fewest overlapping footprints, smallest partials)
+    const FilterTiling t = choose_filter_tiling(c.g, 1, FM_FORWARD, r.tile);
+    if (t.TR == 0) return HTSVD_ERR_UNSUPPORTED;
+    carve(t);
+    if (c.total > kScratchBytes && r.tile == 0) {
+        for (int e = 16; e > t.TR; --e) {
+            const FilterTiling te = choose_filter_tiling(c.g, 1, FM_FORWARD, e);
+            if (te.TR == 0) continue;
+            carve(te);
             break;
         }
     }
-    const int ntx = (g.nrx + TR - 1) / TR, nty = (g.nry + TR - 1) / TR;
-    const int acc = C == 3 ? 4 : 2;
+    return HTSVD_OK;
+}
 
-    // Carve the scratch array; sizes beyond it are rejected before any device work.
-    const size_t n = (size_t)g.ngroups();
-    const size_t b_idx = align256(sizeof(int32_t) * n * K);
-    const size_t b_mom = align256(sizeof(unsigned long long) * 2 * PS2 * C * C);
-    const size_t b_b64 = align256(sizeof(double) * 2 * 2 * C * PS2);
-    const size_t b_b32 = align256(sizeof(float) * 512);
-    const size_t b_part = align256(sizeof(float) * (size_t)ntx * nty * fa.FHmax * fa.FWmax * acc);
-    if (b_idx + b_mom + b_b64 + b_b32 + b_part > kScratchBytes) return HTSVD_ERR_INVALID_ARG;
+}  // namespace
+
+extern "C" int64_t htsvd_internal_noalloc_bytes(int32_t H, int32_t W, int32_t C, const htsvd_params* p) {
+    Resolved r;
+    Carve c;
+    if (plan(H, W, C, p, r, c) != HTSVD_OK) return -1;
+    return (int64_t)c.total;
+}
+
+extern "C" htsvd_status htsvd_denoise_noalloc(const uint8_t* d_noisy, int32_t H, int32_t W, int32_t C, double sigma,
+                                              const htsvd_params* p, float* d_out, cudaStream_t stream) {
+    if (!d_noisy || !d_out || !(sigma >= 0) || std::isinf(sigma)) return HTSVD_ERR_INVALID_ARG;
+    Resolved r;
+    Carve c;
+    htsvd_status st = plan(H, W, C, p, r, c);
+    if (st != HTSVD_OK) return st;
+    // Sizes beyond the array are rejected before any device work.
+    if (c.total > kScratchBytes) return HTSVD_ERR_INVALID_ARG;
 
     void* base = nullptr;
-    htsvd_status st = scratch_address(&base);
-    if (st != HTSVD_OK) return st;
+    if ((st = scratch_address(&base)) != HTSVD_OK) return st;
     unsigned char* q = static_cast<unsigned char*>(base);
-    int32_t* idx = reinterpret_cast<int32_t*>(q);
-    unsigned long long* mom = reinterpret_cast<unsigned long long*>(q + b_idx);
-    double* b64 = reinterpret_cast<double*>(q + b_idx + b_mom);
-    float* b32 = reinterpret_cast<float*>(q + b_idx + b_mom + b_b64);
-    float* part = reinterpret_cast<float*>(q + b_idx + b_mom + b_b64 + b_b32);
+    int32_t* idx = reinterpret_cast<int32_t*>(q + c.o_idx);
+    unsigned long long* mom = reinterpret_cast<unsigned long long*>(q + c.o_mom);
+    double* b64 = reinterpret_cast<double*>(q + c.o_b64);
+    float* b32 = reinterpret_cast<float*>(q + c.o_b32);
+    double* gap = reinterpret_cast<double*>(q + c.o_gap);
+    float* part = reinterpret_cast<float*>(q + c.o_part);
+    const Geo& g = c.g;
 
     BMArgs ba{};
     ba.img = d_noisy;
     ba.g = g;
-    ba.mode = C == 1 ? MM_GRAY : (p->match_mode == HTSVD_MATCH_FULL ? MM_FULL
-                                  : p->match_mode == HTSVD_MATCH_GREEN ? MM_GREEN : MM_GCP);
-    ba.gamma2 = gamma * gamma;
+    ba.mode = resolve_mode(r, C);
+    ba.gamma2 = r.gamma * r.gamma;
     ba.rstep = 1;
     ba.nry_s = g.nry;
     ba.nrx_s = g.nrx;
     ba.TRy = 4;
     ba.TRx = 8;
     bm_fit_tiles(ba);
+    if (bm_smem_bytes(ba) > 227 * 1024) return HTSVD_ERR_UNSUPPORTED;
     ba.idx = idx;
     if (launch_block_match(ba, stream) != cudaSuccess) return HTSVD_ERR_CUDA;
     // launch_moments clears the moment accumulators (left over from the previous call) first.
     if (launch_moments(d_noisy, g, mom, stream) != cudaSuccess) return HTSVD_ERR_CUDA;
-    if (launch_basis(mom, C, b64, b32, stream) != cudaSuccess) return HTSVD_ERR_CUDA;
+    if (launch_basis(mom, C, b64, b32, stream, r.strict_basis ? gap : nullptr) != cudaSuccess) return HTSVD_ERR_CUDA;
+    if (p && p->d_basis_out &&
+        cudaMemcpyAsync(p->d_basis_out, b64, sizeof(double) * 2 * 2 * C * PS2, cudaMemcpyDeviceToDevice, stream) !=
+            cudaSuccess)
+        return HTSVD_ERR_CUDA;
+    if (r.strict_basis) {
+        // the gaps go to a host array on the stack (pageable memory: the copy completes before it returns)
+        double h[8];
+        const int n = basis_problems(C);
+        if (cudaMemcpyAsync(h, gap, sizeof(double) * n, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess)
+            return HTSVD_ERR_CUDA;
+        double m = h[0];
+        for (int i = 1; i < n; ++i) m = m < h[i] ? m : h[i];
+        if (p->h_basis_gap_out) *p->h_basis_gap_out = m;
+        if (p->strict_basis && !(m >= kDegenerateGap)) return HTSVD_ERR_DEGENERATE_BASIS;
+    }
+    if (p && p->h_sigma_out) *p->h_sigma_out = sigma;
 
+    const double tau = r.tau_mult * sigma;
+    FilterArgs fa{};
     fa.img = d_noisy;
     fa.img_is_float = 0;
     fa.g = g;
-    fa.TR = TR;
-    fa.ntx = ntx;
-    fa.nty = nty;
+    fa.TR = c.t.TR;
+    fa.ntx = c.t.ntx;
+    fa.nty = c.t.nty;
+    fa.FHmax = c.t.FHmax;
+    fa.FWmax = c.t.FWmax;
     fa.idx = idx;
     fa.basis32 = b32;
     fa.basis64 = b64;
@@ -134,11 +171,15 @@ extern "C" htsvd_status htsvd_denoise_noalloc(const uint8_t* d_noisy, int32_t H,
     fa.band_rel = kBandRel;
     fa.band_abs = (float)(tau * kBandTau) + 1e-6f;
     fa.w_in = nullptr;
-    fa.agg_mode = p->agg_mode;
+    fa.agg_mode = r.agg_mode;
     fa.partials = part;
     fa.mode = FM_FORWARD;
+    fa.mask_out = p ? p->d_mask_out : nullptr;
+    fa.weights_out = p ? p->d_weights_out : nullptr;
+    fa.coef_out = p ? p->d_coef_out : nullptr;
     if (launch_filter(fa, stream) != cudaSuccess) return HTSVD_ERR_CUDA;
-    if (launch_reduce(part, g, TR, ntx, nty, fa.FHmax, fa.FWmax, d_out, nullptr, 0, nullptr, stream) != cudaSuccess)
+    if (launch_reduce(part, g, c.t.TR, c.t.ntx, c.t.nty, c.t.FHmax, c.t.FWmax, d_out, nullptr, 0, nullptr, stream) !=
+        cudaSuccess)
         return HTSVD_ERR_CUDA;
     return HTSVD_OK;
 }

@@ -47,6 +47,29 @@ def test_status_strings():
     lib = H.load_library()
     assert lib.htsvd_status_string(0) == b"ok"
     assert lib.htsvd_status_string(1) == b"invalid argument"
+    assert b"degenerate" in lib.htsvd_status_string(6)
+    assert _lib.STATUS_NAMES[6] == "DEGENERATE_BASIS"
+
+
+def test_params_struct_matches_the_header():
+    # the ctypes mirror lists the header's fields in order (a mismatch would shift every later field)
+    src = open(os.path.join(ROOT, "include", "htsvd.h")).read()
+    body = re.sub(r"/\*.*?\*/", "", src[src.index("typedef struct htsvd_params {"):src.index("} htsvd_params;")],
+                  flags=re.S)
+    fields = re.findall(r"\b(\w+)\s*;", body)
+    assert fields == [f for f, _ in _lib.CParams._fields_]
+
+
+def test_noalloc_rejects_bad_arguments_on_the_host():
+    lib = H.load_library()
+    cp = H.HtsvdParams.of(dict(K=12)).c()
+    one = ctypes.c_void_p(1)
+    assert lib.htsvd_denoise_noalloc(one, 40, 40, 3, 10.0, ctypes.byref(cp), one, None) == 1
+    cp = H.HtsvdParams.of(None).c()
+    assert lib.htsvd_denoise_noalloc(one, 40, 40, 3, -1.0, ctypes.byref(cp), one, None) == 1   # sigma must be given
+    assert lib.htsvd_denoise_noalloc(one, 40, 40, 2, 10.0, ctypes.byref(cp), one, None) == 1
+    assert lib.htsvd_denoise_noalloc(None, 40, 40, 3, 10.0, ctypes.byref(cp), one, None) == 1
+    assert lib.htsvd_internal_noalloc_bytes(40, 40, 2, ctypes.byref(cp)) == -1
 
 
 def _call_denoise(H_, W_, C, params, ptr=1):

@@ -261,3 +261,24 @@ def test_fp32_coefficient_error_is_well_inside_the_guard_band(key):
     worst_m = float((err.max(axis=2) / nrm_m).max())
     assert worst <= BAND_REL / 4, f"max |S32 - S64| / ||G|| = {worst:.3e}"
     assert worst_m <= BAND_REL / 4, f"max |S32 - S64| / ||G_m|| = {worst_m:.3e}"
+
+
+def test_strict_basis_rejects_a_constant_image_like_the_oracle():
+    img = np.full((40, 48, 3), 77, np.uint8)
+    prm = dict(ps=8, stride=3, window=9, K=8, strict_basis=True)
+    with pytest.raises(O.DegenerateBasis):
+        O.denoise(img, 25.0, prm)
+    from paper_2508_10307_gb300 import _lib
+    with pytest.raises(_lib.DegenerateBasisError):
+        H.denoise(_dev(img), 25.0, prm)
+    out = H.denoise(_dev(img), 25.0, dict(prm, strict_basis=False)).cpu().numpy()   # default mode runs
+    assert max_abs(out, 77.0) <= 1e-3
+
+
+@pytest.mark.parametrize("key", ["gray128", "rgb512"])
+def test_basis_gap_matches_the_oracle(key):
+    clean, noisy, sigma, prm, r = oracle_run(key)
+    out, info = H.denoise(_dev(noisy), sigma, dict(prm, strict_basis=True), return_info=True, basis_gap=True)
+    torch.cuda.synchronize()
+    want = r.extra["basis_gap"]
+    assert want > 1e-9 and abs(info["basis_gap"] - want) <= 1e-6 * want

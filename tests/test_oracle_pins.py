@@ -261,6 +261,36 @@ def test_constant_image_is_fixed_point():
     np.testing.assert_allclose(r.out, 77.0, atol=1e-9)
 
 
+def test_strict_basis_raises_on_coinciding_eigenvalues():
+    """Reading R7: a constant image has rank-one slice scatter matrices (seven eigenvalues 0 in slice 0,
+    all eight 0 in the colour slice), so its eigenvectors are not unique; strict mode refuses it, the
+    default mode runs."""
+    img = np.full((24, 24, 3), 77, dtype=np.uint8)
+    prm = dict(ps=8, stride=3, window=9, K=8)
+    with pytest.raises(O.DegenerateBasis):
+        O.denoise(img, 25.0, dict(prm, strict_basis=True))
+    r = O.denoise(img, 25.0, prm)
+    assert r.extra["basis_gap"] == 0.0
+    U, V, lu, lv = O.global_basis(O.reference_patches(img, O.Params.of(prm)))
+    assert np.count_nonzero(np.abs(lu[0]) > 1e-6 * lu[0].max()) == 1
+
+
+def test_basis_gap_of_a_noisy_image_is_far_from_degenerate():
+    """Distinct eigenvalues: the gap equals the smallest spacing of the textbook (numpy eigvalsh)
+    eigenvalues of the row and column scatter matrices of a gray image (C = 1 reduces the t-SVD to
+    the 2-D SVD), and it is far above the 1e-9 threshold."""
+    clean = synth.clean_image(64, 64, 1, 9)
+    img = synth.add_gaussian(clean, 20.0, 9)
+    p = O.Params.of(dict(ps=8, stride=3, window=9, K=8))
+    P = O.reference_patches(img, p)[..., 0].astype(np.float64)
+    A = np.einsum("nab,ncb->ac", P, P)
+    B = np.einsum("nab,nac->bc", P, P)
+    want = min(O.basis_gap(np.linalg.eigvalsh(A)), O.basis_gap(np.linalg.eigvalsh(B)))
+    r = O.denoise(img, 20.0, dict(ps=8, stride=3, window=9, K=8, strict_basis=True))
+    assert abs(r.extra["basis_gap"] - want) <= 1e-9 * want
+    assert r.extra["basis_gap"] > 1e-6
+
+
 def test_aggregation_denominator_counts_covering_patches():
     noisy = synth.add_gaussian(synth.clean_image(20, 22, 1, 4), 20.0, 4)
     p = O.Params(ps=4, stride=3, window=7, K=4)
