@@ -311,6 +311,16 @@ def make_workload(name):
         return Workload(name, workload_config("rgb4k"), 3 * 3840 * 2160 / 1e6, 3 * n, 3, 32, noisy,
                         lambda d: [H.denoise(x, b, prm) for x, b in zip(d, levels)],
                         3 * 3840 * 2160 * 3 * 4), synth.quantize(clean)
+    if name == "rgb1080":
+        # one image of the headline's geometry at a quarter of its size: the small case that ncu captures
+        clean = synth.clean_image(1080, 1920, 3, 1003)
+        noisy = synth.add_poisson_gaussian(clean, 0.01, 25.0 ** 2, 1003)
+        prm = dict(ps=8, stride=3, window=31, K=32)
+        cfg = {"workload": "rgb1920x1080_pg_b625", "image": "1920x1080x3 uint8", "noise": "poisson-gaussian a=0.01 b=25^2",
+               "sigma": "given (25)", "ps": 8, "stride": 3, "window": 31, "K": 32,
+               "groups_per_image": H.num_groups(1080, 1920, prm)}
+        return Workload(name, cfg, 1920 * 1080 / 1e6, H.num_groups(1080, 1920, prm), 3, 32, [noisy],
+                        lambda d: [H.denoise(d[0], 25.0, prm)], 1920 * 1080 * 3 * 4), synth.quantize(clean)
     if name == "batch64":
         shapes = synth.batch_shapes(64)
         imgs, sig, cleans = [], [], []
@@ -587,7 +597,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="rgb4k", choices=["rgb512", "gray128", "rgb4k", "batch64", "vjp8", "adaptive512",
+    ap.add_argument("--workload", default="rgb4k", choices=["rgb512", "gray128", "rgb4k", "rgb1080", "batch64", "vjp8", "adaptive512",
                                                       "video1080", "sweep512", "sure512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

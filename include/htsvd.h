@@ -100,6 +100,8 @@ typedef struct htsvd_image {
     int32_t H, W, C;
     double sigma;          /* noise level; must be >= 0 in a batch */
     float* d_out;          /* H x W x C float32 */
+    int32_t* d_idx_out;    /* optional (may be NULL): N_groups x K int32 match indices of this image, as the
+                              d_idx_out of htsvd_denoise (the batch then groups into this buffer) */
 } htsvd_image;
 
 /* Alg. 1 (Haar-tSVD) on a uint8 image.

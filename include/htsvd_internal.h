@@ -47,6 +47,11 @@ double htsvd_internal_sigma_from_moments(const unsigned long long* M, const unsi
 int32_t htsvd_internal_sampled_ranks(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const htsvd_params* p,
                                      int32_t* h_ranks, int32_t max_ranks);
 
+/* Tile edge (references per tile side) that the forward filter of htsvd_denoise takes for an H x W x C
+ * uint8 image with parameters p on the current device (it follows the SM count), or -1 on bad
+ * arguments. Host only; launches nothing. */
+int32_t htsvd_internal_filter_tile(int32_t H, int32_t W, int32_t C, const htsvd_params* p);
+
 /* Bytes of the static scratch array that htsvd_denoise_noalloc would use for an H x W x C image
  * with parameters p on the current device (the filter tiles depend on its SM count), or -1 when
  * the arguments fail the checks of htsvd_denoise. Host only; launches nothing. */

@@ -197,8 +197,9 @@ def estimate_sigma(noisy, params=None, stream=None) -> float:
     return s.value
 
 
-def denoise_batch(images, sigmas, params=None, outs=None, stream=None):
-    """Denoises a list of uint8 (H, W, C) CUDA tensors of any sizes with per-image sigma."""
+def denoise_batch(images, sigmas, params=None, outs=None, stream=None, idx_outs=None):
+    """Denoises a list of uint8 (H, W, C) CUDA tensors of any sizes with per-image sigma.
+    idx_outs: optional list of int32 (N_groups, K) CUDA tensors that receive each image's grouping."""
     lib = _lib.load()
     torch = _torch()
     imgs = [_hwc(t) for t in images]
@@ -214,13 +215,20 @@ def denoise_batch(images, sigmas, params=None, outs=None, stream=None):
         raise ValueError(f"denoise_batch: {len(imgs)} images but {len(outs)} outputs")
     for i, (t, o) in enumerate(zip(imgs, outs)):
         _need(o if o.dim() == 3 else o.unsqueeze(-1), f"outs[{i}]", t.shape, torch.float32, t)
+    p = HtsvdParams.of(params)
+    if idx_outs is not None:
+        if len(idx_outs) != len(imgs):
+            raise ValueError(f"denoise_batch: {len(imgs)} images but {len(idx_outs)} index buffers")
+        for i, (t, ix) in enumerate(zip(imgs, idx_outs)):
+            _need(ix, f"idx_outs[{i}]", (num_groups(t.shape[0], t.shape[1], p), p.K), torch.int32, t)
     arr = (_lib.CImage * len(imgs))()
     for i, (t, s, o) in enumerate(zip(imgs, sigmas, outs)):
         arr[i].d_in = t.data_ptr()
         arr[i].H, arr[i].W, arr[i].C = t.shape
         arr[i].sigma = float(s)
         arr[i].d_out = o.data_ptr()
-    cp = HtsvdParams.of(params).c()
+        arr[i].d_idx_out = idx_outs[i].data_ptr() if idx_outs is not None else None
+    cp = p.c()
     _lib.check(lib.htsvd_denoise_batch(arr, len(imgs), ctypes.byref(cp), _stream_ptr(stream)),
                "htsvd_denoise_batch")
     return outs

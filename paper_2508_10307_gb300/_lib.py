@@ -49,6 +49,7 @@ class CImage(ctypes.Structure):
         ("C", ctypes.c_int32),
         ("sigma", ctypes.c_double),
         ("d_out", ctypes.c_void_p),
+        ("d_idx_out", ctypes.c_void_p),
     ]
 
 
@@ -88,6 +89,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                ctypes.POINTER(ctypes.c_double), vp]
     lib.htsvd_internal_alu_probe.argtypes = [i32, i32]
     lib.htsvd_internal_alu_probe.restype = ctypes.c_double
+    lib.htsvd_internal_filter_tile.argtypes = [i32, i32, i32, P]
+    lib.htsvd_internal_filter_tile.restype = i32
     lib.htsvd_internal_noalloc_bytes.argtypes = [i32, i32, i32, P]
     lib.htsvd_internal_noalloc_bytes.restype = ctypes.c_int64
     lib.htsvd_num_groups.argtypes = [i32, i32, P]

@@ -769,6 +769,12 @@ int32_t htsvd_internal_sampled_ranks(const uint8_t* d_img, int32_t H, int32_t W,
     return n;
 }
 
+int32_t htsvd_internal_filter_tile(int32_t H, int32_t W, int32_t C, const htsvd_params* p) {
+    Resolved r;
+    if (resolve(p, C, r) != HTSVD_OK || check_image(H, W, C, r) != HTSVD_OK) return -1;
+    return choose_filter_tiling(make_geo(H, W, C, r.s, r.win, r.K), 1, FM_FORWARD, r.tile).TR;
+}
+
 double htsvd_internal_sigma_from_moments(const unsigned long long* M, const unsigned long long* S, int d, int64_t n,
                                          double* lam) {
     if (!M || !S || d < 1 || n < 1) return -1.0;

@@ -167,6 +167,7 @@ htsvd_status make_plan(const htsvd_image* imgs, int n, const htsvd_params* p, co
         unsigned long long* mom = base ? reinterpret_cast<unsigned long long*>(base + P.mom_bytes) : nullptr;
         P.mom_bytes += b_mom;
         b.idx = base ? reinterpret_cast<int32_t*>(base + off) : nullptr;
+        if (base && im.d_idx_out) b.idx = im.d_idx_out;          // the caller's buffer holds the grouping
         f.idx = b.idx;
         f.basis64 = base ? reinterpret_cast<double*>(base + off + b_idx) : nullptr;
         f.basis32 = base ? reinterpret_cast<float*>(base + off + b_idx + b_b64) : nullptr;
@@ -188,7 +189,7 @@ htsvd_status make_plan(const htsvd_image* imgs, int n, const htsvd_params* p, co
     if (base) {
         for (int i = 0; i < n; ++i) {
             auto sh = [&](auto* q) { return reinterpret_cast<decltype(q)>(reinterpret_cast<unsigned char*>(q) + P.mom_bytes); };
-            P.bm[i].idx = sh(P.bm[i].idx);
+            if (!imgs[i].d_idx_out) P.bm[i].idx = sh(P.bm[i].idx);
             P.fa[i].idx = P.bm[i].idx;
             P.fa[i].basis64 = sh(const_cast<double*>(P.fa[i].basis64));
             P.fa[i].basis32 = sh(const_cast<float*>(P.fa[i].basis32));

@@ -76,18 +76,33 @@ __host__ __device__ inline FLayout f_layout(int FH, int FW, int in_bytes, int mo
 }
 
 // Shared-memory layout of the pipelined forward filter: two group buffers (group q+1 is projected
-// while group q is inverted and aggregated), three position and counter sets, no band bitmaps.
+// while group q is inverted and aggregated), three position and counter sets, no band bitmaps. The
+// fixed part's offsets are compile-time constants (FwdOff), so the kernel addresses it without
+// holding a register per array.
+template <int K, int C>
+struct FwdOff {
+    static constexpr int bas = 0;                                   // basis rows, then the transposed copies
+    static constexpr int gb = bas + 2 * 384 * 4;
+    static constexpr int pos = gb + 2 * K * FCfg<C>::GS * 4;         // positions of three groups (q, q+1, q+2)
+    static constexpr int band = pos + 3 * 64 * 4;                    // per-patch squared norms, two groups
+    static constexpr int nz = band + 2 * 32 * 4;                     // basis-row masks per Haar slot, two groups
+    static constexpr int dlist = nz + 2 * 32 * 4;                    // stage-D work list (256 entries)
+    static constexpr int dcount = dlist + 256;
+    static constexpr int misc = dcount + 16;                         // counters of three groups
+    static constexpr int acc = misc + 3 * 16 * 4;
+};
 template <int K, int C>
 __host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes, int nfr = 1) {
     using G = FCfg<C>;
+    using O = FwdOff<K, C>;
     FLayout L;
-    int o = 0;
-    L.off_bas = o; o += 2 * 384 * 4;           // basis rows, then the transposed copies
-    L.off_gb = o; o += 2 * K * G::GS * 4;
-    L.off_pos = o; o += 3 * 64 * 4;            // positions of three groups (q, q+1, q+2)
-    L.off_band = o; o += 2 * 32 * 4;           // per-patch squared norms of the two groups in flight
-    L.off_rkeep = o;
-    L.off_misc = o; o += 3 * 16 * 4;
+    int o = O::acc;
+    L.off_bas = O::bas;
+    L.off_gb = O::gb;
+    L.off_pos = O::pos;
+    L.off_band = O::band;
+    L.off_rkeep = O::nz;
+    L.off_misc = O::misc;
     L.off_acc = o; o += FH * FW * G::ACC * 4;
     L.off_img = o; o += (nfr * FH * FW * C * in_bytes + 15) / 16 * 16;   // footprints of nfr frames, stacked
     L.off_r = o;
@@ -687,164 +702,144 @@ __device__ __forceinline__ void stage_b2(const float* bas, float* gb, int k, int
     }
 }
 
-// Stage D, two rows (channel DFT, Z_f[i, :] = T_f[i, :] V_f^H), outer-product order.
+// Stage D for one row of a Haar slot in the sparse inverse: thread -> Z_f[i, :] = T_f[i, :] V_f^H of
+// slot k, in place on row i. Same terms and order as stage D, but the row is streamed two columns at
+// a time (load6) and the outer column loop stays rolled, so that the transposed basis rows are not
+// all loaded ahead (with them the kernel outgrew its 128 registers).
 template <int C>
-__device__ __forceinline__ void stage_d2(const float* bas, float* gb, int k, int p) {
+__device__ __forceinline__ void stage_d_row(const float* bas, float* gb, int k, int i) {
     using G = FCfg<C>;
-    const int r0 = row_pair_first(p);
-    float* rows[2] = {gb + k * G::GS + r0 * G::ROW, gb + k * G::GS + (r0 + 2) * G::ROW};
+    float* row = gb + k * G::GS + i * G::ROW;
     const float* bt = bas + G::NBAS;
     if constexpr (C == 3) {
-        float z0[2][PS], zr[2][PS], zi[2][PS];
+        float z0[PS], zr[PS], zi[PS];
 #pragma unroll
-        for (int w = 0; w < 2; ++w)
-#pragma unroll
-            for (int b = 0; b < PS; ++b) z0[w][b] = zr[w][b] = zi[w][b] = 0.f;
+        for (int b = 0; b < PS; ++b) z0[b] = zr[b] = zi[b] = 0.f;
 #pragma unroll 1
         for (int jj2 = 0; jj2 < PS / 2; jj2 += 2)
 #pragma unroll
         for (int par = 0; par < 2; ++par) {
             const int jj = jj2 + par;
-            float t[2][6];
-            load6(rows[0], jj, par, t[0]);
-            load6(rows[1], jj, par, t[1]);
+            float t[6];
+            load6(row, jj, par, t);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = 2 * jj + h;
-                float T0[2], T1r[2], T1i[2];
-#pragma unroll
-                for (int w = 0; w < 2; ++w) {
-                    const float t0 = t[w][3 * h], t1 = t[w][3 * h + 1], t2 = t[w][3 * h + 2];
-                    T0[w] = t0 + t1 + t2;
-                    T1r[w] = t0 - 0.5f * (t1 + t2);
-                    T1i[w] = F_S3H * (t2 - t1);
-                }
+                const float T0 = t[3 * h] + t[3 * h + 1] + t[3 * h + 2];
+                const float T1r = t[3 * h] - 0.5f * (t[3 * h + 1] + t[3 * h + 2]);
+                const float T1i = F_S3H * (t[3 * h + 2] - t[3 * h + 1]);
                 float v0[8], vr[8], vi[8];
                 load8(bt + 192 + j * PS, v0);
                 load8(bt + 256 + j * PS, vr);
                 load8(bt + 320 + j * PS, vi);
 #pragma unroll
-                for (int b = 0; b < PS; ++b)
-#pragma unroll
-                    for (int w = 0; w < 2; ++w) {
-                        z0[w][b] = fmaf(T0[w], v0[b], z0[w][b]);
-                        zr[w][b] = fmaf(T1r[w], vr[b], fmaf(T1i[w], vi[b], zr[w][b]));
-                        zi[w][b] = fmaf(T1i[w], vr[b], fmaf(-T1r[w], vi[b], zi[w][b]));
-                    }
+                for (int b = 0; b < PS; ++b) {
+                    z0[b] = fmaf(T0, v0[b], z0[b]);
+                    zr[b] = fmaf(T1r, vr[b], fmaf(T1i, vi[b], zr[b]));
+                    zi[b] = fmaf(T1i, vr[b], fmaf(-T1r, vi[b], zi[b]));
+                }
             }
         }
+        float4* r4 = reinterpret_cast<float4*>(row);
 #pragma unroll
-        for (int w = 0; w < 2; ++w) {
-            float4* r4 = reinterpret_cast<float4*>(rows[w]);
+        for (int q = 0; q < G::RWF / 4; ++q) {
+            float o[4];
 #pragma unroll
-            for (int q = 0; q < G::RWF / 4; ++q) {
-                float o[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int n = 4 * q + e, b = n / 3, c = n % 3;
-                    o[e] = c == 0 ? z0[w][b] : (c == 1 ? zr[w][b] : zi[w][b]);
-                }
-                r4[q] = make_float4(o[0], o[1], o[2], o[3]);
+            for (int e = 0; e < 4; ++e) {
+                const int n = 4 * q + e, b = n / 3, c = n % 3;
+                o[e] = c == 0 ? z0[b] : (c == 1 ? zr[b] : zi[b]);
             }
+            r4[q] = make_float4(o[0], o[1], o[2], o[3]);
         }
     } else {
-        float t[2][PS], o[2][PS];
-#pragma unroll
-        for (int w = 0; w < 2; ++w) {
-            load8(rows[w], t[w]);
-#pragma unroll
-            for (int b = 0; b < PS; ++b) o[w][b] = 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < PS; ++j) {
-            float v0[8];
-            load8(bt + 64 + j * PS, v0);
-#pragma unroll
-            for (int b = 0; b < PS; ++b)
-#pragma unroll
-                for (int w = 0; w < 2; ++w) o[w][b] = fmaf(t[w][j], v0[b], o[w][b]);
-        }
-#pragma unroll
-        for (int w = 0; w < 2; ++w) {
-            float4* r4 = reinterpret_cast<float4*>(rows[w]);
-            r4[0] = make_float4(o[w][0], o[w][1], o[w][2], o[w][3]);
-            r4[1] = make_float4(o[w][4], o[w][5], o[w][6], o[w][7]);
-        }
+        stage_d<C>(bas, gb, k, i);
     }
 }
 
-// Stage E, two columns (G_f[:, b] = U_f Z_f[:, b], inverse channel DFT), outer-product order.
+// Sparse form of stage E for the inverse of one Haar slot: thread (k, b) -> G_f[:, b] = U_f Z_f[:, b],
+// summing only over the basis rows i set in nzrows (the other rows of Z are zero), then the inverse
+// channel DFT, written in place on column b of slot k. Terms are added in ascending i as in stage E,
+// so the result equals stage E on the same slot bit for bit.
 template <int C>
-__device__ __forceinline__ void stage_e2(const float* bas, float* gb, int k, int p) {
+__device__ __forceinline__ void stage_e_sparse(const float* bas, float* gb, int k, int b, uint32_t nzrows) {
     using G = FCfg<C>;
-    float* col = gb + k * G::GS + 2 * p * C;
+    float* col = gb + k * G::GS + b * C;
     const float* bt = bas + G::NBAS;
     if constexpr (C == 3) {
-        float g0[2][PS], gr[2][PS], gi[2][PS];
+        float g0[PS], gr[PS], gi[PS];
 #pragma unroll
-        for (int w = 0; w < 2; ++w)
-#pragma unroll
-            for (int a = 0; a < PS; ++a) g0[w][a] = gr[w][a] = gi[w][a] = 0.f;
+        for (int a = 0; a < PS; ++a) g0[a] = gr[a] = gi[a] = 0.f;
 #pragma unroll 1
-        for (int i = 0; i < PS; ++i) {
-            const float2* z2 = reinterpret_cast<const float2*>(col + i * G::ROW);
-            const float2 za = z2[0], zb = z2[1], zc = z2[2];
-            const float Z0[2] = {za.x, zb.y}, Zr[2] = {za.y, zc.x}, Zi[2] = {zb.x, zc.y};
+        for (uint32_t m = nzrows; m; m &= m - 1) {
+            const int i = __ffs(m) - 1;
+            const float Z0 = col[i * G::ROW], Zr = col[i * G::ROW + 1], Zi = col[i * G::ROW + 2];
             float u0[8], ur[8], ui[8];
             load8(bt + i * PS, u0);
             load8(bt + 64 + i * PS, ur);
             load8(bt + 128 + i * PS, ui);
 #pragma unroll
-            for (int a = 0; a < PS; ++a)
-#pragma unroll
-                for (int w = 0; w < 2; ++w) {
-                    g0[w][a] = fmaf(u0[a], Z0[w], g0[w][a]);
-                    gr[w][a] = fmaf(ur[a], Zr[w], fmaf(-ui[a], Zi[w], gr[w][a]));
-                    gi[w][a] = fmaf(ur[a], Zi[w], fmaf(ui[a], Zr[w], gi[w][a]));
-                }
+            for (int a = 0; a < PS; ++a) {
+                g0[a] = fmaf(u0[a], Z0, g0[a]);
+                gr[a] = fmaf(ur[a], Zr, fmaf(-ui[a], Zi, gr[a]));
+                gi[a] = fmaf(ur[a], Zi, fmaf(ui[a], Zr, gi[a]));
+            }
         }
 #pragma unroll
         for (int a = 0; a < PS; ++a) {
-            float o[6];
-#pragma unroll
-            for (int w = 0; w < 2; ++w) {
-                o[3 * w + 0] = (g0[w][a] + 2.f * gr[w][a]) * F_THIRD;
-                o[3 * w + 1] = (g0[w][a] - gr[w][a] - F_SQ3 * gi[w][a]) * F_THIRD;
-                o[3 * w + 2] = (g0[w][a] - gr[w][a] + F_SQ3 * gi[w][a]) * F_THIRD;
-            }
-            float2* d = reinterpret_cast<float2*>(col + a * G::ROW);
-            d[0] = make_float2(o[0], o[1]);
-            d[1] = make_float2(o[2], o[3]);
-            d[2] = make_float2(o[4], o[5]);
+            col[a * G::ROW + 0] = (g0[a] + 2.f * gr[a]) * F_THIRD;
+            col[a * G::ROW + 1] = (g0[a] - gr[a] - F_SQ3 * gi[a]) * F_THIRD;
+            col[a * G::ROW + 2] = (g0[a] - gr[a] + F_SQ3 * gi[a]) * F_THIRD;
         }
     } else {
-        float g0[2][PS];
+        float g0[PS];
 #pragma unroll
-        for (int w = 0; w < 2; ++w)
-#pragma unroll
-            for (int a = 0; a < PS; ++a) g0[w][a] = 0.f;
+        for (int a = 0; a < PS; ++a) g0[a] = 0.f;
 #pragma unroll 1
-        for (int i = 0; i < PS; ++i) {
-            const float2 z = *reinterpret_cast<const float2*>(col + i * G::ROW);
+        for (uint32_t m = nzrows; m; m &= m - 1) {
+            const int i = __ffs(m) - 1;
+            const float Z = col[i * G::ROW];
             float u0[8];
             load8(bt + i * PS, u0);
 #pragma unroll
-            for (int a = 0; a < PS; ++a) {
-                g0[0][a] = fmaf(u0[a], z.x, g0[0][a]);
-                g0[1][a] = fmaf(u0[a], z.y, g0[1][a]);
-            }
+            for (int a = 0; a < PS; ++a) g0[a] = fmaf(u0[a], Z, g0[a]);
         }
 #pragma unroll
-        for (int a = 0; a < PS; ++a)
-            *reinterpret_cast<float2*>(col + a * G::ROW) = make_float2(g0[0][a], g0[1][a]);
+        for (int a = 0; a < PS; ++a) col[a * G::ROW] = g0[a];
     }
 }
 
+// Fibre of virtual warp vw, lane l in the Haar stages: the vw-th fibre (in patch-row order) whose
+// group-buffer column falls on bank l, so the 32 fibres a warp handles use 32 distinct banks (each
+// bank holds NF/32 fibres: the rows start ROW words apart and cover RWF words). -1 if none.
+template <int C>
+__device__ __forceinline__ int bank_fibre(int vw, int lane) {
+    using G = FCfg<C>;
+    for (int i = 0, cnt = 0; i < PS; ++i) {
+        const int e = (lane - G::ROW * i) & 31;
+        if (e < G::RWF) {
+            if (cnt == vw) return i * G::RWF + e;
+            ++cnt;
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void bar_sync_lower_half() {       // warps 0 .. 3 only (named barrier 1)
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
 // Forward filter of one tile, software-pipelined over its groups with two CTA barriers per group:
-// [D, E(q) on the first half of the CTA | A, B(q+1) on the second half] then [F(q) aggregation,
-// C(q+1) Haar/threshold/synthesis]. Group buffers alternate; positions and counters rotate over
-// three slots (those of q+2 are written while q and q+1 are in flight). Guard-band entries are
-// re-decided in FP64 by the warp that owns the fibre (no CTA barrier).
+// [inverse of q on the first half of the CTA | A, B(q+1) on the second half] then [F(q) aggregation
+// on all warps, C(q+1) Haar analysis and threshold]. The inverse runs in the Haar domain: the Haar
+// transform along the group mode and the per-patch t-SVD projection commute, so C leaves the
+// thresholded coefficients of every Haar slot in place (scaled for the unnormalised synthesis) and
+// records which basis rows of each slot hold a kept coefficient; the first half then applies stage D
+// to those rows only (a compacted work list), stage E summing over those rows only, and the Haar
+// synthesis per fibre, separated by a named barrier of its four warps. After the threshold most
+// slots keep coefficients in two or three basis rows, so this inverse does a fraction of the dense
+// one's work and gives the same values up to rounding order; the forward half then sets the pace. Group buffers alternate; positions and
+// counters rotate over three slots (those of q+2 are written while q and q+1 are in flight).
+// Guard-band entries are re-decided in FP64 by the warp that owns the fibre (no CTA barrier).
 // MF: video groups (FM_VIDEO). The footprints of the clip's frames f0 .. f0 + nfr - 1 are staged
 // one above the other, the reference frame's first (slot 0, rows [0, FH)), the others after it in
 // frame order; a patch's staged row is slot * FH + its row in the footprint, so every stage reads
@@ -870,12 +865,16 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     const int FH = FY1 - FY0, FW = FX1 - FX0;
     const int nfr = MF ? a.nfr : 1;
     const FLayout L = f_layout_fwd<K, C>(a.FHmax, a.FWmax, (int)sizeof(Tin), nfr);
-    float* bas = reinterpret_cast<float*>(smem + L.off_bas);
-    float* gbb = reinterpret_cast<float*>(smem + L.off_gb);
-    int* posb = reinterpret_cast<int*>(smem + L.off_pos);
-    int* miscb = reinterpret_cast<int*>(smem + L.off_misc);
-    float* pnb = reinterpret_cast<float*>(smem + L.off_band);
-    float* acc = reinterpret_cast<float*>(smem + L.off_acc);
+    using O = FwdOff<K, C>;
+    float* bas = reinterpret_cast<float*>(smem + O::bas);
+    float* gbb = reinterpret_cast<float*>(smem + O::gb);
+    int* posb = reinterpret_cast<int*>(smem + O::pos);
+    int* miscb = reinterpret_cast<int*>(smem + O::misc);
+    float* pnb = reinterpret_cast<float*>(smem + O::band);
+    uint32_t* nzb = reinterpret_cast<uint32_t*>(smem + O::nz);                // [2][32] basis-row masks
+    unsigned char* dlist = smem + O::dlist;                                  // stage-D work list (k << 3 | i)
+    int* dcount = reinterpret_cast<int*>(smem + O::dcount);
+    float* acc = reinterpret_cast<float*>(smem + O::acc);
     Tin* img_s = reinterpret_cast<Tin*>(smem + L.off_img);
     // frame of staging slot sl (slot 0: the reference frame, then the others in order)
     auto slot_frame = [&](int sl) {
@@ -923,6 +922,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     auto pn_of = [&](int q) { return pnb + (q & 1) * 32; };
     auto pos_of = [&](int q) { return posb + (q % 3) * 64; };
     auto misc_of = [&](int q) { return miscb + (q % 3) * 16; };
+    auto nz_of = [&](int q) { return nzb + (q & 1) * 32; };
     // A, B of group q by thread u < NU of the second half; ||G||_F^2 into misc[5] (uint8, exact) or
     // misc[2] (float), and the squared norm of each patch into pn[k]
     auto project = [&](int u, int q) {
@@ -954,17 +954,52 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     // (each bank holds NF/32 fibres: the rows start ROW words apart and cover RWF words).
     int fib = -1, foff = 0;
     if (tid < NF) {
-        for (int i = 0, cnt = 0; i < PS && fib < 0; ++i) {
-            const int e = (lane - G::ROW * i) & 31;
-            if (e < G::RWF) {
-                if (cnt == warp) fib = i * G::RWF + e;
-                ++cnt;
-            }
-        }
+        fib = bank_fibre<C>(warp, lane);
         foff = (fib / G::RWF) * G::ROW + (fib % G::RWF);
     }
     auto clear_masks = [&](int q) {                     // mask words of group q, before its C phase
         if (a.mask_out && tid < NBW) a.mask_out[(size_t)group_of(q) * NBW + tid] = 0u;
+    };
+
+    // F(q): aggregation of group q's estimated patches into the footprint accumulator; the calling warp
+    // adds footprint rows r with r % 8 in {vw0, vw0 + vstep, ...} (no atomics: one warp per row class,
+    // patches in ascending order)
+    auto aggregate = [&](const int q, const int vw0, const int vstep) {
+        const int grp = group_of(q);
+        const float* gbq = gb_of(q);
+        const int* pos = pos_of(q);
+        const int* misc = misc_of(q);
+        float wg = 1.f;
+        if (a.w_in) wg = a.w_in[grp];
+        else if (a.agg_mode == 1) wg = 1.f / (float)max(1, misc[1]);
+        if (tid == 0 && a.weights_out) a.weights_out[grp] = wg;
+#pragma unroll 1
+        for (int vw = vw0; vw < 8; vw += vstep) {
+            // lane k precomputes, for patch k, the offsets of the row that this warp adds (its footprint
+            // row r has r % 8 == vw) in the accumulator and in the group buffer; the loop broadcasts them.
+            // Lane roles: C = 3: 24 numerator lanes (pixel j, channel c) and 8 weight lanes; C = 1: 8 and 8.
+            int my_aoff = 0, my_goff = 0;
+            if (lane < K) {
+                const int py = pos[2 * lane], px = pos[2 * lane + 1];
+                const int i = (vw - py) & 7;
+                my_aoff = ((py + i) * FW + px) * G::ACC;
+                my_goff = lane * G::GS + i * G::ROW;
+                if (MF && py >= FH) my_aoff = -1;     // a patch of another frame: not aggregated here
+            }
+            constexpr int NV = PS * C;                // numerator lanes
+            const bool num = lane < NV, act = lane < NV + PS;
+            const int lofs = num ? (lane / C) * G::ACC + (lane % C) : (lane - NV) * G::ACC + C;
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) {
+                const int aoff = __shfl_sync(0xffffffffu, my_aoff, k);
+                const int goff = __shfl_sync(0xffffffffu, my_goff, k);
+                if (act && (!MF || aoff >= 0)) {
+                    const float x = num ? gbq[goff + lane] : 1.f;
+                    acc[aoff + lofs] += wg * x;
+                }
+                __syncwarp();                         // orders the read-modify-writes of patches k, k+1
+            }
+        }
     };
 
     // C(q): Haar analysis, threshold (FP64 inside the guard band), synthesis, by the NF fibre threads
@@ -985,6 +1020,11 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
             }
             const int wk = __reduce_add_sync(0xffffffffu, __popc(keepb));
             if (lane == 0) atomicAdd(&misc[1], wk);
+        };
+        // basis row of this fibre into the masks of the Haar slots where it kept a coefficient
+        auto mark_rows = [&](uint32_t nzs) {
+            uint32_t* nz = nz_of(q);
+            for (uint32_t b = nzs; b; b &= b - 1) atomicOr(&nz[__ffs(b) - 1], 1u << (fib / G::RWF));
         };
         if constexpr (VAR == 1) {                     // per-patch norms and ||G||_F^2 of the group
             if (tid < K) a.cache_pn[(size_t)grp * 32 + tid] = pn[tid];
@@ -1046,12 +1086,15 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 anyb = __ballot_sync(0xffffffffu, bandb != 0u);
                 if (!anyb) {
                     keep_finish(keepb);
+                    uint32_t nzs = 0;
                     haar_for_each<K>([&](int m, int sl, int L) {
-                        v[sl] = ((keepb >> m) & 1u) ? v[sl] * (1.f / (float)L) : 0.f;
+                        const bool kp = (keepb >> m) & 1u;
+                        v[sl] = kp ? v[sl] * (1.f / (float)L) : 0.f;
+                        nzs |= (kp ? 1u : 0u) << sl;
                     });
-                    haar_inv_sum<K>(v);
 #pragma unroll
                     for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = v[k];
+                    mark_rows(nzs);
                 } else {
 #pragma unroll
                     for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = v[k];    // park the coefficients
@@ -1076,34 +1119,84 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 float w[K];
 #pragma unroll
                 for (int k = 0; k < K; ++k) w[k] = gbq[k * G::GS + foff];
+                uint32_t nzs = 0;
                 haar_for_each<K>([&](int m, int sl, int L) {
-                    w[sl] = ((keepb >> m) & 1u) ? w[sl] * (1.f / (float)L) : 0.f;
+                    const bool kp = (keepb >> m) & 1u;
+                    w[sl] = kp ? w[sl] * (1.f / (float)L) : 0.f;
+                    nzs |= (kp ? 1u : 0u) << sl;
                 });
-                haar_inv_sum<K>(w);
 #pragma unroll
                 for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = w[k];
+                mark_rows(nzs);
             }
         }
     };
 
-    // iteration q: [D, E(q) | A, B(q+1)] then [F(q), C(q+1)]; q = -1 only projects and thresholds group 0
+    // iteration q: [inverse of q: D, E, Haar synthesis | A, B(q+1)] then [F(q), C(q+1)]; q = -1 only
+    // projects and thresholds group 0
     store_pos(fetch_idx(0), pos_of(0));
     if (tid < 48) miscb[tid] = 0;
+    // fibres of the synthesis stage: the first half's warps take the bank-mapped fibres of virtual
+    // warps w and w + 4 (NF / 32 of them: 6 for C = 3, 2 for C = 1)
+    const int fibA = bank_fibre<C>(warp & 3, lane), fibB = bank_fibre<C>((warp & 3) + 4, lane);
+    const int foffA = fibA < 0 ? 0 : (fibA / G::RWF) * G::ROW + (fibA % G::RWF);
+    const int foffB = fibB < 0 ? 0 : (fibB / G::RWF) * G::ROW + (fibB % G::RWF);
     __syncthreads();
 
     for (int q = -1; q < ngr; ++q) {
         // indices of group q+2: loaded here, stored at the end of the second phase
         const int next_idx = q + 2 < ngr ? fetch_idx(q + 2) : 0;
 
-        // ---- D, E(q) (inverse projection) on the first half | A, B(q+1) on the second half
-        if (q >= 0 && tid < NU) {
-            if constexpr (VAR != 1) {
+        // ---- inverse of group q on the first half (warps 0-3, named barrier 1) ...
+        if constexpr (VAR != 1) {
+            if (q >= 0 && tid < 128) {
                 float* gbq = gb_of(q);
-                stage_d2<C>(bas, gbq, tid >> 2, tid & 3);
-                __syncwarp(kU);
-                stage_e2<C>(bas, gbq, tid >> 2, tid & 3);
+                const uint32_t* nz = nz_of(q);
+                // stage-D work list: the (Haar slot k, basis row i) pairs holding a kept coefficient
+                if (warp == 0) {
+                    const uint32_t msk = lane < K ? nz[lane] : 0u;
+                    const int c = __popc(msk);
+                    int incl = c;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += t;
+                    }
+                    int o = incl - c;
+                    for (uint32_t b = msk; b; b &= b - 1) dlist[o++] = (unsigned char)((lane << 3) | (__ffs(b) - 1));
+                    if (lane == 31) *dcount = incl;
+                }
+                bar_sync_lower_half();
+                const int nd = *dcount;
+#pragma unroll 1
+                for (int it = tid; it < nd; it += 128) {
+                    const int e = dlist[it];
+                    stage_d_row<C>(bas, gbq, e >> 3, e & 7);
+                }
+                bar_sync_lower_half();
+#pragma unroll 1
+                for (int u = tid; u < K * PS; u += 128) {
+                    const uint32_t rows = nz[u >> 3];
+                    if (rows) stage_e_sparse<C>(bas, gbq, u >> 3, u & 7, rows);   // slots without a kept
+                }                                                               // coefficient stay zero
+                bar_sync_lower_half();
+                // Haar synthesis along the group mode, per fibre
+#pragma unroll 1
+                for (int pass = 0; pass < 2; ++pass) {
+                    if (((warp & 3) + 4 * pass) * 32 >= NF) break;               // warp-uniform
+                    const int fo = pass == 0 ? foffA : foffB;
+                    float v[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) v[k] = gbq[k * G::GS + fo];
+                    haar_inv_sum<K>(v);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) gbq[k * G::GS + fo] = v[k];
+                }
+                bar_sync_lower_half();
             }
-        } else if (tid >= AB0 && tid < AB0 + NU && q + 1 < ngr) {
+        }
+        // ... beside A, B(q+1) on the second half
+        if (tid >= AB0 && tid < AB0 + NU && q + 1 < ngr) {
             if constexpr (VAR == 2) {
                 // the cached coefficients of group q+1, four fibres per 128-bit word (64 C fibres per
                 // slot; a run of four never crosses a patch row)
@@ -1121,47 +1214,13 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 project(tid - AB0, q + 1);
             }
         }
-        if (q + 1 < ngr) clear_masks(q + 1);
-        __syncthreads();
-        if (VAR != 1 && q >= 0) {
-            const int grp = group_of(q);
-            const float* gbq = gb_of(q);
-            const int* pos = pos_of(q);
-            const int* misc = misc_of(q);
-            // ---- F(q): aggregation (warp `warp` owns footprint rows r with r % 8 == warp) ...
-            float wg = 1.f;
-            if (a.w_in) wg = a.w_in[grp];
-            else if (a.agg_mode == 1) wg = 1.f / (float)max(1, misc[1]);
-            if (tid == 0 && a.weights_out) a.weights_out[grp] = wg;
-            {
-                // lane k precomputes, for patch k, the offsets of the row that this warp adds (its
-                // footprint row r has r % 8 == warp) in the accumulator and in the group buffer; the
-                // loop broadcasts them. Lane roles: C = 3: 24 numerator lanes (pixel j, channel c) and
-                // 8 weight lanes; C = 1: 8 and 8.
-                int my_aoff = 0, my_goff = 0;
-                if (lane < K) {
-                    const int py = pos[2 * lane], px = pos[2 * lane + 1];
-                    const int i = (warp - py) & 7;
-                    my_aoff = ((py + i) * FW + px) * G::ACC;
-                    my_goff = lane * G::GS + i * G::ROW;
-                    if (MF && py >= FH) my_aoff = -1;     // a patch of another frame: not aggregated here
-                }
-                constexpr int NV = PS * C;                // numerator lanes
-                const bool num = lane < NV, act = lane < NV + PS;
-                const int lofs = num ? (lane / C) * G::ACC + (lane % C) : (lane - NV) * G::ACC + C;
-#pragma unroll 4
-                for (int k = 0; k < K; ++k) {
-                    const int aoff = __shfl_sync(0xffffffffu, my_aoff, k);
-                    const int goff = __shfl_sync(0xffffffffu, my_goff, k);
-                    if (act && (!MF || aoff >= 0)) {
-                        const float x = num ? gbq[goff + lane] : 1.f;
-                        acc[aoff + lofs] += wg * x;
-                    }
-                    __syncwarp();                         // orders the read-modify-writes of patches k, k+1
-                }
-            }
+        if (q + 1 < ngr) {
+            clear_masks(q + 1);
+            if (tid >= AB0 && tid < AB0 + 32) nz_of(q + 1)[tid - AB0] = 0u;
         }
-        // ... then C(q+1); positions and counters of q+2 into the slot that q-1 used
+        __syncthreads();
+        if (VAR != 1 && q >= 0) aggregate(q, warp, 8);
+        // ---- C(q+1); positions and counters of q+2 into the slot that q-1 used
         if (q + 1 < ngr) phase_c(q + 1);
         if (q + 2 < ngr) {
             store_pos(next_idx, pos_of(q + 2));
