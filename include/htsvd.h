@@ -205,6 +205,23 @@ htsvd_status htsvd_denoise_adaptive(const uint8_t* d_noisy, int32_t H, int32_t W
 htsvd_status htsvd_denoise_batch(const htsvd_image* h_imgs, int32_t n, const htsvd_params* p,
                                  cudaStream_t stream);
 
+/* Alg. 1 on a hyperspectral cube (Sec. III-E, extension to other imaging; Sec. IV, real-world HSI
+ * denoising): a patch is a ps x ps x N tube and the t-SVD runs along the band mode (N Fourier
+ * slices); tau = tau_mult * sigma with tau_mult <= 0 meaning sqrt(2 ln(N K ps^2)).
+ * d_cube: H x W x N uint8, band-interleaved (pixel-major) on the [0, 255] scale (DEVICE); N in [2, 64].
+ * sigma: the noise level (>= 0, finite; the paper's band-mean estimate goes through its CNN, so it is
+ * an input here). Grouping takes the SSD summed over all bands (exact integers; the paper is silent
+ * on matching for cubes): match_mode must be AUTO or FULL.
+ * d_out: H x W x N float32 (DEVICE). d_idx_out (DEVICE, may be NULL): N_groups x K int32 indices as
+ * in htsvd_denoise. Optional outputs of p are honoured (d_mask_out: ceil(K 64 N / 32) words per group;
+ * d_coef_out: K 64 N floats per group; d_basis_out: 2 N 64 complex values). The aggregation adds
+ * with float atomics, so repeated calls agree to rounding rather than bit for bit.
+ * Errors: INVALID_ARG for a null pointer, N outside [2, 64], H or W < ps, a negative or non-finite
+ * sigma, a match mode other than AUTO or FULL, or a search window with fewer than K positions;
+ * UNSUPPORTED when H W N reaches 2^31. */
+htsvd_status htsvd_denoise_cube(const uint8_t* d_cube, int32_t H, int32_t W, int32_t N, double sigma,
+                                const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t stream);
+
 /* Vector-Jacobian product of htsvd_denoise_f32 at x with the grouping (d_idx), the
  * global bases, tau and the threshold masks held fixed (masks are recomputed at x).
  * d_w: per-group weights used by the forward (NULL = all ones); d_out: the forward's

@@ -12,7 +12,7 @@ from dataclasses import dataclass, fields
 from . import _lib
 
 __all__ = ["HtsvdParams", "denoise", "denoise_f32", "estimate_sigma", "denoise_batch", "denoise_adaptive",
-           "denoise_video", "denoise_tau_sweep", "sure", "denoise_vjp", "num_groups", "HtsvdFn", "load_library"]
+           "denoise_video", "denoise_cube", "denoise_tau_sweep", "sure", "denoise_vjp", "num_groups", "HtsvdFn", "load_library"]
 
 _MATCH = {"auto": 0, "gcp": 1, "full": 2, "green": 3}
 _AGG = {"uniform": 0, "sparsity": 1}
@@ -258,6 +258,30 @@ def denoise_adaptive(noisy, sub=(256, 256), params=None, *, return_sigmas=False,
     _lib.check(lib.htsvd_denoise_adaptive(_ptr(x), H, W, C, int(sub[0]), int(sub[1]), ctypes.byref(cp), _ptr(out),
                                           sig, _stream_ptr(stream)), "htsvd_denoise_adaptive")
     return (out, [float(v) for v in sig]) if return_sigmas else out
+
+
+def denoise_cube(cube, sigma, params=None, *, return_info=False, masks=False, weights=False, basis=False,
+                 coeffs=False, stream=None):
+    """Alg. 1 on a hyperspectral uint8 (H, W, N) CUDA tensor (N bands, 2..64) at the given sigma; the
+    t-SVD runs along the band mode. Returns the float32 (H, W, N) estimate, or (estimate, info)."""
+    lib = _lib.load()
+    x = _hwc(cube)
+    if x.dtype != _torch().uint8:
+        raise TypeError("denoise_cube expects uint8")
+    p = HtsvdParams.of(params)
+    cp = p.c()
+    out, idx, info = _outputs(x, p, cp, return_info, masks, weights, False, coeffs)
+    H, W, N = x.shape
+    if basis:
+        info["basis"] = _torch().empty((2, N, 8, 8, 2), dtype=_torch().float64, device=x.device)
+        cp.d_basis_out = info["basis"].data_ptr()
+    st = lib.htsvd_denoise_cube(_ptr(x), H, W, N, float(sigma), ctypes.byref(cp), _ptr(out), _ptr(idx),
+                                _stream_ptr(stream))
+    _lib.check(st, "htsvd_denoise_cube")
+    if return_info:
+        info.update(idx=idx)
+        return out, info
+    return out
 
 
 def denoise_video(frames, sigma=None, params=None, *, T=1, return_info=False, stream=None):

@@ -14,7 +14,7 @@ HTSVD_ERR_DEGENERATE_BASIS = 6
 EXPORTED = ["htsvd_denoise", "htsvd_denoise_f32", "htsvd_estimate_sigma", "htsvd_denoise_batch",
             "htsvd_denoise_vjp", "htsvd_num_groups", "htsvd_status_string", "htsvd_release_workspace",
             "htsvd_profile_enable", "htsvd_profile_collect", "htsvd_denoise_noalloc", "htsvd_denoise_adaptive",
-            "htsvd_denoise_video", "htsvd_denoise_tau_sweep", "htsvd_sure"]
+            "htsvd_denoise_video", "htsvd_denoise_tau_sweep", "htsvd_sure", "htsvd_denoise_cube"]
 
 
 class CParams(ctypes.Structure):
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.htsvd_denoise_batch.argtypes = [ctypes.POINTER(CImage), i32, P, vp]
     lib.htsvd_denoise_vjp.argtypes = [vp, i32, i32, i32, dbl, P, vp, vp, vp, vp, vp, vp, vp]
     lib.htsvd_denoise_noalloc.argtypes = [vp, i32, i32, i32, dbl, P, vp, vp]
+    lib.htsvd_denoise_cube.argtypes = [vp, i32, i32, i32, dbl, P, vp, vp, vp]
     lib.htsvd_denoise_adaptive.argtypes = [vp, i32, i32, i32, i32, i32, P, vp, ctypes.POINTER(ctypes.c_double), vp]
     lib.htsvd_denoise_video.argtypes = [vp, i32, i32, i32, i32, i32, dbl, P, vp, vp, ctypes.POINTER(ctypes.c_double),
                                         vp]
@@ -105,7 +106,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.htsvd_profile_collect.restype = i32
     for name in ["htsvd_denoise", "htsvd_denoise_f32", "htsvd_estimate_sigma", "htsvd_denoise_batch",
                  "htsvd_denoise_vjp", "htsvd_release_workspace", "htsvd_denoise_noalloc", "htsvd_denoise_adaptive",
-                 "htsvd_denoise_video", "htsvd_denoise_tau_sweep", "htsvd_sure"]:
+                 "htsvd_denoise_video", "htsvd_denoise_tau_sweep", "htsvd_sure", "htsvd_denoise_cube"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

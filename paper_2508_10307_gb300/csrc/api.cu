@@ -133,6 +133,7 @@ enum Slot {
     S_COEF, S_CPN, S_CNRM,           // coefficient cache of htsvd_denoise_tau_sweep
     S_SOUT, S_SGX, S_SIDX, S_SRED,   // htsvd_sure: estimate, adjoint or perturbed image, grouping, sums
     S_GAP,                           // eigen-gaps of the basis slices (strict mode)
+    S_CSCR, S_CNUM, S_CDEN,          // hyperspectral cubes: per-CTA Haar slots, numerator, denominator
     S_NSLOT
 };
 
@@ -365,9 +366,9 @@ htsvd_status run_basis(Workspace* w, const uint8_t* q, const Geo& g, double** b6
 // the smallest to p->h_basis_gap_out and fails with DEGENERATE_BASIS below kDegenerateGap when
 // p->strict_basis is set.
 htsvd_status check_basis_gap(const double* d_gap, int C, const htsvd_params* p, cudaStream_t s) {
-    double h[8];
     const int n = basis_problems(C);
-    CK(cudaMemcpyAsync(h, d_gap, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    std::vector<double> h((size_t)n);
+    CK(cudaMemcpyAsync(h.data(), d_gap, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     double m = h[0];
     for (int i = 1; i < n; ++i) m = std::min(m, h[i]);
@@ -1011,6 +1012,81 @@ htsvd_status htsvd_sure(const float* d_y, int32_t H, int32_t W, int32_t C, doubl
         const double div = fd ? (t[3] - t[1]) / eps : t[1];
         h_sure[i] = t[0] / (double)n - sigma * sigma + 2.0 * sigma * sigma / (double)n * div;
     }
+    return HTSVD_OK;
+}
+
+htsvd_status htsvd_denoise_cube(const uint8_t* d_cube, int32_t H, int32_t W, int32_t N, double sigma,
+                                const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t s) {
+    if (!d_cube || !d_out || !(sigma >= 0) || std::isinf(sigma)) return HTSVD_ERR_INVALID_ARG;
+    if (N < 2 || N > 64) return HTSVD_ERR_INVALID_ARG;
+    Resolved r;
+    ST(resolve(p, N, r));
+    if (r.match_mode != HTSVD_MATCH_AUTO && r.match_mode != HTSVD_MATCH_FULL) return HTSVD_ERR_INVALID_ARG;
+    if (H < r.ps || W < r.ps) return HTSVD_ERR_INVALID_ARG;
+    if ((int64_t)H * W * N >= ((int64_t)1 << 31)) return HTSVD_ERR_UNSUPPORTED;
+    const Geo g = make_geo(H, W, N, r.s, r.win, r.K);
+    if ((int64_t)g.wny * g.wnx < r.K) return HTSVD_ERR_INVALID_ARG;
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    const int64_t ng = g.ngroups();
+    int32_t* idx = d_idx_out;
+    if (!idx) {
+        void* ib;
+        ST(ws_get(w, S_IDX, sizeof(int32_t) * ng * r.K, &ib));
+        idx = (int32_t*)ib;
+    }
+    void *mom, *p64, *p32, *gap = nullptr, *scr, *num, *den;
+    ST(ws_get(w, S_MOM, sizeof(unsigned long long) * 2 * PS2 * N * N, &mom));
+    ST(ws_get(w, S_B64, sizeof(double) * 2 * 2 * N * PS2, &p64));
+    ST(ws_get(w, S_B32, sizeof(float) * basis32_floats(N), &p32));
+    if (r.strict_basis) ST(ws_get(w, S_GAP, sizeof(double) * basis_problems(N), &gap));
+    const int grid = cube_grid(N, r.K, ng);
+    ST(ws_get(w, S_CSCR, sizeof(float) * (size_t)grid * r.K * PS2 * N, &scr));
+    ST(ws_get(w, S_CNUM, sizeof(float) * (size_t)H * W * N, &num));
+    ST(ws_get(w, S_CDEN, sizeof(float) * (size_t)H * W, &den));
+    if (cube_smem_bytes(N, r.K) > 227 * 1024) return HTSVD_ERR_UNSUPPORTED;
+    // grouping: SSD over all bands (reading of the paper's silence on matching for cubes)
+    BMArgs ba{};
+    ba.img = d_cube;
+    ba.g = g;
+    ba.mode = MM_FULL;
+    ba.gamma2 = r.gamma * r.gamma;
+    ba.rstep = 1;
+    ba.nry_s = g.nry;
+    ba.nrx_s = g.nrx;
+    choose_bm_tiles(g, 1, ba.TRy, ba.TRx);
+    bm_fit_tiles(ba);
+    if (bm_smem_bytes(ba) > 227 * 1024) return HTSVD_ERR_UNSUPPORTED;
+    ba.idx = idx;
+    { ProfScope ps_("block_match", s); CK(launch_block_match(ba, s)); }
+    { ProfScope ps_("moments", s); CK(launch_cube_moments(d_cube, g, (unsigned long long*)mom, s)); }
+    { ProfScope ps_("basis", s);
+      CK(launch_basis((const unsigned long long*)mom, N, (double*)p64, (float*)p32, s, (double*)gap)); }
+    if (p && p->d_basis_out)
+        CK(cudaMemcpyAsync(p->d_basis_out, p64, sizeof(double) * 2 * 2 * N * PS2, cudaMemcpyDeviceToDevice, s));
+    if (r.strict_basis) ST(check_basis_gap((const double*)gap, N, p, s));
+    if (p && p->h_sigma_out) *p->h_sigma_out = sigma;
+    const double tau = r.tau_mult * sigma;
+    CubeArgs a{};
+    a.img = d_cube;
+    a.g = g;
+    a.idx = idx;
+    a.basis32 = (const float*)p32;
+    a.basis64 = (const double*)p64;
+    a.tau32 = (float)tau;
+    a.tau64 = tau;
+    a.band_rel = kBandRelCube;
+    a.band_abs = (float)(tau * kBandTau) + 1e-6f;
+    a.w_in = nullptr;
+    a.agg_mode = r.agg_mode;
+    a.scratch = (float*)scr;
+    a.num = (float*)num;
+    a.den = (float*)den;
+    a.out = d_out;
+    a.mask_out = p ? p->d_mask_out : nullptr;
+    a.weights_out = p ? p->d_weights_out : nullptr;
+    a.coef_out = p ? p->d_coef_out : nullptr;
+    { ProfScope ps_("cube_filter", s); CK(launch_cube_filter(a, grid, s)); }
     return HTSVD_OK;
 }
 

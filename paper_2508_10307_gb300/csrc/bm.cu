@@ -48,7 +48,7 @@ __device__ inline Region bm_region(const BMArgs& a, int iy0, int iy1, int ix0, i
 
 __host__ __device__ inline int byte_planes(int mode, int C) {
     if (C == 1) return 1;
-    return mode == MM_FULL ? 3 : 1;       // gray | G (green and GCP) | R, G, B (full)
+    return mode == MM_FULL ? C : 1;       // gray | G (green and GCP) | every channel or band (full)
 }
 __host__ __device__ inline bool uses_sum_plane(int mode, int C) { return C == 3 && mode == MM_GCP; }
 __host__ __device__ inline int bytes_pitch(int w) { return ((w + BM_PAD) + 3) & ~3; }
@@ -251,6 +251,91 @@ __device__ __forceinline__ void match_bytes(const BMArgs& a, const Region& Rg, c
     }
 }
 
+// Many byte planes (the bands of a hyperspectral cube, SSD over all of them): as match_bytes, but
+// with the plane loop outermost inside each strip chunk, so that only one plane's reference rows
+// are held in registers (the cross terms of all planes add into the same accumulators; every
+// partial sum stays below 2^31 for up to 500 planes: 64 x 255^2 per plane).
+template <int R>
+__device__ __forceinline__ void match_bytes_n(const BMArgs& a, const Region& Rg, const uint8_t* bp,
+                                              const uint8_t* rbp, int P8, const int* svv, int srr,
+                                              const RefCtx& c, Select& S, int lane, unsigned koff, bool self,
+                                              int nb) {
+    const Geo& g = a.g;
+    const int qpr = (g.wnx + 3) / 4, G = 32 / qpr;
+    const int sg = lane / qpr, q = lane - sg * qpr;
+    const bool active = sg < G;
+    const int cx0 = 4 * q;
+    const int sh = 8 * (c.ox & 3);
+    const int last_row = g.wny + PS - 2;
+    const int nch = (g.wny + G * R - 1) / (G * R);
+    for (int ch = 0; ch < nch; ++ch) {
+        const int cy0 = (ch * G + sg) * R;
+        const bool run = active && cy0 < g.wny;
+        uint32_t acc[R][4];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) acc[k][s] = 0u;
+        if (run) {
+#pragma unroll 1
+            for (int p = 0; p < nb; ++p) {
+                uint32_t rw[PS][2];
+                const uint8_t* rpl = rbp + (size_t)p * Rg.h * P8;
+#pragma unroll
+                for (int i = 0; i < PS; ++i) {
+                    const int bo = (c.ry - Rg.y0 + i) * P8 + (c.rx - Rg.x0);
+                    const uint32_t* wp = reinterpret_cast<const uint32_t*>(rpl + (bo & ~3));
+                    const int u = 8 * (bo & 3);
+                    const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
+                    rw[i][0] = __funnelshift_r(w0, w1, u);
+                    rw[i][1] = __funnelshift_r(w1, w2, u);
+                }
+                const uint8_t* pl = bp + (size_t)p * Rg.h * P8;
+#pragma unroll
+                for (int t = 0; t < R + PS - 1; ++t) {
+                    const int rr = min(cy0 + t, last_row);
+                    const uint32_t* wp =
+                        reinterpret_cast<const uint32_t*>(pl + (((c.oy + rr) * P8 + c.ox + cx0) & ~3));
+                    const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2], w3 = wp[3];
+                    const uint32_t a0 = __funnelshift_r(w0, w1, sh);
+                    const uint32_t a1 = __funnelshift_r(w1, w2, sh);
+                    const uint32_t a2 = __funnelshift_r(w2, w3, sh);
+                    uint32_t lo[4], hi[4];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        lo[s] = s == 0 ? a0 : __funnelshift_r(a0, a1, 8 * s);
+                        hi[s] = s == 0 ? a1 : __funnelshift_r(a1, a2, 8 * s);
+                    }
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        const int i = t - k;
+                        if (i < 0 || i >= PS) continue;
+#pragma unroll
+                        for (int s = 0; s < 4; ++s) {
+                            acc[k][s] = __dp4a(lo[s], rw[i][0], acc[k][s]);
+                            acc[k][s] = __dp4a(hi[s], rw[i][1], acc[k][s]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int cy = cy0 + k, cx = cx0 + s;
+                unsigned long long key = ~0ull;
+                if (run && cy < g.wny && cx < g.wnx) {
+                    const int py = c.wy0 + cy, px = c.wx0 + cx;
+                    if (!self || py != c.ry || px != c.rx)
+                        key = make_key(svv[(c.oy + cy) * c.wv + c.ox + cx] + srr - 2 * (int)acc[k][s], py, px, g.W,
+                                       koff);
+                }
+                sel_offer(S, key, g.K, lane);
+            }
+    }
+}
+
 // R+G+B plane: exact cross terms from FP32 partial sums over two reference rows.
 // sp, svv2: the candidate frame's R+G+B plane and box sums; rsp, srr: the reference frame's plane
 // and the reference's box sum; koff, self as for the byte planes.
@@ -330,7 +415,9 @@ __device__ __forceinline__ void match_sum_plane(const BMArgs& a, const Region& R
 // Grouping of one tile (by, bx) of references; bsm: bm_smem_bytes(a) of shared memory.
 // MF: spatio-temporal search over a.nfr frames (a separate instantiation, so that the image
 // kernels carry no frame loop).
-template <bool MF>
+// CUBE: more than three byte planes (hyperspectral bands), a separate instantiation so that the image
+// kernels carry no plane loop.
+template <bool MF, bool CUBE = false>
 __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigned char* bsm) {
     const Geo& g = a.g;
     const int iy0 = by * a.TRy, ix0 = bx * a.TRx;
@@ -361,9 +448,7 @@ __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigne
             if (g.C == 1) {
                 bp[t_] = px[0];
             } else if (a.mode == MM_FULL) {
-                bp[t_] = px[0];
-                bp[(size_t)Rg.h * P8 + t_] = px[1];
-                bp[(size_t)2 * Rg.h * P8 + t_] = px[2];
+                for (int p = 0; p < nb; ++p) bp[(size_t)p * Rg.h * P8 + t_] = px[p];
             } else {
                 bp[t_] = px[1];
                 if (gcp) sp[r * Rg.w + cc] = (float)((int)px[0] + (int)px[1] + (int)px[2]);
@@ -477,6 +562,8 @@ __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigne
             const int* svv = svv_of(fs);
             if (!green) {
                 match_sum_plane(a, Rg, sum_of(fs), rsp, svv + (size_t)hv * wv, rsrr, rvw, c, S, lane, koff, self);
+            } else if constexpr (CUBE) {
+                match_bytes_n<4>(a, Rg, bp, rbp, P8, svv, rsrr, c, S, lane, koff, self, nb);
             } else if (nb == 3) {
                 match_bytes<4, 3>(a, Rg, bp, rbp, P8, svv, rsrr, c, S, lane, koff, self);
             } else {
@@ -497,6 +584,11 @@ __device__ __forceinline__ void bm_tile(const BMArgs& a, int by, int bx, unsigne
 __global__ void __launch_bounds__(BM_THREADS, 2) block_match_kernel(BMArgs a) {
     extern __shared__ __align__(16) unsigned char bsm[];
     bm_tile<false>(a, blockIdx.y, blockIdx.x, bsm);
+}
+
+__global__ void __launch_bounds__(BM_THREADS, 2) block_match_cube_kernel(BMArgs a) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    bm_tile<false, true>(a, blockIdx.y, blockIdx.x, bsm);
 }
 
 __global__ void __launch_bounds__(BM_THREADS, 2) block_match_video_kernel(BMArgs a) {
@@ -569,7 +661,10 @@ cudaError_t launch_block_match_batch(const BMArgs* d_args, const int* d_prefix, 
 cudaError_t launch_block_match(const BMArgs& a, cudaStream_t s) {
     size_t smem = bm_smem_bytes(a);
     if (smem > BM_SMEM_MAX) return cudaErrorInvalidValue;
-    auto fn = a.nfr > 0 ? block_match_video_kernel : block_match_kernel;
+    if (byte_planes(a.mode, a.g.C) > 3 && a.nfr > 0) return cudaErrorInvalidValue;   // no video cubes
+    auto fn = byte_planes(a.mode, a.g.C) > 3 ? block_match_cube_kernel
+              : a.nfr > 0                    ? block_match_video_kernel
+                                             : block_match_kernel;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -54,6 +54,11 @@ cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long l
 inline int basis_problems(int C) { return 2 * (C / 2 + 1); }
 cudaError_t launch_basis(const unsigned long long* d_mom, int C, double* d_basis64, float* d_basis32,
                          cudaStream_t s, double* d_gap = nullptr);
+// Row and column moments (layout as launch_moments) of a cube with any number of bands g.C.
+cudaError_t launch_cube_moments(const uint8_t* img, const Geo& g, unsigned long long* d_mom, cudaStream_t s);
+// Floats of the packed FP32 basis: C in {1, 3}: 512 (the filter's layout); cubes (other C):
+// [2 (U, V)][C/2 + 1 slices][re, im][8][8].
+inline int basis32_floats(int C) { return (C == 1 || C == 3) ? 512 : 2 * (C / 2 + 1) * 2 * 64; }
 // Quantise a float image: q = clip(rint(x), 0, 255).
 cudaError_t launch_quantize(const float* x, int64_t n, uint8_t* q, cudaStream_t s);
 
@@ -65,6 +70,8 @@ enum FilterMode { FM_FORWARD = 0, FM_DENOM = 1, FM_ADJOINT = 2, FM_VIDEO = 3, FM
 // norm of the group's inputs; kBandTau covers tau rounded to FP32).
 constexpr float kBandRel = 1.9073486328125e-06f;      // 2^-19
 constexpr double kBandTau = 2.384185791015625e-07;    // 2^-22
+// Cubes: the band DFTs add up to N terms per value, so the guard band is four times wider.
+constexpr float kBandRelCube = 7.62939453125e-06f;     // 2^-17
 struct FilterArgs {
     const void* img;         // uint8 or float H x W x C (the values that are filtered)
     int img_is_float;
@@ -118,6 +125,31 @@ cudaError_t launch_sure_terms(const float* out, const float* x, const float* b, 
                               double* scratch, double* res, cudaStream_t s);
 // Adjoint helper: r = gout / den.
 cudaError_t launch_div(const float* gout, const float* den, int64_t npix, int C, float* r, cudaStream_t s);
+
+// ---- hyperspectral cubes (cube.cu): Alg. 1 with C = N bands, one Haar slot of a group at a time
+struct CubeArgs {
+    const uint8_t* img;      // H x W x N uint8
+    Geo g;                   // g.C = N
+    const int32_t* idx;      // [groups][K]
+    const float* basis32;    // basis32_floats(N) floats, cube layout
+    const double* basis64;   // [2][N][8][8] complex
+    float tau32;
+    double tau64;
+    float band_rel, band_abs; // guard band: |S| within band_rel ||G||_F + band_abs of tau -> FP64 decision
+    const float* w_in;       // optional per-group weights
+    int agg_mode;
+    float* scratch;          // grid x K x 64 N floats (spatial Haar slots per CTA)
+    float* num;              // H x W x N, zeroed by the launcher
+    float* den;              // H x W, zeroed by the launcher
+    float* out;              // H x W x N = num / den
+    uint32_t* mask_out;      // optional: ceil(K 64 N / 32) words per group (bit (m 64 + p) N + c)
+    float* weights_out;      // optional
+    float* coef_out;         // optional: K 64 N floats per group
+};
+size_t cube_smem_bytes(int C, int K);
+// CTAs of the persistent cube filter (a few per SM, at most one per group).
+int cube_grid(int C, int K, int64_t ngroups);
+cudaError_t launch_cube_filter(const CubeArgs& a, int grid, cudaStream_t s);
 
 // ---- persistent batch forms over many images (work items -> image by prefix sums)
 int bm_tiles(const BMArgs& a);

@@ -151,6 +151,72 @@ __global__ void __launch_bounds__(256) moments_batch_kernel(const BMArgs* __rest
     }
 }
 
+// Row and column moments of the reference patches of a cube with any number of bands C, in the
+// layout of moments_chunk ([2][8][8][C][C]): with the 8-byte vectors r_(a,c) = P[a][0..7][c] and
+// q_(b,c) = P[0..7][b][c] of a reference, R[a][a'][c][c'] = sum over references of <r_(a,c), r_(a',c')>
+// and Q[b][b'][c][c'] = sum of <q_(b,c), q_(b',c')>: two Gram matrices of 8C vectors per reference,
+// accumulated with DP4A. CTA (x: which, 32-vector row tile, 32-vector column tile; y: chunk of
+// CM_CHUNK references); uint32 partials per CTA (CM_CHUNK * 8 * 255^2 < 2^32), added to uint64 out.
+constexpr int CM_T = 32;
+constexpr int CM_BATCH = 32;
+constexpr int CM_CHUNK = 2048;
+
+__global__ void __launch_bounds__(256) cube_moments_kernel(const uint8_t* __restrict__ img, Geo g, int ntile,
+                                                           unsigned long long* __restrict__ out) {
+    __shared__ uint32_t su[CM_BATCH][CM_T][2], sv[CM_BATCH][CM_T][2];
+    const int C = g.C, D = PS * C;
+    const int which = blockIdx.x / (ntile * ntile);
+    const int rem = blockIdx.x - which * ntile * ntile;
+    const int tu = rem / ntile, tv = rem - tu * ntile;
+    const int N = g.ngroups();
+    const int r0 = blockIdx.y * CM_CHUNK, r1 = min(r0 + CM_CHUNK, N);
+    const int lu = threadIdx.x >> 3, lv0 = (threadIdx.x & 7) * 4;
+    uint32_t acc[4] = {0u, 0u, 0u, 0u};
+    // word (vector x, half h) of reference r: 4 bytes of vector x = (e, c), e = a (rows) or b (columns)
+    auto word = [&](int r, int x, int h) -> uint32_t {
+        if (x >= D) return 0u;
+        const int iy = r / g.nrx, ix = r - iy * g.nrx;
+        const int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
+        const int e = x / C, c = x - e * C;
+        uint32_t w = 0u;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int o = 4 * h + t;                  // b (rows) or a (columns)
+            const int y = which == 0 ? ry + e : ry + o, xx = which == 0 ? rx + o : rx + e;
+            w |= (uint32_t)img[((size_t)y * g.W + xx) * C + c] << (8 * t);
+        }
+        return w;
+    };
+    for (int rb = r0; rb < r1; rb += CM_BATCH) {
+        const int nb = min(CM_BATCH, r1 - rb);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb * CM_T * 2; t += 256) {
+            const int j = t / (CM_T * 2), rm = t - j * CM_T * 2, x = rm >> 1, h = rm & 1;
+            su[j][x][h] = word(rb + j, tu * CM_T + x, h);
+            sv[j][x][h] = word(rb + j, tv * CM_T + x, h);
+        }
+        __syncthreads();
+        for (int j = 0; j < nb; ++j) {
+            const uint32_t u0 = su[j][lu][0], u1 = su[j][lu][1];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc[q] = __dp4a(u0, sv[j][lv0 + q][0], acc[q]);
+                acc[q] = __dp4a(u1, sv[j][lv0 + q][1], acc[q]);
+            }
+        }
+    }
+    const int u = tu * CM_T + lu;
+    if (u >= D) return;
+    const int e = u / C, c = u - e * C;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int v = tv * CM_T + lv0 + q;
+        if (v >= D || acc[q] == 0u) continue;
+        const int e2 = v / C, c2 = v - e2 * C;
+        atomicAdd(out + ((((size_t)which * PS + e) * PS + e2) * C + c) * C + c2, (unsigned long long)acc[q]);
+    }
+}
+
 // Row and column moments from the full second moment M (entry u = a*8C + b*C + c of the packed
 // patch; lower triangle u >= v filled): R[a][a'][c][c'] = sum_b M[(a,b,c)][(a',b,c')] and
 // Q[b][b'][c][c'] = sum_a M[(a,b,c)][(a,b',c')]. Integer sums, so the result equals the direct
@@ -611,9 +677,17 @@ __device__ __forceinline__ void basis_problem(const unsigned long long* __restri
                 const double m = (double)M[((u * PS + v) * C + c) * C + c2];
                 const int d = which == 0 ? (c - c2) : (c2 - c);
                 const int k = ((f * d) % C + C) % C;
+                // w^k, w = exp(-2 pi i / C): exact constants for C = 3, the library's cospi / sinpi otherwise
                 double phr = 1.0, phi = 0.0;
-                if (C == 3 && k == 1) { phr = -0.5; phi = -s32; }
-                if (C == 3 && k == 2) { phr = -0.5; phi = s32; }
+                if (C == 3) {
+                    if (k == 1) { phr = -0.5; phi = -s32; }
+                    if (k == 2) { phr = -0.5; phi = s32; }
+                } else if (k != 0) {
+                    double sn, cs;
+                    sincospi(2.0 * k / C, &sn, &cs);
+                    phr = cs;
+                    phi = -sn;
+                }
                 accr += m * phr;
                 acci += m * phi;
             }
@@ -641,12 +715,18 @@ __device__ __forceinline__ void basis_problem(const unsigned long long* __restri
             oc[0] = re;
             oc[1] = -im;
         }
-        const int per = (C == 3) ? 3 * PS2 : PS2;
-        float* o32 = b32 + which * per;
-        if (f == 0) o32[ai] = (float)re;
-        else {
-            o32[PS2 + ai] = (float)re;
-            o32[2 * PS2 + ai] = (float)im;
+        if (C == 1 || C == 3) {
+            const int per = (C == 3) ? 3 * PS2 : PS2;
+            float* o32 = b32 + which * per;
+            if (f == 0) o32[ai] = (float)re;
+            else {
+                o32[PS2 + ai] = (float)re;
+                o32[2 * PS2 + ai] = (float)im;
+            }
+        } else {                                    // cubes: [which][f][re, im][a][i]
+            float* o32 = b32 + ((size_t)which * nf + f) * 2 * PS2;
+            o32[ai] = (float)re;
+            o32[PS2 + ai] = (float)im;
         }
     }
 }
@@ -856,6 +936,15 @@ cudaError_t launch_full_moment(const uint8_t* img, const Geo& g, unsigned long l
     dim3 grid((n + chunk - 1) / chunk, ntiles);
     if (g.C == 3) full_moment_kernel<3><<<grid, 256, 0, s>>>(img, g, chunk, d_M, d_s);
     else full_moment_kernel<1><<<grid, 256, 0, s>>>(img, g, chunk, d_M, d_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cube_moments(const uint8_t* img, const Geo& g, unsigned long long* d_mom, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_mom, 0, sizeof(unsigned long long) * 2 * PS2 * g.C * g.C, s);
+    if (e != cudaSuccess) return e;
+    const int ntile = (PS * g.C + CM_T - 1) / CM_T;
+    dim3 grid(2 * ntile * ntile, (g.ngroups() + CM_CHUNK - 1) / CM_CHUNK);
+    cube_moments_kernel<<<grid, 256, 0, s>>>(img, g, ntile, d_mom);
     return cudaGetLastError();
 }
 

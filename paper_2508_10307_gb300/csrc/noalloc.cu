@@ -141,7 +141,7 @@ extern "C" htsvd_status htsvd_denoise_noalloc(const uint8_t* d_noisy, int32_t H,
         return HTSVD_ERR_CUDA;
     if (r.strict_basis) {
         // the gaps go to a host array on the stack (pageable memory: the copy completes before it returns)
-        double h[8];
+        double h[8];                              // C is 1 or 3 here: at most 4 problems
         const int n = basis_problems(C);
         if (cudaMemcpyAsync(h, gap, sizeof(double) * n, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
             cudaStreamSynchronize(stream) != cudaSuccess)

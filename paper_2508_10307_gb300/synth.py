@@ -60,6 +60,23 @@ def clean_image(H: int, W: int, C: int, seed: int) -> np.ndarray:
     return np.clip(np.stack(chans, axis=-1), 0, 255)
 
 
+def clean_cube(H: int, W: int, N: int, seed: int) -> np.ndarray:
+    """Clean float64 hyperspectral cube (H, W, N) in [0, 255]: three smooth abundance maps (the
+    image generator's layers, scaled to [0, 1]) mixing three smooth spectra over the N bands
+    (Gaussian bumps at random centres and widths), plus a mild band-dependent offset; real
+    reflectance cubes are likewise close to a few endmember spectra per pixel."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b = np.arange(N, dtype=np.float64)
+    cube = np.zeros((H, W, N))
+    for _ in range(3):
+        ab = _gray_layer(rng, H, W) / 255.0
+        c, w, amp = rng.uniform(0, N), rng.uniform(0.15, 0.6) * N, rng.uniform(60, 140)
+        spec = amp * np.exp(-0.5 * ((b - c) / w) ** 2)
+        cube += ab[:, :, None] * spec[None, None, :]
+    cube += 20.0 + 30.0 * b / max(N - 1, 1)
+    return np.clip(cube, 0, 255)
+
+
 def quantize(x: np.ndarray) -> np.ndarray:
     return np.clip(np.rint(x), 0, 255).astype(np.uint8)
 
