@@ -7,7 +7,8 @@
 // along the group mode and the per-patch t-SVD projection commute, so each slot is formed directly
 // from the uint8 patches in its Haar support (exact integer sums and differences), projected
 //   band DFT -> per slice f: U_f^H X_f V_f -> inverse band DFT,
-// thresholded (FP32, FP64 inside the guard band), and, if it keeps a coefficient, inverted on the
+// thresholded (FP32; FP64 inside a guard band proportional to the slot's own norm), and, if it keeps a
+// coefficient, inverted on the
 // kept basis rows only; the 8 x 8 x N spatial slot goes to a per-CTA scratch in global memory that
 // stays in L2 (K slots per CTA). After the last slot the CTA runs the Haar synthesis per fibre from
 // that scratch and adds every estimated patch into the numerator and denominator planes with float
@@ -23,7 +24,7 @@ namespace {
 constexpr int CB_THREADS = 256;
 
 struct CubeLayout {
-    int bas, tw, xr, fa, fb, sc, pos, misc, pixnz, total;   // byte offsets
+    int bas, tw, tw64, xr, fa, fb, sc, pos, misc, pixnz, total;   // byte offsets
 };
 __host__ __device__ inline CubeLayout cube_layout(int C, int K) {
     const int nf = C / 2 + 1;
@@ -31,6 +32,8 @@ __host__ __device__ inline CubeLayout cube_layout(int C, int K) {
     int o = 0;
     L.bas = o; o += 4 * (2 * nf * 2 * PS2);        // U, V slices f = 0 .. C/2: [which][f][re, im][a][i]
     L.tw = o; o += 4 * (2 * C);                     // cos, sin of 2 pi k / C
+    o = (o + 7) & ~7;
+    L.tw64 = o; o += 8 * (2 * C);                   // the same in FP64 (guard-band recomputation)
     L.xr = o; o += 4 * (PS2 * C);                   // raw Haar slot, [pixel][band]
     L.fa = o; o += 4 * (nf * PS2 * 2);              // Fourier slices [f][pixel][re, im]
     L.fb = o; o += 4 * (nf * PS2 * 2);
@@ -66,12 +69,15 @@ __global__ void __launch_bounds__(CB_THREADS) cube_filter_kernel(CubeArgs a) {
     float* bas = reinterpret_cast<float*>(smem + Ly.bas);
     float* twc = reinterpret_cast<float*>(smem + Ly.tw);
     float* tws = twc + C;
+    double* t64c = reinterpret_cast<double*>(smem + Ly.tw64);
+    double* t64s = t64c + C;
     float* xr = reinterpret_cast<float*>(smem + Ly.xr);
     float* fa = reinterpret_cast<float*>(smem + Ly.fa);
     float* fb = reinterpret_cast<float*>(smem + Ly.fb);
     float* sc = reinterpret_cast<float*>(smem + Ly.sc);
     int* pos = reinterpret_cast<int*>(smem + Ly.pos);
-    int* misc = reinterpret_cast<int*>(smem + Ly.misc);      // 0 kept in group, 1 kept in slot, 2 row mask, 3 norm
+    int* misc = reinterpret_cast<int*>(smem + Ly.misc);      // 0 kept in group, 1 kept in slot, 2 row mask,
+                                                              // 5, 6 squared slot norms (float, by slot parity)
     int* pixnz = reinterpret_cast<int*>(smem + Ly.pixnz);
     const int tid = threadIdx.x, lane = tid & 31;
     float* scratch = a.scratch + (size_t)blockIdx.x * K * NE;
@@ -84,6 +90,10 @@ __global__ void __launch_bounds__(CB_THREADS) cube_filter_kernel(CubeArgs a) {
         sincospif(2.f * (float)t / (float)C, &sn, &cs);
         twc[t] = cs;
         tws[t] = sn;
+        double sd, cd;
+        sincospi(2.0 * t / C, &sd, &cd);
+        t64c[t] = cd;
+        t64s[t] = sd;
     }
     auto U = [&](int f, int ri, int a_, int i) { return bas[((0 * nf + f) * 2 + ri) * PS2 + a_ * PS + i]; };
     auto V = [&](int f, int ri, int b_, int j) { return bas[((1 * nf + f) * 2 + ri) * PS2 + b_ * PS + j]; };
@@ -101,24 +111,11 @@ __global__ void __launch_bounds__(CB_THREADS) cube_filter_kernel(CubeArgs a) {
         if (a.mask_out)
             for (int t = tid; t < nbw; t += CB_THREADS) a.mask_out[(size_t)grp * nbw + t] = 0u;
         __syncthreads();
-        // ||G||_F^2 for the guard band (integer per warp, FP32 across warps)
-        {
-            int sq = 0;
-            for (int t = tid; t < K * NE; t += CB_THREADS) {
-                const int k = t / NE, e = t - k * NE, p = e / C, c = e - p * C;
-                const int v = img[((size_t)(pos[2 * k] + p / PS) * g.W + pos[2 * k + 1] + p % PS) * C + c];
-                sq += v * v;
-            }
-            sq = __reduce_add_sync(0xffffffffu, sq);
-            if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[3]), (float)sq);
-        }
-        __syncthreads();
-        const float delta = a.band_rel * sqrtf(__int_as_float(misc[3])) + a.band_abs;
-
         for (int m = 0; m < K; ++m) {
             int k0, L, half, sl;
             haar_row<K>(m, k0, L, half, sl);
-            // raw slot: integer Haar combination of the support's patches
+            // raw slot: integer Haar combination of the support's patches, and its squared norm
+            float nq = 0.f;
             for (int e = tid; e < NE; e += CB_THREADS) {
                 const int p = e / C, c = e - p * C, pa = p / PS, pb = p - pa * PS;
                 int s = 0;
@@ -127,9 +124,13 @@ __global__ void __launch_bounds__(CB_THREADS) cube_filter_kernel(CubeArgs a) {
                     s += (k - k0 < half) ? v : -v;
                 }
                 xr[e] = (float)s;
+                nq = fmaf((float)s, (float)s, nq);
             }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) nq += __shfl_xor_sync(0xffffffffu, nq, off);
             if (tid == 0) { misc[1] = 0; misc[2] = 0; }
             if (tid < PS2) pixnz[tid] = 0;
+            if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[5 + (m & 1)]), nq);
             __syncthreads();
             // band DFT: X_f[p] = sum_c x[p][c] w^{fc}, w = exp(-2 pi i / C)
             for (int t = tid; t < nf * PS2; t += CB_THREADS) {
@@ -190,7 +191,11 @@ __global__ void __launch_bounds__(CB_THREADS) cube_filter_kernel(CubeArgs a) {
             // unnormalised synthesis. Entries inside the guard band are decided again in FP64 by the
             // warp that met them.
             {
-                const float r = sqrtf((float)L), tl = a.tau32 * r, dl = delta * r;
+                // The FP32 error of a slot's coefficients is bounded by a multiple of the slot's own
+                // norm (its transform is orthonormal up to the unnormalised Haar factor), so the band
+                // is band_rel x ||slot||_F, plus the rounding of tau.
+                const float r = sqrtf((float)L), tl = a.tau32 * r;
+                const float dl = a.band_rel * sqrtf(__int_as_float(misc[5 + (m & 1)])) + a.band_abs * r;
                 const int iters = (NE + CB_THREADS - 1) / CB_THREADS;
                 for (int it = 0; it < iters; ++it) {
                     const int e = it * CB_THREADS + tid;
@@ -206,29 +211,36 @@ __global__ void __launch_bounds__(CB_THREADS) cube_filter_kernel(CubeArgs a) {
                         bal &= bal - 1;
                         const int eb = __shfl_sync(0xffffffffu, e, l);
                         const int pb = eb / C, cb = eb - pb * C, ib = pb / PS, jb = pb - ib * PS;
-                        // FP64: S = (1/C) sum_{a,b,c'} x[a][b][c'] Re(sum_f w^{f(c'-cb)} conj(U_f[a][ib]) V_f[b][jb])
+                        // FP64: P_f = sum_{pixels} conj(U_f[a][ib]) V_f[b][jb] X_f[a][b], X_f the band DFT
+                        // of the raw slot (exact integers); S = (1/C) sum_f w^{-f cb} P_f, slices C - f
+                        // being the conjugates of f. Lane l takes pixels l and l + 32.
                         double acc = 0.0;
-                        for (int q = lane; q < PS2; q += 32) {
-                            const int qa = q / PS, qb = q - qa * PS;
-                            for (int cp = 0; cp < C; ++cp) {
-                                const double x = (double)xr[q * C + cp];
-                                if (x == 0.0) continue;
-                                double kr = 0.0;
-                                for (int f = 0; f < C; ++f) {
-                                    const double* u = a.basis64 + 2 * (((size_t)0 * C + f) * PS2 + qa * PS + ib);
-                                    const double* vv = a.basis64 + 2 * (((size_t)1 * C + f) * PS2 + qb * PS + jb);
-                                    const double pr = u[0] * vv[0] + u[1] * vv[1];    // conj(u) v
-                                    const double pi = u[0] * vv[1] - u[1] * vv[0];
-                                    const int kk = (int)(((long long)f * (cp - cb) % C + C) % C);
-                                    double sn, cs;
-                                    sincospi(2.0 * kk / C, &sn, &cs);              // w^kk = cs - i sn
-                                    kr += pr * cs + pi * sn;
+                        for (int f = 0; 2 * f <= C; ++f) {
+                            double pr = 0.0, pi = 0.0;
+                            for (int q = lane; q < PS2; q += 32) {
+                                const int qa = q / PS, qb = q - qa * PS;
+                                double xre = 0.0, xim = 0.0;
+                                for (int cp = 0, k = 0; cp < C; ++cp, k = (k + f >= C) ? k + f - C : k + f) {
+                                    const double x = (double)xr[q * C + cp];
+                                    xre = fma(x, t64c[k], xre);
+                                    xim = fma(-x, t64s[k], xim);
                                 }
-                                acc += x * kr;
+                                const double* u = a.basis64 + 2 * (((size_t)0 * C + f) * PS2 + qa * PS + ib);
+                                const double* vv = a.basis64 + 2 * (((size_t)1 * C + f) * PS2 + qb * PS + jb);
+                                const double cr = u[0] * vv[0] + u[1] * vv[1];      // conj(u) v
+                                const double ci = u[0] * vv[1] - u[1] * vv[0];
+                                pr += cr * xre - ci * xim;
+                                pi += cr * xim + ci * xre;
                             }
-                        }
 #pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                            for (int off = 16; off > 0; off >>= 1) {
+                                pr += __shfl_xor_sync(0xffffffffu, pr, off);
+                                pi += __shfl_xor_sync(0xffffffffu, pi, off);
+                            }
+                            const int k2 = (int)(((long long)f * cb) % C);
+                            const double wgt = (f == 0 || 2 * f == C) ? 1.0 : 2.0;
+                            acc += wgt * (t64c[k2] * pr - t64s[k2] * pi);  // Re(w^{-f cb} P_f)
+                        }
                         if (lane == l) keep = fabs(acc / (double)C) >= a.tau64 * sqrt((double)L);
                     }
                     if (valid) {
@@ -246,6 +258,7 @@ __global__ void __launch_bounds__(CB_THREADS) cube_filter_kernel(CubeArgs a) {
                     const int wk = __reduce_add_sync(0xffffffffu, keep ? 1 : 0);
                     if (lane == 0 && wk) atomicAdd(&misc[1], wk);
                 }
+                if (tid == 0) misc[5 + ((m + 1) & 1)] = 0;      // the next slot's norm accumulator
             }
             __syncthreads();
             float* dst = scratch + (size_t)sl * NE;

@@ -70,8 +70,9 @@ enum FilterMode { FM_FORWARD = 0, FM_DENOM = 1, FM_ADJOINT = 2, FM_VIDEO = 3, FM
 // norm of the group's inputs; kBandTau covers tau rounded to FP32).
 constexpr float kBandRel = 1.9073486328125e-06f;      // 2^-19
 constexpr double kBandTau = 2.384185791015625e-07;    // 2^-22
-// Cubes: the band DFTs add up to N terms per value, so the guard band is four times wider.
-constexpr float kBandRelCube = 7.62939453125e-06f;     // 2^-17
+// Cubes: band relative to the norm of the Haar slot being thresholded (its FP32 coefficient error,
+// measured on 31-band cubes: 2^-23 of that norm).
+constexpr float kBandRelCube = 1.9073486328125e-06f;   // 2^-19
 struct FilterArgs {
     const void* img;         // uint8 or float H x W x C (the values that are filtered)
     int img_is_float;

@@ -75,3 +75,29 @@ def test_cube_equal_bands_give_the_gray_result():
     gray = H.denoise(torch.from_numpy(g).cuda(), 12.0, prm).cpu().numpy()
     cube = H.denoise_cube(torch.from_numpy(np.repeat(g, 6, axis=2)).cuda(), 12.0, prm).cpu().numpy()
     assert max_abs(cube, np.repeat(gray, 6, axis=2)) <= PIX_TOL
+
+
+BAND_REL_CUBE = 2.0 ** -19     # guard band of the cube threshold, relative to the slot norm (kBandRelCube)
+
+
+def test_cube_fp32_coefficient_error_is_well_inside_the_guard_band():
+    """Outside the guard band the FP32 coefficients decide keep/drop. The cube filter's band for a Haar
+    slot is band * ||slot||_F (the slot's normalised Haar combination of the group's patches, whose
+    transform is orthonormal), so the FP32 error of every coefficient against the oracle's FP64
+    coefficient must stay well below band * ||slot||_F."""
+    clean, noisy = _case(64, 64, 31, 12.0, 91)
+    prm = dict(ps=8, stride=3, window=15, K=16)
+    r = O.denoise(noisy, 12.0, prm)
+    out, info = H.denoise_cube(torch.from_numpy(noisy).cuda(), 12.0, prm, return_info=True, coeffs=True)
+    coef = info["coeffs"].cpu().numpy().astype(np.float64)
+    p = O.Params.of(prm)
+    Hk = O.haar_matrix(p.K)
+    G = O.gather_groups(noisy, r.idx, p.ps).astype(np.float64)
+    S = O.forward_transform(G, r.U, r.V, Hk)
+    n = len(r.idx)
+    err = np.abs(coef.reshape(n, p.K, -1) - S.reshape(n, p.K, -1)).max(axis=2)
+    slots = np.tensordot(Hk, G, axes=([1], [1])).transpose(1, 0, 2, 3, 4)       # [n, m, i, j, band]
+    nrm = np.sqrt((slots.reshape(n, p.K, -1) ** 2).sum(axis=2))
+    worst = float((err / np.maximum(nrm, 1e-30)).max())
+    print(f"cube FP32 coefficient error: max |S32 - S64| / ||slot||_F = 2^{np.log2(worst):.2f}")
+    assert worst <= BAND_REL_CUBE / 4, worst
