@@ -8,13 +8,27 @@
 // from the uint8 patches in its Haar support (exact integer sums and differences), projected
 //   band DFT -> per slice f: U_f^H X_f V_f -> inverse band DFT,
 // thresholded (FP32; FP64 inside a guard band proportional to the slot's own norm), and, if it keeps a
-// coefficient, inverted on the
-// kept basis rows only; the 8 x 8 x N spatial slot goes to a per-CTA scratch in global memory that
-// stays in L2 (K slots per CTA). After the last slot the CTA runs the Haar synthesis per fibre from
+// coefficient, inverted on the kept basis rows only; the 8 x 8 x N spatial slot goes to a per-CTA
+// scratch in global memory that stays in L2 (K slots per CTA; slots without a kept coefficient are
+// neither written nor read). After the last slot the CTA runs the Haar synthesis per fibre from
 // that scratch and adds every estimated patch into the numerator and denominator planes with float
 // atomics (the per-CTA footprint accumulator of the image filter would need (W + 7)^2 x (N + 1)
 // floats). The summation order of the atomics varies between runs, so outputs agree to rounding,
 // not bit for bit.
+//
+// Layout and arithmetic per slot (C bands, nf = C/2 + 1 Fourier slices of the real band axis):
+//   raw slot, folded over the band axis: s_c = x_c + x_{C-c}, d_c = x_c - x_{C-c} (0 < c < C/2),
+//     s_c = x_c, d_c = 0 otherwise; exact integers;
+//   band DFT: Re X_f = sum_c s_c cos(2 pi f c / C), Im X_f = -sum_c d_c sin(2 pi f c / C), f < nf
+//     (half the multiply-adds of the direct sum; the slices f > C/2 are the conjugates);
+//   projection per slice and basis row i (one thread): Y_f[i][:] = sum_a conj(U_f[a][i]) X_f[a][:],
+//     S_f[i][:] = Y_f[i][:] V_f, stored times w_f / C (w_f = 2 for the slices that stand for a
+//     conjugate pair, 1 for f = 0 and f = C/2);
+//   inverse band DFT: x_c = A_c + B_c, x_{C-c} = A_c - B_c with A_c = sum_f Re S_f cos(2 pi f c / C)
+//     and B_c = -sum_f Im S_f sin(2 pi f c / C).
+// Both DFTs are register tiles (2 pixels x 4 frequencies or bands) over a cos table and a -sin
+// table that serve both directions (the tables are symmetric in f and c). Rows of 64 pixels are
+// RS = 68 floats apart, so that the four slices a warp touches at once fall in different banks.
 #include "filter_impl.cuh"
 
 namespace htsvd {
@@ -22,81 +36,264 @@ namespace htsvd {
 namespace {
 
 constexpr int CB_THREADS = 256;
+constexpr int RS = 68;       // floats per 64-pixel row (16-byte aligned; consecutive rows 4 banks apart)
+constexpr int BS = 136;      // floats per basis block [re, im][a][i] of one (U or V, f) (8 banks apart)
 
 struct CubeLayout {
-    int bas, tw, tw64, xr, fa, fb, sc, pos, misc, pixnz, total;   // byte offsets
+    int nf, nfp;                                                  // C/2 + 1 and that rounded up to 4
+    int bas, tc, ts, tw64, R, P, Q, stk, base, misc, total;      // byte offsets
 };
+__host__ __device__ inline int log2_of(int K) {
+    int l = 0;
+    while ((2 << l) <= K) ++l;
+    return l;
+}
 __host__ __device__ inline CubeLayout cube_layout(int C, int K) {
-    const int nf = C / 2 + 1;
     CubeLayout L;
+    L.nf = C / 2 + 1;
+    L.nfp = (L.nf + 3) & ~3;
     int o = 0;
-    L.bas = o; o += 4 * (2 * nf * 2 * PS2);        // U, V slices f = 0 .. C/2: [which][f][re, im][a][i]
-    L.tw = o; o += 4 * (2 * C);                     // cos, sin of 2 pi k / C
+    L.bas = o; o += 4 * (2 * L.nf * BS);           // U, V slices f = 0 .. C/2
+    L.tc = o; o += 4 * (L.nf * L.nfp);             // cos(2 pi f c / C), [c][f] = [f][c], zero padded
+    L.ts = o; o += 4 * (L.nf * L.nfp);             // -sin(2 pi f c / C)
     o = (o + 7) & ~7;
-    L.tw64 = o; o += 8 * (2 * C);                   // the same in FP64 (guard-band recomputation)
-    L.xr = o; o += 4 * (PS2 * C);                   // raw Haar slot, [pixel][band]
-    L.fa = o; o += 4 * (nf * PS2 * 2);              // Fourier slices [f][pixel][re, im]
-    L.fb = o; o += 4 * (nf * PS2 * 2);
-    L.sc = o; o += 4 * (PS2 * C);                   // real coefficients of the slot [pixel][band]
-    L.pos = o; o += 4 * (2 * K);
+    L.tw64 = o; o += 8 * (2 * C);                   // cos, sin of 2 pi k / C in FP64 (guard band)
+    L.R = o; o += 4 * (2 * L.nf * RS);              // folded raw slot s | d; later the spatial slot [c][p]
+    L.P = o; o += 4 * (2 * L.nf * RS);              // Fourier slices Re | Im, or folded coefficients
+    L.Q = o; o += 4 * (2 * L.nf * RS);
+    L.stk = o; o += 4 * (log2_of(K) * L.nf * PS2);  // pending Haar-tree sums, two 16-bit bands per word
+    L.base = o; o += 4 * K;                         // pixel index of each patch's corner
     L.misc = o; o += 4 * 16;
-    L.pixnz = o; o += 4 * PS2;
     L.total = o;
     return L;
 }
 
-// Haar row m of the unnormalised in-place transform: support [k0, k0 + L), first half added, second
-// half subtracted (all added for m = 0), coefficient stored in slot sl (as haar_for_each).
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ float comp(const float4& v, int i) {
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Haar rows as nodes of a binary tree over the K patches (heap order): row m >= 1 at level
+// l = floor(log2 m) has support [k0, k0 + L), L = K >> l, k0 = (m - 2^l) L, and is the sum over its
+// first half minus the sum over its second half, i.e. the difference of its children's sums; row 0
+// is the sum over all K. Slot sl is where the unnormalised in-place transform stores row m (as
+// haar_for_each).
 template <int K>
-__device__ __forceinline__ void haar_row(int m, int& k0, int& L, int& half, int& sl) {
+__device__ __forceinline__ void haar_node(int m, int& k0, int& L, int& sl) {
     if (m == 0) {
-        k0 = 0; L = K; half = K; sl = 0;
+        k0 = 0; L = K; sl = 0;
         return;
     }
     const int l = 31 - __clz(m), mm = m - (1 << l);
     L = K >> l;
     k0 = mm * L;
-    half = L / 2;
     sl = (2 * mm + 1) * (K >> (l + 1));
+}
+// Rows in post order (children before their parent), then row 0: every child's sum is pushed on a
+// stack and its parent pops the two, so each patch is read once per group. First row: K/2.
+template <int K>
+__device__ __forceinline__ int haar_next(int m) {
+    if (m == 1) return 0;
+    if (m & 1) return m >> 1;                       // a right child: its parent is next
+    m += 1;                                          // a left child: the leftmost lowest row under its sibling
+    while (m < K / 2) m <<= 1;
+    return m;
+}
+
+// TP consecutive floats of a shared-memory row (TP = 2 or 4, 8- or 16-byte aligned).
+template <int TP>
+__device__ __forceinline__ void ldv(const float* p, float (&r)[TP]) {
+    if constexpr (TP == 4) {
+        const float4 v = ld4(p);
+        r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    } else {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        r[0] = v.x; r[1] = v.y;
+    }
+}
+template <int TP>
+__device__ __forceinline__ void stv(float* p, const float (&r)[TP]) {
+    if constexpr (TP == 4) *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+    else *reinterpret_cast<float2*>(p) = make_float2(r[0], r[1]);
+}
+
+// The DFT tiles: TP pixels x 4 frequencies (or bands); 64 / TP tiles per frequency quad, a warp
+// covering one quad when TP = 2.
+constexpr int TP = 2;
+constexpr int NPT = PS2 / TP;                 // pixel tiles
+
+// Band DFT of a folded real slot: src rows [0, nf) s_c, [nf, 2 nf) d_c; dst rows [0, nf) Re X_f,
+// [nf, 2 nf) Im X_f.
+__device__ __forceinline__ void band_dft(const float* __restrict__ src, float* __restrict__ dst,
+                                         const float* tc, const float* ts, int nf, int nfp, int tid) {
+    for (int t = tid; t < NPT * (nfp >> 2); t += CB_THREADS) {
+        const int p0 = (t % NPT) * TP, f0 = (t / NPT) << 2;
+        float re[4][TP], im[4][TP];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < TP; ++j) re[i][j] = im[i][j] = 0.f;
+#pragma unroll 2
+        for (int c = 0; c < nf; ++c) {
+            float s[TP], d[TP];
+            ldv<TP>(src + c * RS + p0, s);
+            ldv<TP>(src + (nf + c) * RS + p0, d);
+            const float4 wc = ld4(tc + c * nfp + f0), ws = ld4(ts + c * nfp + f0);
+#pragma unroll
+            for (int fi = 0; fi < 4; ++fi)
+#pragma unroll
+                for (int pi = 0; pi < TP; ++pi) {
+                    re[fi][pi] = fmaf(s[pi], comp(wc, fi), re[fi][pi]);
+                    im[fi][pi] = fmaf(d[pi], comp(ws, fi), im[fi][pi]);
+                }
+        }
+#pragma unroll
+        for (int fi = 0; fi < 4; ++fi)
+            if (f0 + fi < nf) {
+                stv<TP>(dst + (f0 + fi) * RS + p0, re[fi]);
+                stv<TP>(dst + (nf + f0 + fi) * RS + p0, im[fi]);
+            }
+    }
+}
+
+// One tile of the inverse band DFT of slices stored times w_f / C (src rows Re | Im):
+// A[ci][pi] = sum_f Re S_f cos(2 pi f c / C), B[ci][pi] = -sum_f Im S_f sin(2 pi f c / C) at band
+// c = c0 + ci and pixel p0 + pi; x_c = A + B and x_{C-c} = A - B.
+__device__ __forceinline__ void idft_tile(const float* __restrict__ src, const float* tc, const float* ts, int nf,
+                                          int nfp, int p0, int c0, float (&A)[4][TP], float (&B)[4][TP]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TP; ++j) A[i][j] = B[i][j] = 0.f;
+#pragma unroll 2
+    for (int f = 0; f < nf; ++f) {
+        float qr[TP], qi[TP];
+        ldv<TP>(src + f * RS + p0, qr);
+        ldv<TP>(src + (nf + f) * RS + p0, qi);
+        const float4 wc = ld4(tc + f * nfp + c0), ws = ld4(ts + f * nfp + c0);
+#pragma unroll
+        for (int ci = 0; ci < 4; ++ci)
+#pragma unroll
+            for (int pi = 0; pi < TP; ++pi) {
+                A[ci][pi] = fmaf(qr[pi], comp(wc, ci), A[ci][pi]);
+                B[ci][pi] = fmaf(qi[pi], comp(ws, ci), B[ci][pi]);
+            }
+    }
+}
+
+// Inverse band DFT to a spatial slot: x_c to row c of dst, x_{C-c} to row C - c.
+__device__ __forceinline__ void band_idft(const float* __restrict__ src, float* dst, const float* tc,
+                                          const float* ts, int C, int nf, int nfp, int tid) {
+    for (int t = tid; t < NPT * (nfp >> 2); t += CB_THREADS) {
+        const int p0 = (t % NPT) * TP, c0 = (t / NPT) << 2;
+        float A[4][TP], B[4][TP];
+        idft_tile(src, tc, ts, nf, nfp, p0, c0, A, B);
+#pragma unroll
+        for (int ci = 0; ci < 4; ++ci) {
+            const int c = c0 + ci;
+            float lo[TP], hi[TP];
+#pragma unroll
+            for (int pi = 0; pi < TP; ++pi) {
+                lo[pi] = A[ci][pi] + B[ci][pi];
+                hi[pi] = A[ci][pi] - B[ci][pi];
+            }
+            if (c < nf) stv<TP>(dst + c * RS + p0, lo);
+            if (c > 0 && 2 * c < C) stv<TP>(dst + (C - c) * RS + p0, hi);
+        }
+    }
+}
+
+// FP64 value of the coefficient at pixel pb, band cb of a slot whose folded raw values (exact
+// integers) are in R: P_f = sum_{pixels (a, b)} conj(U_f[a][ib]) V_f[b][jb] X_f[a][b] with X_f the
+// band DFT, and S = (1/C) sum_{f <= C/2} w_f Re(w^{-f cb} P_f). Every lane of the warp calls it with
+// the same (pb, cb); lane l takes pixels l and l + 32.
+__device__ __noinline__ double coef64(const float* R, const double* t64c, const double* t64s,
+                                      const double* __restrict__ b64, int C, int nf, int pb, int cb, int lane) {
+    const int ib = pb >> 3, jb = pb & 7;
+    double acc = 0.0;
+    for (int f = 0; f < nf; ++f) {
+        double pr = 0.0, pi = 0.0;
+        for (int q = lane; q < PS2; q += 32) {
+            const int qa = q >> 3, qb = q & 7;
+            double xre = 0.0, xim = 0.0;
+            for (int c = 0, k = 0; c < nf; ++c, k = (k + f >= C) ? k + f - C : k + f) {
+                xre = fma((double)R[c * RS + q], t64c[k], xre);
+                xim = fma(-(double)R[(nf + c) * RS + q], t64s[k], xim);
+            }
+            const double* u = b64 + 2 * (((size_t)0 * C + f) * PS2 + qa * PS + ib);
+            const double* vv = b64 + 2 * (((size_t)1 * C + f) * PS2 + qb * PS + jb);
+            const double cr = u[0] * vv[0] + u[1] * vv[1];      // conj(u) v
+            const double ci = u[0] * vv[1] - u[1] * vv[0];
+            pr += cr * xre - ci * xim;
+            pi += cr * xim + ci * xre;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            pr += __shfl_xor_sync(0xffffffffu, pr, off);
+            pi += __shfl_xor_sync(0xffffffffu, pi, off);
+        }
+        const int k2 = (f * cb) % C;
+        const double wgt = (f == 0 || 2 * f == C) ? 1.0 : 2.0;
+        acc += wgt * (t64c[k2] * pr - t64s[k2] * pi);          // Re(w^{-f cb} P_f)
+    }
+    return acc / (double)C;
+}
+
+__device__ __forceinline__ void load8s(const float* p, float (&r)[8]) {
+    const float4 a = ld4(p), b = ld4(p + 4);
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+    r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+}
+__device__ __forceinline__ void store8s(float* p, const float (&r)[8], float sc) {
+    st4(p, r[0] * sc, r[1] * sc, r[2] * sc, r[3] * sc);
+    st4(p + 4, r[4] * sc, r[5] * sc, r[6] * sc, r[7] * sc);
 }
 
 template <int K>
-__global__ void __launch_bounds__(CB_THREADS) cube_filter_kernel(CubeArgs a) {
+__global__ void __launch_bounds__(CB_THREADS, 3) cube_filter_kernel(CubeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Geo& g = a.g;
-    const int C = g.C, nf = C / 2 + 1, NE = PS2 * C;
+    const int C = g.C, NE = PS2 * C;
     const CubeLayout Ly = cube_layout(C, K);
+    const int nf = Ly.nf, nfp = Ly.nfp, NI = nf * PS2;
     float* bas = reinterpret_cast<float*>(smem + Ly.bas);
-    float* twc = reinterpret_cast<float*>(smem + Ly.tw);
-    float* tws = twc + C;
+    float* tc = reinterpret_cast<float*>(smem + Ly.tc);
+    float* ts = reinterpret_cast<float*>(smem + Ly.ts);
     double* t64c = reinterpret_cast<double*>(smem + Ly.tw64);
     double* t64s = t64c + C;
-    float* xr = reinterpret_cast<float*>(smem + Ly.xr);
-    float* fa = reinterpret_cast<float*>(smem + Ly.fa);
-    float* fb = reinterpret_cast<float*>(smem + Ly.fb);
-    float* sc = reinterpret_cast<float*>(smem + Ly.sc);
-    int* pos = reinterpret_cast<int*>(smem + Ly.pos);
+    float* R = reinterpret_cast<float*>(smem + Ly.R);
+    float* P = reinterpret_cast<float*>(smem + Ly.P);
+    float* Q = reinterpret_cast<float*>(smem + Ly.Q);
+    unsigned* stk = reinterpret_cast<unsigned*>(smem + Ly.stk);
+    int* base = reinterpret_cast<int*>(smem + Ly.base);
     int* misc = reinterpret_cast<int*>(smem + Ly.misc);      // 0 kept in group, 1 kept in slot, 2 row mask,
-                                                              // 5, 6 squared slot norms (float, by slot parity)
-    int* pixnz = reinterpret_cast<int*>(smem + Ly.pixnz);
+                                                              // 3 slots holding a kept coefficient,
+                                                              // 5, 6 squared slot norms (float, by step parity)
     const int tid = threadIdx.x, lane = tid & 31;
     float* scratch = a.scratch + (size_t)blockIdx.x * K * NE;
     const uint8_t* img = a.img;
     const int nbw = (K * NE + 31) / 32;
+    // t / nf and t / C as a high multiply (exact for t < 2^16 and divisors up to 64)
+    const unsigned mg_nf = 0xffffffffu / (unsigned)nf + 1u, mg_c = 0xffffffffu / (unsigned)C + 1u;
 
-    for (int t = tid; t < 2 * nf * 2 * PS2; t += CB_THREADS) bas[t] = a.basis32[t];
+    // the basis, global [U | V][f][re, im][a][i] (128 floats per block) to BS floats per block
+    for (int t = tid; t < 2 * nf * 128; t += CB_THREADS) bas[(t >> 7) * BS + (t & 127)] = a.basis32[t];
+    for (int t = tid; t < nf * nfp; t += CB_THREADS) {
+        const int r = t / nfp, f = t - r * nfp;
+        float sn = 0.f, cs = 0.f;
+        if (f < nf) sincospif(2.f * (float)((r * f) % C) / (float)C, &sn, &cs);
+        tc[t] = cs;
+        ts[t] = -sn;
+    }
     for (int t = tid; t < C; t += CB_THREADS) {
-        float sn, cs;
-        sincospif(2.f * (float)t / (float)C, &sn, &cs);
-        twc[t] = cs;
-        tws[t] = sn;
         double sd, cd;
         sincospi(2.0 * t / C, &sd, &cd);
         t64c[t] = cd;
         t64s[t] = sd;
     }
-    auto U = [&](int f, int ri, int a_, int i) { return bas[((0 * nf + f) * 2 + ri) * PS2 + a_ * PS + i]; };
-    auto V = [&](int f, int ri, int b_, int j) { return bas[((1 * nf + f) * 2 + ri) * PS2 + b_ * PS + j]; };
 
     for (int grp = blockIdx.x; grp < g.ngroups(); grp += gridDim.x) {
         __syncthreads();
@@ -104,246 +301,292 @@ __global__ void __launch_bounds__(CB_THREADS) cube_filter_kernel(CubeArgs a) {
             // a caller-given index outside the image is clamped so that no access leaves it
             const int v = a.idx[(size_t)grp * K + tid];
             const int y = v / g.W, x = v - y * g.W;
-            pos[2 * tid] = min(max(y, 0), g.H - PS);
-            pos[2 * tid + 1] = min(max(x, 0), g.W - PS);
+            base[tid] = min(max(y, 0), g.H - PS) * g.W + min(max(x, 0), g.W - PS);
         }
         if (tid < 16) misc[tid] = 0;
         if (a.mask_out)
             for (int t = tid; t < nbw; t += CB_THREADS) a.mask_out[(size_t)grp * nbw + t] = 0u;
         __syncthreads();
-        for (int m = 0; m < K; ++m) {
-            int k0, L, half, sl;
-            haar_row<K>(m, k0, L, half, sl);
-            // raw slot: integer Haar combination of the support's patches, and its squared norm
+        int sp = 0;
+        for (int step = 0, m = K / 2; step < K; ++step, m = haar_next<K>(m)) {
+            int k0, L, sl;
+            haar_node<K>(m, k0, L, sl);
+            const bool lowest = m != 0 && L == 2;
+            const int sp_in = sp;
+            sp += lowest ? 1 : -1;
+            // raw slot, folded (s | d rows of R), from the children's sums (popped) or, on the lowest
+            // level, from the two patches; the row's own sum is pushed. Sums of uint8 values over at
+            // most K = 32 patches fit 16 bits, so a word holds the two bands c and C - c and one
+            // 32-bit addition adds both.
             float nq = 0.f;
-            for (int e = tid; e < NE; e += CB_THREADS) {
-                const int p = e / C, c = e - p * C, pa = p / PS, pb = p - pa * PS;
-                int s = 0;
-                for (int k = k0; k < k0 + L; ++k) {
-                    const int v = img[((size_t)(pos[2 * k] + pa) * g.W + pos[2 * k + 1] + pb) * C + c];
-                    s += (k - k0 < half) ? v : -v;
+            for (int t = tid; t < NI; t += CB_THREADS) {
+                const int p = __umulhi((unsigned)t, mg_nf), c = t - p * nf;
+                const bool paired = c > 0 && 2 * c < C;
+                unsigned lft, rgt = 0u;
+                if (m == 0) {
+                    lft = stk[(sp_in - 1) * NI + t];
+                } else if (lowest) {
+                    const uint8_t* i1 = img + ((p >> 3) * g.W + (p & 7)) * C + c;
+                    const int o2 = paired ? C - 2 * c : 0;
+                    const int b0 = base[k0] * C, b1 = base[k0 + 1] * C;
+                    lft = (unsigned)i1[b0] | ((unsigned)i1[b0 + o2] << 16);
+                    rgt = (unsigned)i1[b1] | ((unsigned)i1[b1 + o2] << 16);
+                    stk[sp_in * NI + t] = lft + rgt;
+                } else {
+                    rgt = stk[(sp_in - 1) * NI + t];
+                    lft = stk[(sp_in - 2) * NI + t];
+                    stk[(sp_in - 2) * NI + t] = lft + rgt;
                 }
-                xr[e] = (float)s;
-                nq = fmaf((float)s, (float)s, nq);
+                const int s1 = (int)(lft & 0xffffu) - (int)(rgt & 0xffffu);
+                const int s2 = paired ? (int)(lft >> 16) - (int)(rgt >> 16) : 0;
+                R[c * RS + p] = (float)(s1 + s2);
+                R[(nf + c) * RS + p] = (float)(s1 - s2) * (paired ? 1.f : 0.f);
+                nq = fmaf((float)s1, (float)s1, fmaf((float)s2, (float)s2, nq));
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) nq += __shfl_xor_sync(0xffffffffu, nq, off);
             if (tid == 0) { misc[1] = 0; misc[2] = 0; }
-            if (tid < PS2) pixnz[tid] = 0;
-            if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[5 + (m & 1)]), nq);
+            if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[5 + (step & 1)]), nq);
             __syncthreads();
-            // band DFT: X_f[p] = sum_c x[p][c] w^{fc}, w = exp(-2 pi i / C)
-            for (int t = tid; t < nf * PS2; t += CB_THREADS) {
-                const int f = t / PS2, p = t - f * PS2;
-                float re = 0.f, im = 0.f;
-                for (int c = 0, k = 0; c < C; ++c, k = (k + f >= C) ? k + f - C : k + f) {
-                    const float x = xr[p * C + c];
-                    re = fmaf(x, twc[k], re);
-                    im = fmaf(-x, tws[k], im);
-                }
-                fa[2 * t] = re;
-                fa[2 * t + 1] = im;
-            }
+            band_dft(R, P, tc, ts, nf, nfp, tid);
             __syncthreads();
-            // Y_f[i][b] = sum_a conj(U_f[a][i]) X_f[a][b]
-            for (int t = tid; t < nf * PS2; t += CB_THREADS) {
-                const int f = t / PS2, i = (t / PS) % PS, b = t % PS;
-                float re = 0.f, im = 0.f;
+            // S_f[i][:] = (sum_a conj(U_f[a][i]) X_f[a][:]) V_f, one thread per (f, i)
+            for (int t = tid; t < nf * PS; t += CB_THREADS) {
+                const int f = t >> 3, i = t & 7;
+                const float* Ub = bas + f * BS;
+                const float* Vb = bas + (nf + f) * BS;
+                float yr[8], yi[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) yr[b] = yi[b] = 0.f;
 #pragma unroll
                 for (int a_ = 0; a_ < PS; ++a_) {
-                    const float ur = U(f, 0, a_, i), ui = U(f, 1, a_, i);
-                    const float xr_ = fa[2 * (f * PS2 + a_ * PS + b)], xi = fa[2 * (f * PS2 + a_ * PS + b) + 1];
-                    re = fmaf(ur, xr_, fmaf(ui, xi, re));
-                    im = fmaf(ur, xi, fmaf(-ui, xr_, im));
+                    const float ur = Ub[a_ * 8 + i], ui = Ub[64 + a_ * 8 + i];
+                    float xr_[8], xi[8];
+                    load8s(P + f * RS + a_ * 8, xr_);
+                    load8s(P + (nf + f) * RS + a_ * 8, xi);
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        yr[b] = fmaf(ur, xr_[b], fmaf(ui, xi[b], yr[b]));
+                        yi[b] = fmaf(ur, xi[b], fmaf(-ui, xr_[b], yi[b]));
+                    }
                 }
-                fb[2 * t] = re;
-                fb[2 * t + 1] = im;
-            }
-            __syncthreads();
-            // S_f[i][j] = sum_b Y_f[i][b] V_f[b][j]
-            for (int t = tid; t < nf * PS2; t += CB_THREADS) {
-                const int f = t / PS2, i = (t / PS) % PS, j = t % PS;
-                float re = 0.f, im = 0.f;
+                float sr[8], si[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) sr[j] = si[j] = 0.f;
 #pragma unroll
                 for (int b = 0; b < PS; ++b) {
-                    const float vr = V(f, 0, b, j), vi = V(f, 1, b, j);
-                    const float yr = fb[2 * (f * PS2 + i * PS + b)], yi = fb[2 * (f * PS2 + i * PS + b) + 1];
-                    re = fmaf(yr, vr, fmaf(-yi, vi, re));
-                    im = fmaf(yr, vi, fmaf(yi, vr, im));
-                }
-                fa[2 * t] = re;
-                fa[2 * t + 1] = im;
-            }
-            __syncthreads();
-            // inverse band DFT (real result): S[p][c] = (1/C) sum_f S_f[p] w^{-fc}, slices C - f = conj(f)
-            for (int e = tid; e < NE; e += CB_THREADS) {
-                const int p = e / C, c = e - p * C;
-                float s = fa[2 * p];
-                for (int f = 1, k = c; 2 * f < C; ++f, k = (k + c >= C) ? k + c - C : k + c) {
-                    const float re = fa[2 * (f * PS2 + p)], im = fa[2 * (f * PS2 + p) + 1];
-                    s = fmaf(2.f * re, twc[k], fmaf(-2.f * im, tws[k], s));
-                }
-                if ((C & 1) == 0) s = fmaf(fa[2 * ((C / 2) * PS2 + p)], (c & 1) ? -1.f : 1.f, s);
-                sc[e] = s / (float)C;
-            }
-            __syncthreads();
-            // threshold (the unnormalised slot carries sqrt(L)); kept values scaled by 1/L for the
-            // unnormalised synthesis. Entries inside the guard band are decided again in FP64 by the
-            // warp that met them.
-            {
-                // The FP32 error of a slot's coefficients is bounded by a multiple of the slot's own
-                // norm (its transform is orthonormal up to the unnormalised Haar factor), so the band
-                // is band_rel x ||slot||_F, plus the rounding of tau.
-                const float r = sqrtf((float)L), tl = a.tau32 * r;
-                const float dl = a.band_rel * sqrtf(__int_as_float(misc[5 + (m & 1)])) + a.band_abs * r;
-                const int iters = (NE + CB_THREADS - 1) / CB_THREADS;
-                for (int it = 0; it < iters; ++it) {
-                    const int e = it * CB_THREADS + tid;
-                    const bool valid = e < NE;
-                    const float v = valid ? sc[e] : 0.f;
-                    if (valid && a.coef_out) a.coef_out[((size_t)grp * K + m) * NE + e] = v / r;
-                    const float d = fabsf(v) - tl;
-                    const bool band = valid && fabsf(d) <= dl;
-                    bool keep = valid && !band && d >= 0.f;
-                    unsigned bal = __ballot_sync(0xffffffffu, band);
-                    while (bal) {                       // warp-uniform
-                        const int l = __ffs(bal) - 1;
-                        bal &= bal - 1;
-                        const int eb = __shfl_sync(0xffffffffu, e, l);
-                        const int pb = eb / C, cb = eb - pb * C, ib = pb / PS, jb = pb - ib * PS;
-                        // FP64: P_f = sum_{pixels} conj(U_f[a][ib]) V_f[b][jb] X_f[a][b], X_f the band DFT
-                        // of the raw slot (exact integers); S = (1/C) sum_f w^{-f cb} P_f, slices C - f
-                        // being the conjugates of f. Lane l takes pixels l and l + 32.
-                        double acc = 0.0;
-                        for (int f = 0; 2 * f <= C; ++f) {
-                            double pr = 0.0, pi = 0.0;
-                            for (int q = lane; q < PS2; q += 32) {
-                                const int qa = q / PS, qb = q - qa * PS;
-                                double xre = 0.0, xim = 0.0;
-                                for (int cp = 0, k = 0; cp < C; ++cp, k = (k + f >= C) ? k + f - C : k + f) {
-                                    const double x = (double)xr[q * C + cp];
-                                    xre = fma(x, t64c[k], xre);
-                                    xim = fma(-x, t64s[k], xim);
-                                }
-                                const double* u = a.basis64 + 2 * (((size_t)0 * C + f) * PS2 + qa * PS + ib);
-                                const double* vv = a.basis64 + 2 * (((size_t)1 * C + f) * PS2 + qb * PS + jb);
-                                const double cr = u[0] * vv[0] + u[1] * vv[1];      // conj(u) v
-                                const double ci = u[0] * vv[1] - u[1] * vv[0];
-                                pr += cr * xre - ci * xim;
-                                pi += cr * xim + ci * xre;
-                            }
+                    float vr[8], vi[8];
+                    load8s(Vb + b * 8, vr);
+                    load8s(Vb + 64 + b * 8, vi);
 #pragma unroll
-                            for (int off = 16; off > 0; off >>= 1) {
-                                pr += __shfl_xor_sync(0xffffffffu, pr, off);
-                                pi += __shfl_xor_sync(0xffffffffu, pi, off);
-                            }
-                            const int k2 = (int)(((long long)f * cb) % C);
-                            const double wgt = (f == 0 || 2 * f == C) ? 1.0 : 2.0;
-                            acc += wgt * (t64c[k2] * pr - t64s[k2] * pi);  // Re(w^{-f cb} P_f)
-                        }
-                        if (lane == l) keep = fabs(acc / (double)C) >= a.tau64 * sqrt((double)L);
+                    for (int j = 0; j < 8; ++j) {
+                        sr[j] = fmaf(yr[b], vr[j], fmaf(-yi[b], vi[j], sr[j]));
+                        si[j] = fmaf(yr[b], vi[j], fmaf(yi[b], vr[j], si[j]));
                     }
-                    if (valid) {
-                        sc[e] = keep ? v * (1.f / (float)L) : 0.f;
-                        if (keep) {
-                            const int p = e / C;
-                            pixnz[p] = 1;
-                            atomicOr(&misc[2], 1 << (p / PS));
-                            if (a.mask_out) {
-                                const size_t bit = (size_t)m * NE + e;
-                                atomicOr(&a.mask_out[(size_t)grp * nbw + bit / 32], 1u << (bit % 32));
-                            }
-                        }
-                    }
-                    const int wk = __reduce_add_sync(0xffffffffu, keep ? 1 : 0);
-                    if (lane == 0 && wk) atomicAdd(&misc[1], wk);
                 }
-                if (tid == 0) misc[5 + ((m + 1) & 1)] = 0;      // the next slot's norm accumulator
+                const float w = (f == 0 || 2 * f == C ? 1.f : 2.f) / (float)C;
+                store8s(Q + f * RS + i * 8, sr, w);
+                store8s(Q + (nf + f) * RS + i * 8, si, w);
             }
+            __syncthreads();
+            // Inverse band DFT with the threshold in its epilogue (the unnormalised slot carries
+            // sqrt(L)): a coefficient x is kept when |x| - tau sqrt(L) > band, dropped below -band and
+            // decided in FP64 in between (the FP32 error of a slot's coefficients is bounded by a
+            // multiple of the slot's own norm, its transform being orthonormal up to the Haar factor,
+            // so the band is band_rel x ||slot||_F plus the rounding of tau). Kept values times 1/L,
+            // for the unnormalised synthesis, are folded again (s | d rows of P).
+            {
+                const float r = sqrtf((float)L), tl = a.tau32 * r, invL = 1.f / (float)L;
+                const float dl = a.band_rel * sqrtf(__int_as_float(misc[5 + (step & 1)])) + a.band_abs * r;
+                const double tlim = a.tau64 * sqrt((double)L);
+                const int nt = NPT * (nfp >> 2), ntw = (nt + 31) & ~31;
+                constexpr int HB = 4 * TP;                            // values per half of the bit masks
+                for (int t = tid; t < ntw; t += CB_THREADS) {         // whole warps: ballots below
+                    const bool valid = t < nt;
+                    const int p0 = (t % NPT) * TP, c0 = valid ? (t / NPT) << 2 : 0;
+                    float A[4][TP], B[4][TP];
+                    idft_tile(Q, tc, ts, nf, nfp, p0, c0, A, B);
+                    // value j = TP ci + pi: band c0 + ci as bit j, band C - c0 - ci as bit HB + j
+                    unsigned keep = 0u, band = 0u;
+#pragma unroll
+                    for (int ci = 0; ci < 4; ++ci) {
+                        const int c = c0 + ci;
+                        const bool lo_ok = valid && c < nf, hi_ok = valid && c > 0 && 2 * c < C;
+#pragma unroll
+                        for (int pi = 0; pi < TP; ++pi) {
+                            const int j = ci * TP + pi;
+                            const float v0 = A[ci][pi] + B[ci][pi], v1 = A[ci][pi] - B[ci][pi];
+                            const float d0 = fabsf(v0) - tl, d1 = fabsf(v1) - tl;
+                            keep |= ((lo_ok && d0 > dl) ? 1u : 0u) << j;
+                            keep |= ((hi_ok && d1 > dl) ? 1u : 0u) << (HB + j);
+                            band |= ((lo_ok && fabsf(d0) <= dl) ? 1u : 0u) << j;
+                            band |= ((hi_ok && fabsf(d1) <= dl) ? 1u : 0u) << (HB + j);
+                            if (a.coef_out) {
+                                float* co = a.coef_out + ((size_t)grp * K + m) * NE + (p0 + pi) * C;
+                                if (lo_ok) co[c] = v0 / r;
+                                if (hi_ok) co[C - c] = v1 / r;
+                            }
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, band != 0u)) {
+                        for (int j = 0; j < 2 * HB; ++j) {
+                            unsigned bal = __ballot_sync(0xffffffffu, (band >> j) & 1u);
+                            while (bal) {               // warp-uniform
+                                const int l = __ffs(bal) - 1;
+                                bal &= bal - 1;
+                                const int tl_ = __shfl_sync(0xffffffffu, t, l), jj = j % HB;
+                                const int pb = (tl_ % NPT) * TP + jj % TP, cl = ((tl_ / NPT) << 2) + jj / TP;
+                                const double x = coef64(R, t64c, t64s, a.basis64, C, nf, pb, j < HB ? cl : C - cl,
+                                                        lane);
+                                if (lane == l && fabs(x) >= tlim) keep |= 1u << j;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int ci = 0; ci < 4; ++ci) {
+                        const int c = c0 + ci;
+                        if (!valid || c >= nf) continue;
+                        const bool paired = c > 0 && 2 * c < C;
+                        float lo[TP], hi[TP];
+#pragma unroll
+                        for (int pi = 0; pi < TP; ++pi) {
+                            const int j = ci * TP + pi;
+                            const float x0 = ((keep >> j) & 1u) ? (A[ci][pi] + B[ci][pi]) * invL : 0.f;
+                            const float x1 = ((keep >> (HB + j)) & 1u) ? (A[ci][pi] - B[ci][pi]) * invL : 0.f;
+                            lo[pi] = x0 + x1;
+                            hi[pi] = paired ? x0 - x1 : 0.f;
+                        }
+                        stv<TP>(P + c * RS + p0, lo);
+                        stv<TP>(P + (nf + c) * RS + p0, hi);
+                    }
+                    if (a.mask_out)
+                        for (unsigned kb = keep; kb; kb &= kb - 1) {
+                            const int j = __ffs(kb) - 1, jj = j % HB, c = c0 + jj / TP;
+                            const size_t bit = (size_t)m * NE + (p0 + jj % TP) * C + (j < HB ? c : C - c);
+                            atomicOr(&a.mask_out[(size_t)grp * nbw + bit / 32], 1u << (bit % 32));
+                        }
+                    const int nk = __reduce_add_sync(0xffffffffu, __popc(keep));
+                    const unsigned rb = __reduce_or_sync(0xffffffffu, keep ? 1u << (p0 >> 3) : 0u);
+                    if (lane == 0 && nk) {
+                        atomicAdd(&misc[1], nk);
+                        atomicOr(&misc[2], (int)rb);
+                    }
+                }
+                if (tid == 0) misc[5 + ((step + 1) & 1)] = 0;   // the next slot's norm accumulator
+            }
+            __syncthreads();
+            // A slot without a kept coefficient is all zeros: nothing is written for it. No barrier is
+            // needed on that path: the next slot's writes before its first barrier are the raw slot
+            // (read by nobody after the barrier above), the thread's own stack entries and misc[1],
+            // misc[2], which are zero already.
+            if (misc[1] == 0) continue;
+            const int rows = misc[2];
+            if (tid == 0) {
+                misc[0] += misc[1];
+                misc[3] |= 1 << sl;
+            }
+            // inverse: band DFT of the kept coefficients
+            band_dft(P, Q, tc, ts, nf, nfp, tid);
+            __syncthreads();
+            // Z_f[i][:] = T_f[i][:] V_f^H on the kept rows i (to P)
+            for (int t = tid; t < nf * PS; t += CB_THREADS) {
+                const int f = t >> 3, i = t & 7;
+                if (!((rows >> i) & 1)) continue;
+                const float* Vb = bas + (nf + f) * BS;
+                float tr[8], ti[8], zr[8], zi[8];
+                load8s(Q + f * RS + i * 8, tr);
+                load8s(Q + (nf + f) * RS + i * 8, ti);
+#pragma unroll
+                for (int b = 0; b < PS; ++b) {
+                    float vr[8], vi[8];
+                    load8s(Vb + b * 8, vr);
+                    load8s(Vb + 64 + b * 8, vi);
+                    float re = 0.f, im = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        re = fmaf(tr[j], vr[j], fmaf(ti[j], vi[j], re));
+                        im = fmaf(ti[j], vr[j], fmaf(-tr[j], vi[j], im));
+                    }
+                    zr[b] = re;
+                    zi[b] = im;
+                }
+                store8s(P + f * RS + i * 8, zr, 1.f);
+                store8s(P + (nf + f) * RS + i * 8, zi, 1.f);
+            }
+            __syncthreads();
+            // G_f[a][:] = sum_{i kept} U_f[a][i] Z_f[i][:] (to Q, times w_f / C)
+            for (int t = tid; t < nf * PS; t += CB_THREADS) {
+                const int f = t >> 3, a_ = t & 7;
+                float ur[8], ui[8], gr[8], gi[8];
+                load8s(bas + f * BS + a_ * 8, ur);
+                load8s(bas + f * BS + 64 + a_ * 8, ui);
+#pragma unroll
+                for (int b = 0; b < 8; ++b) gr[b] = gi[b] = 0.f;
+#pragma unroll
+                for (int i = 0; i < PS; ++i) {
+                    if (!((rows >> i) & 1)) continue;
+                    float zr[8], zi[8];
+                    load8s(P + f * RS + i * 8, zr);
+                    load8s(P + (nf + f) * RS + i * 8, zi);
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        gr[b] = fmaf(ur[i], zr[b], fmaf(-ui[i], zi[b], gr[b]));
+                        gi[b] = fmaf(ur[i], zi[b], fmaf(ui[i], zr[b], gi[b]));
+                    }
+                }
+                const float w = (f == 0 || 2 * f == C ? 1.f : 2.f) / (float)C;
+                store8s(Q + f * RS + a_ * 8, gr, w);
+                store8s(Q + (nf + f) * RS + a_ * 8, gi, w);
+            }
+            __syncthreads();
+            // inverse band DFT to the spatial slot [c][p] in R, then to the scratch as [p][c]
+            band_idft(Q, R, tc, ts, C, nf, nfp, tid);
             __syncthreads();
             float* dst = scratch + (size_t)sl * NE;
-            if (misc[1] == 0) {
-                for (int e = tid; e < NE; e += CB_THREADS) dst[e] = 0.f;
-                continue;                               // no barrier needed: the next slot's first writes
-            }                                           // (xr, misc, pixnz) are after a barrier below
-            if (tid == 0) misc[0] += misc[1];
-            const int rows = misc[2];
-            // inverse: band DFT of the kept coefficients (pixels without one stay zero)
-            for (int t = tid; t < nf * PS2; t += CB_THREADS) {
-                const int f = t / PS2, p = t - f * PS2;
-                float re = 0.f, im = 0.f;
-                if (pixnz[p])
-                    for (int c = 0, k = 0; c < C; ++c, k = (k + f >= C) ? k + f - C : k + f) {
-                        const float x = sc[p * C + c];
-                        re = fmaf(x, twc[k], re);
-                        im = fmaf(-x, tws[k], im);
-                    }
-                fa[2 * t] = re;
-                fa[2 * t + 1] = im;
-            }
-            __syncthreads();
-            // Z_f[i][b] = sum_j T_f[i][j] conj(V_f[b][j]) on the kept rows
-            for (int t = tid; t < nf * PS2; t += CB_THREADS) {
-                const int f = t / PS2, i = (t / PS) % PS, b = t % PS;
-                float re = 0.f, im = 0.f;
-                if ((rows >> i) & 1)
-#pragma unroll
-                    for (int j = 0; j < PS; ++j) {
-                        const float vr = V(f, 0, b, j), vi = V(f, 1, b, j);
-                        const float tr = fa[2 * (f * PS2 + i * PS + j)], ti = fa[2 * (f * PS2 + i * PS + j) + 1];
-                        re = fmaf(tr, vr, fmaf(ti, vi, re));
-                        im = fmaf(ti, vr, fmaf(-tr, vi, im));
-                    }
-                fb[2 * t] = re;
-                fb[2 * t + 1] = im;
-            }
-            __syncthreads();
-            // G_f[a][b] = sum_i U_f[a][i] Z_f[i][b] over the kept rows
-            for (int t = tid; t < nf * PS2; t += CB_THREADS) {
-                const int f = t / PS2, a_ = (t / PS) % PS, b = t % PS;
-                float re = 0.f, im = 0.f;
-                for (int r = rows; r; r &= r - 1) {
-                    const int i = __ffs(r) - 1;
-                    const float ur = U(f, 0, a_, i), ui = U(f, 1, a_, i);
-                    const float zr = fb[2 * (f * PS2 + i * PS + b)], zi = fb[2 * (f * PS2 + i * PS + b) + 1];
-                    re = fmaf(ur, zr, fmaf(-ui, zi, re));
-                    im = fmaf(ur, zi, fmaf(ui, zr, im));
-                }
-                fa[2 * t] = re;
-                fa[2 * t + 1] = im;
-            }
-            __syncthreads();
-            // inverse band DFT -> spatial slot in the scratch
             for (int e = tid; e < NE; e += CB_THREADS) {
-                const int p = e / C, c = e - p * C;
-                float s = fa[2 * p];
-                for (int f = 1, k = c; 2 * f < C; ++f, k = (k + c >= C) ? k + c - C : k + c) {
-                    const float re = fa[2 * (f * PS2 + p)], im = fa[2 * (f * PS2 + p) + 1];
-                    s = fmaf(2.f * re, twc[k], fmaf(-2.f * im, tws[k], s));
-                }
-                if ((C & 1) == 0) s = fmaf(fa[2 * ((C / 2) * PS2 + p)], (c & 1) ? -1.f : 1.f, s);
-                dst[e] = s / (float)C;
+                const int p = __umulhi((unsigned)e, mg_c), c = e - p * C;
+                dst[e] = R[c * RS + p];
             }
             __syncthreads();
         }
         __syncthreads();
-        // weight of the group, then Haar synthesis per fibre and aggregation
+        // weight of the group, then Haar synthesis per fibre (slots without a kept coefficient are
+        // zero and not read) and aggregation
         float wg = 1.f;
         if (a.w_in) wg = a.w_in[grp];
         else if (a.agg_mode == 1) wg = 1.f / (float)max(1, misc[0]);
         if (tid == 0 && a.weights_out) a.weights_out[grp] = wg;
+        const unsigned nzs = (unsigned)misc[3];
         for (int e = tid; e < NE; e += CB_THREADS) {
-            float v[K];
+            const int p = __umulhi((unsigned)e, mg_c), c = e - p * C, pa = p >> 3, pb = p & 7;
+            if (nzs) {
+                // after the first level of the synthesis (slots 0 and K/2) the two halves of the
+                // in-place layout are independent: K = 32 runs as two syntheses of 16
+                constexpr int KH = K > 16 ? K / 2 : K;
+#pragma unroll 1
+                for (int h = 0; h < K / KH; ++h) {
+                    float v[KH];
 #pragma unroll
-            for (int k = 0; k < K; ++k) v[k] = scratch[(size_t)k * NE + e];
-            haar_inv_sum<K>(v);
-            const int p = e / C, c = e - p * C, pa = p / PS, pb = p - pa * PS;
+                    for (int k = 1; k < KH; ++k) {
+                        const int sk = h * KH + k;
+                        v[k] = ((nzs >> sk) & 1u) ? scratch[(size_t)sk * NE + e] : 0.f;
+                    }
+                    v[0] = (nzs & 1u) ? scratch[e] : 0.f;
+                    if constexpr (K > KH) {
+                        const float sh = ((nzs >> KH) & 1u) ? scratch[(size_t)KH * NE + e] : 0.f;
+                        v[0] = h == 0 ? v[0] + sh : v[0] - sh;
+                    }
+                    haar_inv_sum<KH>(v);
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const size_t pix = (size_t)(pos[2 * k] + pa) * g.W + pos[2 * k + 1] + pb;
-                atomicAdd(&a.num[pix * C + c], wg * v[k]);
-                if (c == 0) atomicAdd(&a.den[pix], wg);
+                    for (int k = 0; k < KH; ++k) {
+                        const size_t pix = (size_t)base[h * KH + k] + pa * g.W + pb;
+                        atomicAdd(&a.num[pix * C + c], wg * v[k]);
+                    }
+                }
             }
+            if (c == 0)
+#pragma unroll
+                for (int k = 0; k < K; ++k) atomicAdd(&a.den[(size_t)base[k] + pa * g.W + pb], wg);
         }
     }
 }
@@ -364,14 +607,32 @@ cudaError_t launch_cube_t(const CubeArgs& a, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// resident CTAs per SM of the filter for C bands (registers and shared memory), at least 1
+template <int K>
+int cube_per_sm(int C) {
+    const int smem = cube_layout(C, K).total;
+    auto fn = cube_filter_kernel<K>;
+    int n = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, CB_THREADS, smem) != cudaSuccess)
+        n = 1;
+    return n < 1 ? 1 : n;
+}
+
 }  // namespace
 
 size_t cube_smem_bytes(int C, int K) { return (size_t)cube_layout(C, K).total; }
 
 int cube_grid(int C, int K, int64_t ngroups) {
-    const size_t smem = cube_smem_bytes(C, K);
-    int per_sm = (int)((227 * 1024) / (smem + 1024));
-    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    int per_sm = 1;
+    switch (K) {
+        case 2: per_sm = cube_per_sm<2>(C); break;
+        case 4: per_sm = cube_per_sm<4>(C); break;
+        case 8: per_sm = cube_per_sm<8>(C); break;
+        case 16: per_sm = cube_per_sm<16>(C); break;
+        case 32: per_sm = cube_per_sm<32>(C); break;
+        default: break;
+    }
     const int64_t grid = (int64_t)per_sm * device_sm_count();
     return (int)(grid < ngroups ? grid : ngroups);
 }

@@ -25,6 +25,8 @@ def _case(Hh, Ww, N, sigma, seed):
     ((64, 64, 31), dict(ps=8, stride=3, window=15, K=16), 12.0),     # the 31-band cubes of the ICVL size class
     ((48, 56, 34), dict(ps=8, stride=3, window=11, K=8), 15.0),      # 34 bands (Real-HSI): a real middle slice
     ((40, 45, 5), dict(ps=8, stride=2, window=9, K=4, agg_mode="sparsity"), 20.0),
+    ((56, 60, 34), dict(ps=8, stride=3, window=18, K=32), 12.0),     # the benchmarked cube geometry
+    ((30, 33, 7), dict(ps=8, stride=2, window=9, K=2), 15.0),
 ])
 def test_cube_parity(shape, prm, sigma):
     Hh, Ww, N = shape
