@@ -29,19 +29,29 @@
 // Both DFTs are register tiles (2 pixels x 4 frequencies or bands) over a cos table and a -sin
 // table that serve both directions (the tables are symmetric in f and c). Rows of 64 pixels are
 // RS = 68 floats apart, so that the four slices a warp touches at once fall in different banks.
+#include <type_traits>
+
 #include "filter_impl.cuh"
 
 namespace htsvd {
 
 namespace {
 
-constexpr int CB_THREADS = 256;
+constexpr int CB_MAX_THREADS = 256;
+// Threads of a CTA: one per DFT tile (2 pixels x 4 frequencies), 32 per frequency quad, within
+// [128, 256]: every thread has work in the transform phases, and up to 128 registers each.
+__host__ __device__ inline int cube_threads(int C) {
+    const int n = 32 * ((C / 2 + 1 + 3) / 4);
+    return n < 128 ? 128 : (n > CB_MAX_THREADS ? CB_MAX_THREADS : n);
+}
 constexpr int RS = 68;       // floats per 64-pixel row (16-byte aligned; consecutive rows 4 banks apart)
 constexpr int BS = 136;      // floats per basis block [re, im][a][i] of one (U or V, f) (8 banks apart)
+constexpr int NL = 32;       // slots keeping at most NL coefficients take the sparse inverse
+constexpr int NB = 16;       // guard-band coefficients decided one at a time by the whole CTA
 
 struct CubeLayout {
     int nf, nfp;                                                  // C/2 + 1 and that rounded up to 4
-    int bas, tc, ts, tw64, R, P, Q, stk, base, misc, total;      // byte offsets
+    int bas, tc, ts, tw64, R, P, Q, stk, lst, blist, red, base, misc, total;   // byte offsets
 };
 __host__ __device__ inline int log2_of(int K) {
     int l = 0;
@@ -62,6 +72,9 @@ __host__ __device__ inline CubeLayout cube_layout(int C, int K) {
     L.P = o; o += 4 * (2 * L.nf * RS);              // Fourier slices Re | Im, or folded coefficients
     L.Q = o; o += 4 * (2 * L.nf * RS);
     L.stk = o; o += 4 * (log2_of(K) * L.nf * PS2);  // pending Haar-tree sums, two 16-bit bands per word
+    L.lst = o; o += 16 * NL;                        // kept coefficients of a sparse slot: pixel, band, value
+    L.blist = o; o += 16 * NB;                      // coefficients inside the guard band: pixel, band, value
+    L.red = o; o += 8 * (CB_MAX_THREADS / 32);      // cross-warp sums
     L.base = o; o += 4 * K;                         // pixel index of each patch's corner
     L.misc = o; o += 4 * 16;
     L.total = o;
@@ -128,8 +141,8 @@ constexpr int NPT = PS2 / TP;                 // pixel tiles
 // Band DFT of a folded real slot: src rows [0, nf) s_c, [nf, 2 nf) d_c; dst rows [0, nf) Re X_f,
 // [nf, 2 nf) Im X_f.
 __device__ __forceinline__ void band_dft(const float* __restrict__ src, float* __restrict__ dst,
-                                         const float* tc, const float* ts, int nf, int nfp, int tid) {
-    for (int t = tid; t < NPT * (nfp >> 2); t += CB_THREADS) {
+                                         const float* tc, const float* ts, int nf, int nfp, int tid, int nthr) {
+    for (int t = tid; t < NPT * (nfp >> 2); t += nthr) {
         const int p0 = (t % NPT) * TP, f0 = (t / NPT) << 2;
         float re[4][TP], im[4][TP];
 #pragma unroll
@@ -141,6 +154,50 @@ __device__ __forceinline__ void band_dft(const float* __restrict__ src, float* _
             float s[TP], d[TP];
             ldv<TP>(src + c * RS + p0, s);
             ldv<TP>(src + (nf + c) * RS + p0, d);
+            const float4 wc = ld4(tc + c * nfp + f0), ws = ld4(ts + c * nfp + f0);
+#pragma unroll
+            for (int fi = 0; fi < 4; ++fi)
+#pragma unroll
+                for (int pi = 0; pi < TP; ++pi) {
+                    re[fi][pi] = fmaf(s[pi], comp(wc, fi), re[fi][pi]);
+                    im[fi][pi] = fmaf(d[pi], comp(ws, fi), im[fi][pi]);
+                }
+        }
+#pragma unroll
+        for (int fi = 0; fi < 4; ++fi)
+            if (f0 + fi < nf) {
+                stv<TP>(dst + (f0 + fi) * RS + p0, re[fi]);
+                stv<TP>(dst + (nf + f0 + fi) * RS + p0, im[fi]);
+            }
+    }
+}
+
+// Band DFT of an unfolded real slot (src rows c = 0 .. C-1, band c), folded on load; dst as band_dft.
+__device__ __forceinline__ void band_dft_unfolded(const float* __restrict__ src, float* __restrict__ dst,
+                                                  const float* tc, const float* ts, int C, int nf, int nfp, int tid,
+                                                  int nthr) {
+    for (int t = tid; t < NPT * (nfp >> 2); t += nthr) {
+        const int p0 = (t % NPT) * TP, f0 = (t / NPT) << 2;
+        float re[4][TP], im[4][TP];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < TP; ++j) re[i][j] = im[i][j] = 0.f;
+        for (int c = 0; c < nf; ++c) {
+            float s[TP], d[TP];
+            ldv<TP>(src + c * RS + p0, s);
+            if (c > 0 && 2 * c < C) {
+                float y[TP];
+                ldv<TP>(src + (C - c) * RS + p0, y);
+#pragma unroll
+                for (int pi = 0; pi < TP; ++pi) {
+                    d[pi] = s[pi] - y[pi];
+                    s[pi] += y[pi];
+                }
+            } else {
+#pragma unroll
+                for (int pi = 0; pi < TP; ++pi) d[pi] = 0.f;
+            }
             const float4 wc = ld4(tc + c * nfp + f0), ws = ld4(ts + c * nfp + f0);
 #pragma unroll
             for (int fi = 0; fi < 4; ++fi)
@@ -184,24 +241,56 @@ __device__ __forceinline__ void idft_tile(const float* __restrict__ src, const f
     }
 }
 
-// Inverse band DFT to a spatial slot: x_c to row c of dst, x_{C-c} to row C - c.
-__device__ __forceinline__ void band_idft(const float* __restrict__ src, float* dst, const float* tc,
-                                          const float* ts, int C, int nf, int nfp, int tid) {
-    for (int t = tid; t < NPT * (nfp >> 2); t += CB_THREADS) {
+// The same value summed over the whole CTA (every thread calls it with the same (pb, cb) and gets
+// the result): thread t takes the (slice, pixel) pairs t, t + nthr, ...; red holds nthr / 32 doubles.
+__device__ double coef64_cta(const float* R, const double* t64c, const double* t64s, const double* __restrict__ b64,
+                             int C, int nf, int pb, int cb, int tid, int nthr, double* red) {
+    const int ib = pb >> 3, jb = pb & 7;
+    double acc = 0.0;
+    for (int it = tid; it < nf * PS2; it += nthr) {
+        const int f = it >> 6, q = it & 63, qa = q >> 3, qb = q & 7;
+        double xre = 0.0, xim = 0.0;
+        for (int c = 0, k = 0; c < nf; ++c, k = (k + f >= C) ? k + f - C : k + f) {
+            xre = fma((double)R[c * RS + q], t64c[k], xre);
+            xim = fma(-(double)R[(nf + c) * RS + q], t64s[k], xim);
+        }
+        const double* u = b64 + 2 * (((size_t)0 * C + f) * PS2 + qa * PS + ib);
+        const double* vv = b64 + 2 * (((size_t)1 * C + f) * PS2 + qb * PS + jb);
+        const double cr = u[0] * vv[0] + u[1] * vv[1];          // conj(u) v
+        const double ci = u[0] * vv[1] - u[1] * vv[0];
+        const double pr = cr * xre - ci * xim, pi = cr * xim + ci * xre;
+        const int k2 = (f * cb) % C;
+        const double wgt = (f == 0 || 2 * f == C) ? 1.0 : 2.0;
+        acc += wgt * (t64c[k2] * pr - t64s[k2] * pi);              // Re(w^{-f cb} P_f) terms
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < (nthr >> 5); ++w) tot += red[w];
+    __syncthreads();
+    return tot / (double)C;
+}
+
+// Inverse band DFT to a spatial slot in shared memory, [pixel][band] (the layout of the synthesis):
+// x_c to dst[p C + c], x_{C-c} to dst[p C + C - c].
+__device__ __forceinline__ void band_idft_pc(const float* __restrict__ src, float* __restrict__ dst,
+                                             const float* tc, const float* ts, int C, int nf, int nfp, int tid,
+                                             int nthr) {
+    for (int t = tid; t < NPT * (nfp >> 2); t += nthr) {
         const int p0 = (t % NPT) * TP, c0 = (t / NPT) << 2;
         float A[4][TP], B[4][TP];
         idft_tile(src, tc, ts, nf, nfp, p0, c0, A, B);
 #pragma unroll
         for (int ci = 0; ci < 4; ++ci) {
             const int c = c0 + ci;
-            float lo[TP], hi[TP];
 #pragma unroll
             for (int pi = 0; pi < TP; ++pi) {
-                lo[pi] = A[ci][pi] + B[ci][pi];
-                hi[pi] = A[ci][pi] - B[ci][pi];
+                float* o = dst + (p0 + pi) * C;
+                if (c < nf) o[c] = A[ci][pi] + B[ci][pi];
+                if (c > 0 && 2 * c < C) o[C - c] = A[ci][pi] - B[ci][pi];
             }
-            if (c < nf) stv<TP>(dst + c * RS + p0, lo);
-            if (c > 0 && 2 * c < C) stv<TP>(dst + (C - c) * RS + p0, hi);
         }
     }
 }
@@ -253,7 +342,7 @@ __device__ __forceinline__ void store8s(float* p, const float (&r)[8], float sc)
 }
 
 template <int K>
-__global__ void __launch_bounds__(CB_THREADS, 3) cube_filter_kernel(CubeArgs a) {
+__global__ void __launch_bounds__(CB_MAX_THREADS, 2) cube_filter_kernel(CubeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Geo& g = a.g;
     const int C = g.C, NE = PS2 * C;
@@ -268,11 +357,15 @@ __global__ void __launch_bounds__(CB_THREADS, 3) cube_filter_kernel(CubeArgs a) 
     float* P = reinterpret_cast<float*>(smem + Ly.P);
     float* Q = reinterpret_cast<float*>(smem + Ly.Q);
     unsigned* stk = reinterpret_cast<unsigned*>(smem + Ly.stk);
+    int4* lst = reinterpret_cast<int4*>(smem + Ly.lst);
+    int4* blist = reinterpret_cast<int4*>(smem + Ly.blist);
+    double* red = reinterpret_cast<double*>(smem + Ly.red);
     int* base = reinterpret_cast<int*>(smem + Ly.base);
     int* misc = reinterpret_cast<int*>(smem + Ly.misc);      // 0 kept in group, 1 kept in slot, 2 row mask,
-                                                              // 3 slots holding a kept coefficient,
+                                                              // 3 slots holding a kept coefficient, 7 kept listed,
+                                                              // 8 the slot has band coefficients, 9 listed,
                                                               // 5, 6 squared slot norms (float, by step parity)
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
     float* scratch = a.scratch + (size_t)blockIdx.x * K * NE;
     const uint8_t* img = a.img;
     const int nbw = (K * NE + 31) / 32;
@@ -280,15 +373,15 @@ __global__ void __launch_bounds__(CB_THREADS, 3) cube_filter_kernel(CubeArgs a) 
     const unsigned mg_nf = 0xffffffffu / (unsigned)nf + 1u, mg_c = 0xffffffffu / (unsigned)C + 1u;
 
     // the basis, global [U | V][f][re, im][a][i] (128 floats per block) to BS floats per block
-    for (int t = tid; t < 2 * nf * 128; t += CB_THREADS) bas[(t >> 7) * BS + (t & 127)] = a.basis32[t];
-    for (int t = tid; t < nf * nfp; t += CB_THREADS) {
+    for (int t = tid; t < 2 * nf * 128; t += nthr) bas[(t >> 7) * BS + (t & 127)] = a.basis32[t];
+    for (int t = tid; t < nf * nfp; t += nthr) {
         const int r = t / nfp, f = t - r * nfp;
         float sn = 0.f, cs = 0.f;
         if (f < nf) sincospif(2.f * (float)((r * f) % C) / (float)C, &sn, &cs);
         tc[t] = cs;
         ts[t] = -sn;
     }
-    for (int t = tid; t < C; t += CB_THREADS) {
+    for (int t = tid; t < C; t += nthr) {
         double sd, cd;
         sincospi(2.0 * t / C, &sd, &cd);
         t64c[t] = cd;
@@ -305,7 +398,7 @@ __global__ void __launch_bounds__(CB_THREADS, 3) cube_filter_kernel(CubeArgs a) 
         }
         if (tid < 16) misc[tid] = 0;
         if (a.mask_out)
-            for (int t = tid; t < nbw; t += CB_THREADS) a.mask_out[(size_t)grp * nbw + t] = 0u;
+            for (int t = tid; t < nbw; t += nthr) a.mask_out[(size_t)grp * nbw + t] = 0u;
         __syncthreads();
         int sp = 0;
         for (int step = 0, m = K / 2; step < K; ++step, m = haar_next<K>(m)) {
@@ -319,39 +412,62 @@ __global__ void __launch_bounds__(CB_THREADS, 3) cube_filter_kernel(CubeArgs a) 
             // most K = 32 patches fit 16 bits, so a word holds the two bands c and C - c and one
             // 32-bit addition adds both.
             float nq = 0.f;
-            for (int t = tid; t < NI; t += CB_THREADS) {
+            // the lowest rows read patches k0 and k0 + 1 (b1 bytes after k0; negative if it lies above)
+            const uint8_t* img0 = img + (lowest ? (size_t)base[k0] * C : 0);
+            const int b1 = lowest ? (base[k0 + 1] - base[k0]) * C : 0;
+            auto emit = [&](int t, unsigned lft, unsigned rgt) {
                 const int p = __umulhi((unsigned)t, mg_nf), c = t - p * nf;
                 const bool paired = c > 0 && 2 * c < C;
-                unsigned lft, rgt = 0u;
-                if (m == 0) {
-                    lft = stk[(sp_in - 1) * NI + t];
-                } else if (lowest) {
-                    const uint8_t* i1 = img + ((p >> 3) * g.W + (p & 7)) * C + c;
-                    const int o2 = paired ? C - 2 * c : 0;
-                    const int b0 = base[k0] * C, b1 = base[k0 + 1] * C;
-                    lft = (unsigned)i1[b0] | ((unsigned)i1[b0 + o2] << 16);
-                    rgt = (unsigned)i1[b1] | ((unsigned)i1[b1 + o2] << 16);
-                    stk[sp_in * NI + t] = lft + rgt;
-                } else {
-                    rgt = stk[(sp_in - 1) * NI + t];
-                    lft = stk[(sp_in - 2) * NI + t];
-                    stk[(sp_in - 2) * NI + t] = lft + rgt;
-                }
                 const int s1 = (int)(lft & 0xffffu) - (int)(rgt & 0xffffu);
                 const int s2 = paired ? (int)(lft >> 16) - (int)(rgt >> 16) : 0;
                 R[c * RS + p] = (float)(s1 + s2);
                 R[(nf + c) * RS + p] = (float)(s1 - s2) * (paired ? 1.f : 0.f);
                 nq = fmaf((float)s1, (float)s1, fmaf((float)s2, (float)s2, nq));
+            };
+            if (lowest) {
+                // four items' bytes are requested before any is used (the patches come from L2)
+                constexpr int U = 4;
+                for (int t0 = tid; t0 < NI; t0 += U * nthr) {
+                    unsigned lft[U], rgt[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int t = t0 + u * nthr;
+                        lft[u] = rgt[u] = 0u;
+                        if (t < NI) {
+                            const int p = __umulhi((unsigned)t, mg_nf), c = t - p * nf;
+                            const uint8_t* i1 = img0 + ((p >> 3) * g.W + (p & 7)) * C + c;
+                            const int o2 = (c > 0 && 2 * c < C) ? C - 2 * c : 0;
+                            lft[u] = (unsigned)i1[0] | ((unsigned)i1[o2] << 16);
+                            rgt[u] = (unsigned)i1[b1] | ((unsigned)i1[b1 + o2] << 16);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int t = t0 + u * nthr;
+                        if (t < NI) {
+                            stk[sp_in * NI + t] = lft[u] + rgt[u];
+                            emit(t, lft[u], rgt[u]);
+                        }
+                    }
+                }
+            } else if (m == 0) {
+                for (int t = tid; t < NI; t += nthr) emit(t, stk[(sp_in - 1) * NI + t], 0u);
+            } else {
+                for (int t = tid; t < NI; t += nthr) {
+                    const unsigned rgt = stk[(sp_in - 1) * NI + t], lft = stk[(sp_in - 2) * NI + t];
+                    stk[(sp_in - 2) * NI + t] = lft + rgt;
+                    emit(t, lft, rgt);
+                }
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) nq += __shfl_xor_sync(0xffffffffu, nq, off);
-            if (tid == 0) { misc[1] = 0; misc[2] = 0; }
+            if (tid == 0) { misc[1] = 0; misc[2] = 0; misc[7] = 0; misc[8] = 0; misc[9] = 0; }
             if (lane == 0) atomicAdd(reinterpret_cast<float*>(&misc[5 + (step & 1)]), nq);
             __syncthreads();
-            band_dft(R, P, tc, ts, nf, nfp, tid);
+            band_dft(R, P, tc, ts, nf, nfp, tid, nthr);
             __syncthreads();
             // S_f[i][:] = (sum_a conj(U_f[a][i]) X_f[a][:]) V_f, one thread per (f, i)
-            for (int t = tid; t < nf * PS; t += CB_THREADS) {
+            for (int t = tid; t < nf * PS; t += nthr) {
                 const int f = t >> 3, i = t & 7;
                 const float* Ub = bas + f * BS;
                 const float* Vb = bas + (nf + f) * BS;
@@ -394,128 +510,208 @@ __global__ void __launch_bounds__(CB_THREADS, 3) cube_filter_kernel(CubeArgs a) 
             // decided in FP64 in between (the FP32 error of a slot's coefficients is bounded by a
             // multiple of the slot's own norm, its transform being orthonormal up to the Haar factor,
             // so the band is band_rel x ||slot||_F plus the rounding of tau). Kept values times 1/L,
-            // for the unnormalised synthesis, are folded again (s | d rows of P).
+            // for the unnormalised synthesis, go to row c of P (band c, pixels along the row). The
+            // epilogue only flags band coefficients; a slot that has some runs the tiles again and
+            // decides them in FP64 (a warp per coefficient).
             {
                 const float r = sqrtf((float)L), tl = a.tau32 * r, invL = 1.f / (float)L;
                 const float dl = a.band_rel * sqrtf(__int_as_float(misc[5 + (step & 1)])) + a.band_abs * r;
-                const double tlim = a.tau64 * sqrt((double)L);
                 const int nt = NPT * (nfp >> 2), ntw = (nt + 31) & ~31;
-                constexpr int HB = 4 * TP;                            // values per half of the bit masks
-                for (int t = tid; t < ntw; t += CB_THREADS) {         // whole warps: ballots below
+                for (int t = tid; t < ntw; t += nthr) {
                     const bool valid = t < nt;
                     const int p0 = (t % NPT) * TP, c0 = valid ? (t / NPT) << 2 : 0;
                     float A[4][TP], B[4][TP];
                     idft_tile(Q, tc, ts, nf, nfp, p0, c0, A, B);
-                    // value j = TP ci + pi: band c0 + ci as bit j, band C - c0 - ci as bit HB + j
-                    unsigned keep = 0u, band = 0u;
+                    float x[4][TP], y[4][TP];               // kept values times 1/L (band c, band C - c)
+                    unsigned km = 0u;                       // which: bit TP ci + pi (c), 4 TP + TP ci + pi (C - c)
+                    bool anyband = false;
 #pragma unroll
                     for (int ci = 0; ci < 4; ++ci) {
                         const int c = c0 + ci;
                         const bool lo_ok = valid && c < nf, hi_ok = valid && c > 0 && 2 * c < C;
 #pragma unroll
                         for (int pi = 0; pi < TP; ++pi) {
-                            const int j = ci * TP + pi;
                             const float v0 = A[ci][pi] + B[ci][pi], v1 = A[ci][pi] - B[ci][pi];
                             const float d0 = fabsf(v0) - tl, d1 = fabsf(v1) - tl;
-                            keep |= ((lo_ok && d0 > dl) ? 1u : 0u) << j;
-                            keep |= ((hi_ok && d1 > dl) ? 1u : 0u) << (HB + j);
-                            band |= ((lo_ok && fabsf(d0) <= dl) ? 1u : 0u) << j;
-                            band |= ((hi_ok && fabsf(d1) <= dl) ? 1u : 0u) << (HB + j);
-                            if (a.coef_out) {
-                                float* co = a.coef_out + ((size_t)grp * K + m) * NE + (p0 + pi) * C;
-                                if (lo_ok) co[c] = v0 / r;
-                                if (hi_ok) co[C - c] = v1 / r;
-                            }
+                            const bool k0 = d0 > dl, k1 = d1 > dl;
+                            anyband |= (lo_ok && fabsf(d0) <= dl) || (hi_ok && fabsf(d1) <= dl);
+                            x[ci][pi] = k0 ? v0 * invL : 0.f;
+                            y[ci][pi] = k1 ? v1 * invL : 0.f;
+                            km |= ((lo_ok && k0) ? 1u : 0u) << (ci * TP + pi);
+                            km |= ((hi_ok && k1) ? 1u : 0u) << (4 * TP + ci * TP + pi);
                         }
+                        if (lo_ok) stv<TP>(P + c * RS + p0, x[ci]);
+                        if (hi_ok) stv<TP>(P + (C - c) * RS + p0, y[ci]);
                     }
-                    if (__any_sync(0xffffffffu, band != 0u)) {
-                        for (int j = 0; j < 2 * HB; ++j) {
-                            unsigned bal = __ballot_sync(0xffffffffu, (band >> j) & 1u);
-                            while (bal) {               // warp-uniform
-                                const int l = __ffs(bal) - 1;
-                                bal &= bal - 1;
-                                const int tl_ = __shfl_sync(0xffffffffu, t, l), jj = j % HB;
-                                const int pb = (tl_ % NPT) * TP + jj % TP, cl = ((tl_ / NPT) << 2) + jj / TP;
-                                const double x = coef64(R, t64c, t64s, a.basis64, C, nf, pb, j < HB ? cl : C - cl,
-                                                        lane);
-                                if (lane == l && fabs(x) >= tlim) keep |= 1u << j;
-                            }
-                        }
-                    }
+                    const int nk = __popc(km);
+                    if (nk) {
+                        // the kept values, for the sparse inverse (positions past NL are counted only)
+                        int at = atomicAdd(&misc[7], nk);
 #pragma unroll
-                    for (int ci = 0; ci < 4; ++ci) {
-                        const int c = c0 + ci;
-                        if (!valid || c >= nf) continue;
-                        const bool paired = c > 0 && 2 * c < C;
-                        float lo[TP], hi[TP];
-#pragma unroll
-                        for (int pi = 0; pi < TP; ++pi) {
-                            const int j = ci * TP + pi;
-                            const float x0 = ((keep >> j) & 1u) ? (A[ci][pi] + B[ci][pi]) * invL : 0.f;
-                            const float x1 = ((keep >> (HB + j)) & 1u) ? (A[ci][pi] - B[ci][pi]) * invL : 0.f;
-                            lo[pi] = x0 + x1;
-                            hi[pi] = paired ? x0 - x1 : 0.f;
+                        for (int j = 0; j < 8 * TP; ++j) {
+                            if (!((km >> j) & 1u)) continue;
+                            const int ci = (j % (4 * TP)) / TP, pi = j % TP, c = c0 + ci;
+                            if (at < NL)
+                                lst[at] = make_int4(p0 + pi, j >= 4 * TP ? C - c : c,
+                                                    __float_as_int(j >= 4 * TP ? y[ci][pi] : x[ci][pi]), 0);
+                            ++at;
                         }
-                        stv<TP>(P + c * RS + p0, lo);
-                        stv<TP>(P + (nf + c) * RS + p0, hi);
                     }
-                    if (a.mask_out)
-                        for (unsigned kb = keep; kb; kb &= kb - 1) {
-                            const int j = __ffs(kb) - 1, jj = j % HB, c = c0 + jj / TP;
-                            const size_t bit = (size_t)m * NE + (p0 + jj % TP) * C + (j < HB ? c : C - c);
-                            atomicOr(&a.mask_out[(size_t)grp * nbw + bit / 32], 1u << (bit % 32));
+                    const int wk = __reduce_add_sync(0xffffffffu, nk);
+                    const unsigned rb = __reduce_or_sync(0xffffffffu, nk ? 1u << (p0 >> 3) : 0u);
+                    const bool wb = __any_sync(0xffffffffu, anyband);
+                    if (lane == 0) {
+                        if (wk) {
+                            atomicAdd(&misc[1], wk);
+                            atomicOr(&misc[2], (int)rb);
                         }
-                    const int nk = __reduce_add_sync(0xffffffffu, __popc(keep));
-                    const unsigned rb = __reduce_or_sync(0xffffffffu, keep ? 1u << (p0 >> 3) : 0u);
-                    if (lane == 0 && nk) {
-                        atomicAdd(&misc[1], nk);
-                        atomicOr(&misc[2], (int)rb);
+                        if (wb) misc[8] = 1;
                     }
                 }
                 if (tid == 0) misc[5 + ((step + 1) & 1)] = 0;   // the next slot's norm accumulator
+                __syncthreads();
+                if (misc[8] || a.coef_out || a.mask_out) {
+                    // the tiles again: list the band coefficients, optional outputs of the FP32 decisions
+                    const double tlim = a.tau64 * sqrt((double)L);
+                    auto keep_band = [&](int p, int cb, float v) {
+                        P[cb * RS + p] = v * invL;
+                        atomicAdd(&misc[1], 1);
+                        atomicOr(&misc[2], 1 << (p >> 3));
+                        const int at = atomicAdd(&misc[7], 1);
+                        if (at < NL) lst[at] = make_int4(p, cb, __float_as_int(v * invL), 0);
+                        if (a.mask_out) {
+                            const size_t bit = (size_t)m * NE + p * C + cb;
+                            atomicOr(&a.mask_out[(size_t)grp * nbw + bit / 32], 1u << (bit % 32));
+                        }
+                    };
+                    for (int t = tid; t < nt; t += nthr) {
+                        const int p0 = (t % NPT) * TP, c0 = (t / NPT) << 2;
+                        float A[4][TP], B[4][TP];
+                        idft_tile(Q, tc, ts, nf, nfp, p0, c0, A, B);
+#pragma unroll
+                        for (int j = 0; j < 8 * TP; ++j) {
+                            const int ci = (j % (4 * TP)) / TP, pi = j % TP, c = c0 + ci;
+                            const bool hi = j >= 4 * TP;
+                            if (!(hi ? (c > 0 && 2 * c < C) : c < nf)) continue;
+                            const int cb = hi ? C - c : c, p = p0 + pi;
+                            const float v = hi ? A[ci][pi] - B[ci][pi] : A[ci][pi] + B[ci][pi];
+                            const float d = fabsf(v) - tl;
+                            if (fabsf(d) <= dl) {
+                                const int at = atomicAdd(&misc[9], 1);
+                                if (at < NB) blist[at] = make_int4(p, cb, __float_as_int(v), 0);
+                            }
+                            if (a.coef_out) a.coef_out[((size_t)grp * K + m) * NE + p * C + cb] = v / r;
+                            if (d > dl && a.mask_out) {
+                                const size_t bit = (size_t)m * NE + p * C + cb;
+                                atomicOr(&a.mask_out[(size_t)grp * nbw + bit / 32], 1u << (bit % 32));
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    const int nbl = misc[9];
+                    if (nbl <= NB) {
+                        // FP64 decisions, each over the whole CTA
+                        for (int e = 0; e < nbl; ++e) {
+                            const int4 en = blist[e];
+                            const double xd = coef64_cta(R, t64c, t64s, a.basis64, C, nf, en.x, en.y, tid, nthr, red);
+                            if (tid == 0 && fabs(xd) >= tlim) keep_band(en.x, en.y, __int_as_float(en.z));
+                        }
+                    } else {
+                        // many: each warp decides the band coefficients of its own tiles
+                        for (int t = tid; t < ntw; t += nthr) {
+                            const bool valid = t < nt;
+                            const int p0 = (t % NPT) * TP, c0 = valid ? (t / NPT) << 2 : 0;
+                            float A[4][TP], B[4][TP];
+                            idft_tile(Q, tc, ts, nf, nfp, p0, c0, A, B);
+#pragma unroll
+                            for (int j = 0; j < 8 * TP; ++j) {
+                                const int ci = (j % (4 * TP)) / TP, pi = j % TP, c = c0 + ci;
+                                const bool hi = j >= 4 * TP;
+                                const bool ok = valid && (hi ? (c > 0 && 2 * c < C) : c < nf);
+                                const int cb = hi ? C - c : c, p = p0 + pi;
+                                const float v = hi ? A[ci][pi] - B[ci][pi] : A[ci][pi] + B[ci][pi];
+                                unsigned bal = __ballot_sync(0xffffffffu, ok && fabsf(fabsf(v) - tl) <= dl);
+                                while (bal) {               // warp-uniform
+                                    const int l = __ffs(bal) - 1;
+                                    bal &= bal - 1;
+                                    const int pl = __shfl_sync(0xffffffffu, p, l), cl = __shfl_sync(0xffffffffu, cb, l);
+                                    const double xd = coef64(R, t64c, t64s, a.basis64, C, nf, pl, cl, lane);
+                                    if (lane == l && fabs(xd) >= tlim) keep_band(p, cb, v);
+                                }
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
             }
-            __syncthreads();
             // A slot without a kept coefficient is all zeros: nothing is written for it. No barrier is
             // needed on that path: the next slot's writes before its first barrier are the raw slot
             // (read by nobody after the barrier above), the thread's own stack entries and misc[1],
-            // misc[2], which are zero already.
+            // misc[2], misc[8], which are zero already or read by nobody.
             if (misc[1] == 0) continue;
             const int rows = misc[2];
+            const bool sparse = misc[1] <= NL;
             if (tid == 0) {
                 misc[0] += misc[1];
                 misc[3] |= 1 << sl;
             }
-            // inverse: band DFT of the kept coefficients
-            band_dft(P, Q, tc, ts, nf, nfp, tid);
-            __syncthreads();
-            // Z_f[i][:] = T_f[i][:] V_f^H on the kept rows i (to P)
-            for (int t = tid; t < nf * PS; t += CB_THREADS) {
-                const int f = t >> 3, i = t & 7;
-                if (!((rows >> i) & 1)) continue;
-                const float* Vb = bas + (nf + f) * BS;
-                float tr[8], ti[8], zr[8], zi[8];
-                load8s(Q + f * RS + i * 8, tr);
-                load8s(Q + (nf + f) * RS + i * 8, ti);
+            if (sparse) {
+                // Z_f[i][b] = sum over the listed (i, j, c) of t w^{f c} conj(V_f[b][j]), without the
+                // band DFT of the whole slot (to Q)
+                const int nl = misc[7];
+                for (int t = tid; t < nf * PS; t += nthr) {
+                    const int f = t >> 3, b = t & 7;
+                    const float* Vb = bas + (nf + f) * BS + b * 8;
+                    float* zr = Q + f * RS + b;
+                    float* zi = Q + (nf + f) * RS + b;
 #pragma unroll
-                for (int b = 0; b < PS; ++b) {
-                    float vr[8], vi[8];
-                    load8s(Vb + b * 8, vr);
-                    load8s(Vb + 64 + b * 8, vi);
-                    float re = 0.f, im = 0.f;
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        re = fmaf(tr[j], vr[j], fmaf(ti[j], vi[j], re));
-                        im = fmaf(ti[j], vr[j], fmaf(-tr[j], vi[j], im));
+                    for (int i = 0; i < PS; ++i)
+                        if ((rows >> i) & 1) zr[i * 8] = zi[i * 8] = 0.f;
+                    for (int k = 0; k < nl; ++k) {
+                        const int4 en = lst[k];
+                        const int i = en.x >> 3, j = en.x & 7, c = en.y;
+                        const bool lo = c < nf;                 // w^{f c} from the tables of band c or C - c
+                        const int cr = lo ? c : C - c;
+                        const float tv = __int_as_float(en.z), sn = ts[cr * nfp + f];
+                        const float Tr = tv * tc[cr * nfp + f], Ti = tv * (lo ? sn : -sn);
+                        const float vr = Vb[j], vi = Vb[64 + j];
+                        zr[i * 8] += fmaf(Tr, vr, Ti * vi);
+                        zi[i * 8] += fmaf(Ti, vr, -Tr * vi);
                     }
-                    zr[b] = re;
-                    zi[b] = im;
                 }
-                store8s(P + f * RS + i * 8, zr, 1.f);
-                store8s(P + (nf + f) * RS + i * 8, zi, 1.f);
+            } else {
+                // band DFT of the kept coefficients (folded on load) to R, then
+                // Z_f[i][:] = T_f[i][:] V_f^H on the kept rows i (to Q)
+                band_dft_unfolded(P, R, tc, ts, C, nf, nfp, tid, nthr);
+                __syncthreads();
+                for (int t = tid; t < nf * PS; t += nthr) {
+                    const int f = t >> 3, i = t & 7;
+                    if (!((rows >> i) & 1)) continue;
+                    const float* Vb = bas + (nf + f) * BS;
+                    float tr[8], ti[8], zr[8], zi[8];
+                    load8s(R + f * RS + i * 8, tr);
+                    load8s(R + (nf + f) * RS + i * 8, ti);
+#pragma unroll
+                    for (int b = 0; b < PS; ++b) {
+                        float vr[8], vi[8];
+                        load8s(Vb + b * 8, vr);
+                        load8s(Vb + 64 + b * 8, vi);
+                        float re = 0.f, im = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            re = fmaf(tr[j], vr[j], fmaf(ti[j], vi[j], re));
+                            im = fmaf(ti[j], vr[j], fmaf(-tr[j], vi[j], im));
+                        }
+                        zr[b] = re;
+                        zi[b] = im;
+                    }
+                    store8s(Q + f * RS + i * 8, zr, 1.f);
+                    store8s(Q + (nf + f) * RS + i * 8, zi, 1.f);
+                }
             }
             __syncthreads();
-            // G_f[a][:] = sum_{i kept} U_f[a][i] Z_f[i][:] (to Q, times w_f / C)
-            for (int t = tid; t < nf * PS; t += CB_THREADS) {
+            // G_f[a][:] = sum_{i kept} U_f[a][i] Z_f[i][:] (to P, times w_f / C)
+            for (int t = tid; t < nf * PS; t += nthr) {
                 const int f = t >> 3, a_ = t & 7;
                 float ur[8], ui[8], gr[8], gi[8];
                 load8s(bas + f * BS + a_ * 8, ur);
@@ -526,8 +722,8 @@ __global__ void __launch_bounds__(CB_THREADS, 3) cube_filter_kernel(CubeArgs a) 
                 for (int i = 0; i < PS; ++i) {
                     if (!((rows >> i) & 1)) continue;
                     float zr[8], zi[8];
-                    load8s(P + f * RS + i * 8, zr);
-                    load8s(P + (nf + f) * RS + i * 8, zi);
+                    load8s(Q + f * RS + i * 8, zr);
+                    load8s(Q + (nf + f) * RS + i * 8, zi);
 #pragma unroll
                     for (int b = 0; b < 8; ++b) {
                         gr[b] = fmaf(ur[i], zr[b], fmaf(-ui[i], zi[b], gr[b]));
@@ -535,19 +731,19 @@ __global__ void __launch_bounds__(CB_THREADS, 3) cube_filter_kernel(CubeArgs a) 
                     }
                 }
                 const float w = (f == 0 || 2 * f == C ? 1.f : 2.f) / (float)C;
-                store8s(Q + f * RS + a_ * 8, gr, w);
-                store8s(Q + (nf + f) * RS + a_ * 8, gi, w);
+                store8s(P + f * RS + a_ * 8, gr, w);
+                store8s(P + (nf + f) * RS + a_ * 8, gi, w);
             }
             __syncthreads();
-            // inverse band DFT to the spatial slot [c][p] in R, then to the scratch as [p][c]
-            band_idft(Q, R, tc, ts, C, nf, nfp, tid);
+            // inverse band DFT to the slot, [p][c], staged in Q and copied to the scratch in 16-byte
+            // words (the next slot's first write to Q, its projection, comes after two barriers)
+            band_idft_pc(P, Q, tc, ts, C, nf, nfp, tid, nthr);
             __syncthreads();
-            float* dst = scratch + (size_t)sl * NE;
-            for (int e = tid; e < NE; e += CB_THREADS) {
-                const int p = __umulhi((unsigned)e, mg_c), c = e - p * C;
-                dst[e] = R[c * RS + p];
+            {
+                const float4* s4 = reinterpret_cast<const float4*>(Q);
+                float4* d4 = reinterpret_cast<float4*>(scratch + (size_t)sl * NE);
+                for (int e = tid; e < NE / 4; e += nthr) d4[e] = s4[e];
             }
-            __syncthreads();
         }
         __syncthreads();
         // weight of the group, then Haar synthesis per fibre (slots without a kept coefficient are
@@ -557,37 +753,62 @@ __global__ void __launch_bounds__(CB_THREADS, 3) cube_filter_kernel(CubeArgs a) 
         else if (a.agg_mode == 1) wg = 1.f / (float)max(1, misc[0]);
         if (tid == 0 && a.weights_out) a.weights_out[grp] = wg;
         const unsigned nzs = (unsigned)misc[3];
-        for (int e = tid; e < NE; e += CB_THREADS) {
-            const int p = __umulhi((unsigned)e, mg_c), c = e - p * C, pa = p >> 3, pb = p & 7;
-            if (nzs) {
-                // after the first level of the synthesis (slots 0 and K/2) the two halves of the
-                // in-place layout are independent: K = 32 runs as two syntheses of 16
-                constexpr int KH = K > 16 ? K / 2 : K;
+        // VW consecutive bands of a pixel per thread (2 when C is even: 8-byte vector atomics)
+        auto synthesis = [&](auto vw_tag) {
+            constexpr int VW = decltype(vw_tag)::value;
+            using VT = typename std::conditional<VW == 2, float2, float>::type;
+            for (int e = tid * VW; e < NE; e += nthr * VW) {
+                const int p = __umulhi((unsigned)e, mg_c), c = e - p * C, pa = p >> 3, pb = p & 7;
+                if (nzs) {
+                    // after the first level of the synthesis (slots 0 and K/2) the two halves of the
+                    // in-place layout are independent: K = 32 runs as two syntheses of 16
+                    constexpr int KH = K > 16 ? K / 2 : K;
 #pragma unroll 1
-                for (int h = 0; h < K / KH; ++h) {
-                    float v[KH];
+                    for (int h = 0; h < K / KH; ++h) {
+                        float v[VW][KH];
+                        auto ld = [&](int sk, float (&o)[VW]) {
+                            if ((nzs >> sk) & 1u) {
+                                const VT x = *reinterpret_cast<const VT*>(scratch + (size_t)sk * NE + e);
+                                if constexpr (VW == 2) { o[0] = x.x; o[1] = x.y; }
+                                else o[0] = x;
+                            } else {
 #pragma unroll
-                    for (int k = 1; k < KH; ++k) {
-                        const int sk = h * KH + k;
-                        v[k] = ((nzs >> sk) & 1u) ? scratch[(size_t)sk * NE + e] : 0.f;
-                    }
-                    v[0] = (nzs & 1u) ? scratch[e] : 0.f;
-                    if constexpr (K > KH) {
-                        const float sh = ((nzs >> KH) & 1u) ? scratch[(size_t)KH * NE + e] : 0.f;
-                        v[0] = h == 0 ? v[0] + sh : v[0] - sh;
-                    }
-                    haar_inv_sum<KH>(v);
+                                for (int w = 0; w < VW; ++w) o[w] = 0.f;
+                            }
+                        };
 #pragma unroll
-                    for (int k = 0; k < KH; ++k) {
-                        const size_t pix = (size_t)base[h * KH + k] + pa * g.W + pb;
-                        atomicAdd(&a.num[pix * C + c], wg * v[k]);
+                        for (int k = 0; k < KH; ++k) {
+                            float o[VW];
+                            ld(k == 0 ? 0 : h * KH + k, o);
+#pragma unroll
+                            for (int w = 0; w < VW; ++w) v[w][k] = o[w];
+                        }
+                        if constexpr (K > KH) {
+                            float sh[VW];
+                            ld(KH, sh);
+#pragma unroll
+                            for (int w = 0; w < VW; ++w) v[w][0] = h == 0 ? v[w][0] + sh[w] : v[w][0] - sh[w];
+                        }
+#pragma unroll
+                        for (int w = 0; w < VW; ++w) haar_inv_sum<KH>(v[w]);
+#pragma unroll
+                        for (int k = 0; k < KH; ++k) {
+                            const size_t pix = (size_t)base[h * KH + k] + pa * g.W + pb;
+                            if constexpr (VW == 2)
+                                atomicAdd(reinterpret_cast<float2*>(a.num + pix * C + c),
+                                          make_float2(wg * v[0][k], wg * v[1][k]));
+                            else
+                                atomicAdd(&a.num[pix * C + c], wg * v[0][k]);
+                        }
                     }
                 }
-            }
-            if (c == 0)
+                if (c == 0)
 #pragma unroll
-                for (int k = 0; k < K; ++k) atomicAdd(&a.den[(size_t)base[k] + pa * g.W + pb], wg);
-        }
+                    for (int k = 0; k < K; ++k) atomicAdd(&a.den[(size_t)base[k] + pa * g.W + pb], wg);
+            }
+        };
+        if ((C & 1) == 0) synthesis(std::integral_constant<int, 2>{});
+        else synthesis(std::integral_constant<int, 1>{});
     }
 }
 
@@ -603,7 +824,7 @@ cudaError_t launch_cube_t(const CubeArgs& a, int grid, cudaStream_t s) {
     auto fn = cube_filter_kernel<K>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    fn<<<grid, CB_THREADS, smem, s>>>(a);
+    fn<<<grid, cube_threads(a.g.C), smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -614,7 +835,7 @@ int cube_per_sm(int C) {
     auto fn = cube_filter_kernel<K>;
     int n = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, CB_THREADS, smem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, cube_threads(C), smem) != cudaSuccess)
         n = 1;
     return n < 1 ? 1 : n;
 }
