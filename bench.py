@@ -575,6 +575,19 @@ def run_gpu(args):
                 "peak_basis": f"FP32 FMA: {nsm} SMs (device query) x {FP32_LANES_PER_SM} lanes x 2 flop x "
                               f"{MAX_SM_MHZ:.0f} MHz (unit counts and max clock); issue-rate probe in this run: "
                               f"{probe['ffma']:.1f} FFMA, {probe['imad']:.1f} IMAD, {probe['dp4a']:.1f} DP4A per SM clock"}
+    elif dom == "cube_filter":
+        # forward transforms of every Haar slot as the kernel computes them (the inverse of the slots that
+        # keep a coefficient depends on the data and is not counted): folded band DFT and its inverse,
+        # 64 nf^2 MACs each for the real and the imaginary part, and two per-slice 8x8 complex products
+        n_launch, ms = prof["cube_filter"]
+        nf = wl.C // 2 + 1
+        flops = wl.groups_per_step * wl.K * 2 * (256 * nf * nf + 4096 * nf) * args.steps / n_launch
+        achieved = flops / (ms / n_launch / 1000.0) / 1e12
+        peak = nsm * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "cube_filter",
+                "peak_basis": f"FP32 FMA: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {MAX_SM_MHZ:.0f} MHz; "
+                              "achieved counts the forward transforms only"}
     elif dom is not None:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
                 "kernel": dom}
