@@ -79,6 +79,13 @@ Readings where the paper is silent or ambiguous:
      so 'auto' matching takes the SSD over all bands (exact integers); tau = sigma sqrt(2 ln(N K
      ps^2)) (Sec. IV-A with c = N, as R9). The paper's band-mean noise estimate goes through its
      CNN, so for cubes sigma is an input.
+  R19 per-group weight tuning by SURE (the aggregation weights of R10 as free parameters, tuned
+     through the vector-Jacobian product; the paper's tuning remark in Sec. III-E): for weights
+     w > 0, f_w(x) = N_w(x) / D_w with the grouping, bases and masks of x (none depends on w),
+     SURE(w) = ||f_w(y) - y||^2 / n - sigma^2 + (2 sigma^2 / n) b^T (f_w(z) - f_w(y)) / eps with z as
+     in R17 (eps > 0), and its gradient is exact through the weight part G_x of the adjoint (R14):
+     dSURE/dw = G_y((2/n)(f_w(y) - y) - (2 sigma^2 / (n eps)) b) + G_z((2 sigma^2 / (n eps)) b).
+     Tuning takes exponentiated-gradient steps w <- w exp(-step g / max|g|), which keep w > 0.
 
 Parity pins for every function are in tests/test_oracle_pins.py.
 """
@@ -831,3 +838,51 @@ def sure(x: np.ndarray, sigma: float, tau_mults, probe: np.ndarray, params=None,
         res.append(((r.out - xf) ** 2).sum() / n - sigma ** 2 + 2.0 * sigma ** 2 / n * div)
     return np.array(res)
 
+
+# --------------------------------------------------------------------------- weight tuning (reading R19)
+
+def perturbed(x: np.ndarray, probe: np.ndarray, eps: float) -> np.ndarray:
+    """z = y + eps b formed in float32 as the device forms it (reading R17)."""
+    return (x.astype(np.float32) + np.float32(eps) * probe.astype(np.float32)).astype(np.float64)
+
+
+def sure_weights(x: np.ndarray, sigma: float, w: np.ndarray, probe: np.ndarray, params=None,
+                 eps: float = 1.0):
+    """Reading R19: SURE of the denoiser with per-group weights w (tau = tau_mult sigma) and its
+    gradient in w. Returns (sure, grad_w)."""
+    p = Params.of(params)
+    if x.ndim == 2:
+        x = x[:, :, None]
+    if probe.ndim == 2:
+        probe = probe[:, :, None]
+    xf = x.astype(np.float64)
+    b = probe.astype(np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    n = xf.size
+    z = perturbed(x, probe, eps)
+    ry = denoise(xf, sigma, p, weights=w, keep_masks=True)
+    rz = denoise(z, sigma, p, weights=w, keep_masks=True)
+    beta = 2.0 * sigma ** 2 / (n * eps)
+    sure_w = ((ry.out - xf) ** 2).sum() / n - sigma ** 2 + beta * float((b * (rz.out - ry.out)).sum())
+    _, gy = denoise_fixed_vjp(xf, 2.0 / n * (ry.out - xf) - beta * b, ry.idx, ry.masks, ry.U, ry.V, w, p.ps)
+    _, gz = denoise_fixed_vjp(z, beta * b, rz.idx, rz.masks, rz.U, rz.V, w, p.ps)
+    return float(sure_w), gy + gz
+
+
+def tune_weights(x: np.ndarray, sigma: float, probe: np.ndarray, params=None, eps: float = 1.0,
+                 steps: int = 3, step: float = 0.5, w0=None):
+    """Reading R19: `steps` exponentiated-gradient steps on SURE(w) from w0 (default all ones).
+    Returns (w, trace) with trace the SURE before each step and after the last."""
+    p = Params.of(params)
+    n_groups = len(reference_positions(x.shape[0], p.ps, p.stride)) * len(reference_positions(x.shape[1], p.ps, p.stride))
+    w = np.ones(n_groups) if w0 is None else np.asarray(w0, dtype=np.float64).copy()
+    trace = []
+    for it in range(steps + 1):
+        sv, g = sure_weights(x, sigma, w, probe, p, eps)
+        trace.append(sv)
+        if it == steps:
+            break
+        gm = np.abs(g).max()
+        if gm > 0:
+            w = w * np.exp(-step * g / gm)
+    return w, np.array(trace)

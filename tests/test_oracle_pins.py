@@ -742,3 +742,63 @@ def test_hsi_zero_threshold_is_the_identity_and_rgb_modes_refuse_cubes():
     for mode in ("gcp", "gray"):
         with pytest.raises(ValueError):
             O.block_match(y, O.Params(ps=8, stride=3, window=7, K=4, match_mode=mode))
+
+
+# ----------------------------------------------------------------------------- weight tuning (reading R19)
+
+def _sure_w_case(seed=7, sigma=20.0):
+    clean = synth.clean_image(40, 44, 3, seed)
+    y = synth.add_gaussian_float(clean, sigma, seed).astype(np.float32)
+    rng = np.random.default_rng(seed + 1)
+    b = rng.choice([-1.0, 1.0], size=y.shape).astype(np.float32)
+    prm = dict(ps=8, stride=3, window=9, K=8)
+    n = len(O.reference_positions(40, 8, 3)) * len(O.reference_positions(44, 8, 3))
+    return clean, y, b, prm, rng.uniform(0.5, 1.5, n), rng
+
+
+def test_sure_weight_gradient_matches_central_differences():
+    """SURE(w) is a ratio of sums linear in w with masks independent of w, so its central difference
+    along any direction converges to <grad, d> (a dropped term of the gradient, its z part or a sign
+    in the cotangent, fails this)."""
+    clean, y, b, prm, w, rng = _sure_w_case()
+    _, g = O.sure_weights(y, 20.0, w, b, prm, eps=2.0)
+    for _ in range(3):
+        d = rng.standard_normal(w.size)
+        h = 1e-5
+        sp, _ = O.sure_weights(y, 20.0, w + h * d, b, prm, eps=2.0)
+        sm, _ = O.sure_weights(y, 20.0, w - h * d, b, prm, eps=2.0)
+        fd, ad = (sp - sm) / (2 * h), float(g @ d)
+        assert abs(fd - ad) <= 1e-5 * max(1.0, abs(ad)), (fd, ad)
+
+
+def test_sure_weights_are_scale_free():
+    """f_w = N_w / D_w does not change when every weight is scaled, so SURE(c w) = SURE(w) and, by
+    Euler's identity for a function homogeneous of degree 0, sum_g w_g dSURE/dw_g = 0."""
+    clean, y, b, prm, w, rng = _sure_w_case(11)
+    s1, g = O.sure_weights(y, 20.0, w, b, prm, eps=2.0)
+    s2, g2 = O.sure_weights(y, 20.0, 3.5 * w, b, prm, eps=2.0)
+    assert abs(s1 - s2) <= 1e-9 * abs(s1)
+    assert abs(float(w @ g)) <= 1e-9 * float(np.abs(w * g).sum())
+    np.testing.assert_allclose(g2 * 3.5, g, rtol=1e-7, atol=1e-12)      # grad scales as 1 / c
+
+
+def test_sure_weights_do_not_matter_at_zero_threshold():
+    """At tau = 0 every coefficient is kept and each group returns its own patches, so f_w(x) = x for
+    any w: SURE is sigma^2 (2 / eps) b^T (z - y) / n - sigma^2 and its gradient vanishes."""
+    clean, y, b, prm, w, rng = _sure_w_case(13)
+    prm = dict(prm, tau_mult=1e-12)
+    s, g = O.sure_weights(y, 20.0, w, b, prm, eps=2.0)
+    z = O.perturbed(y, b, 2.0)
+    n = y.size
+    expect = 2.0 * 20.0 ** 2 / (n * 2.0) * float((b.astype(np.float64) * (z - y.astype(np.float64))).sum()) - 20.0 ** 2
+    assert abs(s - expect) <= 1e-9 * abs(expect)
+    assert np.abs(g).max() <= 1e-10
+
+
+def test_weight_tuning_lowers_the_risk_estimate():
+    """Exponentiated-gradient steps on SURE(w) from uniform weights lower SURE (small steps along
+    the negative gradient) and keep every weight positive."""
+    clean, y, b, prm, w, rng = _sure_w_case(17)
+    wt, trace = O.tune_weights(y, 20.0, b, prm, eps=2.0, steps=3, step=0.3)
+    assert np.all(np.diff(trace) < 0), trace
+    assert np.all(wt > 0)
