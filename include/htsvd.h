@@ -171,6 +171,33 @@ htsvd_status htsvd_sure(const float* d_y, int32_t H, int32_t W, int32_t C, doubl
                         int32_t n_tau, const float* d_probe, double eps, const htsvd_params* p, double* h_sure,
                         cudaStream_t stream);
 
+/* Per-group aggregation weights scored by Stein's unbiased risk estimate (tuning, Sec. III-E, with
+ * the weights of the aggregation, Sec. II-B, as the free parameters). For weights w (d_w: N_groups
+ * floats > 0, DEVICE, N_groups = htsvd_num_groups) let f_w(x) be htsvd_denoise_f32 of x aggregated
+ * with w (tau = tau_mult * sigma; the grouping, bases and masks of x, none of which depends on w).
+ * With y = d_y (H x W x C float32 on the [0, 255] scale, DEVICE), b = d_probe (same shape, DEVICE; a
+ * +-1 Rademacher vector), n = H W C and z = y + eps b formed in float32 as in htsvd_sure:
+ *   h_sure = ||f_w(y) - y||^2 / n - sigma^2 + (2 sigma^2 / n) b^T (f_w(z) - f_w(y)) / eps,
+ *   d_grad_w = dSURE/dw = G_y((2/n)(f_w(y) - y) - (2 sigma^2 / (n eps)) b) + G_z((2 sigma^2 / (n eps)) b),
+ * G_x(u) the weight gradient of htsvd_denoise_vjp at x for the cotangent u. f_w is a ratio of sums
+ * linear in w, so this is the exact gradient of SURE for the groupings and masks of y and z.
+ * h_sure: HOST double; d_grad_w: N_groups floats (DEVICE). Synchronises `stream`. Errors:
+ * INVALID_ARG for a null pointer, sigma not positive and finite, eps not positive, finite and
+ * non-zero in float32, or an image that fails the checks of htsvd_denoise; optional outputs of p are
+ * ignored. */
+htsvd_status htsvd_sure_weights(const float* d_y, int32_t H, int32_t W, int32_t C, double sigma, const float* d_w,
+                                const float* d_probe, double eps, const htsvd_params* p, double* h_sure,
+                                float* d_grad_w, cudaStream_t stream);
+
+/* n_steps exponentiated-gradient steps on the SURE of htsvd_sure_weights: from d_w (in: start, out:
+ * tuned; N_groups floats > 0, DEVICE), w <- w exp(-step g / max|g|) with g the gradient, which keeps
+ * every weight positive (nothing moves when g vanishes). The groupings and bases of y and z are formed
+ * once. h_sure: n_steps + 1 doubles (HOST): SURE before each step and after the last. step > 0 and
+ * finite, n_steps >= 0; otherwise errors as htsvd_sure_weights. Synchronises `stream` once per step. */
+htsvd_status htsvd_tune_weights(const float* d_y, int32_t H, int32_t W, int32_t C, double sigma, const float* d_probe,
+                                double eps, int32_t n_steps, double step, const htsvd_params* p, float* d_w,
+                                double* h_sure, cudaStream_t stream);
+
 /* Noise level from the eigenvalues of the covariance of the reference patches:
  * ascending eigenvalues l_1..l_d, r* = max{r : mean(l_1..r) <= 1.02 median(l_1..r)},
  * sigma = sqrt(mean(l_1..r*)). With p->adapt the eigen-rank vote of Sec. III-D,

@@ -12,7 +12,8 @@ from dataclasses import dataclass, fields
 from . import _lib
 
 __all__ = ["HtsvdParams", "denoise", "denoise_f32", "estimate_sigma", "denoise_batch", "denoise_adaptive",
-           "denoise_video", "denoise_cube", "denoise_tau_sweep", "sure", "denoise_vjp", "num_groups", "HtsvdFn", "load_library"]
+           "denoise_video", "denoise_cube", "denoise_tau_sweep", "sure", "sure_weights", "tune_weights", "denoise_vjp",
+           "num_groups", "HtsvdFn", "load_library"]
 
 _MATCH = {"auto": 0, "gcp": 1, "full": 2, "green": 3}
 _AGG = {"uniform": 0, "sparsity": 1}
@@ -349,6 +350,54 @@ def sure(y, sigma, tau_mults, probe, params=None, eps=None, stream=None):
     _lib.check(lib.htsvd_sure(_ptr(x.contiguous()), H, W, C, float(sigma), (ctypes.c_double * len(m))(*m), len(m),
                               _ptr(b), e, ctypes.byref(cp), res, _stream_ptr(stream)), "htsvd_sure")
     return [float(v) for v in res]
+
+
+def sure_weights(y, sigma, w, probe, params=None, eps=None, stream=None):
+    """SURE of the denoiser aggregating with per-group weights w (float32 CUDA tensor of num_groups
+    values > 0) on the float32 (H, W[, C]) CUDA image y, and its gradient in w (htsvd_sure_weights;
+    eps > 0, default sigma / 10). Returns (sure: float, grad_w: tensor); synchronises the stream."""
+    lib = _lib.load()
+    torch = _torch()
+    x = _hwc(y)
+    if x.dtype != torch.float32:
+        raise TypeError("sure_weights expects float32")
+    b = _need(probe if probe.dim() == 3 else probe.unsqueeze(-1), "probe", x.shape, torch.float32, x)
+    H, W, C = x.shape
+    p = HtsvdParams.of(params)
+    n = num_groups(H, W, p)
+    wt = _need(w.contiguous(), "w", (n,), torch.float32, x)
+    g = torch.empty(n, dtype=torch.float32, device=x.device)
+    res = ctypes.c_double()
+    cp = p.c()
+    e = 0.1 * float(sigma) if eps is None else float(eps)
+    _lib.check(lib.htsvd_sure_weights(_ptr(x.contiguous()), H, W, C, float(sigma), _ptr(wt), _ptr(b.contiguous()), e,
+                                      ctypes.byref(cp), ctypes.byref(res), _ptr(g), _stream_ptr(stream)),
+               "htsvd_sure_weights")
+    return float(res.value), g
+
+
+def tune_weights(y, sigma, probe, params=None, eps=None, steps=3, step=0.5, w0=None, stream=None):
+    """Per-group weights tuned by exponentiated-gradient steps on their SURE (htsvd_tune_weights),
+    from w0 (default all ones). Returns (w, trace) with trace the SURE before each step and after the
+    last."""
+    lib = _lib.load()
+    torch = _torch()
+    x = _hwc(y)
+    if x.dtype != torch.float32:
+        raise TypeError("tune_weights expects float32")
+    b = _need(probe if probe.dim() == 3 else probe.unsqueeze(-1), "probe", x.shape, torch.float32, x)
+    H, W, C = x.shape
+    p = HtsvdParams.of(params)
+    n = num_groups(H, W, p)
+    w = (torch.ones(n, dtype=torch.float32, device=x.device) if w0 is None
+         else _need(w0.contiguous(), "w0", (n,), torch.float32, x).clone())
+    trace = (ctypes.c_double * (int(steps) + 1))()
+    cp = p.c()
+    e = 0.1 * float(sigma) if eps is None else float(eps)
+    _lib.check(lib.htsvd_tune_weights(_ptr(x.contiguous()), H, W, C, float(sigma), _ptr(b.contiguous()), e,
+                                      int(steps), float(step), ctypes.byref(cp), _ptr(w), trace, _stream_ptr(stream)),
+               "htsvd_tune_weights")
+    return w, [float(v) for v in trace]
 
 
 def denoise_vjp(x, sigma, idx, w, out, grad_out, params=None, want_grad_w=True, stream=None):

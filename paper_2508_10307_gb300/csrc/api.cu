@@ -133,6 +133,7 @@ enum Slot {
     S_COEF, S_CPN, S_CNRM,           // coefficient cache of htsvd_denoise_tau_sweep
     S_SOUT, S_SGX, S_SIDX, S_SRED,   // htsvd_sure: estimate, adjoint or perturbed image, grouping, sums
     S_GAP,                           // eigen-gaps of the basis slices (strict mode)
+    S_WIDX0, S_WIDX1, S_WB64, S_WB32, S_WZ, S_WF, S_WU, S_WGX, S_WG2, S_WRED,   // weight tuning by SURE
     S_CSCR, S_CNUM, S_CDEN,          // hyperspectral cubes: per-CTA Haar slots, numerator, denominator
     S_NSLOT
 };
@@ -745,6 +746,95 @@ htsvd_status vjp_core(Workspace* w, const float* d_x, const Geo& g, const Resolv
     return HTSVD_OK;
 }
 
+// SURE of the per-group weights (reading R19). The grouping and the bases of y and of z = y + eps b
+// do not depend on w: prepared once, then any number of evaluations.
+struct SureW {
+    Geo g;
+    Resolved r;
+    int64_t n = 0, ng = 0;
+    double sigma = 0.0, eps = 0.0, tau = 0.0;
+    const float* y = nullptr;
+    const float* b = nullptr;
+    const float* img[2] = {};       // y, z
+    int32_t* idx[2] = {};
+    double* b64[2] = {};
+    float* b32[2] = {};
+};
+
+htsvd_status sure_w_prepare(Workspace* w, const float* d_y, int H, int W, int C, double sigma, const float* d_probe,
+                            double eps, const htsvd_params* p, SureW& c, cudaStream_t s) {
+    if (!d_y || !d_probe) return HTSVD_ERR_INVALID_ARG;
+    if (!(sigma > 0) || std::isinf(sigma)) return HTSVD_ERR_INVALID_ARG;
+    if (!(eps > 0.0) || !std::isfinite((float)eps) || !((float)eps > 0.0f)) return HTSVD_ERR_INVALID_ARG;
+    ST(resolve(p, C, c.r));
+    ST(check_image(H, W, C, c.r));
+    c.g = make_geo(H, W, C, c.r.s, c.r.win, c.r.K);
+    c.n = (int64_t)H * W * C;
+    c.ng = c.g.ngroups();
+    c.sigma = sigma;
+    c.eps = eps;
+    c.tau = c.r.tau_mult * sigma;
+    c.y = d_y;
+    c.b = d_probe;
+    void *z, *i0, *i1, *b64, *b32, *qb;
+    ST(ws_get(w, S_WZ, sizeof(float) * c.n, &z));
+    ST(ws_get(w, S_WIDX0, sizeof(int32_t) * c.ng * c.r.K, &i0));
+    ST(ws_get(w, S_WIDX1, sizeof(int32_t) * c.ng * c.r.K, &i1));
+    ST(ws_get(w, S_WB64, sizeof(double) * 2 * 2 * 2 * C * PS2, &b64));
+    ST(ws_get(w, S_WB32, sizeof(float) * 2 * 512, &b32));
+    ST(ws_get(w, S_Q, (size_t)c.n, &qb));
+    { ProfScope ps_("perturb", s); CK(launch_perturb(d_y, d_probe, (float)eps, c.n, (float*)z, s)); }
+    c.img[0] = d_y;
+    c.img[1] = (const float*)z;
+    c.idx[0] = (int32_t*)i0;
+    c.idx[1] = (int32_t*)i1;
+    for (int k = 0; k < 2; ++k) {
+        c.b64[k] = (double*)b64 + (size_t)k * 2 * 2 * C * PS2;
+        c.b32[k] = (float*)b32 + (size_t)k * 512;
+        { ProfScope ps_("quantize", s); CK(launch_quantize(c.img[k], c.n, (uint8_t*)qb, s)); }
+        double* p64;
+        float* p32;
+        ST(run_basis(w, (const uint8_t*)qb, c.g, &p64, &p32, s));
+        CK(cudaMemcpyAsync(c.b64[k], p64, sizeof(double) * 2 * 2 * C * PS2, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(c.b32[k], p32, sizeof(float) * 512, cudaMemcpyDeviceToDevice, s));
+        ST(run_block_match((const uint8_t*)qb, c.g, c.r, 1, c.idx[k], s));
+    }
+    return HTSVD_OK;
+}
+
+// SURE(w) to *h_sure (HOST; synchronises s) and its gradient to d_grad_w.
+htsvd_status sure_w_eval(Workspace* w, const SureW& c, const float* d_w, double* h_sure, float* d_grad_w,
+                         cudaStream_t s) {
+    void *f, *u, *gx, *g2, *red;
+    ST(ws_get(w, S_WF, sizeof(float) * c.n, &f));
+    ST(ws_get(w, S_WU, sizeof(float) * c.n, &u));
+    ST(ws_get(w, S_WGX, sizeof(float) * c.n, &gx));
+    ST(ws_get(w, S_WG2, sizeof(float) * c.ng, &g2));
+    ST(ws_get(w, S_WRED, sizeof(double) * (sure_scratch_doubles() + 4), &red));
+    double* scratch = (double*)red;
+    double* terms = scratch + sure_scratch_doubles();   // |f_y - y|^2, b.f_y, |f_z - z|^2, b.f_z
+    // beta = 2 sigma^2 / (n eps): the divergence's weight in SURE
+    const double beta = 2.0 * c.sigma * c.sigma / ((double)c.n * c.eps);
+    for (int k = 0; k < 2; ++k) {
+        ST(run_forward_filter(w, c.img[k], 1, c.g, c.r, c.idx[k], c.b64[k], c.b32[k], c.tau, d_w, nullptr, (float*)f,
+                              s));
+        { ProfScope ps_("sure_terms", s);
+          CK(launch_sure_terms((const float*)f, c.img[k], c.b, (const float*)f, c.n, scratch, terms + 2 * k, s)); }
+        // cotangents: (2/n)(f_y - y) - beta b at y, beta b at z
+        { ProfScope ps_("cotangent", s);
+          CK(launch_sure_cotangent((const float*)f, c.img[k], c.b, k == 0 ? (float)(2.0 / (double)c.n) : 0.f,
+                                   k == 0 ? (float)beta : -(float)beta, c.n, (float*)u, s)); }
+        ST(vjp_core(w, c.img[k], c.g, c.r, c.idx[k], d_w, c.b64[k], c.b32[k], c.tau, (const float*)f,
+                    (const float*)u, (float*)gx, k == 0 ? d_grad_w : (float*)g2, s));
+    }
+    { ProfScope ps_("add", s); CK(launch_add((const float*)g2, d_grad_w, c.ng, s)); }
+    double h[4];
+    CK(cudaMemcpyAsync(h, terms, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *h_sure = h[0] / (double)c.n - c.sigma * c.sigma + beta * (h[3] - h[1]);
+    return HTSVD_OK;
+}
+
 }  // namespace
 
 // ============================================================================= C ABI
@@ -1011,6 +1101,37 @@ htsvd_status htsvd_sure(const float* d_y, int32_t H, int32_t W, int32_t C, doubl
         const double* t = &h[4 * (size_t)i];
         const double div = fd ? (t[3] - t[1]) / eps : t[1];
         h_sure[i] = t[0] / (double)n - sigma * sigma + 2.0 * sigma * sigma / (double)n * div;
+    }
+    return HTSVD_OK;
+}
+
+htsvd_status htsvd_sure_weights(const float* d_y, int32_t H, int32_t W, int32_t C, double sigma, const float* d_w,
+                                const float* d_probe, double eps, const htsvd_params* p, double* h_sure,
+                                float* d_grad_w, cudaStream_t s) {
+    if (!d_w || !h_sure || !d_grad_w) return HTSVD_ERR_INVALID_ARG;
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    SureW c;
+    ST(sure_w_prepare(w, d_y, H, W, C, sigma, d_probe, eps, p, c, s));
+    return sure_w_eval(w, c, d_w, h_sure, d_grad_w, s);
+}
+
+htsvd_status htsvd_tune_weights(const float* d_y, int32_t H, int32_t W, int32_t C, double sigma, const float* d_probe,
+                                double eps, int32_t n_steps, double step, const htsvd_params* p, float* d_w,
+                                double* h_sure, cudaStream_t s) {
+    if (!d_w || !h_sure || n_steps < 0 || !(step > 0.0) || !std::isfinite((float)step)) return HTSVD_ERR_INVALID_ARG;
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    SureW c;
+    ST(sure_w_prepare(w, d_y, H, W, C, sigma, d_probe, eps, p, c, s));
+    void *gw, *mx;
+    ST(ws_get(w, S_SGX, sizeof(float) * c.ng, &gw));
+    ST(ws_get(w, S_SIDX, sizeof(unsigned), &mx));
+    for (int it = 0; it <= n_steps; ++it) {
+        ST(sure_w_eval(w, c, d_w, &h_sure[it], (float*)gw, s));
+        if (it == n_steps) break;
+        ProfScope ps_("eg_update", s);
+        CK(launch_eg_update(d_w, (const float*)gw, c.ng, (float)step, (unsigned*)mx, s));
     }
     return HTSVD_OK;
 }

@@ -200,7 +200,65 @@ __global__ void perturb_kernel(const float* __restrict__ y, const float* __restr
         z[i] = __fadd_rn(y[i], __fmul_rn(eps, b[i]));
 }
 
+// Cotangent of SURE(w) at one of its two images: u = alpha (f - x) - beta b.
+__global__ void sure_cotangent_kernel(const float* __restrict__ f, const float* __restrict__ x,
+                                      const float* __restrict__ b, float alpha, float beta, int64_t n,
+                                      float* __restrict__ u) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] = alpha * (f[i] - x[i]) - beta * b[i];
+}
+
+__global__ void add_kernel(const float* __restrict__ a, float* __restrict__ acc, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc[i] += a[i];
+}
+
+// max |g| as the bits of a non-negative float (their integer order is the float order); *res is
+// zeroed by the launcher.
+__global__ void absmax_kernel(const float* __restrict__ g, int64_t n, unsigned* __restrict__ res) {
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(g[i]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(res, __float_as_uint(m));
+}
+
+// w <- w exp(-step g / max|g|) (nothing when g vanishes).
+__global__ void eg_update_kernel(float* __restrict__ w, const float* __restrict__ g, int64_t n, float step,
+                                 const unsigned* __restrict__ gmax) {
+    const float m = __uint_as_float(*gmax);
+    if (!(m > 0.f)) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] *= expf(-step * g[i] / m);
+}
+
+int elementwise_blocks(int64_t n) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
+    return blocks < 1 ? 1 : (int)blocks;
+}
+
 }  // namespace
+
+cudaError_t launch_sure_cotangent(const float* f, const float* x, const float* b, float alpha, float beta, int64_t n,
+                                  float* u, cudaStream_t s) {
+    sure_cotangent_kernel<<<elementwise_blocks(n), 256, 0, s>>>(f, x, b, alpha, beta, n, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add(const float* a, float* acc, int64_t n, cudaStream_t s) {
+    add_kernel<<<elementwise_blocks(n), 256, 0, s>>>(a, acc, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eg_update(float* w, const float* g, int64_t n, float step, unsigned* scratch, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    absmax_kernel<<<elementwise_blocks(n), 256, 0, s>>>(g, n, scratch);
+    eg_update_kernel<<<elementwise_blocks(n), 256, 0, s>>>(w, g, n, step, scratch);
+    return cudaGetLastError();
+}
 
 size_t sure_scratch_doubles() { return 2 * (size_t)SURE_BLOCKS; }
 

@@ -122,6 +122,12 @@ cudaError_t launch_perturb(const float* y, const float* b, float eps, int64_t n,
 // SURE terms in FP64: res[0] = sum (out - x)^2, res[1] = sum b * g over n floats (deterministic
 // two-level reduction; scratch: sure_scratch_doubles() doubles).
 size_t sure_scratch_doubles();
+// Weight tuning (SURE of the per-group weights): u = alpha (f - x) - beta b; acc += a;
+// w <- w exp(-step g / max|g|) (scratch: one unsigned, for max|g|).
+cudaError_t launch_sure_cotangent(const float* f, const float* x, const float* b, float alpha, float beta, int64_t n,
+                                  float* u, cudaStream_t s);
+cudaError_t launch_add(const float* a, float* acc, int64_t n, cudaStream_t s);
+cudaError_t launch_eg_update(float* w, const float* g, int64_t n, float step, unsigned* scratch, cudaStream_t s);
 cudaError_t launch_sure_terms(const float* out, const float* x, const float* b, const float* g, int64_t n,
                               double* scratch, double* res, cudaStream_t s);
 // Adjoint helper: r = gout / den.
