@@ -467,6 +467,33 @@ def make_workload(name):
 
         return Workload(name, cfg, len(mults) * 512 * 512 / 1e6, len(mults) * n, 3, 32, [y], step, 8 * len(mults),
                         forward_only, "forward_only_per_tau"), None
+    if name == "tunew512":
+        clean = synth.clean_image(512, 512, 3, 5101)
+        y = synth.add_gaussian_float(clean, 25.0, 5101).astype(np.float32)
+        probe = np.random.default_rng(5102).choice([-1.0, 1.0], size=y.shape).astype(np.float32)
+        prm = dict(ps=8, stride=3, window=31, K=32)
+        steps = 4
+        cfg = {"workload": "tune_weights_rgb512_f32", "image": "512x512x3 float32", "noise": "gaussian sigma=25",
+               "sigma": "given (25)", "ps": 8, "stride": 3, "window": 31, "K": 32, "steps": steps, "step": 0.5,
+               "form": "per-group weights tuned by exponentiated-gradient steps on their SURE (eps = sigma/10): "
+                       "grouping and bases of y and y + eps probe once, per step two forward passes and two VJPs "
+                       "(MP count: one image per SURE evaluation)"}
+        n = H.num_groups(512, 512, prm)
+        pb = [None]
+        trace = [None]
+
+        def step(d):
+            if pb[0] is None:
+                pb[0] = dev(probe)
+            w, tr = H.tune_weights(d[0], 25.0, pb[0], prm, eps=2.5, steps=steps, step=0.5)
+            trace[0] = tr
+            return [w]
+
+        def forward_only(d):
+            return [H.denoise_f32(d[0], 25.0, prm)]
+
+        return Workload(name, cfg, (steps + 1) * 512 * 512 / 1e6, (steps + 1) * n, 3, 32, [y], step, 4 * n,
+                        forward_only, "forward_only"), None
     raise ValueError(name)
 
 
@@ -625,7 +652,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rgb4k", choices=["rgb512", "gray128", "rgb4k", "rgb1080", "hsi696", "batch64", "vjp8", "adaptive512",
-                                                      "video1080", "sweep512", "sure512"])
+                                                      "video1080", "sweep512", "sure512", "tunew512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
