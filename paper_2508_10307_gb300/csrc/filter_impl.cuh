@@ -961,10 +961,12 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         if (a.mask_out && tid < NBW) a.mask_out[(size_t)group_of(q) * NBW + tid] = 0u;
     };
 
-    // F(q): aggregation of group q's estimated patches into the footprint accumulator; the calling warp
-    // adds footprint rows r with r % 8 in {vw0, vw0 + vstep, ...} (no atomics: one warp per row class,
-    // patches in ascending order)
-    auto aggregate = [&](const int q, const int vw0, const int vstep) {
+    // F(q) on two warps: warp h adds the footprint rows r with r % 8 in {4h, ..., 4h + 3}; lane
+    // (row class 4h + lane / 8, pixel lane % 8) adds that pixel's C numerators and its weight as one
+    // vector. The four row classes of a warp are four different footprint rows, so the lanes of one
+    // instruction never share an address; patches go in ascending order (no atomics), and these
+    // warps run beside the C phase of the next group on the others.
+    auto aggregate2 = [&](const int q, const int h) {
         const int grp = group_of(q);
         const float* gbq = gb_of(q);
         const int* pos = pos_of(q);
@@ -972,30 +974,41 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         float wg = 1.f;
         if (a.w_in) wg = a.w_in[grp];
         else if (a.agg_mode == 1) wg = 1.f / (float)max(1, misc[1]);
-        if (tid == 0 && a.weights_out) a.weights_out[grp] = wg;
+        if (h == 0 && lane == 0 && a.weights_out) a.weights_out[grp] = wg;
+        const int rc = 4 * h + (lane >> 3), j = lane & 7;
+        constexpr int CH = K < 4 ? K : 4;             // patches whose offsets and values are fetched ahead
+        static_assert(K % CH == 0, "the chunks cover the group exactly");
 #pragma unroll 1
-        for (int vw = vw0; vw < 8; vw += vstep) {
-            // lane k precomputes, for patch k, the offsets of the row that this warp adds (its footprint
-            // row r has r % 8 == vw) in the accumulator and in the group buffer; the loop broadcasts them.
-            // Lane roles: C = 3: 24 numerator lanes (pixel j, channel c) and 8 weight lanes; C = 1: 8 and 8.
-            int my_aoff = 0, my_goff = 0;
-            if (lane < K) {
-                const int py = pos[2 * lane], px = pos[2 * lane + 1];
-                const int i = (vw - py) & 7;
-                my_aoff = ((py + i) * FW + px) * G::ACC;
-                my_goff = lane * G::GS + i * G::ROW;
-                if (MF && py >= FH) my_aoff = -1;     // a patch of another frame: not aggregated here
+        for (int k0 = 0; k0 < K; k0 += CH) {
+            int ao[CH];
+            float xv[CH][C];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int k = k0 + u, py = pos[2 * k], px = pos[2 * k + 1], i = (rc - py) & 7;
+                ao[u] = ((py + i) * FW + px + j) * G::ACC;
+                if (MF && py >= FH) ao[u] = -1;       // a patch of another frame: not aggregated here
+                const float* src = gbq + k * G::GS + i * G::ROW + j * C;
+#pragma unroll
+                for (int c = 0; c < C; ++c) xv[u][c] = src[c];
             }
-            constexpr int NV = PS * C;                // numerator lanes
-            const bool num = lane < NV, act = lane < NV + PS;
-            const int lofs = num ? (lane / C) * G::ACC + (lane % C) : (lane - NV) * G::ACC + C;
-#pragma unroll 4
-            for (int k = 0; k < K; ++k) {
-                const int aoff = __shfl_sync(0xffffffffu, my_aoff, k);
-                const int goff = __shfl_sync(0xffffffffu, my_goff, k);
-                if (act && (!MF || aoff >= 0)) {
-                    const float x = num ? gbq[goff + lane] : 1.f;
-                    acc[aoff + lofs] += wg * x;
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if (!MF || ao[u] >= 0) {
+                    if constexpr (C == 3) {
+                        float4* d = reinterpret_cast<float4*>(acc + ao[u]);
+                        float4 t = *d;
+                        t.x = fmaf(wg, xv[u][0], t.x);
+                        t.y = fmaf(wg, xv[u][1], t.y);
+                        t.z = fmaf(wg, xv[u][2], t.z);
+                        t.w += wg;
+                        *d = t;
+                    } else {
+                        float2* d = reinterpret_cast<float2*>(acc + ao[u]);
+                        float2 t = *d;
+                        t.x = fmaf(wg, xv[u][0], t.x);
+                        t.y += wg;
+                        *d = t;
+                    }
                 }
                 __syncwarp();                         // orders the read-modify-writes of patches k, k+1
             }
@@ -1219,9 +1232,13 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
             if (tid >= AB0 && tid < AB0 + 32) nz_of(q + 1)[tid - AB0] = 0u;
         }
         __syncthreads();
-        if (VAR != 1 && q >= 0) aggregate(q, warp, 8);
-        // ---- C(q+1); positions and counters of q+2 into the slot that q-1 used
-        if (q + 1 < ngr) phase_c(q + 1);
+        // ---- F(q) on warps 6, 7 beside C(q+1) on the fibre warps; positions and counters of q+2
+        // into the slot that q-1 used
+        if (warp >= 6) {
+            if (VAR != 1 && q >= 0) aggregate2(q, warp - 6);
+        } else if (q + 1 < ngr) {
+            phase_c(q + 1);
+        }
         if (q + 2 < ngr) {
             store_pos(next_idx, pos_of(q + 2));
             if (tid < 16) misc_of(q + 2)[tid] = 0;
