@@ -827,6 +827,10 @@ __device__ __forceinline__ int bank_fibre(int vw, int lane) {
 __device__ __forceinline__ void bar_sync_lower_half() {       // warps 0 .. 3 only (named barrier 1)
     asm volatile("bar.sync 1, 128;" ::: "memory");
 }
+// Named barrier 2, all 256 threads: the first half arrives (its writes before it become visible to
+// the second half) without waiting; the second half waits for it.
+__device__ __forceinline__ void bar_arrive_handoff() { asm volatile("bar.arrive 2, 256;" ::: "memory"); }
+__device__ __forceinline__ void bar_sync_handoff() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
 
 // Forward filter of one tile, software-pipelined over its groups with two CTA barriers per group:
 // [inverse of q on the first half of the CTA | A, B(q+1) on the second half] then [F(q) aggregation
@@ -1192,23 +1196,21 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                     const uint32_t rows = nz[u >> 3];
                     if (rows) stage_e_sparse<C>(bas, gbq, u >> 3, u & 7, rows);   // slots without a kept
                 }                                                               // coefficient stay zero
+                // Haar synthesis along the group mode, per fibre: virtual warps 0-3 here, 4 and 5
+                // (C = 3) on the second half once its projections are done (hand-off barrier)
+                bar_arrive_handoff();
                 bar_sync_lower_half();
-                // Haar synthesis along the group mode, per fibre
-#pragma unroll 1
-                for (int pass = 0; pass < 2; ++pass) {
-                    if (((warp & 3) + 4 * pass) * 32 >= NF) break;               // warp-uniform
-                    const int fo = pass == 0 ? foffA : foffB;
+                if ((warp & 3) * 32 < NF) {                                      // warp-uniform
                     float v[K];
 #pragma unroll
-                    for (int k = 0; k < K; ++k) v[k] = gbq[k * G::GS + fo];
+                    for (int k = 0; k < K; ++k) v[k] = gbq[k * G::GS + foffA];
                     haar_inv_sum<K>(v);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) gbq[k * G::GS + fo] = v[k];
+                    for (int k = 0; k < K; ++k) gbq[k * G::GS + foffA] = v[k];
                 }
-                bar_sync_lower_half();
             }
         }
-        // ... beside A, B(q+1) on the second half
+        // ... beside A, B(q+1) on the second half, which then takes virtual warps 4-7 of the synthesis
         if (tid >= AB0 && tid < AB0 + NU && q + 1 < ngr) {
             if constexpr (VAR == 2) {
                 // the cached coefficients of group q+1, four fibres per 128-bit word (64 C fibres per
@@ -1225,6 +1227,19 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 if (u == 0) misc_of(q + 1)[sizeof(Tin) == 1 ? 5 : 2] = a.cache_nrm[g1];
             } else {
                 project(tid - AB0, q + 1);
+            }
+        }
+        if (VAR != 1 && q >= 0 && tid >= AB0) {
+            // every thread of the second half meets the hand-off once per group the first half inverts
+            bar_sync_handoff();
+            if (((warp & 3) + 4) * 32 < NF) {                                    // warp-uniform
+                float* gbq = gb_of(q);
+                float v[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) v[k] = gbq[k * G::GS + foffB];
+                haar_inv_sum<K>(v);
+#pragma unroll
+                for (int k = 0; k < K; ++k) gbq[k * G::GS + foffB] = v[k];
             }
         }
         if (q + 1 < ngr) {
