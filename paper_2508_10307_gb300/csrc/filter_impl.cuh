@@ -827,10 +827,10 @@ __device__ __forceinline__ int bank_fibre(int vw, int lane) {
 __device__ __forceinline__ void bar_sync_lower_half() {       // warps 0 .. 3 only (named barrier 1)
     asm volatile("bar.sync 1, 128;" ::: "memory");
 }
-// Named barrier 2, all 256 threads: the first half arrives (its writes before it become visible to
-// the second half) without waiting; the second half waits for it.
-__device__ __forceinline__ void bar_arrive_handoff() { asm volatile("bar.arrive 2, 256;" ::: "memory"); }
-__device__ __forceinline__ void bar_sync_handoff() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+// Named barrier 3, all 256 threads: the fibre warps arrive after the C phase, the aggregation warps
+// wait for it (they build the next group's stage-D work list from its finished row masks).
+__device__ __forceinline__ void bar_arrive_cdone() { asm volatile("bar.arrive 3, 256;" ::: "memory"); }
+__device__ __forceinline__ void bar_sync_cdone() { asm volatile("bar.sync 3, 256;" ::: "memory"); }
 
 // Forward filter of one tile, software-pipelined over its groups with two CTA barriers per group:
 // [inverse of q on the first half of the CTA | A, B(q+1) on the second half] then [F(q) aggregation
@@ -1169,21 +1169,8 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
             if (q >= 0 && tid < 128) {
                 float* gbq = gb_of(q);
                 const uint32_t* nz = nz_of(q);
-                // stage-D work list: the (Haar slot k, basis row i) pairs holding a kept coefficient
-                if (warp == 0) {
-                    const uint32_t msk = lane < K ? nz[lane] : 0u;
-                    const int c = __popc(msk);
-                    int incl = c;
-#pragma unroll
-                    for (int off = 1; off < 32; off <<= 1) {
-                        const int t = __shfl_up_sync(0xffffffffu, incl, off);
-                        if (lane >= off) incl += t;
-                    }
-                    int o = incl - c;
-                    for (uint32_t b = msk; b; b &= b - 1) dlist[o++] = (unsigned char)((lane << 3) | (__ffs(b) - 1));
-                    if (lane == 31) *dcount = incl;
-                }
-                bar_sync_lower_half();
+                // stage D over the work list of the (Haar slot k, basis row i) pairs holding a kept
+                // coefficient (built at the end of the group's C phase)
                 const int nd = *dcount;
 #pragma unroll 1
                 for (int it = tid; it < nd; it += 128) {
@@ -1196,21 +1183,22 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                     const uint32_t rows = nz[u >> 3];
                     if (rows) stage_e_sparse<C>(bas, gbq, u >> 3, u & 7, rows);   // slots without a kept
                 }                                                               // coefficient stay zero
-                // Haar synthesis along the group mode, per fibre: virtual warps 0-3 here, 4 and 5
-                // (C = 3) on the second half once its projections are done (hand-off barrier)
-                bar_arrive_handoff();
                 bar_sync_lower_half();
-                if ((warp & 3) * 32 < NF) {                                      // warp-uniform
+                // Haar synthesis along the group mode, per fibre (virtual warps w and w + 4)
+#pragma unroll 1
+                for (int pass = 0; pass < 2; ++pass) {
+                    if (((warp & 3) + 4 * pass) * 32 >= NF) break;               // warp-uniform
+                    const int fo = pass == 0 ? foffA : foffB;
                     float v[K];
 #pragma unroll
-                    for (int k = 0; k < K; ++k) v[k] = gbq[k * G::GS + foffA];
+                    for (int k = 0; k < K; ++k) v[k] = gbq[k * G::GS + fo];
                     haar_inv_sum<K>(v);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) gbq[k * G::GS + foffA] = v[k];
+                    for (int k = 0; k < K; ++k) gbq[k * G::GS + fo] = v[k];
                 }
             }
         }
-        // ... beside A, B(q+1) on the second half, which then takes virtual warps 4-7 of the synthesis
+        // ... beside A, B(q+1) on the second half
         if (tid >= AB0 && tid < AB0 + NU && q + 1 < ngr) {
             if constexpr (VAR == 2) {
                 // the cached coefficients of group q+1, four fibres per 128-bit word (64 C fibres per
@@ -1229,19 +1217,6 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 project(tid - AB0, q + 1);
             }
         }
-        if (VAR != 1 && q >= 0 && tid >= AB0) {
-            // every thread of the second half meets the hand-off once per group the first half inverts
-            bar_sync_handoff();
-            if (((warp & 3) + 4) * 32 < NF) {                                    // warp-uniform
-                float* gbq = gb_of(q);
-                float v[K];
-#pragma unroll
-                for (int k = 0; k < K; ++k) v[k] = gbq[k * G::GS + foffB];
-                haar_inv_sum<K>(v);
-#pragma unroll
-                for (int k = 0; k < K; ++k) gbq[k * G::GS + foffB] = v[k];
-            }
-        }
         if (q + 1 < ngr) {
             clear_masks(q + 1);
             if (tid >= AB0 && tid < AB0 + 32) nz_of(q + 1)[tid - AB0] = 0u;
@@ -1251,8 +1226,27 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         // into the slot that q-1 used
         if (warp >= 6) {
             if (VAR != 1 && q >= 0) aggregate2(q, warp - 6);
+            if (VAR != 1 && q + 1 < ngr) {
+                // stage-D work list of group q+1 once its row masks are final: the (Haar slot k,
+                // basis row i) pairs holding a kept coefficient, in (k, i) order
+                bar_sync_cdone();
+                if (warp == 6) {
+                    const uint32_t msk = lane < K ? nz_of(q + 1)[lane] : 0u;
+                    const int c = __popc(msk);
+                    int incl = c;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += t;
+                    }
+                    int o = incl - c;
+                    for (uint32_t b = msk; b; b &= b - 1) dlist[o++] = (unsigned char)((lane << 3) | (__ffs(b) - 1));
+                    if (lane == 31) *dcount = incl;
+                }
+            }
         } else if (q + 1 < ngr) {
             phase_c(q + 1);
+            if (VAR != 1) bar_arrive_cdone();
         }
         if (q + 2 < ngr) {
             store_pos(next_idx, pos_of(q + 2));
