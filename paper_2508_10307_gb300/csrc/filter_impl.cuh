@@ -1073,8 +1073,11 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                     float* cdst = a.coef_out + (size_t)grp * K * NF;
                     haar_for_each<K>([&](int m, int sl, int L) { cdst[m * NF + fib] = v[sl] * rsqrtf((float)L); });
                 }
+                // decided coefficients are scaled (kept, by 1 / L) or zeroed in place; a coefficient
+                // inside the band keeps its raw value until it is decided
                 float dlast = 0.f;
                 int mlast = 0;
+                uint32_t nzs = 0;
                 haar_for_each<K>([&](int m, int sl, int L) {
                     const float r = sqrtf((float)L);      // folds to a constant once unrolled
                     const float d = fmaf(-a.tau32, r, fabsf(v[sl]));
@@ -1082,8 +1085,11 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                         bandb |= 1u << m;
                         dlast = d;
                         mlast = m;
-                    } else if (d >= 0.f) {
-                        keepb |= 1u << m;
+                    } else {
+                        const bool kp = d >= 0.f;
+                        keepb |= (kp ? 1u : 0u) << m;
+                        nzs |= (kp ? 1u : 0u) << sl;
+                        v[sl] = kp ? v[sl] * (1.f / (float)L) : 0.f;
                     }
                 });
                 if (bandb != 0u && (bandb & (bandb - 1u)) == 0u) {
@@ -1097,24 +1103,22 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                     for (int k = k0; k < k0 + L; ++k) sq += pn[k];
                     if (fabsf(dlast) > (a.band_rel * sqrtf(sq) + a.band_abs) * sqrtf((float)L)) {
                         bandb = 0u;
-                        if (dlast >= 0.f) keepb |= 1u << m;
+                        const bool kp = dlast >= 0.f;
+                        keepb |= (kp ? 1u : 0u) << m;
+                        haar_for_each<K>([&](int mm, int sl, int LL) {
+                            if (mm == m) {
+                                v[sl] = kp ? v[sl] * (1.f / (float)LL) : 0.f;
+                                nzs |= (kp ? 1u : 0u) << sl;
+                            }
+                        });
                     }
                 }
                 anyb = __ballot_sync(0xffffffffu, bandb != 0u);
+#pragma unroll
+                for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = v[k];    // band coefficients still raw
                 if (!anyb) {
                     keep_finish(keepb);
-                    uint32_t nzs = 0;
-                    haar_for_each<K>([&](int m, int sl, int L) {
-                        const bool kp = (keepb >> m) & 1u;
-                        v[sl] = kp ? v[sl] * (1.f / (float)L) : 0.f;
-                        nzs |= (kp ? 1u : 0u) << sl;
-                    });
-#pragma unroll
-                    for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = v[k];
                     mark_rows(nzs);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = v[k];    // park the coefficients
                 }
             }
             if (anyb) {                                   // warp-uniform
@@ -1139,7 +1143,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 uint32_t nzs = 0;
                 haar_for_each<K>([&](int m, int sl, int L) {
                     const bool kp = (keepb >> m) & 1u;
-                    w[sl] = kp ? w[sl] * (1.f / (float)L) : 0.f;
+                    if ((bandb >> m) & 1u) w[sl] = kp ? w[sl] * (1.f / (float)L) : 0.f;    // the rest is final
                     nzs |= (kp ? 1u : 0u) << sl;
                 });
 #pragma unroll
