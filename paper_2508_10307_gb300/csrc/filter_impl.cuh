@@ -89,7 +89,8 @@ struct FwdOff {
     static constexpr int dlist = nz + 2 * 32 * 4;                    // stage-D work list (256 entries)
     static constexpr int dcount = dlist + 256;
     static constexpr int misc = dcount + 16;                         // counters of three groups
-    static constexpr int acc = misc + 3 * 16 * 4;
+    static constexpr int aofs = misc + 3 * 16 * 4;                   // aggregation offsets [32][8] int2
+    static constexpr int acc = aofs + 32 * 8 * 8;
 };
 template <int K, int C>
 __host__ __device__ inline FLayout f_layout_fwd(int FH, int FW, int in_bytes, int nfr = 1) {
@@ -878,6 +879,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     uint32_t* nzb = reinterpret_cast<uint32_t*>(smem + O::nz);                // [2][32] basis-row masks
     unsigned char* dlist = smem + O::dlist;                                  // stage-D work list (k << 3 | i)
     int* dcount = reinterpret_cast<int*>(smem + O::dcount);
+    int2* aofs = reinterpret_cast<int2*>(smem + O::aofs);                     // [patch][row class]
     float* acc = reinterpret_cast<float*>(smem + O::acc);
     Tin* img_s = reinterpret_cast<Tin*>(smem + L.off_img);
     // frame of staging slot sl (slot 0: the reference frame, then the others in order)
@@ -973,7 +975,6 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
     auto aggregate2 = [&](const int q, const int h) {
         const int grp = group_of(q);
         const float* gbq = gb_of(q);
-        const int* pos = pos_of(q);
         const int* misc = misc_of(q);
         float wg = 1.f;
         if (a.w_in) wg = a.w_in[grp];
@@ -988,10 +989,9 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
             float xv[CH][C];
 #pragma unroll
             for (int u = 0; u < CH; ++u) {
-                const int k = k0 + u, py = pos[2 * k], px = pos[2 * k + 1], i = (rc - py) & 7;
-                ao[u] = ((py + i) * FW + px + j) * G::ACC;
-                if (MF && py >= FH) ao[u] = -1;       // a patch of another frame: not aggregated here
-                const float* src = gbq + k * G::GS + i * G::ROW + j * C;
+                const int2 o = aofs[(k0 + u) * 8 + rc];   // (accumulator, group-buffer) offsets of the row
+                ao[u] = o.x < 0 ? -1 : o.x + j * G::ACC;
+                const float* src = gbq + o.y + j * C;
 #pragma unroll
                 for (int c = 0; c < C; ++c) xv[u][c] = src[c];
             }
@@ -1019,6 +1019,20 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         }
     };
 
+    // offsets for aggregate2 of group q, for the four row classes of warp h: patch k's row i with
+    // (py + i) % 8 = rc starts at accumulator float ((py + i) FW + px) ACC (-1: a patch of another
+    // frame) and group-buffer float k GS + i ROW
+    auto agg_offsets = [&](const int q, const int h) {
+        const int* pos = pos_of(q);
+        for (int e = lane; e < K * 4; e += 32) {
+            const int k = e >> 2, rc = 4 * h + (e & 3);
+            const int py = pos[2 * k], px = pos[2 * k + 1], i = (rc - py) & 7;
+            int ao = ((py + i) * FW + px) * G::ACC;
+            if (MF && py >= FH) ao = -1;
+            aofs[k * 8 + rc] = make_int2(ao, k * G::GS + i * G::ROW);
+        }
+    };
+
     // C(q): Haar analysis, threshold (FP64 inside the guard band), synthesis, by the NF fibre threads
     auto phase_c = [&](const int q) {
         const int grp = group_of(q);
@@ -1027,15 +1041,18 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         int* misc = misc_of(q);
         const float* pn = pn_of(q);
         // final keep decisions of the warp's fibres: optional mask output, kept count
-        auto keep_finish = [&](uint32_t keepb) {
+        // (nzs: kept coefficients as bits by Haar slot)
+        auto keep_finish = [&](uint32_t nzs) {
             if (a.mask_out) {                             // words cleared a phase earlier
+                uint32_t keepb = 0;                       // the same bits by Haar row
+                haar_for_each<K>([&](int m, int sl, int L) { keepb |= ((nzs >> sl) & 1u) << m; });
                 uint32_t* mo = a.mask_out + (size_t)grp * NBW;
                 for (uint32_t b = keepb; b; b &= b - 1) {
                     const int m = __ffs(b) - 1;
                     atomicOr(&mo[m * (NF / 32) + (fib >> 5)], 1u << (fib & 31));
                 }
             }
-            const int wk = __reduce_add_sync(0xffffffffu, __popc(keepb));
+            const int wk = __reduce_add_sync(0xffffffffu, __popc(nzs));
             if (lane == 0) atomicAdd(&misc[1], wk);
         };
         // basis row of this fibre into the masks of the Haar slots where it kept a coefficient
@@ -1053,7 +1070,7 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
             // (the rare guard-band path finishes the fibre in a scope of its own, with a second
             // array reloaded from shared memory, so that no K-register array is live across the
             // FP64 refinement loop: that would push the array to local memory)
-            uint32_t keepb = 0, bandb = 0;
+            uint32_t nzs = 0, bandb = 0;                  // kept (by Haar slot), inside the band (by Haar row)
             unsigned anyb;
             // The Haar transform runs unnormalised (sums and differences): row m's coefficient is
             // sqrt(L_m) times the normalised one, so threshold and band scale by sqrt(L_m) (one pair of
@@ -1075,53 +1092,46 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                 }
                 // decided coefficients are scaled (kept, by 1 / L) or zeroed in place; a coefficient
                 // inside the band keeps its raw value until it is decided
-                float dlast = 0.f;
-                int mlast = 0;
-                uint32_t nzs = 0;
                 haar_for_each<K>([&](int m, int sl, int L) {
                     const float r = sqrtf((float)L);      // folds to a constant once unrolled
                     const float d = fmaf(-a.tau32, r, fabsf(v[sl]));
-                    if (fabsf(d) <= delta * r) {
-                        bandb |= 1u << m;
-                        dlast = d;
-                        mlast = m;
-                    } else {
-                        const bool kp = d >= 0.f;
-                        keepb |= (kp ? 1u : 0u) << m;
-                        nzs |= (kp ? 1u : 0u) << sl;
-                        v[sl] = kp ? v[sl] * (1.f / (float)L) : 0.f;
-                    }
+                    const bool band = fabsf(d) <= delta * r;
+                    const bool kp = !band && d >= 0.f;
+                    bandb |= (band ? 1u : 0u) << m;
+                    nzs |= (kp ? 1u : 0u) << sl;
+                    v[sl] = band ? v[sl] : (kp ? v[sl] * (1.f / (float)L) : 0.f);
                 });
+#pragma unroll
+                for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = v[k];    // band coefficients still raw
                 if (bandb != 0u && (bandb & (bandb - 1u)) == 0u) {
                     // one entry inside the group-wide band (the usual case): the FP32 error of row m
                     // only involves the patches of its Haar support (L = K / 2^level patches from k0),
-                    // so the band narrows to their norm
-                    const int m = mlast;
+                    // so the band narrows to their norm. Row m >= 1 of level lv sits in slot
+                    // (2 (m - 2^lv) + 1) K / 2^(lv + 1); row 0 in slot 0.
+                    const int m = __ffs(bandb) - 1;
                     const int lv = m == 0 ? 0 : 31 - __clz(m);
                     const int L = m == 0 ? K : K >> lv, k0 = m == 0 ? 0 : (m - (1 << lv)) * L;
+                    const int sl = m == 0 ? 0 : (2 * (m - (1 << lv)) + 1) * (K >> (lv + 1));
+                    float* cm = gbq + sl * G::GS + foff;
+                    const float raw = *cm, dm = fmaf(-a.tau32, sqrtf((float)L), fabsf(raw));
                     float sq = 0.f;
                     for (int k = k0; k < k0 + L; ++k) sq += pn[k];
-                    if (fabsf(dlast) > (a.band_rel * sqrtf(sq) + a.band_abs) * sqrtf((float)L)) {
+                    if (fabsf(dm) > (a.band_rel * sqrtf(sq) + a.band_abs) * sqrtf((float)L)) {
                         bandb = 0u;
-                        const bool kp = dlast >= 0.f;
-                        keepb |= (kp ? 1u : 0u) << m;
-                        haar_for_each<K>([&](int mm, int sl, int LL) {
-                            if (mm == m) {
-                                v[sl] = kp ? v[sl] * (1.f / (float)LL) : 0.f;
-                                nzs |= (kp ? 1u : 0u) << sl;
-                            }
-                        });
+                        const bool kp = dm >= 0.f;
+                        *cm = kp ? raw * (1.f / (float)L) : 0.f;
+                        nzs |= (kp ? 1u : 0u) << sl;
                     }
                 }
                 anyb = __ballot_sync(0xffffffffu, bandb != 0u);
-#pragma unroll
-                for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = v[k];    // band coefficients still raw
                 if (!anyb) {
-                    keep_finish(keepb);
+                    keep_finish(nzs);
                     mark_rows(nzs);
                 }
             }
             if (anyb) {                                   // warp-uniform
+                uint32_t keepb = 0;                       // the kept bits by Haar row, then the FP64 ones
+                haar_for_each<K>([&](int m, int sl, int L) { keepb |= ((nzs >> sl) & 1u) << m; });
                 __syncwarp();
                 do {
                     const int l = __ffs(anyb) - 1;
@@ -1136,19 +1146,19 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
                     }
                 } while (anyb);
                 __syncwarp();
-                keep_finish(keepb);
                 float w[K];
 #pragma unroll
                 for (int k = 0; k < K; ++k) w[k] = gbq[k * G::GS + foff];
-                uint32_t nzs = 0;
+                uint32_t nzf = 0;
                 haar_for_each<K>([&](int m, int sl, int L) {
                     const bool kp = (keepb >> m) & 1u;
                     if ((bandb >> m) & 1u) w[sl] = kp ? w[sl] * (1.f / (float)L) : 0.f;    // the rest is final
-                    nzs |= (kp ? 1u : 0u) << sl;
+                    nzf |= (kp ? 1u : 0u) << sl;
                 });
 #pragma unroll
                 for (int k = 0; k < K; ++k) gbq[k * G::GS + foff] = w[k];
-                mark_rows(nzs);
+                keep_finish(nzf);
+                mark_rows(nzf);
             }
         }
     };
@@ -1231,6 +1241,8 @@ __device__ __forceinline__ void filter_tile_fwd(const FilterArgs& a, const int t
         if (warp >= 6) {
             if (VAR != 1 && q >= 0) aggregate2(q, warp - 6);
             if (VAR != 1 && q + 1 < ngr) {
+                __syncwarp();                         // every lane is done with group q's offsets
+                agg_offsets(q + 1, warp - 6);
                 // stage-D work list of group q+1 once its row masks are final: the (Haar slot k,
                 // basis row i) pairs holding a kept coefficient, in (k, i) order
                 bar_sync_cdone();
