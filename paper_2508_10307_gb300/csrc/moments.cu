@@ -668,29 +668,42 @@ __device__ __forceinline__ void basis_problem(const unsigned long long* __restri
     double (*Vr)[PS] = reinterpret_cast<double (*)[PS]>(work + 2 * PS2);
     double (*Vi)[PS] = reinterpret_cast<double (*)[PS]>(work + 3 * PS2);
     const unsigned long long* M = mom + (size_t)which * PS * PS * C * C;
-    const double s32 = 0.5 * sqrt(3.0);
+    // w^k, w = exp(-2 pi i / C), k < C: exact constants for C = 3, the library's cospi / sinpi otherwise
+    __shared__ double phr[64], phi[64];
+    for (int k = lane; k < C; k += 32) {
+        double cr = 1.0, ci = 0.0;
+        if (C == 3) {
+            const double s32 = 0.5 * sqrt(3.0);
+            if (k == 1) { cr = -0.5; ci = -s32; }
+            if (k == 2) { cr = -0.5; ci = s32; }
+        } else if (k != 0) {
+            double sn, cs;
+            sincospi(2.0 * k / C, &sn, &cs);
+            cr = cs;
+            ci = -sn;
+        }
+        phr[k] = cr;
+        phi[k] = ci;
+    }
+    __syncwarp();
+    // A_f[u][v] = sum_{c, c2} M[u v][c][c2] w^{f (c - c2)} (U) or w^{f (c2 - c)} (V): the moments of one
+    // band difference d = c - c2 (mod C) share the phase, so they are summed first, exactly in
+    // integers, and each difference takes one complex product
     for (int e = lane; e < PS2; e += 32) {
         const int u = e / PS, v = e % PS;
+        const unsigned long long* Me = M + (size_t)(u * PS + v) * C * C;
         double accr = 0.0, acci = 0.0;
-        for (int c = 0; c < C; ++c)
-            for (int c2 = 0; c2 < C; ++c2) {
-                const double m = (double)M[((u * PS + v) * C + c) * C + c2];
-                const int d = which == 0 ? (c - c2) : (c2 - c);
-                const int k = ((f * d) % C + C) % C;
-                // w^k, w = exp(-2 pi i / C): exact constants for C = 3, the library's cospi / sinpi otherwise
-                double phr = 1.0, phi = 0.0;
-                if (C == 3) {
-                    if (k == 1) { phr = -0.5; phi = -s32; }
-                    if (k == 2) { phr = -0.5; phi = s32; }
-                } else if (k != 0) {
-                    double sn, cs;
-                    sincospi(2.0 * k / C, &sn, &cs);
-                    phr = cs;
-                    phi = -sn;
-                }
-                accr += m * phr;
-                acci += m * phi;
+        for (int d = 0; d < C; ++d) {
+            unsigned long long sd = 0;
+            for (int c = 0, c2 = C - d; c < C; ++c, ++c2) {
+                if (c2 >= C) c2 -= C;                        // c2 = (c - d) mod C
+                sd += Me[c * C + c2];
             }
+            const int dd = which == 0 ? d : (C - d) % C;
+            const int k = (f * dd) % C;
+            accr += (double)sd * phr[k];
+            acci += (double)sd * phi[k];
+        }
         Ar[u][v] = accr;
         Ai[u][v] = u == v ? 0.0 : acci;
     }
