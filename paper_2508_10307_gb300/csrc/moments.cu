@@ -155,65 +155,95 @@ __global__ void __launch_bounds__(256) moments_batch_kernel(const BMArgs* __rest
 // layout of moments_chunk ([2][8][8][C][C]): with the 8-byte vectors r_(a,c) = P[a][0..7][c] and
 // q_(b,c) = P[0..7][b][c] of a reference, R[a][a'][c][c'] = sum over references of <r_(a,c), r_(a',c')>
 // and Q[b][b'][c][c'] = sum of <q_(b,c), q_(b',c')>: two Gram matrices of 8C vectors per reference,
-// accumulated with DP4A. CTA (x: which, 32-vector row tile, 32-vector column tile; y: chunk of
-// CM_CHUNK references); uint32 partials per CTA (CM_CHUNK * 8 * 255^2 < 2^32), added to uint64 out.
-constexpr int CM_T = 32;
-constexpr int CM_BATCH = 32;
-constexpr int CM_CHUNK = 2048;
+// accumulated with DP4A. The Gram matrices are symmetric, so only tile pairs tu <= tv are formed and
+// an off-diagonal tile also writes its mirror. CTA (x: which, tile pair of 64-vector tiles; y: chunk
+// of CM_CHUNK references), 16 x 16 threads with 4 x 4 entries each; uint32 partials per CTA
+// (CM_CHUNK * 8 * 255^2 < 2^32), added to uint64 out.
+constexpr int CM_T = 64;
+constexpr int CM_BATCH = 16;
+constexpr int CM_CHUNK = 1024;
 
 __global__ void __launch_bounds__(256) cube_moments_kernel(const uint8_t* __restrict__ img, Geo g, int ntile,
                                                            unsigned long long* __restrict__ out) {
-    __shared__ uint32_t su[CM_BATCH][CM_T][2], sv[CM_BATCH][CM_T][2];
+    __shared__ __align__(16) uint2 su[CM_BATCH][CM_T], sv[CM_BATCH][CM_T];
+    __shared__ int rbase[CM_BATCH];
     const int C = g.C, D = PS * C;
-    const int which = blockIdx.x / (ntile * ntile);
-    const int rem = blockIdx.x - which * ntile * ntile;
-    const int tu = rem / ntile, tv = rem - tu * ntile;
+    const int npair = ntile * (ntile + 1) / 2;
+    const int which = blockIdx.x / npair;
+    int pr = blockIdx.x - which * npair, tu = 0;
+    while (pr >= ntile - tu) {
+        pr -= ntile - tu;
+        ++tu;
+    }
+    const int tv = tu + pr;                           // tu <= tv
+    const bool diag = tu == tv;
     const int N = g.ngroups();
     const int r0 = blockIdx.y * CM_CHUNK, r1 = min(r0 + CM_CHUNK, N);
-    const int lu = threadIdx.x >> 3, lv0 = (threadIdx.x & 7) * 4;
-    uint32_t acc[4] = {0u, 0u, 0u, 0u};
-    // word (vector x, half h) of reference r: 4 bytes of vector x = (e, c), e = a (rows) or b (columns)
-    auto word = [&](int r, int x, int h) -> uint32_t {
-        if (x >= D) return 0u;
-        const int iy = r / g.nrx, ix = r - iy * g.nrx;
-        const int ry = ref_pos(iy, g.s, g.H), rx = ref_pos(ix, g.s, g.W);
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    uint32_t acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = 0u;
+    // the 8 bytes of vector x = (e, c) of the reference whose corner is byte rb: row e, columns 0..7
+    // (which = 0) or column e, rows 0..7 (which = 1), band c
+    const size_t st = (size_t)(which == 0 ? 1 : g.W) * C;
+    auto vec = [&](int rb, int x) -> uint2 {
+        if (x >= D) return make_uint2(0u, 0u);
         const int e = x / C, c = x - e * C;
-        uint32_t w = 0u;
+        const uint8_t* p0 = img + rb + (size_t)(which == 0 ? e * g.W : e) * C + c;
+        uint32_t w0 = 0u, w1 = 0u;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            const int o = 4 * h + t;                  // b (rows) or a (columns)
-            const int y = which == 0 ? ry + e : ry + o, xx = which == 0 ? rx + o : rx + e;
-            w |= (uint32_t)img[((size_t)y * g.W + xx) * C + c] << (8 * t);
+            w0 |= (uint32_t)p0[t * st] << (8 * t);
+            w1 |= (uint32_t)p0[(4 + t) * st] << (8 * t);
         }
-        return w;
+        return make_uint2(w0, w1);
     };
-    for (int rb = r0; rb < r1; rb += CM_BATCH) {
-        const int nb = min(CM_BATCH, r1 - rb);
+    for (int rb0 = r0; rb0 < r1; rb0 += CM_BATCH) {
+        const int nb = min(CM_BATCH, r1 - rb0);
         __syncthreads();
-        for (int t = threadIdx.x; t < nb * CM_T * 2; t += 256) {
-            const int j = t / (CM_T * 2), rm = t - j * CM_T * 2, x = rm >> 1, h = rm & 1;
-            su[j][x][h] = word(rb + j, tu * CM_T + x, h);
-            sv[j][x][h] = word(rb + j, tv * CM_T + x, h);
+        if (threadIdx.x < nb) {
+            const int r = rb0 + threadIdx.x, iy = r / g.nrx, ix = r - iy * g.nrx;
+            rbase[threadIdx.x] = (ref_pos(iy, g.s, g.H) * g.W + ref_pos(ix, g.s, g.W)) * C;
         }
         __syncthreads();
-        for (int j = 0; j < nb; ++j) {
-            const uint32_t u0 = su[j][lu][0], u1 = su[j][lu][1];
+        for (int t = threadIdx.x; t < nb * CM_T; t += 256) {
+            const int jj = t / CM_T, x = t - jj * CM_T;
+            su[jj][x] = vec(rbase[jj], tu * CM_T + x);
+            if (!diag) sv[jj][x] = vec(rbase[jj], tv * CM_T + x);
+        }
+        __syncthreads();
+        const uint2 (*Vs)[CM_T] = diag ? su : sv;
+        for (int jj = 0; jj < nb; ++jj) {
+            const uint4* pa = reinterpret_cast<const uint4*>(&su[jj][ty * 4]);
+            const uint4* pb = reinterpret_cast<const uint4*>(&Vs[jj][tx * 4]);
+            const uint4 a01 = pa[0], a23 = pa[1], b01 = pb[0], b23 = pb[1];
+            const uint32_t au[4][2] = {{a01.x, a01.y}, {a01.z, a01.w}, {a23.x, a23.y}, {a23.z, a23.w}};
+            const uint32_t bv[4][2] = {{b01.x, b01.y}, {b01.z, b01.w}, {b23.x, b23.y}, {b23.z, b23.w}};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                acc[q] = __dp4a(u0, sv[j][lv0 + q][0], acc[q]);
-                acc[q] = __dp4a(u1, sv[j][lv0 + q][1], acc[q]);
-            }
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[i][q] = __dp4a(au[i][0], bv[q][0], acc[i][q]);
+                    acc[i][q] = __dp4a(au[i][1], bv[q][1], acc[i][q]);
+                }
         }
     }
-    const int u = tu * CM_T + lu;
-    if (u >= D) return;
-    const int e = u / C, c = u - e * C;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int v = tv * CM_T + lv0 + q;
-        if (v >= D || acc[q] == 0u) continue;
-        const int e2 = v / C, c2 = v - e2 * C;
-        atomicAdd(out + ((((size_t)which * PS + e) * PS + e2) * C + c) * C + c2, (unsigned long long)acc[q]);
+    for (int i = 0; i < 4; ++i) {
+        const int u = tu * CM_T + ty * 4 + i;
+        if (u >= D) continue;
+        const int e = u / C, c = u - e * C;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int v = tv * CM_T + tx * 4 + q;
+            if (v >= D || acc[i][q] == 0u) continue;
+            const int e2 = v / C, c2 = v - e2 * C;
+            atomicAdd(out + ((((size_t)which * PS + e) * PS + e2) * C + c) * C + c2, (unsigned long long)acc[i][q]);
+            if (!diag)
+                atomicAdd(out + ((((size_t)which * PS + e2) * PS + e) * C + c2) * C + c, (unsigned long long)acc[i][q]);
+        }
     }
 }
 
@@ -956,7 +986,7 @@ cudaError_t launch_cube_moments(const uint8_t* img, const Geo& g, unsigned long 
     cudaError_t e = cudaMemsetAsync(d_mom, 0, sizeof(unsigned long long) * 2 * PS2 * g.C * g.C, s);
     if (e != cudaSuccess) return e;
     const int ntile = (PS * g.C + CM_T - 1) / CM_T;
-    dim3 grid(2 * ntile * ntile, (g.ngroups() + CM_CHUNK - 1) / CM_CHUNK);
+    dim3 grid(2 * (ntile * (ntile + 1) / 2), (g.ngroups() + CM_CHUNK - 1) / CM_CHUNK);
     cube_moments_kernel<<<grid, 256, 0, s>>>(img, g, ntile, d_mom);
     return cudaGetLastError();
 }
