@@ -53,8 +53,8 @@ MAX_SM_MHZ = 2070.0              # GB300 maximum SM clock
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum) on the 1920x1080x3 workload,
 # which has the 3840x2160 frames' geometry and tile edge; a 3840x2160 launch scales it by its
 # groups (919,601 / 229,401: the traffic is the tile partials and indices, both proportional).
-FILTER_DRAM_BYTES = {"rgb1080": 36.178176e6 + 304.66944e6,
-                     "rgb4k": (36.178176e6 + 304.66944e6) * 919601 / 229401}
+FILTER_DRAM_BYTES = {"rgb1080": 37.154816e6 + 304.592384e6,
+                     "rgb4k": (37.154816e6 + 304.592384e6) * 919601 / 229401}
 
 
 def filter_flops_per_group(C: int, K: int) -> int:
