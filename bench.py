@@ -57,6 +57,15 @@ FILTER_DRAM_BYTES = {"rgb1080": 37.154816e6 + 304.592384e6,
                      "rgb4k": (37.154816e6 + 304.592384e6) * 919601 / 229401}
 
 
+def measured_peak(key: str):
+    """A peak from the measured MEASURED_PEAKS.json beside this file, or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def filter_flops_per_group(C: int, K: int) -> int:
     """Algorithmic FP32 flops of one group in the structured per-Fourier-slice form:
     t-SVD projections (per patch and direction: 10,240 for C=3, 2,048 for C=1), channel DFTs
@@ -395,6 +404,35 @@ def make_workload(name):
 
         return Workload(name, cfg, 8 * 512 * 512 / 1e6, 8 * n, 3, 32, xs, step, 8 * 512 * 512 * 3 * 4,
                         forward_only, "forward_only"), None
+    if name == "proj512":
+        # the batched basis projection of every patch of every group of the 512x512x3 workload (64,009
+        # groups x 32 members), on the tensor cores; compared with the structured FP32 form on the CUDA cores
+        clean, noisy, _, prm = synth.workload_rgb512()
+        setup = {}
+        cfg = {"workload": "projection_rgb512_members", "image": "512x512x3 uint8",
+               "noise": "poisson-gaussian a=0.01 b=15^2", "ps": 8, "stride": 2, "window": 31, "K": 32,
+               "patches_per_step": 64009 * 32,
+               "form": "S = U^T * P * V of every group member (64,009 x 32 patches, 192 FP32 coefficients each), "
+                       "tensor cores: dense 192x192 contraction, matrix split in three BF16 pieces"}
+
+        def prepare(x):
+            if "pos" not in setup:
+                _, info = H.denoise(x, None, prm, return_info=True, basis=True)
+                setup["pos"] = info["idx"].reshape(-1).contiguous()
+                setup["basis"] = info["basis"].reshape(-1).contiguous()
+                setup["out"] = torch.empty((setup["pos"].numel(), 192), dtype=torch.float32, device="cuda")
+            return setup
+
+        def step(d):
+            st = prepare(d[0])
+            return [H.project_patches(d[0], st["pos"], st["basis"], out=st["out"])]
+
+        def structured(d):
+            st = prepare(d[0])
+            return [H.project_patches(d[0], st["pos"], st["basis"], out=st["out"], structured=True)]
+
+        return Workload(name, cfg, 512 * 512 / 1e6, 64009, 3, 32, [noisy], step, 64009 * 32 * 192 * 4,
+                        structured, "structured_fp32_cuda_cores"), None
     if name == "adaptive512":
         clean, noisy, _, prm = synth.workload_rgb512()
         prm = dict(prm, adapt=True)
@@ -658,6 +696,22 @@ def run_gpu(args):
                 "traffic": None, "kernel": "cube_filter",
                 "peak_basis": f"FP32 FMA: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {MAX_SM_MHZ:.0f} MHz; "
                               "achieved counts the forward transforms only"}
+    elif dom == "project_tc":
+        # the dense contraction as the algorithm of this kernel: 2 (64 C)^2 flop per patch (three BF16
+        # products of it execute); peak: the measured BF16 dense rate
+        n_launch, ms = prof["project_tc"]
+        patches = wl.groups_per_step * wl.K
+        flops = 2.0 * (64 * wl.C) ** 2 * patches * args.steps / n_launch
+        achieved = flops / (ms / n_launch / 1000.0) / 1e12
+        peak = measured_peak("bf16_tflops")
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None, "kernel": "project_tc",
+                "executed_tflops": 3 * achieved,
+                "out_gbs": patches * 64 * wl.C * 4 * args.steps / n_launch / (ms / n_launch / 1000.0) / 1e9,
+                "peak_basis": "BF16 dense, cuBLAS burst (measured, MEASURED_PEAKS.json); achieved counts the "
+                              "dense contraction once (three BF16 pieces execute)"}
+        if "project_simt" in prof or wl.compare is not None:
+            roof["structured_flops_per_patch"] = 10240 + 2 * 17 * 64
     elif dom is not None:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
                 "kernel": dom}
@@ -695,7 +749,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rgb4k", choices=["rgb512", "gray128", "rgb4k", "rgb1080", "hsi696", "batch64", "vjp8", "adaptive512",
-                                                      "video1080", "sweep512", "sure512", "tunew512"])
+                                                      "video1080", "sweep512", "sure512", "tunew512", "proj512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -249,6 +249,26 @@ htsvd_status htsvd_denoise_batch(const htsvd_image* h_imgs, int32_t n, const hts
 htsvd_status htsvd_denoise_cube(const uint8_t* d_cube, int32_t H, int32_t W, int32_t N, double sigma,
                                 const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t stream);
 
+/* Batched forward projection of patches onto the global t-SVD bases (Sec. III-B.2, Eq. (forward
+ * transform) before the Haar transform along the group mode; Sec. II-C, Def. T-product): for each
+ * of n patches, S = U^T * P * V of the ps x ps x C uint8 patch P whose top-left corner is d_pos[t]
+ * (linear index y * W + x), i.e. per channel-Fourier slice f, U_f^H P_f V_f, then the inverse DFT
+ * along the channel mode. d_img: H x W x C uint8 (DEVICE, 4-byte aligned); d_pos: n int32 (DEVICE);
+ * d_basis: the FP64 bases in the layout of htsvd_params.d_basis_out (DEVICE; e.g. from htsvd_denoise
+ * of the same image); d_coef: n x 64 C float32 (DEVICE, 16-byte aligned), coefficient
+ * (i * 8 + j) * C + c of patch t at d_coef[t * 64 C + ...] (the order of the mask bits).
+ * The map P -> S is one real (64 C) x (64 C) matrix; it runs on the tensor cores as a dense
+ * contraction: the patch bytes are exact in BF16, the matrix is split into three BF16 pieces
+ * (each the rounding of what the earlier ones leave), FP32 accumulation, so the coefficients carry
+ * an FP32-level error (measured below 2^-22 of the patch norm). A position whose patch does not
+ * lie inside the image gives NaN coefficients. d_flag (DEVICE, may be NULL): bit 0 is set if a wait
+ * for the tensor cores ran out (about two seconds; the affected tile is not written).
+ * Errors: INVALID_ARG for C not 1 or 3, H or W < 8, n < 0, a null pointer with n > 0, or a
+ * misaligned d_img or d_coef; UNSUPPORTED when H W C reaches 2^31. Asynchronous on stream. */
+htsvd_status htsvd_project_patches(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const int32_t* d_pos,
+                                   int64_t n, const double* d_basis, float* d_coef, int32_t* d_flag,
+                                   cudaStream_t stream);
+
 /* Vector-Jacobian product of htsvd_denoise_f32 at x with the grouping (d_idx), the
  * global bases, tau and the threshold masks held fixed (masks are recomputed at x).
  * d_w: per-group weights used by the forward (NULL = all ones); d_out: the forward's

@@ -57,6 +57,13 @@ int32_t htsvd_internal_filter_tile(int32_t H, int32_t W, int32_t C, const htsvd_
  * the arguments fail the checks of htsvd_denoise. Host only; launches nothing. */
 int64_t htsvd_internal_noalloc_bytes(int32_t H, int32_t W, int32_t C, const htsvd_params* p);
 
+/* DEVICE: the projection of htsvd_project_patches (same arguments, same output) in the structured
+ * per-slice form on the CUDA cores in FP32 (channel DFT, U_f^H X_f, (.) V_f, inverse channel DFT),
+ * the arithmetic of the group filter's projection stages; for comparison with the tensor-core form.
+ * Asynchronous on stream; errors as htsvd_project_patches. */
+htsvd_status htsvd_internal_project_simt(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const int32_t* d_pos,
+                                         int64_t n, const double* d_basis, float* d_coef, cudaStream_t stream);
+
 /* DEVICE probe of an arithmetic pipe's issue rate on the current device: 2 CTAs of 512 threads per
  * SM, each thread running 8 independent chains of one instruction for 32 * iters steps (op 0: FP32
  * fused multiply-add, 1: 32-bit integer multiply-add, 2: 4-way byte dot product with accumulate).

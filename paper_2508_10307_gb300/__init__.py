@@ -12,7 +12,7 @@ from dataclasses import dataclass, fields
 from . import _lib
 
 __all__ = ["HtsvdParams", "denoise", "denoise_f32", "estimate_sigma", "denoise_batch", "denoise_adaptive",
-           "denoise_video", "denoise_cube", "denoise_tau_sweep", "sure", "sure_weights", "tune_weights", "denoise_vjp",
+           "denoise_video", "denoise_cube", "denoise_tau_sweep", "sure", "sure_weights", "tune_weights", "denoise_vjp", "project_patches",
            "num_groups", "HtsvdFn", "load_library"]
 
 _MATCH = {"auto": 0, "gcp": 1, "full": 2, "green": 3}
@@ -422,6 +422,39 @@ def denoise_vjp(x, sigma, idx, w, out, grad_out, params=None, want_grad_w=True, 
                                _ptr(out), _ptr(grad_out), _ptr(gx), _ptr(gw), _stream_ptr(stream))
     _lib.check(st, "htsvd_denoise_vjp")
     return gx, gw
+
+
+def project_patches(img, pos, basis, *, out=None, flag=None, stream=None, structured=False):
+    """Coefficients S = U^T * P * V (64 C per patch, mask-bit order) of the 8 x 8 patches of a uint8
+    HWC image at linear top-left positions pos (int32), with the FP64 bases `basis` (the layout of
+    denoise(..., basis=True)). The tensor-core path by default; structured=True runs the per-slice
+    FP32 form on the CUDA cores (internal comparison hook)."""
+    lib = _lib.load()
+    torch = _torch()
+    img = _hwc(img)
+    if img.dtype != torch.uint8:
+        raise TypeError("project_patches expects a uint8 image")
+    H, W, C = img.shape
+    pos = _need(pos.contiguous().view(-1), "pos", (pos.numel(),), torch.int32, img)
+    basis = _need(basis.contiguous(), "basis", (2 * C * 64 * 2,) if basis.dim() == 1 else tuple(basis.shape),
+                  torch.float64, img)
+    if basis.numel() != 2 * C * 64 * 2:
+        raise ValueError(f"basis must hold {2 * C * 64 * 2} doubles")
+    n = pos.numel()
+    if out is None:
+        out = torch.empty((n, 64 * C), dtype=torch.float32, device=img.device)
+    out = _need(out, "out", (n, 64 * C), torch.float32, img)
+    if structured:
+        st = lib.htsvd_internal_project_simt(_ptr(img), H, W, C, _ptr(pos), n, _ptr(basis), _ptr(out),
+                                             _stream_ptr(stream))
+        _lib.check(st, "htsvd_internal_project_simt")
+    else:
+        if flag is not None:
+            flag = _need(flag, "flag", (1,), torch.int32, img)
+        st = lib.htsvd_project_patches(_ptr(img), H, W, C, _ptr(pos), n, _ptr(basis), _ptr(out), _ptr(flag),
+                                       _stream_ptr(stream))
+        _lib.check(st, "htsvd_project_patches")
+    return out
 
 
 def _make_fn():

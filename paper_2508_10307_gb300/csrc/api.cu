@@ -135,6 +135,7 @@ enum Slot {
     S_GAP,                           // eigen-gaps of the basis slices (strict mode)
     S_WIDX0, S_WIDX1, S_WB64, S_WB32, S_WZ, S_WF, S_WU, S_WGX, S_WG2, S_WRED,   // weight tuning by SURE
     S_CSCR, S_CNUM, S_CDEN,          // hyperspectral cubes: per-CTA Haar slots, numerator, denominator
+    S_PROJ,                          // split BF16 basis matrix of htsvd_project_patches
     S_NSLOT
 };
 
@@ -1208,6 +1209,39 @@ htsvd_status htsvd_denoise_cube(const uint8_t* d_cube, int32_t H, int32_t W, int
     a.weights_out = p ? p->d_weights_out : nullptr;
     a.coef_out = p ? p->d_coef_out : nullptr;
     { ProfScope ps_("cube_filter", s); CK(launch_cube_filter(a, grid, s)); }
+    return HTSVD_OK;
+}
+
+static htsvd_status check_projection(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const int32_t* d_pos,
+                                     int64_t n, const double* d_basis, const float* d_coef) {
+    if (C != 1 && C != 3) return HTSVD_ERR_INVALID_ARG;
+    if (H < PS || W < PS || n < 0) return HTSVD_ERR_INVALID_ARG;
+    if ((int64_t)H * W * C >= ((int64_t)1 << 31)) return HTSVD_ERR_UNSUPPORTED;
+    if (n == 0) return HTSVD_OK;
+    if (!d_img || !d_pos || !d_basis || !d_coef) return HTSVD_ERR_INVALID_ARG;
+    if (((uintptr_t)d_img & 3) || ((uintptr_t)d_coef & 15)) return HTSVD_ERR_INVALID_ARG;
+    return HTSVD_OK;
+}
+
+htsvd_status htsvd_project_patches(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const int32_t* d_pos,
+                                   int64_t n, const double* d_basis, float* d_coef, int32_t* d_flag, cudaStream_t s) {
+    ST(check_projection(d_img, H, W, C, d_pos, n, d_basis, d_coef));
+    if (n == 0) return HTSVD_OK;
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    void* pieces;
+    ST(ws_get(w, S_PROJ, project_pieces_bytes(C), &pieces));
+    { ProfScope ps_("project_split", s); CK(launch_project_split(d_basis, C, pieces, s)); }
+    { ProfScope ps_("project_tc", s);
+      CK(launch_project_tc(d_img, H, W, C, d_pos, n, pieces, d_coef, (int*)d_flag, s)); }
+    return HTSVD_OK;
+}
+
+htsvd_status htsvd_internal_project_simt(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const int32_t* d_pos,
+                                         int64_t n, const double* d_basis, float* d_coef, cudaStream_t s) {
+    ST(check_projection(d_img, H, W, C, d_pos, n, d_basis, d_coef));
+    if (n == 0) return HTSVD_OK;
+    { ProfScope ps_("project_simt", s); CK(launch_project_simt(d_img, H, W, C, d_pos, n, d_basis, d_coef, s)); }
     return HTSVD_OK;
 }
 

@@ -133,6 +133,18 @@ cudaError_t launch_sure_terms(const float* out, const float* x, const float* b, 
 // Adjoint helper: r = gout / den.
 cudaError_t launch_div(const float* gout, const float* den, int64_t npix, int C, float* r, cudaStream_t s);
 
+// ---- batched patch projection (project.cu): S = U^T * P * V per patch, 64 C coefficients in the
+// order n = (i * 8 + j) * C + c; positions are linear top-left indices y * W + x (outside: NaN).
+// Bytes of the split BF16 basis matrix (three pieces, both halves) that launch_project_split writes.
+size_t project_pieces_bytes(int C);
+cudaError_t launch_project_split(const double* d_b64, int C, void* d_pieces, cudaStream_t s);
+// Tensor cores (C in {1, 3}); flag (may be null) gets bit 0 set if a wait for the tensor cores ran out.
+cudaError_t launch_project_tc(const uint8_t* img, int H, int W, int C, const int32_t* pos, long long n,
+                              const void* d_pieces, float* coef, int* flag, cudaStream_t s);
+// Structured per-slice FP32 form on the CUDA cores.
+cudaError_t launch_project_simt(const uint8_t* img, int H, int W, int C, const int32_t* pos, long long n,
+                                const double* d_b64, float* coef, cudaStream_t s);
+
 // ---- hyperspectral cubes (cube.cu): Alg. 1 with C = N bands, one Haar slot of a group at a time
 struct CubeArgs {
     const uint8_t* img;      // H x W x N uint8
