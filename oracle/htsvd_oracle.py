@@ -86,6 +86,15 @@ Readings where the paper is silent or ambiguous:
      in R17 (eps > 0), and its gradient is exact through the weight part G_x of the adjoint (R14):
      dSURE/dw = G_y((2/n)(f_w(y) - y) - (2 sigma^2 / (n eps)) b) + G_z((2 sigma^2 / (n eps)) b).
      Tuning takes exponentiated-gradient steps w <- w exp(-step g / max|g|), which keep w > 0.
+  R20 MRI volumes (Sec. III-E, extension to other imaging: an MRI patch is a ps x ps x ps cube;
+     Sec. IV, MRI denoising: ps = 4, K = 32, W = 5): a (D, H, W) volume (slices z, rows y,
+     columns x) is Alg. 1 on cubes P[i][j][k] = v[z + k, y + i, x + j], i.e. a cube is a ps x ps x
+     c tensor whose tube (the t-SVD's Fourier mode) runs along z, c = ps; the reference grid is R3
+     per axis, the window W x W x W candidate positions clamped per axis (R4), the distance the
+     exact integer SSD over the ps^3 voxels, keys (SSD, (z H + y) W + x), slot 0 the reference
+     (R5); bases per tube-Fourier slice as R6/R7; tau = sigma sqrt(2 ln(ps^3 K)) (R9 with c = ps);
+     aggregation into the volume as R10. The paper's Rician noise goes through variance-
+     stabilising transforms, which are outside this core: sigma is the (stabilised) noise level.
 
 Parity pins for every function are in tests/test_oracle_pins.py.
 """
@@ -886,3 +895,113 @@ def tune_weights(x: np.ndarray, sigma: float, probe: np.ndarray, params=None, ep
         if gm > 0:
             w = w * np.exp(-step * g / gm)
     return w, np.array(trace)
+
+
+# --------------------------------------------------------------------------- MRI volumes (reading R20)
+
+def volume_reference_positions(shape, p: Params) -> np.ndarray:
+    """Linear positions (z H + y) W + x of the reference cubes, z-major over the grid of R3 per axis."""
+    D, Hh, Wd = shape
+    zs, ys, xs = (reference_positions(n, p.ps, p.stride) for n in (D, Hh, Wd))
+    return ((zs[:, None, None] * Hh + ys[None, :, None]) * Wd + xs[None, None, :]).ravel()
+
+
+def gather_cubes(v: np.ndarray, idx: np.ndarray, ps: int) -> np.ndarray:
+    """The cubes at linear positions idx as (..., ps, ps, ps) float64 tensors P[i][j][k] =
+    v[z + k, y + i, x + j] (rows along y, columns along x, the tube along z)."""
+    D, Hh, Wd = v.shape
+    views = sliding_window_view(v.astype(np.float64), (ps, ps, ps))      # [z, y, x, dz, dy, dx]
+    z, r = np.divmod(idx, Hh * Wd)
+    y, x = np.divmod(r, Wd)
+    return np.ascontiguousarray(np.moveaxis(views[z, y, x], -3, -1))
+
+
+def block_match_volume(v: np.ndarray, params=None) -> np.ndarray:
+    """Grouping of a (D, H, W) uint8 volume (reading R20): for every reference cube of the grid,
+    itself in slot 0, then the K - 1 other candidates of its W x W x W window with the smallest
+    (exact integer SSD over the ps^3 voxels, linear index) keys. Returns (N_ref, K) int64."""
+    p = Params.of(params)
+    D, Hh, Wd = v.shape
+    ps = p.ps
+    views = sliding_window_view(v.astype(np.int64), (ps, ps, ps))
+    zs, ys, xs = (reference_positions(n, ps, p.stride) for n in (D, Hh, Wd))
+    out = np.empty((len(zs) * len(ys) * len(xs), p.K), dtype=np.int64)
+    g = 0
+    for z in zs:
+        z0, nz = window_range(int(z), D, ps, p.window)
+        for y in ys:
+            y0, ny = window_range(int(y), Hh, ps, p.window)
+            for x in xs:
+                x0, nx = window_range(int(x), Wd, ps, p.window)
+                ref = views[z, y, x]
+                cand = views[z0:z0 + nz, y0:y0 + ny, x0:x0 + nx]
+                ssd = ((cand - ref) ** 2).sum(axis=(3, 4, 5)).ravel()
+                cz, cy, cx = np.meshgrid(np.arange(z0, z0 + nz), np.arange(y0, y0 + ny), np.arange(x0, x0 + nx),
+                                         indexing="ij")
+                lin = ((cz * Hh + cy) * Wd + cx).ravel()
+                me = (int(z) * Hh + int(y)) * Wd + int(x)
+                keep = lin != me
+                order = np.lexsort((lin[keep], ssd[keep]))
+                if order.size < p.K - 1:
+                    raise ValueError("the search window holds fewer than K cubes")
+                out[g, 0] = me
+                out[g, 1:] = lin[keep][order[:p.K - 1]]
+                g += 1
+    return out
+
+
+def aggregate_volume(shape, idx: np.ndarray, Ghat: np.ndarray, w: np.ndarray, ps: int):
+    """Weighted write-back of every estimated cube into the volume: num += w_g Ghat, den += w_g."""
+    D, Hh, Wd = shape
+    z, r = np.divmod(idx, Hh * Wd)
+    y, x = np.divmod(r, Wd)
+    ii, jj, kk = np.meshgrid(np.arange(ps), np.arange(ps), np.arange(ps), indexing="ij")
+    e = (slice(None), slice(None), None, None, None)
+    vox = ((z[e] + kk) * Hh + (y[e] + ii)) * Wd + (x[e] + jj)                  # (n, K, i, j, k)
+    we = w[:, None, None, None, None]
+    wg = np.broadcast_to(we, vox.shape)
+    num = np.bincount(vox.ravel(), weights=(Ghat * we).ravel(), minlength=D * Hh * Wd)
+    den = np.bincount(vox.ravel(), weights=wg.ravel(), minlength=D * Hh * Wd)
+    return num.reshape(D, Hh, Wd), den.reshape(D, Hh, Wd)
+
+
+def denoise_volume(v: np.ndarray, sigma: float, params=None, *, idx=None, keep_masks=False, tau=None,
+                   chunk=1024) -> Result:
+    """Alg. 1 on a (D, H, W) uint8 volume with ps x ps x ps cubes (reading R20): grouping, global
+    bases of the reference cubes per tube-Fourier slice, forward transform, hard threshold,
+    inverse, aggregation. idx fixes the grouping (as block_match_volume would return it)."""
+    p = Params.of(params)
+    D, Hh, Wd = v.shape
+    ps = p.ps
+    if idx is None:
+        idx = block_match_volume(v, p)
+    U, V, lu, lv = global_basis(gather_cubes(v, volume_reference_positions(v.shape, p), ps))
+    gap = global_basis_gap(lu, lv)
+    if p.strict_basis and not gap >= DEGENERATE_GAP:
+        raise DegenerateBasis(f"smallest relative eigen-gap {gap:.3g} < {DEGENERATE_GAP:g}")
+    Hk = haar_matrix(p.K)
+    if tau is None:
+        tau = tau_multiplier(p, ps) * float(sigma)
+    n = idx.shape[0]
+    w = np.ones(n)
+    num = np.zeros((D, Hh, Wd))
+    den = np.zeros((D, Hh, Wd))
+    masks = np.zeros((n, p.K, ps, ps, ps), dtype=bool) if keep_masks else None
+    amb = []
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        G = gather_cubes(v, idx[a:b], ps)
+        S = forward_transform(G, U, V, Hk)
+        m = hard_threshold_mask(S, tau)
+        near = np.nonzero(np.abs(np.abs(S.reshape(b - a, -1)) - tau) <= 1e-9 * max(tau, 1.0))
+        amb.extend(zip((near[0] + a).tolist(), near[1].tolist()))
+        if p.agg_mode == "sparsity":
+            w[a:b] = 1.0 / np.maximum(1, m.reshape(b - a, -1).sum(axis=1))
+        Ghat = inverse_transform(S * m, U, V, Hk)
+        nu, de = aggregate_volume(v.shape, idx[a:b], Ghat, w[a:b], ps)
+        num += nu
+        den += de
+        if keep_masks:
+            masks[a:b] = m
+    return Result(out=num / den, idx=idx, tau=tau, U=U, V=V, weights=w, masks=masks, den=den,
+                  ambiguous=np.array(amb, dtype=np.int64).reshape(-1, 2), extra={"basis_gap": gap})

@@ -77,6 +77,31 @@ def clean_cube(H: int, W: int, N: int, seed: int) -> np.ndarray:
     return np.clip(cube, 0, 255)
 
 
+def clean_volume(D: int, H: int, W: int, seed: int) -> np.ndarray:
+    """Clean float64 volume (D, H, W) in [0, 255] shaped like a T1-weighted head scan: zero background,
+    a soft head ellipsoid of intensity 90 holding 20 soft ellipsoids of amplitude U(-60, 80) (tissue
+    compartments), plus 3 plane waves of period 6-20 voxels and amplitude 5-15 inside the head."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    zz, yy, xx = np.mgrid[0:D, 0:H, 0:W].astype(np.float64)
+
+    def soft_ellipsoid(c, ax):
+        rho = np.sqrt(((zz - c[0]) / ax[0]) ** 2 + ((yy - c[1]) / ax[1]) ** 2 + ((xx - c[2]) / ax[2]) ** 2)
+        return 1.0 / (1.0 + np.exp(np.clip(8.0 * (rho - 1.0), -60, 60)))
+
+    head = soft_ellipsoid((D / 2, H / 2, W / 2), (0.45 * D, 0.45 * H, 0.45 * W))
+    vol = 90.0 * np.ones((D, H, W))
+    for _ in range(20):
+        c = (rng.uniform(0.2, 0.8) * D, rng.uniform(0.2, 0.8) * H, rng.uniform(0.2, 0.8) * W)
+        ax = (rng.uniform(0.05, 0.3) * D, rng.uniform(0.05, 0.3) * H, rng.uniform(0.05, 0.3) * W)
+        vol += rng.uniform(-60, 80) * soft_ellipsoid(c, ax)
+    for _ in range(3):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        vol += rng.uniform(5, 15) * np.sin(2 * np.pi * (d[0] * zz + d[1] * yy + d[2] * xx) / rng.uniform(6, 20)
+                                           + rng.uniform(0, 2 * np.pi))
+    return np.clip(vol * head, 0, 255)
+
+
 def quantize(x: np.ndarray) -> np.ndarray:
     return np.clip(np.rint(x), 0, 255).astype(np.uint8)
 

@@ -802,3 +802,136 @@ def test_weight_tuning_lowers_the_risk_estimate():
     wt, trace = O.tune_weights(y, 20.0, b, prm, eps=2.0, steps=3, step=0.3)
     assert np.all(np.diff(trace) < 0), trace
     assert np.all(wt > 0)
+
+
+# ----------------------------------------------------------------------------- MRI volumes (reading R20)
+
+def _volume(D, Hh, Wd, seed, sigma=11.0):
+    return synth.add_gaussian(synth.clean_volume(D, Hh, Wd, seed), sigma, seed)
+
+
+def test_volume_grouping_against_brute_force():
+    """Grouping of cubes: exact SSD over the ps^3 voxels of every candidate of the clamped W^3 window,
+    written out voxel by voxel in plain Python; a volume with repeated 2 x 2 x 2 tiles makes many
+    keys tie, which the lowest linear index must break."""
+    rng = np.random.default_rng(61)
+    tile = rng.integers(0, 256, size=(2, 2, 2))
+    v = np.tile(tile, (5, 6, 5)).astype(np.int64)
+    v[rng.random(v.shape) < 0.2] = 9
+    v = v.astype(np.uint8)[:9, :11, :10]
+    p = O.Params(ps=4, stride=2, window=3, K=6)
+    idx = O.block_match_volume(v, p)
+    D, Hh, Wd = v.shape
+    vv = v.astype(int).tolist()
+    n = 0
+    for rz in O.reference_positions(D, 4, 2):
+        for ry in O.reference_positions(Hh, 4, 2):
+            for rx in O.reference_positions(Wd, 4, 2):
+                rz, ry, rx = int(rz), int(ry), int(rx)
+                st = [min(max(r - 1, 0), n_ - 4 + 1 - 3) for r, n_ in ((rz, D), (ry, Hh), (rx, Wd))]
+                keys = []
+                for z in range(st[0], st[0] + 3):
+                    for y in range(st[1], st[1] + 3):
+                        for x in range(st[2], st[2] + 3):
+                            if (z, y, x) != (rz, ry, rx):
+                                d = sum((vv[rz + c][ry + a][rx + b] - vv[z + c][y + a][x + b]) ** 2
+                                        for a in range(4) for b in range(4) for c in range(4))
+                                keys.append((d, (z * Hh + y) * Wd + x))
+                keys.sort()
+                assert list(idx[n]) == [(rz * Hh + ry) * Wd + rx] + [k[1] for k in keys[:5]]
+                n += 1
+    assert n == idx.shape[0]
+
+
+def test_volume_cube_gather_and_aggregation_counts():
+    """A cube is v[z + k, y + i, x + j] at P[i][j][k]; the denominator counts, per voxel, the
+    cubes of all groups that cover it (brute force over the placements)."""
+    v = np.arange(7 * 8 * 9, dtype=np.int64).reshape(7, 8, 9) % 251
+    lin = np.array([(2 * 8 + 3) * 9 + 4])
+    P = O.gather_cubes(v.astype(np.uint8), lin, 4)[0]
+    for i in range(4):
+        for j in range(4):
+            for k in range(4):
+                assert P[i, j, k] == v[2 + k, 3 + i, 4 + j]
+    rng = np.random.default_rng(3)
+    idx = rng.integers(0, 4 * 5 * 6, size=(5, 4))
+    zz, r = np.divmod(idx, 5 * 6)
+    yy, xx = np.divmod(r, 6)
+    idx = (zz * 8 + yy) * 9 + xx                                   # top corners with room for the cube
+    w = rng.uniform(0.5, 2.0, 5)
+    _, den = O.aggregate_volume(v.shape, idx, np.zeros((5, 4, 4, 4, 4)), w, 4)
+    ref = np.zeros(v.shape)
+    for g in range(5):
+        for k in range(4):
+            z, rr = divmod(int(idx[g, k]), 8 * 9)
+            y, x = divmod(rr, 9)
+            ref[z:z + 4, y:y + 4, x:x + 4] += w[g]
+    assert np.abs(den - ref).max() <= 1e-12
+
+
+def test_volume_bases_are_unitary_with_conjugate_tube_slices():
+    """Cube bases per tube-Fourier slice (R6 with c = ps = 4): unitary, slice 2 (the Nyquist slice)
+    real, slice 3 the conjugate of slice 1, and the t-product U^T * U is the identity tensor."""
+    v = _volume(14, 16, 15, 5)
+    p = O.Params(ps=4, stride=2, window=5, K=8)
+    U, V, _, _ = O.global_basis(O.gather_cubes(v, O.volume_reference_positions(v.shape, p), 4))
+    for B in (U, V):
+        for f in range(4):
+            np.testing.assert_allclose(B[f].conj().T @ B[f], np.eye(4), atol=1e-12)
+        assert np.abs(B[0].imag).max() <= 1e-12 and np.abs(B[2].imag).max() <= 1e-12
+        np.testing.assert_allclose(B[3], B[1].conj(), atol=0)
+        Ut = np.fft.ifft(B, axis=0).real.transpose(1, 2, 0)          # spatial-domain tensor (4, 4, 4)
+        I = O.t_product_bcirc(O.t_transpose(Ut), Ut)
+        E = np.zeros((4, 4, 4))
+        E[:, :, 0] = np.eye(4)
+        np.testing.assert_allclose(I, E, atol=1e-12)
+
+
+def test_volume_zero_and_infinite_threshold():
+    v = _volume(12, 13, 14, 7)
+    prm = dict(ps=4, stride=2, window=5, K=8)
+    assert np.abs(O.denoise_volume(v, 10.0, prm, tau=0.0).out - v).max() <= 1e-9
+    assert np.abs(O.denoise_volume(v, 10.0, prm, tau=1e9).out).max() == 0.0
+
+
+def test_volume_denoiser_commutes_with_transposing_rows_and_columns():
+    """Swapping y and x transposes every cube slice: the row and column scatter matrices trade places
+    (U_f of the transposed volume is conj(V_f), V_f is conj(U_f)), so every coefficient moves to the
+    transposed position and the output is the transposed output. The grouping is held fixed (the
+    transposed indices) so that ties of the integer SSD cannot reorder a group."""
+    v = _volume(12, 14, 14, 9)
+    prm = dict(ps=4, stride=2, window=5, K=8, tau_mult=2.2)
+    r = O.denoise_volume(v, 11.0, prm)
+    D, Hh, Wd = v.shape
+    z, rr = np.divmod(r.idx, Hh * Wd)
+    y, x = np.divmod(rr, Wd)
+    idx_t = (z * Wd + x) * Hh + y
+    # the transposed grid lists the same references in (z, x, y) order: reorder the groups to match
+    ng = len(O.reference_positions(Hh, 4, 2))
+    order = np.arange(r.idx.shape[0]).reshape(-1, ng, ng).transpose(0, 2, 1).ravel()
+    t = O.denoise_volume(np.ascontiguousarray(v.transpose(0, 2, 1)), 11.0, prm, idx=idx_t[order])
+    assert np.abs(t.out - r.out.transpose(0, 2, 1)).max() <= 1e-9
+
+
+def test_volume_denoiser_commutes_with_reversing_the_tube_axis():
+    """Reversing z reverses every cube's tube: each tube-Fourier slice becomes a phase times its
+    conjugate, so the scatter matrices and bases are conjugated and the coefficients reverse along
+    the tube; thresholds keep the same set and the output is the reversed output (grid symmetric:
+    (D - ps) divisible by the stride; grouping held fixed as above)."""
+    v = _volume(14, 12, 13, 11)
+    prm = dict(ps=4, stride=2, window=5, K=8, tau_mult=2.2)
+    r = O.denoise_volume(v, 11.0, prm)
+    D, Hh, Wd = v.shape
+    z, rr = np.divmod(r.idx, Hh * Wd)
+    idx_f = (D - 4 - z) * Hh * Wd + rr
+    nz = len(O.reference_positions(D, 4, 2))
+    order = np.arange(r.idx.shape[0]).reshape(nz, -1)[::-1].ravel()
+    f = O.denoise_volume(np.ascontiguousarray(v[::-1]), 11.0, prm, idx=idx_f[order])
+    assert np.abs(f.out - r.out[::-1]).max() <= 1e-9
+
+
+def test_volume_default_threshold_counts_the_cube_voxels():
+    """tau = sigma sqrt(2 ln(c K ps^2)) with the tube length c = ps: sqrt(2 ln(ps^3 K))."""
+    v = _volume(10, 10, 10, 13)
+    r = O.denoise_volume(v, 10.0, dict(ps=4, stride=2, window=5, K=32))
+    assert abs(r.tau - 10.0 * math.sqrt(2 * math.log(4 ** 3 * 32))) <= 1e-12
