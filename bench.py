@@ -57,6 +57,14 @@ FILTER_DRAM_BYTES = {"rgb1080": 37.154816e6 + 304.592384e6,
                      "rgb4k": (37.154816e6 + 304.592384e6) * 919601 / 229401}
 
 
+def volume_flops_per_group(K: int) -> int:
+    """Algorithmic FP32 flops of one group of 4 x 4 x 4 cubes: per cube and direction the per-slice
+    projections (slices 0 and 2 real, 2 x 64 MACs each; slice 1 complex, 2 x 64 complex MACs: 1,536
+    flop) and the tube DFTs (384 flop), the Haar butterflies (4 flop, K - 1 per fibre and direction,
+    64 fibres) and one compare per coefficient. K = 32: 140,800."""
+    return K * 2 * (1536 + 384) + 2 * 4 * (K - 1) * 64 + K * 64
+
+
 def measured_peak(key: str):
     """A peak from the measured MEASURED_PEAKS.json beside this file, or None."""
     try:
@@ -404,6 +412,22 @@ def make_workload(name):
 
         return Workload(name, cfg, 8 * 512 * 512 / 1e6, 8 * n, 3, 32, xs, step, 8 * 512 * 512 * 3 * 4,
                         forward_only, "forward_only"), None
+    if name == "mri176":
+        # an MRI-sized volume (the OASIS T1-weighted grid, 176 x 208 x 176) at the paper's MRI setting
+        clean = synth.clean_volume(176, 208, 176, 3)
+        noisy = synth.add_gaussian(clean, 11.5, 3)
+        prm = dict(ps=4, stride=2, window=5, K=32)
+        n = 87 * 103 * 87
+        cfg = {"workload": "mri_volume_176x208x176", "volume": "176x208x176 uint8 (head-like phantom)",
+               "noise": "gaussian sigma=11.5 (4.5% of 255; stands in for VST-stabilised Rician noise)",
+               "sigma": "given", "ps": "4x4x4", "stride": 2, "window": "5x5x5", "K": 32,
+               "unit_note": "MP/s counts voxels (D H W) as pixels"}
+
+        def step(d):
+            return [H.denoise_volume(x, 11.5, prm) for x in d]
+
+        return Workload(name, cfg, 176 * 208 * 176 / 1e6, n, 4, 32, [noisy], step, 176 * 208 * 176 * 4), \
+            synth.quantize(clean)
     if name == "proj512":
         # the batched basis projection of every patch of every group of the 512x512x3 workload (64,009
         # groups x 32 members), on the tensor cores; compared with the structured FP32 form on the CUDA cores
@@ -696,6 +720,14 @@ def run_gpu(args):
                 "traffic": None, "kernel": "cube_filter",
                 "peak_basis": f"FP32 FMA: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {MAX_SM_MHZ:.0f} MHz; "
                               "achieved counts the forward transforms only"}
+    elif dom == "volume_filter":
+        n_launch, ms = prof["volume_filter"]
+        flops = wl.groups_per_step * volume_flops_per_group(wl.K) * args.steps / n_launch
+        achieved = flops / (ms / n_launch / 1000.0) / 1e12
+        peak = nsm * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "volume_filter",
+                "peak_basis": f"FP32 FMA: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {MAX_SM_MHZ:.0f} MHz"}
     elif dom == "project_tc":
         # the dense contraction as the algorithm of this kernel: 2 (64 C)^2 flop per patch (three BF16
         # products of it execute); peak: the measured BF16 dense rate
@@ -749,7 +781,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rgb4k", choices=["rgb512", "gray128", "rgb4k", "rgb1080", "hsi696", "batch64", "vjp8", "adaptive512",
-                                                      "video1080", "sweep512", "sure512", "tunew512", "proj512"])
+                                                      "video1080", "sweep512", "sure512", "tunew512", "proj512", "mri176"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -249,6 +249,29 @@ htsvd_status htsvd_denoise_batch(const htsvd_image* h_imgs, int32_t n, const hts
 htsvd_status htsvd_denoise_cube(const uint8_t* d_cube, int32_t H, int32_t W, int32_t N, double sigma,
                                 const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t stream);
 
+/* Alg. 1 on an MRI volume (Sec. III-E, extension to other imaging: an MRI patch is a ps x ps x ps
+ * cube; Sec. IV, MRI denoising with ps 4, K 32, W 5). d_vol: D x H x W uint8 (slices z, rows y,
+ * columns x; DEVICE, 4-byte aligned). A cube P[i][j][k] = v[z + k][y + i][x + j] is a 4 x 4 x 4 tensor
+ * whose tube (the t-SVD's Fourier mode, 4 slices) runs along z; the reference grid is {0, s, 2s, ...}
+ * U {n - 4} per axis, the search window W x W x W candidate cubes clamped per axis, the distance the
+ * exact integer SSD over the 64 voxels with ties broken by the lowest linear index (z H + y) W + x,
+ * the reference itself in slot 0; tau = tau_mult * sigma, tau_mult <= 0 meaning sqrt(2 ln(4^3 K)).
+ * sigma: the noise level (>= 0; for Rician MRI data, the level after a variance-stabilising
+ * transform, which is the caller's). Parameters: ps 0 or 4 (others UNSUPPORTED), stride 0 -> 2,
+ * window 0 -> 5 (at most 8), K 0 -> 32 (a power of two, at most 32); match_mode AUTO or FULL.
+ * d_out: D x H x W float32 (DEVICE). d_idx_out (DEVICE, may be NULL): N_groups x K int32 linear
+ * indices, groups z-major over the grid. Optional outputs of p are honoured (d_mask_out: 2 K words
+ * per group, bit m 64 + (i 4 + j) 4 + k for Haar row m; d_weights_out; d_basis_out: 2 x 4 x 16
+ * complex values, U slices then V slices, each [a][i]; h_sigma_out; strict_basis and
+ * h_basis_gap_out as in htsvd_denoise). The bases are solved on the host (one synchronisation on
+ * an event, overlapped with the grouping). The aggregation adds with float atomics, so repeated
+ * calls agree to rounding rather than bit for bit.
+ * Errors: INVALID_ARG for a null or misaligned pointer, a negative or non-finite sigma, D, H or W
+ * below 4, K not a power of two in [2, 32], window outside [1, 8], a window with fewer than K
+ * cubes, or another match or aggregation mode; UNSUPPORTED for ps other than 4 or D H W >= 2^31. */
+htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, int32_t W, double sigma,
+                                  const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t stream);
+
 /* Batched forward projection of patches onto the global t-SVD bases (Sec. III-B.2, Eq. (forward
  * transform) before the Haar transform along the group mode; Sec. II-C, Def. T-product): for each
  * of n patches, S = U^T * P * V of the ps x ps x C uint8 patch P whose top-left corner is d_pos[t]

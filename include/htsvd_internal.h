@@ -64,6 +64,13 @@ int64_t htsvd_internal_noalloc_bytes(int32_t H, int32_t W, int32_t C, const htsv
 htsvd_status htsvd_internal_project_simt(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const int32_t* d_pos,
                                          int64_t n, const double* d_basis, float* d_coef, cudaStream_t stream);
 
+/* HOST: the global bases of htsvd_denoise_volume from its integer cube moments mom (HOST, 512 uint64:
+ * rows R[a][a'][c][c'] = sum over reference cubes and columns b of P[a][b][c] P[a'][b][c'], then
+ * columns Q[b][b'][c][c'] = sum over reference cubes and rows a of P[a][b][c] P[a][b'][c'], each
+ * [4][4][4][4] row-major; P[a][b][c] = v[z + c][y + a][x + b]). b64 (HOST) receives 256 doubles in the
+ * layout of htsvd_params.d_basis_out. Returns the smallest relative eigen-gap of the slices 0..2. */
+double htsvd_internal_volume_bases(const unsigned long long* mom, double* b64);
+
 /* DEVICE probe of an arithmetic pipe's issue rate on the current device: 2 CTAs of 512 threads per
  * SM, each thread running 8 independent chains of one instruction for 32 * iters steps (op 0: FP32
  * fused multiply-add, 1: 32-bit integer multiply-add, 2: 4-way byte dot product with accumulate).

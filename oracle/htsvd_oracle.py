@@ -916,37 +916,39 @@ def gather_cubes(v: np.ndarray, idx: np.ndarray, ps: int) -> np.ndarray:
     return np.ascontiguousarray(np.moveaxis(views[z, y, x], -3, -1))
 
 
-def block_match_volume(v: np.ndarray, params=None) -> np.ndarray:
+def block_match_volume(v: np.ndarray, params=None, only=None) -> np.ndarray:
     """Grouping of a (D, H, W) uint8 volume (reading R20): for every reference cube of the grid,
     itself in slot 0, then the K - 1 other candidates of its W x W x W window with the smallest
-    (exact integer SSD over the ps^3 voxels, linear index) keys. Returns (N_ref, K) int64."""
+    (exact integer SSD over the ps^3 voxels, linear index) keys. Returns (N_ref, K) int64; with
+    `only` (group numbers, z-major over the grid) just those groups, in that order."""
     p = Params.of(params)
     D, Hh, Wd = v.shape
     ps = p.ps
     views = sliding_window_view(v.astype(np.int64), (ps, ps, ps))
     zs, ys, xs = (reference_positions(n, ps, p.stride) for n in (D, Hh, Wd))
-    out = np.empty((len(zs) * len(ys) * len(xs), p.K), dtype=np.int64)
-    g = 0
-    for z in zs:
-        z0, nz = window_range(int(z), D, ps, p.window)
-        for y in ys:
-            y0, ny = window_range(int(y), Hh, ps, p.window)
-            for x in xs:
-                x0, nx = window_range(int(x), Wd, ps, p.window)
-                ref = views[z, y, x]
-                cand = views[z0:z0 + nz, y0:y0 + ny, x0:x0 + nx]
-                ssd = ((cand - ref) ** 2).sum(axis=(3, 4, 5)).ravel()
-                cz, cy, cx = np.meshgrid(np.arange(z0, z0 + nz), np.arange(y0, y0 + ny), np.arange(x0, x0 + nx),
-                                         indexing="ij")
-                lin = ((cz * Hh + cy) * Wd + cx).ravel()
-                me = (int(z) * Hh + int(y)) * Wd + int(x)
-                keep = lin != me
-                order = np.lexsort((lin[keep], ssd[keep]))
-                if order.size < p.K - 1:
-                    raise ValueError("the search window holds fewer than K cubes")
-                out[g, 0] = me
-                out[g, 1:] = lin[keep][order[:p.K - 1]]
-                g += 1
+    if only is None:
+        only = np.arange(len(zs) * len(ys) * len(xs))
+    out = np.empty((len(only), p.K), dtype=np.int64)
+    for g, gi in enumerate(np.asarray(only, dtype=np.int64)):
+        iz, r = divmod(int(gi), len(ys) * len(xs))
+        iy, ix = divmod(r, len(xs))
+        z, y, x = int(zs[iz]), int(ys[iy]), int(xs[ix])
+        z0, nz = window_range(z, D, ps, p.window)
+        y0, ny = window_range(y, Hh, ps, p.window)
+        x0, nx = window_range(x, Wd, ps, p.window)
+        ref = views[z, y, x]
+        cand = views[z0:z0 + nz, y0:y0 + ny, x0:x0 + nx]
+        ssd = ((cand - ref) ** 2).sum(axis=(3, 4, 5)).ravel()
+        cz, cy, cx = np.meshgrid(np.arange(z0, z0 + nz), np.arange(y0, y0 + ny), np.arange(x0, x0 + nx),
+                                 indexing="ij")
+        lin = ((cz * Hh + cy) * Wd + cx).ravel()
+        me = (z * Hh + y) * Wd + x
+        keep = lin != me
+        order = np.lexsort((lin[keep], ssd[keep]))
+        if order.size < p.K - 1:
+            raise ValueError("the search window holds fewer than K cubes")
+        out[g, 0] = me
+        out[g, 1:] = lin[keep][order[:p.K - 1]]
     return out
 
 

@@ -12,7 +12,7 @@ from dataclasses import dataclass, fields
 from . import _lib
 
 __all__ = ["HtsvdParams", "denoise", "denoise_f32", "estimate_sigma", "denoise_batch", "denoise_adaptive",
-           "denoise_video", "denoise_cube", "denoise_tau_sweep", "sure", "sure_weights", "tune_weights", "denoise_vjp", "project_patches",
+           "denoise_video", "denoise_cube", "denoise_tau_sweep", "sure", "sure_weights", "tune_weights", "denoise_vjp", "project_patches", "denoise_volume",
            "num_groups", "HtsvdFn", "load_library"]
 
 _MATCH = {"auto": 0, "gcp": 1, "full": 2, "green": 3}
@@ -281,6 +281,48 @@ def denoise_cube(cube, sigma, params=None, *, return_info=False, masks=False, we
     _lib.check(st, "htsvd_denoise_cube")
     if return_info:
         info.update(idx=idx)
+        return out, info
+    return out
+
+
+VOLUME_DEFAULTS = dict(ps=4, stride=2, window=5, K=32)
+
+
+def denoise_volume(vol, sigma, params=None, *, return_info=False, masks=False, weights=False, basis=False,
+                   stream=None):
+    """Alg. 1 on a uint8 (D, H, W) CUDA volume with 4 x 4 x 4 cubes (the t-SVD tube along z) at the
+    given sigma; params default to the paper's MRI setting (ps 4, K 32, window 5; stride 2).
+    Returns the float32 (D, H, W) estimate, or (estimate, info)."""
+    lib = _lib.load()
+    torch = _torch()
+    if vol.dim() != 3 or not vol.is_cuda or not vol.is_contiguous() or vol.dtype != torch.uint8:
+        raise ValueError("denoise_volume expects a contiguous uint8 CUDA tensor (D, H, W)")
+    if params is None or isinstance(params, dict):
+        params = dict(VOLUME_DEFAULTS, **(params or {}))
+    p = HtsvdParams.of(params)
+    cp = p.c()
+    D, H, W = vol.shape
+    nz, ny, nx = (len(range(0, n - p.ps + 1, p.stride)) + (1 if (n - p.ps) % p.stride else 0) for n in (D, H, W))
+    n = nz * ny * nx
+    out = torch.empty((D, H, W), dtype=torch.float32, device=vol.device)
+    idx = torch.empty((n, p.K), dtype=torch.int32, device=vol.device)
+    info = {}
+    if masks:
+        info["masks"] = torch.empty((n, 2 * p.K), dtype=torch.int32, device=vol.device)
+        cp.d_mask_out = info["masks"].data_ptr()
+    if weights:
+        info["weights"] = torch.empty(n, dtype=torch.float32, device=vol.device)
+        cp.d_weights_out = info["weights"].data_ptr()
+    if basis:
+        info["basis"] = torch.empty((2, 4, 4, 4, 2), dtype=torch.float64, device=vol.device)
+        cp.d_basis_out = info["basis"].data_ptr()
+    gap = ctypes.c_double(0.0)
+    cp.h_basis_gap_out = ctypes.pointer(gap)
+    st = lib.htsvd_denoise_volume(_ptr(vol), D, H, W, float(sigma), ctypes.byref(cp), _ptr(out), _ptr(idx),
+                                  _stream_ptr(stream))
+    _lib.check(st, "htsvd_denoise_volume")
+    if return_info:
+        info.update(idx=idx, basis_gap=gap.value)
         return out, info
     return out
 

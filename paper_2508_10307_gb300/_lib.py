@@ -15,7 +15,7 @@ EXPORTED = ["htsvd_denoise", "htsvd_denoise_f32", "htsvd_estimate_sigma", "htsvd
             "htsvd_denoise_vjp", "htsvd_num_groups", "htsvd_status_string", "htsvd_release_workspace",
             "htsvd_profile_enable", "htsvd_profile_collect", "htsvd_denoise_noalloc", "htsvd_denoise_adaptive",
             "htsvd_denoise_video", "htsvd_denoise_tau_sweep", "htsvd_sure", "htsvd_denoise_cube",
-            "htsvd_sure_weights", "htsvd_tune_weights", "htsvd_project_patches"]
+            "htsvd_sure_weights", "htsvd_tune_weights", "htsvd_project_patches", "htsvd_denoise_volume"]
 
 
 class CParams(ctypes.Structure):
@@ -92,8 +92,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.htsvd_sure_weights.argtypes = [vp, i32, i32, i32, dbl, vp, vp, dbl, P, ctypes.POINTER(ctypes.c_double), vp, vp]
     lib.htsvd_tune_weights.argtypes = [vp, i32, i32, i32, dbl, vp, dbl, i32, dbl, P, vp,
                                        ctypes.POINTER(ctypes.c_double), vp]
+    lib.htsvd_denoise_volume.argtypes = [vp, i32, i32, i32, dbl, P, vp, vp, vp]
     lib.htsvd_project_patches.argtypes = [vp, i32, i32, i32, vp, ctypes.c_int64, vp, vp, vp, vp]
     lib.htsvd_internal_project_simt.argtypes = [vp, i32, i32, i32, vp, ctypes.c_int64, vp, vp, vp]
+    lib.htsvd_internal_volume_bases.argtypes = [vp, vp]
+    lib.htsvd_internal_volume_bases.restype = ctypes.c_double
     lib.htsvd_internal_alu_probe.argtypes = [i32, i32]
     lib.htsvd_internal_alu_probe.restype = ctypes.c_double
     lib.htsvd_internal_filter_tile.argtypes = [i32, i32, i32, P]
@@ -114,7 +117,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                  "htsvd_denoise_vjp", "htsvd_release_workspace", "htsvd_denoise_noalloc", "htsvd_denoise_adaptive",
                  "htsvd_denoise_video", "htsvd_denoise_tau_sweep", "htsvd_sure", "htsvd_denoise_cube",
                  "htsvd_sure_weights", "htsvd_tune_weights", "htsvd_project_patches",
-                 "htsvd_internal_project_simt"]:
+                 "htsvd_internal_project_simt", "htsvd_denoise_volume"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

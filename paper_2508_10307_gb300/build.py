@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libhtsvd.so")
 OBJ_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["api.cu", "bm.cu", "moments.cu", "filter.cu", "batch.cu", "noalloc.cu", "probe.cu", "cube.cu", "project.cu", "eig_host.cpp"]
+SOURCES = ["api.cu", "bm.cu", "moments.cu", "filter.cu", "batch.cu", "noalloc.cu", "probe.cu", "cube.cu", "project.cu", "volume.cu", "eig_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -136,6 +136,7 @@ enum Slot {
     S_WIDX0, S_WIDX1, S_WB64, S_WB32, S_WZ, S_WF, S_WU, S_WGX, S_WG2, S_WRED,   // weight tuning by SURE
     S_CSCR, S_CNUM, S_CDEN,          // hyperspectral cubes: per-CTA Haar slots, numerator, denominator
     S_PROJ,                          // split BF16 basis matrix of htsvd_project_patches
+    S_VMOM, S_VB64, S_VNUM, S_VDEN,  // MRI volumes: moments, bases, numerator, denominator
     S_NSLOT
 };
 
@@ -1209,6 +1210,80 @@ htsvd_status htsvd_denoise_cube(const uint8_t* d_cube, int32_t H, int32_t W, int
     a.weights_out = p ? p->d_weights_out : nullptr;
     a.coef_out = p ? p->d_coef_out : nullptr;
     { ProfScope ps_("cube_filter", s); CK(launch_cube_filter(a, grid, s)); }
+    return HTSVD_OK;
+}
+
+htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, int32_t W, double sigma,
+                                  const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t s) {
+    if (!d_vol || !d_out || !(sigma >= 0) || std::isinf(sigma)) return HTSVD_ERR_INVALID_ARG;
+    if ((uintptr_t)d_vol & 3) return HTSVD_ERR_INVALID_ARG;
+    htsvd_params z;
+    std::memset(&z, 0, sizeof(z));
+    const htsvd_params& q = p ? *p : z;
+    const int ps = q.ps > 0 ? q.ps : 4, stride = q.stride > 0 ? q.stride : 2;
+    const int win = q.window > 0 ? q.window : 5, K = q.K > 0 ? q.K : 32;
+    if (ps != 4) return HTSVD_ERR_UNSUPPORTED;
+    if (K < 2 || K > 32 || (K & (K - 1)) != 0 || win < 1 || win > volume_max_window()) return HTSVD_ERR_INVALID_ARG;
+    if (q.match_mode != HTSVD_MATCH_AUTO && q.match_mode != HTSVD_MATCH_FULL) return HTSVD_ERR_INVALID_ARG;
+    if (q.agg_mode != HTSVD_AGG_UNIFORM && q.agg_mode != HTSVD_AGG_SPARSITY) return HTSVD_ERR_INVALID_ARG;
+    if (D < ps || H < ps || W < ps) return HTSVD_ERR_INVALID_ARG;
+    if ((int64_t)D * H * W >= ((int64_t)1 << 31)) return HTSVD_ERR_UNSUPPORTED;
+    const VolGeo g = make_vol_geo(D, H, W, stride, win, K);
+    if ((int64_t)g.wnz * g.wny * g.wnx < K) return HTSVD_ERR_INVALID_ARG;
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    const int64_t ng = (int64_t)g.nrz * g.nry * g.nrx;
+    const int64_t nvox = (int64_t)D * H * W;
+    int32_t* idx = d_idx_out;
+    if (!idx) {
+        void* ib;
+        ST(ws_get(w, S_IDX, sizeof(int32_t) * ng * K, &ib));
+        idx = (int32_t*)ib;
+    }
+    void *mom, *b64, *num, *den, *hbuf;
+    ST(ws_get(w, S_VMOM, sizeof(unsigned long long) * 512, &mom));
+    ST(ws_get(w, S_VB64, sizeof(double) * 256, &b64));
+    ST(ws_get(w, S_VNUM, sizeof(float) * nvox, &num));
+    ST(ws_get(w, S_VDEN, sizeof(float) * nvox, &den));
+    ST(ws_host(w, sizeof(unsigned long long) * 512 + sizeof(double) * 256, &hbuf));
+    ST(ws_side(w));
+    unsigned long long* hmom = (unsigned long long*)hbuf;
+    double* hb64 = (double*)(hmom + 512);
+    // moments first, their copy to the host, then the grouping runs while the host solves the bases
+    { ProfScope ps_("volume_moments", s); CK(launch_volume_moments(d_vol, g, (unsigned long long*)mom, s)); }
+    CK(cudaMemcpyAsync(hmom, mom, sizeof(unsigned long long) * 512, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(w->ev_join, s));
+    { ProfScope ps_("block_match_volume", s); CK(launch_block_match_volume(d_vol, g, idx, s)); }
+    CK(cudaEventSynchronize(w->ev_join));
+    double gap;
+    { HostProfScope hp_("volume_bases_host"); gap = volume_bases_host(hmom, hb64); }
+    if (p && p->h_basis_gap_out) *p->h_basis_gap_out = gap;
+    if (q.strict_basis && !(gap >= kDegenerateGap)) return HTSVD_ERR_DEGENERATE_BASIS;
+    CK(cudaMemcpyAsync(b64, hb64, sizeof(double) * 256, cudaMemcpyHostToDevice, s));
+    if (p && p->d_basis_out)
+        CK(cudaMemcpyAsync(p->d_basis_out, b64, sizeof(double) * 256, cudaMemcpyDeviceToDevice, s));
+    if (p && p->h_sigma_out) *p->h_sigma_out = sigma;
+    const double tau_mult = q.tau_mult > 0 ? q.tau_mult : std::sqrt(2.0 * std::log((double)ps * K * ps * ps));
+    const double tau = tau_mult * sigma;
+    VolFilterArgs a{};
+    a.vol = d_vol;
+    a.g = g;
+    a.idx = idx;
+    a.basis64 = (const double*)b64;
+    a.tau32 = (float)tau;
+    a.tau64 = tau;
+    a.band_rel = kBandRel;
+    a.band_abs = (float)(tau * kBandTau) + 1e-6f;
+    a.w_in = nullptr;
+    a.agg_mode = q.agg_mode;
+    a.num = (float*)num;
+    a.den = (float*)den;
+    a.mask_out = p ? p->d_mask_out : nullptr;
+    a.weights_out = p ? p->d_weights_out : nullptr;
+    CK(cudaMemsetAsync(num, 0, sizeof(float) * nvox, s));
+    CK(cudaMemsetAsync(den, 0, sizeof(float) * nvox, s));
+    { ProfScope ps_("volume_filter", s); CK(launch_volume_filter(a, s)); }
+    { ProfScope ps_("volume_finalize", s); CK(launch_volume_finalize((const float*)num, (const float*)den, nvox, d_out, s)); }
     return HTSVD_OK;
 }
 

@@ -145,6 +145,42 @@ cudaError_t launch_project_tc(const uint8_t* img, int H, int W, int C, const int
 cudaError_t launch_project_simt(const uint8_t* img, int H, int W, int C, const int32_t* pos, long long n,
                                 const double* d_b64, float* coef, cudaStream_t s);
 
+// ---- MRI volumes (volume.cu): Alg. 1 on 4 x 4 x 4 cubes of a D x H x W uint8 volume, the t-SVD
+// tube along z (cube P[i][j][k] = v[z + k][y + i][x + j]); linear indices (z H + y) W + x.
+struct VolGeo {
+    int D, H, W;
+    int s, win, K;
+    int nrz, nry, nrx;       // references per axis
+    int npz, npy, npx;       // candidate positions per axis
+    int wnz, wny, wnx;       // window extent per axis
+};
+VolGeo make_vol_geo(int D, int H, int W, int s, int win, int K);
+int volume_max_window();
+cudaError_t launch_block_match_volume(const uint8_t* vol, const VolGeo& g, int32_t* idx, cudaStream_t s);
+// uint64 [2][4][4][4][4]: rows R[a][a'][c][c'] then columns Q[b][b'][c][c'] of the reference cubes.
+cudaError_t launch_volume_moments(const uint8_t* vol, const VolGeo& g, unsigned long long* d_mom, cudaStream_t s);
+// HOST: canonical bases from the moments: b64 [2 (U, V)][4 slices][4][4] complex (re, im), slice 3 the
+// conjugate of slice 1; returns the smallest relative eigen-gap over the slices 0..2 of U and V.
+double volume_bases_host(const unsigned long long* mom, double* b64);
+struct VolFilterArgs {
+    const uint8_t* vol;
+    VolGeo g;
+    const int32_t* idx;      // [N][K]
+    const double* basis64;   // device copy of the host bases
+    float tau32;
+    double tau64;
+    float band_rel, band_abs;
+    const float* w_in;       // optional per-group weights
+    int agg_mode;
+    float* num;              // D H W, zeroed by the caller
+    float* den;
+    uint32_t* mask_out;      // optional, 2 K words per group (bit m * 64 + (i * 4 + j) * 4 + k)
+    float* weights_out;      // optional
+};
+size_t volume_filter_smem_bytes(const VolGeo& g);
+cudaError_t launch_volume_filter(const VolFilterArgs& a, cudaStream_t s);
+cudaError_t launch_volume_finalize(const float* num, const float* den, long long n, float* out, cudaStream_t s);
+
 // ---- hyperspectral cubes (cube.cu): Alg. 1 with C = N bands, one Haar slot of a group at a time
 struct CubeArgs {
     const uint8_t* img;      // H x W x N uint8

@@ -29,7 +29,8 @@
 namespace htsvd {
 namespace {
 
-constexpr int kProjThreads = 256;
+constexpr int kProjThreads = 256;           // structured FP32 kernel
+constexpr int kTcThreads = 512;             // tensor-core kernel: 16 warps gather, one thread issues the MMAs
 constexpr int kTileM = 128;                 // patches per MMA tile (TMEM lanes)
 
 template <int C>
@@ -38,9 +39,11 @@ struct ProjDims {
     static constexpr int NH = D / 2;                      // coefficients per CTA (one half)
     static constexpr int KCH = D / 8;                     // 8-element K chunks (core-matrix columns)
     static constexpr int KSTEPS = D / 16;                 // MMAs per piece (K = 16 each)
-    static constexpr int LBO_A = kTileM * 16;             // bytes between K-adjacent core matrices of A
+    // bytes between K-adjacent core matrices of A: a plane of 128 rows of 16 bytes plus 64 bytes, so that
+    // the gather's stores into the three planes of a patch row fall in two halves of the banks
+    static constexpr int LBO_A = kTileM * 16 + 64;
     static constexpr int LBO_B = NH * 16;                 // ... of B
-    static constexpr int A_BYTES = kTileM * D * 2;
+    static constexpr int A_BYTES = KCH * LBO_A;
     static constexpr int B_PIECE = NH * D * 2;
     static constexpr int ACC_COLS = C == 3 ? 128 : 32;   // TMEM column stride of the two accumulators
     static constexpr int TMEM_COLS = 2 * ACC_COLS;       // power of two >= 32
@@ -115,19 +118,17 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes 32 (w % 4) ..),
-// waited for inside the same statement so no use of the registers can precede the wait.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 8 consecutive FP32 columns of this thread's TMEM lane, waited for in the same statement.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
         : "r"(taddr)
         : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Byte offset of the top-left of the patch at linear position p (y * W + x) in an H x W x C image,
@@ -195,42 +196,47 @@ __global__ void split_basis_kernel(const double* __restrict__ b64, __nv_bfloat16
 
 // ------------------------------------------------------------------------------ tensor-core kernel
 
-// Gathers patches tile * 128 .. + 127 into the A stage (no-swizzle K-major: [k chunk][patch][8] BF16).
-// Groups of 8 lanes take one (patch, patch row): lanes 0 .. 2C - 1 each convert 4 bytes of the row
-// (8 C bytes), lane 2C loads the word after the row for the byte shift. Rows of missing or invalid
-// patches are zero. soff holds the patches' byte offsets (-1: none).
+// Gathers patches tile * 128 .. + 127 into the A stage (no-swizzle K-major: plane k chunk, row patch,
+// 8 BF16). Groups of 8 lanes take one (patch, patch row): lanes 0 .. 2C - 1 each convert 4 bytes of
+// the row (8 C bytes), lane 2C loads the word after the row for the byte shift. All sixteen words of
+// a lane are loaded before any is used. Rows of missing or invalid patches are zero. soff holds the
+// patches' byte offsets (-1: none).
 template <int C>
 __device__ __forceinline__ void gather_a_tile(const uint8_t* __restrict__ img, long long total, int rowbytes,
                                               const int* soff, uint8_t* sa, int tid) {
+    using Dm = ProjDims<C>;
     constexpr int NW = 2 * C;
+    constexpr int PASSES = kTileM * PS / (kTcThreads / 8);      // 16: pass p covers row p / 2 of 64 patches
     const int g = tid >> 3, l = tid & 7;
-#pragma unroll 4
-    for (int pass = 0; pass < kTileM * PS / 32; ++pass) {
-        const int task = pass * 32 + g;
-        const int m = task & (kTileM - 1), a = task >> 7;
-        const int o = soff[m];
-        uint32_t w = 0;
-        if (o >= 0 && l <= NW) {
-            const long long ob = (long long)o + (long long)a * rowbytes;
-            w = image_word(img, (ob & ~3ll) + 4 * l, total);
+    const int o[2] = {soff[g], soff[64 + g]};                   // patches g and 64 + g
+    uint32_t w[PASSES];
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p) {
+        const int op = o[p & 1];
+        w[p] = 0;
+        if (op >= 0 && l <= NW) {
+            const long long ob = (long long)op + (long long)(p >> 1) * rowbytes;
+            w[p] = image_word(img, (ob & ~3ll) + 4 * l, total);
         }
-        const uint32_t wn = __shfl_down_sync(0xffffffffu, w, 1, 8);
+    }
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p) {
+        const uint32_t wn = __shfl_down_sync(0xffffffffu, w[p], 1, 8);
+        const int op = o[p & 1], a = p >> 1, m = ((p & 1) << 6) | g;
         if (l < NW) {
             uint2 v = make_uint2(0u, 0u);
-            if (o >= 0) {
-                const int sh = ((o + a * rowbytes) & 3) * 8;
-                const uint32_t bytes = __funnelshift_r(w, wn, sh);
+            if (op >= 0) {
+                const uint32_t bytes = __funnelshift_r(w[p], wn, ((op + a * rowbytes) & 3) * 8);
                 v.x = bf16x2_of_bytes(bytes, 0);
                 v.y = bf16x2_of_bytes(bytes, 2);
             }
-            const int chunk = a * C + (l >> 1);
-            *reinterpret_cast<uint2*>(sa + chunk * (kTileM * 16) + m * 16 + (l & 1) * 8) = v;
+            *reinterpret_cast<uint2*>(sa + (a * C + (l >> 1)) * Dm::LBO_A + m * 16 + (l & 1) * 8) = v;
         }
     }
 }
 
 template <int C>
-__global__ void __launch_bounds__(kProjThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
 project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* __restrict__ pos, long long n,
                   const uint4* __restrict__ pieces, float* __restrict__ coef, int* __restrict__ flag) {
     using Dm = ProjDims<C>;
@@ -250,7 +256,7 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
     {   // this half's three pieces of T, one contiguous block in the kernel's smem layout
         const uint4* src = pieces + (size_t)half * (3 * Dm::B_PIECE / 16);
         uint4* dst = reinterpret_cast<uint4*>(sB);
-        for (int i = tid; i < 3 * Dm::B_PIECE / 16; i += kProjThreads) dst[i] = src[i];
+        for (int i = tid; i < 3 * Dm::B_PIECE / 16; i += kTcThreads) dst[i] = src[i];
     }
     if (tid == 0) {
         mbar_init(smem_u32(&bars[0]), 1);
@@ -315,20 +321,19 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
             ok = __syncthreads_and(done) != 0;
             if (!ok) break;
             tc_fence_after();
-            const int cb = (warp >> 2) * (Dm::NH / 2);
+            const int cb = (warp >> 2) * (Dm::NH / 4);       // four warps per lane quarter, NH / 4 columns each
             const uint32_t ta = tmem + pb * Dm::ACC_COLS + ((uint32_t)(q * 32) << 16) + cb;
             float* dst = coef + P * Dm::D + half * Dm::NH + cb;
 #pragma unroll
-            for (int c = 0; c < Dm::NH / 2; c += 16) {
-                float v[16];
-                tmem_ld16(ta + c, v);
+            for (int c = 0; c < Dm::NH / 4; c += 8) {
+                float v[8];
+                tmem_ld8(ta + c, v);
                 if (P < n) {
                     if (!valid)
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] = __int_as_float(0x7fc00000);
-#pragma unroll
-                    for (int i = 0; i < 16; i += 4)
-                        *reinterpret_cast<float4*>(dst + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                        for (int i = 0; i < 8; ++i) v[i] = __int_as_float(0x7fc00000);
+                    *reinterpret_cast<float4*>(dst + c) = make_float4(v[0], v[1], v[2], v[3]);
+                    *reinterpret_cast<float4*>(dst + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
                 }
             }
         }
@@ -512,7 +517,7 @@ static cudaError_t launch_tc_c(const uint8_t* img, int H, int W, const int32_t* 
     const int half_grid = device_sm_count() / 2 > 0 ? device_sm_count() / 2 : 1;
     const long long ntiles = (n + kTileM - 1) / kTileM;
     const int g = (int)(ntiles < half_grid ? ntiles : half_grid);
-    project_tc_kernel<C><<<2 * g, kProjThreads, Dm::SMEM, s>>>(img, H, W, pos, n, static_cast<const uint4*>(pieces),
+    project_tc_kernel<C><<<2 * g, kTcThreads, Dm::SMEM, s>>>(img, H, W, pos, n, static_cast<const uint4*>(pieces),
                                                                 coef, flag);
     return cudaGetLastError();
 }

@@ -75,3 +75,21 @@ def test_host_sigma_rejects_bad_args():
     S = np.zeros(64, np.uint64)
     assert f(M.ctypes.data, S.ctypes.data, 64, 0, None) == -1.0
     assert f(None, S.ctypes.data, 64, 5, None) == -1.0
+
+
+@pytest.mark.parametrize("shape,seed", [((20, 24, 22), 5), ((40, 36, 30), 8)])
+def test_host_volume_bases_match_oracle(shape, seed):
+    """Bases of the MRI volume path (reading R20), solved on the host from exact integer cube
+    moments (4 x 4 Hermitian slices, slice 1 through its real embedding), against the oracle's
+    numpy eigh of the tube-Fourier slices of the reference cubes; same canonical phases."""
+    lib = H.load_library()
+    v = synth.add_gaussian(synth.clean_volume(*shape, seed), 11.0, seed)
+    p = O.Params(ps=4, stride=2, window=5, K=8)
+    P = O.gather_cubes(v, O.volume_reference_positions(v.shape, p), 4)      # (n, i, j, k)
+    mom = _moments(P)
+    b = np.zeros(256)
+    gap = lib.htsvd_internal_volume_bases(mom.ctypes.data, b.ctypes.data)
+    U, V, lu, lv = O.global_basis(P)
+    z = (b[0::2] + 1j * b[1::2]).reshape(2, 4, 4, 4)
+    assert np.abs(z[0] - U).max() < 1e-9 and np.abs(z[1] - V).max() < 1e-9
+    assert abs(gap - O.global_basis_gap(lu, lv)) <= 1e-9 * max(gap, 1e-12)
