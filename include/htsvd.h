@@ -281,9 +281,9 @@ htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, in
  * of the same image); d_coef: n x 64 C float32 (DEVICE, 16-byte aligned), coefficient
  * (i * 8 + j) * C + c of patch t at d_coef[t * 64 C + ...] (the order of the mask bits).
  * The map P -> S is one real (64 C) x (64 C) matrix; it runs on the tensor cores as a dense
- * contraction: the patch bytes are exact in BF16, the matrix is split into three BF16 pieces
- * (each the rounding of what the earlier ones leave), FP32 accumulation, so the coefficients carry
- * an FP32-level error (measured below 2^-22 of the patch norm). A position whose patch does not
+ * contraction: the patch bytes are exact in FP16, the matrix (scaled by 2^14) is split into two
+ * FP16 pieces (the second the rounding of what the first leaves), FP32 accumulation, so the
+ * coefficients carry an FP32-level error (tested against 2^-21 of the patch norm). A position whose patch does not
  * lie inside the image gives NaN coefficients. d_flag (DEVICE, may be NULL): bit 0 is set if a wait
  * for the tensor cores ran out (about two seconds; the affected tile is not written).
  * Errors: INVALID_ARG for C not 1 or 3, H or W < 8, n < 0, a null pointer with n > 0, or a

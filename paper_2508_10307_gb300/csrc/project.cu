@@ -8,20 +8,21 @@
 // * project_tc_kernel: the map P -> S is one real (64 C) x (64 C) matrix T (real because slices
 //   f and C - f are conjugate), so a batch of patches is a dense contraction S = P T^T on the
 //   fifth-generation tensor cores (tcgen05.mma, kind::f16, FP32 accumulation in tensor memory).
-//   The patch bytes are exact in BF16; T is split into three BF16 pieces T = T_hi + T_mid + T_lo
-//   (each the rounding of what the previous ones leave), so three products per K step give an
-//   FP32-level result. T would take 3 x 72 KB of shared memory at C = 3, so each CTA holds the
-//   pieces of one half of the coefficients (N = 32 C) and the grid runs both halves; the A tile
-//   (128 patches x 64 C BF16, gathered from the image) is double-buffered, the accumulator is
-//   double-buffered in tensor memory, and one thread issues the MMAs of tile t while the CTA
-//   reads tile t - 1 out of tensor memory and gathers tile t + 1.
+//   The patch bytes are exact in FP16; T (scaled by 2^14) is split into two FP16 pieces
+//   T = T_hi + T_lo (T_lo the rounding of what T_hi leaves: 22 significant bits), so two products
+//   per K step give an FP32-level result. The pieces of all of T would take 2 x 72 KB of shared
+//   memory at C = 3 beside the A tiles, so each CTA holds the pieces of one half of the
+//   coefficients (N = 32 C) and the grid runs both halves; the A tile (128 patches x 64 C FP16,
+//   gathered from the image by 16 warps) is double-buffered, the accumulator is double-buffered in
+//   tensor memory, and one thread issues the MMAs of tile t while the CTA loads the image words of
+//   tile t + 1 and reads tile t - 1 out of tensor memory.
 // * project_simt_kernel: the structured per-slice form in FP32 on the CUDA cores (channel DFT,
 //   U_f^H X_f on patch columns, (.) V_f on patch rows, inverse channel DFT), the form the group
 //   filter uses, for comparison.
 //
 // Coefficient order of both: n = (i * 8 + j) * C + c (basis row i, basis column j, channel c),
 // patch input order k = (a * 8 + b) * C + c (image row a, column b, channel c of the patch).
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 #include "kernels.h"
@@ -32,6 +33,8 @@ namespace {
 constexpr int kProjThreads = 256;           // structured FP32 kernel
 constexpr int kTcThreads = 512;             // tensor-core kernel: 16 warps gather, one thread issues the MMAs
 constexpr int kTileM = 128;                 // patches per MMA tile (TMEM lanes)
+constexpr int kPieces = 2;                  // FP16 pieces of the basis matrix
+constexpr float kSplitScale = 16384.0f;     // 2^14: the matrix is split after this scaling, undone on output
 
 template <int C>
 struct ProjDims {
@@ -47,15 +50,15 @@ struct ProjDims {
     static constexpr int B_PIECE = NH * D * 2;
     static constexpr int ACC_COLS = C == 3 ? 128 : 32;   // TMEM column stride of the two accumulators
     static constexpr int TMEM_COLS = 2 * ACC_COLS;       // power of two >= 32
-    static constexpr int POS_OFF = 2 * A_BYTES + 3 * B_PIECE;   // [2][128] int32 patch byte offsets
+    static constexpr int POS_OFF = 2 * A_BYTES + kPieces * B_PIECE;   // [2][128] int32 patch byte offsets
     static constexpr int BAR_OFF = POS_OFF + 2 * kTileM * 4;    // two mbarriers, then the TMEM slot
     static constexpr int SMEM = BAR_OFF + 32;
 };
 static_assert(ProjDims<3>::SMEM <= 232448, "projection tile does not fit shared memory");
 
-// Instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B FP16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -104,7 +107,7 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -149,20 +152,16 @@ __device__ __forceinline__ uint32_t image_word(const uint8_t* img, long long wa,
     return v;
 }
 
-// BF16 bits of two bytes (exact: integers below 256 have at most 8 significant bits).
-__device__ __forceinline__ uint32_t bf16x2_of_bytes(uint32_t w, int b0) {
-    const uint32_t lo = __float_as_uint((float)((w >> (8 * b0)) & 0xFF)) >> 16;
-    const uint32_t hi = __float_as_uint((float)((w >> (8 * b0 + 8)) & 0xFF)) >> 16;
-    return lo | (hi << 16);
-}
 
 // ------------------------------------------------------------------------------ split basis matrix
 
 // T[n][k] with n = (i, j, co), k = (a, b, ci):  T = Re (1/C) sum_f e^{2 pi i f (co - ci) / C} conj(U_f[a][i]) V_f[b][j]
-// in FP64, then T_hi = bf16(T), T_mid = bf16(T - T_hi), T_lo = bf16(T - T_hi - T_mid), written in the
-// shared-memory image of the projection kernel: [half][piece][k chunk][n within half][8].
+// in FP64, scaled by 2^14 (|T| <= 1: the pieces stay normal FP16 numbers down to |T| ~ 2^-17, below which
+// the dropped part is under 2^-39 absolute), then T_hi = f16(2^14 T), T_lo = f16(2^14 T - T_hi); the
+// pair carries 22 significant bits. Written in the shared-memory image of the projection kernel:
+// [half][piece][k chunk][n within half][8].
 template <int C>
-__global__ void split_basis_kernel(const double* __restrict__ b64, __nv_bfloat16* __restrict__ out) {
+__global__ void split_basis_kernel(const double* __restrict__ b64, __half* __restrict__ out) {
     using Dm = ProjDims<C>;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= Dm::D * Dm::D) return;
@@ -180,55 +179,70 @@ __global__ void split_basis_kernel(const double* __restrict__ b64, __nv_bfloat16
         if (d != 0) sincospi(2.0 * d / C, &sn, &cs);
         t += pr * cs - pi * sn;                                                    // Re(phase * product)
     }
-    t /= C;
-    const __nv_bfloat16 hi = __float2bfloat16_rn((float)t);
-    const double r1 = t - (double)__bfloat162float(hi);
-    const __nv_bfloat16 mid = __float2bfloat16_rn((float)r1);
-    const double r2 = r1 - (double)__bfloat162float(mid);
-    const __nv_bfloat16 lo = __float2bfloat16_rn((float)r2);
+    t = t / C * kSplitScale;
+    const __half hi = __float2half_rn((float)t);
+    const __half lo = __float2half_rn((float)(t - (double)__half2float(hi)));
     const int h = n / Dm::NH, r = n % Dm::NH;
-    const __nv_bfloat16 pieces[3] = {hi, mid, lo};
-    for (int p = 0; p < 3; ++p) {
-        const size_t off = ((((size_t)h * 3 + p) * Dm::KCH + k / 8) * Dm::NH + r) * 8 + (k % 8);
-        out[off] = pieces[p];
-    }
+    out[((((size_t)h * kPieces + 0) * Dm::KCH + k / 8) * Dm::NH + r) * 8 + (k % 8)] = hi;
+    out[((((size_t)h * kPieces + 1) * Dm::KCH + k / 8) * Dm::NH + r) * 8 + (k % 8)] = lo;
 }
 
 // ------------------------------------------------------------------------------ tensor-core kernel
 
-// Gathers patches tile * 128 .. + 127 into the A stage (no-swizzle K-major: plane k chunk, row patch,
-// 8 BF16). Groups of 8 lanes take one (patch, patch row): lanes 0 .. 2C - 1 each convert 4 bytes of
-// the row (8 C bytes), lane 2C loads the word after the row for the byte shift. All sixteen words of
-// a lane are loaded before any is used. Rows of missing or invalid patches are zero. soff holds the
-// patches' byte offsets (-1: none).
+// FP16 pair (b0 + 1024, b1 + 1024) from two bytes of w (exact: 1024 + b has 11 significant bits),
+// then minus 1024: the bytes as FP16, also exact.
+__device__ __forceinline__ uint32_t f16x2_of_bytes(uint32_t w, uint32_t sel) {
+    const uint32_t biased = __byte_perm(w, 0x00006400u, sel);
+    __half2 h = *reinterpret_cast<const __half2*>(&biased);
+    h = __hsub2(h, __half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// One tile's share of the gather for this lane. Groups of 8 lanes take one patch row at a time:
+// lanes 0 .. 2C - 1 each convert 4 bytes of the row (8 C bytes), lane 2C loads the word after the row
+// for the byte shift. Lane group g covers patches g and 64 + g of the tile, rows 0..7 (16 words).
+struct GatherRegs {
+    int o[2];            // byte offsets of the two patches (-1: none)
+    uint32_t w[16];      // word of pass p: patch p & 1, row p >> 1
+};
+
 template <int C>
-__device__ __forceinline__ void gather_a_tile(const uint8_t* __restrict__ img, long long total, int rowbytes,
-                                              const int* soff, uint8_t* sa, int tid) {
-    using Dm = ProjDims<C>;
+__device__ __forceinline__ void gather_fetch(const uint8_t* __restrict__ img, int total, int rowbytes,
+                                             const int32_t* __restrict__ pos, long long n, int H, int W,
+                                             long long tile, int g, int l, GatherRegs& R) {
     constexpr int NW = 2 * C;
-    constexpr int PASSES = kTileM * PS / (kTcThreads / 8);      // 16: pass p covers row p / 2 of 64 patches
-    const int g = tid >> 3, l = tid & 7;
-    const int o[2] = {soff[g], soff[64 + g]};                   // patches g and 64 + g
-    uint32_t w[PASSES];
 #pragma unroll
-    for (int p = 0; p < PASSES; ++p) {
-        const int op = o[p & 1];
-        w[p] = 0;
-        if (op >= 0 && l <= NW) {
-            const long long ob = (long long)op + (long long)(p >> 1) * rowbytes;
-            w[p] = image_word(img, (ob & ~3ll) + 4 * l, total);
-        }
+    for (int h = 0; h < 2; ++h) {
+        const long long P = tile * kTileM + h * 64 + g;
+        R.o[h] = P < n ? patch_offset(__ldg(pos + P), H, W, C) : -1;
     }
 #pragma unroll
-    for (int p = 0; p < PASSES; ++p) {
-        const uint32_t wn = __shfl_down_sync(0xffffffffu, w[p], 1, 8);
-        const int op = o[p & 1], a = p >> 1, m = ((p & 1) << 6) | g;
+    for (int p = 0; p < 16; ++p) {
+        const int op = R.o[p & 1];
+        R.w[p] = 0;
+        if (op >= 0 && l <= NW) {
+            const int wa = ((op + (p >> 1) * rowbytes) & ~3) + 4 * l;       // < H W C < 2^31
+            R.w[p] = wa + 4 <= total ? __ldg(reinterpret_cast<const uint32_t*>(img + wa))
+                                     : image_word(img, wa, total);
+        }
+    }
+}
+
+// Converts the fetched words into the A stage (no-swizzle K-major: plane k chunk, row patch, 8 FP16).
+template <int C>
+__device__ __forceinline__ void gather_store(const GatherRegs& R, int rowbytes, int g, int l, uint8_t* sa) {
+    using Dm = ProjDims<C>;
+    constexpr int NW = 2 * C;
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+        const uint32_t wn = __shfl_down_sync(0xffffffffu, R.w[p], 1, 8);
+        const int op = R.o[p & 1], a = p >> 1, m = ((p & 1) << 6) | g;
         if (l < NW) {
             uint2 v = make_uint2(0u, 0u);
             if (op >= 0) {
-                const uint32_t bytes = __funnelshift_r(w[p], wn, ((op + a * rowbytes) & 3) * 8);
-                v.x = bf16x2_of_bytes(bytes, 0);
-                v.y = bf16x2_of_bytes(bytes, 2);
+                const uint32_t bytes = __funnelshift_r(R.w[p], wn, ((op + a * rowbytes) & 3) * 8);
+                v.x = f16x2_of_bytes(bytes, 0x5150u);
+                v.y = f16x2_of_bytes(bytes, 0x5352u);
             }
             *reinterpret_cast<uint2*>(sa + (a * C + (l >> 1)) * Dm::LBO_A + m * 16 + (l & 1) * 8) = v;
         }
@@ -247,16 +261,17 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Dm::BAR_OFF);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Dm::BAR_OFF + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = tid >> 3, l = tid & 7;
     const int half = blockIdx.x & 1;
     const long long stride = gridDim.x >> 1;
     const long long ntiles = (n + kTileM - 1) / kTileM;
     const long long total = (long long)H * W * C;
     const int rowbytes = W * C;
 
-    {   // this half's three pieces of T, one contiguous block in the kernel's smem layout
-        const uint4* src = pieces + (size_t)half * (3 * Dm::B_PIECE / 16);
+    {   // this half's pieces of T, one contiguous block in the kernel's smem layout
+        const uint4* src = pieces + (size_t)half * (kPieces * Dm::B_PIECE / 16);
         uint4* dst = reinterpret_cast<uint4*>(sB);
-        for (int i = tid; i < 3 * Dm::B_PIECE / 16; i += kTcThreads) dst[i] = src[i];
+        for (int i = tid; i < kPieces * Dm::B_PIECE / 16; i += kTcThreads) dst[i] = src[i];
     }
     if (tid == 0) {
         mbar_init(smem_u32(&bars[0]), 1);
@@ -274,20 +289,28 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    constexpr uint32_t kIdesc = idesc_bf16(kTileM, Dm::NH);
+    constexpr uint32_t kIdesc = idesc_f16(kTileM, Dm::NH);
 
+    // Software pipeline: the image words of tile t + 2 stride are loaded into the register set that
+    // tile t was just stored from, so every load has a whole iteration (the MMAs of tile t and the
+    // read-out of tile t - stride) to arrive.
+    GatherRegs RA, RB;
+    const long long t0 = blockIdx.x >> 1;
+    const int totali = (int)total;
+    if (t0 < ntiles) gather_fetch<C>(img, totali, rowbytes, pos, n, H, W, t0, g, l, RA);
+    if (t0 + stride < ntiles) gather_fetch<C>(img, totali, rowbytes, pos, n, H, W, t0 + stride, g, l, RB);
     bool ok = true;
     long long it = 0;
-    for (long long t = blockIdx.x >> 1;; t += stride, ++it) {
+    long long t = t0;
+    auto step = [&](GatherRegs& R) -> bool {
         const bool have = t < ntiles;        // uniform over the CTA
         const int b = (int)(it & 1);
         if (have) {
-            if (tid < kTileM) {
-                const long long P = t * kTileM + tid;
-                sOff[b * kTileM + tid] = P < n ? patch_offset(pos[P], H, W, C) : -1;
+            gather_store<C>(R, rowbytes, g, l, sA + b * Dm::A_BYTES);
+            if (l == 0) {
+                sOff[b * kTileM + g] = R.o[0];
+                sOff[b * kTileM + 64 + g] = R.o[1];
             }
-            __syncthreads();
-            gather_a_tile<C>(img, total, rowbytes, sOff + b * kTileM, sA + b * Dm::A_BYTES, tid);
             fence_async_smem();
         }
         tc_fence_before();
@@ -298,17 +321,18 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
             const uint32_t d = tmem + b * Dm::ACC_COLS;
             uint32_t acc = 0;
 #pragma unroll 1
-            for (int p = 2; p >= 0; --p) {            // smallest piece first
+            for (int p = kPieces - 1; p >= 0; --p) {            // smaller piece first
 #pragma unroll
                 for (int s = 0; s < Dm::KSTEPS; ++s) {
                     const uint64_t ad = smem_desc(a0 + s * 2 * Dm::LBO_A, Dm::LBO_A, 128);
                     const uint64_t bd = smem_desc(b0 + p * Dm::B_PIECE + s * 2 * Dm::LBO_B, Dm::LBO_B, 128);
-                    mma_bf16(d, ad, bd, kIdesc, acc);
+                    mma_f16(d, ad, bd, kIdesc, acc);
                     acc = 1;
                 }
             }
             mma_commit(smem_u32(&bars[b]));
         }
+        if (t + 2 * stride < ntiles) gather_fetch<C>(img, totali, rowbytes, pos, n, H, W, t + 2 * stride, g, l, R);
         if (it > 0) {   // read out tile t - stride (buffer b ^ 1)
             const int pb = b ^ 1;
             const int q = warp & 3;
@@ -319,26 +343,31 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
             const bool valid = sOff[pb * kTileM + m] >= 0;
             const bool done = mbar_wait_bounded(smem_u32(&bars[pb]), (uint32_t)(((it - 1) >> 1) & 1));
             ok = __syncthreads_and(done) != 0;
-            if (!ok) break;
+            if (!ok) return false;
             tc_fence_after();
             const int cb = (warp >> 2) * (Dm::NH / 4);       // four warps per lane quarter, NH / 4 columns each
             const uint32_t ta = tmem + pb * Dm::ACC_COLS + ((uint32_t)(q * 32) << 16) + cb;
             float* dst = coef + P * Dm::D + half * Dm::NH + cb;
+            constexpr float unscale = 1.0f / kSplitScale;
 #pragma unroll
             for (int c = 0; c < Dm::NH / 4; c += 8) {
                 float v[8];
                 tmem_ld8(ta + c, v);
                 if (P < n) {
-                    if (!valid)
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) v[i] = __int_as_float(0x7fc00000);
+                    for (int i = 0; i < 8; ++i) v[i] = valid ? v[i] * unscale : __int_as_float(0x7fc00000);
                     *reinterpret_cast<float4*>(dst + c) = make_float4(v[0], v[1], v[2], v[3]);
                     *reinterpret_cast<float4*>(dst + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
                 }
             }
         }
         tc_fence_before();
-        if (!have) break;
+        if (!have) return false;
+        t += stride;
+        ++it;
+        return true;
+    };
+    while (step(RA) && step(RB)) {
     }
     tc_fence_before();
     if (!ok) {
@@ -491,13 +520,13 @@ project_simt_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t
 }  // namespace
 
 size_t project_pieces_bytes(int C) {
-    return C == 3 ? (size_t)2 * 3 * ProjDims<3>::B_PIECE : (size_t)2 * 3 * ProjDims<1>::B_PIECE;
+    return C == 3 ? (size_t)2 * kPieces * ProjDims<3>::B_PIECE : (size_t)2 * kPieces * ProjDims<1>::B_PIECE;
 }
 
 cudaError_t launch_project_split(const double* d_b64, int C, void* d_pieces, cudaStream_t s) {
     const int D = 64 * C, nth = 256, nbl = (D * D + nth - 1) / nth;
-    if (C == 3) split_basis_kernel<3><<<nbl, nth, 0, s>>>(d_b64, static_cast<__nv_bfloat16*>(d_pieces));
-    else split_basis_kernel<1><<<nbl, nth, 0, s>>>(d_b64, static_cast<__nv_bfloat16*>(d_pieces));
+    if (C == 3) split_basis_kernel<3><<<nbl, nth, 0, s>>>(d_b64, static_cast<__half*>(d_pieces));
+    else split_basis_kernel<1><<<nbl, nth, 0, s>>>(d_b64, static_cast<__half*>(d_pieces));
     return cudaGetLastError();
 }
 

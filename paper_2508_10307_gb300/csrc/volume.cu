@@ -30,7 +30,7 @@ namespace {
 
 constexpr int VPS = 4;                 // cube edge
 constexpr int VTR = 4;                 // references per tile edge of the filter
-constexpr int kVolWarps = 8;
+constexpr int kVolWarps = 6;
 constexpr int kMaxCand = 512;          // W^3 <= 512 (W <= 8)
 constexpr int kHcBytes = kVolWarps * 32 * 65 * 4;
 
@@ -165,34 +165,39 @@ __global__ void __launch_bounds__(256) volume_moments_kernel(const uint8_t* __re
 
 // ------------------------------------------------------------------------------ filter
 
-__device__ __forceinline__ float haar_level(float x, int lane, int st, float r2) {
-    const float y = __shfl_xor_sync(0xffffffffu, x, st);
-    if ((lane & (st - 1)) == 0) x = (lane & st) ? (y - x) * r2 : (x + y) * r2;
-    return x;
-}
-
-// Normalised Haar analysis (and, the butterfly being an involution, synthesis with the levels in
-// reverse order) along the group mode: lane l holds slot l; after the analysis lane 0 holds row 0,
-// lane l > 0 the level-(ctz(l) + 1) difference, row K / 2^(ctz(l)+1) + (l >> (ctz(l) + 1)).
-template <int NV>
-__device__ __forceinline__ void haar_fwd(float (&v)[NV], int lane, int K) {
+// Normalised Haar analysis along the group mode on K values in registers (Sec. II-D, Eqs. (H_2),
+// (H_2N)): level by level, (a, b) -> ((a + b) / sqrt 2, (a - b) / sqrt 2) on slots (j, j + st). Slot 0
+// ends as row 0 of H_K, slot j > 0 as row K / 2^L + (j >> L), L = ctz(j) + 1. The butterfly is its own
+// inverse, so the synthesis runs the same levels in reverse order.
+template <int K>
+__device__ __forceinline__ void haar_analysis(float (&v)[K]) {
     const float r2 = 0.70710678118654752f;
+#pragma unroll
     for (int st = 1; st < K; st <<= 1)
 #pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] = haar_level(v[q], lane, st, r2);
+        for (int j = 0; j < K; j += 2 * st) {
+            const float a = v[j], b = v[j + st];
+            v[j] = (a + b) * r2;
+            v[j + st] = (a - b) * r2;
+        }
 }
-template <int NV>
-__device__ __forceinline__ void haar_inv(float (&v)[NV], int lane, int K) {
+template <int K>
+__device__ __forceinline__ void haar_synthesis(float (&v)[K]) {
     const float r2 = 0.70710678118654752f;
+#pragma unroll
     for (int st = K >> 1; st >= 1; st >>= 1)
 #pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] = haar_level(v[q], lane, st, r2);
+        for (int j = 0; j < K; j += 2 * st) {
+            const float a = v[j], b = v[j + st];
+            v[j] = (a + b) * r2;
+            v[j + st] = (a - b) * r2;
+        }
 }
 
-__device__ __forceinline__ int haar_row(int lane, int K) {
-    if (lane == 0) return 0;
-    const int L = __ffs(lane);             // ctz + 1
-    return (K >> L) + (lane >> L);
+__device__ __forceinline__ int haar_row(int j, int K) {
+    if (j == 0) return 0;
+    const int L = __ffs(j);                // ctz + 1
+    return (K >> L) + (j >> L);
 }
 
 struct VolSmem {
@@ -241,6 +246,7 @@ __device__ __forceinline__ void load_cube(const uint8_t* fb, int fy, int FXp, in
         }
 }
 
+template <int K>
 __global__ void __launch_bounds__(kVolWarps * 32, 2)
 volume_filter_kernel(VolFilterArgs A) {
     const VolGeo g = A.g;
@@ -248,10 +254,9 @@ volume_filter_kernel(VolFilterArgs A) {
     extern __shared__ __align__(16) unsigned char dyn[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // tile of references and its footprint
-    const int ntz = (g.nrz + VTR - 1) / VTR, nty = (g.nry + VTR - 1) / VTR, ntx = (g.nrx + VTR - 1) / VTR;
+    const int nty = (g.nry + VTR - 1) / VTR, ntx = (g.nrx + VTR - 1) / VTR;
     const int tz = blockIdx.x / (nty * ntx), trem = blockIdx.x - tz * (nty * ntx);
     const int ty = trem / ntx, tx = trem - (trem / ntx) * ntx;
-    (void)ntz;
     int f0[3], fn[3];
     {
         const int t3[3] = {tz, ty, tx}, nr[3] = {g.nrz, g.nry, g.nrx}, nn[3] = {g.D, g.H, g.W};
@@ -263,14 +268,17 @@ volume_filter_kernel(VolFilterArgs A) {
         }
     }
     const int FXp = ((fn[2] + 3) & ~3) + 4;            // staged row length: aligned, one spare word
-    // per lane, the Haar-domain coefficients of its slot of the warp's group (row pad 65: the lanes'
-    // accesses to one coefficient fall in distinct banks)
-    float* hc = reinterpret_cast<float*>(dyn) + (warp * 32 + lane) * 65;
+    // the warp's group as a 32 x 65 float block: row k = the coefficients of cube k (lane k writes and
+    // reads it), column e = fibre e (lane e % 32 reads it for the Haar transform); the pad of 65 keeps
+    // both access patterns free of bank conflicts
+    float* hcw = reinterpret_cast<float*>(dyn) + warp * 32 * 65;
+    float* hcl = hcw + lane * 65;
     uint8_t* fb = dyn + kHcBytes;                        // footprint bytes [fz][fy][FXp]
     const int nfb = fn[0] * fn[1] * FXp;
-    float* num = reinterpret_cast<float*>(dyn + kHcBytes + ((nfb + 15) & ~15));
     const int nvox = fn[0] * fn[1] * fn[2];
-    float* den = num + nvox;
+    float* num = reinterpret_cast<float*>(dyn + kHcBytes + ((nfb + 15) & ~15));
+    float* org = num + nvox;                             // weights summed at the cubes' first voxel
+    float* tmp = org + nvox;
     const long long plane = (long long)g.H * g.W;
     const long long total = (long long)g.D * plane;
     for (int e = tid; e < 2 * 3 * 2 * 16; e += blockDim.x) {
@@ -294,16 +302,14 @@ volume_filter_kernel(VolFilterArgs A) {
     for (int q = tid; q < 2 * nvox; q += blockDim.x) num[q] = 0.f;
     __syncthreads();
 
-    const int K = g.K;
     const float tau = A.tau32;
     const int r0z = tz * VTR, r0y = ty * VTR, r0x = tx * VTR;
     const int nz = min(VTR, g.nrz - r0z), ny = min(VTR, g.nry - r0y), nx = min(VTR, g.nrx - r0x);
-    const int myrow = haar_row(lane, K);
     for (int q = warp; q < nz * ny * nx; q += kVolWarps) {
         const int qz = q / (ny * nx), qr = q - qz * (ny * nx), qy = qr / nx, qx = qr - (qr / nx) * nx;
         const long long gi = ((long long)(r0z + qz) * g.nry + (r0y + qy)) * g.nrx + (r0x + qx);
         const bool act = lane < K;
-        int lin = act ? A.idx[gi * K + lane] : 0;
+        const int lin = act ? A.idx[gi * K + lane] : 0;
         const int cz = (int)(lin / plane), crem = (int)(lin - (long long)cz * plane);
         const int cy = crem / g.W, cx = crem - (crem / g.W) * g.W;
         const int oz = cz - f0[0], oy = cy - f0[1], ox = cx - f0[2];
@@ -316,7 +322,7 @@ volume_filter_kernel(VolFilterArgs A) {
         unsigned long long ss64 = ss;
         for (int o = 16; o >= 1; o >>= 1) ss64 += __shfl_xor_sync(0xffffffffu, ss64, o);
         const float band = A.band_rel * sqrtf((float)ss64) + A.band_abs;
-        // tube DFT of the cube: X0 (real), X2 (real), X1 = xr + i xi, per (a, b)
+        // forward projection of cube `lane`: tube DFT X0 (real), X2 (real), X1 = xr + i xi per (a, b)
         float x0[16], x2[16], xr[16], xi[16];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -329,7 +335,6 @@ volume_filter_kernel(VolFilterArgs A) {
                 xr[a * 4 + b] = p0 - p2;
                 xi[a * 4 + b] = p3 - p1;
             }
-        unsigned long long mk = 0ull, amb = 0ull;        // bit e: kept / inside the guard band
 #pragma unroll 1
         for (int i = 0; i < 4; ++i) {
             // row i of S: Y_f[i][b] = sum_a conj(U_f[a][i]) X_f[a][b]; Z_f[i][j] = sum_b Y_f[i][b] V_f[b][j]
@@ -348,7 +353,6 @@ volume_filter_kernel(VolFilterArgs A) {
                 }
                 y0[b] = s0; y2[b] = s2; yr[b] = sr; yi[b] = si;
             }
-            float c[16];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float z0 = 0.f, z2 = 0.f, zr = 0.f, zi = 0.f;
@@ -361,111 +365,136 @@ volume_filter_kernel(VolFilterArgs A) {
                     zr = fmaf(yr[b], vr, fmaf(-yi[b], vi, zr));
                     zi = fmaf(yr[b], vi, fmaf(yi[b], vr, zi));
                 }
-                c[j * 4 + 0] = 0.25f * ((z0 + z2) + 2.f * zr);
-                c[j * 4 + 1] = 0.25f * ((z0 - z2) - 2.f * zi);
-                c[j * 4 + 2] = 0.25f * ((z0 + z2) - 2.f * zr);
-                c[j * 4 + 3] = 0.25f * ((z0 - z2) + 2.f * zi);
-            }
-            haar_fwd(c, lane, K);
-            unsigned rk = 0u, ra = 0u;
-#pragma unroll
-            for (int q2 = 0; q2 < 16; ++q2) {
-                const float m = fabsf(c[q2]);
-                const bool keep = m >= tau, near = fabsf(m - tau) <= band;
-                rk |= (keep ? 1u : 0u) << q2;
-                ra |= (near ? 1u : 0u) << q2;
-                // a coefficient inside the band keeps its FP32 value until its FP64 decision below
-                hc[i * 16 + q2] = (keep || near) ? c[q2] : 0.f;
-            }
-            if (act) {
-                mk |= (unsigned long long)rk << (16 * i);
-                amb |= (unsigned long long)ra << (16 * i);
+                hcl[i * 16 + j * 4 + 0] = 0.25f * ((z0 + z2) + 2.f * zr);
+                hcl[i * 16 + j * 4 + 1] = 0.25f * ((z0 - z2) - 2.f * zi);
+                hcl[i * 16 + j * 4 + 2] = 0.25f * ((z0 + z2) - 2.f * zr);
+                hcl[i * 16 + j * 4 + 3] = 0.25f * ((z0 - z2) + 2.f * zi);
             }
         }
-        // FP64 decisions inside the guard band, one coefficient at a time, the whole warp computing it
+        __syncwarp();
+        // Haar transform along the group mode of fibres e0 = lane and e1 = lane + 32, in registers
+        float v0[K], v1[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            v0[k] = hcw[k * 65 + lane];
+            v1[k] = hcw[k * 65 + lane + 32];
+        }
+        haar_analysis(v0);
+        haar_analysis(v1);
+        unsigned kb0 = 0u, kb1 = 0u, nb0 = 0u, nb1 = 0u, db0 = 0u, db1 = 0u;   // bit j: kept / in band / dropped
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const float m0 = fabsf(v0[j]), m1 = fabsf(v1[j]);
+            const bool k0 = m0 >= tau, k1 = m1 >= tau, n0 = fabsf(m0 - tau) <= band, n1 = fabsf(m1 - tau) <= band;
+            kb0 |= (k0 ? 1u : 0u) << j;
+            kb1 |= (k1 ? 1u : 0u) << j;
+            nb0 |= (n0 ? 1u : 0u) << j;
+            nb1 |= (n1 ? 1u : 0u) << j;
+            if (!k0 && !n0) v0[j] = 0.f;
+            if (!k1 && !n1) v1[j] = 0.f;
+        }
+        // FP64 decisions inside the guard band, one coefficient at a time, the whole warp computing it:
+        // lane k forms cube k's FP64 coefficient, the Haar row of the slot weighs the cubes
         for (;;) {
-            const unsigned bal = __ballot_sync(0xffffffffu, amb != 0ull);
+            const unsigned bal = __ballot_sync(0xffffffffu, (nb0 | nb1) != 0u);
             if (!bal) break;
             const int owner = __ffs(bal) - 1;
-            int e = 0;
-            if (lane == owner) e = __ffsll((long long)amb) - 1;
-            e = __shfl_sync(0xffffffffu, e, owner);
+            int code = 0;
+            if (lane == owner) code = nb0 ? (__ffs(nb0) - 1) : (64 + __ffs(nb1) - 1);
+            code = __shfl_sync(0xffffffffu, code, owner);
+            const int j = code & 63, e = owner + ((code >> 6) ? 32 : 0);
             uint32_t wr[16];                             // the cube's bytes again (not kept in registers)
             load_cube(fb, fn[1], FXp, oz, oy, ox, act, wr);
             const double mine = act ? coef64(wr, e, sm) : 0.0;
-            // Haar row of the owner: level L, support [owner - st, owner + st) (+ left, - right); DC: all
             double h = 0.0;
             if (act) {
-                if (owner == 0) h = 1.0 / sqrt((double)K);
+                if (j == 0) h = 1.0 / sqrt((double)K);
                 else {
-                    const int L = __ffs(owner), st = 1 << (L - 1);
+                    const int L = __ffs(j), st = 1 << (L - 1);
                     const double mag = 1.0 / sqrt((double)(1 << L));
-                    if (lane >= owner - st && lane < owner) h = mag;
-                    else if (lane >= owner && lane < owner + st) h = -mag;
+                    if (lane >= j - st && lane < j) h = mag;
+                    else if (lane >= j && lane < j + st) h = -mag;
                 }
             }
             double t = h * mine;
             for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
             if (lane == owner) {
-                const unsigned long long bit = 1ull << e;
-                if (fabs(t) >= A.tau64) mk |= bit;
-                else {
-                    mk &= ~bit;
-                    hc[e] = 0.f;
+                const unsigned bit = 1u << j;
+                const bool keep = fabs(t) >= A.tau64;
+                if (code >> 6) {
+                    kb1 = keep ? (kb1 | bit) : (kb1 & ~bit);
+                    db1 |= keep ? 0u : bit;
+                    nb1 &= ~bit;
+                } else {
+                    kb0 = keep ? (kb0 | bit) : (kb0 & ~bit);
+                    db0 |= keep ? 0u : bit;
+                    nb0 &= ~bit;
                 }
-                amb &= ~bit;
             }
         }
-        int kept = act ? __popcll(mk) : 0;
+        int kept = __popc(kb0) + __popc(kb1);
         for (int o = 16; o >= 1; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
-        float wgt = A.w_in ? A.w_in[gi] : (A.agg_mode == 1 ? 1.0f / (float)max(1, kept) : 1.0f);
+        const float wgt = A.w_in ? A.w_in[gi] : (A.agg_mode == 1 ? 1.0f / (float)max(1, kept) : 1.0f);
         if (lane == 0 && A.weights_out) A.weights_out[gi] = wgt;
-        if (act && A.mask_out) {
-            A.mask_out[gi * 2 * K + 2 * myrow] = (uint32_t)mk;
-            A.mask_out[gi * 2 * K + 2 * myrow + 1] = (uint32_t)(mk >> 32);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if ((db0 >> j) & 1u) v0[j] = 0.f;
+            if ((db1 >> j) & 1u) v1[j] = 0.f;
+            if (A.mask_out) {
+                const unsigned m0 = __ballot_sync(0xffffffffu, (kb0 >> j) & 1u);
+                const unsigned m1 = __ballot_sync(0xffffffffu, (kb1 >> j) & 1u);
+                if (lane == 0) {
+                    A.mask_out[gi * 2 * K + 2 * haar_row(j, K)] = m0;
+                    A.mask_out[gi * 2 * K + 2 * haar_row(j, K) + 1] = m1;
+                }
+            }
+        }
+        haar_synthesis(v0);
+        haar_synthesis(v1);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            hcw[k * 65 + lane] = v0[k];
+            hcw[k * 65 + lane + 32] = v1[k];
         }
         __syncwarp();
-        // inverse: per row i, Haar synthesis across the lanes, then P_f += U_f[:, i] (Z_f[i, :] V_f^H)
-        float p0[16], p2[16], pr[16], pi[16];
-#pragma unroll
-        for (int q2 = 0; q2 < 16; ++q2) p0[q2] = p2[q2] = pr[q2] = pi[q2] = 0.f;
-#pragma unroll 1
-        for (int i = 0; i < 4; ++i) {
-            float c[16];
-#pragma unroll
-            for (int q2 = 0; q2 < 16; ++q2) c[q2] = hc[i * 16 + q2];
-            haar_inv(c, lane, K);
-            float w0[4], w2[4], wr[4], wi[4];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) { w0[b] = w2[b] = wr[b] = wi[b] = 0.f; }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float s0 = c[j * 4 + 0], s1 = c[j * 4 + 1], s2 = c[j * 4 + 2], s3 = c[j * 4 + 3];
-                const float z0 = (s0 + s1) + (s2 + s3), z2 = (s0 - s1) + (s2 - s3), zr = s0 - s2, zi = s3 - s1;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const float v0 = sm.ub[1][0][0][b * 4 + j], v2 = sm.ub[1][2][0][b * 4 + j];
-                    const float vr = sm.ub[1][1][0][b * 4 + j], vi = sm.ub[1][1][1][b * 4 + j];
-                    w0[b] = fmaf(z0, v0, w0[b]);
-                    w2[b] = fmaf(z2, v2, w2[b]);
-                    wr[b] = fmaf(zr, vr, fmaf(zi, vi, wr[b]));             // z conj(v)
-                    wi[b] = fmaf(zi, vr, fmaf(-zr, vi, wi[b]));
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const float u0 = sm.ub[0][0][0][a * 4 + i], u2 = sm.ub[0][2][0][a * 4 + i];
-                const float ur = sm.ub[0][1][0][a * 4 + i], ui = sm.ub[0][1][1][a * 4 + i];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    p0[a * 4 + b] = fmaf(u0, w0[b], p0[a * 4 + b]);
-                    p2[a * 4 + b] = fmaf(u2, w2[b], p2[a * 4 + b]);
-                    pr[a * 4 + b] = fmaf(ur, wr[b], fmaf(-ui, wi[b], pr[a * 4 + b]));
-                    pi[a * 4 + b] = fmaf(ur, wi[b], fmaf(ui, wr[b], pi[a * 4 + b]));
-                }
-            }
-        }
+        // inverse projection of cube `lane`, row by row: P_f += U_f[:, i] (Z_f[i, :] V_f^H)
         if (act) {
+            float p0[16], p2[16], pr[16], pi[16];
+#pragma unroll
+            for (int q2 = 0; q2 < 16; ++q2) p0[q2] = p2[q2] = pr[q2] = pi[q2] = 0.f;
+#pragma unroll 1
+            for (int i = 0; i < 4; ++i) {
+                float w0[4], w2[4], wrr[4], wi[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) { w0[b] = w2[b] = wrr[b] = wi[b] = 0.f; }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float s0 = hcl[i * 16 + j * 4 + 0], s1 = hcl[i * 16 + j * 4 + 1];
+                    const float s2 = hcl[i * 16 + j * 4 + 2], s3 = hcl[i * 16 + j * 4 + 3];
+                    const float z0 = (s0 + s1) + (s2 + s3), z2 = (s0 - s1) + (s2 - s3), zr = s0 - s2, zi = s3 - s1;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const float vv0 = sm.ub[1][0][0][b * 4 + j], vv2 = sm.ub[1][2][0][b * 4 + j];
+                        const float vr = sm.ub[1][1][0][b * 4 + j], vi = sm.ub[1][1][1][b * 4 + j];
+                        w0[b] = fmaf(z0, vv0, w0[b]);
+                        w2[b] = fmaf(z2, vv2, w2[b]);
+                        wrr[b] = fmaf(zr, vr, fmaf(zi, vi, wrr[b]));           // z conj(v)
+                        wi[b] = fmaf(zi, vr, fmaf(-zr, vi, wi[b]));
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float u0 = sm.ub[0][0][0][a * 4 + i], u2 = sm.ub[0][2][0][a * 4 + i];
+                    const float ur = sm.ub[0][1][0][a * 4 + i], ui = sm.ub[0][1][1][a * 4 + i];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        p0[a * 4 + b] = fmaf(u0, w0[b], p0[a * 4 + b]);
+                        p2[a * 4 + b] = fmaf(u2, w2[b], p2[a * 4 + b]);
+                        pr[a * 4 + b] = fmaf(ur, wrr[b], fmaf(-ui, wi[b], pr[a * 4 + b]));
+                        pi[a * 4 + b] = fmaf(ur, wi[b], fmaf(ui, wrr[b], pi[a * 4 + b]));
+                    }
+                }
+            }
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -474,20 +503,35 @@ volume_filter_kernel(VolFilterArgs A) {
                     const float v[4] = {0.25f * ((p0[q2] + p2[q2]) + 2.f * pr[q2]), 0.25f * ((p0[q2] - p2[q2]) - 2.f * pi[q2]),
                                         0.25f * ((p0[q2] + p2[q2]) - 2.f * pr[q2]), 0.25f * ((p0[q2] - p2[q2]) + 2.f * pi[q2])};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int o = ((oz + k) * fn[1] + (oy + a)) * fn[2] + ox + b;
-                        atomicAdd(num + o, wgt * v[k]);
-                        atomicAdd(den + o, wgt);
-                    }
+                    for (int k = 0; k < 4; ++k)
+                        atomicAdd(num + ((oz + k) * fn[1] + (oy + a)) * fn[2] + ox + b, wgt * v[k]);
                 }
+            atomicAdd(org + (oz * fn[1] + oy) * fn[2] + ox, wgt);
         }
         __syncwarp();
     }
     __syncthreads();
-    for (int q = tid; q < nvox; q += blockDim.x) {
-        const float d = den[q];
+    // denominator: the weights of every cube covering a voxel = a 4 x 4 x 4 box sum of the origin weights
+    for (int q = tid; q < nvox; q += blockDim.x) {                 // along x
+        const int xx = q % fn[2];
+        float s = 0.f;
+        for (int d = 0; d < 4 && d <= xx; ++d) s += org[q - d];
+        tmp[q] = s;
+    }
+    __syncthreads();
+    for (int q = tid; q < nvox; q += blockDim.x) {                 // along y
+        const int yy = (q / fn[2]) % fn[1];
+        float s = 0.f;
+        for (int d = 0; d < 4 && d <= yy; ++d) s += tmp[q - d * fn[2]];
+        org[q] = s;
+    }
+    __syncthreads();
+    for (int q = tid; q < nvox; q += blockDim.x) {                 // along z, then into the volume
+        const int zz = q / (fn[1] * fn[2]);
+        float d = 0.f;
+        for (int k = 0; k < 4 && k <= zz; ++k) d += org[q - k * fn[1] * fn[2]];
         if (d == 0.f) continue;
-        const int zz = q / (fn[1] * fn[2]), rem = q - zz * (fn[1] * fn[2]);
+        const int rem = q - zz * (fn[1] * fn[2]);
         const int yy = rem / fn[2], xx = rem - (rem / fn[2]) * fn[2];
         const long long o = (long long)(f0[0] + zz) * plane + (long long)(f0[1] + yy) * g.W + f0[2] + xx;
         atomicAdd(A.num + o, num[q]);
@@ -688,24 +732,36 @@ size_t volume_filter_smem_bytes(const VolGeo& g) {
     for (int d = 0; d < 3; ++d) fn[d] = (VTR - 1) * g.s + ext[d] + VPS - 1;
     const int FXp = ((fn[2] + 3) & ~3) + 4;
     const size_t nfb = (size_t)fn[0] * fn[1] * FXp;
-    return kHcBytes + ((nfb + 15) & ~(size_t)15) + sizeof(float) * 2 * (size_t)fn[0] * fn[1] * fn[2];
+    return kHcBytes + ((nfb + 15) & ~(size_t)15) + sizeof(float) * 3 * (size_t)fn[0] * fn[1] * fn[2];
+}
+
+template <int K>
+static cudaError_t launch_volume_filter_k(const VolFilterArgs& a, int ntiles, size_t smem, cudaStream_t s) {
+    static int configured = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured != dev) {
+        e = cudaFuncSetAttribute(volume_filter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e != cudaSuccess) return e;
+        configured = dev;
+    }
+    volume_filter_kernel<K><<<ntiles, kVolWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_volume_filter(const VolFilterArgs& a, cudaStream_t s) {
     const VolGeo& g = a.g;
     const int ntiles = ((g.nrz + VTR - 1) / VTR) * ((g.nry + VTR - 1) / VTR) * ((g.nrx + VTR - 1) / VTR);
     const size_t smem = volume_filter_smem_bytes(g);
-    static int configured = -1;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (configured != dev) {
-        e = cudaFuncSetAttribute(volume_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        if (e != cudaSuccess) return e;
-        configured = dev;
+    switch (g.K) {
+        case 2: return launch_volume_filter_k<2>(a, ntiles, smem, s);
+        case 4: return launch_volume_filter_k<4>(a, ntiles, smem, s);
+        case 8: return launch_volume_filter_k<8>(a, ntiles, smem, s);
+        case 16: return launch_volume_filter_k<16>(a, ntiles, smem, s);
+        case 32: return launch_volume_filter_k<32>(a, ntiles, smem, s);
     }
-    volume_filter_kernel<<<ntiles, kVolWarps * 32, smem, s>>>(a);
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_volume_finalize(const float* num, const float* den, long long n, float* out, cudaStream_t s) {

@@ -1,7 +1,7 @@
 """Batched basis projection (Sec. III-B.2, Eq. (forward transform) before the Haar step) on the GPU.
 
 htsvd_project_patches runs S = U^T * P * V of a batch of patches as one dense contraction on the
-tensor cores (patch bytes exact in BF16, the basis matrix split in three BF16 pieces, FP32
+tensor cores (patch bytes exact in FP16, the basis matrix split in two FP16 pieces, FP32
 accumulation); htsvd_internal_project_simt runs the structured per-slice FP32 form on the CUDA cores.
 Both are compared with the oracle's patch_forward (FP64, its own bases) patch by patch. The bar is a
 quarter of the group filter's guard band per patch: |S_gpu - S_oracle| <= 2^-21 ||P||_F, so that a
