@@ -428,6 +428,33 @@ def make_workload(name):
 
         return Workload(name, cfg, 176 * 208 * 176 / 1e6, n, 4, 32, [noisy], step, 176 * 208 * 176 * 4), \
             synth.quantize(clean)
+    if name == "proj512all":
+        # the batched basis projection of every patch position of the 512x512x3 image (505 x 505 =
+        # 255,025 patches, an im2col batch), tensor cores against the structured FP32 form
+        clean, noisy, _, prm = synth.workload_rgb512()
+        setup = {}
+        cfg = {"workload": "projection_rgb512_every_position", "image": "512x512x3 uint8",
+               "noise": "poisson-gaussian a=0.01 b=15^2", "patches_per_step": 505 * 505,
+               "form": "S = U^T * P * V of every 8x8x3 patch position (192 FP32 coefficients each), tensor cores: "
+                       "dense 192x192 contraction, matrix split in two FP16 pieces, im2col tiles"}
+
+        def prepare(x):
+            if "basis" not in setup:
+                _, info = H.denoise(x, None, prm, return_info=True, basis=True)
+                setup["basis"] = info["basis"].reshape(-1).contiguous()
+                setup["out"] = torch.empty((505 * 505, 192), dtype=torch.float32, device="cuda")
+            return setup
+
+        def step(d):
+            st = prepare(d[0])
+            return [H.project_patches(d[0], None, st["basis"], out=st["out"])]
+
+        def structured(d):
+            st = prepare(d[0])
+            return [H.project_patches(d[0], None, st["basis"], out=st["out"], structured=True)]
+
+        return Workload(name, cfg, 512 * 512 / 1e6, 505 * 505, 3, 1, [noisy], step, 505 * 505 * 192 * 4,
+                        structured, "structured_fp32_cuda_cores"), None
     if name == "proj512":
         # the batched basis projection of every patch of every group of the 512x512x3 workload (64,009
         # groups x 32 members), on the tensor cores; compared with the structured FP32 form on the CUDA cores
@@ -779,7 +806,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rgb4k", choices=["rgb512", "gray128", "rgb4k", "rgb1080", "hsi696", "batch64", "vjp8", "adaptive512",
-                                                      "video1080", "sweep512", "sure512", "tunew512", "proj512", "mri176"])
+                                                      "video1080", "sweep512", "sure512", "tunew512", "proj512", "proj512all", "mri176"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

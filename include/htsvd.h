@@ -276,7 +276,9 @@ htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, in
  * transform) before the Haar transform along the group mode; Sec. II-C, Def. T-product): for each
  * of n patches, S = U^T * P * V of the ps x ps x C uint8 patch P whose top-left corner is d_pos[t]
  * (linear index y * W + x), i.e. per channel-Fourier slice f, U_f^H P_f V_f, then the inverse DFT
- * along the channel mode. d_img: H x W x C uint8 (DEVICE, 4-byte aligned); d_pos: n int32 (DEVICE);
+ * along the channel mode. d_img: H x W x C uint8 (DEVICE, 4-byte aligned); d_pos: n int32 (DEVICE), or
+ * NULL for every position of the image, row-major over the (H - 7) x (W - 7) top-left corners (n must
+ * then be (H - 7)(W - 7); the kernel stages the image rows a tile of positions shares, im2col-style);
  * d_basis: the FP64 bases in the layout of htsvd_params.d_basis_out (DEVICE; e.g. from htsvd_denoise
  * of the same image); d_coef: n x 64 C float32 (DEVICE, 16-byte aligned), coefficient
  * (i * 8 + j) * C + c of patch t at d_coef[t * 64 C + ...] (the order of the mask bits).
@@ -286,8 +288,9 @@ htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, in
  * coefficients carry an FP32-level error (tested against 2^-21 of the patch norm). A position whose patch does not
  * lie inside the image gives NaN coefficients. d_flag (DEVICE, may be NULL): bit 0 is set if a wait
  * for the tensor cores ran out (about two seconds; the affected tile is not written).
- * Errors: INVALID_ARG for C not 1 or 3, H or W < 8, n < 0, a null pointer with n > 0, or a
- * misaligned d_img or d_coef; UNSUPPORTED when H W C reaches 2^31. Asynchronous on stream. */
+ * Errors: INVALID_ARG for C not 1 or 3, H or W < 8, n < 0, a null image, basis or output pointer with
+ * n > 0, a null d_pos with n other than (H - 7)(W - 7), or a misaligned d_img or d_coef;
+ * UNSUPPORTED when H W C reaches 2^31. Asynchronous on stream. */
 htsvd_status htsvd_project_patches(const uint8_t* d_img, int32_t H, int32_t W, int32_t C, const int32_t* d_pos,
                                    int64_t n, const double* d_basis, float* d_coef, int32_t* d_flag,
                                    cudaStream_t stream);

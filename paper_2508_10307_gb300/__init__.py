@@ -468,7 +468,8 @@ def denoise_vjp(x, sigma, idx, w, out, grad_out, params=None, want_grad_w=True, 
 
 def project_patches(img, pos, basis, *, out=None, flag=None, stream=None, structured=False):
     """Coefficients S = U^T * P * V (64 C per patch, mask-bit order) of the 8 x 8 patches of a uint8
-    HWC image at linear top-left positions pos (int32), with the FP64 bases `basis` (the layout of
+    HWC image at linear top-left positions pos (int32), or of every position (row-major over the
+    (H - 7) x (W - 7) corners) when pos is None, with the FP64 bases `basis` (the layout of
     denoise(..., basis=True)). The tensor-core path by default; structured=True runs the per-slice
     FP32 form on the CUDA cores (internal comparison hook)."""
     lib = _lib.load()
@@ -477,12 +478,15 @@ def project_patches(img, pos, basis, *, out=None, flag=None, stream=None, struct
     if img.dtype != torch.uint8:
         raise TypeError("project_patches expects a uint8 image")
     H, W, C = img.shape
-    pos = _need(pos.contiguous().view(-1), "pos", (pos.numel(),), torch.int32, img)
+    if pos is None:
+        n = (H - 7) * (W - 7)
+    else:
+        pos = _need(pos.contiguous().view(-1), "pos", (pos.numel(),), torch.int32, img)
+        n = pos.numel()
     basis = _need(basis.contiguous(), "basis", (2 * C * 64 * 2,) if basis.dim() == 1 else tuple(basis.shape),
                   torch.float64, img)
     if basis.numel() != 2 * C * 64 * 2:
         raise ValueError(f"basis must hold {2 * C * 64 * 2} doubles")
-    n = pos.numel()
     if out is None:
         out = torch.empty((n, 64 * C), dtype=torch.float32, device=img.device)
     out = _need(out, "out", (n, 64 * C), torch.float32, img)

@@ -1293,7 +1293,8 @@ static htsvd_status check_projection(const uint8_t* d_img, int32_t H, int32_t W,
     if (H < PS || W < PS || n < 0) return HTSVD_ERR_INVALID_ARG;
     if ((int64_t)H * W * C >= ((int64_t)1 << 31)) return HTSVD_ERR_UNSUPPORTED;
     if (n == 0) return HTSVD_OK;
-    if (!d_img || !d_pos || !d_basis || !d_coef) return HTSVD_ERR_INVALID_ARG;
+    if (!d_img || !d_basis || !d_coef) return HTSVD_ERR_INVALID_ARG;
+    if (!d_pos && n != (int64_t)(H - PS + 1) * (W - PS + 1)) return HTSVD_ERR_INVALID_ARG;
     if (((uintptr_t)d_img & 3) || ((uintptr_t)d_coef & 15)) return HTSVD_ERR_INVALID_ARG;
     return HTSVD_OK;
 }

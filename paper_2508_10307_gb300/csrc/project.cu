@@ -53,6 +53,12 @@ struct ProjDims {
     static constexpr int POS_OFF = 2 * A_BYTES + kPieces * B_PIECE;   // [2][128] int32 patch byte offsets
     static constexpr int BAR_OFF = POS_OFF + 2 * kTileM * 4;    // two mbarriers, then the TMEM slot
     static constexpr int SMEM = BAR_OFF + 32;
+    // every-position batches: the eight image rows of a tile staged as words (their first byte shifted
+    // by up to 3), SW words per row
+    static constexpr int SW = (((kTileM + PS - 1) * C + 6) / 4 + 3) & ~3;
+    static constexpr int STAGE_OFF = 2 * A_BYTES + kPieces * B_PIECE;
+    static constexpr int DBAR_OFF = STAGE_OFF + PS * SW * 4;
+    static constexpr int SMEM_DENSE = DBAR_OFF + 32;
 };
 static_assert(ProjDims<3>::SMEM <= 232448, "projection tile does not fit shared memory");
 
@@ -249,6 +255,50 @@ __device__ __forceinline__ void gather_store(const GatherRegs& R, int rowbytes, 
     }
 }
 
+// The MMAs of one tile: D[128 x N] = A[128 x K] B^T summed over the pieces (smallest first),
+// committed to the tile's mbarrier. Issued by one thread.
+template <int C>
+__device__ __forceinline__ void issue_tile_mmas(uint32_t a0, uint32_t b0, uint32_t d, uint32_t bar) {
+    using Dm = ProjDims<C>;
+    constexpr uint32_t kIdesc = idesc_f16(kTileM, Dm::NH);
+    uint32_t acc = 0;
+#pragma unroll 1
+    for (int p = kPieces - 1; p >= 0; --p) {
+#pragma unroll
+        for (int s = 0; s < Dm::KSTEPS; ++s) {
+            const uint64_t ad = smem_desc(a0 + s * 2 * Dm::LBO_A, Dm::LBO_A, 128);
+            const uint64_t bd = smem_desc(b0 + p * Dm::B_PIECE + s * 2 * Dm::LBO_B, Dm::LBO_B, 128);
+            mma_f16(d, ad, bd, kIdesc, acc);
+            acc = 1;
+        }
+    }
+    mma_commit(bar);
+}
+
+// Copies this thread's share of a tile's accumulator (TMEM lanes 32 (warp % 4) .., NH / 4 columns
+// from (warp / 4) NH / 4) to row `row` of the output (nothing if row < 0; NaN if !valid).
+template <int C>
+__device__ __forceinline__ void read_out_tile(uint32_t tacc, int warp, long long row, bool valid, int half,
+                                              float* __restrict__ coef) {
+    using Dm = ProjDims<C>;
+    const int q = warp & 3;
+    const int cb = (warp >> 2) * (Dm::NH / 4);
+    const uint32_t ta = tacc + ((uint32_t)(q * 32) << 16) + cb;
+    float* dst = coef + row * Dm::D + half * Dm::NH + cb;
+    constexpr float unscale = 1.0f / kSplitScale;
+#pragma unroll
+    for (int c = 0; c < Dm::NH / 4; c += 8) {
+        float v[8];
+        tmem_ld8(ta + c, v);
+        if (row >= 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = valid ? v[i] * unscale : __int_as_float(0x7fc00000);
+            *reinterpret_cast<float4*>(dst + c) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(dst + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        }
+    }
+}
+
 template <int C>
 __global__ void __launch_bounds__(kTcThreads, 1)
 project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* __restrict__ pos, long long n,
@@ -289,7 +339,6 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    constexpr uint32_t kIdesc = idesc_f16(kTileM, Dm::NH);
 
     // Software pipeline: the image words of tile t + 2 stride are loaded into the register set that
     // tile t was just stored from, so every load has a whole iteration (the MMAs of tile t and the
@@ -316,27 +365,13 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (have && tid == 0) {
-            const uint32_t a0 = smem_u32(sA + b * Dm::A_BYTES), b0 = smem_u32(sB);
-            const uint32_t d = tmem + b * Dm::ACC_COLS;
-            uint32_t acc = 0;
-#pragma unroll 1
-            for (int p = kPieces - 1; p >= 0; --p) {            // smaller piece first
-#pragma unroll
-                for (int s = 0; s < Dm::KSTEPS; ++s) {
-                    const uint64_t ad = smem_desc(a0 + s * 2 * Dm::LBO_A, Dm::LBO_A, 128);
-                    const uint64_t bd = smem_desc(b0 + p * Dm::B_PIECE + s * 2 * Dm::LBO_B, Dm::LBO_B, 128);
-                    mma_f16(d, ad, bd, kIdesc, acc);
-                    acc = 1;
-                }
-            }
-            mma_commit(smem_u32(&bars[b]));
-        }
+        if (have && tid == 0)
+            issue_tile_mmas<C>(smem_u32(sA + b * Dm::A_BYTES), smem_u32(sB), tmem + b * Dm::ACC_COLS,
+                               smem_u32(&bars[b]));
         if (t + 2 * stride < ntiles) gather_fetch<C>(img, totali, rowbytes, pos, n, H, W, t + 2 * stride, g, l, R);
         if (it > 0) {   // read out tile t - stride (buffer b ^ 1)
             const int pb = b ^ 1;
-            const int q = warp & 3;
-            const int m = q * 32 + lane;
+            const int m = (warp & 3) * 32 + lane;
             const long long P = (t - stride) * kTileM + m;
             // read before the barrier: once every thread has passed it, the next tile's offsets may
             // overwrite this buffer
@@ -345,21 +380,7 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
             ok = __syncthreads_and(done) != 0;
             if (!ok) return false;
             tc_fence_after();
-            const int cb = (warp >> 2) * (Dm::NH / 4);       // four warps per lane quarter, NH / 4 columns each
-            const uint32_t ta = tmem + pb * Dm::ACC_COLS + ((uint32_t)(q * 32) << 16) + cb;
-            float* dst = coef + P * Dm::D + half * Dm::NH + cb;
-            constexpr float unscale = 1.0f / kSplitScale;
-#pragma unroll
-            for (int c = 0; c < Dm::NH / 4; c += 8) {
-                float v[8];
-                tmem_ld8(ta + c, v);
-                if (P < n) {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) v[i] = valid ? v[i] * unscale : __int_as_float(0x7fc00000);
-                    *reinterpret_cast<float4*>(dst + c) = make_float4(v[0], v[1], v[2], v[3]);
-                    *reinterpret_cast<float4*>(dst + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
-                }
-            }
+            read_out_tile<C>(tmem + pb * Dm::ACC_COLS, warp, P < n ? P : -1, valid, half, coef);
         }
         tc_fence_before();
         if (!have) return false;
@@ -373,6 +394,140 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
     if (!ok) {
         // a read-out wait ran out: report it, and give the tile issued last the same bounded wait before
         // the tensor memory is released
+        if (tid == 0 && flag) atomicOr(flag, 1);
+        if ((blockIdx.x >> 1) + it * stride < ntiles)
+            mbar_wait_bounded(smem_u32(&bars[it & 1]), (uint32_t)((it >> 1) & 1));
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Dm::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// Every patch position of the image, row-major over the (H - 7) x (W - 7) grid of top-left corners
+// (an im2col batch): a tile is 128 consecutive positions of one grid row, so the eight image rows it
+// covers hold all its bytes; each thread loads two words of them, coalesced, for the next tile while
+// the current one is multiplied, and the A tile is built from the staged rows in shared memory.
+template <int C>
+__global__ void __launch_bounds__(kTcThreads, 1)
+project_tc_dense_kernel(const uint8_t* __restrict__ img, int H, int W, const uint4* __restrict__ pieces,
+                        float* __restrict__ coef, int* __restrict__ flag) {
+    using Dm = ProjDims<C>;
+    constexpr int NW = 2 * C;
+    constexpr int SW = Dm::SW;
+    static_assert(PS * SW <= 2 * kTcThreads, "two staged words per thread");
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + 2 * Dm::A_BYTES;
+    uint32_t* sS = reinterpret_cast<uint32_t*>(smem + Dm::STAGE_OFF);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Dm::DBAR_OFF);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Dm::DBAR_OFF + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = tid >> 3, l = tid & 7;
+    const int half = blockIdx.x & 1;
+    const long long stride = gridDim.x >> 1;
+    const int npx = W - PS + 1, npy = H - PS + 1;
+    const int tpr = (npx + kTileM - 1) / kTileM;                 // tiles per row of positions
+    const long long ntiles = (long long)npy * tpr;
+    const int rowbytes = W * C;
+    const long long total = (long long)H * rowbytes;
+
+    {
+        const uint4* src = pieces + (size_t)half * (kPieces * Dm::B_PIECE / 16);
+        uint4* dst = reinterpret_cast<uint4*>(sB);
+        for (int i = tid; i < kPieces * Dm::B_PIECE / 16; i += kTcThreads) dst[i] = src[i];
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&bars[0]), 1);
+        mbar_init(smem_u32(&bars[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(Dm::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    // word w of staged row a of tile tt: the image word at ((y + a) W + x0) C rounded down to 4, + 4 w
+    auto fetch = [&](long long tt, uint32_t (&wd)[2]) {
+        const int y = (int)(tt / tpr), x0 = (int)(tt % tpr) * kTileM;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int idx = tid + h * kTcThreads;
+            wd[h] = 0;
+            if (idx < PS * SW) {
+                const int a = idx / SW, w = idx - (idx / SW) * SW;
+                const long long base = ((long long)(y + a) * rowbytes + (long long)x0 * C) & ~3ll;
+                wd[h] = image_word(img, base + 4 * w, total);
+            }
+        }
+    };
+    uint32_t wd[2];
+    const long long t0 = blockIdx.x >> 1;
+    if (t0 < ntiles) fetch(t0, wd);
+    bool ok = true;
+    long long it = 0;
+    for (long long t = t0;; t += stride, ++it) {
+        const bool have = t < ntiles;        // uniform over the CTA
+        const int b = (int)(it & 1);
+        if (have) {
+            if (tid < PS * SW) sS[tid] = wd[0];
+            if (tid + kTcThreads < PS * SW) sS[tid + kTcThreads] = wd[1];
+        }
+        __syncthreads();
+        if (have) {
+            const int y = (int)(t / tpr), x0 = (int)(t % tpr) * kTileM;
+            const int cnt = min(kTileM, npx - x0);
+            uint8_t* sa = sA + b * Dm::A_BYTES;
+#pragma unroll 4
+            for (int p = 0; p < 16; ++p) {                // pass p: patch row p / 2 of patches g, 64 + g
+                const int a = p >> 1, m = ((p & 1) << 6) | g;
+                if (l < NW) {
+                    uint2 v = make_uint2(0u, 0u);
+                    if (m < cnt) {
+                        const int bo = (int)(((long long)(y + a) * rowbytes + (long long)x0 * C) & 3) + m * C + 4 * l;
+                        const uint32_t* row = sS + a * SW + (bo >> 2);
+                        const uint32_t bytes = __funnelshift_r(row[0], row[1], (bo & 3) * 8);
+                        v.x = f16x2_of_bytes(bytes, 0x5150u);
+                        v.y = f16x2_of_bytes(bytes, 0x5352u);
+                    }
+                    *reinterpret_cast<uint2*>(sa + (a * C + (l >> 1)) * Dm::LBO_A + m * 16 + (l & 1) * 8) = v;
+                }
+            }
+            fence_async_smem();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (have && tid == 0)
+            issue_tile_mmas<C>(smem_u32(sA + b * Dm::A_BYTES), smem_u32(sB), tmem + b * Dm::ACC_COLS,
+                               smem_u32(&bars[b]));
+        if (t + stride < ntiles) fetch(t + stride, wd);
+        if (it > 0) {   // read out tile t - stride (buffer b ^ 1)
+            const int pb = b ^ 1;
+            const long long tp = t - stride;
+            const int y = (int)(tp / tpr), x0 = (int)(tp % tpr) * kTileM;
+            const int m = (warp & 3) * 32 + lane;
+            const long long row = m < min(kTileM, npx - x0) ? (long long)y * npx + x0 + m : -1;
+            const bool done = mbar_wait_bounded(smem_u32(&bars[pb]), (uint32_t)(((it - 1) >> 1) & 1));
+            ok = __syncthreads_and(done) != 0;
+            if (!ok) break;
+            tc_fence_after();
+            read_out_tile<C>(tmem + pb * Dm::ACC_COLS, warp, row, true, half, coef);
+        }
+        tc_fence_before();
+        if (!have) break;
+    }
+    tc_fence_before();
+    if (!ok) {
         if (tid == 0 && flag) atomicOr(flag, 1);
         if ((blockIdx.x >> 1) + it * stride < ntiles)
             mbar_wait_bounded(smem_u32(&bars[it & 1]), (uint32_t)((it >> 1) & 1));
@@ -419,7 +574,8 @@ project_simt_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t
         __syncthreads();
         {   // stage row l of patch pl: 2C words from the 2C + 1 aligned words that cover it
             const long long P = base + pl;
-            const int o = P < n ? patch_offset(pos[P], H, W, C) : -1;
+            const int o = P < n ? patch_offset(pos ? pos[P] : (int)(P / (W - PS + 1)) * W + (int)(P % (W - PS + 1)), H, W, C)
+                                : -1;
             if (l == 0) sOk[pl] = o >= 0 ? 1 : 0;
             const long long ob = (long long)(o >= 0 ? o : 0) + (long long)l * rowbytes;
             const int sh = (int)(ob & 3) * 8;
@@ -540,14 +696,22 @@ static cudaError_t launch_tc_c(const uint8_t* img, int H, int W, const int32_t* 
     if (e != cudaSuccess) return e;
     if (configured_device != dev) {
         e = cudaFuncSetAttribute(project_tc_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, Dm::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(project_tc_dense_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Dm::SMEM_DENSE);
         if (e != cudaSuccess) return e;
         configured_device = dev;
     }
     const int half_grid = device_sm_count() / 2 > 0 ? device_sm_count() / 2 : 1;
-    const long long ntiles = (n + kTileM - 1) / kTileM;
+    const long long ntiles = pos ? (n + kTileM - 1) / kTileM
+                                 : (long long)(H - PS + 1) * ((W - PS + 1 + kTileM - 1) / kTileM);
     const int g = (int)(ntiles < half_grid ? ntiles : half_grid);
-    project_tc_kernel<C><<<2 * g, kTcThreads, Dm::SMEM, s>>>(img, H, W, pos, n, static_cast<const uint4*>(pieces),
-                                                                coef, flag);
+    if (pos)
+        project_tc_kernel<C><<<2 * g, kTcThreads, Dm::SMEM, s>>>(img, H, W, pos, n, static_cast<const uint4*>(pieces),
+                                                                  coef, flag);
+    else
+        project_tc_dense_kernel<C><<<2 * g, kTcThreads, Dm::SMEM_DENSE, s>>>(img, H, W,
+                                                                             static_cast<const uint4*>(pieces), coef, flag);
     return cudaGetLastError();
 }
 

@@ -122,6 +122,48 @@ def _patch_norms2(x, pos):
     return out
 
 
+@pytest.mark.parametrize("shape", [(40, 48, 1), (72, 200, 3), (33, 41, 3), (19, 301, 3)])
+def test_projection_of_every_position_matches_oracle(shape):
+    """pos = None: every top-left corner, row-major (the im2col batch: tiles of 128 positions of one
+    row, the last of a row ragged; rows narrower and wider than a tile)."""
+    Hh, Ww, C = shape
+    clean = synth.clean_image(Hh, Ww, C, 90 + Ww)
+    noisy = synth.add_gaussian(clean, 20.0, 90 + Ww)
+    x, _, basis = _gpu_setup(noisy, dict(ps=8, stride=3, window=7, K=4))
+    tc = H.project_patches(x, None, basis)
+    st = H.project_patches(x, None, basis, structured=True)
+    torch.cuda.synchronize()
+    ys, xs = np.mgrid[0:Hh - 7, 0:Ww - 7]
+    pos = (ys * Ww + xs).ravel()
+    ref, norms = _oracle_coefficients(noisy, dict(ps=8, stride=3, window=7, K=4), pos)
+    _check(tc.cpu().numpy(), ref, norms, "tensor cores, every position")
+    _check(st.cpu().numpy(), ref, norms, "CUDA cores, every position")
+
+
+def test_projection_of_every_position_at_the_benchmarked_size():
+    """Every position of the 512x512x3 workload (255,025 patches) as the benchmark times it: a sample
+    against the oracle, the two forms against each other everywhere, two calls bitwise equal, and
+    the same coefficients as the position-list form."""
+    clean, noisy, _, prm = synth.workload_rgb512()
+    x = torch.from_numpy(noisy).cuda()
+    _, info = H.denoise(x, None, prm, return_info=True, basis=True)
+    basis = info["basis"].reshape(-1).contiguous()
+    tc = H.project_patches(x, None, basis)
+    tc2 = H.project_patches(x, None, basis)
+    st = H.project_patches(x, None, basis, structured=True)
+    ys, xs = np.mgrid[0:505, 0:505]
+    pos = torch.from_numpy((ys * 512 + xs).ravel().astype(np.int32)).cuda()
+    lst = H.project_patches(x, pos, basis)
+    torch.cuda.synchronize()
+    assert torch.equal(tc, tc2) and torch.equal(tc, lst)
+    rng = np.random.default_rng(7)
+    pick = np.sort(rng.choice(tc.shape[0], 2000, replace=False))
+    ref, norms = _oracle_coefficients(noisy, prm, pos.cpu().numpy()[pick])
+    _check(tc.cpu().numpy()[pick], ref, norms, "tensor cores")
+    pn = torch.sqrt(_patch_norms2(x, pos)).clamp_min(1.0)
+    assert ((tc - st).abs().amax(dim=1) / pn).max().item() <= 2 * BAR
+
+
 def test_projection_empty_and_bad_arguments():
     noisy = synth.add_gaussian(synth.clean_image(24, 24, 3, 9), 15.0, 9)
     x = torch.from_numpy(noisy).cuda()
