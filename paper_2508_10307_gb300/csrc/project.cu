@@ -12,10 +12,10 @@
 //   T = T_hi + T_lo (T_lo the rounding of what T_hi leaves: 22 significant bits), so two products
 //   per K step give an FP32-level result. The pieces of all of T would take 2 x 72 KB of shared
 //   memory at C = 3 beside the A tiles, so each CTA holds the pieces of one half of the
-//   coefficients (N = 32 C) and the grid runs both halves; the A tile (128 patches x 64 C FP16,
-//   gathered from the image by 16 warps) is double-buffered, the accumulator is double-buffered in
-//   tensor memory, and one thread issues the MMAs of tile t while the CTA loads the image words of
-//   tile t + 1 and reads tile t - 1 out of tensor memory.
+//   coefficients (N = 32 C) and the grid runs both halves. Warp-specialised: eleven warps gather
+//   128-patch A tiles (FP16) into a two-stage ring, one thread issues the MMAs into one of two TMEM
+//   accumulators, four warps read the accumulators out; mbarriers hand the stages and accumulators
+//   over. Batches are a list of positions or every position of the image (row-major corners).
 // * project_simt_kernel: the structured per-slice form in FP32 on the CUDA cores (channel DFT,
 //   U_f^H X_f on patch columns, (.) V_f on patch rows, inverse channel DFT), the form the group
 //   filter uses, for comparison.
@@ -51,14 +51,8 @@ struct ProjDims {
     static constexpr int ACC_COLS = C == 3 ? 128 : 32;   // TMEM column stride of the two accumulators
     static constexpr int TMEM_COLS = 2 * ACC_COLS;       // power of two >= 32
     static constexpr int POS_OFF = 2 * A_BYTES + kPieces * B_PIECE;   // [2][128] int32 patch byte offsets
-    static constexpr int BAR_OFF = POS_OFF + 2 * kTileM * 4;    // two mbarriers, then the TMEM slot
-    static constexpr int SMEM = BAR_OFF + 32;
-    // every-position batches: the eight image rows of a tile staged as words (their first byte shifted
-    // by up to 3), SW words per row
-    static constexpr int SW = (((kTileM + PS - 1) * C + 6) / 4 + 3) & ~3;
-    static constexpr int STAGE_OFF = 2 * A_BYTES + kPieces * B_PIECE;
-    static constexpr int DBAR_OFF = STAGE_OFF + PS * SW * 4;
-    static constexpr int SMEM_DENSE = DBAR_OFF + 32;
+    static constexpr int BAR_OFF = POS_OFF + 2 * kTileM * 4;    // eight mbarriers, the TMEM slot, the abort word
+    static constexpr int SMEM = BAR_OFF + 80;
 };
 static_assert(ProjDims<3>::SMEM <= 232448, "projection tile does not fit shared memory");
 
@@ -204,61 +198,48 @@ __device__ __forceinline__ uint32_t f16x2_of_bytes(uint32_t w, uint32_t sel) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// One tile's share of the gather for this lane. Groups of 8 lanes take one patch row at a time:
-// lanes 0 .. 2C - 1 each convert 4 bytes of the row (8 C bytes), lane 2C loads the word after the row
-// for the byte shift. Lane group g covers patches g and 64 + g of the tile, rows 0..7 (16 words).
-struct GatherRegs {
-    int o[2];            // byte offsets of the two patches (-1: none)
-    uint32_t w[16];      // word of pass p: patch p & 1, row p >> 1
-};
-
-template <int C>
-__device__ __forceinline__ void gather_fetch(const uint8_t* __restrict__ img, int total, int rowbytes,
-                                             const int32_t* __restrict__ pos, long long n, int H, int W,
-                                             long long tile, int g, int l, GatherRegs& R) {
-    constexpr int NW = 2 * C;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const long long P = tile * kTileM + h * 64 + g;
-        R.o[h] = P < n ? patch_offset(__ldg(pos + P), H, W, C) : -1;
+// Waits for the phase of `parity` of an mbarrier, giving up when the CTA's abort word is set or after
+// about two seconds (then it sets the abort word). Returns false on giving up.
+__device__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_word) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (int i = 0; i < (1 << 28); ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_word) return false;
+        if (global_ns() - t0 > 2000000000ull) break;
     }
-#pragma unroll
-    for (int p = 0; p < 16; ++p) {
-        const int op = R.o[p & 1];
-        R.w[p] = 0;
-        if (op >= 0 && l <= NW) {
-            const int wa = ((op + (p >> 1) * rowbytes) & ~3) + 4 * l;       // < H W C < 2^31
-            R.w[p] = wa + 4 <= total ? __ldg(reinterpret_cast<const uint32_t*>(img + wa))
-                                     : image_word(img, wa, total);
-        }
-    }
+    *abort_word = 1;
+    return false;
 }
 
-// Converts the fetched words into the A stage (no-swizzle K-major: plane k chunk, row patch, 8 FP16).
-template <int C>
-__device__ __forceinline__ void gather_store(const GatherRegs& R, int rowbytes, int g, int l, uint8_t* sa) {
-    using Dm = ProjDims<C>;
-    constexpr int NW = 2 * C;
-#pragma unroll
-    for (int p = 0; p < 16; ++p) {
-        const uint32_t wn = __shfl_down_sync(0xffffffffu, R.w[p], 1, 8);
-        const int op = R.o[p & 1], a = p >> 1, m = ((p & 1) << 6) | g;
-        if (l < NW) {
-            uint2 v = make_uint2(0u, 0u);
-            if (op >= 0) {
-                const uint32_t bytes = __funnelshift_r(R.w[p], wn, ((op + a * rowbytes) & 3) * 8);
-                v.x = f16x2_of_bytes(bytes, 0x5150u);
-                v.y = f16x2_of_bytes(bytes, 0x5352u);
-            }
-            *reinterpret_cast<uint2*>(sa + (a * C + (l >> 1)) * Dm::LBO_A + m * 16 + (l & 1) * 8) = v;
-        }
-    }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// The MMAs of one tile: D[128 x N] = A[128 x K] B^T summed over the pieces (smallest first),
-// committed to the tile's mbarrier. Issued by one thread.
+// Eight bytes of the image at byte offset o (any alignment) as eight FP16 values (exact).
+__device__ __forceinline__ uint4 f16x8_of_image(const uint8_t* __restrict__ img, int o, int total) {
+    const int a = o & ~3;
+    uint32_t w0, w1, w2;
+    if (a + 12 <= total) {
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(img + a);
+        w0 = __ldg(p);
+        w1 = __ldg(p + 1);
+        w2 = __ldg(p + 2);
+    } else {
+        w0 = image_word(img, a, total);
+        w1 = image_word(img, a + 4, total);
+        w2 = image_word(img, a + 8, total);
+    }
+    const int sh = (o & 3) * 8;
+    const uint32_t lo = __funnelshift_r(w0, w1, sh), hi = __funnelshift_r(w1, w2, sh);
+    return make_uint4(f16x2_of_bytes(lo, 0x5150u), f16x2_of_bytes(lo, 0x5352u), f16x2_of_bytes(hi, 0x5150u),
+                      f16x2_of_bytes(hi, 0x5352u));
+}
+
+// The MMAs of one tile: D[128 x N] = A[128 x K] B^T summed over the pieces (smallest first). Issued by
+// one thread; the caller commits.
 template <int C>
-__device__ __forceinline__ void issue_tile_mmas(uint32_t a0, uint32_t b0, uint32_t d, uint32_t bar) {
+__device__ __forceinline__ void issue_tile_mmas(uint32_t a0, uint32_t b0, uint32_t d) {
     using Dm = ProjDims<C>;
     constexpr uint32_t kIdesc = idesc_f16(kTileM, Dm::NH);
     uint32_t acc = 0;
@@ -272,51 +253,55 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t a0, uint32_t b0, uint32
             acc = 1;
         }
     }
-    mma_commit(bar);
 }
 
-// Copies this thread's share of a tile's accumulator (TMEM lanes 32 (warp % 4) .., NH / 4 columns
-// from (warp / 4) NH / 4) to row `row` of the output (nothing if row < 0; NaN if !valid).
-template <int C>
-__device__ __forceinline__ void read_out_tile(uint32_t tacc, int warp, long long row, bool valid, int half,
-                                              float* __restrict__ coef) {
-    using Dm = ProjDims<C>;
-    const int q = warp & 3;
-    const int cb = (warp >> 2) * (Dm::NH / 4);
-    const uint32_t ta = tacc + ((uint32_t)(q * 32) << 16) + cb;
-    float* dst = coef + row * Dm::D + half * Dm::NH + cb;
-    constexpr float unscale = 1.0f / kSplitScale;
-#pragma unroll
-    for (int c = 0; c < Dm::NH / 4; c += 8) {
-        float v[8];
-        tmem_ld8(ta + c, v);
-        if (row >= 0) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = valid ? v[i] * unscale : __int_as_float(0x7fc00000);
-            *reinterpret_cast<float4*>(dst + c) = make_float4(v[0], v[1], v[2], v[3]);
-            *reinterpret_cast<float4*>(dst + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
-        }
+// Byte offset of patch m of tile t (-1: none) and its output row (-1: none). DENSE: tile t is positions
+// x0 .. x0 + 127 of row y of the (H - 7) x (W - 7) corner grid; otherwise patches t * 128 + m of pos.
+template <int C, bool DENSE>
+__device__ __forceinline__ int tile_patch(long long t, int m, const int32_t* __restrict__ pos, long long n, int H,
+                                          int W, int tpr, long long& row) {
+    if (DENSE) {
+        const int npx = W - PS + 1;
+        const int y = (int)(t / tpr), x = (int)(t % tpr) * kTileM + m;
+        if (x >= npx) { row = -1; return -1; }
+        row = (long long)y * npx + x;
+        return (y * W + x) * C;
     }
+    const long long P = t * kTileM + m;
+    if (P >= n) { row = -1; return -1; }
+    row = P;
+    return patch_offset(__ldg(pos + P), H, W, C);
 }
 
-template <int C>
+// Warp-specialised projection (one CTA per SM, 16 warps, each CTA one half of the coefficients):
+//   warps 5..15 gather: patch bytes of tile i -> FP16 A stage i % 2 (one task = 8 bytes of a patch row
+//     -> 16 bytes of a core-matrix row), then arrive on full[i % 2];
+//   warp 4, one thread: waits full[s] and the accumulator's release, issues the tile's MMAs into TMEM
+//     accumulator i % 2, commits to empty[s] (the stage may be refilled) and accfull[b];
+//   warps 0..3 (TMEM lane quarters 0..3): wait accfull[b], read the accumulator out, release it.
+// Every wait is bounded; a wait that runs out sets the CTA's abort word, which ends every role.
+template <int C, bool DENSE>
 __global__ void __launch_bounds__(kTcThreads, 1)
 project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* __restrict__ pos, long long n,
                   const uint4* __restrict__ pieces, float* __restrict__ coef, int* __restrict__ flag) {
     using Dm = ProjDims<C>;
+    constexpr int kProdWarp0 = 5;
+    constexpr int kProdThreads = kTcThreads - kProdWarp0 * 32;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;
     uint8_t* sB = smem + 2 * Dm::A_BYTES;
-    int* sOff = reinterpret_cast<int*>(smem + Dm::POS_OFF);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Dm::BAR_OFF);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Dm::BAR_OFF + 16);
+    int* sOff = reinterpret_cast<int*>(smem + Dm::POS_OFF);                  // [2][128] patch byte offsets
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Dm::BAR_OFF);        // full[2] empty[2] accfull[2] accempty[2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Dm::BAR_OFF + 64);
+    volatile int* abort_word = reinterpret_cast<volatile int*>(smem + Dm::BAR_OFF + 68);
+    volatile int* issued = reinterpret_cast<volatile int*>(smem + Dm::BAR_OFF + 72);   // tiles the MMA thread issued
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = tid >> 3, l = tid & 7;
     const int half = blockIdx.x & 1;
     const long long stride = gridDim.x >> 1;
-    const long long ntiles = (n + kTileM - 1) / kTileM;
-    const long long total = (long long)H * W * C;
+    const int tpr = (W - PS + 1 + kTileM - 1) / kTileM;
+    const long long ntiles = DENSE ? (long long)(H - PS + 1) * tpr : (n + kTileM - 1) / kTileM;
     const int rowbytes = W * C;
+    const int total = H * rowbytes;
 
     {   // this half's pieces of T, one contiguous block in the kernel's smem layout
         const uint4* src = pieces + (size_t)half * (kPieces * Dm::B_PIECE / 16);
@@ -324,11 +309,17 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
         for (int i = tid; i < kPieces * Dm::B_PIECE / 16; i += kTcThreads) dst[i] = src[i];
     }
     if (tid == 0) {
-        mbar_init(smem_u32(&bars[0]), 1);
-        mbar_init(smem_u32(&bars[1]), 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&bars[s]), kProdThreads);          // full: every gather thread
+            mbar_init(smem_u32(&bars[2 + s]), 1);                 // empty: the MMA commit
+            mbar_init(smem_u32(&bars[4 + s]), 1);                 // accfull: the MMA commit
+            mbar_init(smem_u32(&bars[6 + s]), 128);               // accempty: every read-out thread
+        }
+        *abort_word = 0;
+        *issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                      "r"(Dm::TMEM_COLS)
                      : "memory");
@@ -339,201 +330,100 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-
-    // Software pipeline: the image words of tile t + 2 stride are loaded into the register set that
-    // tile t was just stored from, so every load has a whole iteration (the MMAs of tile t and the
-    // read-out of tile t - stride) to arrive.
-    GatherRegs RA, RB;
     const long long t0 = blockIdx.x >> 1;
-    const int totali = (int)total;
-    if (t0 < ntiles) gather_fetch<C>(img, totali, rowbytes, pos, n, H, W, t0, g, l, RA);
-    if (t0 + stride < ntiles) gather_fetch<C>(img, totali, rowbytes, pos, n, H, W, t0 + stride, g, l, RB);
-    bool ok = true;
-    long long it = 0;
-    long long t = t0;
-    auto step = [&](GatherRegs& R) -> bool {
-        const bool have = t < ntiles;        // uniform over the CTA
-        const int b = (int)(it & 1);
-        if (have) {
-            gather_store<C>(R, rowbytes, g, l, sA + b * Dm::A_BYTES);
-            if (l == 0) {
-                sOff[b * kTileM + g] = R.o[0];
-                sOff[b * kTileM + 64 + g] = R.o[1];
+
+    if (warp >= kProdWarp0) {
+        // ---- gather
+        const int pt = tid - kProdWarp0 * 32;
+        long long row;
+        long long i = 0;
+        for (long long t = t0; t < ntiles; t += stride, ++i) {
+            const int s = (int)(i & 1);
+            const bool free_ = i < 2 || mbar_wait_or_abort(smem_u32(&bars[2 + s]), (uint32_t)(((i >> 1) & 1) ^ 1),
+                                                          abort_word);
+            if (free_ && pt < kTileM) sOff[s * kTileM + pt] = tile_patch<C, DENSE>(t, pt, pos, n, H, W, tpr, row);
+            // every gather thread passes this barrier, and all of them leave together if any wait ran out
+            uint32_t all_free;
+            asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                         "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                         : "=r"(all_free)
+                         : "r"((uint32_t)free_), "n"(kProdThreads)
+                         : "memory");
+            if (!all_free) break;
+            uint8_t* sa = sA + s * Dm::A_BYTES;
+#pragma unroll 4
+            for (int task = pt; task < kTileM * PS * C; task += kProdThreads) {
+                const int m = task & (kTileM - 1), r = task >> 7;
+                const int a = r / C, c = r - (r / C) * C;
+                const int o = sOff[s * kTileM + m];
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (o >= 0) v = f16x8_of_image(img, o + a * rowbytes + 8 * c, total);
+                *reinterpret_cast<uint4*>(sa + (a * C + c) * Dm::LBO_A + m * 16) = v;
             }
             fence_async_smem();
+            mbar_arrive(smem_u32(&bars[s]));
+            // the offsets of this stage are read again only by the next use of the stage, after
+            // empty[s]; the gather threads pass the named barrier before rewriting them
         }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (have && tid == 0)
-            issue_tile_mmas<C>(smem_u32(sA + b * Dm::A_BYTES), smem_u32(sB), tmem + b * Dm::ACC_COLS,
-                               smem_u32(&bars[b]));
-        if (t + 2 * stride < ntiles) gather_fetch<C>(img, totali, rowbytes, pos, n, H, W, t + 2 * stride, g, l, R);
-        if (it > 0) {   // read out tile t - stride (buffer b ^ 1)
-            const int pb = b ^ 1;
-            const int m = (warp & 3) * 32 + lane;
-            const long long P = (t - stride) * kTileM + m;
-            // read before the barrier: once every thread has passed it, the next tile's offsets may
-            // overwrite this buffer
-            const bool valid = sOff[pb * kTileM + m] >= 0;
-            const bool done = mbar_wait_bounded(smem_u32(&bars[pb]), (uint32_t)(((it - 1) >> 1) & 1));
-            ok = __syncthreads_and(done) != 0;
-            if (!ok) return false;
-            tc_fence_after();
-            read_out_tile<C>(tmem + pb * Dm::ACC_COLS, warp, P < n ? P : -1, valid, half, coef);
-        }
-        tc_fence_before();
-        if (!have) return false;
-        t += stride;
-        ++it;
-        return true;
-    };
-    while (step(RA) && step(RB)) {
-    }
-    tc_fence_before();
-    if (!ok) {
-        // a read-out wait ran out: report it, and give the tile issued last the same bounded wait before
-        // the tensor memory is released
-        if (tid == 0 && flag) atomicOr(flag, 1);
-        if ((blockIdx.x >> 1) + it * stride < ntiles)
-            mbar_wait_bounded(smem_u32(&bars[it & 1]), (uint32_t)((it >> 1) & 1));
-    }
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Dm::TMEM_COLS)
-                     : "memory");
-    }
-}
-
-// Every patch position of the image, row-major over the (H - 7) x (W - 7) grid of top-left corners
-// (an im2col batch): a tile is 128 consecutive positions of one grid row, so the eight image rows it
-// covers hold all its bytes; each thread loads two words of them, coalesced, for the next tile while
-// the current one is multiplied, and the A tile is built from the staged rows in shared memory.
-template <int C>
-__global__ void __launch_bounds__(kTcThreads, 1)
-project_tc_dense_kernel(const uint8_t* __restrict__ img, int H, int W, const uint4* __restrict__ pieces,
-                        float* __restrict__ coef, int* __restrict__ flag) {
-    using Dm = ProjDims<C>;
-    constexpr int NW = 2 * C;
-    constexpr int SW = Dm::SW;
-    static_assert(PS * SW <= 2 * kTcThreads, "two staged words per thread");
-    extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + 2 * Dm::A_BYTES;
-    uint32_t* sS = reinterpret_cast<uint32_t*>(smem + Dm::STAGE_OFF);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Dm::DBAR_OFF);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Dm::DBAR_OFF + 16);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = tid >> 3, l = tid & 7;
-    const int half = blockIdx.x & 1;
-    const long long stride = gridDim.x >> 1;
-    const int npx = W - PS + 1, npy = H - PS + 1;
-    const int tpr = (npx + kTileM - 1) / kTileM;                 // tiles per row of positions
-    const long long ntiles = (long long)npy * tpr;
-    const int rowbytes = W * C;
-    const long long total = (long long)H * rowbytes;
-
-    {
-        const uint4* src = pieces + (size_t)half * (kPieces * Dm::B_PIECE / 16);
-        uint4* dst = reinterpret_cast<uint4*>(sB);
-        for (int i = tid; i < kPieces * Dm::B_PIECE / 16; i += kTcThreads) dst[i] = src[i];
-    }
-    if (tid == 0) {
-        mbar_init(smem_u32(&bars[0]), 1);
-        mbar_init(smem_u32(&bars[1]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(Dm::TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-
-    // word w of staged row a of tile tt: the image word at ((y + a) W + x0) C rounded down to 4, + 4 w
-    auto fetch = [&](long long tt, uint32_t (&wd)[2]) {
-        const int y = (int)(tt / tpr), x0 = (int)(tt % tpr) * kTileM;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int idx = tid + h * kTcThreads;
-            wd[h] = 0;
-            if (idx < PS * SW) {
-                const int a = idx / SW, w = idx - (idx / SW) * SW;
-                const long long base = ((long long)(y + a) * rowbytes + (long long)x0 * C) & ~3ll;
-                wd[h] = image_word(img, base + 4 * w, total);
+    } else if (warp == 4) {
+        // ---- MMA issue
+        if (lane == 0) {
+            long long i = 0;
+            for (long long t = t0; t < ntiles; t += stride, ++i) {
+                const int s = (int)(i & 1);
+                const uint32_t ph = (uint32_t)((i >> 1) & 1);
+                if (!mbar_wait_or_abort(smem_u32(&bars[s]), ph, abort_word)) break;
+                if (i >= 2 && !mbar_wait_or_abort(smem_u32(&bars[6 + s]), ph ^ 1u, abort_word)) break;
+                tc_fence_after();
+                issue_tile_mmas<C>(smem_u32(sA + s * Dm::A_BYTES), smem_u32(sB), tmem + s * Dm::ACC_COLS);
+                mma_commit(smem_u32(&bars[2 + s]));
+                mma_commit(smem_u32(&bars[4 + s]));
             }
+            *issued = (int)i;
         }
-    };
-    uint32_t wd[2];
-    const long long t0 = blockIdx.x >> 1;
-    if (t0 < ntiles) fetch(t0, wd);
-    bool ok = true;
-    long long it = 0;
-    for (long long t = t0;; t += stride, ++it) {
-        const bool have = t < ntiles;        // uniform over the CTA
-        const int b = (int)(it & 1);
-        if (have) {
-            if (tid < PS * SW) sS[tid] = wd[0];
-            if (tid + kTcThreads < PS * SW) sS[tid + kTcThreads] = wd[1];
-        }
-        __syncthreads();
-        if (have) {
-            const int y = (int)(t / tpr), x0 = (int)(t % tpr) * kTileM;
-            const int cnt = min(kTileM, npx - x0);
-            uint8_t* sa = sA + b * Dm::A_BYTES;
+        __syncwarp();
+    } else {
+        // ---- read-out: warp w holds TMEM lanes 32 w .. 32 w + 31 = patches of the tile
+        const int m = warp * 32 + lane;
+        constexpr float unscale = 1.0f / kSplitScale;
+        long long i = 0;
+        for (long long t = t0; t < ntiles; t += stride, ++i) {
+            const int b = (int)(i & 1);
+            long long row;
+            const int o = tile_patch<C, DENSE>(t, m, pos, n, H, W, tpr, row);
+            const bool got = mbar_wait_or_abort(smem_u32(&bars[4 + b]), (uint32_t)((i >> 1) & 1), abort_word);
+            if (__any_sync(0xffffffffu, !got)) break;
+            tc_fence_after();
+            const uint32_t ta = tmem + b * Dm::ACC_COLS + ((uint32_t)(warp * 32) << 16);
+            float* dst = coef + row * Dm::D + half * Dm::NH;
 #pragma unroll 4
-            for (int p = 0; p < 16; ++p) {                // pass p: patch row p / 2 of patches g, 64 + g
-                const int a = p >> 1, m = ((p & 1) << 6) | g;
-                if (l < NW) {
-                    uint2 v = make_uint2(0u, 0u);
-                    if (m < cnt) {
-                        const int bo = (int)(((long long)(y + a) * rowbytes + (long long)x0 * C) & 3) + m * C + 4 * l;
-                        const uint32_t* row = sS + a * SW + (bo >> 2);
-                        const uint32_t bytes = __funnelshift_r(row[0], row[1], (bo & 3) * 8);
-                        v.x = f16x2_of_bytes(bytes, 0x5150u);
-                        v.y = f16x2_of_bytes(bytes, 0x5352u);
-                    }
-                    *reinterpret_cast<uint2*>(sa + (a * C + (l >> 1)) * Dm::LBO_A + m * 16 + (l & 1) * 8) = v;
+            for (int c = 0; c < Dm::NH; c += 8) {
+                float v[8];
+                tmem_ld8(ta + c, v);
+                if (row >= 0) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = o >= 0 ? v[q] * unscale : __int_as_float(0x7fc00000);
+                    *reinterpret_cast<float4*>(dst + c) = make_float4(v[0], v[1], v[2], v[3]);
+                    *reinterpret_cast<float4*>(dst + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
                 }
             }
-            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(smem_u32(&bars[6 + b]));
         }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (have && tid == 0)
-            issue_tile_mmas<C>(smem_u32(sA + b * Dm::A_BYTES), smem_u32(sB), tmem + b * Dm::ACC_COLS,
-                               smem_u32(&bars[b]));
-        if (t + stride < ntiles) fetch(t + stride, wd);
-        if (it > 0) {   // read out tile t - stride (buffer b ^ 1)
-            const int pb = b ^ 1;
-            const long long tp = t - stride;
-            const int y = (int)(tp / tpr), x0 = (int)(tp % tpr) * kTileM;
-            const int m = (warp & 3) * 32 + lane;
-            const long long row = m < min(kTileM, npx - x0) ? (long long)y * npx + x0 + m : -1;
-            const bool done = mbar_wait_bounded(smem_u32(&bars[pb]), (uint32_t)(((it - 1) >> 1) & 1));
-            ok = __syncthreads_and(done) != 0;
-            if (!ok) break;
-            tc_fence_after();
-            read_out_tile<C>(tmem + pb * Dm::ACC_COLS, warp, row, true, half, coef);
-        }
-        tc_fence_before();
-        if (!have) break;
     }
     tc_fence_before();
-    if (!ok) {
-        if (tid == 0 && flag) atomicOr(flag, 1);
-        if ((blockIdx.x >> 1) + it * stride < ntiles)
-            mbar_wait_bounded(smem_u32(&bars[it & 1]), (uint32_t)((it >> 1) & 1));
-    }
     __syncthreads();
-    if (warp == 0) {
+    if (*abort_word) {
+        // a wait ran out: report it, and let the MMAs issued last finish (they complete in order; the
+        // wait is bounded) before the tensor memory is released
+        if (warp == 4 && lane == 0) {
+            if (flag) atomicOr(flag, 1);
+            const int last = *issued - 1;
+            if (last >= 0) mbar_wait_bounded(smem_u32(&bars[4 + (last & 1)]), (uint32_t)((last >> 1) & 1));
+        }
+        __syncthreads();
+    }
+    if (warp == 4) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Dm::TMEM_COLS)
                      : "memory");
@@ -695,10 +585,9 @@ static cudaError_t launch_tc_c(const uint8_t* img, int H, int W, const int32_t* 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured_device != dev) {
-        e = cudaFuncSetAttribute(project_tc_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, Dm::SMEM);
+        e = cudaFuncSetAttribute(project_tc_kernel<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Dm::SMEM);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(project_tc_dense_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     Dm::SMEM_DENSE);
+            e = cudaFuncSetAttribute(project_tc_kernel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Dm::SMEM);
         if (e != cudaSuccess) return e;
         configured_device = dev;
     }
@@ -706,12 +595,9 @@ static cudaError_t launch_tc_c(const uint8_t* img, int H, int W, const int32_t* 
     const long long ntiles = pos ? (n + kTileM - 1) / kTileM
                                  : (long long)(H - PS + 1) * ((W - PS + 1 + kTileM - 1) / kTileM);
     const int g = (int)(ntiles < half_grid ? ntiles : half_grid);
-    if (pos)
-        project_tc_kernel<C><<<2 * g, kTcThreads, Dm::SMEM, s>>>(img, H, W, pos, n, static_cast<const uint4*>(pieces),
-                                                                  coef, flag);
-    else
-        project_tc_dense_kernel<C><<<2 * g, kTcThreads, Dm::SMEM_DENSE, s>>>(img, H, W,
-                                                                             static_cast<const uint4*>(pieces), coef, flag);
+    const uint4* pc = static_cast<const uint4*>(pieces);
+    if (pos) project_tc_kernel<C, false><<<2 * g, kTcThreads, Dm::SMEM, s>>>(img, H, W, pos, n, pc, coef, flag);
+    else project_tc_kernel<C, true><<<2 * g, kTcThreads, Dm::SMEM, s>>>(img, H, W, pos, n, pc, coef, flag);
     return cudaGetLastError();
 }
 
