@@ -257,7 +257,9 @@ htsvd_status htsvd_denoise_cube(const uint8_t* d_cube, int32_t H, int32_t W, int
  * exact integer SSD over the 64 voxels with ties broken by the lowest linear index (z H + y) W + x,
  * the reference itself in slot 0; tau = tau_mult * sigma, tau_mult <= 0 meaning sqrt(2 ln(4^3 K)).
  * sigma: the noise level (>= 0; for Rician MRI data, the level after a variance-stabilising
- * transform, which is the caller's). Parameters: ps 0 or 4 (others UNSUPPORTED), stride 0 -> 2,
+ * transform, which is the caller's), or < 0 to estimate it with the eigenvalue rule of
+ * htsvd_estimate_sigma on the covariance of the reference cubes (64 x 64, host FP64; the paper's CNN
+ * estimator is replaced as for images; the used value goes to h_sigma_out). Parameters: ps 0 or 4 (others UNSUPPORTED), stride 0 -> 2,
  * window 0 -> 5 (at most 8), K 0 -> 32 (a power of two, at most 32); match_mode AUTO or FULL.
  * d_out: D x H x W float32 (DEVICE). d_idx_out (DEVICE, may be NULL): N_groups x K int32 linear
  * indices, groups z-major over the grid. Optional outputs of p are honoured (d_mask_out: 2 K words
@@ -266,8 +268,7 @@ htsvd_status htsvd_denoise_cube(const uint8_t* d_cube, int32_t H, int32_t W, int
  * h_basis_gap_out as in htsvd_denoise). The bases are solved on the host (one synchronisation on
  * an event, overlapped with the grouping). The aggregation adds with float atomics, so repeated
  * calls agree to rounding rather than bit for bit.
- * Errors: INVALID_ARG for a null or misaligned pointer, a negative or non-finite sigma, D, H or W
- * below 4, K not a power of two in [2, 32], window outside [1, 8], a window with fewer than K
+ * Errors: INVALID_ARG for a null or misaligned pointer, a non-finite sigma, D, H or W below 4, K not a power of two in [2, 32], window outside [1, 8], a window with fewer than K
  * cubes, or another match or aggregation mode; UNSUPPORTED for ps other than 4 or D H W >= 2^31. */
 htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, int32_t W, double sigma,
                                   const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t stream);

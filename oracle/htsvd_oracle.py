@@ -94,7 +94,8 @@ Readings where the paper is silent or ambiguous:
      exact integer SSD over the ps^3 voxels, keys (SSD, (z H + y) W + x), slot 0 the reference
      (R5); bases per tube-Fourier slice as R6/R7; tau = sigma sqrt(2 ln(ps^3 K)) (R9 with c = ps);
      aggregation into the volume as R10. The paper's Rician noise goes through variance-
-     stabilising transforms, which are outside this core: sigma is the (stabilised) noise level.
+     stabilising transforms, which are outside this core: sigma is the (stabilised) noise level,
+     given or estimated by R11 on the covariance of the reference cubes (in place of the CNN).
 
 Parity pins for every function are in tests/test_oracle_pins.py.
 """
@@ -1007,3 +1008,12 @@ def denoise_volume(v: np.ndarray, sigma: float, params=None, *, idx=None, keep_m
             masks[a:b] = m
     return Result(out=num / den, idx=idx, tau=tau, U=U, V=V, weights=w, masks=masks, den=den,
                   ambiguous=np.array(amb, dtype=np.int64).reshape(-1, 2), extra={"basis_gap": gap})
+
+
+def estimate_sigma_volume(v: np.ndarray, params=None) -> float:
+    """Noise level of a volume (reading R20 with R11): the eigenvalue rule on the covariance of the
+    reference cubes, each flattened in (i, j, k) order."""
+    p = Params.of(params)
+    P = gather_cubes(v, volume_reference_positions(v.shape, p), p.ps).reshape(-1, p.ps ** 3)
+    mu = P.mean(axis=0)
+    return sigma_from_eigenvalues(np.linalg.eigvalsh(P.T @ P / P.shape[0] - np.outer(mu, mu)))

@@ -288,11 +288,12 @@ def denoise_cube(cube, sigma, params=None, *, return_info=False, masks=False, we
 VOLUME_DEFAULTS = dict(ps=4, stride=2, window=5, K=32)
 
 
-def denoise_volume(vol, sigma, params=None, *, return_info=False, masks=False, weights=False, basis=False,
+def denoise_volume(vol, sigma=None, params=None, *, return_info=False, masks=False, weights=False, basis=False,
                    stream=None):
     """Alg. 1 on a uint8 (D, H, W) CUDA volume with 4 x 4 x 4 cubes (the t-SVD tube along z) at the
-    given sigma; params default to the paper's MRI setting (ps 4, K 32, window 5; stride 2).
-    Returns the float32 (D, H, W) estimate, or (estimate, info)."""
+    given sigma (None: estimated from the reference cubes' covariance eigenvalues); params default to
+    the paper's MRI setting (ps 4, K 32, window 5; stride 2). Returns the float32 (D, H, W) estimate,
+    or (estimate, info)."""
     lib = _lib.load()
     torch = _torch()
     if vol.dim() != 3 or not vol.is_cuda or not vol.is_contiguous() or vol.dtype != torch.uint8:
@@ -317,12 +318,14 @@ def denoise_volume(vol, sigma, params=None, *, return_info=False, masks=False, w
         info["basis"] = torch.empty((2, 4, 4, 4, 2), dtype=torch.float64, device=vol.device)
         cp.d_basis_out = info["basis"].data_ptr()
     gap = ctypes.c_double(0.0)
+    used = ctypes.c_double(0.0)
     cp.h_basis_gap_out = ctypes.pointer(gap)
-    st = lib.htsvd_denoise_volume(_ptr(vol), D, H, W, float(sigma), ctypes.byref(cp), _ptr(out), _ptr(idx),
-                                  _stream_ptr(stream))
+    cp.h_sigma_out = ctypes.pointer(used)
+    st = lib.htsvd_denoise_volume(_ptr(vol), D, H, W, -1.0 if sigma is None else float(sigma), ctypes.byref(cp),
+                                  _ptr(out), _ptr(idx), _stream_ptr(stream))
     _lib.check(st, "htsvd_denoise_volume")
     if return_info:
-        info.update(idx=idx, basis_gap=gap.value)
+        info.update(idx=idx, basis_gap=gap.value, sigma=used.value)
         return out, info
     return out
 

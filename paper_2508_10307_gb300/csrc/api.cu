@@ -1215,7 +1215,7 @@ htsvd_status htsvd_denoise_cube(const uint8_t* d_cube, int32_t H, int32_t W, int
 
 htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, int32_t W, double sigma,
                                   const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t s) {
-    if (!d_vol || !d_out || !(sigma >= 0) || std::isinf(sigma)) return HTSVD_ERR_INVALID_ARG;
+    if (!d_vol || !d_out || std::isnan(sigma) || std::isinf(sigma)) return HTSVD_ERR_INVALID_ARG;
     if ((uintptr_t)d_vol & 3) return HTSVD_ERR_INVALID_ARG;
     htsvd_params z;
     std::memset(&z, 0, sizeof(z));
@@ -1245,18 +1245,34 @@ htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, in
     ST(ws_get(w, S_VB64, sizeof(double) * 256, &b64));
     ST(ws_get(w, S_VNUM, sizeof(float) * nvox, &num));
     ST(ws_get(w, S_VDEN, sizeof(float) * nvox, &den));
-    ST(ws_host(w, sizeof(unsigned long long) * 512 + sizeof(double) * 256, &hbuf));
+    const bool estimate = sigma < 0;
+    const size_t fm_words = estimate ? 64 * 64 + 64 : 0;
+    ST(ws_host(w, sizeof(unsigned long long) * (512 + fm_words) + sizeof(double) * 256, &hbuf));
     ST(ws_side(w));
     unsigned long long* hmom = (unsigned long long*)hbuf;
-    double* hb64 = (double*)(hmom + 512);
-    // moments first, their copy to the host, then the grouping runs while the host solves the bases
+    unsigned long long* hfm = hmom + 512;
+    double* hb64 = (double*)(hfm + fm_words);
+    // moments first (and the full moment when sigma is estimated), their copy to the host, then the
+    // grouping runs while the host solves the bases and the noise level
     { ProfScope ps_("volume_moments", s); CK(launch_volume_moments(d_vol, g, (unsigned long long*)mom, s)); }
     CK(cudaMemcpyAsync(hmom, mom, sizeof(unsigned long long) * 512, cudaMemcpyDeviceToHost, s));
+    if (estimate) {
+        void* fm;
+        ST(ws_get(w, S_FULLM, sizeof(unsigned long long) * fm_words, &fm));
+        unsigned long long* dM = (unsigned long long*)fm;
+        { ProfScope ps_("volume_full_moment", s); CK(launch_volume_full_moment(d_vol, g, dM, dM + 64 * 64, s)); }
+        CK(cudaMemcpyAsync(hfm, dM, sizeof(unsigned long long) * fm_words, cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaEventRecord(w->ev_join, s));
     { ProfScope ps_("block_match_volume", s); CK(launch_block_match_volume(d_vol, g, idx, s)); }
     CK(cudaEventSynchronize(w->ev_join));
     double gap;
     { HostProfScope hp_("volume_bases_host"); gap = volume_bases_host(hmom, hb64); }
+    if (estimate) {
+        HostProfScope hp_("volume_sigma_host");
+        sigma = sigma_from_moments(hfm, hfm + 64 * 64, 64, ng);
+        if (!(sigma >= 0)) return HTSVD_ERR_CUDA;
+    }
     if (p && p->h_basis_gap_out) *p->h_basis_gap_out = gap;
     if (q.strict_basis && !(gap >= kDegenerateGap)) return HTSVD_ERR_DEGENERATE_BASIS;
     CK(cudaMemcpyAsync(b64, hb64, sizeof(double) * 256, cudaMemcpyHostToDevice, s));

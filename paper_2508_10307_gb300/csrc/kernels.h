@@ -162,6 +162,10 @@ cudaError_t launch_volume_moments(const uint8_t* vol, const VolGeo& g, unsigned 
 // HOST: canonical bases from the moments: b64 [2 (U, V)][4 slices][4][4] complex (re, im), slice 3 the
 // conjugate of slice 1; returns the smallest relative eigen-gap over the slices 0..2 of U and V.
 double volume_bases_host(const unsigned long long* mom, double* b64);
+// Full second moment M (64 x 64) and sums S (64) of the reference cubes (uint64, exact), for the noise
+// estimate; entry order u = (a * 4 + b) * 4 + c.
+cudaError_t launch_volume_full_moment(const uint8_t* vol, const VolGeo& g, unsigned long long* d_M,
+                                      unsigned long long* d_S, cudaStream_t s);
 struct VolFilterArgs {
     const uint8_t* vol;
     VolGeo g;

@@ -163,6 +163,54 @@ __global__ void __launch_bounds__(256) volume_moments_kernel(const uint8_t* __re
         if (acc[h]) atomicAdd(mom + t + 256 * h, acc[h]);
 }
 
+// Full second moment of the reference cubes for the noise estimate: M[u][v] = sum_r P_r[u] P_r[v] and
+// S[u] = sum_r P_r[u] (uint64, exact), u = (a * 4 + b) * 4 + c. Each thread owns 16 entries of M.
+__global__ void __launch_bounds__(256) volume_full_moment_kernel(const uint8_t* __restrict__ vol, VolGeo g,
+                                                                 unsigned long long* __restrict__ M,
+                                                                 unsigned long long* __restrict__ S) {
+    __shared__ uint8_t sc[kMomRefs][64];
+    const int t = threadIdx.x;
+    const long long total = (long long)g.D * g.H * g.W;
+    const long long plane = (long long)g.H * g.W;
+    const long long nref = (long long)g.nrz * g.nry * g.nrx;
+    unsigned long long acc[16] = {};
+    unsigned long long sacc = 0;
+    for (long long base = (long long)blockIdx.x * kMomRefs; base < nref; base += (long long)gridDim.x * kMomRefs) {
+        __syncthreads();
+        for (int q = t; q < kMomRefs * 16; q += 256) {       // (ref, tube c, row a): 4 bytes along b
+            const int rr = q >> 4, c = (q >> 2) & 3, a = q & 3;
+            const long long r = base + rr;
+            uint32_t w = 0;
+            if (r < nref) {
+                const int iz = (int)(r / ((long long)g.nry * g.nrx));
+                const int rem = (int)(r - (long long)iz * g.nry * g.nrx);
+                const int iy = rem / g.nrx, ix = rem - (rem / g.nrx) * g.nrx;
+                const long long off = (long long)(vref_pos(iz, g.s, g.D) + c) * plane +
+                                      (long long)(vref_pos(iy, g.s, g.H) + a) * g.W + vref_pos(ix, g.s, g.W);
+                w = bytes4(vol, off, total);
+            }
+            for (int b = 0; b < 4; ++b) sc[rr][(a * 4 + b) * 4 + c] = (uint8_t)(w >> (8 * b));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int e = t + 256 * q, u = e >> 6, v = e & 63;
+            unsigned s = 0;                                   // < 64 * 255^2 < 2^32
+            for (int rr = 0; rr < kMomRefs; ++rr) s += (unsigned)sc[rr][u] * (unsigned)sc[rr][v];
+            acc[q] += s;
+        }
+        if (t < 64) {
+            unsigned s = 0;
+            for (int rr = 0; rr < kMomRefs; ++rr) s += sc[rr][t];
+            sacc += s;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        if (acc[q]) atomicAdd(M + t + 256 * q, acc[q]);
+    if (t < 64 && sacc) atomicAdd(S + t, sacc);
+}
+
 // ------------------------------------------------------------------------------ filter
 
 // Normalised Haar analysis along the group mode on K values in registers (Sec. II-D, Eqs. (H_2),
@@ -690,6 +738,18 @@ cudaError_t launch_volume_moments(const uint8_t* vol, const VolGeo& g, unsigned 
     const long long rounds = (nref + kMomRefs - 1) / kMomRefs;
     const long long cap = (long long)device_sm_count() * 2;
     volume_moments_kernel<<<(int)(rounds < cap ? rounds : cap), 256, 0, s>>>(vol, g, d_mom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_volume_full_moment(const uint8_t* vol, const VolGeo& g, unsigned long long* d_M,
+                                      unsigned long long* d_S, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_M, 0, sizeof(unsigned long long) * 64 * 64, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_S, 0, sizeof(unsigned long long) * 64, s);
+    if (e != cudaSuccess) return e;
+    const long long nref = (long long)g.nrz * g.nry * g.nrx;
+    const long long rounds = (nref + kMomRefs - 1) / kMomRefs;
+    const long long cap = (long long)device_sm_count() * 2;
+    volume_full_moment_kernel<<<(int)(rounds < cap ? rounds : cap), 256, 0, s>>>(vol, g, d_M, d_S);
     return cudaGetLastError();
 }
 

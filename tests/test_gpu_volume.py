@@ -68,7 +68,7 @@ def test_volume_zero_threshold_is_the_identity_and_repeats_agree():
 def test_volume_at_the_benchmarked_size():
     """A 176 x 208 x 176 volume (the OASIS T1-weighted size) at the paper's MRI setting: the
     grouping of 400 sampled references against the oracle, the bases against the oracle's from all
-    reference cubes, and the estimate within the range of the noisy input's values."""
+    reference cubes, a PSNR gain over the input, and the estimated sigma against the oracle's."""
     clean, noisy = _case((176, 208, 176), 11.5, 3)
     prm = dict(ps=4, stride=2, window=5, K=32)
     x = torch.from_numpy(noisy).cuda()
@@ -86,6 +86,26 @@ def test_volume_at_the_benchmarked_size():
     o = out.cpu().numpy()
     assert np.isfinite(o).all()
     assert psnr(o, clean) > psnr(noisy.astype(np.float64), clean) + 3.0
+    _, est = H.denoise_volume(x, None, prm, return_info=True)
+    torch.cuda.synchronize()
+    s_ref = O.estimate_sigma_volume(noisy, prm)
+    assert abs(est["sigma"] - s_ref) <= 1e-9 * s_ref
+
+
+@pytest.mark.parametrize("shape,prm,sigma", [
+    ((20, 24, 22), dict(ps=4, stride=2, window=5, K=16), 11.5),
+    ((30, 33, 17), dict(ps=4, stride=2, window=5, K=32), 7.65),
+])
+def test_volume_estimated_sigma_matches_oracle(shape, prm, sigma):
+    """sigma < 0: the eigenvalue rule on the reference cubes' covariance (exact integer moments, host
+    FP64 eigenvalues) against the oracle's numpy eigvalsh, then the denoiser at that sigma."""
+    clean, noisy = _case(shape, sigma, 120 + shape[0])
+    s_ref = O.estimate_sigma_volume(noisy, prm)
+    r = O.denoise_volume(noisy, s_ref, prm)
+    out, info = H.denoise_volume(torch.from_numpy(noisy).cuda(), None, prm, return_info=True)
+    torch.cuda.synchronize()
+    assert abs(info["sigma"] - s_ref) <= 1e-9 * s_ref
+    assert max_abs(out.cpu().numpy(), r.out) <= PIX_TOL
 
 
 def test_volume_bad_arguments():

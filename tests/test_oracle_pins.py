@@ -935,3 +935,21 @@ def test_volume_default_threshold_counts_the_cube_voxels():
     v = _volume(10, 10, 10, 13)
     r = O.denoise_volume(v, 10.0, dict(ps=4, stride=2, window=5, K=32))
     assert abs(r.tau - 10.0 * math.sqrt(2 * math.log(4 ** 3 * 32))) <= 1e-12
+
+
+@pytest.mark.parametrize("sigma", [5.0, 10.0])
+def test_volume_sigma_estimate_recovers_pure_noise(sigma):
+    """Pure Gaussian noise around 128 (no clipping at these levels): the covariance of the reference
+    cubes is sigma^2 I up to sampling error, so the rule recovers sigma within 2 %."""
+    rng = np.random.default_rng(int(sigma))
+    v = np.clip(np.rint(128.0 + sigma * rng.standard_normal((40, 44, 42))), 0, 255).astype(np.uint8)
+    s = O.estimate_sigma_volume(v, dict(ps=4, stride=2, window=5, K=8))
+    assert abs(s - sigma) <= 0.02 * sigma
+
+
+def test_volume_sigma_estimate_of_a_noise_free_ramp_is_zero():
+    """A linear ramp has a covariance of rank <= 4 (a cube is determined by its corner value and three
+    slopes), so at least 60 of its 64 eigenvalues vanish and the rule returns 0."""
+    zz, yy, xx = np.mgrid[0:20, 0:22, 0:24]
+    v = (10 + 2 * zz + 3 * yy + xx).astype(np.uint8)
+    assert O.estimate_sigma_volume(v, dict(ps=4, stride=2, window=5, K=8)) <= 1e-6
