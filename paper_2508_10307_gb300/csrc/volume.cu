@@ -5,7 +5,8 @@
 //
 // * block_match_volume_kernel: one warp per reference cube; exact SSD of every candidate of the
 //   clamped W x W x W window (byte rows through __vabsdiffu4 + DP4A), keys (SSD, linear index) in
-//   shared memory, the K - 1 smallest other keys found by rank (keys are unique).
+//   shared memory; the (K-1)-th smallest SSD by a ballot binary search, then the keys at or below it
+//   ranked among themselves (keys are unique) for the K - 1 kept slots.
 // * volume_moments_kernel: exact row and column moments of the reference cubes per (tube index
 //   pair), from which the host forms the per-slice scatter matrices (Sec. III-B.1, Eq. (BCR
 //   nonlocal SVD simplified), read as a 2-D SVD per tube-Fourier slice).
@@ -66,6 +67,7 @@ __device__ __forceinline__ uint32_t bytes4(const uint8_t* base, long long off, l
 __global__ void __launch_bounds__(kVolWarps * 32)
 block_match_volume_kernel(const uint8_t* __restrict__ vol, VolGeo g, int32_t* __restrict__ idx) {
     __shared__ unsigned long long skey[kVolWarps][kMaxCand];
+    __shared__ unsigned long long skey2[kVolWarps][kMaxCand];    // keys that can be kept, compacted
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long total = (long long)g.D * g.H * g.W;
     const long long nref = (long long)g.nrz * g.nry * g.nrx;
@@ -94,13 +96,39 @@ block_match_volume_kernel(const uint8_t* __restrict__ vol, VolGeo g, int32_t* __
             skey[warp][c] = lin == me ? ~0ull : (((unsigned long long)ssd << 32) | (unsigned long long)lin);
         }
         __syncwarp();
+        // T = the (K-1)-th smallest SSD of the other candidates (binary search over SSD < 2^22 with
+        // warp ballots); only keys with SSD <= T can be among the K-1 kept, so only they are ranked,
+        // against each other (full keys: ties broken by the linear index)
+        const int nslot = (ncand + 31) / 32;
+        unsigned lo = 0, hi = 1u << 22;
+        while (lo < hi) {
+            const unsigned mid = (lo + hi) >> 1;
+            int cnt = 0;
+            for (int j = 0; j < nslot; ++j) {
+                const int c = lane + 32 * j;
+                const bool le = c < ncand && (unsigned)(skey[warp][c] >> 32) <= mid;
+                cnt += __popc(__ballot_sync(0xffffffffu, le));
+            }
+            if (cnt >= g.K - 1) hi = mid;
+            else lo = mid + 1;
+        }
+        unsigned long long* sel = skey2[warp];
+        int m = 0;
+        for (int j = 0; j < nslot; ++j) {
+            const int c = lane + 32 * j;
+            const unsigned long long k = c < ncand ? skey[warp][c] : ~0ull;
+            const bool take = (unsigned)(k >> 32) <= lo;
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            if (take) sel[m + __popc(bal & ((1u << lane) - 1u))] = k;
+            m += __popc(bal);
+        }
+        __syncwarp();
         int32_t* out = idx + r * g.K;
         if (lane == 0) out[0] = (int32_t)me;
-        for (int c = lane; c < ncand; c += 32) {
-            const unsigned long long k = skey[warp][c];
-            if (k == ~0ull) continue;
+        for (int c = lane; c < m; c += 32) {
+            const unsigned long long k = sel[c];
             int rank = 0;
-            for (int o = 0; o < ncand; ++o) rank += skey[warp][o] < k ? 1 : 0;
+            for (int o = 0; o < m; ++o) rank += sel[o] < k ? 1 : 0;
             if (rank < g.K - 1) out[1 + rank] = (int32_t)(k & 0xffffffffull);
         }
         __syncwarp();
@@ -254,7 +282,8 @@ struct VolSmem {
 };
 
 // FP64 coefficient e = (i * 4 + j) * 4 + k of one cube (bytes w[(c * 4 + a)] = row a of tube slice c).
-__device__ double coef64(const uint32_t (&w)[16], int e, const VolSmem& sm) {
+// Out of line: it runs only for coefficients inside the guard band.
+__device__ __noinline__ double coef64(const uint32_t (&w)[16], int e, const VolSmem& sm) {
     const int i = e >> 4, j = (e >> 2) & 3, k = e & 3;
     double t0 = 0, t2 = 0, t1r = 0, t1i = 0;
     for (int a = 0; a < 4; ++a)
