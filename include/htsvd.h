@@ -279,7 +279,7 @@ htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, in
  * (linear index y * W + x), i.e. per channel-Fourier slice f, U_f^H P_f V_f, then the inverse DFT
  * along the channel mode. d_img: H x W x C uint8 (DEVICE, 4-byte aligned); d_pos: n int32 (DEVICE), or
  * NULL for every position of the image, row-major over the (H - 7) x (W - 7) top-left corners (n must
- * then be (H - 7)(W - 7); the kernel stages the image rows a tile of positions shares, im2col-style);
+ * then be (H - 7)(W - 7); a tile is then 128 consecutive positions of one row, im2col-style);
  * d_basis: the FP64 bases in the layout of htsvd_params.d_basis_out (DEVICE; e.g. from htsvd_denoise
  * of the same image); d_coef: n x 64 C float32 (DEVICE, 16-byte aligned), coefficient
  * (i * 8 + j) * C + c of patch t at d_coef[t * 64 C + ...] (the order of the mask bits).
