@@ -108,6 +108,15 @@ def test_volume_estimated_sigma_matches_oracle(shape, prm, sigma):
     assert max_abs(out.cpu().numpy(), r.out) <= PIX_TOL
 
 
+def test_volume_strict_basis_refuses_a_constant_volume():
+    x = torch.full((12, 13, 14), 77, dtype=torch.uint8, device="cuda")
+    with pytest.raises(_lib.DegenerateBasisError):
+        H.denoise_volume(x, 5.0, dict(ps=4, stride=2, window=5, K=8, strict_basis=True))
+    out = H.denoise_volume(x, 5.0, dict(ps=4, stride=2, window=5, K=8))      # default mode proceeds
+    torch.cuda.synchronize()
+    assert max_abs(out.cpu().numpy(), np.full((12, 13, 14), 77.0)) <= PIX_TOL
+
+
 def test_volume_bad_arguments():
     _, noisy = _case((12, 12, 12), 10.0, 2)
     x = torch.from_numpy(noisy).cuda()

@@ -93,3 +93,18 @@ def test_host_volume_bases_match_oracle(shape, seed):
     z = (b[0::2] + 1j * b[1::2]).reshape(2, 4, 4, 4)
     assert np.abs(z[0] - U).max() < 1e-9 and np.abs(z[1] - V).max() < 1e-9
     assert abs(gap - O.global_basis_gap(lu, lv)) <= 1e-9 * max(gap, 1e-12)
+
+
+def test_host_volume_bases_report_a_degenerate_constant_volume():
+    """Reading R7 for volumes: a constant volume makes every slice scatter matrix rank one (repeated zero
+    eigenvalues), so the smallest relative gap is 0, as the oracle's, and the oracle's strict mode raises."""
+    lib = H.load_library()
+    v = np.full((12, 13, 14), 77, dtype=np.uint8)
+    p = O.Params(ps=4, stride=2, window=5, K=8)
+    P = O.gather_cubes(v, O.volume_reference_positions(v.shape, p), 4)
+    b = np.zeros(256)
+    gap = lib.htsvd_internal_volume_bases(_moments(P).ctypes.data, b.ctypes.data)
+    _, _, lu, lv = O.global_basis(P)
+    assert gap == 0.0 and O.global_basis_gap(lu, lv) == 0.0
+    with pytest.raises(O.DegenerateBasis):
+        O.denoise_volume(v, 5.0, dict(ps=4, stride=2, window=5, K=8, strict_basis=True))
