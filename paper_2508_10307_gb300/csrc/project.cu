@@ -216,26 +216,6 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Eight bytes of the image at byte offset o (any alignment) as eight FP16 values (exact).
-__device__ __forceinline__ uint4 f16x8_of_image(const uint8_t* __restrict__ img, int o, int total) {
-    const int a = o & ~3;
-    uint32_t w0, w1, w2;
-    if (a + 12 <= total) {
-        const uint32_t* p = reinterpret_cast<const uint32_t*>(img + a);
-        w0 = __ldg(p);
-        w1 = __ldg(p + 1);
-        w2 = __ldg(p + 2);
-    } else {
-        w0 = image_word(img, a, total);
-        w1 = image_word(img, a + 4, total);
-        w2 = image_word(img, a + 8, total);
-    }
-    const int sh = (o & 3) * 8;
-    const uint32_t lo = __funnelshift_r(w0, w1, sh), hi = __funnelshift_r(w1, w2, sh);
-    return make_uint4(f16x2_of_bytes(lo, 0x5150u), f16x2_of_bytes(lo, 0x5352u), f16x2_of_bytes(hi, 0x5150u),
-                      f16x2_of_bytes(hi, 0x5352u));
-}
-
 // The MMAs of one tile: D[128 x N] = A[128 x K] B^T summed over the pieces (smallest first). Issued by
 // one thread; the caller commits.
 template <int C>
@@ -351,14 +331,52 @@ project_tc_kernel(const uint8_t* __restrict__ img, int H, int W, const int32_t* 
                          : "memory");
             if (!all_free) break;
             uint8_t* sa = sA + s * Dm::A_BYTES;
-#pragma unroll 4
-            for (int task = pt; task < kTileM * PS * C; task += kProdThreads) {
-                const int m = task & (kTileM - 1), r = task >> 7;
-                const int a = r / C, c = r - (r / C) * C;
-                const int o = sOff[s * kTileM + m];
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (o >= 0) v = f16x8_of_image(img, o + a * rowbytes + 8 * c, total);
-                *reinterpret_cast<uint4*>(sa + (a * C + c) * Dm::LBO_A + m * 16) = v;
+            // every load of this thread's tasks first (three aligned words per task), then the
+            // conversions and stores, so that all of them are in flight together
+            constexpr int NTASK = kTileM * PS * C;
+            constexpr int NT = (NTASK + kProdThreads - 1) / kProdThreads;
+            uint32_t wv[NT][3];
+            int sh[NT];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int task = pt + j * kProdThreads;
+                wv[j][0] = wv[j][1] = wv[j][2] = 0u;
+                sh[j] = -1;
+                if (task < NTASK) {
+                    const int m = task & (kTileM - 1), r = task >> 7;
+                    const int a = r / C, c = r - (r / C) * C;
+                    const int o = sOff[s * kTileM + m];
+                    if (o >= 0) {
+                        const int off = o + a * rowbytes + 8 * c, al = off & ~3;
+                        if (al + 12 <= total) {
+                            const uint32_t* p = reinterpret_cast<const uint32_t*>(img + al);
+                            wv[j][0] = __ldg(p);
+                            wv[j][1] = __ldg(p + 1);
+                            wv[j][2] = __ldg(p + 2);
+                        } else {
+                            wv[j][0] = image_word(img, al, total);
+                            wv[j][1] = image_word(img, al + 4, total);
+                            wv[j][2] = image_word(img, al + 8, total);
+                        }
+                        sh[j] = (off & 3) * 8;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int task = pt + j * kProdThreads;
+                if (task < NTASK) {
+                    const int m = task & (kTileM - 1), r = task >> 7;
+                    const int a = r / C, c = r - (r / C) * C;
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    if (sh[j] >= 0) {
+                        const uint32_t lo = __funnelshift_r(wv[j][0], wv[j][1], sh[j]);
+                        const uint32_t hi = __funnelshift_r(wv[j][1], wv[j][2], sh[j]);
+                        v = make_uint4(f16x2_of_bytes(lo, 0x5150u), f16x2_of_bytes(lo, 0x5352u),
+                                       f16x2_of_bytes(hi, 0x5150u), f16x2_of_bytes(hi, 0x5352u));
+                    }
+                    *reinterpret_cast<uint4*>(sa + (a * C + c) * Dm::LBO_A + m * 16) = v;
+                }
             }
             fence_async_smem();
             mbar_arrive(smem_u32(&bars[s]));
