@@ -27,7 +27,6 @@ def _oracle_coefficients(noisy, prm, pos):
     """Oracle patch_forward of the patches at linear positions pos, with the oracle's own bases."""
     p = O.Params.of(prm)
     U, V, _, _ = O.global_basis(O.reference_patches(noisy, p))
-    Wd = noisy.shape[1]
     G = O.gather_groups(noisy, pos[:, None].astype(np.int64), 8)[:, 0]       # (n, 8, 8, C)
     S = O.patch_forward(G, U, V).reshape(len(pos), -1)
     norms = np.sqrt((G.astype(np.float64) ** 2).reshape(len(pos), -1).sum(axis=1))
