@@ -277,9 +277,14 @@ __device__ __forceinline__ int haar_row(int j, int K) {
 }
 
 struct VolSmem {
-    float ub[2][3][2][16];                 // [U, V][slice 0..2][re, im][a * 4 + i]
+    __align__(16) float ub[2][3][2][16];   // [U, V][slice 0..2][re, im][i * 4 + a]: columns contiguous
     double ud[2][3][2][16];
 };
+
+// Column c of basis w (0: U, 1: V), slice f, real or imaginary part: rows 0..3 in one 128-bit load.
+__device__ __forceinline__ float4 ucol(const VolSmem& sm, int w, int f, int ri, int c) {
+    return *reinterpret_cast<const float4*>(&sm.ub[w][f][ri][c * 4]);
+}
 
 // FP64 coefficient e = (i * 4 + j) * 4 + k of one cube (bytes w[(c * 4 + a)] = row a of tube slice c).
 // Out of line: it runs only for coefficients inside the guard band.
@@ -362,7 +367,7 @@ volume_filter_kernel(VolFilterArgs A) {
         const int w = e / 96, f = (e / 32) % 3, ri = (e / 16) & 1, ai = e & 15;
         const double v = A.basis64[((w * 4 + f) * 16 + ai) * 2 + ri];
         sm.ud[w][f][ri][ai] = v;
-        sm.ub[w][f][ri][ai] = (float)v;
+        sm.ub[w][f][ri][(ai & 3) * 4 + (ai >> 2)] = (float)v;
     }
     for (int q = tid; q < fn[0] * fn[1] * (FXp / 4); q += blockDim.x) {
         const int zz = q / (fn[1] * (FXp / 4)), rem = q - zz * (fn[1] * (FXp / 4));
@@ -416,31 +421,35 @@ volume_filter_kernel(VolFilterArgs A) {
         for (int i = 0; i < 4; ++i) {
             // row i of S: Y_f[i][b] = sum_a conj(U_f[a][i]) X_f[a][b]; Z_f[i][j] = sum_b Y_f[i][b] V_f[b][j]
             float y0[4], y2[4], yr[4], yi[4];
+            const float4 cu0 = ucol(sm, 0, 0, 0, i), cu2 = ucol(sm, 0, 2, 0, i);
+            const float4 cur = ucol(sm, 0, 1, 0, i), cui = ucol(sm, 0, 1, 1, i);
+            const float U0[4] = {cu0.x, cu0.y, cu0.z, cu0.w}, U2[4] = {cu2.x, cu2.y, cu2.z, cu2.w};
+            const float UR[4] = {cur.x, cur.y, cur.z, cur.w}, UI[4] = {cui.x, cui.y, cui.z, cui.w};
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 float s0 = 0.f, s2 = 0.f, sr = 0.f, si = 0.f;
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const float u0 = sm.ub[0][0][0][a * 4 + i], u2 = sm.ub[0][2][0][a * 4 + i];
-                    const float ur = sm.ub[0][1][0][a * 4 + i], ui = sm.ub[0][1][1][a * 4 + i];
-                    s0 = fmaf(u0, x0[a * 4 + b], s0);
-                    s2 = fmaf(u2, x2[a * 4 + b], s2);
-                    sr = fmaf(ur, xr[a * 4 + b], fmaf(ui, xi[a * 4 + b], sr));
-                    si = fmaf(ur, xi[a * 4 + b], fmaf(-ui, xr[a * 4 + b], si));
+                    s0 = fmaf(U0[a], x0[a * 4 + b], s0);
+                    s2 = fmaf(U2[a], x2[a * 4 + b], s2);
+                    sr = fmaf(UR[a], xr[a * 4 + b], fmaf(UI[a], xi[a * 4 + b], sr));
+                    si = fmaf(UR[a], xi[a * 4 + b], fmaf(-UI[a], xr[a * 4 + b], si));
                 }
                 y0[b] = s0; y2[b] = s2; yr[b] = sr; yi[b] = si;
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float z0 = 0.f, z2 = 0.f, zr = 0.f, zi = 0.f;
+                const float4 cv0 = ucol(sm, 1, 0, 0, j), cv2 = ucol(sm, 1, 2, 0, j);
+                const float4 cvr = ucol(sm, 1, 1, 0, j), cvi = ucol(sm, 1, 1, 1, j);
+                const float V0[4] = {cv0.x, cv0.y, cv0.z, cv0.w}, V2[4] = {cv2.x, cv2.y, cv2.z, cv2.w};
+                const float VR[4] = {cvr.x, cvr.y, cvr.z, cvr.w}, VI[4] = {cvi.x, cvi.y, cvi.z, cvi.w};
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const float v0 = sm.ub[1][0][0][b * 4 + j], v2 = sm.ub[1][2][0][b * 4 + j];
-                    const float vr = sm.ub[1][1][0][b * 4 + j], vi = sm.ub[1][1][1][b * 4 + j];
-                    z0 = fmaf(y0[b], v0, z0);
-                    z2 = fmaf(y2[b], v2, z2);
-                    zr = fmaf(yr[b], vr, fmaf(-yi[b], vi, zr));
-                    zi = fmaf(yr[b], vi, fmaf(yi[b], vr, zi));
+                    z0 = fmaf(y0[b], V0[b], z0);
+                    z2 = fmaf(y2[b], V2[b], z2);
+                    zr = fmaf(yr[b], VR[b], fmaf(-yi[b], VI[b], zr));
+                    zi = fmaf(yr[b], VI[b], fmaf(yi[b], VR[b], zi));
                 }
                 hcl[i * 16 + j * 4 + 0] = 0.25f * ((z0 + z2) + 2.f * zr);
                 hcl[i * 16 + j * 4 + 1] = 0.25f * ((z0 - z2) - 2.f * zi);
@@ -549,26 +558,30 @@ volume_filter_kernel(VolFilterArgs A) {
                     const float s0 = hcl[i * 16 + j * 4 + 0], s1 = hcl[i * 16 + j * 4 + 1];
                     const float s2 = hcl[i * 16 + j * 4 + 2], s3 = hcl[i * 16 + j * 4 + 3];
                     const float z0 = (s0 + s1) + (s2 + s3), z2 = (s0 - s1) + (s2 - s3), zr = s0 - s2, zi = s3 - s1;
+                    const float4 cv0 = ucol(sm, 1, 0, 0, j), cv2 = ucol(sm, 1, 2, 0, j);
+                    const float4 cvr = ucol(sm, 1, 1, 0, j), cvi = ucol(sm, 1, 1, 1, j);
+                    const float V0[4] = {cv0.x, cv0.y, cv0.z, cv0.w}, V2[4] = {cv2.x, cv2.y, cv2.z, cv2.w};
+                    const float VR[4] = {cvr.x, cvr.y, cvr.z, cvr.w}, VI[4] = {cvi.x, cvi.y, cvi.z, cvi.w};
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
-                        const float vv0 = sm.ub[1][0][0][b * 4 + j], vv2 = sm.ub[1][2][0][b * 4 + j];
-                        const float vr = sm.ub[1][1][0][b * 4 + j], vi = sm.ub[1][1][1][b * 4 + j];
-                        w0[b] = fmaf(z0, vv0, w0[b]);
-                        w2[b] = fmaf(z2, vv2, w2[b]);
-                        wrr[b] = fmaf(zr, vr, fmaf(zi, vi, wrr[b]));           // z conj(v)
-                        wi[b] = fmaf(zi, vr, fmaf(-zr, vi, wi[b]));
+                        w0[b] = fmaf(z0, V0[b], w0[b]);
+                        w2[b] = fmaf(z2, V2[b], w2[b]);
+                        wrr[b] = fmaf(zr, VR[b], fmaf(zi, VI[b], wrr[b]));      // z conj(v)
+                        wi[b] = fmaf(zi, VR[b], fmaf(-zr, VI[b], wi[b]));
                     }
                 }
+                const float4 cu0 = ucol(sm, 0, 0, 0, i), cu2 = ucol(sm, 0, 2, 0, i);
+                const float4 cur = ucol(sm, 0, 1, 0, i), cui = ucol(sm, 0, 1, 1, i);
+                const float U0[4] = {cu0.x, cu0.y, cu0.z, cu0.w}, U2[4] = {cu2.x, cu2.y, cu2.z, cu2.w};
+                const float UR[4] = {cur.x, cur.y, cur.z, cur.w}, UI[4] = {cui.x, cui.y, cui.z, cui.w};
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const float u0 = sm.ub[0][0][0][a * 4 + i], u2 = sm.ub[0][2][0][a * 4 + i];
-                    const float ur = sm.ub[0][1][0][a * 4 + i], ui = sm.ub[0][1][1][a * 4 + i];
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
-                        p0[a * 4 + b] = fmaf(u0, w0[b], p0[a * 4 + b]);
-                        p2[a * 4 + b] = fmaf(u2, w2[b], p2[a * 4 + b]);
-                        pr[a * 4 + b] = fmaf(ur, wrr[b], fmaf(-ui, wi[b], pr[a * 4 + b]));
-                        pi[a * 4 + b] = fmaf(ur, wi[b], fmaf(ui, wrr[b], pi[a * 4 + b]));
+                        p0[a * 4 + b] = fmaf(U0[a], w0[b], p0[a * 4 + b]);
+                        p2[a * 4 + b] = fmaf(U2[a], w2[b], p2[a * 4 + b]);
+                        pr[a * 4 + b] = fmaf(UR[a], wrr[b], fmaf(-UI[a], wi[b], pr[a * 4 + b]));
+                        pi[a * 4 + b] = fmaf(UR[a], wi[b], fmaf(UI[a], wrr[b], pi[a * 4 + b]));
                     }
                 }
             }
