@@ -969,16 +969,19 @@ def aggregate_volume(shape, idx: np.ndarray, Ghat: np.ndarray, w: np.ndarray, ps
 
 
 def denoise_volume(v: np.ndarray, sigma: float, params=None, *, idx=None, keep_masks=False, tau=None,
-                   chunk=1024) -> Result:
+                   chunk=1024, basis=None) -> Result:
     """Alg. 1 on a (D, H, W) uint8 volume with ps x ps x ps cubes (reading R20): grouping, global
     bases of the reference cubes per tube-Fourier slice, forward transform, hard threshold,
-    inverse, aggregation. idx fixes the grouping (as block_match_volume would return it)."""
+    inverse, aggregation. idx fixes the grouping (as block_match_volume would return it); basis =
+    global_basis(...) of this volume's reference cubes skips its recomputation."""
     p = Params.of(params)
     D, Hh, Wd = v.shape
     ps = p.ps
     if idx is None:
         idx = block_match_volume(v, p)
-    U, V, lu, lv = global_basis(gather_cubes(v, volume_reference_positions(v.shape, p), ps))
+    if basis is None:
+        basis = global_basis(gather_cubes(v, volume_reference_positions(v.shape, p), ps))
+    U, V, lu, lv = basis
     gap = global_basis_gap(lu, lv)
     if p.strict_basis and not gap >= DEGENERATE_GAP:
         raise DegenerateBasis(f"smallest relative eigen-gap {gap:.3g} < {DEGENERATE_GAP:g}")
