@@ -1020,3 +1020,21 @@ def estimate_sigma_volume(v: np.ndarray, params=None) -> float:
     P = gather_cubes(v, volume_reference_positions(v.shape, p), p.ps).reshape(-1, p.ps ** 3)
     mu = P.mean(axis=0)
     return sigma_from_eigenvalues(np.linalg.eigvalsh(P.T @ P / P.shape[0] - np.outer(mu, mu)))
+
+
+def a_haar_tsvd_volume(v: np.ndarray, sub: tuple, params=None):
+    """Alg. 2 on a volume (readings R15 and R20, the paper's adaptive variant on MRI): each axis cut
+    into sub-volumes as R15 cuts image axes; per sub-volume the noise level by the eigenvalue rule on
+    its reference cubes (estimate_sigma_volume) and Alg. 1 at that level. The eigen-rank vote of R12
+    is not applied to volumes. Returns (output (D, H, W) float64, sigmas in z-major sub-volume order)."""
+    p = Params.of(params)
+    out = np.zeros(v.shape)
+    sigmas = []
+    for (z0, z1) in subimage_bounds(v.shape[0], sub[0]):
+        for (y0, y1) in subimage_bounds(v.shape[1], sub[1]):
+            for (x0, x1) in subimage_bounds(v.shape[2], sub[2]):
+                part = np.ascontiguousarray(v[z0:z1, y0:y1, x0:x1])
+                sg = estimate_sigma_volume(part, p)
+                sigmas.append(sg)
+                out[z0:z1, y0:y1, x0:x1] = denoise_volume(part, sg, p).out
+    return out, np.array(sigmas)

@@ -953,3 +953,27 @@ def test_volume_sigma_estimate_of_a_noise_free_ramp_is_zero():
     zz, yy, xx = np.mgrid[0:20, 0:22, 0:24]
     v = (10 + 2 * zz + 3 * yy + xx).astype(np.uint8)
     assert O.estimate_sigma_volume(v, dict(ps=4, stride=2, window=5, K=8)) <= 1e-6
+
+
+def test_adaptive_volume_single_part_is_alg1_with_the_estimated_sigma():
+    v = _volume(14, 15, 16, 21)
+    prm = dict(ps=4, stride=2, window=5, K=8)
+    out, sig = O.a_haar_tsvd_volume(v, (100, 100, 100), prm)
+    s = O.estimate_sigma_volume(v, prm)
+    assert sig.shape == (1,) and sig[0] == s
+    assert np.abs(out - O.denoise_volume(v, s, prm).out).max() == 0.0
+
+
+def test_adaptive_volume_estimates_each_part_on_its_own():
+    """Two halves along z with noise 4 and 16 on a flat volume: each half's estimate follows its own
+    level (within 5 %), and each half's output is Alg. 1 of that half alone."""
+    rng = np.random.default_rng(22)
+    base = np.full((32, 24, 24), 120.0)
+    noise = np.concatenate([4.0 * rng.standard_normal((16, 24, 24)), 16.0 * rng.standard_normal((16, 24, 24))])
+    v = np.clip(np.rint(base + noise), 0, 255).astype(np.uint8)
+    prm = dict(ps=4, stride=2, window=5, K=8)
+    out, sig = O.a_haar_tsvd_volume(v, (16, 24, 24), prm)
+    assert sig.shape == (2,)
+    assert abs(sig[0] - 4.0) <= 0.05 * 4.0 and abs(sig[1] - 16.0) <= 0.05 * 16.0
+    lower = np.ascontiguousarray(v[16:])
+    assert np.abs(out[16:] - O.denoise_volume(lower, sig[1], prm).out).max() == 0.0
