@@ -273,6 +273,22 @@ htsvd_status htsvd_denoise_cube(const uint8_t* d_cube, int32_t H, int32_t W, int
 htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, int32_t W, double sigma,
                                   const htsvd_params* p, float* d_out, int32_t* d_idx_out, cudaStream_t stream);
 
+/* A-Haar-tSVD (Alg. 2) on an MRI volume (Sec. IV, MRI denoising: the adaptive variant with ps 4,
+ * K 32, W 5). d_vol: D x H x W uint8 (DEVICE). Each axis of length n is cut into t = max(1, n / n_sub)
+ * parts with boundaries floor(i n / t), as the image axes of htsvd_denoise_adaptive (sub_d, sub_h,
+ * sub_w >= 1). Step 1 estimates sigma per sub-volume with the eigenvalue rule on its reference cubes'
+ * covariance (as htsvd_denoise_volume with sigma < 0; the eigen-rank vote is not applied to
+ * volumes); Step 2 denoises every sub-volume on its own (Alg. 1 of htsvd_denoise_volume: its own
+ * grouping, bases and threshold) at that sigma and writes it into d_out (D x H x W float32, DEVICE).
+ * h_sigmas (HOST, may be NULL) receives the sigmas in z-major sub-volume order. Synchronises
+ * `stream` once per sub-volume (host eigenvalue step). Errors: INVALID_ARG for a null pointer, a
+ * sub size < 1, or a sub-volume that fails the checks of htsvd_denoise_volume (each part must be
+ * at least 4 long and hold K cubes in its window); UNSUPPORTED as for htsvd_denoise_volume. The
+ * per-volume optional outputs of p (masks, weights, basis, gap, sigma) are ignored. */
+htsvd_status htsvd_denoise_volume_adaptive(const uint8_t* d_vol, int32_t D, int32_t H, int32_t W, int32_t sub_d,
+                                           int32_t sub_h, int32_t sub_w, const htsvd_params* p, float* d_out,
+                                           double* h_sigmas, cudaStream_t stream);
+
 /* Batched forward projection of patches onto the global t-SVD bases (Sec. III-B.2, Eq. (forward
  * transform) before the Haar transform along the group mode; Sec. II-C, Def. T-product): for each
  * of n patches, S = U^T * P * V of the ps x ps x C uint8 patch P whose top-left corner is d_pos[t]

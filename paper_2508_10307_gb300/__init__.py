@@ -330,6 +330,31 @@ def denoise_volume(vol, sigma=None, params=None, *, return_info=False, masks=Fal
     return out
 
 
+def denoise_volume_adaptive(vol, sub=(88, 104, 88), params=None, *, return_sigmas=False, stream=None):
+    """A-Haar-tSVD (Alg. 2) on a uint8 (D, H, W) CUDA volume: each axis cut into parts at least
+    sub long, a sigma per sub-volume by the eigenvalue rule on its reference cubes, and Alg. 1 of
+    denoise_volume on each part at its sigma. Returns the float32 (D, H, W) estimate, and the
+    sub-volume sigmas (z-major) if asked."""
+    lib = _lib.load()
+    torch = _torch()
+    if vol.dim() != 3 or not vol.is_cuda or not vol.is_contiguous() or vol.dtype != torch.uint8:
+        raise ValueError("denoise_volume_adaptive expects a contiguous uint8 CUDA tensor (D, H, W)")
+    if params is None or isinstance(params, dict):
+        params = dict(VOLUME_DEFAULTS, **(params or {}))
+    cp = HtsvdParams.of(params).c()
+    D, H, W = vol.shape
+    sd, sh, sw = (int(v) for v in sub)
+    n = 1
+    for length, part in ((D, sd), (H, sh), (W, sw)):
+        n *= len(subimage_bounds(length, max(part, 1)))
+    out = torch.empty((D, H, W), dtype=torch.float32, device=vol.device)
+    sig = (ctypes.c_double * n)()
+    st = lib.htsvd_denoise_volume_adaptive(_ptr(vol), D, H, W, sd, sh, sw, ctypes.byref(cp), _ptr(out), sig,
+                                           _stream_ptr(stream))
+    _lib.check(st, "htsvd_denoise_volume_adaptive")
+    return (out, [float(v) for v in sig]) if return_sigmas else out
+
+
 def denoise_video(frames, sigma=None, params=None, *, T=1, return_info=False, stream=None):
     """A clip of uint8 frames (F, H, W[, C]) on the GPU, frame by frame with spatio-temporal grouping
     over frames t-T..t+T; sigma=None estimates it per frame. Returns float32 (F, H, W, C), or

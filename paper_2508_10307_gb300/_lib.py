@@ -15,7 +15,8 @@ EXPORTED = ["htsvd_denoise", "htsvd_denoise_f32", "htsvd_estimate_sigma", "htsvd
             "htsvd_denoise_vjp", "htsvd_num_groups", "htsvd_status_string", "htsvd_release_workspace",
             "htsvd_profile_enable", "htsvd_profile_collect", "htsvd_denoise_noalloc", "htsvd_denoise_adaptive",
             "htsvd_denoise_video", "htsvd_denoise_tau_sweep", "htsvd_sure", "htsvd_denoise_cube",
-            "htsvd_sure_weights", "htsvd_tune_weights", "htsvd_project_patches", "htsvd_denoise_volume"]
+            "htsvd_sure_weights", "htsvd_tune_weights", "htsvd_project_patches", "htsvd_denoise_volume",
+            "htsvd_denoise_volume_adaptive"]
 
 
 class CParams(ctypes.Structure):
@@ -93,6 +94,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.htsvd_tune_weights.argtypes = [vp, i32, i32, i32, dbl, vp, dbl, i32, dbl, P, vp,
                                        ctypes.POINTER(ctypes.c_double), vp]
     lib.htsvd_denoise_volume.argtypes = [vp, i32, i32, i32, dbl, P, vp, vp, vp]
+    lib.htsvd_denoise_volume_adaptive.argtypes = [vp, i32, i32, i32, i32, i32, i32, P, vp,
+                                                  ctypes.POINTER(ctypes.c_double), vp]
     lib.htsvd_project_patches.argtypes = [vp, i32, i32, i32, vp, ctypes.c_int64, vp, vp, vp, vp]
     lib.htsvd_internal_project_simt.argtypes = [vp, i32, i32, i32, vp, ctypes.c_int64, vp, vp, vp]
     lib.htsvd_internal_volume_bases.argtypes = [vp, vp]
@@ -117,7 +120,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                  "htsvd_denoise_vjp", "htsvd_release_workspace", "htsvd_denoise_noalloc", "htsvd_denoise_adaptive",
                  "htsvd_denoise_video", "htsvd_denoise_tau_sweep", "htsvd_sure", "htsvd_denoise_cube",
                  "htsvd_sure_weights", "htsvd_tune_weights", "htsvd_project_patches",
-                 "htsvd_internal_project_simt", "htsvd_denoise_volume"]:
+                 "htsvd_internal_project_simt", "htsvd_denoise_volume", "htsvd_denoise_volume_adaptive"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

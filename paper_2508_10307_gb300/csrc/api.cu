@@ -129,7 +129,7 @@ namespace {
 
 enum Slot {
     S_IDX, S_MOM, S_B64, S_B32, S_PART, S_FULLM, S_FULLS, S_RANKS, S_IDX2, S_Q, S_DEN, S_R, S_TMP,
-    S_AIN, S_AOUT,                   // S_AIN, S_AOUT: subimages of htsvd_denoise_adaptive
+    S_AIN, S_AOUT,                   // S_AIN, S_AOUT: parts of the adaptive image and volume calls
     S_COEF, S_CPN, S_CNRM,           // coefficient cache of htsvd_denoise_tau_sweep
     S_SOUT, S_SGX, S_SIDX, S_SRED,   // htsvd_sure: estimate, adjoint or perturbed image, grouping, sums
     S_GAP,                           // eigen-gaps of the basis slices (strict mode)
@@ -1300,6 +1300,83 @@ htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, in
     CK(cudaMemsetAsync(den, 0, sizeof(float) * nvox, s));
     { ProfScope ps_("volume_filter", s); CK(launch_volume_filter(a, s)); }
     { ProfScope ps_("volume_finalize", s); CK(launch_volume_finalize((const float*)num, (const float*)den, nvox, d_out, s)); }
+    return HTSVD_OK;
+}
+
+// One 3-D box of a uint8 or float volume moved between a whole volume and a packed sub-volume.
+static cudaError_t copy_box(void* dst, size_t dst_pitch, size_t dst_rows, const void* src, size_t src_pitch,
+                            size_t src_rows, size_t row_bytes, size_t rows, size_t slabs, cudaStream_t s) {
+    cudaMemcpy3DParms m;
+    std::memset(&m, 0, sizeof(m));
+    m.srcPtr = make_cudaPitchedPtr(const_cast<void*>(src), src_pitch, row_bytes, src_rows);
+    m.dstPtr = make_cudaPitchedPtr(dst, dst_pitch, row_bytes, dst_rows);
+    m.extent = make_cudaExtent(row_bytes, rows, slabs);
+    m.kind = cudaMemcpyDeviceToDevice;
+    return cudaMemcpy3DAsync(&m, s);
+}
+
+htsvd_status htsvd_denoise_volume_adaptive(const uint8_t* d_vol, int32_t D, int32_t H, int32_t W, int32_t sub_d,
+                                           int32_t sub_h, int32_t sub_w, const htsvd_params* p, float* d_out,
+                                           double* h_sigmas, cudaStream_t s) {
+    if (!d_vol || !d_out || sub_d < 1 || sub_h < 1 || sub_w < 1 || D < 1 || H < 1 || W < 1)
+        return HTSVD_ERR_INVALID_ARG;
+    if ((int64_t)D * H * W >= ((int64_t)1 << 31)) return HTSVD_ERR_UNSUPPORTED;
+    // each axis cut as the subimage axes of Alg. 2: t = max(1, n / n_sub) parts, boundaries floor(i n / t)
+    auto bounds = [](int n, int sub) {
+        const int t = std::max(1, n / sub);
+        std::vector<int> b(t + 1);
+        for (int i = 0; i <= t; ++i) b[i] = (int)(((int64_t)i * n) / t);
+        return b;
+    };
+    const std::vector<int> bz = bounds(D, sub_d), by = bounds(H, sub_h), bx = bounds(W, sub_w);
+    const int nz = (int)bz.size() - 1, ny = (int)by.size() - 1, nx = (int)bx.size() - 1;
+    const int n = nz * ny * nx;
+    struct Box {
+        int z0, y0, x0, d, h, w;
+        size_t in_off, out_off;
+    };
+    std::vector<Box> boxes(n);
+    size_t in_bytes = 0, out_bytes = 0;
+    for (int t = 0; t < n; ++t) {
+        Box& B = boxes[t];
+        const int iz = t / (ny * nx), iy = (t / nx) % ny, ix = t % nx;
+        B.z0 = bz[iz];
+        B.y0 = by[iy];
+        B.x0 = bx[ix];
+        B.d = bz[iz + 1] - B.z0;
+        B.h = by[iy + 1] - B.y0;
+        B.w = bx[ix + 1] - B.x0;
+        B.in_off = in_bytes;
+        B.out_off = out_bytes;
+        in_bytes += ((size_t)B.d * B.h * B.w + 255) & ~(size_t)255;
+        out_bytes += (sizeof(float) * B.d * B.h * B.w + 255) & ~(size_t)255;
+    }
+    Workspace* w = workspace_for(s);
+    if (!w) return HTSVD_ERR_OOM;
+    void *vin, *vout;
+    ST(ws_get(w, S_AIN, in_bytes, &vin));
+    ST(ws_get(w, S_AOUT, out_bytes, &vout));
+    uint8_t* tin = (uint8_t*)vin;
+    unsigned char* tout = (unsigned char*)vout;
+    htsvd_params q;
+    if (p) q = *p;
+    else std::memset(&q, 0, sizeof(q));
+    // per-volume outputs have no meaning for the parts; each part reports only its noise level
+    q.d_basis_out = nullptr;
+    q.d_mask_out = nullptr;
+    q.d_weights_out = nullptr;
+    q.h_basis_gap_out = nullptr;
+    for (int t = 0; t < n; ++t) {
+        const Box& B = boxes[t];
+        CK(copy_box(tin + B.in_off, B.w, B.h, d_vol + ((size_t)B.z0 * H + B.y0) * W + B.x0, W, H, B.w, B.h, B.d, s));
+        double sg = -1.0;
+        q.h_sigma_out = &sg;
+        // Step 1 (Alg. 2): the part's noise level by the eigenvalue rule; Step 2: Alg. 1 at that level
+        ST(htsvd_denoise_volume(tin + B.in_off, B.d, B.h, B.w, -1.0, &q, (float*)(tout + B.out_off), nullptr, s));
+        if (h_sigmas) h_sigmas[t] = sg;
+        CK(copy_box(d_out + ((size_t)B.z0 * H + B.y0) * W + B.x0, sizeof(float) * W, H, tout + B.out_off,
+                    sizeof(float) * B.w, B.h, sizeof(float) * B.w, B.h, B.d, s));
+    }
     return HTSVD_OK;
 }
 

@@ -127,3 +127,33 @@ def test_volume_bad_arguments():
         assert _lib.STATUS_NAMES[code] in str(e.value)
     with pytest.raises(_lib.HtsvdError):
         H.denoise_volume(torch.zeros((3, 12, 12), dtype=torch.uint8, device="cuda"), 10.0)
+
+
+@pytest.mark.parametrize("shape,sub,prm", [
+    ((40, 28, 30), (20, 28, 30), dict(ps=4, stride=2, window=5, K=16)),      # two noise levels along z
+    ((24, 26, 29), (12, 13, 14), dict(ps=4, stride=2, window=4, K=8)),       # 2 x 2 x 2 ragged parts
+])
+def test_volume_adaptive_matches_oracle(shape, sub, prm):
+    """A-Haar-tSVD on a volume: per sub-volume sigma (eigenvalue rule) against the oracle's, and the
+    composed estimate voxel by voxel against the oracle's adaptive variant."""
+    clean = synth.clean_volume(*shape, 140 + shape[0])
+    rng = np.random.default_rng(shape[1])
+    level = np.where(np.arange(shape[0])[:, None, None] < shape[0] // 2, 5.0, 15.0)
+    noisy = np.clip(np.rint(clean + level * rng.standard_normal(shape)), 0, 255).astype(np.uint8)
+    ref, s_ref = O.a_haar_tsvd_volume(noisy, sub, prm)
+    out, sig = H.denoise_volume_adaptive(torch.from_numpy(noisy).cuda(), sub, prm, return_sigmas=True)
+    torch.cuda.synchronize()
+    assert len(sig) == len(s_ref)
+    assert np.abs(np.array(sig) - s_ref).max() <= 1e-9 * s_ref.max()
+    assert max_abs(out.cpu().numpy(), ref) <= PIX_TOL
+    if shape[0] == 40:
+        assert s_ref[1] > 2.0 * s_ref[0]
+
+
+def test_volume_adaptive_bad_arguments():
+    _, noisy = _case((16, 16, 16), 10.0, 4)
+    x = torch.from_numpy(noisy).cuda()
+    for sub in ((0, 8, 8), (2, 16, 16)):             # a zero size; parts two voxels deep
+        with pytest.raises(_lib.HtsvdError) as e:
+            H.denoise_volume_adaptive(x, sub, dict(K=8))
+        assert _lib.STATUS_NAMES[1] in str(e.value)
