@@ -96,6 +96,10 @@ Readings where the paper is silent or ambiguous:
      aggregation into the volume as R10. The paper's Rician noise goes through variance-
      stabilising transforms, which are outside this core: sigma is the (stabilised) noise level,
      given or estimated by R11 on the covariance of the reference cubes (in place of the CNN).
+  R21 the adaptive variant on MRI (Sec. IV runs A-Haar-tSVD on volumes; Alg. 2 is written for
+     subimages): each volume axis is cut as R15 cuts image axes; per part sigma by R11 on its own
+     reference cubes and Alg. 1 of R20 on the part alone; the eigen-rank vote of R12 is given for
+     image groups and is not applied to volumes.
 
 Parity pins for every function are in tests/test_oracle_pins.py.
 """
@@ -1023,7 +1027,7 @@ def estimate_sigma_volume(v: np.ndarray, params=None) -> float:
 
 
 def a_haar_tsvd_volume(v: np.ndarray, sub: tuple, params=None):
-    """Alg. 2 on a volume (readings R15 and R20, the paper's adaptive variant on MRI): each axis cut
+    """Alg. 2 on a volume (reading R21, the paper's adaptive variant on MRI): each axis cut
     into sub-volumes as R15 cuts image axes; per sub-volume the noise level by the eigenvalue rule on
     its reference cubes (estimate_sigma_volume) and Alg. 1 at that level. The eigen-rank vote of R12
     is not applied to volumes. Returns (output (D, H, W) float64, sigmas in z-major sub-volume order)."""
