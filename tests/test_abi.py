@@ -175,3 +175,16 @@ def test_binding_checks_buffers_before_they_reach_the_library():
         _need(t.transpose(0, 1), "out", (5, 4, 3), torch.float32)
     with pytest.raises(ValueError, match="CUDA"):
         _need(t, "grad_out", (4, 5, 3), torch.float32)     # a host tensor never reaches the library
+
+
+def test_volume_adaptive_rejects_bad_arguments_on_the_host():
+    lib = H.load_library()
+    cp = H.HtsvdParams.of(None).c()
+    one = ctypes.c_void_p(1)
+    sig = (ctypes.c_double * 8)()
+    f = lib.htsvd_denoise_volume_adaptive
+    assert f(None, 32, 32, 32, 16, 16, 16, ctypes.byref(cp), one, sig, None) == 1          # no input
+    assert f(one, 32, 32, 32, 16, 16, 16, ctypes.byref(cp), None, sig, None) == 1          # no output
+    assert f(one, 32, 32, 32, 0, 16, 16, ctypes.byref(cp), one, sig, None) == 1            # part size 0
+    assert f(one, 0, 32, 32, 16, 16, 16, ctypes.byref(cp), one, sig, None) == 1            # empty volume
+    assert f(one, 2048, 1024, 1024, 512, 512, 512, ctypes.byref(cp), one, sig, None) == 2  # 2^31 voxels
