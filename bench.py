@@ -363,6 +363,22 @@ class Workload:
         self.per_input = per_input
 
 
+def volume_adaptive_groups(shape, sub, ps, stride):
+    """Reference cubes over all sub-volumes of the adaptive volume call: per part and axis the grid
+    {0, s, 2s, ...} plus the last position n - ps."""
+    from paper_2508_10307_gb300 import subimage_bounds
+
+    def grid(n):
+        return len(range(0, n - ps + 1, stride)) + (1 if (n - ps) % stride else 0)
+
+    total = 0
+    for z0, z1 in subimage_bounds(shape[0], sub[0]):
+        for y0, y1 in subimage_bounds(shape[1], sub[1]):
+            for x0, x1 in subimage_bounds(shape[2], sub[2]):
+                total += grid(z1 - z0) * grid(y1 - y0) * grid(x1 - x0)
+    return total
+
+
 def make_workload(name):
     import numpy as np
     import torch
@@ -487,6 +503,26 @@ def make_workload(name):
 
         def step(d):
             return [H.denoise_volume(x, None if est else 11.5, prm) for x in d]
+
+        return Workload(name, cfg, 176 * 208 * 176 / 1e6, n, 4, 32, [noisy], step, 176 * 208 * 176 * 4), \
+            synth.quantize(clean)
+    if name == "mri176adapt":
+        # the adaptive variant (Alg. 2) on the MRI-sized volume: 2 x 2 x 2 sub-volumes of 88 x 104 x 88, a
+        # sigma per sub-volume from its reference cubes' covariance eigenvalues, each part denoised on its own
+        clean = synth.clean_volume(176, 208, 176, 3)
+        noisy = synth.add_gaussian(clean, 11.5, 3)
+        prm = dict(ps=4, stride=2, window=5, K=32)
+        sub = (88, 104, 88)
+        n = volume_adaptive_groups((176, 208, 176), sub, 4, 2)
+        cfg = {"workload": "mri_volume_176x208x176_adaptive_2x2x2",
+               "volume": "176x208x176 uint8 (head-like phantom)",
+               "noise": "gaussian sigma=11.5 (4.5% of 255; stands in for VST-stabilised Rician noise)",
+               "sigma": "estimated per sub-volume (cube-covariance eigenvalues)", "sub_volume": "88x104x88",
+               "ps": "4x4x4", "stride": 2, "window": "5x5x5", "K": 32,
+               "unit_note": "MP/s counts voxels (D H W) as pixels"}
+
+        def step(d):
+            return [H.denoise_volume_adaptive(x, sub, prm) for x in d]
 
         return Workload(name, cfg, 176 * 208 * 176 / 1e6, n, 4, 32, [noisy], step, 176 * 208 * 176 * 4), \
             synth.quantize(clean)
@@ -869,7 +905,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rgb4k", choices=["rgb512", "gray128", "rgb4k", "rgb1080", "hsi696", "batch64", "vjp8", "adaptive512",
-                                                      "video1080", "sweep512", "sure512", "tunew512", "proj512", "proj512all", "mri176", "mri176est"])
+                                                      "video1080", "sweep512", "sure512", "tunew512", "proj512", "proj512all", "mri176", "mri176est",
+                                                      "mri176adapt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
