@@ -977,3 +977,27 @@ def test_adaptive_volume_estimates_each_part_on_its_own():
     assert abs(sig[0] - 4.0) <= 0.05 * 4.0 and abs(sig[1] - 16.0) <= 0.05 * 16.0
     lower = np.ascontiguousarray(v[16:])
     assert np.abs(out[16:] - O.denoise_volume(lower, sig[1], prm).out).max() == 0.0
+
+
+def test_subimage_bounds_are_the_floor_boundaries():
+    """Reading R15's boundaries floor(i n / t), worked by hand: a ceiling or rounded variant moves them."""
+    assert O.subimage_bounds(41, 20) == [(0, 20), (20, 41)]
+    assert O.subimage_bounds(100, 30) == [(0, 33), (33, 66), (66, 100)]
+    assert O.subimage_bounds(29, 14) == [(0, 14), (14, 29)]
+    assert O.subimage_bounds(26, 13) == [(0, 13), (13, 26)]
+    assert O.subimage_bounds(7, 20) == [(0, 7)]
+
+
+def test_adaptive_volume_places_ragged_parts_where_they_came_from():
+    """2 x 1 x 2 ragged parts of a 21 x 12 x 23 volume (bounds worked by hand: z 0|10|21, x 0|11|23):
+    every part of the output is Alg. 1 on that part alone at that part's own estimate."""
+    v = _volume(21, 12, 23, 23)
+    prm = dict(ps=4, stride=2, window=4, K=8)
+    out, sig = O.a_haar_tsvd_volume(v, (10, 12, 11), prm)
+    assert sig.shape == (4,)
+    parts = [((0, 10), (0, 11)), ((0, 10), (11, 23)), ((10, 21), (0, 11)), ((10, 21), (11, 23))]
+    for t, ((z0, z1), (x0, x1)) in enumerate(parts):
+        part = np.ascontiguousarray(v[z0:z1, :, x0:x1])
+        s = O.estimate_sigma_volume(part, prm)
+        assert sig[t] == s
+        assert np.abs(out[z0:z1, :, x0:x1] - O.denoise_volume(part, s, prm).out).max() == 0.0
