@@ -810,20 +810,22 @@ def _volume(D, Hh, Wd, seed, sigma=11.0):
     return synth.add_gaussian(synth.clean_volume(D, Hh, Wd, seed), sigma, seed)
 
 
-def test_volume_grouping_against_brute_force():
+@pytest.mark.parametrize("spoil", [0.2, 0.004])
+def test_volume_grouping_against_brute_force(spoil):
     """Grouping of cubes: exact SSD over the ps^3 voxels of every candidate of the clamped W^3 window,
-    written out voxel by voxel in plain Python; a volume with repeated 2 x 2 x 2 tiles makes many
-    keys tie, which the lowest linear index must break."""
+    written out voxel by voxel in plain Python; a volume with repeated 2 x 2 x 2 tiles, a few voxels
+    overwritten, makes many keys tie, which the lowest linear index must break (the sparse case has
+    groups whose K - 1 cut falls inside a run of equal keys)."""
     rng = np.random.default_rng(61)
     tile = rng.integers(0, 256, size=(2, 2, 2))
     v = np.tile(tile, (5, 6, 5)).astype(np.int64)
-    v[rng.random(v.shape) < 0.2] = 9
+    v[rng.random(v.shape) < spoil] = 9
     v = v.astype(np.uint8)[:9, :11, :10]
     p = O.Params(ps=4, stride=2, window=3, K=6)
     idx = O.block_match_volume(v, p)
     D, Hh, Wd = v.shape
     vv = v.astype(int).tolist()
-    n = 0
+    n = cut_ties = 0
     for rz in O.reference_positions(D, 4, 2):
         for ry in O.reference_positions(Hh, 4, 2):
             for rx in O.reference_positions(Wd, 4, 2):
@@ -839,8 +841,11 @@ def test_volume_grouping_against_brute_force():
                                 keys.append((d, (z * Hh + y) * Wd + x))
                 keys.sort()
                 assert list(idx[n]) == [(rz * Hh + ry) * Wd + rx] + [k[1] for k in keys[:5]]
+                cut_ties += keys[4][0] == keys[5][0]
                 n += 1
     assert n == idx.shape[0]
+    if spoil < 0.1:
+        assert cut_ties > 0
 
 
 def test_volume_cube_gather_and_aggregation_counts():
@@ -1001,3 +1006,60 @@ def test_adaptive_volume_places_ragged_parts_where_they_came_from():
         s = O.estimate_sigma_volume(part, prm)
         assert sig[t] == s
         assert np.abs(out[z0:z1, :, x0:x1] - O.denoise_volume(part, s, prm).out).max() == 0.0
+
+
+def test_rank_gamma_is_13K_over_32_rounded_half_up():
+    """Reading R12's default gamma_rank = 13 K / 32 rounded half up, worked by hand (K = 16: 6.5 -> 7)."""
+    for K, g in ((2, 1), (4, 2), (8, 3), (16, 7), (32, 13), (64, 26)):
+        assert O.rank_gamma(O.Params(K=K)) == g
+
+
+def test_canonical_phase_takes_the_lowest_index_among_equal_moduli():
+    """Reading R7 on matrices whose eigenvectors have two entries of equal modulus (worked by hand):
+    [[2, 1], [1, 2]] has (1, 1)/sqrt 2 for 3 and (1, -1)/sqrt 2 for 1; [[2, i], [-i, 2]] has
+    (1, -i)/sqrt 2 for 3 and (1, i)/sqrt 2 for 1: the first entry is made real positive."""
+    r = 1 / math.sqrt(2)
+    w, Q = O.canonical_eigvecs(np.array([[2.0, 1.0], [1.0, 2.0]], dtype=complex))
+    assert np.allclose(w, [3.0, 1.0]) and np.allclose(Q, [[r, r], [r, -r]], atol=1e-14)
+    w, Q = O.canonical_eigvecs(np.array([[2.0, 1j], [-1j, 2.0]]))
+    assert np.allclose(w, [3.0, 1.0]) and np.allclose(Q, [[r, r], [-1j * r, 1j * r]], atol=1e-14)
+
+
+def test_threshold_keeps_a_coefficient_equal_to_tau():
+    """Reading R9: a coefficient whose magnitude equals tau is kept; one ulp below is dropped."""
+    tau = 7.25
+    below = np.nextafter(tau, 0.0)
+    S = np.array([tau, -tau, below, -below, 2 * tau, 0.0])
+    assert O.hard_threshold_mask(S, tau).tolist() == [True, True, False, False, True, False]
+
+
+def test_sigma_rule_takes_the_mean_of_the_largest_qualifying_run():
+    """Reading R11 worked by hand. [0.9, 1, 1, 1.05, 40, 90]: the runs r = 1..4 qualify (mean against
+    1.02 median: 0.9/0.9, 0.95/0.95, 0.967/1, 0.9875/1), r = 5, 6 do not, so sigma^2 = 0.9875, the run's
+    mean (its median is 1). [1] * 4 + [3] * 8: r = 5..7 fail, r = 8..12 qualify again (r = 12: mean
+    7/3 <= 1.02 x 3), so r* = 12, the largest qualifying run, not the last before a failure."""
+    assert abs(O.sigma_from_eigenvalues(np.array([0.9, 1.0, 1.0, 1.05, 40.0, 90.0])) - math.sqrt(0.9875)) < 1e-12
+    assert abs(O.sigma_from_eigenvalues(np.array([1.0] * 4 + [3.0] * 8)) - math.sqrt(7.0 / 3.0)) < 1e-12
+
+
+def _offset_pair(shape, seed):
+    rng = np.random.default_rng(seed)
+    base = np.clip(np.rint(60.0 + 25.0 * rng.standard_normal(shape)), 0, 150).astype(np.int64)
+    ramp = (np.indices(shape).sum(axis=0) % 7) * 3          # some structure besides the noise
+    a = np.clip(base + ramp, 0, 150)
+    return a.astype(np.uint8), (a + 100).astype(np.uint8)
+
+
+def test_sigma_estimate_is_invariant_to_a_constant_offset():
+    """The patch covariance is centred (Sec. III-D), so adding a constant to every pixel (no clipping)
+    leaves the estimate unchanged; an uncentred second moment would move it."""
+    a, b = _offset_pair((96, 104, 3), 31)
+    sa, sb = (O.estimate_sigma(x, dict(ps=8, stride=2)) for x in (a, b))
+    assert abs(sa - sb) <= 1e-9 * sa
+
+
+def test_volume_sigma_estimate_is_invariant_to_a_constant_offset():
+    a, b = _offset_pair((30, 28, 26), 32)
+    prm = dict(ps=4, stride=2, window=5, K=8)
+    sa, sb = (O.estimate_sigma_volume(x, prm) for x in (a, b))
+    assert abs(sa - sb) <= 1e-9 * sa
