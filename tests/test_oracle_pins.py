@@ -1063,3 +1063,70 @@ def test_volume_sigma_estimate_is_invariant_to_a_constant_offset():
     prm = dict(ps=4, stride=2, window=5, K=8)
     sa, sb = (O.estimate_sigma_volume(x, prm) for x in (a, b))
     assert abs(sa - sb) <= 1e-9 * sa
+
+
+def test_float_inputs_are_quantised_by_rounding_to_nearest():
+    """Reading R13: q = clip(rint(x)), worked by hand (rint takes halves to even)."""
+    x = np.array([[[0.4], [0.6], [254.6], [-3.0]], [[300.0], [2.5], [3.5], [17.49]]])
+    assert O._as_quantised(x)[..., 0].tolist() == [[0, 1, 255, 0], [255, 2, 4, 17]]
+
+
+def test_sparsity_weight_of_a_group_keeping_one_coefficient_is_one():
+    """Reading R10: w_g = 1 / max(1, #kept). On a constant image every patch of every group is the same
+    constant patch, whose only non-zero coefficient is the DC one (Haar row 0, basis row and column 0),
+    so at a small threshold each group keeps exactly one coefficient and its weight is 1."""
+    x = np.full((24, 28, 1), 100, dtype=np.uint8)
+    r = O.denoise(x, 1.0, dict(ps=8, stride=4, window=9, K=8, tau_mult=1e-3, agg_mode="sparsity"), keep_masks=True)
+    assert (r.masks.reshape(r.masks.shape[0], -1).sum(axis=1) == 1).all()
+    assert (r.weights == 1.0).all()
+    assert np.abs(r.out - 100.0).max() < 1e-9
+
+
+def test_sparsity_weight_of_a_group_keeping_nothing_is_one():
+    """Reading R10's max(1, .): a group that keeps no coefficient still weighs 1 (images and volumes);
+    with nothing kept the estimate is zero."""
+    x = synth.add_gaussian(synth.clean_image(24, 28, 3, seed=46), 10.0, seed=46)
+    r = O.denoise(x, 10.0, dict(ps=8, stride=4, window=9, K=8, tau_mult=1e9, agg_mode="sparsity"))
+    assert (r.weights == 1.0).all() and np.abs(r.out).max() == 0.0
+    v = _volume(12, 13, 14, 46)
+    r = O.denoise_volume(v, 10.0, dict(ps=4, stride=2, window=5, K=8, tau_mult=1e9, agg_mode="sparsity"))
+    assert (r.weights == 1.0).all() and np.abs(r.out).max() == 0.0
+
+
+def test_video_estimates_sigma_frame_by_frame():
+    """Reading R16: sigma = None estimates each frame's own level; frames with noise 4 and 16 on the
+    same flat frame give estimates in the ratio 4."""
+    rng = np.random.default_rng(44)
+    base = np.full((96, 96), 120.0)
+    clip = np.stack([np.clip(np.rint(base + s * rng.standard_normal(base.shape)), 0, 255) for s in (4.0, 16.0)])
+    _, res = O.denoise_video(clip.astype(np.uint8), None, dict(ps=8, stride=4, window=9, K=8), T=0)
+    s0, s1 = (r.extra["sigma"] for r in res)
+    # 529 reference patches of 64 pixels bias both estimates low alike; their ratio is the noise ratio
+    assert abs(s1 / s0 - 4.0) <= 0.05 * 4.0
+    assert abs(s0 - 4.0) <= 0.15 * 4.0 and abs(s1 - 16.0) <= 0.15 * 16.0
+
+
+def test_perturbed_image_is_formed_in_float32():
+    """Reading R17: z = y + eps b is formed in float32 with each operation rounded once, so every value
+    of z is a float32 number and equals the float32 sum of the float32 product."""
+    rng = np.random.default_rng(45)
+    y = (255 * rng.random((17, 19, 3))).astype(np.float32)
+    b = rng.choice([-1.0, 1.0], size=y.shape) * (1 + rng.random(y.shape))
+    z = O.perturbed(y, b, 0.37)
+    assert (z.astype(np.float32).astype(np.float64) == z).all()
+    assert (z == (y + np.float32(0.37) * b.astype(np.float32)).astype(np.float64)).all()
+    assert not (z == y.astype(np.float64) + 0.37 * b).all()
+
+
+def test_basis_gap_is_relative_to_the_largest_eigenvalue():
+    """Reading R7's gap: min |l_i - l_(i+1)| / |l_max|, worked by hand; unchanged by scaling."""
+    assert O.basis_gap(np.array([4.0, 1.0, 2.0])) == 0.25
+    assert O.basis_gap(np.array([400.0, 100.0, 200.0])) == 0.25
+    assert O.basis_gap(np.array([3.0, 3.0, 1.0])) == 0.0
+
+
+def test_volume_reference_positions_are_z_major():
+    """Reading R20: the reference cubes of a 6 x 6 x 6 volume at ps 4, stride 2 (per axis {0, 2}),
+    z-major, as linear positions (z H + y) W + x worked by hand."""
+    assert O.volume_reference_positions((6, 6, 6), O.Params(ps=4, stride=2)).tolist() == \
+        [0, 2, 12, 14, 72, 74, 84, 86]
