@@ -1130,3 +1130,33 @@ def test_volume_reference_positions_are_z_major():
     z-major, as linear positions (z H + y) W + x worked by hand."""
     assert O.volume_reference_positions((6, 6, 6), O.Params(ps=4, stride=2)).tolist() == \
         [0, 2, 12, 14, 72, 74, 84, 86]
+
+
+def test_weight_tuning_step_is_normalised_by_the_largest_gradient():
+    """Reading R19's step w <- w exp(-step g / max|g|): from uniform weights one step moves the weight
+    with the largest gradient by exactly a factor exp(-+step) and every other weight by less, in the
+    direction opposite to its gradient."""
+    clean, y, b, prm, w, rng = _sure_w_case(18)
+    _, g = O.sure_weights(y, 20.0, np.ones_like(w), b, prm, eps=2.0)
+    wt, _ = O.tune_weights(y, 20.0, b, prm, eps=2.0, steps=1, step=0.3)
+    lw = np.log(wt)
+    assert abs(np.abs(lw).max() - 0.3) < 1e-12
+    assert np.argmax(np.abs(lw)) == np.argmax(np.abs(g))
+    assert np.all(lw * g <= 0)
+
+
+def test_reference_patches_in_row_major_grid_order():
+    """Reading R3: reference patches of a 10 x 12 image at ps 8, stride 2 (rows {0, 2}, columns
+    {0, 2, 4}), row-major, identified by their top-left pixel (the image holds y * 12 + x)."""
+    x = (np.arange(10 * 12).reshape(10, 12, 1) % 256).astype(np.uint8)
+    P = O.reference_patches(x, O.Params(ps=8, stride=2))
+    assert P[:, 0, 0, 0].tolist() == [0, 2, 4, 24, 26, 28]
+
+
+def test_rgb_green_plane_mode_groups_on_the_green_channel():
+    """The green-plane mode on RGB matches on G alone: its grouping is the gray grouping of G."""
+    img = synth.add_gaussian(synth.clean_image(40, 44, 3, seed=47), 15.0, seed=47)
+    prm = dict(ps=8, stride=3, window=9, K=8)
+    idx_rgb, _ = O.block_match(img, O.Params.of(dict(prm, match_mode="gray")))
+    idx_g, _ = O.block_match(np.ascontiguousarray(img[:, :, 1:2]), O.Params.of(prm))
+    np.testing.assert_array_equal(idx_rgb, idx_g)
