@@ -7,10 +7,12 @@
  *
  * Conventions shared by every entry point
  *  - Images are contiguous row-major H x W x C (HWC), C in {1, 3}, on the
- *    [0, 255] scale. Pointers named d_* are DEVICE pointers owned by the caller;
- *    pointers named h_* or documented as host are HOST pointers.
+ *    [0, 255] scale (hyperspectral cubes take C = N bands and MRI volumes are
+ *    D x H x W: see those calls). Pointers named d_* are DEVICE pointers owned by
+ *    the caller; pointers named h_* or documented as host are HOST pointers.
  *  - Patches are ps x ps with ps = 8 (the paper's value, Sec. IV-A; other sizes
- *    return HTSVD_ERR_UNSUPPORTED). K is a power of two in [2, 32].
+ *    return HTSVD_ERR_UNSUPPORTED; volumes use 4 x 4 x 4 cubes). K is a power of
+ *    two in [2, 32].
  *  - Reference patches sit on the grid {0, s, 2s, ...} U {n - ps} of each axis,
  *    row-major; group g belongs to the g-th reference of that order.
  *  - Match indices are int32 linear top-left positions y * W + x, K per group;
@@ -72,7 +74,7 @@ typedef struct htsvd_params {
     int32_t agg_mode;      /* htsvd_agg_mode */
     int32_t adapt;         /* sigma estimation: apply the eigen-rank vote of Eq. (adjust noise level) */
     double  beta;          /* <= 0 -> 1.2 (Sec. III-D) */
-    int32_t rank_gamma;    /* <= 0 -> round(13 K / 32) (Sec. III-D) */
+    int32_t rank_gamma;    /* <= 0 -> 13 K / 32 rounded half up, (13 K + 16) / 32 (Sec. III-D) */
     int32_t tile;          /* reference tile edge for the filter (0 -> automatic), at most 16 */
     /* Optional outputs (may be NULL). */
     double*   h_sigma_out;   /* HOST: the sigma actually used (estimated when sigma < 0) */
@@ -87,8 +89,9 @@ typedef struct htsvd_params {
      * scatter matrices; where two eigenvalues coincide the eigenvectors, and so the thresholded
      * coefficients, are not unique). The gap of a slice is min_i |l_i - l_{i+1}| / |l_max| over its
      * eigenvalues; the check takes the smallest over all U and V slices. Either field makes the call
-     * synchronise `stream` once after the basis solve. Honoured by htsvd_denoise, htsvd_denoise_f32 and
-     * htsvd_denoise_noalloc. */
+     * synchronise `stream` once after the basis solve. Honoured by htsvd_denoise, htsvd_denoise_f32,
+     * htsvd_denoise_noalloc, htsvd_denoise_cube and htsvd_denoise_volume; htsvd_denoise_volume_adaptive
+     * applies strict_basis to every part and does not report a gap. */
     int32_t   strict_basis;  /* nonzero: return HTSVD_ERR_DEGENERATE_BASIS (before the filter runs, d_out
                                 unwritten) when that gap is below 1e-9; zero: no check (production) */
     double*   h_basis_gap_out; /* HOST (may be NULL): receives that smallest relative gap */
