@@ -108,3 +108,22 @@ def test_host_volume_bases_report_a_degenerate_constant_volume():
     assert gap == 0.0 and O.global_basis_gap(lu, lv) == 0.0
     with pytest.raises(O.DegenerateBasis):
         O.denoise_volume(v, 5.0, dict(ps=4, stride=2, window=5, K=8, strict_basis=True))
+
+
+def test_host_volume_bases_take_the_lowest_index_among_equal_moduli():
+    """Reading R7's tie rule in the library's 4 x 4 solver: reference cubes closed under swapping rows 0
+    and 1 (and columns 0 and 1) make every slice matrix commute with that swap, so its antisymmetric
+    eigenvectors have two entries of equal modulus; the first is made real positive, as in the oracle."""
+    lib = H.load_library()
+    rng = np.random.default_rng(12)
+    P0 = rng.integers(0, 256, size=(40, 4, 4, 4)).astype(np.float64)
+    Pi = P0[:, [1, 0, 2, 3]]
+    P = np.concatenate([P0, Pi, P0[:, :, [1, 0, 2, 3]], Pi[:, :, [1, 0, 2, 3]]])
+    b = np.zeros(256)
+    lib.htsvd_internal_volume_bases(_moments(P).ctypes.data, b.ctypes.data)
+    U, V, _, _ = O.global_basis(P)
+    z = (b[0::2] + 1j * b[1::2]).reshape(2, 4, 4, 4)
+    ties = sum(int(np.sum(np.isclose(np.abs(M[f][:, i]), np.abs(M[f][:, i]).max(), rtol=1e-9)) > 1)
+               for M in (U, V) for f in range(4) for i in range(4))
+    assert ties > 0
+    assert np.abs(z[0] - U).max() < 1e-9 and np.abs(z[1] - V).max() < 1e-9
