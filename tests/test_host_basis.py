@@ -127,3 +127,31 @@ def test_host_volume_bases_take_the_lowest_index_among_equal_moduli():
                for M in (U, V) for f in range(4) for i in range(4))
     assert ties > 0
     assert np.abs(z[0] - U).max() < 1e-9 and np.abs(z[1] - V).max() < 1e-9
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_host_slice_basis_takes_the_lowest_index_among_equal_moduli(C):
+    """The image path's slice solver on reference patches closed under swapping rows 0 and 1 (and
+    columns 0 and 1): antisymmetric eigenvectors have two entries of equal modulus, and the first is
+    made real positive, as in the oracle (reading R7)."""
+    lib = H.load_library()
+    lib.htsvd_internal_slice_basis.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_void_p]
+    lib.htsvd_internal_slice_basis.restype = None
+    rng = np.random.default_rng(13 + C)
+    sw = [1, 0, 2, 3, 4, 5, 6, 7]
+    P0 = rng.integers(0, 256, size=(30, 8, 8, C)).astype(np.int64)
+    Pi = P0[:, sw]
+    P = np.concatenate([P0, Pi, P0[:, :, sw], Pi[:, :, sw]])
+    U, V, _, _ = O.global_basis(P.astype(float))
+    mom = _moments(P)
+    ties = 0
+    for which, ref in ((0, U), (1, V)):
+        for f in range(C // 2 + 1):
+            out = np.zeros(128)
+            lib.htsvd_internal_slice_basis(mom.ctypes.data, C, which, f, out.ctypes.data)
+            z = (out[0::2] + 1j * out[1::2]).reshape(8, 8)
+            assert np.abs(z - ref[f]).max() < 1e-9
+            ties += sum(int(np.sum(np.isclose(np.abs(ref[f][:, i]), np.abs(ref[f][:, i]).max(), rtol=1e-9)) > 1)
+                        for i in range(8))
+    assert ties > 0
