@@ -417,7 +417,7 @@ def sure(y, sigma, tau_mults, probe, params=None, eps=None, stream=None):
     res = (ctypes.c_double * len(m))()
     cp = HtsvdParams.of(params).c()
     e = 0.1 * float(sigma) if eps is None else float(eps)
-    _lib.check(lib.htsvd_sure(_ptr(x.contiguous()), H, W, C, float(sigma), (ctypes.c_double * len(m))(*m), len(m),
+    _lib.check(lib.htsvd_sure(_ptr(x), H, W, C, float(sigma), (ctypes.c_double * len(m))(*m), len(m),
                               _ptr(b), e, ctypes.byref(cp), res, _stream_ptr(stream)), "htsvd_sure")
     return [float(v) for v in res]
 
@@ -440,7 +440,7 @@ def sure_weights(y, sigma, w, probe, params=None, eps=None, stream=None):
     res = ctypes.c_double()
     cp = p.c()
     e = 0.1 * float(sigma) if eps is None else float(eps)
-    _lib.check(lib.htsvd_sure_weights(_ptr(x.contiguous()), H, W, C, float(sigma), _ptr(wt), _ptr(b.contiguous()), e,
+    _lib.check(lib.htsvd_sure_weights(_ptr(x), H, W, C, float(sigma), _ptr(wt), _ptr(b), e,
                                       ctypes.byref(cp), ctypes.byref(res), _ptr(g), _stream_ptr(stream)),
                "htsvd_sure_weights")
     return float(res.value), g
@@ -464,7 +464,7 @@ def tune_weights(y, sigma, probe, params=None, eps=None, steps=3, step=0.5, w0=N
     trace = (ctypes.c_double * (int(steps) + 1))()
     cp = p.c()
     e = 0.1 * float(sigma) if eps is None else float(eps)
-    _lib.check(lib.htsvd_tune_weights(_ptr(x.contiguous()), H, W, C, float(sigma), _ptr(b.contiguous()), e,
+    _lib.check(lib.htsvd_tune_weights(_ptr(x), H, W, C, float(sigma), _ptr(b), e,
                                       int(steps), float(step), ctypes.byref(cp), _ptr(w), trace, _stream_ptr(stream)),
                "htsvd_tune_weights")
     return w, [float(v) for v in trace]

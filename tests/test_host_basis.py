@@ -102,8 +102,9 @@ def test_host_volume_bases_report_a_degenerate_constant_volume():
     v = np.full((12, 13, 14), 77, dtype=np.uint8)
     p = O.Params(ps=4, stride=2, window=5, K=8)
     P = O.gather_cubes(v, O.volume_reference_positions(v.shape, p), 4)
+    mom = _moments(P)                      # held: the library reads it through a raw pointer
     b = np.zeros(256)
-    gap = lib.htsvd_internal_volume_bases(_moments(P).ctypes.data, b.ctypes.data)
+    gap = lib.htsvd_internal_volume_bases(mom.ctypes.data, b.ctypes.data)
     _, _, lu, lv = O.global_basis(P)
     assert gap == 0.0 and O.global_basis_gap(lu, lv) == 0.0
     with pytest.raises(O.DegenerateBasis):
@@ -119,8 +120,9 @@ def test_host_volume_bases_take_the_lowest_index_among_equal_moduli():
     P0 = rng.integers(0, 256, size=(40, 4, 4, 4)).astype(np.float64)
     Pi = P0[:, [1, 0, 2, 3]]
     P = np.concatenate([P0, Pi, P0[:, :, [1, 0, 2, 3]], Pi[:, :, [1, 0, 2, 3]]])
+    mom = _moments(P)                      # held: the library reads it through a raw pointer
     b = np.zeros(256)
-    lib.htsvd_internal_volume_bases(_moments(P).ctypes.data, b.ctypes.data)
+    lib.htsvd_internal_volume_bases(mom.ctypes.data, b.ctypes.data)
     U, V, _, _ = O.global_basis(P)
     z = (b[0::2] + 1j * b[1::2]).reshape(2, 4, 4, 4)
     ties = sum(int(np.sum(np.isclose(np.abs(M[f][:, i]), np.abs(M[f][:, i]).max(), rtol=1e-9)) > 1)
