@@ -286,7 +286,8 @@ htsvd_status htsvd_denoise_volume(const uint8_t* d_vol, int32_t D, int32_t H, in
  * h_sigmas (HOST, may be NULL) receives the sigmas in z-major sub-volume order. Synchronises
  * `stream` once per sub-volume (host eigenvalue step). Errors: INVALID_ARG for a null pointer, a
  * sub size < 1, or a sub-volume that fails the checks of htsvd_denoise_volume (each part must be
- * at least 4 long and hold K cubes in its window); UNSUPPORTED as for htsvd_denoise_volume. The
+ * at least 4 long and hold K cubes in its window); UNSUPPORTED as for htsvd_denoise_volume. Every
+ * part is checked before any device work, so on these errors d_out is left untouched. The
  * per-volume optional outputs of p (masks, weights, basis, gap, sigma) are ignored. */
 htsvd_status htsvd_denoise_volume_adaptive(const uint8_t* d_vol, int32_t D, int32_t H, int32_t W, int32_t sub_d,
                                            int32_t sub_h, int32_t sub_w, const htsvd_params* p, float* d_out,

@@ -1351,6 +1351,24 @@ htsvd_status htsvd_denoise_volume_adaptive(const uint8_t* d_vol, int32_t D, int3
         in_bytes += ((size_t)B.d * B.h * B.w + 255) & ~(size_t)255;
         out_bytes += (sizeof(float) * B.d * B.h * B.w + 255) & ~(size_t)255;
     }
+    // every part passes the checks of htsvd_denoise_volume before any device work, so a bad part
+    // size leaves d_out untouched
+    {
+        htsvd_params z;
+        std::memset(&z, 0, sizeof(z));
+        const htsvd_params& c = p ? *p : z;
+        const int ps = c.ps > 0 ? c.ps : 4, stride = c.stride > 0 ? c.stride : 2;
+        const int win = c.window > 0 ? c.window : 5, K = c.K > 0 ? c.K : 32;
+        if (ps != 4) return HTSVD_ERR_UNSUPPORTED;
+        if (K < 2 || K > 32 || (K & (K - 1)) != 0 || win < 1 || win > volume_max_window()) return HTSVD_ERR_INVALID_ARG;
+        if (c.match_mode != HTSVD_MATCH_AUTO && c.match_mode != HTSVD_MATCH_FULL) return HTSVD_ERR_INVALID_ARG;
+        if (c.agg_mode != HTSVD_AGG_UNIFORM && c.agg_mode != HTSVD_AGG_SPARSITY) return HTSVD_ERR_INVALID_ARG;
+        for (const Box& B : boxes) {
+            if (B.d < ps || B.h < ps || B.w < ps) return HTSVD_ERR_INVALID_ARG;
+            const VolGeo g = make_vol_geo(B.d, B.h, B.w, stride, win, K);
+            if ((int64_t)g.wnz * g.wny * g.wnx < K) return HTSVD_ERR_INVALID_ARG;
+        }
+    }
     Workspace* w = workspace_for(s);
     if (!w) return HTSVD_ERR_OOM;
     void *vin, *vout;

@@ -188,3 +188,14 @@ def test_volume_adaptive_rejects_bad_arguments_on_the_host():
     assert f(one, 32, 32, 32, 0, 16, 16, ctypes.byref(cp), one, sig, None) == 1            # part size 0
     assert f(one, 0, 32, 32, 16, 16, 16, ctypes.byref(cp), one, sig, None) == 1            # empty volume
     assert f(one, 2048, 1024, 1024, 512, 512, 512, ctypes.byref(cp), one, sig, None) == 2  # 2^31 voxels
+    # every part is checked before any device work (no GPU is touched here)
+    vp = H.HtsvdParams.of(dict(H.VOLUME_DEFAULTS)).c()
+    assert f(one, 16, 16, 16, 2, 16, 16, ctypes.byref(vp), one, sig, None) == 1            # parts 2 deep
+    assert f(one, 16, 16, 16, 16, 16, 3, ctypes.byref(vp), one, sig, None) == 1            # parts 3 wide
+    small = H.HtsvdParams.of(dict(H.VOLUME_DEFAULTS, window=1, K=4)).c()
+    assert f(one, 16, 16, 16, 8, 8, 8, ctypes.byref(small), one, sig, None) == 1           # 1 cube per window < K
+    for bad in (dict(K=12), dict(window=9), dict(match_mode="gcp")):
+        c = H.HtsvdParams.of(dict(H.VOLUME_DEFAULTS, **bad)).c()
+        assert f(one, 16, 16, 16, 8, 8, 8, ctypes.byref(c), one, sig, None) == 1
+    c = H.HtsvdParams.of(dict(H.VOLUME_DEFAULTS, ps=8)).c()
+    assert f(one, 16, 16, 16, 8, 8, 8, ctypes.byref(c), one, sig, None) == 2
