@@ -199,3 +199,56 @@ def test_volume_adaptive_rejects_bad_arguments_on_the_host():
         assert f(one, 16, 16, 16, 8, 8, 8, ctypes.byref(c), one, sig, None) == 1
     c = H.HtsvdParams.of(dict(H.VOLUME_DEFAULTS, ps=8)).c()
     assert f(one, 16, 16, 16, 8, 8, 8, ctypes.byref(c), one, sig, None) == 2
+
+
+def test_volume_rejects_bad_arguments_on_the_host():
+    lib = H.load_library()
+    one, four = ctypes.c_void_p(1), ctypes.c_void_p(4)
+    f = lambda vol, D, Hh, Wd, sigma, prm, out=four: lib.htsvd_denoise_volume(
+        vol, D, Hh, Wd, sigma, ctypes.byref(H.HtsvdParams.of(dict(H.VOLUME_DEFAULTS, **prm)).c()), out, None, None)
+    assert f(None, 16, 16, 16, 10.0, {}) == 1                  # no volume
+    assert f(four, 16, 16, 16, 10.0, {}, None) == 1            # no output
+    assert f(one, 16, 16, 16, 10.0, {}) == 1                   # volume not 4-byte aligned
+    assert f(four, 16, 16, 16, float("nan"), {}) == 1          # sigma not a number
+    assert f(four, 16, 16, 16, float("inf"), {}) == 1
+    assert f(four, 3, 16, 16, 10.0, {}) == 1                   # thinner than a cube
+    assert f(four, 16, 16, 16, 10.0, dict(ps=8)) == 2          # only 4 x 4 x 4 cubes are built
+    assert f(four, 16, 16, 16, 10.0, dict(K=12)) == 1          # K not a power of two
+    assert f(four, 16, 16, 16, 10.0, dict(K=64)) == 1          # K above 32
+    assert f(four, 16, 16, 16, 10.0, dict(window=9)) == 1      # window above 8
+    assert f(four, 16, 16, 16, 10.0, dict(match_mode="gcp")) == 1
+    assert f(four, 16, 16, 16, 10.0, dict(window=1, K=4)) == 1  # one cube per window, fewer than K
+    assert f(four, 2048, 1024, 1024, 10.0, {}) == 2            # 2^31 voxels
+
+
+def test_cube_rejects_bad_arguments_on_the_host():
+    lib = H.load_library()
+    one = ctypes.c_void_p(1)
+    f = lambda cube, Hh, Wd, N, sigma, prm, out=one: lib.htsvd_denoise_cube(
+        cube, Hh, Wd, N, sigma, ctypes.byref(H.HtsvdParams.of(prm).c()), out, None, None)
+    assert f(None, 64, 64, 31, 10.0, {}) == 1                  # no cube
+    assert f(one, 64, 64, 31, 10.0, {}, None) == 1             # no output
+    assert f(one, 64, 64, 31, -1.0, {}) == 1                   # sigma must be given
+    assert f(one, 64, 64, 31, float("inf"), {}) == 1
+    assert f(one, 64, 64, 1, 10.0, {}) == 1                    # N below 2
+    assert f(one, 64, 64, 65, 10.0, {}) == 1                   # N above 64
+    assert f(one, 64, 64, 31, 10.0, dict(match_mode="gcp")) == 1
+    assert f(one, 7, 64, 31, 10.0, {}) == 1                    # smaller than a patch
+    assert f(one, 9, 9, 31, 10.0, dict(K=8, window=3)) == 1    # fewer than K candidates
+    assert f(one, 8192, 8192, 64, 10.0, {}) == 2               # H W N reaches 2^31
+
+
+def test_projection_rejects_bad_arguments_on_the_host():
+    lib = H.load_library()
+    four, sixteen = ctypes.c_void_p(4), ctypes.c_void_p(16)
+    f = lambda img, Hh, Wd, C, pos, n, basis=sixteen, coef=sixteen: lib.htsvd_project_patches(
+        img, Hh, Wd, C, pos, n, basis, coef, None, None)
+    assert f(four, 24, 24, 2, four, 4) == 1                    # C not 1 or 3
+    assert f(four, 7, 24, 3, four, 4) == 1                     # smaller than a patch
+    assert f(four, 24, 24, 3, four, -1) == 1                   # negative count
+    assert f(four, 24, 24, 3, four, 0) == 0                    # nothing to do: no device work
+    assert f(None, 24, 24, 3, four, 4) == 1                    # no image
+    assert f(four, 24, 24, 3, four, 4, None) == 1              # no bases
+    assert f(four, 24, 24, 3, None, 4) == 1                    # no positions, and not every corner
+    assert f(ctypes.c_void_p(5), 24, 24, 3, four, 4) == 1      # image not 4-byte aligned
+    assert f(four, 24, 24, 3, four, 4, coef=ctypes.c_void_p(20)) == 1    # coefficients not 16-byte aligned
