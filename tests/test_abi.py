@@ -252,3 +252,30 @@ def test_projection_rejects_bad_arguments_on_the_host():
     assert f(four, 24, 24, 3, None, 4) == 1                    # no positions, and not every corner
     assert f(ctypes.c_void_p(5), 24, 24, 3, four, 4) == 1      # image not 4-byte aligned
     assert f(four, 24, 24, 3, four, 4, coef=ctypes.c_void_p(20)) == 1    # coefficients not 16-byte aligned
+
+
+def test_estimate_sigma_f32_and_vjp_refuse_bad_arguments_on_the_host():
+    lib = H.load_library()
+    one = ctypes.c_void_p(1)
+    cp = H.HtsvdParams().c()
+    s = ctypes.c_double()
+    assert lib.htsvd_estimate_sigma(None, 64, 64, 3, ctypes.byref(cp), ctypes.byref(s), None) == 1
+    assert lib.htsvd_estimate_sigma(one, 64, 64, 3, ctypes.byref(cp), None, None) == 1
+    assert lib.htsvd_estimate_sigma(one, 64, 64, 2, ctypes.byref(cp), ctypes.byref(s), None) == 1
+    assert lib.htsvd_estimate_sigma(one, 7, 64, 3, ctypes.byref(cp), ctypes.byref(s), None) == 1
+    f32 = lambda x, Hh, C, prm=None, out=one: lib.htsvd_denoise_f32(
+        x, Hh, 64, C, 10.0, ctypes.byref(H.HtsvdParams.of(prm).c()), None, out, None, None)
+    assert f32(None, 64, 3) == 1
+    assert f32(one, 64, 3, out=None) == 1
+    assert f32(one, 64, 2) == 1
+    assert f32(one, 64, 3, dict(K=12)) == 1
+    assert f32(one, 64, 3, dict(ps=4)) == 2
+    vjp = lambda sigma, x=one, idx=one, out=one, g=one, gx=one, C=3: lib.htsvd_denoise_vjp(
+        x, 64, 64, C, sigma, ctypes.byref(cp), idx, None, out, g, gx, None, None)
+    assert vjp(10.0, x=None) == 1
+    assert vjp(10.0, idx=None) == 1
+    assert vjp(10.0, out=None) == 1
+    assert vjp(10.0, g=None) == 1
+    assert vjp(10.0, gx=None) == 1
+    assert vjp(-1.0) == 1                       # the forward's sigma must be passed
+    assert vjp(10.0, C=2) == 1
