@@ -43,7 +43,11 @@ class HtsvdParams:
         if isinstance(p, HtsvdParams):
             return p
         names = {f.name for f in fields(HtsvdParams)}
-        return HtsvdParams(**{k: v for k, v in dict(p).items() if k in names})
+        d = dict(p)
+        unknown = sorted(set(d) - names)
+        if unknown:                       # a misspelt parameter would otherwise fall back to its default
+            raise ValueError(f"unknown parameters {unknown}; known: {sorted(names)}")
+        return HtsvdParams(**d)
 
     def c(self) -> _lib.CParams:
         cp = _lib.CParams()

@@ -279,3 +279,11 @@ def test_estimate_sigma_f32_and_vjp_refuse_bad_arguments_on_the_host():
     assert vjp(10.0, gx=None) == 1
     assert vjp(-1.0) == 1                       # the forward's sigma must be passed
     assert vjp(10.0, C=2) == 1
+
+
+def test_parameters_refuse_unknown_names():
+    """A misspelt parameter raises instead of silently taking its default."""
+    with pytest.raises(ValueError, match="unknown parameters"):
+        H.HtsvdParams.of(dict(windw=5))
+    assert H.HtsvdParams.of(dict(window=5, K=8, tile=4, strict_basis=True)).window == 5
+    assert H.HtsvdParams.of(dict(H.VOLUME_DEFAULTS)).ps == 4
