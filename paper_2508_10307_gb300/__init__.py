@@ -53,6 +53,9 @@ class HtsvdParams:
         cp = _lib.CParams()
         cp.ps, cp.stride, cp.window, cp.K = self.ps, self.stride, self.window, self.K
         cp.tau_mult = float(self.tau_mult)
+        if self.match_mode not in _MATCH or self.agg_mode not in _AGG:
+            raise ValueError(f"match_mode must be one of {sorted(_MATCH)} and agg_mode one of {sorted(_AGG)}, "
+                             f"got {self.match_mode!r} and {self.agg_mode!r}")
         cp.match_mode = _MATCH[self.match_mode]
         cp.gcp_gamma = float(self.gcp_gamma)
         cp.agg_mode = _AGG[self.agg_mode]

@@ -287,3 +287,6 @@ def test_parameters_refuse_unknown_names():
         H.HtsvdParams.of(dict(windw=5))
     assert H.HtsvdParams.of(dict(window=5, K=8, tile=4, strict_basis=True)).window == 5
     assert H.HtsvdParams.of(dict(H.VOLUME_DEFAULTS)).ps == 4
+    for bad in (dict(match_mode="nonsense"), dict(agg_mode="median")):
+        with pytest.raises(ValueError, match="match_mode must be one of"):
+            H.HtsvdParams.of(bad).c()
