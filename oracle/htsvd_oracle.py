@@ -45,7 +45,7 @@ Readings where the paper is silent or ambiguous:
      r* = max{r : mean(l_1..r) <= 1.02 median(l_1..r)}, sigma = sqrt(mean(l_1..r*)).
   R12 adaptive adjustment: groups of every 8th reference per axis; rank
      a = 1 + #{f : lambda_f < lambda_{K/2}}; majority of a <= gamma_rank divides
-     sigma by beta.
+     sigma by beta; gamma_rank defaults to 13 K / 32 rounded half up (13 at K = 32).
   R13 float inputs: matching, bases and sigma use q = clip(rint(x)); the
      transforms use x.
   R14 vector-Jacobian product: grouping, bases, tau and masks held fixed (masks
@@ -126,7 +126,7 @@ class Params:
     agg_mode: str = "uniform"      # uniform | sparsity
     adapt: bool = False            # Sec. III-D adjustment
     beta: float = 1.2
-    rank_gamma: int = 0            # 0 -> round(13 K / 32)
+    rank_gamma: int = 0            # 0 -> 13 K / 32 rounded half up (reading R12)
     strict_basis: bool = False     # raise DegenerateBasis when a basis slice has coinciding eigenvalues
 
     @staticmethod
